@@ -1,0 +1,255 @@
+/*
+ * nurbs_splat.h -- C ABI of the NURBS Splatting hot path (sm_103a).
+ *
+ * The path turns planar NURBS curves into isotropic Gaussians and splats them,
+ * forward and backward:
+ *
+ *   nurbs_sample    curves -> Gaussians: contour samples along open and closed
+ *                   strokes (§3.2, Eq. 1-5) and SDF-modulated fill inside
+ *                   closed filled curves (§3.3, Eq. 6-7, Eq. S1-S3)
+ *   splat_forward   Gaussians -> image: tile binning, a sort by (tile, layer,
+ *                   sample) and per-tile front-to-back compositing (§3.4, Eq. 8-9)
+ *   splat_backward  dL/dimage -> gradients of control points, rational weights,
+ *                   knot intervals, widths, colours and opacities (§3.5)
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named in a struct or argument as "device" point to GPU memory
+ *     the caller owns; the library never allocates, frees or keeps them.
+ *   - `stream` is a cudaStream_t passed as void*.  Every call only enqueues
+ *     work on it and returns without synchronising, except ns_poll_status.
+ *   - Scalar arguments are checked on the host: a bad one returns
+ *     NS_ERR_INVALID_ARG before anything is enqueued, and ns_last_error()
+ *     says which.  Per-curve data lives on the device and is checked there:
+ *     a bad curve emits no Gaussians and raises a device status that
+ *     ns_poll_status reports.  Nothing aborts, traps or waits without bound.
+ *   - Sizes that depend on the data (Gaussians, boundary points, tile pairs)
+ *     are bounded by the capacities in ns_capacity.  Work beyond a capacity
+ *     is dropped (never written out of bounds) and NS_ERR_CAPACITY is raised
+ *     with the size that would have been needed.
+ *   - Coordinates are pixels; pixel (x, y) is sampled at (x + 1/2, y + 1/2);
+ *     y grows downwards.  Images are float32 [n_scenes, height, width, channels].
+ */
+#ifndef NURBS_SPLAT_H
+#define NURBS_SPLAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NS_OK = 0,
+  NS_ERR_INVALID_ARG = 1,   /* host-side argument check failed */
+  NS_ERR_CAPACITY = 2,      /* a data-dependent size exceeded its capacity */
+  NS_ERR_INVALID_CURVE = 3, /* a curve's degree, key count or interval count is inconsistent */
+  NS_ERR_CUDA = 4           /* a CUDA launch or copy failed */
+} ns_status;
+
+#define NS_CLOSED 1 /* curve flag: closed (periodic) curve */
+#define NS_FILLED 2 /* curve flag: closed curve whose interior is filled */
+#define NS_MAX_DEGREE 5
+
+/*
+ * A batch of scenes and their curves (§3.1).  All scenes share one image size.
+ * Curves are grouped by scene and listed back to front inside a scene
+ * (painter's order: the last curve of a scene is in front).
+ *
+ * Key points are the learnable parameters (§3.1): an open curve of degree p
+ * with n_k key points uses them as its n_k control points and stores n_k - p
+ * knot intervals; a closed curve wraps the last ceil(p/2) and first floor(p/2)
+ * key points into n_k + p control points and stores n_k core knot intervals.
+ * The width s is the control points' third coordinate (§3.1, last paragraph).
+ */
+typedef struct {
+  int32_t n_scenes, n_curves, n_keys, n_taus;
+  int32_t height, width, channels;     /* channels: 1 or 3 (first colour components) */
+  const int32_t* scene_curve_offset;   /* device [n_scenes+1]; NULL: one scene holds all curves */
+  const int32_t* degree;               /* device [n_curves], 1..NS_MAX_DEGREE */
+  const int32_t* flags;                /* device [n_curves], NS_CLOSED | NS_FILLED */
+  const int32_t* key_offset;           /* device [n_curves+1], CSR into key */
+  const int32_t* tau_offset;           /* device [n_curves+1], CSR into tau */
+  const float* key;                    /* device [n_keys*4]: {x, y, s, w} per key point */
+  const float* tau;                    /* device [n_taus]: knot intervals, >= 0 */
+  const float* color;                  /* device [n_curves*4]: {r, g, b, opacity} */
+} ns_curves;
+
+/* Sampling settings (§3.2, §3.3; defaults of Table S1 from ns_default_sample_params). */
+typedef struct {
+  float delta_c;    /* contour density: M = ceil(delta_c L) samples (§3.2) */
+  float rho;        /* sigma = s / rho for contours, eta h / rho for fills (Eq. 5, 6) */
+  float delta_b;    /* boundary density: ceil(delta_b L) polyline points (§3.3) */
+  float h;          /* fill grid step in pixels (Eq. 6) */
+  float eta;        /* fill coverage factor (Eq. 6) */
+  float gamma;      /* sigmoid sharpness of the fill opacity (Eq. 7) */
+  float pad_frac;   /* padding of the boundary's box, fraction of its extent */
+  int32_t kappa;    /* endpoint replicas of open curves (§3.2, last paragraph) */
+  int32_t nl_mult;  /* N_L = nl_mult * max(width, height) arc-length nodes (Eq. 3) */
+  int32_t fill_rule;/* 0: inside iff winding number > 0.5 (Eq. S3); 1: nonzero */
+} ns_sample_params;
+
+/* Rasterizer settings (§3.4). */
+typedef struct {
+  int32_t tile;     /* tile edge in pixels: 16 */
+  float k_sigma;    /* a Gaussian is binned to the tiles of mu +- k_sigma sigma */
+  float alpha_min;  /* a Gaussian with alpha < alpha_min at a pixel is skipped there */
+  float alpha_max;  /* alpha is capped at alpha_max (keeps 1 - alpha > 0) */
+  float t_min;      /* compositing stops before transmittance would drop below t_min */
+  float bg[3];      /* background colour behind the residual transmittance (§3.4) */
+} ns_raster_params;
+
+/* Capacities that bound the data-dependent sizes. */
+typedef struct {
+  int64_t gaussians;  /* Gaussian records */
+  int64_t pairs;      /* (tile, Gaussian) pairs */
+  int64_t boundary;   /* boundary polyline points of filled curves */
+} ns_capacity;
+
+/*
+ * A Gaussian set, caller-owned device memory of `capacity` records.  Records
+ * are stored front to back inside each scene: scene ascending, then curve
+ * from the last (front) to the first, then sample index ascending.
+ */
+typedef struct {
+  int64_t capacity;
+  float* rec;       /* device [capacity*4]: {mu_x, mu_y, sigma, opacity} */
+  int32_t* curve;   /* device [capacity]: owning curve (selects colour and scene) */
+  int32_t* aux;     /* device [capacity]: fills: nearest boundary segment i*, as
+                       i* (inside) or ~i* (outside); contours: -1 */
+  int32_t* count;   /* device scalar: records in use */
+} ns_gaussians;
+
+/* Gradient outputs, caller-owned device memory, accumulated into (the caller
+ * zeroes them, or passes zero_outputs = 1 to splat_backward). */
+typedef struct {
+  float* dkey;      /* device [n_keys*4]: dL/d{x, y, s, w} */
+  float* dtau;      /* device [n_taus] */
+  float* dcolor;    /* device [n_curves*4]: dL/d{r, g, b, opacity} */
+} ns_curve_grads;
+
+/* What ns_poll_status reads back. */
+typedef struct {
+  int32_t status;        /* ns_status raised on the device (first one wins) */
+  int32_t bad_curve;     /* first curve that failed validation, or -1 */
+  int64_t gaussians;     /* Gaussians the last nurbs_sample needed */
+  int64_t pairs;         /* tile pairs the last splat_forward needed */
+  int64_t boundary;      /* boundary points the last nurbs_sample needed */
+  int64_t fill_culled;   /* fill Gaussians with opacity below alpha_min (bin no tile) */
+} ns_report;
+
+ns_sample_params ns_default_sample_params(void);
+ns_raster_params ns_default_raster_params(void);
+
+/*
+ * Bytes of device workspace for a batch with these sizes.  The same workspace
+ * must be passed to nurbs_sample, splat_forward and splat_backward of one
+ * step: it carries the per-curve plan (knot vectors, counts, offsets, boundary
+ * polylines), the sorted tile lists and the per-pixel state that the backward
+ * pass reuses.  The caller allocates it (256-byte aligned); its contents need
+ * no initialisation.  Returns 0 for invalid sizes (see ns_last_error).
+ */
+size_t ns_workspace_size(const ns_curves* curves, const ns_capacity* cap,
+                         const ns_raster_params* raster);
+
+/*
+ * Curves -> Gaussians (§3.1-§3.3).  Per curve: knot vector from the intervals
+ * (§3.1), arc length by N_L-node midpoint quadrature of |C'| (Eq. 2-3), then
+ *   open or closed stroke: M = ceil(delta_c L) samples uniform in the domain
+ *     [u_p, u_{m-p}] (open: both ends included, plus kappa copies of the first
+ *     and last centre; closed: the start is not repeated); centre C_xy(u_j)
+ *     evaluated span-locally (Eq. 4), sigma = C_s(u_j) / rho, opacity o (Eq. 5);
+ *   filled closed curve: ceil(delta_b L) boundary points, their box padded by
+ *     pad_frac of its extent and clipped to the canvas, a grid of step h with
+ *     points at origin + (i + 1/2) h; per point sigma = eta h / rho and opacity
+ *     o * sigmoid(gamma / h * sdf), sdf = sign(winding) * distance to the
+ *     closed polyline (Eq. 6-7, S1-S3).
+ * Writes out->rec/curve/aux/count (count = Gaussians emitted, at most
+ * out->capacity; see ns_report.gaussians for the size needed).
+ */
+ns_status nurbs_sample(const ns_curves* curves, const ns_sample_params* sp,
+                       const ns_capacity* cap, const ns_gaussians* out,
+                       void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Gaussians -> image (§3.4, Eq. 8-9).  Bins each Gaussian to the tiles
+ * overlapped by mu +- k_sigma sigma (float32 rule: floor((mu -+ k_sigma*sigma)
+ * * (1/tile)), each operation rounded to nearest), sorts the (tile, Gaussian)
+ * pairs by (tile, layer, sample), and composites each pixel front to back:
+ *   alpha = min(alpha_max, o exp(-|x - mu|^2 / (2 sigma^2))),
+ *   skipped where alpha < alpha_min, stopping before T would drop below t_min,
+ *   image = sum c alpha T + T_final bg.
+ * `g` is usually nurbs_sample's output but may be any set in the documented
+ * order.  image: device [n_scenes*height*width*channels], overwritten.
+ */
+ns_status splat_forward(const ns_curves* curves, const ns_gaussians* g,
+                        const ns_raster_params* rp, const ns_capacity* cap,
+                        float* image, void* workspace, size_t workspace_bytes,
+                        void* stream);
+
+/*
+ * dL/dimage -> gradients (§3.5).  Walks each tile's list back to front from
+ * the last Gaussian each pixel composited, recovering the transmittance by
+ * division rather than storing it, and accumulates per-Gaussian gradients of
+ * (mu, sigma, opacity, colour).  If `out` is non-NULL these are chained
+ * through the sampling of nurbs_sample (same workspace, same settings) into
+ * the key points, knot intervals, colours and opacities; counts, spans, grid
+ * placement, nearest segments and winding signs are held fixed.
+ *   dL_dimage: device, same layout as the image.
+ *   dgauss: device [g->capacity*8] or NULL: {dmu_x, dmu_y, dsigma, dopacity,
+ *     dr, dg, db, 0} per Gaussian, zeroed and written by this call.
+ *   zero_outputs: 1 zeroes *out before accumulating, 0 adds to it.
+ */
+ns_status splat_backward(const ns_curves* curves, const ns_gaussians* g,
+                         const ns_sample_params* sp, const ns_raster_params* rp,
+                         const ns_capacity* cap, const float* dL_dimage,
+                         float* dgauss, const ns_curve_grads* out, int32_t zero_outputs,
+                         void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * L2 image loss (Eq. 10 with an L2 image term): loss = mean((image - target)^2)
+ * over n values; dL_dimage = 2 (image - target) / n.  loss: device scalar,
+ * overwritten.  dL_dimage may be NULL.
+ */
+ns_status ns_mse_loss(const float* image, const float* target, int64_t n,
+                      float* dL_dimage, float* loss, void* stream);
+
+/*
+ * One Adam step on n parameters in place, then a clamp of each value to
+ * [lo, hi] (the paper clamps weights to [0.01, 10] and knot intervals to
+ * [0, 2], Table S1).  m, v: device moment buffers of n floats.  step >= 1.
+ */
+ns_status ns_adam_step(float* param, const float* grad, float* m, float* v, int64_t n,
+                       float lr, float beta1, float beta2, float eps, int32_t step,
+                       float lo, float hi, void* stream);
+
+/* Synchronises `stream`, reads the device status and counters. */
+ns_status ns_poll_status(void* workspace, ns_report* report, void* stream);
+
+/* Clears the device status word (enqueued on `stream`). */
+ns_status ns_clear_status(void* workspace, void* stream);
+
+/*
+ * Internal arrays of a workspace, for tests and tools: copies `bytes` bytes of
+ * array `which` to device memory `dst` (enqueued on `stream`).
+ *   0 sorted pair tile ids (uint32), 1 sorted pair Gaussian ids (uint32),
+ *   2 tile ranges (int32 [n_tiles*2], [start, end) per tile),
+ *   3 per-curve plan records, 64 bytes each: float32 {L, a, b, x0, y0} (arc
+ *     length, parameter domain, fill grid origin) then int32 {kind (0 invalid,
+ *     1 open, 2 closed stroke, 3 filled), M (contour samples, or boundary
+ *     points of a fill), Gaussians, nx, ny, first Gaussian, first boundary
+ *     point, first task, scene, 0, 0},
+ *   4 boundary points (float32 pairs), 5 per-pixel final transmittance,
+ *   6 per-pixel composited-list length (int32)
+ */
+ns_status ns_workspace_copy(void* workspace, const ns_curves* curves, const ns_capacity* cap,
+                            const ns_raster_params* rp, int32_t which, void* dst,
+                            size_t bytes, void* stream);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* ns_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NURBS_SPLAT_H */

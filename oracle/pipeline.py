@@ -132,3 +132,32 @@ def render_records(scene, rec, curve, mode="tiled", return_flags=False):
         img, fl = rs.render_tiled(*args, return_flags=True)
         return img.numpy(), fl.numpy()
     return rs.render_tiled(*args).numpy()
+
+
+def _records_g(scene, rec, curve, requires_grad=False):
+    cs = scene.curve_scene()
+    rec64 = torch.tensor(rec.astype(np.float64), requires_grad=requires_grad)
+    off = scene.scene_curve_offset
+    return rec64, dict(mu=rec64[:, 0:2], sigma=rec64[:, 2], o=rec64[:, 3],
+                       curve=torch.as_tensor(curve.astype(np.int64)), sample=torch.arange(rec.shape[0]),
+                       layer=torch.as_tensor((off[cs[curve] + 1] - 1 - curve).astype(np.int64)),
+                       scene=torch.as_tensor(cs[curve].astype(np.int64)))
+
+
+def pairs_records(scene, rec, curve):
+    """Sorted (tile, Gaussian) pairs of a given FP32 Gaussian set in the
+    documented order; Gaussian ids are positions in that set."""
+    _, g = _records_g(scene, rec, curve)
+    r = scene.raster
+    return rs.sorted_pairs(g, scene.height, scene.width, int(r["tile"]), r["k_sigma"], r["alpha_min"],
+                           scene.n_scenes)
+
+
+def record_grads(scene, rec, curve, dimage):
+    """Gradient of sum(image * dimage) with respect to each record's
+    (mu_x, mu_y, sigma, o) and each curve's colour, for a given FP32 set."""
+    rec64, g = _records_g(scene, rec, curve, requires_grad=True)
+    color_t = torch.tensor(scene.color.astype(np.float64), requires_grad=True)
+    img = rs.render_tiled(g, color_t, scene.n_scenes, scene.height, scene.width, scene.channels, scene.raster)
+    (img * torch.as_tensor(dimage, dtype=DT)).sum().backward()
+    return rec64.grad.numpy(), color_t.grad.numpy()

@@ -1,0 +1,119 @@
+"""ctypes binding of the C ABI in include/nurbs_splat.h (argument marshalling only).
+
+Every entry point keeps its C name.  Structures mirror the header field by
+field.  Loading fails loudly when the shared library has not been built: there
+is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnurbs_splat.so")
+
+NS_OK, NS_ERR_INVALID_ARG, NS_ERR_CAPACITY, NS_ERR_INVALID_CURVE, NS_ERR_CUDA = range(5)
+STATUS_NAMES = {0: "NS_OK", 1: "NS_ERR_INVALID_ARG", 2: "NS_ERR_CAPACITY", 3: "NS_ERR_INVALID_CURVE",
+                4: "NS_ERR_CUDA"}
+NS_CLOSED, NS_FILLED = 1, 2
+
+_p = C.c_void_p
+
+
+class NsCurves(C.Structure):
+    _fields_ = [("n_scenes", C.c_int32), ("n_curves", C.c_int32), ("n_keys", C.c_int32), ("n_taus", C.c_int32),
+                ("height", C.c_int32), ("width", C.c_int32), ("channels", C.c_int32),
+                ("scene_curve_offset", _p), ("degree", _p), ("flags", _p), ("key_offset", _p),
+                ("tau_offset", _p), ("key", _p), ("tau", _p), ("color", _p)]
+
+
+class NsSampleParams(C.Structure):
+    _fields_ = [("delta_c", C.c_float), ("rho", C.c_float), ("delta_b", C.c_float), ("h", C.c_float),
+                ("eta", C.c_float), ("gamma", C.c_float), ("pad_frac", C.c_float), ("kappa", C.c_int32),
+                ("nl_mult", C.c_int32), ("fill_rule", C.c_int32)]
+
+
+class NsRasterParams(C.Structure):
+    _fields_ = [("tile", C.c_int32), ("k_sigma", C.c_float), ("alpha_min", C.c_float), ("alpha_max", C.c_float),
+                ("t_min", C.c_float), ("bg", C.c_float * 3)]
+
+
+class NsCapacity(C.Structure):
+    _fields_ = [("gaussians", C.c_int64), ("pairs", C.c_int64), ("boundary", C.c_int64)]
+
+
+class NsGaussians(C.Structure):
+    _fields_ = [("capacity", C.c_int64), ("rec", _p), ("curve", _p), ("aux", _p), ("count", _p)]
+
+
+class NsCurveGrads(C.Structure):
+    _fields_ = [("dkey", _p), ("dtau", _p), ("dcolor", _p)]
+
+
+class NsReport(C.Structure):
+    _fields_ = [("status", C.c_int32), ("bad_curve", C.c_int32), ("gaussians", C.c_int64), ("pairs", C.c_int64),
+                ("boundary", C.c_int64), ("fill_culled", C.c_int64)]
+
+
+# name -> (restype, argtypes); the declarations of include/nurbs_splat.h
+SIGNATURES = {
+    "ns_default_sample_params": (NsSampleParams, []),
+    "ns_default_raster_params": (NsRasterParams, []),
+    "ns_workspace_size": (C.c_size_t, [C.POINTER(NsCurves), C.POINTER(NsCapacity), C.POINTER(NsRasterParams)]),
+    "nurbs_sample": (C.c_int, [C.POINTER(NsCurves), C.POINTER(NsSampleParams), C.POINTER(NsCapacity),
+                               C.POINTER(NsGaussians), _p, C.c_size_t, _p]),
+    "splat_forward": (C.c_int, [C.POINTER(NsCurves), C.POINTER(NsGaussians), C.POINTER(NsRasterParams),
+                                C.POINTER(NsCapacity), _p, _p, C.c_size_t, _p]),
+    "splat_backward": (C.c_int, [C.POINTER(NsCurves), C.POINTER(NsGaussians), C.POINTER(NsSampleParams),
+                                 C.POINTER(NsRasterParams), C.POINTER(NsCapacity), _p, _p,
+                                 C.POINTER(NsCurveGrads), C.c_int32, _p, C.c_size_t, _p]),
+    "ns_mse_loss": (C.c_int, [_p, _p, C.c_int64, _p, _p, _p]),
+    "ns_adam_step": (C.c_int, [_p, _p, _p, _p, C.c_int64, C.c_float, C.c_float, C.c_float, C.c_float,
+                               C.c_int32, C.c_float, C.c_float, _p]),
+    "ns_poll_status": (C.c_int, [_p, C.POINTER(NsReport), _p]),
+    "ns_clear_status": (C.c_int, [_p, _p]),
+    "ns_workspace_copy": (C.c_int, [_p, C.POINTER(NsCurves), C.POINTER(NsCapacity), C.POINTER(NsRasterParams),
+                                    C.c_int32, _p, C.c_size_t, _p]),
+    "ns_last_error": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+class NsError(RuntimeError):
+    def __init__(self, fn, status, msg):
+        super().__init__(f"{fn} -> {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def load(path: str = LIB_PATH):
+    """Load the library (once) and declare its signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing "
+                           "(run `python -m paper_2606_31764_b300.build` or __graft_entry__.build())")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(fn_name: str, status: int):
+    if status != NS_OK:
+        raise NsError(fn_name, status, load().ns_last_error().decode())
+
+
+def call(name: str, *args):
+    """Call an entry point that returns ns_status; raise NsError on failure."""
+    st = getattr(load(), name)(*args)
+    check(name, st)
+    return st
+
+
+def exported_symbols():
+    return list(SIGNATURES)

@@ -1,0 +1,292 @@
+// Host side of the C ABI: defaults, workspace layout, status, the L2 loss,
+// the Adam step and the error channel.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <string>
+
+#include "ns_internal.cuh"
+
+namespace ns {
+
+static thread_local std::string g_error;
+
+void set_error(const std::string& msg) { g_error = msg; }
+
+int num_sms() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 148;
+  return n;
+}
+
+static size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+bool make_layout(const ns_curves* c, const ns_capacity* cap, const ns_raster_params* rp, Layout* L) {
+  if (!c || !cap || !rp) {
+    set_error("null curves, capacity or raster parameters");
+    return false;
+  }
+  if (c->n_scenes < 1 || c->n_curves < 0 || c->n_keys < 0 || c->n_taus < 0 || c->height < 1 || c->width < 1 ||
+      (c->channels != 1 && c->channels != 3)) {
+    set_error("invalid sizes: need n_scenes >= 1, height, width >= 1, channels 1 or 3");
+    return false;
+  }
+  if (c->n_curves > 0 && (!c->degree || !c->flags || !c->key_offset || !c->tau_offset || !c->key || !c->tau ||
+                          !c->color)) {
+    set_error("curve tables must be non-null");
+    return false;
+  }
+  if (c->n_scenes > 1 && !c->scene_curve_offset) {
+    set_error("scene_curve_offset is required with more than one scene");
+    return false;
+  }
+  if (cap->gaussians < 0 || cap->pairs < 0 || cap->boundary < 0 || cap->gaussians >= (1LL << 31) ||
+      cap->pairs >= (1LL << 31) || cap->boundary >= (1LL << 31)) {
+    set_error("capacities must lie in [0, 2^31)");
+    return false;
+  }
+  if (rp->tile != 16) {
+    set_error("tile must be 16");
+    return false;
+  }
+  L->S = c->n_scenes;
+  L->H = c->height;
+  L->W = c->width;
+  L->C = c->channels;
+  L->tile = rp->tile;
+  L->tiles_x = (c->width + rp->tile - 1) / rp->tile;
+  L->tiles_y = (c->height + rp->tile - 1) / rp->tile;
+  const long long nt = (long long)L->S * L->tiles_x * L->tiles_y;
+  if (nt >= (1LL << 31)) {
+    set_error("too many tiles");
+    return false;
+  }
+  L->n_tiles = int(nt);
+  L->n_pix = (int64_t)L->S * L->H * L->W;
+  L->nc = c->n_curves;
+  L->nk = c->n_keys;
+  L->nt = c->n_taus;
+  L->gcap = cap->gaussians;
+  L->pcap = cap->pairs;
+  L->bcap = cap->boundary;
+  L->bin_blocks = (L->gcap + kBinItems - 1) / kBinItems;
+  L->sort_blocks = (L->pcap + kSortItems - 1) / kSortItems;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t r = o;
+    o = align_up(o + bytes);
+    return r;
+  };
+  const size_t nkn = (size_t)L->nt + (size_t)kKnotPad * L->nc;
+  L->o_state = take(sizeof(DevState));
+  L->o_plan = take(sizeof(CurvePlan) * (size_t)L->nc);
+  L->o_knots = take(sizeof(float) * nkn);
+  L->o_dknots = take(sizeof(float) * nkn);
+  L->o_order = take(sizeof(int) * (size_t)L->nc);
+  L->o_curve_scene = take(sizeof(int) * (size_t)L->nc);
+  L->o_bpts = take(sizeof(float2) * (size_t)L->bcap);
+  L->o_dbpts = take(sizeof(float2) * (size_t)L->bcap);
+  L->o_bsum = take(sizeof(int) * (size_t)(L->bin_blocks + 1));
+  L->o_k0 = take(sizeof(uint32_t) * (size_t)L->pcap);
+  L->o_v0 = take(sizeof(uint32_t) * (size_t)L->pcap);
+  L->o_k1 = take(sizeof(uint32_t) * (size_t)L->pcap);
+  L->o_v1 = take(sizeof(uint32_t) * (size_t)L->pcap);
+  L->o_hist = take(sizeof(uint32_t) * 256 * (size_t)(L->sort_blocks + 1));
+  L->o_ranges = take(sizeof(int2) * (size_t)L->n_tiles);
+  L->o_T = take(sizeof(float) * (size_t)L->n_pix);
+  L->o_nlast = take(sizeof(int) * (size_t)L->n_pix);
+  L->o_dgauss = take(sizeof(float) * 8 * (size_t)L->gcap);
+  L->total = o;
+  return true;
+}
+
+int sorted_buffer(const Layout& L);
+
+__global__ void k_reset_state(DevState* st) {
+  st->status = 0;
+  st->bad_curve = -1;
+  st->n_chunks = 0;
+  st->g_total = st->b_total = st->pair_total = st->culled = 0;
+  st->g_count = st->pair_count = st->b_count = 0;
+}
+
+void launch_reset_state(DevState* st, cudaStream_t s) { k_reset_state<<<1, 1, 0, s>>>(st); }
+
+__global__ void __launch_bounds__(256) k_mse(const float* __restrict__ a, const float* __restrict__ b, long long n,
+                                             float* __restrict__ grad, float* loss) {
+  __shared__ float red[8];
+  const float scale = 2.f / float(n);
+  float acc = 0.f;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float d = a[i] - b[i];
+    acc = fmaf(d, d, acc);
+    if (grad) grad[i] = scale * d;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.f;
+    for (int w = 0; w < 8; ++w) s += red[w];
+    atomicAdd(loss, s / float(n));
+  }
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       long long n, float lr, float b1, float b2, float eps, float c1, float c2, float lo, float hi) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float mh = mi / c1, vh = vi / c2;
+    const float x = p[i] - lr * mh / (sqrtf(vh) + eps);
+    p[i] = fminf(fmaxf(x, lo), hi);
+  }
+}
+
+}  // namespace ns
+
+using namespace ns;
+
+extern "C" {
+
+ns_sample_params ns_default_sample_params(void) {
+  ns_sample_params p;
+  p.delta_c = 10.f;   // Table S1
+  p.rho = 2.f;
+  p.delta_b = 0.5f;
+  p.h = 1.f;
+  p.eta = 1.5f;
+  p.gamma = 5.f;
+  p.pad_frac = 0.1f;  // padding "proportional to the extent": 10 %
+  p.kappa = 4;
+  p.nl_mult = 3;
+  p.fill_rule = 0;
+  return p;
+}
+
+ns_raster_params ns_default_raster_params(void) {
+  ns_raster_params r;
+  r.tile = 16;
+  r.k_sigma = 3.5f;
+  r.alpha_min = 1.f / 255.f;
+  r.alpha_max = 0.99f;
+  r.t_min = 1e-4f;
+  r.bg[0] = r.bg[1] = r.bg[2] = 1.f;
+  return r;
+}
+
+size_t ns_workspace_size(const ns_curves* curves, const ns_capacity* cap, const ns_raster_params* raster) {
+  Layout L;
+  if (!make_layout(curves, cap, raster, &L)) return 0;
+  return L.total;
+}
+
+ns_status ns_poll_status(void* ws, ns_report* r, void* stream) {
+  if (!ws || !r) {
+    set_error("ns_poll_status: null argument");
+    return NS_ERR_INVALID_ARG;
+  }
+  DevState st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(&st, ws, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    set_error(std::string("ns_poll_status: ") + cudaGetErrorString(cudaGetLastError()));
+    return NS_ERR_CUDA;
+  }
+  r->status = st.status;
+  r->bad_curve = st.bad_curve;
+  r->gaussians = (int64_t)st.g_total;
+  r->pairs = (int64_t)st.pair_total;
+  r->boundary = (int64_t)st.b_total;
+  r->fill_culled = (int64_t)st.culled;
+  return NS_OK;
+}
+
+ns_status ns_clear_status(void* ws, void* stream) {
+  if (!ws) {
+    set_error("ns_clear_status: null workspace");
+    return NS_ERR_INVALID_ARG;
+  }
+  k_reset_state<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<DevState*>(ws));
+  return cudaGetLastError() == cudaSuccess ? NS_OK : NS_ERR_CUDA;
+}
+
+ns_status ns_mse_loss(const float* image, const float* target, int64_t n, float* dL, float* loss, void* stream) {
+  if (!image || !target || !loss || n <= 0) {
+    set_error("ns_mse_loss: null argument or n <= 0");
+    return NS_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaMemsetAsync(loss, 0, sizeof(float), s);
+  const long long blocks = (n + 255) / 256;
+  const int grid = int(blocks < num_sms() * 8 ? blocks : num_sms() * 8);
+  k_mse<<<grid, 256, 0, s>>>(image, target, n, dL, loss);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string("ns_mse_loss: ") + cudaGetErrorString(e));
+    return NS_ERR_CUDA;
+  }
+  return NS_OK;
+}
+
+ns_status ns_adam_step(float* param, const float* grad, float* m, float* v, int64_t n, float lr, float beta1,
+                       float beta2, float eps, int32_t step, float lo, float hi, void* stream) {
+  if (!param || !grad || !m || !v || n < 0 || step < 1 || !(lo <= hi)) {
+    set_error("ns_adam_step: invalid argument");
+    return NS_ERR_INVALID_ARG;
+  }
+  if (n == 0) return NS_OK;
+  const float c1 = 1.f - powf(beta1, float(step));
+  const float c2 = 1.f - powf(beta2, float(step));
+  const long long blocks = (n + 255) / 256;
+  const int grid = int(blocks < num_sms() * 8 ? blocks : num_sms() * 8);
+  k_adam<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(param, grad, m, v, n, lr, beta1, beta2, eps, c1, c2,
+                                                               lo, hi);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string("ns_adam_step: ") + cudaGetErrorString(e));
+    return NS_ERR_CUDA;
+  }
+  return NS_OK;
+}
+
+ns_status ns_workspace_copy(void* ws, const ns_curves* curves, const ns_capacity* cap, const ns_raster_params* rp,
+                            int32_t which, void* dst, size_t bytes, void* stream) {
+  Layout L;
+  if (!ws || !dst || !make_layout(curves, cap, rp, &L)) {
+    if (!ws || !dst) set_error("ns_workspace_copy: null argument");
+    return NS_ERR_INVALID_ARG;
+  }
+  const int sb = sorted_buffer(L);
+  size_t off = 0, avail = 0;
+  switch (which) {
+    case 0: off = sb ? L.o_k1 : L.o_k0; avail = 4 * (size_t)L.pcap; break;
+    case 1: off = sb ? L.o_v1 : L.o_v0; avail = 4 * (size_t)L.pcap; break;
+    case 2: off = L.o_ranges; avail = 8 * (size_t)L.n_tiles; break;
+    case 3: off = L.o_plan; avail = sizeof(CurvePlan) * (size_t)L.nc; break;
+    case 4: off = L.o_bpts; avail = 8 * (size_t)L.bcap; break;
+    case 5: off = L.o_T; avail = 4 * (size_t)L.n_pix; break;
+    case 6: off = L.o_nlast; avail = 4 * (size_t)L.n_pix; break;
+    default:
+      set_error("ns_workspace_copy: unknown array");
+      return NS_ERR_INVALID_ARG;
+  }
+  if (bytes > avail) {
+    set_error("ns_workspace_copy: more bytes than the array holds");
+    return NS_ERR_INVALID_ARG;
+  }
+  if (bytes && cudaMemcpyAsync(dst, static_cast<char*>(ws) + off, bytes, cudaMemcpyDeviceToDevice,
+                               static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+    set_error("ns_workspace_copy: copy failed");
+    return NS_ERR_CUDA;
+  }
+  return NS_OK;
+}
+
+const char* ns_last_error(void) { return g_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,397 @@
+// splat_backward: per-Gaussian gradients -> curve parameters (paper §3.5).
+//
+// After the blend adjoint (ns_raster.cu) has accumulated dL/d(mu, sigma,
+// opacity, colour) per Gaussian:
+//   k_chain           persistent over the sampling tasks of nurbs_sample.
+//                     Contour task: per sample, the reverse sweep of the
+//                     span-local Cox-de Boor triangle gives dL/dN, dL/du and
+//                     dL/d(local knots); with C = S/W (Eq. 1) this yields
+//                     dL/dP (x, y, s), dL/dw and, through u = a + t(b - a),
+//                     the domain-end terms.  The task's control-point and knot
+//                     windows are accumulated in shared memory and flushed once.
+//                     Fill task: dL/do_j -> curve opacity (times the sigmoid),
+//                     and dL/dsdf -> the two end points of the nearest segment
+//                     (Eq. 7, S1), accumulated per boundary point in shared memory.
+//   k_chain_boundary  per boundary point: dL/db_i -> control points, weights
+//                     and knots through C(u_i), as for contours.
+//   k_knot_grads      per curve: dL/dU -> dL/dtau by suffix sums over the
+//                     cumulative-sum knot construction; wrapped intervals of
+//                     closed curves fold back onto their core interval (§3.1).
+#include <cuda_runtime.h>
+#include <float.h>
+
+#include "ns_internal.cuh"
+
+namespace ns {
+
+ns_status launch_blend_bwd(const Layout& L, const ns_curves* curves, const ns_gaussians* g,
+                           const ns_raster_params* rp, const float* dimage, float* dgauss, void* ws,
+                           cudaStream_t s);
+bool raster_params_ok(const ns_raster_params* rp);
+
+constexpr int kWin = 1024;   // control points (and knots) per task window in shared memory
+constexpr int kWinB = 2 * kWin;  // boundary points per fill task window (float2, aliases s_cp)
+
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sums v over the block into red[slot] (red must hold 8 warps x nslots).
+__device__ __forceinline__ void block_add(float v, float* red, int slot) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) atomicAdd(&red[slot], v);
+}
+
+// Reverse of one curve point: gC = dL/dC (x, y, s) at parameter u (span i,
+// domain fraction t).  Adds to the control-point and knot accumulators.
+template <int P, class AddCP, class AddKnot>
+__device__ __forceinline__ void curve_point_bwd(const ns_curves& cv, const CurveRef& cr, const float* U, int i,
+                                                float u, float t, const float gC[3], AddCP add_cp,
+                                                AddKnot add_knot, float& dA, float& dB) {
+  Eval<P> e;
+  eval_curve<P>(reinterpret_cast<const float4*>(cv.key), cr, U, i, u, e);
+  const float iw = 1.f / e.W;
+  float gN[P + 1];
+#pragma unroll
+  for (int l = 0; l <= P; ++l) {
+    const float4 q = e.cp[l];
+    const float R = e.t.N[l] * q.w * iw;              // rational basis N w / W
+    const float proj = gC[0] * (q.x - e.C[0]) + gC[1] * (q.y - e.C[1]) + gC[2] * (q.z - e.C[2]);
+    gN[l] = q.w * proj * iw;                            // dL/dN_l
+    add_cp(i - P + l, gC[0] * R, gC[1] * R, gC[2] * R, e.t.N[l] * proj * iw);
+  }
+  float du = 0.f, dU[2 * P];
+#pragma unroll
+  for (int k = 0; k < 2 * P; ++k) dU[k] = 0.f;
+  basis_bwd<P>(e.t, gN, &du, dU);
+#pragma unroll
+  for (int k = 0; k < 2 * P; ++k) add_knot(i - P + 1 + k, dU[k]);
+  dA += du * (1.f - t);   // u = a + t (b - a)
+  dB += du * t;
+}
+
+struct ChainParams {
+  float rho, h, gamma;
+  int kappa;
+};
+
+template <int P>
+__device__ void chain_contour_sample(const ns_curves& cv, const CurveRef& cr, const float* U, const CurvePlan& pl,
+                                     int l, const ChainParams& cp, const float4 g0, float* s_cp, float* s_kn,
+                                     int cp_lo, int kn_lo, bool use_smem, float* dkey, float* dknots, float& dA,
+                                     float& dB) {
+  const float u = contour_u(pl, l, cp.kappa);
+  const float t = contour_t(pl, l, cp.kappa);
+  const int i = find_span(U, P, cr.n, u);
+  const float gC[3] = {g0.x, g0.y, g0.z / cp.rho};
+  auto add_cp = [&](int cpi, float dx, float dy, float ds, float dw) {
+    if (use_smem && cpi >= cp_lo && cpi - cp_lo < kWin) {
+      float* a = s_cp + 4 * (cpi - cp_lo);
+      atomicAdd(a + 0, dx);
+      atomicAdd(a + 1, dy);
+      atomicAdd(a + 2, ds);
+      atomicAdd(a + 3, dw);
+    } else {
+      float* a = dkey + 4 * (long long)(cr.key0 + cp_to_key(cpi, P, cr.closed, cr.nk));
+      atomicAdd(a + 0, dx);
+      atomicAdd(a + 1, dy);
+      atomicAdd(a + 2, ds);
+      atomicAdd(a + 3, dw);
+    }
+  };
+  auto add_knot = [&](int k, float v) {
+    if (use_smem && k >= kn_lo && k - kn_lo < kWin + 2 * kMaxP) atomicAdd(s_kn + (k - kn_lo), v);
+    else atomicAdd(dknots + cr.knot0 + k, v);
+  };
+  curve_point_bwd<P>(cv, cr, U, i, u, t, gC, add_cp, add_knot, dA, dB);
+}
+
+template <int P>
+__device__ __forceinline__ int span_at(const CurveRef& cr, const float* U, float u) {
+  return find_span(U, P, cr.n, u);
+}
+
+__global__ void __launch_bounds__(256) k_chain(ns_curves cv, ChainParams cp, const CurvePlan* __restrict__ plan,
+                                               const int* __restrict__ order, const float* __restrict__ knots,
+                                               const float2* __restrict__ bpts, const DevState* __restrict__ st,
+                                               const float4* __restrict__ rec, const int* __restrict__ gaux,
+                                               const float* __restrict__ dgauss, long long gcap, long long bcap,
+                                               float* dkey, float* dknots, float2* dbpts, float* dcolor) {
+  __shared__ float s_cp[4 * kWin];
+  __shared__ float s_kn[kWin + 2 * kMaxP];
+  __shared__ float s_red[8];
+  __shared__ int s_span[2];
+  float2* s_db = reinterpret_cast<float2*>(s_cp);   // fill tasks reuse the window
+  const int n_tasks = st->n_chunks;
+  const int nc = cv.n_curves;
+  for (int task = blockIdx.x; task < n_tasks; task += gridDim.x) {
+    const int c = curve_of_task(plan, order, nc, task);
+    const CurvePlan pl = plan[c];
+    const CurveRef cr = curve_ref(cv, c);
+    const float* U = knots + cr.knot0;
+    const int l0 = (task - pl.chunk_off) * kChunk;
+    const int l = l0 + threadIdx.x;
+    const long long g = (long long)pl.g_off + l;
+    const bool valid = l < pl.count && g < gcap;
+    __syncthreads();
+    if (threadIdx.x < 8) s_red[threadIdx.x] = 0.f;
+    float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0;
+    if (valid) {
+      g0 = reinterpret_cast<const float4*>(dgauss)[2 * g];
+      g1 = reinterpret_cast<const float4*>(dgauss)[2 * g + 1];
+    }
+    if (pl.kind != kFill) {
+      // window of control points [span(first) - p, span(last)], knots
+      // [span(first) - p + 1, span(last) + p]
+      if (threadIdx.x == 0) {
+        const int lf = l0, ll = min(l0 + kChunk, pl.count) - 1;
+        int sf = 0, sl = 0;
+        NS_DISPATCH_P(cr.p, sf = span_at<P>(cr, U, contour_u(pl, lf, cp.kappa));
+                      sl = span_at<P>(cr, U, contour_u(pl, ll, cp.kappa)));
+        s_span[0] = sf;
+        s_span[1] = sl;
+      }
+      __syncthreads();
+      const int cp_lo = s_span[0] - cr.p;
+      const int ncp = s_span[1] - s_span[0] + cr.p + 1;
+      const int kn_lo = s_span[0] - cr.p + 1;
+      const int nkn = s_span[1] - s_span[0] + 2 * cr.p;
+      const bool use_smem = ncp <= kWin && nkn <= kWin + 2 * kMaxP && s_span[1] >= s_span[0];
+      if (use_smem) {
+        for (int k = threadIdx.x; k < 4 * ncp; k += blockDim.x) s_cp[k] = 0.f;
+        for (int k = threadIdx.x; k < nkn; k += blockDim.x) s_kn[k] = 0.f;
+      }
+      __syncthreads();
+      float dA = 0.f, dB = 0.f;
+      if (valid) {
+        NS_DISPATCH_P(cr.p, chain_contour_sample<P>(cv, cr, U, pl, l, cp, g0, s_cp, s_kn, cp_lo, kn_lo, use_smem,
+                                                     dkey, dknots, dA, dB));
+      }
+      block_add(dA, s_red, 0);
+      block_add(dB, s_red, 1);
+      block_add(g1.x, s_red, 2);
+      block_add(g1.y, s_red, 3);
+      block_add(g1.z, s_red, 4);
+      block_add(g0.w, s_red, 5);
+      __syncthreads();
+      if (use_smem) {
+        for (int k = threadIdx.x; k < ncp; k += blockDim.x) {
+          const int key = cr.key0 + cp_to_key(cp_lo + k, cr.p, cr.closed, cr.nk);
+          float* a = dkey + 4 * (long long)key;
+          const float* v = s_cp + 4 * k;
+          if (v[0] != 0.f) atomicAdd(a + 0, v[0]);
+          if (v[1] != 0.f) atomicAdd(a + 1, v[1]);
+          if (v[2] != 0.f) atomicAdd(a + 2, v[2]);
+          if (v[3] != 0.f) atomicAdd(a + 3, v[3]);
+        }
+        for (int k = threadIdx.x; k < nkn; k += blockDim.x)
+          if (s_kn[k] != 0.f) atomicAdd(dknots + cr.knot0 + kn_lo + k, s_kn[k]);
+      }
+      if (threadIdx.x == 0) {
+        atomicAdd(dknots + cr.knot0 + cr.p, s_red[0]);
+        atomicAdd(dknots + cr.knot0 + cr.n + 1, s_red[1]);
+        atomicAdd(dcolor + 4 * c + 0, s_red[2]);
+        atomicAdd(dcolor + 4 * c + 1, s_red[3]);
+        atomicAdd(dcolor + 4 * c + 2, s_red[4]);
+        atomicAdd(dcolor + 4 * c + 3, s_red[5]);
+      }
+      continue;
+    }
+    // fill task (skipped when its polyline overflowed the boundary capacity)
+    if ((long long)pl.b_off + pl.M > bcap) continue;
+    const int B = pl.M;
+    const bool use_smem = B <= kWinB;
+    if (use_smem)
+      for (int k = threadIdx.x; k < B; k += blockDim.x) s_db[k] = make_float2(0.f, 0.f);
+    __syncthreads();
+    float dO = 0.f;
+    if (valid) {
+      const float o = cv.color[4 * c + 3];
+      const int aux = gaux[g];
+      const bool inside = aux >= 0;
+      const int i0 = inside ? aux : ~aux;
+      const int i1 = i0 + 1 == B ? 0 : i0 + 1;
+      const float4 r = rec[g];
+      const float2 b0 = bpts[pl.b_off + i0], b1 = bpts[pl.b_off + i1];
+      const float ex = b1.x - b0.x, ey = b1.y - b0.y;
+      const float rx = r.x - b0.x, ry = r.y - b0.y;
+      const float ee = ex * ex + ey * ey;
+      const float t = ee > 0.f ? fminf(fmaxf((rx * ex + ry * ey) / ee, 0.f), 1.f) : 0.f;
+      const float dx = rx - t * ex, dy = ry - t * ey;
+      const float d = sqrtf(dx * dx + dy * dy);
+      const float sdf = inside ? d : -d;
+      const float sig = 1.f / (1.f + __expf(-(cp.gamma / cp.h * sdf)));
+      dO = sig * g0.w;
+      const float dsdf = g0.w * o * sig * (1.f - sig) * (cp.gamma / cp.h);
+      const float dd = inside ? dsdf : -dsdf;
+      if (d > 0.f && dd != 0.f) {
+        // d = |q - b0 - t e|, t at its optimum: dd/db0 = -(1-t) n, dd/db1 = -t n
+        const float nx = dx / d, ny = dy / d;
+        const float a0 = -dd * (1.f - t), a1 = -dd * t;
+        if (use_smem) {
+          atomicAdd(&s_db[i0].x, a0 * nx);
+          atomicAdd(&s_db[i0].y, a0 * ny);
+          atomicAdd(&s_db[i1].x, a1 * nx);
+          atomicAdd(&s_db[i1].y, a1 * ny);
+        } else {
+          atomicAdd(&dbpts[pl.b_off + i0].x, a0 * nx);
+          atomicAdd(&dbpts[pl.b_off + i0].y, a0 * ny);
+          atomicAdd(&dbpts[pl.b_off + i1].x, a1 * nx);
+          atomicAdd(&dbpts[pl.b_off + i1].y, a1 * ny);
+        }
+      }
+    }
+    block_add(dO, s_red, 5);
+    block_add(g1.x, s_red, 2);
+    block_add(g1.y, s_red, 3);
+    block_add(g1.z, s_red, 4);
+    __syncthreads();
+    if (use_smem) {
+      for (int k = threadIdx.x; k < B; k += blockDim.x) {
+        const float2 v = s_db[k];
+        if (v.x != 0.f) atomicAdd(&dbpts[pl.b_off + k].x, v.x);
+        if (v.y != 0.f) atomicAdd(&dbpts[pl.b_off + k].y, v.y);
+      }
+    }
+    if (threadIdx.x == 0) {
+      atomicAdd(dcolor + 4 * c + 0, s_red[2]);
+      atomicAdd(dcolor + 4 * c + 1, s_red[3]);
+      atomicAdd(dcolor + 4 * c + 2, s_red[4]);
+      atomicAdd(dcolor + 4 * c + 3, s_red[5]);
+    }
+  }
+}
+
+template <int P>
+__device__ void chain_boundary_point(const ns_curves& cv, const CurveRef& cr, const float* U, const CurvePlan& pl,
+                                     int j, float2 db, float* dkey, float* dknots) {
+  const float t = float(j) / float(pl.M);
+  const float u = pl.a + t * (pl.b - pl.a);
+  const int i = find_span(U, P, cr.n, u);
+  const float gC[3] = {db.x, db.y, 0.f};
+  auto add_cp = [&](int cpi, float dx, float dy, float ds, float dw) {
+    float* a = dkey + 4 * (long long)(cr.key0 + cp_to_key(cpi, P, cr.closed, cr.nk));
+    atomicAdd(a + 0, dx);
+    atomicAdd(a + 1, dy);
+    atomicAdd(a + 3, dw);
+  };
+  auto add_knot = [&](int k, float v) { atomicAdd(dknots + cr.knot0 + k, v); };
+  float dA = 0.f, dB = 0.f;
+  curve_point_bwd<P>(cv, cr, U, i, u, t, gC, add_cp, add_knot, dA, dB);
+  atomicAdd(dknots + cr.knot0 + cr.p, dA);
+  atomicAdd(dknots + cr.knot0 + cr.n + 1, dB);
+}
+
+__global__ void k_chain_boundary(ns_curves cv, const CurvePlan* __restrict__ plan, const float* __restrict__ knots,
+                                 const DevState* __restrict__ st, const float2* __restrict__ dbpts, float* dkey,
+                                 float* dknots) {
+  const int nb = st->b_count;
+  const int nc = cv.n_curves;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nb; j += gridDim.x * blockDim.x) {
+    const float2 db = dbpts[j];
+    if (db.x == 0.f && db.y == 0.f) continue;
+    int lo = 0, hi = nc - 1;   // largest curve with b_off <= j (offsets increase with the curve index)
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (plan[mid].b_off <= j) lo = mid; else hi = mid - 1;
+    }
+    const CurvePlan pl = plan[lo];
+    if (pl.kind != kFill) continue;
+    const CurveRef cr = curve_ref(cv, lo);
+    const float* U = knots + cr.knot0;
+    NS_DISPATCH_P(cr.p, chain_boundary_point<P>(cv, cr, U, pl, j - pl.b_off, db, dkey, dknots));
+  }
+}
+
+// dL/dU -> dL/dtau.  U_k is the sum of the intervals before k, so dL/d(interval q)
+// = sum_{k > q} dL/dU_k; interval q of the extended list maps back to tau.
+__global__ void k_knot_grads(ns_curves cv, const CurvePlan* __restrict__ plan, const float* __restrict__ dknots,
+                             float* dtau) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cv.n_curves || plan[c].kind == kNone) return;
+  const CurveRef cr = curve_ref(cv, c);
+  const int t0 = cv.tau_offset[c];
+  const int nt = cr.ntau, p = cr.p;
+  const int n_int = nt + 2 * p;
+  const float* dU = dknots + cr.knot0;
+  float acc = 0.f;
+  for (int q = n_int - 1; q >= 0; --q) {
+    acc += dU[q + 1];
+    int k;
+    if (!cr.closed) {
+      if (q < p || q >= p + nt) continue;
+      k = q - p;
+    } else {
+      k = q < p ? nt - p + q : (q < p + nt ? q - p : q - p - nt);
+      k %= nt;
+      if (k < 0) k += nt;
+    }
+    dtau[t0 + k] += acc;
+  }
+}
+
+}  // namespace ns
+
+using namespace ns;
+
+extern "C" ns_status splat_backward(const ns_curves* curves, const ns_gaussians* g, const ns_sample_params* sp,
+                                    const ns_raster_params* rp, const ns_capacity* cap, const float* dL_dimage,
+                                    float* dgauss, const ns_curve_grads* out, int32_t zero_outputs, void* ws,
+                                    size_t ws_bytes, void* stream) {
+  Layout L;
+  if (!curves || !g || !cap || !dL_dimage || !ws || !g->rec || !g->curve || !g->count) {
+    set_error("splat_backward: null argument");
+    return NS_ERR_INVALID_ARG;
+  }
+  if (!raster_params_ok(rp)) return NS_ERR_INVALID_ARG;
+  if (!make_layout(curves, cap, rp, &L)) return NS_ERR_INVALID_ARG;
+  if (ws_bytes < L.total || g->capacity < cap->gaussians) {
+    set_error("splat_backward: workspace or Gaussian arrays smaller than the capacities");
+    return NS_ERR_INVALID_ARG;
+  }
+  if (out && (!sp || !out->dkey || !out->dtau || !out->dcolor || !g->aux)) {
+    set_error("splat_backward: curve gradients need sample parameters, aux and all three outputs");
+    return NS_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  float* dg = dgauss ? dgauss : at<float>(ws, L.o_dgauss);
+  cudaMemsetAsync(dg, 0, sizeof(float) * 8 * (size_t)L.gcap, s);
+  launch_blend_bwd(L, curves, g, rp, dL_dimage, dg, ws, s);
+  if (out) {
+    DevState* st = at<DevState>(ws, L.o_state);
+    const CurvePlan* plan = at<CurvePlan>(ws, L.o_plan);
+    const int* order = at<int>(ws, L.o_order);
+    const float* knots = at<float>(ws, L.o_knots);
+    float* dknots = at<float>(ws, L.o_dknots);
+    const float2* bpts = at<float2>(ws, L.o_bpts);
+    float2* dbpts = at<float2>(ws, L.o_dbpts);
+    const size_t n_knots = (size_t)L.nt + (size_t)kKnotPad * L.nc;
+    cudaMemsetAsync(dknots, 0, sizeof(float) * n_knots, s);
+    cudaMemsetAsync(dbpts, 0, sizeof(float2) * (size_t)L.bcap, s);
+    if (zero_outputs) {
+      cudaMemsetAsync(out->dkey, 0, sizeof(float) * 4 * (size_t)L.nk, s);
+      cudaMemsetAsync(out->dtau, 0, sizeof(float) * (size_t)L.nt, s);
+      cudaMemsetAsync(out->dcolor, 0, sizeof(float) * 4 * (size_t)L.nc, s);
+    }
+    if (L.nc > 0) {
+      ChainParams cp;
+      cp.rho = sp->rho;
+      cp.h = sp->h;
+      cp.gamma = sp->gamma;
+      cp.kappa = sp->kappa;
+      k_chain<<<num_sms() * 8, 256, 0, s>>>(*curves, cp, plan, order, knots, bpts, st,
+                                            reinterpret_cast<const float4*>(g->rec), g->aux, dg, cap->gaussians,
+                                            cap->boundary, out->dkey, dknots, dbpts, out->dcolor);
+      if (L.bcap > 0)
+        k_chain_boundary<<<num_sms() * 4, 256, 0, s>>>(*curves, plan, knots, st, dbpts, out->dkey, dknots);
+      k_knot_grads<<<(L.nc + 127) / 128, 128, 0, s>>>(*curves, plan, dknots, out->dtau);
+    }
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string("splat_backward: ") + cudaGetErrorString(e));
+    return NS_ERR_CUDA;
+  }
+  return NS_OK;
+}

@@ -1,0 +1,295 @@
+// Internal definitions shared by the library's translation units: workspace
+// layout, device state, per-curve plan records and the span-local NURBS
+// evaluator (forward and reverse mode).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "nurbs_splat.h"
+
+namespace ns {
+
+constexpr int kMaxP = NS_MAX_DEGREE;
+constexpr int kChunk = 256;          // Gaussians per sampling / chain task (one block)
+constexpr int kBinItems = 2048;      // Gaussians per binning block (256 threads x 8)
+constexpr int kSortItems = 4096;     // pairs per radix-sort block (256 threads x 16)
+constexpr int kKnotPad = 2 * kMaxP + 1;  // knots per curve = intervals + 2p + 1
+
+enum CurveKind : int { kNone = 0, kOpen = 1, kClosedStroke = 2, kFill = 3 };
+
+// Device-side status and counters, at the start of the workspace.
+struct DevState {
+  int status;          // ns_status, first error wins
+  int bad_curve;
+  int n_chunks;        // sampling / chain tasks of the current sample
+  int sorted_buf;      // which pair buffer holds the sorted result
+  unsigned long long g_total;     // Gaussians needed
+  unsigned long long b_total;     // boundary points needed
+  unsigned long long pair_total;  // pairs needed
+  unsigned long long culled;      // fill Gaussians with opacity < alpha_min
+  int g_count;         // min(g_total, capacity)
+  int pair_count;      // min(pair_total, capacity)
+  int b_count;
+  int pad[5];
+};
+
+// One curve's sampling plan (written by the planning kernels).
+struct CurvePlan {
+  float L, a, b, x0, y0;   // arc length, domain [a, b], fill grid origin
+  int kind;                // CurveKind
+  int M;                   // contour samples (open/closed) or boundary points (fill)
+  int count;               // Gaussians emitted
+  int nx, ny;              // fill grid
+  int g_off;               // first Gaussian (front-to-back order)
+  int b_off;               // first boundary point
+  int chunk_off;           // first task
+  int scene;
+  int pad[2];
+};
+static_assert(sizeof(CurvePlan) == 64, "plan record is one 64-byte line");
+
+struct Layout {
+  int S = 0, H = 0, W = 0, C = 0, tile = 16, tiles_x = 0, tiles_y = 0, n_tiles = 0;
+  int64_t n_pix = 0;
+  int nc = 0, nk = 0, nt = 0;
+  int64_t gcap = 0, pcap = 0, bcap = 0;
+  int64_t bin_blocks = 0, sort_blocks = 0;
+  size_t o_state = 0, o_plan = 0, o_knots = 0, o_dknots = 0, o_bpts = 0, o_dbpts = 0, o_bsum = 0,
+         o_k0 = 0, o_v0 = 0, o_k1 = 0, o_v1 = 0, o_hist = 0, o_ranges = 0, o_T = 0, o_nlast = 0,
+         o_dgauss = 0, o_curve_scene = 0, o_order = 0, total = 0;
+};
+
+// Host helpers (ns_api.cu).
+void set_error(const std::string& msg);
+bool make_layout(const ns_curves* c, const ns_capacity* cap, const ns_raster_params* rp, Layout* L);
+int num_sms();
+void launch_reset_state(DevState* st, cudaStream_t s);
+
+template <typename T>
+inline T* at(void* ws, size_t off) { return reinterpret_cast<T*>(static_cast<char*>(ws) + off); }
+
+// ---------------------------------------------------------------------------
+// device helpers
+
+__device__ __forceinline__ void raise_status(DevState* st, int code) {
+  atomicCAS(&st->status, 0, code);
+}
+
+__device__ __forceinline__ int cp_to_key(int cp, int p, bool closed, int nk) {
+  if (!closed) return cp;
+  int k = cp - (p + 1) / 2;
+  k %= nk;
+  return k < 0 ? k + nk : k;
+}
+
+// Largest span i in [p, n] with U[i] <= u and U[i] < U[i+1] (a non-empty
+// span; at the right end of the domain and at repeated knots the last
+// non-empty span below u is used).
+__device__ __forceinline__ int find_span(const float* U, int p, int n, float u) {
+  if (!(u >= U[p])) return p;
+  int lo = p, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (U[mid] <= u) lo = mid; else hi = mid - 1;
+  }
+  while (lo > p && !(U[lo] < U[lo + 1])) --lo;
+  return lo;
+}
+
+// Span-local Cox-de Boor triangle for degree P at parameter u in span i.
+// lev[j][r] keeps N_{i-j+r, j} for j < P (needed by the reverse sweep and the
+// derivative), N[r] = N_{i-P+r, P}.  left[j] = u - U[i+1-j], right[j] = U[i+j] - u.
+template <int P>
+struct Tri {
+  float lev[P][P];
+  float N[P + 1];
+  float left[P + 1], right[P + 1];
+};
+
+template <int P>
+__device__ __forceinline__ void basis_fwd(const float* __restrict__ U, int i, float u, Tri<P>& t) {
+  float N[P + 1];
+  N[0] = 1.f;
+#pragma unroll
+  for (int j = 1; j <= P; ++j) {
+    t.left[j] = u - U[i + 1 - j];
+    t.right[j] = U[i + j] - u;
+#pragma unroll
+    for (int r = 0; r < j; ++r) t.lev[j - 1][r] = N[r];
+    float saved = 0.f;
+#pragma unroll
+    for (int r = 0; r < j; ++r) {
+      const float temp = N[r] / (t.right[r + 1] + t.left[j - r]);
+      N[r] = saved + t.right[r + 1] * temp;
+      saved = t.left[j - r] * temp;
+    }
+    N[j] = saved;
+  }
+#pragma unroll
+  for (int r = 0; r <= P; ++r) t.N[r] = N[r];
+}
+
+// First derivatives N'_{i-P+r, P}, r = 0..P, from level P-1 of the triangle.
+template <int P>
+__device__ __forceinline__ void basis_deriv(const Tri<P>& t, float* dN) {
+  float tmp[P + 1];
+#pragma unroll
+  for (int r = 0; r < P; ++r) tmp[r] = t.lev[P - 1][r] / (t.right[r + 1] + t.left[P - r]);
+#pragma unroll
+  for (int r = 0; r <= P; ++r) {
+    const float a = r > 0 ? tmp[r - 1] : 0.f;
+    const float b = r < P ? tmp[r] : 0.f;
+    dN[r] = float(P) * (a - b);
+  }
+}
+
+// Reverse sweep through the triangle.  Given g[r] = dL/dN_{i-P+r,P}, adds
+// dL/du to *du and dL/dU[k] to dU[k - (i-P+1)] for the 2P local knots.
+// Level j forms N^{(j)}[r] = beta_r x_r + alpha_{r-1} x_{r-1}, x = level j-1,
+// alpha_r = (u - U_lo)/(U_hi - U_lo), beta_r = 1 - alpha_r,
+// lo = i+r+1-j, hi = i+r+1.
+template <int P>
+__device__ __forceinline__ void basis_bwd(const Tri<P>& t, const float* gN, float* du, float* dU) {
+  float g[P + 1];
+#pragma unroll
+  for (int r = 0; r <= P; ++r) g[r] = gN[r];
+#pragma unroll
+  for (int j = P; j >= 1; --j) {
+    float gp[P];
+#pragma unroll
+    for (int r = 0; r < j; ++r) {
+      const float x = t.lev[j - 1][r];
+      const float D = t.right[r + 1] + t.left[j - r];
+      const float inv = 1.f / D;
+      const float al = t.left[j - r] * inv;
+      const float be = t.right[r + 1] * inv;
+      gp[r] = be * g[r] + al * g[r + 1];
+      const float dal = x * (g[r + 1] - g[r]);
+      *du += dal * inv;
+      dU[r + P - j] += dal * (al - 1.f) * inv;
+      dU[r + P] -= dal * al * inv;
+    }
+#pragma unroll
+    for (int r = 0; r < j; ++r) g[r] = gp[r];
+  }
+}
+
+// Per-curve constants resolved from the input tables.
+struct CurveRef {
+  int p, nk, ntau, key0, knot0, n;  // n: last control point index
+  bool closed, filled;
+};
+
+__device__ __forceinline__ CurveRef curve_ref(const ns_curves& cv, int c) {
+  CurveRef r;
+  r.p = cv.degree[c];
+  const int fl = cv.flags[c];
+  r.closed = (fl & NS_CLOSED) != 0;
+  r.filled = (fl & NS_FILLED) != 0;
+  r.key0 = cv.key_offset[c];
+  r.nk = cv.key_offset[c + 1] - r.key0;
+  const int t0 = cv.tau_offset[c];
+  r.ntau = cv.tau_offset[c + 1] - t0;
+  r.knot0 = t0 + kKnotPad * c;
+  r.n = r.closed ? r.nk + r.p - 1 : r.nk - 1;
+  return r;
+}
+
+// C(u) = S/W (Eq. 1) in span i with its triangle; optionally C'(u) (Eq. 2).
+template <int P>
+struct Eval {
+  Tri<P> t;
+  float4 cp[P + 1];   // {x, y, s, w} of the span's control points
+  float S[3], W, C[3];
+};
+
+template <int P>
+__device__ __forceinline__ void eval_curve(const float4* __restrict__ key, const CurveRef& cr,
+                                           const float* __restrict__ U, int i, float u, Eval<P>& e) {
+  basis_fwd<P>(U, i, u, e.t);
+  e.S[0] = e.S[1] = e.S[2] = 0.f;
+  e.W = 0.f;
+#pragma unroll
+  for (int l = 0; l <= P; ++l) {
+    const int k = cp_to_key(i - P + l, P, cr.closed, cr.nk);
+    const float4 q = __ldg(&key[cr.key0 + k]);
+    e.cp[l] = q;
+    const float nw = e.t.N[l] * q.w;
+    e.S[0] = fmaf(nw, q.x, e.S[0]);
+    e.S[1] = fmaf(nw, q.y, e.S[1]);
+    e.S[2] = fmaf(nw, q.z, e.S[2]);
+    e.W += nw;
+  }
+  const float iw = 1.f / e.W;
+  e.C[0] = e.S[0] * iw;
+  e.C[1] = e.S[1] * iw;
+  e.C[2] = e.S[2] * iw;
+}
+
+// |C'_xy(u)| by the quotient rule (Eq. 2), after eval_curve.
+template <int P>
+__device__ __forceinline__ float speed_xy(const Eval<P>& e) {
+  float dN[P + 1];
+  basis_deriv<P>(e.t, dN);
+  float dS0 = 0.f, dS1 = 0.f, dW = 0.f;
+#pragma unroll
+  for (int l = 0; l <= P; ++l) {
+    const float nw = dN[l] * e.cp[l].w;
+    dS0 = fmaf(nw, e.cp[l].x, dS0);
+    dS1 = fmaf(nw, e.cp[l].y, dS1);
+    dW += nw;
+  }
+  const float iw = 1.f / e.W;
+  const float dx = (dS0 - e.C[0] * dW) * iw;   // (W S' - S W')/W^2 = (S' - C W')/W
+  const float dy = (dS1 - e.C[1] * dW) * iw;
+  return sqrtf(dx * dx + dy * dy);
+}
+
+// Runtime degree -> template dispatch.
+#define NS_DISPATCH_P(p, ...)                     \
+  switch (p) {                                    \
+    case 1: { constexpr int P = 1; __VA_ARGS__; } break; \
+    case 2: { constexpr int P = 2; __VA_ARGS__; } break; \
+    case 3: { constexpr int P = 3; __VA_ARGS__; } break; \
+    case 4: { constexpr int P = 4; __VA_ARGS__; } break; \
+    case 5: { constexpr int P = 5; __VA_ARGS__; } break; \
+    default: break;                               \
+  }
+
+// Parameter of sample l of a contour curve (open: [first x kappa, M samples,
+// last x kappa]; closed: M samples without repeating the start).
+__device__ __forceinline__ float contour_u(const CurvePlan& pl, int l, int kappa) {
+  float t;
+  if (pl.kind == kOpen) {
+    const int j = l - kappa;
+    t = j <= 0 ? 0.f : (j >= pl.M - 1 ? 1.f : float(j) / float(pl.M - 1));
+  } else {
+    t = float(l) / float(pl.M);
+  }
+  return pl.a + t * (pl.b - pl.a);
+}
+
+__device__ __forceinline__ float contour_t(const CurvePlan& pl, int l, int kappa) {
+  if (pl.kind == kOpen) {
+    const int j = l - kappa;
+    return j <= 0 ? 0.f : (j >= pl.M - 1 ? 1.f : float(j) / float(pl.M - 1));
+  }
+  return float(l) / float(pl.M);
+}
+
+// The block task (chunk) -> curve map: largest c with plan[c].chunk_off <= task,
+// over curves in front-to-back order (chunk offsets are increasing in that order).
+__device__ __forceinline__ int curve_of_task(const CurvePlan* __restrict__ plan, const int* __restrict__ order,
+                                             int nc, int task) {
+  int lo = 0, hi = nc - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (plan[order[mid]].chunk_off <= task) lo = mid; else hi = mid - 1;
+  }
+  return order[lo];
+}
+
+}  // namespace ns

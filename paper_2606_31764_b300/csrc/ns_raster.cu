@@ -1,0 +1,667 @@
+// splat_forward and the blend adjoint: Gaussians -> image (paper §3.4, Eq. 8-9).
+//
+// Kernels, in launch order:
+//   k_curve_scene   scene of every curve (binary search of the scene offsets)
+//   k_bin_count     per 2048 Gaussians: tiles overlapped by mu +- k sigma (exact
+//                   float32 rule), block sums
+//   k_scan_small    one block: block sums -> block offsets, pair total
+//   k_bin_emit      recount, block-local scan, write (tile, Gaussian) pairs in
+//                   Gaussian order, which is front to back inside each scene
+//   k_radix_hist / k_radix_scan / k_radix_scatter
+//                   stable LSD radix sort of the pairs on the tile id bits
+//                   only: pairs enter in (layer, sample) order, so a stable sort
+//                   by tile yields the full (tile, layer, sample) order
+//   k_ranges        [start, end) of every tile's run
+//   k_blend_fwd     one 16x16 tile per block: the tile's list staged in shared
+//                   memory 256 records at a time, each thread composites one
+//                   pixel front to back; the block stops once every pixel is done
+//   k_blend_bwd     the adjoint, back to front from each pixel's last
+//                   composited entry, transmittance recovered by division,
+//                   warp-reduced per-Gaussian gradients
+#include <cuda_runtime.h>
+#include <float.h>
+
+#include "ns_internal.cuh"
+
+namespace ns {
+
+constexpr int kTile = 16;
+
+__global__ void k_curve_scene(ns_curves cv, int* curve_scene) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cv.n_curves) return;
+  int s = 0;
+  if (cv.scene_curve_offset) {
+    int lo = 0, hi = cv.n_scenes - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (cv.scene_curve_offset[mid] <= c) lo = mid; else hi = mid - 1;
+    }
+    s = lo;
+  }
+  curve_scene[c] = s;
+}
+
+struct BinParams {
+  float k_sigma, inv_tile, alpha_min;
+  int tiles_x, tiles_y, tiles_per_scene;
+  int n_curves, gcap;   // Gaussians naming a curve outside [0, n_curves) cover no tile
+};
+
+// Tile rectangle of one Gaussian; every step one float32 operation rounded to
+// nearest so that the result is reproducible bit for bit.
+__device__ __forceinline__ int tile_rect(const float4 r, const BinParams& bp, int& x0, int& y0, int& nx) {
+  const float ks = __fmul_rn(bp.k_sigma, r.z);
+  const float xlo = floorf(__fmul_rn(__fsub_rn(r.x, ks), bp.inv_tile));
+  const float xhi = floorf(__fmul_rn(__fadd_rn(r.x, ks), bp.inv_tile));
+  const float ylo = floorf(__fmul_rn(__fsub_rn(r.y, ks), bp.inv_tile));
+  const float yhi = floorf(__fmul_rn(__fadd_rn(r.y, ks), bp.inv_tile));
+  const bool ok = r.z > 0.f && r.w > 0.f && r.w >= bp.alpha_min && xhi >= 0.f && yhi >= 0.f &&
+                  xlo <= float(bp.tiles_x - 1) && ylo <= float(bp.tiles_y - 1);
+  if (!ok) return 0;
+  x0 = int(fmaxf(xlo, 0.f));
+  const int x1 = int(fminf(xhi, float(bp.tiles_x - 1)));
+  y0 = int(fmaxf(ylo, 0.f));
+  const int y1 = int(fminf(yhi, float(bp.tiles_y - 1)));
+  nx = x1 - x0 + 1;
+  return nx * (y1 - y0 + 1);
+}
+
+__device__ __forceinline__ int block_excl_scan_int(int v, int* s_warp, int& total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int t = lane < nw ? s_warp[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < nw) s_warp[lane] = t;
+  }
+  __syncthreads();
+  total = s_warp[nw - 1];
+  const int r = (w > 0 ? s_warp[w - 1] : 0) + x - v;
+  __syncthreads();
+  return r;
+}
+
+// 256 threads x 8 consecutive Gaussians.
+__global__ void __launch_bounds__(256) k_bin_count(const float4* __restrict__ rec, const int* __restrict__ gcurve,
+                                                   const int* __restrict__ gcount, BinParams bp, int* bsum,
+                                                   DevState* st) {
+  __shared__ int s_warp[32];
+  const int G = min(*gcount, bp.gcap);
+  const long long base = (long long)blockIdx.x * kBinItems;
+  if (base >= G) return;
+  int cnt = 0, culled = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const long long g = base + threadIdx.x * 8 + k;
+    if (g < G) {
+      const float4 r = rec[g];
+      int x0, y0, nx;
+      const int cv = gcurve[g];
+      if (cv >= 0 && cv < bp.n_curves) cnt += tile_rect(r, bp, x0, y0, nx);
+      culled += (r.z > 0.f && r.w < bp.alpha_min) ? 1 : 0;
+    }
+  }
+  int total;
+  block_excl_scan_int(cnt, s_warp, total);
+  int ctot;
+  block_excl_scan_int(culled, s_warp, ctot);
+  if (threadIdx.x == 0) {
+    bsum[blockIdx.x] = total;
+    if (ctot) atomicAdd(&st->culled, (unsigned long long)ctot);
+  }
+}
+
+__global__ void k_scan_small(int* vals, const int* gcount, int gcap, int items_per_block, DevState* st,
+                             long long cap) {
+  __shared__ long long s_warp[32];
+  __shared__ long long s_carry;
+  const int G = min(*gcount, gcap);
+  const int n = (G + items_per_block - 1) / items_per_block;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int base = 0; base < n; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const long long v = i < n ? vals[i] : 0;
+    long long x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      long long t = lane < nw ? s_warp[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      if (lane < nw) s_warp[lane] = t;
+    }
+    __syncthreads();
+    const long long excl = s_carry + (w > 0 ? s_warp[w - 1] : 0) + x - v;
+    if (i < n) vals[i] = int(excl < 0x7fffffffLL ? excl : 0x7fffffffLL);
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) s_carry = excl + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const long long tot = s_carry;
+    st->pair_total = (unsigned long long)tot;
+    st->pair_count = int(tot < cap ? tot : cap);
+    if (tot > cap) raise_status(st, NS_ERR_CAPACITY);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_bin_emit(const float4* __restrict__ rec, const int* __restrict__ gcurve,
+                                                  const int* __restrict__ gcount, const int* __restrict__ curve_scene,
+                                                  BinParams bp, const int* __restrict__ boff, uint32_t* keys,
+                                                  uint32_t* vals, long long pcap) {
+  __shared__ int s_warp[32];
+  const int G = min(*gcount, bp.gcap);
+  const long long base = (long long)blockIdx.x * kBinItems;
+  if (base >= G) return;
+  int cnt[8], x0[8], y0[8], nx[8];
+  int tot = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const long long g = base + threadIdx.x * 8 + k;
+    cnt[k] = 0;
+    if (g < G) {
+      const int cv = gcurve[g];
+      if (cv >= 0 && cv < bp.n_curves) cnt[k] = tile_rect(rec[g], bp, x0[k], y0[k], nx[k]);
+    }
+    tot += cnt[k];
+  }
+  int btot;
+  long long off = (long long)boff[blockIdx.x] + block_excl_scan_int(tot, s_warp, btot);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (!cnt[k]) continue;
+    const long long g = base + threadIdx.x * 8 + k;
+    const int sbase = curve_scene[gcurve[g]] * bp.tiles_per_scene;
+    for (int j = 0; j < cnt[k]; ++j, ++off) {
+      if (off >= pcap) break;
+      const int tx = x0[k] + j % nx[k];
+      const int ty = y0[k] + j / nx[k];
+      keys[off] = uint32_t(sbase + ty * bp.tiles_x + tx);
+      vals[off] = uint32_t(g);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// stable LSD radix sort of (tile, Gaussian) pairs on the tile bits
+
+__global__ void __launch_bounds__(256) k_radix_hist(const uint32_t* __restrict__ keys, const DevState* st, int shift,
+                                                    int bits, uint32_t* hist) {
+  __shared__ uint32_t h[256];
+  const int n = st->pair_count;
+  const int nb = (n + kSortItems - 1) / kSortItems;
+  if ((int)blockIdx.x >= nb) return;
+  const int nd = 1 << bits;
+  for (int d = threadIdx.x; d < nd; d += blockDim.x) h[d] = 0;
+  __syncthreads();
+  const long long base = (long long)blockIdx.x * kSortItems;
+  for (int k = threadIdx.x; k < kSortItems; k += blockDim.x) {
+    const long long i = base + k;
+    if (i < n) atomicAdd(&h[(keys[i] >> shift) & (nd - 1)], 1u);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < nd; d += blockDim.x) hist[(long long)d * nb + blockIdx.x] = h[d];
+}
+
+// Exclusive scan of the digit-major histogram (digit, block).
+__global__ void k_radix_scan(uint32_t* hist, const DevState* st, int bits) {
+  __shared__ uint32_t s_warp[32];
+  __shared__ uint32_t s_carry;
+  const int n_pairs = st->pair_count;
+  const int nb = (n_pairs + kSortItems - 1) / kSortItems;
+  const long long n = (long long)nb << bits;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (long long base = 0; base < n; base += blockDim.x) {
+    const long long i = base + threadIdx.x;
+    const uint32_t v = i < n ? hist[i] : 0u;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      uint32_t t = lane < nw ? s_warp[lane] : 0u;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      if (lane < nw) s_warp[lane] = t;
+    }
+    __syncthreads();
+    const uint32_t excl = s_carry + (w > 0 ? s_warp[w - 1] : 0u) + x - v;
+    if (i < n) hist[i] = excl;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) s_carry = excl + v;
+    __syncthreads();
+  }
+}
+
+// Each warp ranks its 512 consecutive pairs in 16 rounds of 32 with
+// __match_any_sync; per-warp digit counters keep the order stable.
+__global__ void __launch_bounds__(256) k_radix_scatter(const uint32_t* __restrict__ kin,
+                                                       const uint32_t* __restrict__ vin, uint32_t* kout,
+                                                       uint32_t* vout, const uint32_t* __restrict__ hist,
+                                                       const DevState* st, int shift, int bits) {
+  constexpr int kWarps = 8, kPerWarp = kSortItems / kWarps, kRounds = kPerWarp / 32;
+  __shared__ uint32_t wcnt[kWarps][256];
+  const int n = st->pair_count;
+  const int nb = (n + kSortItems - 1) / kSortItems;
+  if ((int)blockIdx.x >= nb) return;
+  const int nd = 1 << bits;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int d = lane; d < nd; d += 32) wcnt[w][d] = 0;
+  __syncwarp();
+  const long long base = (long long)blockIdx.x * kSortItems + (long long)w * kPerWarp;
+  uint32_t key[kRounds], val[kRounds];
+  uint32_t rank[kRounds];
+#pragma unroll
+  for (int r = 0; r < kRounds; ++r) {
+    const long long i = base + r * 32 + lane;
+    const bool ok = i < n;
+    key[r] = ok ? kin[i] : 0u;
+    val[r] = ok ? vin[i] : 0u;
+    const uint32_t d = ok ? (key[r] >> shift) & (nd - 1) : 0xffffffffu;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t below = peers & ((1u << lane) - 1u);
+    const uint32_t base_cnt = ok ? wcnt[w][d] : 0u;
+    rank[r] = base_cnt + __popc(below);
+    __syncwarp();
+    if (ok && below == 0u) wcnt[w][d] = base_cnt + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // exclusive prefix over warps per digit, plus the global base of (digit, block)
+  for (int d = threadIdx.x; d < nd; d += blockDim.x) {
+    uint32_t acc = hist[(long long)d * nb + blockIdx.x];
+#pragma unroll
+    for (int ww = 0; ww < kWarps; ++ww) {
+      const uint32_t c = wcnt[ww][d];
+      wcnt[ww][d] = acc;
+      acc += c;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kRounds; ++r) {
+    const long long i = base + r * 32 + lane;
+    if (i < n) {
+      const uint32_t d = (key[r] >> shift) & (nd - 1);
+      const uint32_t pos = wcnt[w][d] + rank[r];
+      kout[pos] = key[r];
+      vout[pos] = val[r];
+    }
+  }
+}
+
+__global__ void k_ranges(const uint32_t* __restrict__ keys, const DevState* st, int2* ranges) {
+  const int n = st->pair_count;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const uint32_t t = keys[i];
+    if (i == 0 || keys[i - 1] != t) ranges[t].x = int(i);
+    if (i == n - 1 || keys[i + 1] != t) ranges[t].y = int(i + 1);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// compositing
+
+struct BlendParams {
+  float alpha_min, alpha_max, t_min;
+  float bg0, bg1, bg2;
+  int W, H, tiles_x, tiles_per_scene;
+};
+
+// alpha = min(alpha_max, o exp(ncoef d^2)), ncoef = -1/(2 sigma^2) (Eq. 9).
+// Written with explicit roundings so that the forward and the backward kernels
+// compute the same bits.
+__device__ __forceinline__ float gauss_alpha(float fx, float fy, float4 q, float amax, float& dx, float& dy,
+                                             float& d2, float& e) {
+  dx = __fsub_rn(fx, q.x);
+  dy = __fsub_rn(fy, q.y);
+  d2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
+  e = __expf(__fmul_rn(q.z, d2));
+  return fminf(__fmul_rn(q.w, e), amax);
+}
+
+__device__ __forceinline__ float ncoef(float sigma) { return __fdiv_rn(-0.5f, __fmul_rn(sigma, sigma)); }
+
+template <int C>
+__global__ void __launch_bounds__(256) k_blend_fwd(const int2* __restrict__ ranges, const uint32_t* __restrict__ gid,
+                                                   const float4* __restrict__ rec, const int* __restrict__ gcurve,
+                                                   const float4* __restrict__ color, BlendParams bp, float* image,
+                                                   float* Tfinal, int* nlast) {
+  __shared__ float4 s_g[256];
+  __shared__ float4 s_c[256];
+  const int tile = blockIdx.x;
+  const int s = tile / bp.tiles_per_scene;
+  const int t = tile - s * bp.tiles_per_scene;
+  const int px = (t % bp.tiles_x) * kTile + (threadIdx.x & 15);
+  const int py = (t / bp.tiles_x) * kTile + (threadIdx.x >> 4);
+  const bool inside = px < bp.W && py < bp.H;
+  const float fx = px + 0.5f, fy = py + 0.5f;
+  const int2 rg = ranges[tile];
+  const int n = rg.y - rg.x;
+  float T = 1.f, acc[C];
+#pragma unroll
+  for (int ch = 0; ch < C; ++ch) acc[ch] = 0.f;
+  bool done = !inside;
+  int last = 0;
+  for (int base = 0; base < n; base += 256) {
+    const int idx = base + threadIdx.x;
+    if (idx < n) {
+      const uint32_t g = gid[rg.x + idx];
+      const float4 r = rec[g];
+      s_g[threadIdx.x] = make_float4(r.x, r.y, ncoef(r.z), r.w);
+      s_c[threadIdx.x] = color[gcurve[g]];
+    }
+    __syncthreads();
+    if (!done) {
+      const int cnt = min(256, n - base);
+      for (int k = 0; k < cnt; ++k) {
+        float dx, dy, d2, e;
+        const float a = gauss_alpha(fx, fy, s_g[k], bp.alpha_max, dx, dy, d2, e);
+        if (a < bp.alpha_min) continue;
+        const float test = T * (1.f - a);
+        if (test < bp.t_min) { done = true; break; }
+        const float w = a * T;
+        const float4 cc = s_c[k];
+        acc[0] = fmaf(cc.x, w, acc[0]);
+        if (C == 3) {
+          acc[1] = fmaf(cc.y, w, acc[1]);
+          acc[2] = fmaf(cc.z, w, acc[2]);
+        }
+        T = test;
+        last = base + k + 1;
+      }
+    }
+    if (__syncthreads_count(done) == (int)blockDim.x) break;
+  }
+  if (inside) {
+    const long long pix = ((long long)s * bp.H + py) * bp.W + px;
+    float* out = image + pix * C;
+    out[0] = acc[0] + T * bp.bg0;
+    if (C == 3) {
+      out[1] = acc[1] + T * bp.bg1;
+      out[2] = acc[2] + T * bp.bg2;
+    }
+    Tfinal[pix] = T;
+    nlast[pix] = last;
+  }
+}
+
+template <int C>
+__global__ void __launch_bounds__(256) k_blend_bwd(const int2* __restrict__ ranges, const uint32_t* __restrict__ gid,
+                                                   const float4* __restrict__ rec, const int* __restrict__ gcurve,
+                                                   const float4* __restrict__ color, BlendParams bp,
+                                                   const float* __restrict__ dimage, const float* __restrict__ Tfinal,
+                                                   const int* __restrict__ nlast, float* dgauss) {
+  __shared__ float4 s_g[256];
+  __shared__ float4 s_c[256];
+  __shared__ float s_sig[256];
+  __shared__ uint32_t s_id[256];
+  __shared__ int s_max;
+  const int tile = blockIdx.x;
+  const int s = tile / bp.tiles_per_scene;
+  const int t = tile - s * bp.tiles_per_scene;
+  const int px = (t % bp.tiles_x) * kTile + (threadIdx.x & 15);
+  const int py = (t / bp.tiles_x) * kTile + (threadIdx.x >> 4);
+  const bool inside = px < bp.W && py < bp.H;
+  const float fx = px + 0.5f, fy = py + 0.5f;
+  const int2 rg = ranges[tile];
+  const long long pix = ((long long)s * bp.H + py) * bp.W + px;
+  float T = 1.f, dI[3] = {0.f, 0.f, 0.f}, Bk[3] = {bp.bg0, bp.bg1, bp.bg2};
+  int last = 0;
+  if (inside) {
+    T = Tfinal[pix];
+    last = nlast[pix];
+#pragma unroll
+    for (int ch = 0; ch < C; ++ch) dI[ch] = dimage[pix * C + ch];
+  }
+  if (threadIdx.x == 0) s_max = 0;
+  __syncthreads();
+  if (last) atomicMax(&s_max, last);
+  __syncthreads();
+  const int nmax = s_max;
+  const int lane = threadIdx.x & 31;
+  for (int end = nmax; end > 0; end -= 256) {
+    const int beg = max(0, end - 256);
+    const int idx = beg + threadIdx.x;
+    __syncthreads();
+    if (idx < end) {
+      const uint32_t g = gid[rg.x + idx];
+      const float4 r = rec[g];
+      s_g[threadIdx.x] = make_float4(r.x, r.y, ncoef(r.z), r.w);
+      s_c[threadIdx.x] = color[gcurve[g]];
+      s_sig[threadIdx.x] = r.z;
+      s_id[threadIdx.x] = g;
+    }
+    __syncthreads();
+    for (int k = end - 1; k >= beg; --k) {
+      const int kk = k - beg;
+      float gmx = 0.f, gmy = 0.f, gs = 0.f, go = 0.f, gc0 = 0.f, gc1 = 0.f, gc2 = 0.f;
+      bool contrib = false;
+      if (k < last) {
+        const float4 q = s_g[kk];
+        float dx, dy, d2, e;
+        const float a = gauss_alpha(fx, fy, q, bp.alpha_max, dx, dy, d2, e);
+        if (a >= bp.alpha_min) {
+          contrib = true;
+          T = T / (1.f - a);
+          const float w = a * T;
+          const float4 cc = s_c[kk];
+          float da = (cc.x - Bk[0]) * dI[0];
+          gc0 = w * dI[0];
+          Bk[0] = a * cc.x + (1.f - a) * Bk[0];
+          if (C == 3) {
+            da += (cc.y - Bk[1]) * dI[1] + (cc.z - Bk[2]) * dI[2];
+            gc1 = w * dI[1];
+            gc2 = w * dI[2];
+            Bk[1] = a * cc.y + (1.f - a) * Bk[1];
+            Bk[2] = a * cc.z + (1.f - a) * Bk[2];
+          }
+          da *= T;
+          if (__fmul_rn(q.w, e) < bp.alpha_max) {
+            const float sg = s_sig[kk];
+            const float is2 = 1.f / (sg * sg);
+            go = e * da;
+            const float aa = da * a * is2;
+            gmx = aa * dx;
+            gmy = aa * dy;
+            gs = aa * d2 / sg;
+          }
+        }
+      }
+      if (__any_sync(0xffffffffu, contrib)) {
+        for (int o = 16; o > 0; o >>= 1) {
+          gmx += __shfl_xor_sync(0xffffffffu, gmx, o);
+          gmy += __shfl_xor_sync(0xffffffffu, gmy, o);
+          gs += __shfl_xor_sync(0xffffffffu, gs, o);
+          go += __shfl_xor_sync(0xffffffffu, go, o);
+          gc0 += __shfl_xor_sync(0xffffffffu, gc0, o);
+          if (C == 3) {
+            gc1 += __shfl_xor_sync(0xffffffffu, gc1, o);
+            gc2 += __shfl_xor_sync(0xffffffffu, gc2, o);
+          }
+        }
+        if (lane == 0) {
+          float* d = dgauss + (long long)s_id[kk] * 8;
+          atomicAdd(d + 0, gmx);
+          atomicAdd(d + 1, gmy);
+          atomicAdd(d + 2, gs);
+          atomicAdd(d + 3, go);
+          atomicAdd(d + 4, gc0);
+          if (C == 3) {
+            atomicAdd(d + 5, gc1);
+            atomicAdd(d + 6, gc2);
+          }
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+
+struct RasterPlan {
+  int passes, bits_per_pass;
+};
+
+static RasterPlan radix_plan(int n_tiles) {
+  int bits = 1;
+  while ((1LL << bits) < n_tiles) ++bits;
+  RasterPlan r;
+  r.passes = (bits + 7) / 8;
+  r.bits_per_pass = (bits + r.passes - 1) / r.passes;
+  return r;
+}
+
+static BlendParams blend_params(const Layout& L, const ns_raster_params* rp) {
+  BlendParams bp;
+  bp.alpha_min = rp->alpha_min;
+  bp.alpha_max = rp->alpha_max;
+  bp.t_min = rp->t_min;
+  bp.bg0 = rp->bg[0];
+  bp.bg1 = rp->bg[1];
+  bp.bg2 = rp->bg[2];
+  bp.W = L.W;
+  bp.H = L.H;
+  bp.tiles_x = L.tiles_x;
+  bp.tiles_per_scene = L.tiles_x * L.tiles_y;
+  return bp;
+}
+
+static bool check_raster(const ns_raster_params* rp) {
+  if (!rp || rp->tile != kTile || !(rp->k_sigma > 0.f) || !(rp->alpha_max > 0.f) || !(rp->alpha_max < 1.f) ||
+      !(rp->alpha_min >= 0.f) || !(rp->t_min >= 0.f) || !(rp->t_min < 1.f)) {
+    set_error("invalid raster parameters (tile must be 16, 0 < alpha_max < 1, k_sigma > 0)");
+    return false;
+  }
+  return true;
+}
+
+// Sorted-pair buffer index after the sort (for tools).
+int sorted_buffer(const Layout& L) { return radix_plan(L.n_tiles).passes & 1; }
+
+}  // namespace ns
+
+using namespace ns;
+
+extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* g, const ns_raster_params* rp,
+                                   const ns_capacity* cap, float* image, void* ws, size_t ws_bytes, void* stream) {
+  Layout L;
+  if (!curves || !g || !cap || !image || !ws || !g->rec || !g->curve || !g->count) {
+    set_error("splat_forward: null argument");
+    return NS_ERR_INVALID_ARG;
+  }
+  if (!check_raster(rp)) return NS_ERR_INVALID_ARG;
+  if (!make_layout(curves, cap, rp, &L)) return NS_ERR_INVALID_ARG;
+  if (ws_bytes < L.total || g->capacity < cap->gaussians) {
+    set_error("splat_forward: workspace or Gaussian arrays smaller than the capacities");
+    return NS_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DevState* st = at<DevState>(ws, L.o_state);
+  int* curve_scene = at<int>(ws, L.o_curve_scene);
+  int* bsum = at<int>(ws, L.o_bsum);
+  uint32_t* k0 = at<uint32_t>(ws, L.o_k0);
+  uint32_t* v0 = at<uint32_t>(ws, L.o_v0);
+  uint32_t* k1 = at<uint32_t>(ws, L.o_k1);
+  uint32_t* v1 = at<uint32_t>(ws, L.o_v1);
+  uint32_t* hist = at<uint32_t>(ws, L.o_hist);
+  int2* ranges = at<int2>(ws, L.o_ranges);
+  float* Tf = at<float>(ws, L.o_T);
+  int* nl = at<int>(ws, L.o_nlast);
+  const float4* rec = reinterpret_cast<const float4*>(g->rec);
+
+  cudaMemsetAsync(&st->culled, 0, sizeof(unsigned long long), s);
+  if (curves->n_curves > 0)
+    k_curve_scene<<<(curves->n_curves + 255) / 256, 256, 0, s>>>(*curves, curve_scene);
+  BinParams bp;
+  bp.k_sigma = rp->k_sigma;
+  bp.inv_tile = 1.f / float(kTile);
+  bp.alpha_min = rp->alpha_min;
+  bp.tiles_x = L.tiles_x;
+  bp.tiles_y = L.tiles_y;
+  bp.tiles_per_scene = L.tiles_x * L.tiles_y;
+  bp.n_curves = L.nc;
+  bp.gcap = int(L.gcap);
+  const int bin_blocks = int(L.bin_blocks);
+  if (bin_blocks > 0) {
+    k_bin_count<<<bin_blocks, 256, 0, s>>>(rec, g->curve, g->count, bp, bsum, st);
+  }
+  k_scan_small<<<1, 1024, 0, s>>>(bsum, g->count, int(L.gcap), kBinItems, st, cap->pairs);
+  if (bin_blocks > 0) {
+    k_bin_emit<<<bin_blocks, 256, 0, s>>>(rec, g->curve, g->count, curve_scene, bp, bsum, k0, v0, cap->pairs);
+  }
+  const RasterPlan rpn = radix_plan(L.n_tiles);
+  const int sort_blocks = int(L.sort_blocks);
+  uint32_t *kin = k0, *vin = v0, *kout = k1, *vout = v1;
+  for (int pass = 0; pass < rpn.passes; ++pass) {
+    const int shift = pass * rpn.bits_per_pass;
+    if (sort_blocks > 0) {
+      k_radix_hist<<<sort_blocks, 256, 0, s>>>(kin, st, shift, rpn.bits_per_pass, hist);
+      k_radix_scan<<<1, 1024, 0, s>>>(hist, st, rpn.bits_per_pass);
+      k_radix_scatter<<<sort_blocks, 256, 0, s>>>(kin, vin, kout, vout, hist, st, shift, rpn.bits_per_pass);
+    }
+    std::swap(kin, kout);
+    std::swap(vin, vout);
+  }
+  cudaMemsetAsync(ranges, 0, sizeof(int2) * (size_t)L.n_tiles, s);
+  k_ranges<<<num_sms() * 4, 256, 0, s>>>(kin, st, ranges);
+  const BlendParams blp = blend_params(L, rp);
+  const float4* col = reinterpret_cast<const float4*>(curves->color);
+  if (L.C == 3)
+    k_blend_fwd<3><<<L.n_tiles, 256, 0, s>>>(ranges, vin, rec, g->curve, col, blp, image, Tf, nl);
+  else
+    k_blend_fwd<1><<<L.n_tiles, 256, 0, s>>>(ranges, vin, rec, g->curve, col, blp, image, Tf, nl);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string("splat_forward: ") + cudaGetErrorString(e));
+    return NS_ERR_CUDA;
+  }
+  return NS_OK;
+}
+
+namespace ns {
+// Blend adjoint, used by splat_backward (ns_backward.cu).
+ns_status launch_blend_bwd(const Layout& L, const ns_curves* curves, const ns_gaussians* g,
+                           const ns_raster_params* rp, const float* dimage, float* dgauss, void* ws,
+                           cudaStream_t s) {
+  const RasterPlan rpn = radix_plan(L.n_tiles);
+  const uint32_t* vsorted = (rpn.passes & 1) ? at<uint32_t>(ws, L.o_v1) : at<uint32_t>(ws, L.o_v0);
+  const int2* ranges = at<int2>(ws, L.o_ranges);
+  const float* Tf = at<float>(ws, L.o_T);
+  const int* nl = at<int>(ws, L.o_nlast);
+  const BlendParams blp = blend_params(L, rp);
+  const float4* col = reinterpret_cast<const float4*>(curves->color);
+  const float4* rec = reinterpret_cast<const float4*>(g->rec);
+  if (L.C == 3)
+    k_blend_bwd<3><<<L.n_tiles, 256, 0, s>>>(ranges, vsorted, rec, g->curve, col, blp, dimage, Tf, nl, dgauss);
+  else
+    k_blend_bwd<1><<<L.n_tiles, 256, 0, s>>>(ranges, vsorted, rec, g->curve, col, blp, dimage, Tf, nl, dgauss);
+  return NS_OK;
+}
+bool raster_params_ok(const ns_raster_params* rp) { return check_raster(rp); }
+}  // namespace ns

@@ -1,0 +1,439 @@
+// nurbs_sample: curves -> Gaussians (paper §3.1-§3.3).
+//
+// Kernels, in launch order:
+//   k_plan          one block per curve: validation, knot vector (FP64 running
+//                   sum, stored FP32), arc length by N_L-node midpoint
+//                   quadrature of |C'| (Eq. 2-3, block reduction), counts
+//   k_scan_boundary one block: boundary-point offsets of filled curves
+//   k_boundary      one block per filled curve: boundary polyline b_i, its
+//                   padded and clipped box, the fill grid size
+//   k_scan_gauss    one block: Gaussian and task offsets in front-to-back order
+//   k_emit          persistent: one 256-Gaussian task per block iteration;
+//                   contour samples (Eq. 4-5) or fill points with the SDF of
+//                   Eq. S1-S3 against the polyline staged in shared memory (Eq. 6-7)
+#include <cuda_runtime.h>
+#include <float.h>
+
+#include "ns_internal.cuh"
+
+namespace ns {
+
+constexpr int kPlanThreads = 128;
+constexpr int kSegBatch = 1024;   // boundary segments staged in shared memory per pass
+
+__device__ __forceinline__ float block_sum(float v, float* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  float s = 0.f;
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) red[0] = s;
+  }
+  __syncthreads();
+  return red[0];
+}
+
+__device__ __forceinline__ float block_reduce_minmax(float v, float* red, bool is_max) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const float x = __shfl_xor_sync(0xffffffffu, v, o);
+    v = is_max ? fmaxf(v, x) : fminf(v, x);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : (is_max ? -FLT_MAX : FLT_MAX);
+    for (int o = 16; o > 0; o >>= 1) {
+      const float x = __shfl_xor_sync(0xffffffffu, s, o);
+      s = is_max ? fmaxf(s, x) : fminf(s, x);
+    }
+    if (threadIdx.x == 0) red[0] = s;
+  }
+  __syncthreads();
+  return red[0];
+}
+
+template <int P>
+__device__ float arc_length_part(const ns_curves& cv, const CurveRef& cr, const float* U, float a, float b,
+                                 int NL) {
+  const float du = (b - a) / float(NL);
+  float acc = 0.f;
+  for (int j = threadIdx.x; j < NL; j += blockDim.x) {
+    const float u = a + (float(j) + 0.5f) * du;
+    const int i = find_span(U, P, cr.n, u);
+    Eval<P> e;
+    eval_curve<P>(reinterpret_cast<const float4*>(cv.key), cr, U, i, u, e);
+    acc += speed_xy<P>(e);
+  }
+  return acc * du;
+}
+
+// One block per curve.
+__global__ void __launch_bounds__(kPlanThreads) k_plan(ns_curves cv, ns_sample_params sp, CurvePlan* plan,
+                                                       float* knots, int* order, DevState* st) {
+  __shared__ float red[32];
+  __shared__ int s_ok;
+  const int c = blockIdx.x;
+  const CurveRef cr = curve_ref(cv, c);
+  float* U = knots + cr.knot0;
+  if (threadIdx.x == 0) {
+    int ok = cr.p >= 1 && cr.p <= kMaxP && cr.key0 >= 0 && cr.nk >= 0 && cv.tau_offset[c] >= 0 &&
+             cr.ntau >= 0 && cv.key_offset[c + 1] <= cv.n_keys && cv.tau_offset[c + 1] <= cv.n_taus;
+    if (ok) ok = cr.closed ? (cr.nk >= cr.p && cr.nk >= 2 && cr.ntau == cr.nk)
+                           : (cr.nk >= cr.p + 1 && cr.ntau == cr.nk - cr.p);
+    if (ok && cr.filled && !cr.closed) ok = 0;
+    // scene and front-to-back position: reverse order inside the scene
+    int s = 0, s0 = 0, s1 = cv.n_curves;
+    if (cv.scene_curve_offset) {
+      int lo = 0, hi = cv.n_scenes - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (cv.scene_curve_offset[mid] <= c) lo = mid; else hi = mid - 1;
+      }
+      s = lo;
+      s0 = cv.scene_curve_offset[s];
+      s1 = cv.scene_curve_offset[s + 1];
+    }
+    if (s0 <= c && c < s1 && s1 <= cv.n_curves) order[s0 + (s1 - 1 - c)] = c;
+    else ok = 0;   // inconsistent scene offsets
+    plan[c].scene = s;
+    // knot vector (§3.1): open -> p zero intervals on both sides; closed ->
+    // last p core intervals before, first p after; cumulative sum from 0.
+    if (ok) {
+      const float* tau = cv.tau + cv.tau_offset[c];
+      const int p = cr.p, nt = cr.ntau;
+      const int n_int = nt + 2 * p;
+      double acc = 0.0;
+      U[0] = 0.f;
+      for (int q = 0; q < n_int; ++q) {
+        float v;
+        if (!cr.closed) {
+          v = (q < p || q >= p + nt) ? 0.f : tau[q - p];
+        } else {
+          int k = q < p ? nt - p + q : (q < p + nt ? q - p : q - p - nt);
+          k %= nt;
+          if (k < 0) k += nt;
+          v = tau[k];
+        }
+        if (!(v >= 0.f)) ok = 0;   // negative or NaN interval
+        acc += double(v);
+        U[q + 1] = float(acc);
+      }
+      if (ok && !(U[cr.n + 1] > U[p])) ok = 0;   // empty domain
+    }
+    if (!ok) {
+      atomicCAS(&st->bad_curve, -1, c);
+      raise_status(st, NS_ERR_INVALID_CURVE);
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  CurvePlan pl;
+  if (!s_ok) {
+    if (threadIdx.x == 0) {
+      plan[c].kind = kNone;
+      plan[c].count = 0;
+      plan[c].M = 0;
+      plan[c].L = 0.f;
+    }
+    return;
+  }
+  const float a = U[cr.p], b = U[cr.n + 1];
+  const int NL = sp.nl_mult * max(cv.width, cv.height);
+  float part = 0.f;
+  NS_DISPATCH_P(cr.p, part = arc_length_part<P>(cv, cr, U, a, b, NL));
+  const float L = block_sum(part, red);
+  if (threadIdx.x == 0) {
+    pl.L = L;
+    pl.a = a;
+    pl.b = b;
+    pl.x0 = pl.y0 = 0.f;
+    pl.nx = pl.ny = 0;
+    if (cr.filled) {
+      pl.kind = kFill;
+      pl.M = max(3, int(ceilf(sp.delta_b * L)));
+      pl.count = 0;   // set by k_boundary
+    } else if (cr.closed) {
+      pl.kind = kClosedStroke;
+      pl.M = max(1, int(ceilf(sp.delta_c * L)));
+      pl.count = pl.M;
+    } else {
+      pl.kind = kOpen;
+      pl.M = max(2, int(ceilf(sp.delta_c * L)));
+      pl.count = pl.M + 2 * sp.kappa;
+    }
+    pl.scene = plan[c].scene;
+    pl.g_off = pl.b_off = pl.chunk_off = 0;
+    plan[c] = pl;
+  }
+}
+
+// Exclusive scan of one int per item with a single block; `get(i)` gives the
+// item's value, `put(i, offset)` receives its offset; returns the total.
+template <class Get, class Put>
+__device__ long long block_scan_items(int n, Get get, Put put) {
+  __shared__ long long s_carry;
+  __shared__ long long s_warp[32];
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int base = 0; base < n; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    long long v = i < n ? (long long)get(i) : 0;
+    long long x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      long long t = lane < nw ? s_warp[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      if (lane < nw) s_warp[lane] = t;
+    }
+    __syncthreads();
+    const long long excl = s_carry + (w > 0 ? s_warp[w - 1] : 0) + x - v;
+    if (i < n) put(i, excl);
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) s_carry = excl + v;
+    __syncthreads();
+  }
+  return s_carry;
+}
+
+__global__ void k_scan_boundary(int nc, CurvePlan* plan, DevState* st, long long bcap) {
+  const long long tot = block_scan_items(
+      nc, [&](int c) { return plan[c].kind == kFill ? plan[c].M : 0; },
+      [&](int c, long long off) { plan[c].b_off = int(off); });
+  if (threadIdx.x == 0) {
+    st->b_total = (unsigned long long)tot;
+    st->b_count = int(tot < bcap ? tot : bcap);
+    if (tot > bcap) raise_status(st, NS_ERR_CAPACITY);
+  }
+}
+
+template <int P>
+__device__ void boundary_points(const ns_curves& cv, const CurveRef& cr, const float* U, const CurvePlan& pl,
+                                float2* bpts, long long bcap, float4& box) {
+  float xmin = FLT_MAX, ymin = FLT_MAX, xmax = -FLT_MAX, ymax = -FLT_MAX;
+  for (int j = threadIdx.x; j < pl.M; j += blockDim.x) {
+    const float t = float(j) / float(pl.M);
+    const float u = pl.a + t * (pl.b - pl.a);
+    const int i = find_span(U, P, cr.n, u);
+    Eval<P> e;
+    eval_curve<P>(reinterpret_cast<const float4*>(cv.key), cr, U, i, u, e);
+    const long long o = (long long)pl.b_off + j;
+    if (o < bcap) bpts[o] = make_float2(e.C[0], e.C[1]);
+    xmin = fminf(xmin, e.C[0]);
+    xmax = fmaxf(xmax, e.C[0]);
+    ymin = fminf(ymin, e.C[1]);
+    ymax = fmaxf(ymax, e.C[1]);
+  }
+  box = make_float4(xmin, ymin, xmax, ymax);
+}
+
+// One block per curve; filled curves only.
+__global__ void __launch_bounds__(kPlanThreads) k_boundary(ns_curves cv, ns_sample_params sp, CurvePlan* plan,
+                                                           const float* knots, float2* bpts, long long bcap) {
+  __shared__ float red[32];
+  const int c = blockIdx.x;
+  if (plan[c].kind != kFill) return;
+  const CurveRef cr = curve_ref(cv, c);
+  const float* U = knots + cr.knot0;
+  const CurvePlan pl = plan[c];
+  float4 box = make_float4(FLT_MAX, FLT_MAX, -FLT_MAX, -FLT_MAX);
+  NS_DISPATCH_P(cr.p, boundary_points<P>(cv, cr, U, pl, bpts, bcap, box));
+  const float xmin = block_reduce_minmax(box.x, red, false);
+  const float ymin = block_reduce_minmax(box.y, red, false);
+  const float xmax = block_reduce_minmax(box.z, red, true);
+  const float ymax = block_reduce_minmax(box.w, red, true);
+  if (threadIdx.x == 0) {
+    const float padx = sp.pad_frac * (xmax - xmin);
+    const float pady = sp.pad_frac * (ymax - ymin);
+    const float x0 = fmaxf(0.f, xmin - padx), x1 = fminf(float(cv.width), xmax + padx);
+    const float y0 = fmaxf(0.f, ymin - pady), y1 = fminf(float(cv.height), ymax + pady);
+    const int nx = x1 > x0 ? int(ceilf((x1 - x0) / sp.h)) : 0;
+    const int ny = y1 > y0 ? int(ceilf((y1 - y0) / sp.h)) : 0;
+    plan[c].x0 = x0;
+    plan[c].y0 = y0;
+    plan[c].nx = nx;
+    plan[c].ny = ny;
+    plan[c].count = nx * ny;   // counted even when the polyline overflowed (sizing)
+  }
+}
+
+__global__ void k_scan_gauss(int nc, CurvePlan* plan, const int* order, DevState* st, long long gcap,
+                             int* g_count_out) {
+  const long long tot = block_scan_items(
+      nc, [&](int f) { return plan[order[f]].count; },
+      [&](int f, long long off) { plan[order[f]].g_off = int(off < 0x7fffffff ? off : 0x7fffffff); });
+  const long long tasks = block_scan_items(
+      nc, [&](int f) { return (plan[order[f]].count + kChunk - 1) / kChunk; },
+      [&](int f, long long off) { plan[order[f]].chunk_off = int(off); });
+  if (threadIdx.x == 0) {
+    st->g_total = (unsigned long long)tot;
+    const int gc = int(tot < gcap ? tot : gcap);
+    st->g_count = gc;
+    st->n_chunks = int(tasks);
+    if (g_count_out) *g_count_out = gc;
+    if (tot > gcap) raise_status(st, NS_ERR_CAPACITY);
+  }
+}
+
+template <int P>
+__device__ void emit_contour(const ns_curves& cv, const CurveRef& cr, const float* U, const CurvePlan& pl, int l,
+                             const ns_sample_params& sp, float o, float4& rec) {
+  const float u = contour_u(pl, l, sp.kappa);
+  const int i = find_span(U, P, cr.n, u);
+  Eval<P> e;
+  eval_curve<P>(reinterpret_cast<const float4*>(cv.key), cr, U, i, u, e);
+  rec = make_float4(e.C[0], e.C[1], e.C[2] / sp.rho, o);
+}
+
+// Persistent: each block iteration handles one task of 256 Gaussians of one curve.
+__global__ void __launch_bounds__(256) k_emit(ns_curves cv, ns_sample_params sp, const CurvePlan* __restrict__ plan,
+                                              const int* __restrict__ order, const float* __restrict__ knots,
+                                              const float2* __restrict__ bpts, const DevState* __restrict__ st,
+                                              float4* rec, int* gcurve, int* gaux, long long gcap, long long bcap) {
+  __shared__ float4 seg[kSegBatch];   // {b0.x, b0.y, e.x, e.y}
+  __shared__ float seginv[kSegBatch]; // 1/|e|^2 (0 for a zero-length segment)
+  const int n_tasks = st->n_chunks;
+  const int nc = cv.n_curves;
+  for (int task = blockIdx.x; task < n_tasks; task += gridDim.x) {
+    const int c = curve_of_task(plan, order, nc, task);
+    const CurvePlan pl = plan[c];
+    const CurveRef cr = curve_ref(cv, c);
+    const float* U = knots + cr.knot0;
+    const int l = (task - pl.chunk_off) * kChunk + threadIdx.x;
+    const long long g = (long long)pl.g_off + l;
+    const bool valid = l < pl.count && g < gcap;
+    const float o = cv.color[4 * c + 3];
+    if (pl.kind != kFill) {
+      if (valid) {
+        float4 r;
+        NS_DISPATCH_P(cr.p, emit_contour<P>(cv, cr, U, pl, l, sp, o, r));
+        rec[g] = r;
+        gcurve[g] = c;
+        gaux[g] = -1;
+      }
+      continue;
+    }
+    // fill point: grid row-major over the padded box; a curve whose polyline
+    // did not fit the boundary capacity emits nothing (NS_ERR_CAPACITY is set)
+    if ((long long)pl.b_off + pl.M > bcap) continue;
+    const int nxx = max(pl.nx, 1);
+    const float qx = pl.x0 + (float(l % nxx) + 0.5f) * sp.h;
+    const float qy = pl.y0 + (float(l / nxx) + 0.5f) * sp.h;
+    const int B = pl.M;
+    float best = FLT_MAX;
+    int arg = 0, wn = 0;
+    for (int base = 0; base < B; base += kSegBatch) {
+      const int nseg = min(kSegBatch, B - base);
+      __syncthreads();
+      for (int s = threadIdx.x; s < nseg; s += blockDim.x) {
+        const int i = base + s;
+        const float2 b0 = bpts[pl.b_off + i];
+        const float2 b1 = bpts[pl.b_off + (i + 1 == B ? 0 : i + 1)];
+        const float ex = b1.x - b0.x, ey = b1.y - b0.y;
+        const float ee = ex * ex + ey * ey;
+        seg[s] = make_float4(b0.x, b0.y, ex, ey);
+        seginv[s] = ee > 0.f ? 1.f / ee : 0.f;
+      }
+      __syncthreads();
+      if (valid) {
+        for (int s = 0; s < nseg; ++s) {
+          const float4 sg = seg[s];
+          const float rx = qx - sg.x, ry = qy - sg.y;
+          const float t = fminf(fmaxf((rx * sg.z + ry * sg.w) * seginv[s], 0.f), 1.f);
+          const float dx = rx - t * sg.z, dy = ry - t * sg.w;
+          const float d2 = dx * dx + dy * dy;
+          if (d2 < best) { best = d2; arg = base + s; }
+          // winding number by signed crossings of the horizontal ray (Eq. S2
+          // is integral off the polyline; this evaluates it exactly there)
+          const float y1 = sg.y + sg.w;
+          const float isleft = sg.z * ry - rx * sg.w;
+          if (sg.y <= qy) {
+            if (y1 > qy && isleft > 0.f) ++wn;
+          } else {
+            if (y1 <= qy && isleft < 0.f) --wn;
+          }
+        }
+      }
+    }
+    if (valid) {
+      const bool inside = sp.fill_rule == 0 ? wn > 0 : wn != 0;
+      const float d = sqrtf(best);
+      const float sdf = inside ? d : -d;
+      const float z = sp.gamma / sp.h * sdf;
+      const float sig = 1.f / (1.f + __expf(-z));
+      rec[g] = make_float4(qx, qy, sp.eta * sp.h / sp.rho, o * sig);
+      gcurve[g] = c;
+      gaux[g] = inside ? arg : ~arg;
+    }
+  }
+}
+
+}  // namespace ns
+
+using namespace ns;
+
+extern "C" ns_status nurbs_sample(const ns_curves* curves, const ns_sample_params* sp, const ns_capacity* cap,
+                                  const ns_gaussians* out, void* ws, size_t ws_bytes, void* stream) {
+  Layout L;
+  if (!curves || !sp || !cap || !out || !ws) {
+    set_error("nurbs_sample: null argument");
+    return NS_ERR_INVALID_ARG;
+  }
+  ns_raster_params rp = ns_default_raster_params();
+  if (!make_layout(curves, cap, &rp, &L)) return NS_ERR_INVALID_ARG;
+  if (ws_bytes < L.total) {
+    set_error("nurbs_sample: workspace too small");
+    return NS_ERR_INVALID_ARG;
+  }
+  if (!(sp->h > 0.f) || !(sp->rho > 0.f) || !(sp->delta_c > 0.f) || !(sp->delta_b > 0.f) || sp->kappa < 0 ||
+      sp->nl_mult < 1 || !(sp->eta > 0.f) || !(sp->pad_frac >= 0.f) || sp->fill_rule < 0 || sp->fill_rule > 1) {
+    set_error("nurbs_sample: invalid sample parameters");
+    return NS_ERR_INVALID_ARG;
+  }
+  if (out->capacity < cap->gaussians || !out->rec || !out->curve || !out->aux || !out->count) {
+    set_error("nurbs_sample: output arrays missing or smaller than the Gaussian capacity");
+    return NS_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DevState* st = at<DevState>(ws, L.o_state);
+  CurvePlan* plan = at<CurvePlan>(ws, L.o_plan);
+  float* knots = at<float>(ws, L.o_knots);
+  int* order = at<int>(ws, L.o_order);
+  float2* bpts = at<float2>(ws, L.o_bpts);
+  const int nc = curves->n_curves;
+  launch_reset_state(st, s);
+  if (nc > 0) cudaMemsetAsync(order, 0, sizeof(int) * (size_t)nc, s);   // in range even if offsets are bad
+  if (nc == 0) {
+    cudaMemsetAsync(out->count, 0, sizeof(int), s);
+    cudaMemsetAsync(&st->n_chunks, 0, sizeof(int), s);
+    cudaMemsetAsync(&st->g_count, 0, sizeof(int), s);
+    return cudaGetLastError() == cudaSuccess ? NS_OK : NS_ERR_CUDA;
+  }
+  k_plan<<<nc, kPlanThreads, 0, s>>>(*curves, *sp, plan, knots, order, st);
+  k_scan_boundary<<<1, 1024, 0, s>>>(nc, plan, st, cap->boundary);
+  k_boundary<<<nc, kPlanThreads, 0, s>>>(*curves, *sp, plan, knots, bpts, cap->boundary);
+  k_scan_gauss<<<1, 1024, 0, s>>>(nc, plan, order, st, cap->gaussians, out->count);
+  const int grid = num_sms() * 8;
+  k_emit<<<grid, 256, 0, s>>>(*curves, *sp, plan, order, knots, bpts, st, reinterpret_cast<float4*>(out->rec),
+                              out->curve, out->aux, cap->gaussians, cap->boundary);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string("nurbs_sample: ") + cudaGetErrorString(e));
+    return NS_ERR_CUDA;
+  }
+  return NS_OK;
+}

@@ -1,0 +1,226 @@
+"""PyTorch-facing layer over the C ABI: device tables, buffers sized by the
+library's own counts, the three stages and a torch.autograd.Function.
+
+PyTorch only provides device memory and the stream; every computation runs in
+the library's kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+
+import torch
+
+from . import binding as B
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else C.c_void_p(0)
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def sample_params(d: dict) -> B.NsSampleParams:
+    p = B.NsSampleParams()
+    for k in ("delta_c", "rho", "delta_b", "h", "eta", "gamma", "pad_frac"):
+        setattr(p, k, float(d[k]))
+    p.kappa = int(d["kappa"])
+    p.nl_mult = int(d["nl_mult"])
+    p.fill_rule = int(d["fill_rule"])
+    return p
+
+
+def raster_params(d: dict) -> B.NsRasterParams:
+    r = B.NsRasterParams()
+    r.tile = int(d["tile"])
+    r.k_sigma = float(d["k_sigma"])
+    r.alpha_min = float(d["alpha_min"])
+    r.alpha_max = float(d["alpha_max"])
+    r.t_min = float(d["t_min"])
+    for i in range(3):
+        r.bg[i] = float(d["bg"][i])
+    return r
+
+
+@dataclasses.dataclass
+class Report:
+    status: int
+    bad_curve: int
+    gaussians: int
+    pairs: int
+    boundary: int
+    fill_culled: int
+
+
+class DeviceCurves:
+    """The static curve tables of a scene batch on the device (int32 CSR)."""
+
+    def __init__(self, scene, device="cuda"):
+        i32 = dict(dtype=torch.int32, device=device)
+        self.n_scenes = scene.n_scenes
+        self.height, self.width, self.channels = scene.height, scene.width, scene.channels
+        self.scene_curve_offset = torch.as_tensor(scene.scene_curve_offset, **i32)
+        self.degree = torch.as_tensor(scene.degree, **i32)
+        self.flags = torch.as_tensor(scene.flags, **i32)
+        self.key_offset = torch.as_tensor(scene.key_offset, **i32)
+        self.tau_offset = torch.as_tensor(scene.tau_offset, **i32)
+        self.n_curves = int(scene.degree.shape[0])
+        self.n_keys = int(scene.key.shape[0])
+        self.n_taus = int(scene.tau.shape[0])
+
+    def struct_sizes(self) -> B.NsCurves:
+        """The table with placeholder parameter pointers: enough for
+        ns_workspace_size, which reads sizes only."""
+        c = B.NsCurves()
+        c.n_scenes, c.n_curves, c.n_keys, c.n_taus = self.n_scenes, self.n_curves, self.n_keys, self.n_taus
+        c.height, c.width, c.channels = self.height, self.width, self.channels
+        c.scene_curve_offset = _ptr(self.scene_curve_offset)
+        c.degree, c.flags = _ptr(self.degree), _ptr(self.flags)
+        c.key_offset, c.tau_offset = _ptr(self.key_offset), _ptr(self.tau_offset)
+        c.key = c.tau = c.color = C.c_void_p(256)
+        return c
+
+    def struct(self, key, tau, color) -> B.NsCurves:
+        for t, n in ((key, self.n_keys * 4), (tau, self.n_taus), (color, self.n_curves * 4)):
+            if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous() or t.numel() != n:
+                raise ValueError("key/tau/color must be contiguous float32 CUDA tensors of the scene's sizes")
+        c = B.NsCurves()
+        c.n_scenes, c.n_curves, c.n_keys, c.n_taus = self.n_scenes, self.n_curves, self.n_keys, self.n_taus
+        c.height, c.width, c.channels = self.height, self.width, self.channels
+        c.scene_curve_offset = _ptr(self.scene_curve_offset)
+        c.degree, c.flags = _ptr(self.degree), _ptr(self.flags)
+        c.key_offset, c.tau_offset = _ptr(self.key_offset), _ptr(self.tau_offset)
+        c.key, c.tau, c.color = _ptr(key), _ptr(tau), _ptr(color)
+        return c
+
+
+class Splatter:
+    """Buffers and calls for one scene batch: nurbs_sample -> splat_forward ->
+    splat_backward on a shared workspace.  Capacities grow to the sizes the
+    library reports (`fit`); after that a step enqueues only kernels (no host
+    synchronisation), so it can be captured in a CUDA graph."""
+
+    def __init__(self, scene, sample=None, raster=None, capacity=(1 << 16, 1 << 17, 1 << 12), device="cuda"):
+        self.dev = DeviceCurves(scene, device)
+        self.device = device
+        self.sp = sample_params(sample or scene.sample)
+        self.rp = raster_params(raster or scene.raster)
+        self.cap = B.NsCapacity(*[int(x) for x in capacity])
+        self.image = torch.empty(scene.n_scenes, scene.height, scene.width, scene.channels, device=device)
+        self._alloc()
+
+    def _alloc(self):
+        lib = B.load()
+        G = max(int(self.cap.gaussians), 1)
+        self.rec = torch.empty(G, 4, device=self.device)
+        self.curve = torch.empty(G, dtype=torch.int32, device=self.device)
+        self.aux = torch.empty(G, dtype=torch.int32, device=self.device)
+        self.count = torch.zeros(1, dtype=torch.int32, device=self.device)
+        self.dgauss = torch.empty(G, 8, device=self.device)
+        cs = self.dev.struct_sizes()
+        n = lib.ns_workspace_size(C.byref(cs), C.byref(self.cap), C.byref(self.rp))
+        if n == 0:
+            raise B.NsError("ns_workspace_size", B.NS_ERR_INVALID_ARG, lib.ns_last_error().decode())
+        self.ws = torch.empty(n, dtype=torch.uint8, device=self.device)
+        self.g = B.NsGaussians(int(self.cap.gaussians), _ptr(self.rec), _ptr(self.curve), _ptr(self.aux),
+                               _ptr(self.count))
+        B.call("ns_clear_status", _ptr(self.ws), _stream())
+
+    @property
+    def ws_bytes(self):
+        return self.ws.numel()
+
+    def report(self) -> Report:
+        r = B.NsReport()
+        B.call("ns_poll_status", _ptr(self.ws), C.byref(r), _stream())
+        return Report(r.status, r.bad_curve, r.gaussians, r.pairs, r.boundary, r.fill_culled)
+
+    # -- stages ---------------------------------------------------------
+    def sample(self, key, tau, color):
+        cs = self.dev.struct(key, tau, color)
+        B.call("nurbs_sample", C.byref(cs), C.byref(self.sp), C.byref(self.cap), C.byref(self.g),
+               _ptr(self.ws), C.c_size_t(self.ws_bytes), _stream())
+
+    def forward_gaussians(self, key, tau, color, image=None):
+        cs = self.dev.struct(key, tau, color)
+        img = self.image if image is None else image
+        B.call("splat_forward", C.byref(cs), C.byref(self.g), C.byref(self.rp), C.byref(self.cap), _ptr(img),
+               _ptr(self.ws), C.c_size_t(self.ws_bytes), _stream())
+        return img
+
+    def forward(self, key, tau, color, image=None):
+        self.sample(key, tau, color)
+        return self.forward_gaussians(key, tau, color, image)
+
+    def backward(self, key, tau, color, dimage, grads=None, chain=True):
+        cs = self.dev.struct(key, tau, color)
+        if grads is None:
+            grads = (torch.empty_like(key), torch.empty_like(tau), torch.empty_like(color))
+        out = B.NsCurveGrads(_ptr(grads[0]), _ptr(grads[1]), _ptr(grads[2])) if chain else None
+        B.call("splat_backward", C.byref(cs), C.byref(self.g), C.byref(self.sp), C.byref(self.rp),
+               C.byref(self.cap), _ptr(dimage.contiguous()), _ptr(self.dgauss),
+               C.byref(out) if out is not None else None, C.c_int32(1), _ptr(self.ws),
+               C.c_size_t(self.ws_bytes), _stream())
+        return grads
+
+    def mse(self, image, target, dimage, loss):
+        B.call("ns_mse_loss", _ptr(image), _ptr(target), C.c_int64(image.numel()), _ptr(dimage), _ptr(loss),
+               _stream())
+
+    # -- sizing ---------------------------------------------------------
+    def fit(self, key, tau, color, headroom=1.25, max_rounds=4):
+        """Run sample + forward, read the sizes the library needed, and grow
+        the capacities until nothing overflows.  Synchronises."""
+        for _ in range(max_rounds):
+            self.forward(key, tau, color)
+            r = self.report()
+            if r.status not in (B.NS_OK, B.NS_ERR_CAPACITY):
+                raise B.NsError("nurbs_sample/splat_forward", r.status,
+                                f"device status {B.STATUS_NAMES.get(r.status)} (bad curve {r.bad_curve})")
+            need = (r.gaussians, r.pairs, r.boundary)
+            have = (self.cap.gaussians, self.cap.pairs, self.cap.boundary)
+            if r.status == B.NS_OK and all(n <= h for n, h in zip(need, have)):
+                return r
+            self.cap = B.NsCapacity(*[max(h, int(n * headroom) + 1) for n, h in zip(need, have)])
+            self._alloc()
+        raise RuntimeError("capacities did not converge")
+
+    def workspace_array(self, which, nbytes, dtype):
+        out = torch.empty(nbytes // torch.empty(0, dtype=dtype).element_size(), dtype=dtype, device=self.device)
+        cs = self.dev.struct(*self._last) if hasattr(self, "_last") else None
+        if cs is None:
+            raise RuntimeError("call remember() with the key/tau/color tensors first")
+        B.call("ns_workspace_copy", _ptr(self.ws), C.byref(cs), C.byref(self.cap), C.byref(self.rp),
+               C.c_int32(which), _ptr(out), C.c_size_t(nbytes), _stream())
+        return out
+
+    def remember(self, key, tau, color):
+        self._last = (key, tau, color)
+
+
+class NurbsSplatFunction(torch.autograd.Function):
+    """image = NurbsSplatFunction.apply(key, tau, color, splatter); the backward
+    runs splat_backward and returns gradients for key, tau and color."""
+
+    @staticmethod
+    def forward(ctx, key, tau, color, splatter):
+        img = splatter.forward(key, tau, color, image=torch.empty_like(splatter.image))
+        ctx.splatter = splatter
+        ctx.save_for_backward(key, tau, color)
+        return img
+
+    @staticmethod
+    def backward(ctx, dimage):
+        key, tau, color = ctx.saved_tensors
+        dk, dt, dc = ctx.splatter.backward(key, tau, color, dimage.contiguous())
+        return dk, dt, dc, None
+
+
+def scene_tensors(scene, device="cuda"):
+    """The learnable inputs of a scene as contiguous float32 device tensors."""
+    k = torch.as_tensor(scene.key, device=device).reshape(-1).contiguous()
+    t = torch.as_tensor(scene.tau, device=device).contiguous()
+    c = torch.as_tensor(scene.color, device=device).reshape(-1).contiguous()
+    return k, t, c

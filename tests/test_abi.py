@@ -1,0 +1,62 @@
+"""The C ABI library loads and exports every entry point include/*.h declares
+(no device calls: runs without a GPU)."""
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2606_31764_b300 import binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = open(h).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([A-Za-z_][A-Za-z0-9_]*)\s*\(", txt,
+                             re.M):
+            names.add(m.group(1))
+    return names - {"if", "while", "for", "return", "sizeof"}
+
+
+def test_header_declares_the_boundary():
+    d = _declared()
+    for name in ("nurbs_sample", "splat_forward", "splat_backward", "ns_workspace_size", "ns_poll_status"):
+        assert name in d
+
+
+def test_library_exports_every_declared_symbol():
+    if not os.path.exists(binding.LIB_PATH):
+        from paper_2606_31764_b300 import build
+        build.build()
+    lib = binding.load()
+    for name in _declared():
+        assert hasattr(lib, name), name
+    assert set(binding.exported_symbols()) == _declared()
+
+
+def test_defaults_match_table_s1():
+    import json
+    lib = binding.load()
+    sp = lib.ns_default_sample_params()
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "table_s1_defaults.json")))
+    for k in ("delta_c", "rho", "delta_b", "h", "eta", "gamma", "kappa", "nl_mult"):
+        assert getattr(sp, k) == pytest.approx(gold[k]), k
+
+
+def test_host_side_argument_errors_need_no_gpu():
+    import ctypes as C
+    lib = binding.load()
+    c = binding.NsCurves()
+    c.n_scenes, c.n_curves, c.height, c.width, c.channels = 1, 0, 32, 32, 2   # channels must be 1 or 3
+    cap = binding.NsCapacity(16, 16, 16)
+    rp = lib.ns_default_raster_params()
+    assert lib.ns_workspace_size(C.byref(c), C.byref(cap), C.byref(rp)) == 0
+    assert b"channels" in lib.ns_last_error()
+    c.channels = 3
+    assert lib.ns_workspace_size(C.byref(c), C.byref(cap), C.byref(rp)) > 0
+    rp.tile = 12
+    assert lib.ns_workspace_size(C.byref(c), C.byref(cap), C.byref(rp)) == 0

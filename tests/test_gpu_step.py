@@ -1,0 +1,56 @@
+"""The whole step on the GPU (sample -> splat -> L2 loss -> backward through
+the curves) against the oracle's FP64 values and exact gradients.
+
+Gradients: per tensor ||g_gpu - g_ref|| <= 1e-3 ||g_ref|| and elementwise
+|g_gpu - g_ref| <= 1e-3 max|g_ref|.  The end-to-end image tolerance follows
+from the record bound of the sampling test: records move by up to
+32 eps32 (W + L) px, and an isotropic Gaussian's alpha has slope at most
+1/(sigma sqrt(e)) per px, so |dI| <= 32 eps32 (W + L) / sigma_min + 1e-5."""
+import math
+
+import numpy as np
+import pytest
+
+import scenes
+from oracle import pipeline as op
+
+from gpu_util import run_step
+
+pytestmark = pytest.mark.gpu
+EPS32 = float(np.finfo(np.float32).eps)
+
+CASES = [
+    ("open", lambda: scenes.small_open(51, n_curves=3, size=48, p=(2, 3, 5))),
+    ("open-gray", lambda: scenes.small_open(52, n_curves=3, size=40, channels=1)),
+    ("closed-strokes", lambda: scenes.small_closed(53, n_curves=3, size=48, filled=False, degrees=(2, 3, 4))),
+    ("filled", lambda: scenes.small_closed(54, n_curves=3, size=48, filled=True, h=2.0)),
+    ("filled-h1-batched", lambda: scenes.small_closed(55, n_curves=2, size=40, filled=True, h=1.0, n_scenes=2)),
+    ("config1", lambda: scenes.config1().with_raster(**scenes.RASTER_PARITY)),
+]
+
+
+def _rel_ok(gpu, ref, tol=1e-3):
+    gpu = np.asarray(gpu, np.float64).reshape(-1)
+    ref = np.asarray(ref, np.float64).reshape(-1)
+    nr = np.linalg.norm(ref)
+    if nr == 0:
+        return np.abs(gpu).max() <= 1e-9
+    return (np.linalg.norm(gpu - ref) <= tol * nr) and (np.abs(gpu - ref).max() <= tol * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+def test_step_matches_oracle(name, make):
+    sc = make()
+    ref = op.loss_and_grads(sc)
+    assert all(m > 1e-3 for p in ref["plans"] for m in p.margin.values())
+    out = run_step(sc)
+    assert out["report"].status == 0
+    Lmax = max(p.length for p in ref["plans"])
+    smin = float(np.min(ref["gaussians"]["sigma"])) if ref["gaussians"]["sigma"].size else 1.0
+    tol_img = 32 * EPS32 * (max(sc.width, sc.height) + Lmax) / (smin * math.sqrt(math.e)) + 1e-5
+    assert np.abs(out["image"] - ref["image"]).max() <= tol_img
+    assert abs(out["loss"] - ref["loss"]) <= 1e-4 * ref["loss"] + 1e-7
+    assert _rel_ok(out["dcolor"], ref["dcolor"]), "dcolor"
+    assert _rel_ok(out["dtau"], ref["dtau"]), "dtau"
+    for j, nm in enumerate("xysw"):
+        assert _rel_ok(out["dkey"][:, j], ref["dkey"][:, j]), "dkey." + nm
