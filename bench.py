@@ -1,0 +1,490 @@
+#!/usr/bin/env python
+"""Benchmark of the NURBS splatting step: fwd+bwd Gaussians/s.
+
+One step = nurbs_sample -> splat_forward -> L2 loss -> splat_backward (blend
+adjoint + chain into key points, knot intervals, colours and opacities) over
+one batch of synthetic scenes resident in HBM.  The workload is the 1024x1024
+vectorisation-scale scene (2048 closed filled NURBS paths, p in {2..5}, 8-64
+key points, fill grid step h = 1, ~8M Gaussians).  The step is captured as a
+CUDA graph; the timed region replays one graph holding K steps back to back.
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import scenes  # noqa: E402
+
+PEAKS_FALLBACK = dict(hbm_gbs=6400.0, sm_max_mhz=2032.0)
+METRIC = "fwd+bwd Gaussians/s at 1024^2 (batched, graph-captured step)"
+FLOP_SEGMENT = 20        # one (grid point, boundary segment) SDF test: distance 14 + crossing 6
+FLOP_EVAL = 10           # one alpha evaluation (Eq. 9): dx, dy, d^2, scale, exp arg, *o, cap, skip test
+FLOP_CONTRIB_FWD = 10    # composite one pair (Eq. 8), 3 channels
+FLOP_CONTRIB_BWD = 33    # adjoint of one composited pair, 3 channels
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-per-scene", action="store_true")
+    ap.add_argument("--paths", type=int, default=2048, help="paths of the 1024x1024 workload (2048 = full)")
+    ap.add_argument("--cpu-sample-curves", type=int, default=64)
+    ap.add_argument("--ref-sample-curves", type=int, default=8)
+    return ap.parse_args()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return dict(hbm_gbs=float(d["hbm_gbs"]), sm_max_mhz=float(d.get("sm_max_mhz", 2032.0)), source="measured")
+    return dict(PEAKS_FALLBACK, source="fallback")
+
+
+# ----------------------------------------------------------------------------
+# distributed plumbing (one process per GPU; replicas of independent scenes)
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+        return dist, rank, ws
+    return None, 0, 1
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, x):
+    if dist is None:
+        return x
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["unavailable"], samples=0)
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["no samples"], samples=0)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return dict(sm_mhz=float(np.median(sm)) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                    reasons=sorted(reasons), samples=len(rows))
+
+
+# ----------------------------------------------------------------------------
+# the GPU step
+
+class Step:
+    """Preallocated buffers and the four calls of one training step."""
+
+    def __init__(self, scene, capacity):
+        import torch
+        from paper_2606_31764_b300.splat import Splatter, scene_tensors
+        self.torch = torch
+        self.scene = scene
+        self.sp = Splatter(scene, capacity=capacity)
+        self.key, self.tau, self.color = scene_tensors(scene)
+        self.rep = self.sp.fit(self.key, self.tau, self.color)
+        self.target = torch.as_tensor(scene.target, device="cuda").contiguous()
+        self.image = self.sp.image
+        self.dimage = torch.empty_like(self.image)
+        self.loss = torch.zeros(1, device="cuda")
+        self.grads = (torch.empty_like(self.key), torch.empty_like(self.tau), torch.empty_like(self.color))
+
+    def __call__(self):
+        sp = self.sp
+        sp.sample(self.key, self.tau, self.color)
+        sp.forward_gaussians(self.key, self.tau, self.color, self.image)
+        sp.mse(self.image, self.target, self.dimage, self.loss)
+        sp.backward(self.key, self.tau, self.color, self.dimage, grads=self.grads)
+
+    def gaussians(self):
+        return int(self.sp.count.item())
+
+
+def capture(torch, fn, n_steps=1, arm=None):
+    """A CUDA graph of n_steps calls of fn; arm(i) arms profiling before step i."""
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        fn()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for i in range(n_steps):
+            if arm is not None:
+                arm(i)
+            fn()
+    return g
+
+
+def plan_costs(step):
+    """Per-step unit counts from the sampling plans: SDF segment tests and
+    contour samples."""
+    import torch
+    sp = step.sp
+    nc = step.scene.n_curves
+    sp.remember(step.key, step.tau, step.color)
+    raw = sp.workspace_array(3, 64 * nc, torch.int32).cpu().numpy().reshape(nc, 16)
+    kind, M, cnt = raw[:, 5], raw[:, 6], raw[:, 7]
+    fill = kind == 3
+    return dict(segment_tests=int((cnt[fill].astype(np.int64) * M[fill]).sum()),
+                fill_gaussians=int(cnt[fill].sum()), contour_gaussians=int(cnt[~fill].sum()))
+
+
+def run_gpu(args, dist, rank, world):
+    import torch
+    from paper_2606_31764_b300 import binding as B
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    lib = B.load()
+    peaks = load_peaks()
+    sc = scenes.config5(seed=1005 + rank, n_paths=args.paths)
+    step = Step(sc, capacity=(10_000_000, 20_000_000, 400_000))
+    step()
+    torch.cuda.synchronize()
+    rep = step.sp.report()
+    if rep.status != 0:
+        raise RuntimeError(f"device status {rep}")
+    G = step.gaussians()
+    costs = plan_costs(step)
+
+    # kernels per step (counted by the library while one step is enqueued)
+    n0 = lib.ns_launch_count()
+    step()
+    launches_per_step = int(lib.ns_launch_count() - n0)
+    g1 = capture(torch, step)
+    for _ in range(args.warmup):
+        g1.replay()
+    torch.cuda.synchronize()
+
+    # K-step graph with per-kernel events armed in every step
+    prof = ["emit", "bin_emit", "radix_scatter", "blend_fwd", "blend_bwd", "chain", "chain_boundary"]
+    ev = {k: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)] for k in prof}
+    for k in prof:                      # torch creates the CUDA events on first record
+        for a, b in ev[k]:
+            a.record()
+            b.record()
+    torch.cuda.synchronize()
+
+    def arm(i):
+        for k in prof:
+            a, b = ev[k][i]
+            B.call("ns_profile_next_launch", C.c_int32(B.KERNELS[k]), C.c_void_p(a.cuda_event),
+                   C.c_void_p(b.cuda_event))
+
+    gK = capture(torch, step, args.steps, arm)
+    lib.ns_profile_next_launch(0, None, None)
+    gK.replay()          # warm the K-step graph once
+    torch.cuda.synchronize()
+    rep = step.sp.report()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier(dist)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    e0.record()
+    gK.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    barrier(dist)
+    ck = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    ms_total = max_over_ranks(dist, ms_total)
+    ms_step = ms_total / args.steps
+    per_kernel = {k: float(np.mean([a.elapsed_time(b) for a, b in ev[k]])) for k in prof}
+    value = world * G * args.steps / (ms_total / 1e3)
+
+    # roofline of the dominant kernel
+    clk = peaks["sm_max_mhz"] * 1e6
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    fp32_peak = 2.0 * 128 * sms * clk / 1e12        # TFLOP/s, FMA = 2 FLOP
+    work = dict(
+        emit=("alu", costs["segment_tests"] * FLOP_SEGMENT / 1e12, "TFLOP/s", fp32_peak),
+        blend_fwd=("alu", (rep.blend_evals * FLOP_EVAL + rep.blend_contribs * FLOP_CONTRIB_FWD) / 1e12, "TFLOP/s",
+                   fp32_peak),
+        blend_bwd=("alu", (rep.blend_bwd_evals * FLOP_EVAL + rep.blend_contribs * FLOP_CONTRIB_BWD) / 1e12,
+                   "TFLOP/s", fp32_peak),
+        radix_scatter=("hbm", rep.pairs * 16 / 1e9, "GB/s", peaks["hbm_gbs"]),
+        bin_emit=("hbm", (G * 16 + G * 4 + rep.pairs * 8) / 1e9, "GB/s", peaks["hbm_gbs"]),
+    )
+    dom = max(per_kernel, key=per_kernel.get)
+    kernels = {}
+    for k, ms in per_kernel.items():
+        d = dict(ms=round(ms, 4), share_of_step=round(ms / ms_step, 4))
+        if k in work:
+            bound, amount, unit, peak = work[k]
+            ach = amount / (ms / 1e3)
+            d.update(bound=bound, achieved=round(ach, 3), unit=unit, frac=round(ach / peak, 4))
+        kernels[k] = d
+    roof = None
+    if dom in work:
+        bound, amount, unit, peak = work[dom]
+        ach = amount / (per_kernel[dom] / 1e3)
+        roof = dict(kernel=dom, bound=bound, achieved=round(ach, 3), peak=round(peak, 2), unit=unit,
+                    frac=round(ach / peak, 4), traffic=None,
+                    peak_source=("FP32 lanes x SMs x max SM clock" if bound == "alu"
+                                 else f"{peaks['source']} HBM copy bandwidth"))
+
+    # end to end through the public API with host buffers
+    e2e = run_e2e(torch, step, g1, args)
+
+    out = dict(metric=METRIC, value=round(value, 1), unit="Gaussians/s", n_gpus=world, steps=args.steps,
+               warmup=args.warmup, ms_per_step=round(ms_step, 4), higher_is_better=True,
+               scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+               config=dict(workload=f"vectorize-{args.paths}-1024: 1024x1024 RGB, {args.paths} closed filled NURBS "
+                                    "paths p in {2,3,4,5}, 8-64 key points, fill grid step h=1",
+                           gaussians_per_step=G, pairs_per_step=int(rep.pairs), curves=sc.n_curves,
+                           fill_culled=int(rep.fill_culled), l2="inputs larger than L2 (records+pairs "
+                           f"{(G * 32 + rep.pairs * 16) / 1e6:.0f} MB > 126 MB)",
+                           timed="one CUDA-graph replay of K steps", parallelism=f"replicas x{world}"),
+               gpu_launches=launches_per_step * args.steps, launches_per_step=launches_per_step,
+               clocks=ck, roofline=roof, kernels=kernels, e2e=e2e,
+               blend=dict(evals_fwd=int(rep.blend_evals), evals_bwd=int(rep.blend_bwd_evals),
+                          composited=int(rep.blend_contribs)),
+               sample=costs)
+    if not args.no_per_scene:
+        out["per_scene"] = run_per_scene(torch, step, args, value)
+    return out, step
+
+
+def run_e2e(torch, step, g1, args):
+    """Same metric through the public API with host buffers: every step copies
+    key points, knot intervals and colours from pinned host memory, replays the
+    step and reads the loss and all gradients back."""
+    hk = step.key.cpu().pin_memory()
+    ht = step.tau.cpu().pin_memory()
+    hc = step.color.cpu().pin_memory()
+    out = [torch.empty(x.shape, dtype=x.dtype, pin_memory=True) for x in (step.loss, *step.grads)]
+    h2d = sum(x.numel() * 4 for x in (hk, ht, hc))
+    d2h = sum(x.numel() * 4 for x in out)
+    G = step.gaussians()
+    K = max(2, args.steps // 2)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(K):
+        step.key.copy_(hk, non_blocking=True)
+        step.tau.copy_(ht, non_blocking=True)
+        step.color.copy_(hc, non_blocking=True)
+        g1.replay()
+        for dst, src in zip(out, (step.loss, *step.grads)):
+            dst.copy_(src, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return dict(value=round(G * K / (ms / 1e3), 1), unit="Gaussians/s", h2d_bytes_per_step=h2d,
+                d2h_bytes_per_step=d2h, steps=K, ms_per_step=round(ms / K, 4))
+
+
+def run_per_scene(torch, step, args, batched_value):
+    """The unbatched comparison: the batched 64-scene workload (256x256 RGB,
+    1-40 closed paths per scene, half filled at h = 1) launched scene by scene
+    with host reads of the counts between stages and no graph, against the
+    same scenes in one batched, graph-captured step."""
+    from paper_2606_31764_b300.splat import Splatter, scene_tensors
+    sc = scenes.config4()
+    K = max(2, min(args.steps, 5))
+    # batched
+    bstep = Step(sc, capacity=(4_000_000, 8_000_000, 200_000))
+    gb = capture(torch, bstep)
+    for _ in range(2):
+        gb.replay()
+    torch.cuda.synchronize()
+    Gb = bstep.gaussians()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        gb.replay()
+    torch.cuda.synchronize()
+    tb = (time.perf_counter() - t0) / K
+    del gb
+    # per scene
+    subs = [sc.subset([s]) for s in range(sc.n_scenes)]
+    steps = [Step(x, capacity=(200_000, 400_000, 20_000)) for x in subs]
+    Gs = sum(s.gaussians() for s in steps)
+
+    def one_pass():
+        for s in steps:
+            s.sp.sample(s.key, s.tau, s.color)
+            s.sp.report()                      # host reads the counts
+            s.sp.forward_gaussians(s.key, s.tau, s.color, s.image)
+            s.sp.report()
+            s.sp.mse(s.image, s.target, s.dimage, s.loss)
+            s.sp.backward(s.key, s.tau, s.color, s.dimage, grads=s.grads)
+            torch.cuda.synchronize()
+
+    one_pass()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        one_pass()
+    tp = (time.perf_counter() - t0) / K
+    return dict(workload="batched-64x256: 64 scenes 256x256 RGB, 1-40 closed paths each",
+                batched_gaussians_per_s=round(Gb / tb, 1), per_scene_gaussians_per_s=round(Gs / tp, 1),
+                speedup=round((Gb / tb) / (Gs / tp), 2), gaussians_per_step=Gb, ms_batched=round(tb * 1e3, 3),
+                ms_per_scene_path=round(tp * 1e3, 3))
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle on a bounded sample
+
+def oracle_sample_scene(n_curves, seed=1005):
+    """The first n_curves paths of the 1024x1024 workload (same generator)."""
+    sc = scenes.config5(seed=seed)
+    b = scenes._Builder(1, sc.height, sc.width, sc.channels)
+    for c in range(n_curves):
+        k0, k1 = sc.key_offset[c], sc.key_offset[c + 1]
+        t0, t1 = sc.tau_offset[c], sc.tau_offset[c + 1]
+        b.add(0, int(sc.degree[c]), sc.key[k0:k1], sc.tau[t0:t1], sc.color[c], True, True)
+    return b.build("vectorize-sample", sc.target, dict(sc.sample), dict(sc.raster))
+
+
+def run_oracle_sample(n_curves):
+    import torch
+    from oracle import pipeline as op
+    sub = oracle_sample_scene(n_curves)
+    t0 = time.perf_counter()
+    ref = op.loss_and_grads(sub)
+    dt = time.perf_counter() - t0
+    G = int(sum(p.count for p in ref["plans"]))
+    return sub, ref, dt, G, torch.get_num_threads()
+
+
+def grad_rel_err(sub, ref):
+    """GPU step on the oracle's sample; max over tensors of ||g - g_ref|| / ||g_ref||."""
+    import torch
+    step = Step(sub, capacity=(200_000, 800_000, 20_000))
+    step()
+    torch.cuda.synchronize()
+    errs = {}
+    for nm, g, r in (("dkey", step.grads[0], ref["dkey"]), ("dtau", step.grads[1], ref["dtau"]),
+                     ("dcolor", step.grads[2], ref["dcolor"])):
+        gg = g.cpu().numpy().astype(np.float64).reshape(-1)
+        rr = np.asarray(r, np.float64).reshape(-1)
+        errs[nm] = float(np.linalg.norm(gg - rr) / max(np.linalg.norm(rr), 1e-30))
+    img_err = float(np.abs(step.image.cpu().numpy() - ref["image"]).max())
+    return max(errs.values()), errs, img_err
+
+
+def main():
+    args = parse()
+    dist, rank, world = dist_setup(args)
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        sub, ref, dt, G, cores = run_oracle_sample(args.ref_sample_curves)   # also the warm-up
+        times = []
+        from oracle import pipeline as op
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            op.loss_and_grads(sub)
+            times.append(time.perf_counter() - t0)
+        ms = 1e3 * float(np.mean(times))
+        val = G / (ms / 1e3)
+        sample = (f"first {args.ref_sample_curves} of the 2048 paths of the 1024x1024 workload, full canvas, "
+                  f"{G} Gaussians per step")
+        print(json.dumps(dict(impl="reference", metric=METRIC, value=round(val, 1), unit="Gaussians/s",
+                              n_gpus=world, steps=args.steps, warmup=args.warmup, ms_per_step=round(ms, 2),
+                              higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+                              data="synthetic", config=dict(workload="vectorize-2048-1024 (bounded sample)"),
+                              cpu_baseline=dict(value=round(val, 1), unit="Gaussians/s", cores=cores,
+                                                kind="oracle", sample=sample),
+                              e2e=dict(value=round(val, 1), unit="Gaussians/s", h2d_bytes_per_step=0,
+                                       d2h_bytes_per_step=0))))
+        return
+    out, _ = run_gpu(args, dist, rank, world)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sub, ref, dt, G, cores = run_oracle_sample(args.cpu_sample_curves)
+        out["cpu_baseline"] = dict(value=round(G / dt, 1), unit="Gaussians/s", cores=cores, kind="oracle",
+                                   sample=f"first {args.cpu_sample_curves} of the 2048 paths of the 1024x1024 "
+                                          f"workload on the full canvas, {G} Gaussians, one fwd+bwd",
+                                   seconds=round(dt, 2))
+        gre, errs, img_err = grad_rel_err(sub, ref)
+        out["grad_rel_err"] = round(gre, 7)
+        out["grad_rel_err_detail"] = {k: round(v, 7) for k, v in errs.items()}
+        out["image_max_abs_err_vs_oracle"] = img_err
+    if rank == 0:
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

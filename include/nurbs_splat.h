@@ -136,7 +136,19 @@ typedef struct {
   int64_t pairs;         /* tile pairs the last splat_forward needed */
   int64_t boundary;      /* boundary points the last nurbs_sample needed */
   int64_t fill_culled;   /* fill Gaussians with opacity below alpha_min (bin no tile) */
+  int64_t blend_evals;   /* (pixel, Gaussian) alpha evaluations of the last splat_forward */
+  int64_t blend_bwd_evals; /* the same for the last splat_backward */
+  int64_t blend_contribs;  /* (pixel, Gaussian) pairs composited by the last splat_forward */
 } ns_report;
+
+/* Kernel ids for ns_profile_next_launch. */
+enum {
+  NS_KERNEL_PLAN = 1, NS_KERNEL_BOUNDARY = 2, NS_KERNEL_EMIT = 3, NS_KERNEL_BIN_COUNT = 4,
+  NS_KERNEL_BIN_EMIT = 5, NS_KERNEL_RADIX_HIST = 6, NS_KERNEL_RADIX_SCATTER = 7, NS_KERNEL_RANGES = 8,
+  NS_KERNEL_BLEND_FWD = 9, NS_KERNEL_BLEND_BWD = 10, NS_KERNEL_CHAIN = 11, NS_KERNEL_CHAIN_BOUNDARY = 12,
+  NS_KERNEL_KNOT_GRADS = 13, NS_KERNEL_MSE = 14, NS_KERNEL_ADAM = 15, NS_KERNEL_SCAN = 16,
+  NS_KERNEL_OTHER = 17
+};
 
 ns_sample_params ns_default_sample_params(void);
 ns_raster_params ns_default_raster_params(void);
@@ -245,6 +257,19 @@ ns_status ns_clear_status(void* workspace, void* stream);
 ns_status ns_workspace_copy(void* workspace, const ns_curves* curves, const ns_capacity* cap,
                             const ns_raster_params* rp, int32_t which, void* dst,
                             size_t bytes, void* stream);
+
+/*
+ * Profiling aid.  The next launch of kernel `kernel_id` issued by the calling
+ * thread records the cudaEvent_t `start` just before it and `stop` just after
+ * it on the launch stream; while that stream is being captured into a CUDA
+ * graph the two records are captured as external event-record nodes, so they
+ * fire on every replay.  Up to 32 launches can be armed at once (each call
+ * arms one; each armed entry fires once).  kernel_id 0 disarms all.
+ */
+ns_status ns_profile_next_launch(int32_t kernel_id, void* start, void* stop);
+
+/* Number of kernels the calling thread has launched (or captured) through the library. */
+uint64_t ns_launch_count(void);
 
 /* Message of the last error on the calling thread ("" if none). */
 const char* ns_last_error(void);

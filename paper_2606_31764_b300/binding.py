@@ -52,7 +52,8 @@ class NsCurveGrads(C.Structure):
 
 class NsReport(C.Structure):
     _fields_ = [("status", C.c_int32), ("bad_curve", C.c_int32), ("gaussians", C.c_int64), ("pairs", C.c_int64),
-                ("boundary", C.c_int64), ("fill_culled", C.c_int64)]
+                ("boundary", C.c_int64), ("fill_culled", C.c_int64), ("blend_evals", C.c_int64),
+                ("blend_bwd_evals", C.c_int64), ("blend_contribs", C.c_int64)]
 
 
 # name -> (restype, argtypes); the declarations of include/nurbs_splat.h
@@ -74,8 +75,14 @@ SIGNATURES = {
     "ns_clear_status": (C.c_int, [_p, _p]),
     "ns_workspace_copy": (C.c_int, [_p, C.POINTER(NsCurves), C.POINTER(NsCapacity), C.POINTER(NsRasterParams),
                                     C.c_int32, _p, C.c_size_t, _p]),
+    "ns_profile_next_launch": (C.c_int, [C.c_int32, _p, _p]),
+    "ns_launch_count": (C.c_uint64, []),
     "ns_last_error": (C.c_char_p, []),
 }
+
+KERNELS = dict(plan=1, boundary=2, emit=3, bin_count=4, bin_emit=5, radix_hist=6, radix_scatter=7, ranges=8,
+               blend_fwd=9, blend_bwd=10, chain=11, chain_boundary=12, knot_grads=13, mse=14, adam=15, scan=16,
+               other=17)
 
 _lib = None
 

@@ -10,13 +10,53 @@
 namespace ns {
 
 static thread_local std::string g_error;
+static thread_local unsigned long long g_launches = 0;
+// Armed profiling records: one-shot (kernel, start event, stop event) entries.
+struct ProfArm {
+  int kernel;
+  cudaEvent_t start, stop;
+  bool started;
+};
+constexpr int kMaxArms = 32;
+static thread_local ProfArm g_arms[kMaxArms];
+static thread_local int g_n_arms = 0;
 
 void set_error(const std::string& msg) { g_error = msg; }
 
+static void record_event(cudaEvent_t e, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  if (cs == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+  else cudaEventRecord(e, s);
+}
+
+void before_launch(int kernel_id, cudaStream_t s) {
+  ++g_launches;
+  for (int i = 0; i < g_n_arms; ++i)
+    if (g_arms[i].kernel == kernel_id && !g_arms[i].started) {
+      record_event(g_arms[i].start, s);
+      g_arms[i].started = true;
+      break;
+    }
+}
+
+void after_launch(int kernel_id, cudaStream_t s) {
+  for (int i = 0; i < g_n_arms; ++i)
+    if (g_arms[i].kernel == kernel_id && g_arms[i].started) {
+      record_event(g_arms[i].stop, s);
+      g_arms[i] = g_arms[--g_n_arms];   // one shot: drop the entry
+      break;
+    }
+}
+
 int num_sms() {
+  static thread_local int cached_dev = -1, cached_n = 148;
   int dev = 0, n = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return 148;
-  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 148;
+  if (cudaGetDevice(&dev) != cudaSuccess) return cached_n;
+  if (dev == cached_dev) return cached_n;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return cached_n;
+  cached_dev = dev;
+  cached_n = n;
   return n;
 }
 
@@ -109,9 +149,10 @@ __global__ void k_reset_state(DevState* st) {
   st->n_chunks = 0;
   st->g_total = st->b_total = st->pair_total = st->culled = 0;
   st->g_count = st->pair_count = st->b_count = 0;
+  st->blend_evals = st->blend_bwd_evals = st->blend_contribs = 0;
 }
 
-void launch_reset_state(DevState* st, cudaStream_t s) { k_reset_state<<<1, 1, 0, s>>>(st); }
+void launch_reset_state(DevState* st, cudaStream_t s) { NS_LAUNCH(NS_KERNEL_OTHER, k_reset_state, 1, 1, 0, s, st); }
 
 __global__ void __launch_bounds__(256) k_mse(const float* __restrict__ a, const float* __restrict__ b, long long n,
                                              float* __restrict__ grad, float* loss) {
@@ -203,6 +244,9 @@ ns_status ns_poll_status(void* ws, ns_report* r, void* stream) {
   r->pairs = (int64_t)st.pair_total;
   r->boundary = (int64_t)st.b_total;
   r->fill_culled = (int64_t)st.culled;
+  r->blend_evals = (int64_t)st.blend_evals;
+  r->blend_bwd_evals = (int64_t)st.blend_bwd_evals;
+  r->blend_contribs = (int64_t)st.blend_contribs;
   return NS_OK;
 }
 
@@ -211,7 +255,7 @@ ns_status ns_clear_status(void* ws, void* stream) {
     set_error("ns_clear_status: null workspace");
     return NS_ERR_INVALID_ARG;
   }
-  k_reset_state<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<DevState*>(ws));
+  NS_LAUNCH(NS_KERNEL_OTHER, k_reset_state, 1, 1, 0, static_cast<cudaStream_t>(stream), static_cast<DevState*>(ws));
   return cudaGetLastError() == cudaSuccess ? NS_OK : NS_ERR_CUDA;
 }
 
@@ -224,7 +268,7 @@ ns_status ns_mse_loss(const float* image, const float* target, int64_t n, float*
   cudaMemsetAsync(loss, 0, sizeof(float), s);
   const long long blocks = (n + 255) / 256;
   const int grid = int(blocks < num_sms() * 8 ? blocks : num_sms() * 8);
-  k_mse<<<grid, 256, 0, s>>>(image, target, n, dL, loss);
+  NS_LAUNCH(NS_KERNEL_MSE, k_mse, grid, 256, 0, s, image, target, n, dL, loss);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_error(std::string("ns_mse_loss: ") + cudaGetErrorString(e));
@@ -244,7 +288,7 @@ ns_status ns_adam_step(float* param, const float* grad, float* m, float* v, int6
   const float c2 = 1.f - powf(beta2, float(step));
   const long long blocks = (n + 255) / 256;
   const int grid = int(blocks < num_sms() * 8 ? blocks : num_sms() * 8);
-  k_adam<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(param, grad, m, v, n, lr, beta1, beta2, eps, c1, c2,
+  NS_LAUNCH(NS_KERNEL_ADAM, k_adam, grid, 256, 0, static_cast<cudaStream_t>(stream), param, grad, m, v, n, lr, beta1, beta2, eps, c1, c2,
                                                                lo, hi);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -286,6 +330,25 @@ ns_status ns_workspace_copy(void* ws, const ns_curves* curves, const ns_capacity
   }
   return NS_OK;
 }
+
+ns_status ns_profile_next_launch(int32_t kernel_id, void* start, void* stop) {
+  if (kernel_id == 0) {
+    g_n_arms = 0;
+    return NS_OK;
+  }
+  if (!start || !stop) {
+    set_error("ns_profile_next_launch: events required");
+    return NS_ERR_INVALID_ARG;
+  }
+  if (g_n_arms >= kMaxArms) {
+    set_error("ns_profile_next_launch: too many armed launches");
+    return NS_ERR_INVALID_ARG;
+  }
+  g_arms[g_n_arms++] = ProfArm{kernel_id, static_cast<cudaEvent_t>(start), static_cast<cudaEvent_t>(stop), false};
+  return NS_OK;
+}
+
+uint64_t ns_launch_count(void) { return g_launches; }
 
 const char* ns_last_error(void) { return g_error.c_str(); }
 

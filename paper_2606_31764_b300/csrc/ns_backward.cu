@@ -380,12 +380,12 @@ extern "C" ns_status splat_backward(const ns_curves* curves, const ns_gaussians*
       cp.h = sp->h;
       cp.gamma = sp->gamma;
       cp.kappa = sp->kappa;
-      k_chain<<<num_sms() * 8, 256, 0, s>>>(*curves, cp, plan, order, knots, bpts, st,
+      NS_LAUNCH(NS_KERNEL_CHAIN, k_chain, num_sms() * 8, 256, 0, s, *curves, cp, plan, order, knots, bpts, st,
                                             reinterpret_cast<const float4*>(g->rec), g->aux, dg, cap->gaussians,
                                             cap->boundary, out->dkey, dknots, dbpts, out->dcolor);
       if (L.bcap > 0)
-        k_chain_boundary<<<num_sms() * 4, 256, 0, s>>>(*curves, plan, knots, st, dbpts, out->dkey, dknots);
-      k_knot_grads<<<(L.nc + 127) / 128, 128, 0, s>>>(*curves, plan, dknots, out->dtau);
+        NS_LAUNCH(NS_KERNEL_CHAIN_BOUNDARY, k_chain_boundary, num_sms() * 4, 256, 0, s, *curves, plan, knots, st, dbpts, out->dkey, dknots);
+      NS_LAUNCH(NS_KERNEL_KNOT_GRADS, k_knot_grads, (L.nc + 127) / 128, 128, 0, s, *curves, plan, dknots, out->dtau);
     }
   }
   const cudaError_t e = cudaGetLastError();

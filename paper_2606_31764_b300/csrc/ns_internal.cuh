@@ -34,6 +34,9 @@ struct DevState {
   int pair_count;      // min(pair_total, capacity)
   int b_count;
   int pad[5];
+  unsigned long long blend_evals;      // alpha evaluations of the last forward blend
+  unsigned long long blend_bwd_evals;  // alpha evaluations of the last backward blend
+  unsigned long long blend_contribs;   // composited (pixel, Gaussian) pairs of the last forward blend
 };
 
 // One curve's sampling plan (written by the planning kernels).
@@ -67,6 +70,16 @@ void set_error(const std::string& msg);
 bool make_layout(const ns_curves* c, const ns_capacity* cap, const ns_raster_params* rp, Layout* L);
 int num_sms();
 void launch_reset_state(DevState* st, cudaStream_t s);
+
+// Launch bookkeeping: counts launches and fires the armed profiling events.
+void before_launch(int kernel_id, cudaStream_t s);
+void after_launch(int kernel_id, cudaStream_t s);
+#define NS_LAUNCH(id, kernel, grid, block, smem, stream, ...)   \
+  do {                                                         \
+    ::ns::before_launch(id, stream);                           \
+    kernel<<<grid, block, smem, stream>>>(__VA_ARGS__);        \
+    ::ns::after_launch(id, stream);                            \
+  } while (0)
 
 template <typename T>
 inline T* at(void* ws, size_t off) { return reinterpret_cast<T*>(static_cast<char*>(ws) + off); }

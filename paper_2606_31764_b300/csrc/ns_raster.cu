@@ -347,11 +347,17 @@ __device__ __forceinline__ float gauss_alpha(float fx, float fy, float4 q, float
 
 __device__ __forceinline__ float ncoef(float sigma) { return __fdiv_rn(-0.5f, __fmul_rn(sigma, sigma)); }
 
+// Adds a per-thread count to a device counter, one atomic per warp.
+__device__ __forceinline__ void count_evals(unsigned long long* ctr, unsigned int v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(ctr, (unsigned long long)v);
+}
+
 template <int C>
 __global__ void __launch_bounds__(256) k_blend_fwd(const int2* __restrict__ ranges, const uint32_t* __restrict__ gid,
                                                    const float4* __restrict__ rec, const int* __restrict__ gcurve,
                                                    const float4* __restrict__ color, BlendParams bp, float* image,
-                                                   float* Tfinal, int* nlast) {
+                                                   float* Tfinal, int* nlast, DevState* st) {
   __shared__ float4 s_g[256];
   __shared__ float4 s_c[256];
   const int tile = blockIdx.x;
@@ -368,6 +374,7 @@ __global__ void __launch_bounds__(256) k_blend_fwd(const int2* __restrict__ rang
   for (int ch = 0; ch < C; ++ch) acc[ch] = 0.f;
   bool done = !inside;
   int last = 0;
+  unsigned int evals = 0, contribs = 0;
   for (int base = 0; base < n; base += 256) {
     const int idx = base + threadIdx.x;
     if (idx < n) {
@@ -379,7 +386,8 @@ __global__ void __launch_bounds__(256) k_blend_fwd(const int2* __restrict__ rang
     __syncthreads();
     if (!done) {
       const int cnt = min(256, n - base);
-      for (int k = 0; k < cnt; ++k) {
+      int k = 0;
+      for (; k < cnt; ++k) {
         float dx, dy, d2, e;
         const float a = gauss_alpha(fx, fy, s_g[k], bp.alpha_max, dx, dy, d2, e);
         if (a < bp.alpha_min) continue;
@@ -394,10 +402,14 @@ __global__ void __launch_bounds__(256) k_blend_fwd(const int2* __restrict__ rang
         }
         T = test;
         last = base + k + 1;
+        ++contribs;
       }
+      evals += (unsigned int)min(k + 1, cnt);
     }
     if (__syncthreads_count(done) == (int)blockDim.x) break;
   }
+  count_evals(&st->blend_evals, evals);
+  count_evals(&st->blend_contribs, contribs);
   if (inside) {
     const long long pix = ((long long)s * bp.H + py) * bp.W + px;
     float* out = image + pix * C;
@@ -416,7 +428,7 @@ __global__ void __launch_bounds__(256) k_blend_bwd(const int2* __restrict__ rang
                                                    const float4* __restrict__ rec, const int* __restrict__ gcurve,
                                                    const float4* __restrict__ color, BlendParams bp,
                                                    const float* __restrict__ dimage, const float* __restrict__ Tfinal,
-                                                   const int* __restrict__ nlast, float* dgauss) {
+                                                   const int* __restrict__ nlast, float* dgauss, DevState* st) {
   __shared__ float4 s_g[256];
   __shared__ float4 s_c[256];
   __shared__ float s_sig[256];
@@ -445,6 +457,7 @@ __global__ void __launch_bounds__(256) k_blend_bwd(const int2* __restrict__ rang
   __syncthreads();
   const int nmax = s_max;
   const int lane = threadIdx.x & 31;
+  count_evals(&st->blend_bwd_evals, (unsigned int)last);
   for (int end = nmax; end > 0; end -= 256) {
     const int beg = max(0, end - 256);
     const int idx = beg + threadIdx.x;
@@ -596,8 +609,10 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
   const float4* rec = reinterpret_cast<const float4*>(g->rec);
 
   cudaMemsetAsync(&st->culled, 0, sizeof(unsigned long long), s);
+  cudaMemsetAsync(&st->blend_evals, 0, sizeof(unsigned long long), s);
+  cudaMemsetAsync(&st->blend_contribs, 0, sizeof(unsigned long long), s);
   if (curves->n_curves > 0)
-    k_curve_scene<<<(curves->n_curves + 255) / 256, 256, 0, s>>>(*curves, curve_scene);
+    NS_LAUNCH(NS_KERNEL_OTHER, k_curve_scene, (curves->n_curves + 255) / 256, 256, 0, s, *curves, curve_scene);
   BinParams bp;
   bp.k_sigma = rp->k_sigma;
   bp.inv_tile = 1.f / float(kTile);
@@ -609,11 +624,11 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
   bp.gcap = int(L.gcap);
   const int bin_blocks = int(L.bin_blocks);
   if (bin_blocks > 0) {
-    k_bin_count<<<bin_blocks, 256, 0, s>>>(rec, g->curve, g->count, bp, bsum, st);
+    NS_LAUNCH(NS_KERNEL_BIN_COUNT, k_bin_count, bin_blocks, 256, 0, s, rec, g->curve, g->count, bp, bsum, st);
   }
-  k_scan_small<<<1, 1024, 0, s>>>(bsum, g->count, int(L.gcap), kBinItems, st, cap->pairs);
+  NS_LAUNCH(NS_KERNEL_SCAN, k_scan_small, 1, 1024, 0, s, bsum, g->count, int(L.gcap), kBinItems, st, cap->pairs);
   if (bin_blocks > 0) {
-    k_bin_emit<<<bin_blocks, 256, 0, s>>>(rec, g->curve, g->count, curve_scene, bp, bsum, k0, v0, cap->pairs);
+    NS_LAUNCH(NS_KERNEL_BIN_EMIT, k_bin_emit, bin_blocks, 256, 0, s, rec, g->curve, g->count, curve_scene, bp, bsum, k0, v0, cap->pairs);
   }
   const RasterPlan rpn = radix_plan(L.n_tiles);
   const int sort_blocks = int(L.sort_blocks);
@@ -621,21 +636,21 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
   for (int pass = 0; pass < rpn.passes; ++pass) {
     const int shift = pass * rpn.bits_per_pass;
     if (sort_blocks > 0) {
-      k_radix_hist<<<sort_blocks, 256, 0, s>>>(kin, st, shift, rpn.bits_per_pass, hist);
-      k_radix_scan<<<1, 1024, 0, s>>>(hist, st, rpn.bits_per_pass);
-      k_radix_scatter<<<sort_blocks, 256, 0, s>>>(kin, vin, kout, vout, hist, st, shift, rpn.bits_per_pass);
+      NS_LAUNCH(NS_KERNEL_RADIX_HIST, k_radix_hist, sort_blocks, 256, 0, s, kin, st, shift, rpn.bits_per_pass, hist);
+      NS_LAUNCH(NS_KERNEL_SCAN, k_radix_scan, 1, 1024, 0, s, hist, st, rpn.bits_per_pass);
+      NS_LAUNCH(NS_KERNEL_RADIX_SCATTER, k_radix_scatter, sort_blocks, 256, 0, s, kin, vin, kout, vout, hist, st, shift, rpn.bits_per_pass);
     }
     std::swap(kin, kout);
     std::swap(vin, vout);
   }
   cudaMemsetAsync(ranges, 0, sizeof(int2) * (size_t)L.n_tiles, s);
-  k_ranges<<<num_sms() * 4, 256, 0, s>>>(kin, st, ranges);
+  NS_LAUNCH(NS_KERNEL_RANGES, k_ranges, num_sms() * 4, 256, 0, s, kin, st, ranges);
   const BlendParams blp = blend_params(L, rp);
   const float4* col = reinterpret_cast<const float4*>(curves->color);
   if (L.C == 3)
-    k_blend_fwd<3><<<L.n_tiles, 256, 0, s>>>(ranges, vin, rec, g->curve, col, blp, image, Tf, nl);
+    NS_LAUNCH(NS_KERNEL_BLEND_FWD, k_blend_fwd<3>, L.n_tiles, 256, 0, s, ranges, vin, rec, g->curve, col, blp, image, Tf, nl, st);
   else
-    k_blend_fwd<1><<<L.n_tiles, 256, 0, s>>>(ranges, vin, rec, g->curve, col, blp, image, Tf, nl);
+    NS_LAUNCH(NS_KERNEL_BLEND_FWD, k_blend_fwd<1>, L.n_tiles, 256, 0, s, ranges, vin, rec, g->curve, col, blp, image, Tf, nl, st);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_error(std::string("splat_forward: ") + cudaGetErrorString(e));
@@ -657,10 +672,12 @@ ns_status launch_blend_bwd(const Layout& L, const ns_curves* curves, const ns_ga
   const BlendParams blp = blend_params(L, rp);
   const float4* col = reinterpret_cast<const float4*>(curves->color);
   const float4* rec = reinterpret_cast<const float4*>(g->rec);
+  DevState* st = at<DevState>(ws, L.o_state);
+  cudaMemsetAsync(&st->blend_bwd_evals, 0, sizeof(unsigned long long), s);
   if (L.C == 3)
-    k_blend_bwd<3><<<L.n_tiles, 256, 0, s>>>(ranges, vsorted, rec, g->curve, col, blp, dimage, Tf, nl, dgauss);
+    NS_LAUNCH(NS_KERNEL_BLEND_BWD, k_blend_bwd<3>, L.n_tiles, 256, 0, s, ranges, vsorted, rec, g->curve, col, blp, dimage, Tf, nl, dgauss, st);
   else
-    k_blend_bwd<1><<<L.n_tiles, 256, 0, s>>>(ranges, vsorted, rec, g->curve, col, blp, dimage, Tf, nl, dgauss);
+    NS_LAUNCH(NS_KERNEL_BLEND_BWD, k_blend_bwd<1>, L.n_tiles, 256, 0, s, ranges, vsorted, rec, g->curve, col, blp, dimage, Tf, nl, dgauss, st);
   return NS_OK;
 }
 bool raster_params_ok(const ns_raster_params* rp) { return check_raster(rp); }

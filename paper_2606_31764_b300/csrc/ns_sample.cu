@@ -423,12 +423,12 @@ extern "C" ns_status nurbs_sample(const ns_curves* curves, const ns_sample_param
     cudaMemsetAsync(&st->g_count, 0, sizeof(int), s);
     return cudaGetLastError() == cudaSuccess ? NS_OK : NS_ERR_CUDA;
   }
-  k_plan<<<nc, kPlanThreads, 0, s>>>(*curves, *sp, plan, knots, order, st);
-  k_scan_boundary<<<1, 1024, 0, s>>>(nc, plan, st, cap->boundary);
-  k_boundary<<<nc, kPlanThreads, 0, s>>>(*curves, *sp, plan, knots, bpts, cap->boundary);
-  k_scan_gauss<<<1, 1024, 0, s>>>(nc, plan, order, st, cap->gaussians, out->count);
+  NS_LAUNCH(NS_KERNEL_PLAN, k_plan, nc, kPlanThreads, 0, s, *curves, *sp, plan, knots, order, st);
+  NS_LAUNCH(NS_KERNEL_SCAN, k_scan_boundary, 1, 1024, 0, s, nc, plan, st, cap->boundary);
+  NS_LAUNCH(NS_KERNEL_BOUNDARY, k_boundary, nc, kPlanThreads, 0, s, *curves, *sp, plan, knots, bpts, cap->boundary);
+  NS_LAUNCH(NS_KERNEL_SCAN, k_scan_gauss, 1, 1024, 0, s, nc, plan, order, st, cap->gaussians, out->count);
   const int grid = num_sms() * 8;
-  k_emit<<<grid, 256, 0, s>>>(*curves, *sp, plan, order, knots, bpts, st, reinterpret_cast<float4*>(out->rec),
+  NS_LAUNCH(NS_KERNEL_EMIT, k_emit, grid, 256, 0, s, *curves, *sp, plan, order, knots, bpts, st, reinterpret_cast<float4*>(out->rec),
                               out->curve, out->aux, cap->gaussians, cap->boundary);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {

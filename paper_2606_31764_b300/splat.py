@@ -52,6 +52,9 @@ class Report:
     pairs: int
     boundary: int
     fill_culled: int
+    blend_evals: int
+    blend_bwd_evals: int
+    blend_contribs: int
 
 
 class DeviceCurves:
@@ -135,7 +138,8 @@ class Splatter:
     def report(self) -> Report:
         r = B.NsReport()
         B.call("ns_poll_status", _ptr(self.ws), C.byref(r), _stream())
-        return Report(r.status, r.bad_curve, r.gaussians, r.pairs, r.boundary, r.fill_culled)
+        return Report(r.status, r.bad_curve, r.gaussians, r.pairs, r.boundary, r.fill_culled, r.blend_evals,
+                      r.blend_bwd_evals, r.blend_contribs)
 
     # -- stages ---------------------------------------------------------
     def sample(self, key, tau, color):
