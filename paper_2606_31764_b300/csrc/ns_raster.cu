@@ -326,11 +326,25 @@ __global__ void k_ranges(const uint32_t* __restrict__ keys, const DevState* st, 
 
 // ---------------------------------------------------------------------------
 // compositing
+//
+// Thread layout: a 16x16 tile per block of 8 warps; warp w owns the 8x4
+// sub-block at ((w & 1) * 8, (w >> 1) * 4), lane l the pixel (l & 7, l >> 3)
+// inside it.  Records are staged 256 at a time in shared memory.  Before a
+// warp evaluates a Gaussian it tests, 32 Gaussians per instruction (one per
+// lane, then a ballot), whether the Gaussian can reach alpha_min anywhere in
+// its 8x4 sub-block: alpha >= alpha_min needs
+//   d^2 <= 2 sigma^2 ln(o / alpha_min),
+// and the test uses the sub-block's nearest point with a margin of 1e-3 in
+// the logarithm, so a Gaussian it rejects would have been skipped by the
+// alpha < alpha_min rule at every pixel of the sub-block.  The result is the
+// same as evaluating every pair; only the work changes.  With alpha_min = 0
+// nothing is rejected.
 
 struct BlendParams {
   float alpha_min, alpha_max, t_min;
   float bg0, bg1, bg2;
   int W, H, tiles_x, tiles_per_scene;
+  float log_amin;   // ln(alpha_min), or -inf
 };
 
 // alpha = min(alpha_max, o exp(ncoef d^2)), ncoef = -1/(2 sigma^2) (Eq. 9).
@@ -347,10 +361,42 @@ __device__ __forceinline__ float gauss_alpha(float fx, float fy, float4 q, float
 
 __device__ __forceinline__ float ncoef(float sigma) { return __fdiv_rn(-0.5f, __fmul_rn(sigma, sigma)); }
 
+// Squared reach of a Gaussian: beyond it alpha < alpha_min for certain.
+__device__ __forceinline__ float reach2(float sigma, float o, float log_amin) {
+  if (!(log_amin > -1e30f)) return FLT_MAX;
+  return 2.f * sigma * sigma * (__logf(o) - log_amin + 1e-3f);
+}
+
+// Squared distance from (x, y) to the rectangle [x0, x1] x [y0, y1].
+__device__ __forceinline__ float rect_d2(float x, float y, float x0, float x1, float y0, float y1) {
+  const float dx = fmaxf(fmaxf(x0 - x, x - x1), 0.f);
+  const float dy = fmaxf(fmaxf(y0 - y, y - y1), 0.f);
+  return dx * dx + dy * dy;
+}
+
 // Adds a per-thread count to a device counter, one atomic per warp.
 __device__ __forceinline__ void count_evals(unsigned long long* ctr, unsigned int v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   if ((threadIdx.x & 31) == 0 && v) atomicAdd(ctr, (unsigned long long)v);
+}
+
+struct WarpRect {
+  float x0, x1, y0, y1;   // pixel-centre bounds of the warp's 8x4 sub-block
+};
+
+__device__ __forceinline__ void tile_pixel(const BlendParams& bp, int& s, int& px, int& py, WarpRect& wr) {
+  const int tile = blockIdx.x;
+  s = tile / bp.tiles_per_scene;
+  const int t = tile - s * bp.tiles_per_scene;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int bx = (t % bp.tiles_x) * kTile + (w & 1) * 8;
+  const int by = (t / bp.tiles_x) * kTile + (w >> 1) * 4;
+  px = bx + (lane & 7);
+  py = by + (lane >> 3);
+  wr.x0 = bx + 0.5f;
+  wr.x1 = bx + 7.5f;
+  wr.y0 = by + 0.5f;
+  wr.y1 = by + 3.5f;
 }
 
 template <int C>
@@ -360,14 +406,14 @@ __global__ void __launch_bounds__(256) k_blend_fwd(const int2* __restrict__ rang
                                                    float* Tfinal, int* nlast, DevState* st) {
   __shared__ float4 s_g[256];
   __shared__ float4 s_c[256];
-  const int tile = blockIdx.x;
-  const int s = tile / bp.tiles_per_scene;
-  const int t = tile - s * bp.tiles_per_scene;
-  const int px = (t % bp.tiles_x) * kTile + (threadIdx.x & 15);
-  const int py = (t / bp.tiles_x) * kTile + (threadIdx.x >> 4);
+  __shared__ float s_r[256];
+  int s, px, py;
+  WarpRect wr;
+  tile_pixel(bp, s, px, py, wr);
+  const int lane = threadIdx.x & 31;
   const bool inside = px < bp.W && py < bp.H;
   const float fx = px + 0.5f, fy = py + 0.5f;
-  const int2 rg = ranges[tile];
+  const int2 rg = ranges[blockIdx.x];
   const int n = rg.y - rg.x;
   float T = 1.f, acc[C];
 #pragma unroll
@@ -382,29 +428,46 @@ __global__ void __launch_bounds__(256) k_blend_fwd(const int2* __restrict__ rang
       const float4 r = rec[g];
       s_g[threadIdx.x] = make_float4(r.x, r.y, ncoef(r.z), r.w);
       s_c[threadIdx.x] = color[gcurve[g]];
+      s_r[threadIdx.x] = reach2(r.z, r.w, bp.log_amin);
     }
     __syncthreads();
-    if (!done) {
-      const int cnt = min(256, n - base);
-      int k = 0;
-      for (; k < cnt; ++k) {
-        float dx, dy, d2, e;
-        const float a = gauss_alpha(fx, fy, s_g[k], bp.alpha_max, dx, dy, d2, e);
-        if (a < bp.alpha_min) continue;
-        const float test = T * (1.f - a);
-        if (test < bp.t_min) { done = true; break; }
-        const float w = a * T;
-        const float4 cc = s_c[k];
-        acc[0] = fmaf(cc.x, w, acc[0]);
-        if (C == 3) {
-          acc[1] = fmaf(cc.y, w, acc[1]);
-          acc[2] = fmaf(cc.z, w, acc[2]);
+    const int cnt = min(256, n - base);
+    if (!__all_sync(0xffffffffu, done)) {
+      for (int grp = 0; grp < cnt; grp += 32) {
+        const int j = grp + lane;
+        bool hit = false;
+        if (j < cnt) {
+          const float4 q = s_g[j];
+          hit = rect_d2(q.x, q.y, wr.x0, wr.x1, wr.y0, wr.y1) <= s_r[j];
         }
-        T = test;
-        last = base + k + 1;
-        ++contribs;
+        unsigned int mask = __ballot_sync(0xffffffffu, hit);
+        while (mask) {
+          const int b = __ffs(mask) - 1;
+          mask &= mask - 1;
+          const int k = grp + b;
+          if (done) continue;
+          ++evals;
+          float dx, dy, d2, e;
+          const float a = gauss_alpha(fx, fy, s_g[k], bp.alpha_max, dx, dy, d2, e);
+          if (a < bp.alpha_min) continue;
+          const float test = T * (1.f - a);
+          if (test < bp.t_min) {
+            done = true;
+            continue;
+          }
+          const float w = a * T;
+          const float4 cc = s_c[k];
+          acc[0] = fmaf(cc.x, w, acc[0]);
+          if (C == 3) {
+            acc[1] = fmaf(cc.y, w, acc[1]);
+            acc[2] = fmaf(cc.z, w, acc[2]);
+          }
+          T = test;
+          last = base + k + 1;
+          ++contribs;
+        }
+        if (__all_sync(0xffffffffu, done)) break;
       }
-      evals += (unsigned int)min(k + 1, cnt);
     }
     if (__syncthreads_count(done) == (int)blockDim.x) break;
   }
@@ -423,6 +486,38 @@ __global__ void __launch_bounds__(256) k_blend_fwd(const int2* __restrict__ rang
   }
 }
 
+// Sum of 8 values over the 32 lanes of a warp in 9 shuffles: each exchange
+// step hands half of the remaining values to the partner lane.  On return the
+// lanes with (lane & 3) == 0 hold the totals, value (lane >> 2) in lane.
+__device__ __forceinline__ float warp_sum8(const float v[8]) {
+  const int lane = threadIdx.x & 31;
+  float b[4], c[2];
+  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float send = h16 ? v[i] : v[i + 4];
+    const float keep = h16 ? v[i + 4] : v[i];
+    b[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float send = h8 ? b[i] : b[i + 2];
+    const float keep = h8 ? b[i + 2] : b[i];
+    c[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  float d = (h4 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, h4 ? c[0] : c[1], 4);
+  d += __shfl_xor_sync(0xffffffffu, d, 2);
+  d += __shfl_xor_sync(0xffffffffu, d, 1);
+  return d;
+}
+
+__device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
+               : "memory");
+}
+
+// Per-Gaussian gradient slots accumulated in shared memory for one chunk:
+// {dmu_x, dmu_y, dsigma, do, dr, dg, db, 0}.
 template <int C>
 __global__ void __launch_bounds__(256) k_blend_bwd(const int2* __restrict__ ranges, const uint32_t* __restrict__ gid,
                                                    const float4* __restrict__ rec, const int* __restrict__ gcurve,
@@ -431,17 +526,17 @@ __global__ void __launch_bounds__(256) k_blend_bwd(const int2* __restrict__ rang
                                                    const int* __restrict__ nlast, float* dgauss, DevState* st) {
   __shared__ float4 s_g[256];
   __shared__ float4 s_c[256];
+  __shared__ float s_r[256];
   __shared__ float s_sig[256];
-  __shared__ uint32_t s_id[256];
+  __shared__ float s_acc[8][256];
   __shared__ int s_max;
-  const int tile = blockIdx.x;
-  const int s = tile / bp.tiles_per_scene;
-  const int t = tile - s * bp.tiles_per_scene;
-  const int px = (t % bp.tiles_x) * kTile + (threadIdx.x & 15);
-  const int py = (t / bp.tiles_x) * kTile + (threadIdx.x >> 4);
+  int s, px, py;
+  WarpRect wr;
+  tile_pixel(bp, s, px, py, wr);
+  const int lane = threadIdx.x & 31;
   const bool inside = px < bp.W && py < bp.H;
   const float fx = px + 0.5f, fy = py + 0.5f;
-  const int2 rg = ranges[tile];
+  const int2 rg = ranges[blockIdx.x];
   const long long pix = ((long long)s * bp.H + py) * bp.W + px;
   float T = 1.f, dI[3] = {0.f, 0.f, 0.f}, Bk[3] = {bp.bg0, bp.bg1, bp.bg2};
   int last = 0;
@@ -453,13 +548,15 @@ __global__ void __launch_bounds__(256) k_blend_bwd(const int2* __restrict__ rang
   }
   if (threadIdx.x == 0) s_max = 0;
   __syncthreads();
-  if (last) atomicMax(&s_max, last);
+  int wmax = last;
+  for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+  if (lane == 0 && wmax) atomicMax(&s_max, wmax);
   __syncthreads();
+  unsigned int evals = 0;
   const int nmax = s_max;
-  const int lane = threadIdx.x & 31;
-  count_evals(&st->blend_bwd_evals, (unsigned int)last);
   for (int end = nmax; end > 0; end -= 256) {
     const int beg = max(0, end - 256);
+    const int cnt = end - beg;
     const int idx = beg + threadIdx.x;
     __syncthreads();
     if (idx < end) {
@@ -467,72 +564,80 @@ __global__ void __launch_bounds__(256) k_blend_bwd(const int2* __restrict__ rang
       const float4 r = rec[g];
       s_g[threadIdx.x] = make_float4(r.x, r.y, ncoef(r.z), r.w);
       s_c[threadIdx.x] = color[gcurve[g]];
+      s_r[threadIdx.x] = reach2(r.z, r.w, bp.log_amin);
       s_sig[threadIdx.x] = r.z;
-      s_id[threadIdx.x] = g;
     }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s_acc[q][threadIdx.x] = 0.f;
     __syncthreads();
-    for (int k = end - 1; k >= beg; --k) {
-      const int kk = k - beg;
-      float gmx = 0.f, gmy = 0.f, gs = 0.f, go = 0.f, gc0 = 0.f, gc1 = 0.f, gc2 = 0.f;
-      bool contrib = false;
-      if (k < last) {
-        const float4 q = s_g[kk];
-        float dx, dy, d2, e;
-        const float a = gauss_alpha(fx, fy, q, bp.alpha_max, dx, dy, d2, e);
-        if (a >= bp.alpha_min) {
-          contrib = true;
-          T = T / (1.f - a);
-          const float w = a * T;
-          const float4 cc = s_c[kk];
-          float da = (cc.x - Bk[0]) * dI[0];
-          gc0 = w * dI[0];
-          Bk[0] = a * cc.x + (1.f - a) * Bk[0];
-          if (C == 3) {
-            da += (cc.y - Bk[1]) * dI[1] + (cc.z - Bk[2]) * dI[2];
-            gc1 = w * dI[1];
-            gc2 = w * dI[2];
-            Bk[1] = a * cc.y + (1.f - a) * Bk[1];
-            Bk[2] = a * cc.z + (1.f - a) * Bk[2];
+    if (wmax > beg) {
+      // groups of 32 from the back; bits from high to low
+      for (int grp = ((cnt - 1) >> 5) << 5; grp >= 0; grp -= 32) {
+        const int j = grp + lane;
+        bool hit = false;
+        if (j < cnt && beg + j < wmax) {
+          const float4 q = s_g[j];
+          hit = rect_d2(q.x, q.y, wr.x0, wr.x1, wr.y0, wr.y1) <= s_r[j];
+        }
+        unsigned int mask = __ballot_sync(0xffffffffu, hit);
+        while (mask) {
+          const int b = 31 - __clz(mask);
+          mask &= ~(1u << b);
+          const int kk = grp + b;
+          float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+          bool contrib = false;
+          if (beg + kk < last) {
+            ++evals;
+            const float4 q = s_g[kk];
+            float dx, dy, d2, e;
+            const float a = gauss_alpha(fx, fy, q, bp.alpha_max, dx, dy, d2, e);
+            if (a >= bp.alpha_min) {
+              contrib = true;
+              T = T / (1.f - a);
+              const float w = a * T;
+              const float4 cc = s_c[kk];
+              float da = (cc.x - Bk[0]) * dI[0];
+              v[4] = w * dI[0];
+              Bk[0] = a * cc.x + (1.f - a) * Bk[0];
+              if (C == 3) {
+                da += (cc.y - Bk[1]) * dI[1] + (cc.z - Bk[2]) * dI[2];
+                v[5] = w * dI[1];
+                v[6] = w * dI[2];
+                Bk[1] = a * cc.y + (1.f - a) * Bk[1];
+                Bk[2] = a * cc.z + (1.f - a) * Bk[2];
+              }
+              da *= T;
+              if (__fmul_rn(q.w, e) < bp.alpha_max) {
+                const float sg = s_sig[kk];
+                const float is2 = 1.f / (sg * sg);
+                v[3] = e * da;
+                const float aa = da * a * is2;
+                v[0] = aa * dx;
+                v[1] = aa * dy;
+                v[2] = aa * d2 / sg;
+              }
+            }
           }
-          da *= T;
-          if (__fmul_rn(q.w, e) < bp.alpha_max) {
-            const float sg = s_sig[kk];
-            const float is2 = 1.f / (sg * sg);
-            go = e * da;
-            const float aa = da * a * is2;
-            gmx = aa * dx;
-            gmy = aa * dy;
-            gs = aa * d2 / sg;
+          if (__any_sync(0xffffffffu, contrib)) {
+            const float tot = warp_sum8(v);
+            if ((lane & 3) == 0 && (lane >> 2) < 7) atomicAdd(&s_acc[lane >> 2][kk], tot);
           }
         }
       }
-      if (__any_sync(0xffffffffu, contrib)) {
-        for (int o = 16; o > 0; o >>= 1) {
-          gmx += __shfl_xor_sync(0xffffffffu, gmx, o);
-          gmy += __shfl_xor_sync(0xffffffffu, gmy, o);
-          gs += __shfl_xor_sync(0xffffffffu, gs, o);
-          go += __shfl_xor_sync(0xffffffffu, go, o);
-          gc0 += __shfl_xor_sync(0xffffffffu, gc0, o);
-          if (C == 3) {
-            gc1 += __shfl_xor_sync(0xffffffffu, gc1, o);
-            gc2 += __shfl_xor_sync(0xffffffffu, gc2, o);
-          }
-        }
-        if (lane == 0) {
-          float* d = dgauss + (long long)s_id[kk] * 8;
-          atomicAdd(d + 0, gmx);
-          atomicAdd(d + 1, gmy);
-          atomicAdd(d + 2, gs);
-          atomicAdd(d + 3, go);
-          atomicAdd(d + 4, gc0);
-          if (C == 3) {
-            atomicAdd(d + 5, gc1);
-            atomicAdd(d + 6, gc2);
-          }
-        }
+    }
+    __syncthreads();
+    if (threadIdx.x < cnt) {
+      const float a0 = s_acc[0][threadIdx.x], a1 = s_acc[1][threadIdx.x], a2 = s_acc[2][threadIdx.x],
+                  a3 = s_acc[3][threadIdx.x], a4 = s_acc[4][threadIdx.x], a5 = s_acc[5][threadIdx.x],
+                  a6 = s_acc[6][threadIdx.x];
+      if (a0 != 0.f || a1 != 0.f || a2 != 0.f || a3 != 0.f || a4 != 0.f || a5 != 0.f || a6 != 0.f) {
+        float* d = dgauss + (long long)gid[rg.x + beg + threadIdx.x] * 8;
+        red_add_v4(d, a0, a1, a2, a3);
+        red_add_v4(d + 4, a4, a5, a6, 0.f);
       }
     }
   }
+  count_evals(&st->blend_bwd_evals, evals);
 }
 
 // ---------------------------------------------------------------------------
@@ -562,6 +667,7 @@ static BlendParams blend_params(const Layout& L, const ns_raster_params* rp) {
   bp.H = L.H;
   bp.tiles_x = L.tiles_x;
   bp.tiles_per_scene = L.tiles_x * L.tiles_y;
+  bp.log_amin = rp->alpha_min > 0.f ? logf(rp->alpha_min) : -INFINITY;
   return bp;
 }
 
