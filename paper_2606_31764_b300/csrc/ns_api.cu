@@ -137,6 +137,8 @@ bool make_layout(const ns_curves* c, const ns_capacity* cap, const ns_raster_par
   L->o_T = take(sizeof(float) * (size_t)L->n_pix);
   L->o_nlast = take(sizeof(int) * (size_t)L->n_pix);
   L->o_dgauss = take(sizeof(float) * 8 * (size_t)L->gcap);
+  L->o_prep = take(sizeof(float4) * (size_t)L->gcap);
+  L->o_reach = take(sizeof(float2) * (size_t)L->gcap);
   L->total = o;
   return true;
 }

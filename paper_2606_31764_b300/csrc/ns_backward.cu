@@ -32,17 +32,6 @@ bool raster_params_ok(const ns_raster_params* rp);
 constexpr int kWin = 1024;   // control points (and knots) per task window in shared memory
 constexpr int kWinB = 2 * kWin;  // boundary points per fill task window (float2, aliases s_cp)
 
-__device__ __forceinline__ float warp_sum(float v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Sums v over the block into red[slot] (red must hold 8 warps x nslots).
-__device__ __forceinline__ void block_add(float v, float* red, int slot) {
-  v = warp_sum(v);
-  if ((threadIdx.x & 31) == 0) atomicAdd(&red[slot], v);
-}
-
 // Reverse of one curve point: gC = dL/dC (x, y, s) at parameter u (span i,
 // domain fraction t).  Adds to the control-point and knot accumulators.
 template <int P, class AddCP, class AddKnot>
@@ -168,12 +157,12 @@ __global__ void __launch_bounds__(256) k_chain(ns_curves cv, ChainParams cp, con
         NS_DISPATCH_P(cr.p, chain_contour_sample<P>(cv, cr, U, pl, l, cp, g0, s_cp, s_kn, cp_lo, kn_lo, use_smem,
                                                      dkey, dknots, dA, dB));
       }
-      block_add(dA, s_red, 0);
-      block_add(dB, s_red, 1);
-      block_add(g1.x, s_red, 2);
-      block_add(g1.y, s_red, 3);
-      block_add(g1.z, s_red, 4);
-      block_add(g0.w, s_red, 5);
+      {
+        const float v[8] = {dA, dB, g1.x, g1.y, g1.z, g0.w, 0.f, 0.f};
+        const float tot = warp_sum8(v);
+        const int lane = threadIdx.x & 31;
+        if ((lane & 3) == 0 && (lane >> 2) < 6 && tot != 0.f) atomicAdd(&s_red[lane >> 2], tot);
+      }
       __syncthreads();
       if (use_smem) {
         for (int k = threadIdx.x; k < ncp; k += blockDim.x) {
@@ -206,7 +195,7 @@ __global__ void __launch_bounds__(256) k_chain(ns_curves cv, ChainParams cp, con
       for (int k = threadIdx.x; k < B; k += blockDim.x) s_db[k] = make_float2(0.f, 0.f);
     __syncthreads();
     float dO = 0.f;
-    if (valid) {
+    if (valid && g0.w != 0.f) {   // no opacity gradient: nothing reaches the curve but its colour
       const float o = cv.color[4 * c + 3];
       const int aux = gaux[g];
       const bool inside = aux >= 0;
@@ -242,10 +231,12 @@ __global__ void __launch_bounds__(256) k_chain(ns_curves cv, ChainParams cp, con
         }
       }
     }
-    block_add(dO, s_red, 5);
-    block_add(g1.x, s_red, 2);
-    block_add(g1.y, s_red, 3);
-    block_add(g1.z, s_red, 4);
+    {
+      const float v[8] = {0.f, 0.f, g1.x, g1.y, g1.z, dO, 0.f, 0.f};
+      const float tot = warp_sum8(v);
+      const int lane = threadIdx.x & 31;
+      if ((lane & 3) == 0 && (lane >> 2) >= 2 && (lane >> 2) < 6 && tot != 0.f) atomicAdd(&s_red[lane >> 2], tot);
+    }
     __syncthreads();
     if (use_smem) {
       for (int k = threadIdx.x; k < B; k += blockDim.x) {

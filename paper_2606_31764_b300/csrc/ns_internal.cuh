@@ -62,7 +62,7 @@ struct Layout {
   int64_t bin_blocks = 0, sort_blocks = 0;
   size_t o_state = 0, o_plan = 0, o_knots = 0, o_dknots = 0, o_bpts = 0, o_dbpts = 0, o_bsum = 0,
          o_k0 = 0, o_v0 = 0, o_k1 = 0, o_v1 = 0, o_hist = 0, o_ranges = 0, o_T = 0, o_nlast = 0,
-         o_dgauss = 0, o_curve_scene = 0, o_order = 0, total = 0;
+         o_dgauss = 0, o_curve_scene = 0, o_order = 0, o_prep = 0, o_reach = 0, total = 0;
 };
 
 // Host helpers (ns_api.cu).
@@ -259,6 +259,31 @@ __device__ __forceinline__ float speed_xy(const Eval<P>& e) {
   const float dx = (dS0 - e.C[0] * dW) * iw;   // (W S' - S W')/W^2 = (S' - C W')/W
   const float dy = (dS1 - e.C[1] * dW) * iw;
   return sqrtf(dx * dx + dy * dy);
+}
+
+// Sum of 8 values over the 32 lanes of a warp in 9 shuffles: each exchange
+// step hands half of the remaining values to the partner lane.  On return the
+// lanes with (lane & 3) == 0 hold the totals, value (lane >> 2) in lane.
+__device__ __forceinline__ float warp_sum8(const float v[8]) {
+  const int lane = threadIdx.x & 31;
+  float b[4], c[2];
+  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float send = h16 ? v[i] : v[i + 4];
+    const float keep = h16 ? v[i + 4] : v[i];
+    b[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float send = h8 ? b[i] : b[i + 2];
+    const float keep = h8 ? b[i + 2] : b[i];
+    c[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  float d = (h4 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, h4 ? c[0] : c[1], 4);
+  d += __shfl_xor_sync(0xffffffffu, d, 2);
+  d += __shfl_xor_sync(0xffffffffu, d, 1);
+  return d;
 }
 
 // Runtime degree -> template dispatch.

@@ -43,7 +43,7 @@ __global__ void k_curve_scene(ns_curves cv, int* curve_scene) {
 }
 
 struct BinParams {
-  float k_sigma, inv_tile, alpha_min;
+  float k_sigma, inv_tile, alpha_min, log_amin;   // log_amin = ln(alpha_min), or -inf
   int tiles_x, tiles_y, tiles_per_scene;
   int n_curves, gcap;   // Gaussians naming a curve outside [0, n_curves) cover no tile
 };
@@ -92,9 +92,19 @@ __device__ __forceinline__ int block_excl_scan_int(int v, int* s_warp, int& tota
 }
 
 // 256 threads x 8 consecutive Gaussians.
+__device__ __forceinline__ float ncoef(float sigma) { return __fdiv_rn(-0.5f, __fmul_rn(sigma, sigma)); }
+
+// Squared reach of a Gaussian: beyond it alpha < alpha_min for certain
+// (a margin of 1e-3 in the logarithm covers the rounding of exp and of d^2).
+__device__ __forceinline__ float reach2(float sigma, float o, float log_amin) {
+  if (!(log_amin > -1e30f)) return FLT_MAX;
+  return 2.f * sigma * sigma * (__logf(o) - log_amin + 1e-3f);
+}
+
+// Counts tiles per Gaussian and prepares the per-Gaussian blend constants.
 __global__ void __launch_bounds__(256) k_bin_count(const float4* __restrict__ rec, const int* __restrict__ gcurve,
                                                    const int* __restrict__ gcount, BinParams bp, int* bsum,
-                                                   DevState* st) {
+                                                   DevState* st, float4* prep, float2* reach) {
   __shared__ int s_warp[32];
   const int G = min(*gcount, bp.gcap);
   const long long base = (long long)blockIdx.x * kBinItems;
@@ -108,6 +118,8 @@ __global__ void __launch_bounds__(256) k_bin_count(const float4* __restrict__ re
       int x0, y0, nx;
       const int cv = gcurve[g];
       if (cv >= 0 && cv < bp.n_curves) cnt += tile_rect(r, bp, x0, y0, nx);
+      prep[g] = make_float4(r.x, r.y, ncoef(r.z), r.w);
+      reach[g] = make_float2(r.z > 0.f && r.w > 0.f ? reach2(r.z, r.w, bp.log_amin) : -1.f, r.z);
       culled += (r.z > 0.f && r.w < bp.alpha_min) ? 1 : 0;
     }
   }
@@ -329,27 +341,29 @@ __global__ void k_ranges(const uint32_t* __restrict__ keys, const DevState* st, 
 //
 // Thread layout: a 16x16 tile per block of 8 warps; warp w owns the 8x4
 // sub-block at ((w & 1) * 8, (w >> 1) * 4), lane l the pixel (l & 7, l >> 3)
-// inside it.  Records are staged 256 at a time in shared memory.  Before a
-// warp evaluates a Gaussian it tests, 32 Gaussians per instruction (one per
-// lane, then a ballot), whether the Gaussian can reach alpha_min anywhere in
-// its 8x4 sub-block: alpha >= alpha_min needs
-//   d^2 <= 2 sigma^2 ln(o / alpha_min),
-// and the test uses the sub-block's nearest point with a margin of 1e-3 in
-// the logarithm, so a Gaussian it rejects would have been skipped by the
-// alpha < alpha_min rule at every pixel of the sub-block.  The result is the
-// same as evaluating every pair; only the work changes.  With alpha_min = 0
-// nothing is rejected.
+// inside it.  Each warp streams its tile's list on its own, 32 entries at a
+// time, staged in the warp's slice of shared memory (no block barriers, so a
+// warp whose pixels are all done leaves at once).  Before the warp evaluates
+// a Gaussian it tests, one Gaussian per lane and a ballot, whether the
+// Gaussian can reach alpha_min anywhere in its 8x4 sub-block: alpha >=
+// alpha_min needs d^2 <= 2 sigma^2 ln(o / alpha_min); the test uses the
+// sub-block's nearest point with a margin of 1e-3 in the logarithm, so a
+// Gaussian it rejects would have been skipped by the alpha < alpha_min rule
+// at every pixel of the sub-block.  The result is the same as evaluating every
+// pair; only the work changes.  With alpha_min = 0 nothing is rejected.
+//
+// Per-Gaussian constants are prepared once by k_bin_count:
+//   prep  = {mu_x, mu_y, ncoef = -1/(2 sigma^2), o}
+//   reach = {squared reach, sigma}
 
 struct BlendParams {
   float alpha_min, alpha_max, t_min;
   float bg0, bg1, bg2;
   int W, H, tiles_x, tiles_per_scene;
-  float log_amin;   // ln(alpha_min), or -inf
 };
 
-// alpha = min(alpha_max, o exp(ncoef d^2)), ncoef = -1/(2 sigma^2) (Eq. 9).
-// Written with explicit roundings so that the forward and the backward kernels
-// compute the same bits.
+// alpha = min(alpha_max, o exp(ncoef d^2)) (Eq. 9), written with explicit
+// roundings so that the forward and the backward kernels compute the same bits.
 __device__ __forceinline__ float gauss_alpha(float fx, float fy, float4 q, float amax, float& dx, float& dy,
                                              float& d2, float& e) {
   dx = __fsub_rn(fx, q.x);
@@ -357,14 +371,6 @@ __device__ __forceinline__ float gauss_alpha(float fx, float fy, float4 q, float
   d2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
   e = __expf(__fmul_rn(q.z, d2));
   return fminf(__fmul_rn(q.w, e), amax);
-}
-
-__device__ __forceinline__ float ncoef(float sigma) { return __fdiv_rn(-0.5f, __fmul_rn(sigma, sigma)); }
-
-// Squared reach of a Gaussian: beyond it alpha < alpha_min for certain.
-__device__ __forceinline__ float reach2(float sigma, float o, float log_amin) {
-  if (!(log_amin > -1e30f)) return FLT_MAX;
-  return 2.f * sigma * sigma * (__logf(o) - log_amin + 1e-3f);
 }
 
 // Squared distance from (x, y) to the rectangle [x0, x1] x [y0, y1].
@@ -400,17 +406,17 @@ __device__ __forceinline__ void tile_pixel(const BlendParams& bp, int& s, int& p
 }
 
 template <int C>
-__global__ void __launch_bounds__(256) k_blend_fwd(const int2* __restrict__ ranges, const uint32_t* __restrict__ gid,
-                                                   const float4* __restrict__ rec, const int* __restrict__ gcurve,
-                                                   const float4* __restrict__ color, BlendParams bp, float* image,
-                                                   float* Tfinal, int* nlast, DevState* st) {
-  __shared__ float4 s_g[256];
-  __shared__ float4 s_c[256];
-  __shared__ float s_r[256];
+__global__ void __launch_bounds__(256, 4) k_blend_fwd(const int2* __restrict__ ranges, const uint32_t* __restrict__ gid,
+                                                   const float4* __restrict__ prep, const float2* __restrict__ reach,
+                                                   const int* __restrict__ gcurve, const float4* __restrict__ color,
+                                                   BlendParams bp, float* image, float* Tfinal, int* nlast,
+                                                   DevState* st) {
+  __shared__ float4 s_q[8][32];
+  __shared__ float4 s_c[8][32];
   int s, px, py;
   WarpRect wr;
   tile_pixel(bp, s, px, py, wr);
-  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool inside = px < bp.W && py < bp.H;
   const float fx = px + 0.5f, fy = py + 0.5f;
   const int2 rg = ranges[blockIdx.x];
@@ -421,55 +427,45 @@ __global__ void __launch_bounds__(256) k_blend_fwd(const int2* __restrict__ rang
   bool done = !inside;
   int last = 0;
   unsigned int evals = 0, contribs = 0;
-  for (int base = 0; base < n; base += 256) {
-    const int idx = base + threadIdx.x;
-    if (idx < n) {
-      const uint32_t g = gid[rg.x + idx];
-      const float4 r = rec[g];
-      s_g[threadIdx.x] = make_float4(r.x, r.y, ncoef(r.z), r.w);
-      s_c[threadIdx.x] = color[gcurve[g]];
-      s_r[threadIdx.x] = reach2(r.z, r.w, bp.log_amin);
-    }
-    __syncthreads();
-    const int cnt = min(256, n - base);
-    if (!__all_sync(0xffffffffu, done)) {
-      for (int grp = 0; grp < cnt; grp += 32) {
-        const int j = grp + lane;
-        bool hit = false;
-        if (j < cnt) {
-          const float4 q = s_g[j];
-          hit = rect_d2(q.x, q.y, wr.x0, wr.x1, wr.y0, wr.y1) <= s_r[j];
-        }
-        unsigned int mask = __ballot_sync(0xffffffffu, hit);
-        while (mask) {
-          const int b = __ffs(mask) - 1;
-          mask &= mask - 1;
-          const int k = grp + b;
-          if (done) continue;
-          ++evals;
-          float dx, dy, d2, e;
-          const float a = gauss_alpha(fx, fy, s_g[k], bp.alpha_max, dx, dy, d2, e);
-          if (a < bp.alpha_min) continue;
-          const float test = T * (1.f - a);
-          if (test < bp.t_min) {
-            done = true;
-            continue;
-          }
-          const float w = a * T;
-          const float4 cc = s_c[k];
-          acc[0] = fmaf(cc.x, w, acc[0]);
-          if (C == 3) {
-            acc[1] = fmaf(cc.y, w, acc[1]);
-            acc[2] = fmaf(cc.z, w, acc[2]);
-          }
-          T = test;
-          last = base + k + 1;
-          ++contribs;
-        }
-        if (__all_sync(0xffffffffu, done)) break;
+  for (int base = 0; base < n && !__all_sync(0xffffffffu, done); base += 32) {
+    const int j = base + lane;
+    bool hit = false;
+    if (j < n) {
+      const uint32_t g = gid[rg.x + j];
+      const float4 q = prep[g];
+      hit = rect_d2(q.x, q.y, wr.x0, wr.x1, wr.y0, wr.y1) <= reach[g].x;
+      if (hit) {
+        s_q[w][lane] = q;
+        s_c[w][lane] = color[gcurve[g]];
       }
     }
-    if (__syncthreads_count(done) == (int)blockDim.x) break;
+    unsigned int mask = __ballot_sync(0xffffffffu, hit);
+    __syncwarp();
+    while (mask) {
+      const int b = __ffs(mask) - 1;
+      mask &= mask - 1;
+      if (done) continue;
+      ++evals;
+      float dx, dy, d2, e;
+      const float a = gauss_alpha(fx, fy, s_q[w][b], bp.alpha_max, dx, dy, d2, e);
+      if (a < bp.alpha_min) continue;
+      const float test = T * (1.f - a);
+      if (test < bp.t_min) {
+        done = true;
+        continue;
+      }
+      const float wgt = a * T;
+      const float4 cc = s_c[w][b];
+      acc[0] = fmaf(cc.x, wgt, acc[0]);
+      if (C == 3) {
+        acc[1] = fmaf(cc.y, wgt, acc[1]);
+        acc[2] = fmaf(cc.z, wgt, acc[2]);
+      }
+      T = test;
+      last = base + b + 1;
+      ++contribs;
+    }
+    __syncwarp();
   }
   count_evals(&st->blend_evals, evals);
   count_evals(&st->blend_contribs, contribs);
@@ -486,54 +482,26 @@ __global__ void __launch_bounds__(256) k_blend_fwd(const int2* __restrict__ rang
   }
 }
 
-// Sum of 8 values over the 32 lanes of a warp in 9 shuffles: each exchange
-// step hands half of the remaining values to the partner lane.  On return the
-// lanes with (lane & 3) == 0 hold the totals, value (lane >> 2) in lane.
-__device__ __forceinline__ float warp_sum8(const float v[8]) {
-  const int lane = threadIdx.x & 31;
-  float b[4], c[2];
-  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const float send = h16 ? v[i] : v[i + 4];
-    const float keep = h16 ? v[i + 4] : v[i];
-    b[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-  }
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const float send = h8 ? b[i] : b[i + 2];
-    const float keep = h8 ? b[i + 2] : b[i];
-    c[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-  }
-  float d = (h4 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, h4 ? c[0] : c[1], 4);
-  d += __shfl_xor_sync(0xffffffffu, d, 2);
-  d += __shfl_xor_sync(0xffffffffu, d, 1);
-  return d;
-}
-
 __device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
                : "memory");
 }
 
-// Per-Gaussian gradient slots accumulated in shared memory for one chunk:
-// {dmu_x, dmu_y, dsigma, do, dr, dg, db, 0}.
 template <int C>
-__global__ void __launch_bounds__(256) k_blend_bwd(const int2* __restrict__ ranges, const uint32_t* __restrict__ gid,
-                                                   const float4* __restrict__ rec, const int* __restrict__ gcurve,
-                                                   const float4* __restrict__ color, BlendParams bp,
-                                                   const float* __restrict__ dimage, const float* __restrict__ Tfinal,
-                                                   const int* __restrict__ nlast, float* dgauss, DevState* st) {
-  __shared__ float4 s_g[256];
-  __shared__ float4 s_c[256];
-  __shared__ float s_r[256];
-  __shared__ float s_sig[256];
-  __shared__ float s_acc[8][256];
-  __shared__ int s_max;
+__global__ void __launch_bounds__(256, 4) k_blend_bwd(const int2* __restrict__ ranges, const uint32_t* __restrict__ gid,
+                                                   const float4* __restrict__ prep, const float2* __restrict__ reach,
+                                                   const int* __restrict__ gcurve, const float4* __restrict__ color,
+                                                   BlendParams bp, const float* __restrict__ dimage,
+                                                   const float* __restrict__ Tfinal, const int* __restrict__ nlast,
+                                                   float* dgauss, DevState* st) {
+  __shared__ float4 s_q[8][32];
+  __shared__ float4 s_c[8][32];
+  __shared__ float s_sig[8][32];
+  __shared__ uint32_t s_id[8][32];
   int s, px, py;
   WarpRect wr;
   tile_pixel(bp, s, px, py, wr);
-  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool inside = px < bp.W && py < bp.H;
   const float fx = px + 0.5f, fy = py + 0.5f;
   const int2 rg = ranges[blockIdx.x];
@@ -546,96 +514,77 @@ __global__ void __launch_bounds__(256) k_blend_bwd(const int2* __restrict__ rang
 #pragma unroll
     for (int ch = 0; ch < C; ++ch) dI[ch] = dimage[pix * C + ch];
   }
-  if (threadIdx.x == 0) s_max = 0;
-  __syncthreads();
   int wmax = last;
   for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
-  if (lane == 0 && wmax) atomicMax(&s_max, wmax);
-  __syncthreads();
   unsigned int evals = 0;
-  const int nmax = s_max;
-  for (int end = nmax; end > 0; end -= 256) {
-    const int beg = max(0, end - 256);
-    const int cnt = end - beg;
-    const int idx = beg + threadIdx.x;
-    __syncthreads();
-    if (idx < end) {
-      const uint32_t g = gid[rg.x + idx];
-      const float4 r = rec[g];
-      s_g[threadIdx.x] = make_float4(r.x, r.y, ncoef(r.z), r.w);
-      s_c[threadIdx.x] = color[gcurve[g]];
-      s_r[threadIdx.x] = reach2(r.z, r.w, bp.log_amin);
-      s_sig[threadIdx.x] = r.z;
+  for (int base = ((wmax - 1) >> 5) << 5; base >= 0 && wmax > 0; base -= 32) {
+    const int j = base + lane;
+    bool hit = false;
+    if (j < wmax) {
+      const uint32_t g = gid[rg.x + j];
+      const float4 q = prep[g];
+      const float2 rs = reach[g];
+      hit = rect_d2(q.x, q.y, wr.x0, wr.x1, wr.y0, wr.y1) <= rs.x;
+      if (hit) {
+        s_q[w][lane] = q;
+        s_c[w][lane] = color[gcurve[g]];
+        s_sig[w][lane] = rs.y;
+        s_id[w][lane] = g;
+      }
     }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) s_acc[q][threadIdx.x] = 0.f;
-    __syncthreads();
-    if (wmax > beg) {
-      // groups of 32 from the back; bits from high to low
-      for (int grp = ((cnt - 1) >> 5) << 5; grp >= 0; grp -= 32) {
-        const int j = grp + lane;
-        bool hit = false;
-        if (j < cnt && beg + j < wmax) {
-          const float4 q = s_g[j];
-          hit = rect_d2(q.x, q.y, wr.x0, wr.x1, wr.y0, wr.y1) <= s_r[j];
-        }
-        unsigned int mask = __ballot_sync(0xffffffffu, hit);
-        while (mask) {
-          const int b = 31 - __clz(mask);
-          mask &= ~(1u << b);
-          const int kk = grp + b;
-          float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-          bool contrib = false;
-          if (beg + kk < last) {
-            ++evals;
-            const float4 q = s_g[kk];
-            float dx, dy, d2, e;
-            const float a = gauss_alpha(fx, fy, q, bp.alpha_max, dx, dy, d2, e);
-            if (a >= bp.alpha_min) {
-              contrib = true;
-              T = T / (1.f - a);
-              const float w = a * T;
-              const float4 cc = s_c[kk];
-              float da = (cc.x - Bk[0]) * dI[0];
-              v[4] = w * dI[0];
-              Bk[0] = a * cc.x + (1.f - a) * Bk[0];
-              if (C == 3) {
-                da += (cc.y - Bk[1]) * dI[1] + (cc.z - Bk[2]) * dI[2];
-                v[5] = w * dI[1];
-                v[6] = w * dI[2];
-                Bk[1] = a * cc.y + (1.f - a) * Bk[1];
-                Bk[2] = a * cc.z + (1.f - a) * Bk[2];
-              }
-              da *= T;
-              if (__fmul_rn(q.w, e) < bp.alpha_max) {
-                const float sg = s_sig[kk];
-                const float is2 = 1.f / (sg * sg);
-                v[3] = e * da;
-                const float aa = da * a * is2;
-                v[0] = aa * dx;
-                v[1] = aa * dy;
-                v[2] = aa * d2 / sg;
-              }
-            }
+    unsigned int mask = __ballot_sync(0xffffffffu, hit);
+    __syncwarp();
+    while (mask) {
+      const int b = 31 - __clz(mask);
+      mask &= ~(1u << b);
+      float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      bool contrib = false;
+      if (base + b < last) {
+        ++evals;
+        const float4 q = s_q[w][b];
+        float dx, dy, d2, e;
+        const float a = gauss_alpha(fx, fy, q, bp.alpha_max, dx, dy, d2, e);
+        if (a >= bp.alpha_min) {
+          contrib = true;
+          T = T / (1.f - a);
+          const float wgt = a * T;
+          const float4 cc = s_c[w][b];
+          float da = (cc.x - Bk[0]) * dI[0];
+          v[4] = wgt * dI[0];
+          Bk[0] = a * cc.x + (1.f - a) * Bk[0];
+          if (C == 3) {
+            da += (cc.y - Bk[1]) * dI[1] + (cc.z - Bk[2]) * dI[2];
+            v[5] = wgt * dI[1];
+            v[6] = wgt * dI[2];
+            Bk[1] = a * cc.y + (1.f - a) * Bk[1];
+            Bk[2] = a * cc.z + (1.f - a) * Bk[2];
           }
-          if (__any_sync(0xffffffffu, contrib)) {
-            const float tot = warp_sum8(v);
-            if ((lane & 3) == 0 && (lane >> 2) < 7) atomicAdd(&s_acc[lane >> 2][kk], tot);
+          da *= T;
+          if (__fmul_rn(q.w, e) < bp.alpha_max) {
+            const float sg = s_sig[w][b];
+            const float is2 = 1.f / (sg * sg);
+            v[3] = e * da;
+            const float aa = da * a * is2;
+            v[0] = aa * dx;
+            v[1] = aa * dy;
+            v[2] = aa * d2 / sg;
           }
         }
       }
-    }
-    __syncthreads();
-    if (threadIdx.x < cnt) {
-      const float a0 = s_acc[0][threadIdx.x], a1 = s_acc[1][threadIdx.x], a2 = s_acc[2][threadIdx.x],
-                  a3 = s_acc[3][threadIdx.x], a4 = s_acc[4][threadIdx.x], a5 = s_acc[5][threadIdx.x],
-                  a6 = s_acc[6][threadIdx.x];
-      if (a0 != 0.f || a1 != 0.f || a2 != 0.f || a3 != 0.f || a4 != 0.f || a5 != 0.f || a6 != 0.f) {
-        float* d = dgauss + (long long)gid[rg.x + beg + threadIdx.x] * 8;
-        red_add_v4(d, a0, a1, a2, a3);
-        red_add_v4(d + 4, a4, a5, a6, 0.f);
+      if (__any_sync(0xffffffffu, contrib)) {
+        // value k of the warp total sits in lane 4k; gather 0..3 into lane 0
+        // and 4..7 into lane 16, one 16-byte vector reduction each
+        const float t = warp_sum8(v);
+        const float t1 = __shfl_down_sync(0xffffffffu, t, 4);
+        const float t2 = __shfl_down_sync(0xffffffffu, t, 8);
+        const float t3 = __shfl_down_sync(0xffffffffu, t, 12);
+        if ((lane & 15) == 0) {
+          float* d = dgauss + (long long)s_id[w][b] * 8 + (lane >> 2);
+          red_add_v4(d, t, t1, t2, t3);
+        }
       }
     }
+    __syncwarp();
   }
   count_evals(&st->blend_bwd_evals, evals);
 }
@@ -667,7 +616,6 @@ static BlendParams blend_params(const Layout& L, const ns_raster_params* rp) {
   bp.H = L.H;
   bp.tiles_x = L.tiles_x;
   bp.tiles_per_scene = L.tiles_x * L.tiles_y;
-  bp.log_amin = rp->alpha_min > 0.f ? logf(rp->alpha_min) : -INFINITY;
   return bp;
 }
 
@@ -723,6 +671,7 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
   bp.k_sigma = rp->k_sigma;
   bp.inv_tile = 1.f / float(kTile);
   bp.alpha_min = rp->alpha_min;
+  bp.log_amin = rp->alpha_min > 0.f ? logf(rp->alpha_min) : -INFINITY;
   bp.tiles_x = L.tiles_x;
   bp.tiles_y = L.tiles_y;
   bp.tiles_per_scene = L.tiles_x * L.tiles_y;
@@ -730,7 +679,8 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
   bp.gcap = int(L.gcap);
   const int bin_blocks = int(L.bin_blocks);
   if (bin_blocks > 0) {
-    NS_LAUNCH(NS_KERNEL_BIN_COUNT, k_bin_count, bin_blocks, 256, 0, s, rec, g->curve, g->count, bp, bsum, st);
+    NS_LAUNCH(NS_KERNEL_BIN_COUNT, k_bin_count, bin_blocks, 256, 0, s, rec, g->curve, g->count, bp, bsum, st,
+              at<float4>(ws, L.o_prep), at<float2>(ws, L.o_reach));
   }
   NS_LAUNCH(NS_KERNEL_SCAN, k_scan_small, 1, 1024, 0, s, bsum, g->count, int(L.gcap), kBinItems, st, cap->pairs);
   if (bin_blocks > 0) {
@@ -754,9 +704,11 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
   const BlendParams blp = blend_params(L, rp);
   const float4* col = reinterpret_cast<const float4*>(curves->color);
   if (L.C == 3)
-    NS_LAUNCH(NS_KERNEL_BLEND_FWD, k_blend_fwd<3>, L.n_tiles, 256, 0, s, ranges, vin, rec, g->curve, col, blp, image, Tf, nl, st);
+    NS_LAUNCH(NS_KERNEL_BLEND_FWD, k_blend_fwd<3>, L.n_tiles, 256, 0, s, ranges, vin, at<float4>(ws, L.o_prep),
+              at<float2>(ws, L.o_reach), g->curve, col, blp, image, Tf, nl, st);
   else
-    NS_LAUNCH(NS_KERNEL_BLEND_FWD, k_blend_fwd<1>, L.n_tiles, 256, 0, s, ranges, vin, rec, g->curve, col, blp, image, Tf, nl, st);
+    NS_LAUNCH(NS_KERNEL_BLEND_FWD, k_blend_fwd<1>, L.n_tiles, 256, 0, s, ranges, vin, at<float4>(ws, L.o_prep),
+              at<float2>(ws, L.o_reach), g->curve, col, blp, image, Tf, nl, st);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_error(std::string("splat_forward: ") + cudaGetErrorString(e));
@@ -777,13 +729,15 @@ ns_status launch_blend_bwd(const Layout& L, const ns_curves* curves, const ns_ga
   const int* nl = at<int>(ws, L.o_nlast);
   const BlendParams blp = blend_params(L, rp);
   const float4* col = reinterpret_cast<const float4*>(curves->color);
-  const float4* rec = reinterpret_cast<const float4*>(g->rec);
+  
   DevState* st = at<DevState>(ws, L.o_state);
   cudaMemsetAsync(&st->blend_bwd_evals, 0, sizeof(unsigned long long), s);
   if (L.C == 3)
-    NS_LAUNCH(NS_KERNEL_BLEND_BWD, k_blend_bwd<3>, L.n_tiles, 256, 0, s, ranges, vsorted, rec, g->curve, col, blp, dimage, Tf, nl, dgauss, st);
+    NS_LAUNCH(NS_KERNEL_BLEND_BWD, k_blend_bwd<3>, L.n_tiles, 256, 0, s, ranges, vsorted, at<float4>(ws, L.o_prep),
+              at<float2>(ws, L.o_reach), g->curve, col, blp, dimage, Tf, nl, dgauss, st);
   else
-    NS_LAUNCH(NS_KERNEL_BLEND_BWD, k_blend_bwd<1>, L.n_tiles, 256, 0, s, ranges, vsorted, rec, g->curve, col, blp, dimage, Tf, nl, dgauss, st);
+    NS_LAUNCH(NS_KERNEL_BLEND_BWD, k_blend_bwd<1>, L.n_tiles, 256, 0, s, ranges, vsorted, at<float4>(ws, L.o_prep),
+              at<float2>(ws, L.o_reach), g->curve, col, blp, dimage, Tf, nl, dgauss, st);
   return NS_OK;
 }
 bool raster_params_ok(const ns_raster_params* rp) { return check_raster(rp); }

@@ -333,7 +333,7 @@ def config4(seed=1004, n_scenes=64, size=256):
     return b.build("batched-64x256", tgt, dict(SAMPLE_DEFAULTS, h=1.0), dict(RASTER_DEFAULTS))
 
 
-def config5(seed=1005, n_paths=2048, size=1024, median_r=22.0):
+def config5(seed=1005, n_paths=2048, size=1024, median_r=19.0):
     """Vectorization scale: 1024x1024 RGB, 2048 closed filled paths with
     p in {2,3,4,5} and 8-64 key points, lognormal sizes; ~8M fill Gaussians at
     grid step h = 1 (the step the grid-step annealing schedule ends at)."""
