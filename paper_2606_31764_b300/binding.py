@@ -82,7 +82,7 @@ SIGNATURES = {
 
 KERNELS = dict(plan=1, boundary=2, emit=3, bin_count=4, bin_emit=5, radix_hist=6, radix_scatter=7, ranges=8,
                blend_fwd=9, blend_bwd=10, chain=11, chain_boundary=12, knot_grads=13, mse=14, adam=15, scan=16,
-               other=17)
+               other=17, chain_contour=18)
 
 _lib = None
 

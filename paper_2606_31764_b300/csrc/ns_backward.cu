@@ -101,22 +101,27 @@ __device__ __forceinline__ int span_at(const CurveRef& cr, const float* U, float
   return find_span(U, P, cr.n, u);
 }
 
+// kFillTasks selects the tasks a launch handles: contour tasks need the
+// degree-templated reverse sweep (many registers), fill tasks only load and
+// combine a few values (latency-bound, so they run in a lean kernel of their own).
+template <bool kFillTasks>
 __global__ void __launch_bounds__(256) k_chain(ns_curves cv, ChainParams cp, const CurvePlan* __restrict__ plan,
                                                const int* __restrict__ order, const float* __restrict__ knots,
                                                const float2* __restrict__ bpts, const DevState* __restrict__ st,
                                                const float4* __restrict__ rec, const int* __restrict__ gaux,
                                                const float* __restrict__ dgauss, long long gcap, long long bcap,
                                                float* dkey, float* dknots, float2* dbpts, float* dcolor) {
-  __shared__ float s_cp[4 * kWin];
-  __shared__ float s_kn[kWin + 2 * kMaxP];
+  __shared__ float s_cp[kFillTasks ? 2 * kWinB : 4 * kWin];
+  __shared__ float s_kn[kFillTasks ? 1 : kWin + 2 * kMaxP];
   __shared__ float s_red[8];
   __shared__ int s_span[2];
-  float2* s_db = reinterpret_cast<float2*>(s_cp);   // fill tasks reuse the window
+  float2* s_db = reinterpret_cast<float2*>(s_cp);
   const int n_tasks = st->n_chunks;
   const int nc = cv.n_curves;
   for (int task = blockIdx.x; task < n_tasks; task += gridDim.x) {
     const int c = curve_of_task(plan, order, nc, task);
     const CurvePlan pl = plan[c];
+    if ((pl.kind == kFill) != kFillTasks) continue;
     const CurveRef cr = curve_ref(cv, c);
     const float* U = knots + cr.knot0;
     const int l0 = (task - pl.chunk_off) * kChunk;
@@ -130,7 +135,7 @@ __global__ void __launch_bounds__(256) k_chain(ns_curves cv, ChainParams cp, con
       g0 = reinterpret_cast<const float4*>(dgauss)[2 * g];
       g1 = reinterpret_cast<const float4*>(dgauss)[2 * g + 1];
     }
-    if (pl.kind != kFill) {
+    if constexpr (!kFillTasks) {
       // window of control points [span(first) - p, span(last)], knots
       // [span(first) - p + 1, span(last) + p]
       if (threadIdx.x == 0) {
@@ -185,8 +190,7 @@ __global__ void __launch_bounds__(256) k_chain(ns_curves cv, ChainParams cp, con
         atomicAdd(dcolor + 4 * c + 2, s_red[4]);
         atomicAdd(dcolor + 4 * c + 3, s_red[5]);
       }
-      continue;
-    }
+    } else {
     // fill task (skipped when its polyline overflowed the boundary capacity)
     if ((long long)pl.b_off + pl.M > bcap) continue;
     const int B = pl.M;
@@ -250,6 +254,7 @@ __global__ void __launch_bounds__(256) k_chain(ns_curves cv, ChainParams cp, con
       atomicAdd(dcolor + 4 * c + 1, s_red[3]);
       atomicAdd(dcolor + 4 * c + 2, s_red[4]);
       atomicAdd(dcolor + 4 * c + 3, s_red[5]);
+    }
     }
   }
 }
@@ -371,7 +376,10 @@ extern "C" ns_status splat_backward(const ns_curves* curves, const ns_gaussians*
       cp.h = sp->h;
       cp.gamma = sp->gamma;
       cp.kappa = sp->kappa;
-      NS_LAUNCH(NS_KERNEL_CHAIN, k_chain, num_sms() * 8, 256, 0, s, *curves, cp, plan, order, knots, bpts, st,
+      NS_LAUNCH(NS_KERNEL_CHAIN, k_chain<true>, num_sms() * 8, 256, 0, s, *curves, cp, plan, order, knots, bpts, st,
+                reinterpret_cast<const float4*>(g->rec), g->aux, dg, cap->gaussians,
+                cap->boundary, out->dkey, dknots, dbpts, out->dcolor);
+      NS_LAUNCH(NS_KERNEL_CHAIN_CONTOUR, k_chain<false>, num_sms() * 8, 256, 0, s, *curves, cp, plan, order, knots, bpts, st,
                                             reinterpret_cast<const float4*>(g->rec), g->aux, dg, cap->gaussians,
                                             cap->boundary, out->dkey, dknots, dbpts, out->dcolor);
       if (L.bcap > 0)

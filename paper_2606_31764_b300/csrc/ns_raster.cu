@@ -233,19 +233,45 @@ __global__ void __launch_bounds__(256) k_radix_hist(const uint32_t* __restrict__
   for (int d = threadIdx.x; d < nd; d += blockDim.x) hist[(long long)d * nb + blockIdx.x] = h[d];
 }
 
-// Exclusive scan of the digit-major histogram (digit, block).
-__global__ void k_radix_scan(uint32_t* hist, const DevState* st, int bits) {
-  __shared__ uint32_t s_warp[32];
-  __shared__ uint32_t s_carry;
-  const int n_pairs = st->pair_count;
-  const int nb = (n_pairs + kSortItems - 1) / kSortItems;
-  const long long n = (long long)nb << bits;
-  if (threadIdx.x == 0) s_carry = 0;
+// Exclusive scan of the digit-major histogram hist[digit][block], in two
+// parallel steps: one block per digit sums its row, then one block per digit
+// scans its row starting from the total of all smaller digits.
+__device__ __forceinline__ uint32_t block_sum_u32(uint32_t v, uint32_t* s_warp) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = v;
   __syncthreads();
+  uint32_t t = 0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_warp[w];
+  __syncthreads();
+  return t;
+}
+
+__global__ void __launch_bounds__(256) k_radix_totals(const uint32_t* __restrict__ hist, const DevState* st,
+                                                      uint32_t* totals) {
+  __shared__ uint32_t s_warp[8];
+  const int nb = (st->pair_count + kSortItems - 1) / kSortItems;
+  const uint32_t* row = hist + (long long)blockIdx.x * nb;
+  uint32_t v = 0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) v += row[b];
+  const uint32_t t = block_sum_u32(v, s_warp);
+  if (threadIdx.x == 0) totals[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(256) k_radix_scan(uint32_t* hist, const DevState* st,
+                                                    const uint32_t* __restrict__ totals) {
+  __shared__ uint32_t s_warp[8];
+  __shared__ uint32_t s_carry;
+  const int nb = (st->pair_count + kSortItems - 1) / kSortItems;
+  uint32_t base = 0;
+  for (int d = threadIdx.x; d < (int)blockIdx.x; d += blockDim.x) base += totals[d];
+  base = block_sum_u32(base, s_warp);
+  if (threadIdx.x == 0) s_carry = base;
+  __syncthreads();
+  uint32_t* row = hist + (long long)blockIdx.x * nb;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (long long base = 0; base < n; base += blockDim.x) {
-    const long long i = base + threadIdx.x;
-    const uint32_t v = i < n ? hist[i] : 0u;
+  for (int b0 = 0; b0 < nb; b0 += blockDim.x) {
+    const int i = b0 + threadIdx.x;
+    const uint32_t v = i < nb ? row[i] : 0u;
     uint32_t x = v;
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -263,7 +289,7 @@ __global__ void k_radix_scan(uint32_t* hist, const DevState* st, int bits) {
     }
     __syncthreads();
     const uint32_t excl = s_carry + (w > 0 ? s_warp[w - 1] : 0u) + x - v;
-    if (i < n) hist[i] = excl;
+    if (i < nb) row[i] = excl;
     __syncthreads();
     if (threadIdx.x == blockDim.x - 1) s_carry = excl + v;
     __syncthreads();
@@ -657,6 +683,7 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
   uint32_t* k1 = at<uint32_t>(ws, L.o_k1);
   uint32_t* v1 = at<uint32_t>(ws, L.o_v1);
   uint32_t* hist = at<uint32_t>(ws, L.o_hist);
+  uint32_t* totals = hist + 256 * (size_t)L.sort_blocks;   // the layout's spare 256 entries
   int2* ranges = at<int2>(ws, L.o_ranges);
   float* Tf = at<float>(ws, L.o_T);
   int* nl = at<int>(ws, L.o_nlast);
@@ -693,7 +720,8 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
     const int shift = pass * rpn.bits_per_pass;
     if (sort_blocks > 0) {
       NS_LAUNCH(NS_KERNEL_RADIX_HIST, k_radix_hist, sort_blocks, 256, 0, s, kin, st, shift, rpn.bits_per_pass, hist);
-      NS_LAUNCH(NS_KERNEL_SCAN, k_radix_scan, 1, 1024, 0, s, hist, st, rpn.bits_per_pass);
+      NS_LAUNCH(NS_KERNEL_SCAN, k_radix_totals, 1 << rpn.bits_per_pass, 256, 0, s, hist, st, totals);
+      NS_LAUNCH(NS_KERNEL_SCAN, k_radix_scan, 1 << rpn.bits_per_pass, 256, 0, s, hist, st, totals);
       NS_LAUNCH(NS_KERNEL_RADIX_SCATTER, k_radix_scatter, sort_blocks, 256, 0, s, kin, vin, kout, vout, hist, st, shift, rpn.bits_per_pass);
     }
     std::swap(kin, kout);

@@ -20,6 +20,7 @@ namespace ns {
 
 constexpr int kPlanThreads = 128;
 constexpr int kSegBatch = 1024;   // boundary segments staged in shared memory per pass
+constexpr int kCluster = 8;       // consecutive segments per bounding-box cluster
 
 __device__ __forceinline__ float block_sum(float v, float* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -300,12 +301,13 @@ __device__ void emit_contour(const ns_curves& cv, const CurveRef& cr, const floa
 }
 
 // Persistent: each block iteration handles one task of 256 Gaussians of one curve.
-__global__ void __launch_bounds__(256) k_emit(ns_curves cv, ns_sample_params sp, const CurvePlan* __restrict__ plan,
+__global__ void __launch_bounds__(256, 4) k_emit(ns_curves cv, ns_sample_params sp, const CurvePlan* __restrict__ plan,
                                               const int* __restrict__ order, const float* __restrict__ knots,
                                               const float2* __restrict__ bpts, const DevState* __restrict__ st,
                                               float4* rec, int* gcurve, int* gaux, long long gcap, long long bcap) {
   __shared__ float4 seg[kSegBatch];   // {b0.x, b0.y, e.x, e.y}
-  __shared__ float seginv[kSegBatch]; // 1/|e|^2 (0 for a zero-length segment)
+  __shared__ float2 segb[kSegBatch];  // {b1.y, 1/|e|^2 (0 for a zero-length segment)}
+  __shared__ float4 cbox[kSegBatch / kCluster];  // {x0, x1, y0, y1} of each segment cluster
   const int n_tasks = st->n_chunks;
   const int nc = cv.n_curves;
   for (int task = blockIdx.x; task < n_tasks; task += gridDim.x) {
@@ -338,6 +340,7 @@ __global__ void __launch_bounds__(256) k_emit(ns_curves cv, ns_sample_params sp,
     int arg = 0, wn = 0;
     for (int base = 0; base < B; base += kSegBatch) {
       const int nseg = min(kSegBatch, B - base);
+      const int ncl = (nseg + kCluster - 1) / kCluster;
       __syncthreads();
       for (int s = threadIdx.x; s < nseg; s += blockDim.x) {
         const int i = base + s;
@@ -346,25 +349,59 @@ __global__ void __launch_bounds__(256) k_emit(ns_curves cv, ns_sample_params sp,
         const float ex = b1.x - b0.x, ey = b1.y - b0.y;
         const float ee = ex * ex + ey * ey;
         seg[s] = make_float4(b0.x, b0.y, ex, ey);
-        seginv[s] = ee > 0.f ? 1.f / ee : 0.f;
+        segb[s] = make_float2(b1.y, ee > 0.f ? 1.f / ee : 0.f);
+      }
+      // bounding box of each cluster of kCluster consecutive segments
+      for (int cl = threadIdx.x; cl < ncl; cl += blockDim.x) {
+        float x0 = FLT_MAX, x1 = -FLT_MAX, y0 = FLT_MAX, y1 = -FLT_MAX;
+        for (int k = cl * kCluster; k < min(nseg, (cl + 1) * kCluster); ++k) {
+          const int i = base + k;
+          const float2 b0 = bpts[pl.b_off + i];
+          const float2 b1 = bpts[pl.b_off + (i + 1 == B ? 0 : i + 1)];
+          x0 = fminf(x0, fminf(b0.x, b1.x));
+          x1 = fmaxf(x1, fmaxf(b0.x, b1.x));
+          y0 = fminf(y0, fminf(b0.y, b1.y));
+          y1 = fmaxf(y1, fmaxf(b0.y, b1.y));
+        }
+        cbox[cl] = make_float4(x0, x1, y0, y1);
       }
       __syncthreads();
       if (valid) {
-        for (int s = 0; s < nseg; ++s) {
-          const float4 sg = seg[s];
-          const float rx = qx - sg.x, ry = qy - sg.y;
-          const float t = fminf(fmaxf((rx * sg.z + ry * sg.w) * seginv[s], 0.f), 1.f);
-          const float dx = rx - t * sg.z, dy = ry - t * sg.w;
-          const float d2 = dx * dx + dy * dy;
-          if (d2 < best) { best = d2; arg = base + s; }
-          // winding number by signed crossings of the horizontal ray (Eq. S2
-          // is integral off the polyline; this evaluates it exactly there)
-          const float y1 = sg.y + sg.w;
-          const float isleft = sg.z * ry - rx * sg.w;
-          if (sg.y <= qy) {
-            if (y1 > qy && isleft > 0.f) ++wn;
-          } else {
-            if (y1 <= qy && isleft < 0.f) --wn;
+        for (int cl = 0; cl < ncl; ++cl) {
+          const float4 bb = cbox[cl];
+          // distance: a cluster whose box lies farther than the best distance so
+          // far cannot hold a nearer segment (margin covers the rounding of d^2)
+          const float bx = fmaxf(fmaxf(bb.x - qx, qx - bb.y), 0.f);
+          const float by = fmaxf(fmaxf(bb.z - qy, qy - bb.w), 0.f);
+          const float lb2 = bx * bx + by * by;
+          const bool need_d = !(lb2 > best + 1e-3f * (lb2 + 1.f));
+          // crossings of the ray to +x: only a cluster with vertices on both sides
+          // of y = qy (same comparisons as the per-segment test) that reaches
+          // x >= qx - 0.01 can contribute
+          const bool need_w = bb.z <= qy && bb.w > qy && bb.y >= qx - 0.01f;
+          if (!need_d && !need_w) continue;
+          const int k1 = min(nseg, (cl + 1) * kCluster);
+          for (int k = cl * kCluster; k < k1; ++k) {
+            const float4 sg = seg[k];
+            const float rx = qx - sg.x, ry = qy - sg.y;
+            if (need_d) {
+              const float2 sb = segb[k];
+              const float t = fminf(fmaxf((rx * sg.z + ry * sg.w) * sb.y, 0.f), 1.f);
+              const float dx = rx - t * sg.z, dy = ry - t * sg.w;
+              const float d2 = dx * dx + dy * dy;
+              if (d2 < best) { best = d2; arg = base + k; }
+            }
+            if (need_w) {
+              // winding number by signed crossings of the horizontal ray (Eq. S2
+              // is integral off the polyline; this evaluates it exactly there)
+              const float y1 = segb[k].x;
+              const float isleft = sg.z * ry - rx * sg.w;
+              if (sg.y <= qy) {
+                if (y1 > qy && isleft > 0.f) ++wn;
+              } else {
+                if (y1 <= qy && isleft < 0.f) --wn;
+              }
+            }
           }
         }
       }

@@ -85,3 +85,39 @@ def test_capacity_overflow_reports_needed_sizes():
     assert r.status == 2
     assert r.gaussians == sum(p.count for p in pl_o)
     assert r.boundary == sum(p.n_boundary for p in pl_o)
+
+
+@pytest.mark.parametrize("seed,h", [(61, 1.0), (62, 2.0), (63, 1.0)])
+def test_fill_nearest_segment_and_sign(seed, h):
+    """The kernel's nearest segment (aux) attains the oracle's minimum distance
+    from the same grid point, and its inside/outside sign agrees with the
+    winding number wherever the point is not on the polyline."""
+    import torch as _t
+    from oracle import sampling as sm
+    sc = scenes.small_closed(seed, n_curves=4, size=80, filled=True, h=h, degrees=(2, 3, 4, 5))
+    pl_o = op.plan(sc)
+    assert _no_ties(pl_o)
+    sp, img, rep, inputs, G = run_scene(sc)
+    rec = sp.rec[:G].cpu().numpy().astype(np.float64)
+    cur = sp.curve[:G].cpu().numpy()
+    aux = sp.aux[:G].cpu().numpy()
+    k, t, c = op.leaves(sc, False)
+    for cv in range(sc.n_curves):
+        sel = np.nonzero(cur == cv)[0]
+        p, fl, cp, U = sm.curve_inputs(sc, cv, k, t)
+        a, b = sm.nb.domain(U, p)
+        poly = sm.nb.curve_point(cp, U, p, sm.boundary_parameters(a, b, pl_o[cv].n_boundary))[:, :2]
+        q = _t.as_tensor(rec[sel, :2])
+        d_min, _ = sm.unsigned_distance(q, poly)
+        ins = aux[sel] >= 0
+        i0 = np.where(ins, aux[sel], ~aux[sel])
+        b0 = poly[i0]
+        b1 = poly[(i0 + 1) % poly.shape[0]]
+        e = b1 - b0
+        tt = (((q - b0) * e).sum(1) / (e * e).sum(1)).clamp(0, 1)
+        d_sel = (q - b0 - tt[:, None] * e).norm(dim=1)
+        tol = 32 * EPS32 * (sc.width + pl_o[cv].length)
+        assert float((d_sel - d_min).abs().max()) <= tol
+        wn = sm.winding_number(q, poly).numpy()
+        clear = d_min.numpy() > tol
+        assert np.array_equal(ins[clear], (wn > 0.5)[clear])
