@@ -250,7 +250,8 @@ ns_status ns_clear_status(void* workspace, void* stream);
  *     length, parameter domain, fill grid origin) then int32 {kind (0 invalid,
  *     1 open, 2 closed stroke, 3 filled), M (contour samples, or boundary
  *     points of a fill), Gaussians, nx, ny, first Gaussian, first boundary
- *     point, first task, scene, 0, 0},
+ *     point, first task among the curves of its kind (fill or contour), scene,
+ *     tasks of the other kind before it, 0},
  *   4 boundary points (float32 pairs), 5 per-pixel final transmittance,
  *   6 per-pixel composited-list length (int32)
  */

@@ -149,6 +149,7 @@ __global__ void k_reset_state(DevState* st) {
   st->status = 0;
   st->bad_curve = -1;
   st->n_chunks = 0;
+  st->n_ctasks = 0;
   st->g_total = st->b_total = st->pair_total = st->culled = 0;
   st->g_count = st->pair_count = st->b_count = 0;
   st->blend_evals = st->blend_bwd_evals = st->blend_contribs = 0;

@@ -116,12 +116,11 @@ __global__ void __launch_bounds__(256) k_chain(ns_curves cv, ChainParams cp, con
   __shared__ float s_red[8];
   __shared__ int s_span[2];
   float2* s_db = reinterpret_cast<float2*>(s_cp);
-  const int n_tasks = st->n_chunks;
+  const int n_tasks = kFillTasks ? st->n_chunks : st->n_ctasks;
   const int nc = cv.n_curves;
   for (int task = blockIdx.x; task < n_tasks; task += gridDim.x) {
-    const int c = curve_of_task(plan, order, nc, task);
+    const int c = curve_of_task(plan, order, nc, task, kFillTasks);
     const CurvePlan pl = plan[c];
-    if ((pl.kind == kFill) != kFillTasks) continue;
     const CurveRef cr = curve_ref(cv, c);
     const float* U = knots + cr.knot0;
     const int l0 = (task - pl.chunk_off) * kChunk;

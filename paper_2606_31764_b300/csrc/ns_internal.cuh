@@ -24,7 +24,8 @@ enum CurveKind : int { kNone = 0, kOpen = 1, kClosedStroke = 2, kFill = 3 };
 struct DevState {
   int status;          // ns_status, first error wins
   int bad_curve;
-  int n_chunks;        // sampling / chain tasks of the current sample
+  int n_chunks;        // fill tasks of the current sample (numbered first)
+  int n_ctasks;        // contour tasks (numbered after the fill tasks)
   int sorted_buf;      // which pair buffer holds the sorted result
   unsigned long long g_total;     // Gaussians needed
   unsigned long long b_total;     // boundary points needed
@@ -33,7 +34,7 @@ struct DevState {
   int g_count;         // min(g_total, capacity)
   int pair_count;      // min(pair_total, capacity)
   int b_count;
-  int pad[5];
+  int pad[4];
   unsigned long long blend_evals;      // alpha evaluations of the last forward blend
   unsigned long long blend_bwd_evals;  // alpha evaluations of the last backward blend
   unsigned long long blend_contribs;   // composited (pixel, Gaussian) pairs of the last forward blend
@@ -48,7 +49,7 @@ struct CurvePlan {
   int nx, ny;              // fill grid
   int g_off;               // first Gaussian (front-to-back order)
   int b_off;               // first boundary point
-  int chunk_off;           // first task
+  int chunk_off;           // first task of this curve's kind (fill tasks and contour tasks are numbered separately)
   int scene;
   int pad[2];
 };
@@ -318,14 +319,20 @@ __device__ __forceinline__ float contour_t(const CurvePlan& pl, int l, int kappa
   return float(l) / float(pl.M);
 }
 
-// The block task (chunk) -> curve map: largest c with plan[c].chunk_off <= task,
-// over curves in front-to-back order (chunk offsets are increasing in that order).
+// Task -> curve map.  Tasks are 256 Gaussians of one curve; fill tasks and
+// contour tasks are numbered separately, each kind in front-to-back curve
+// order, and a curve's chunk_off counts the tasks of its own kind before it.
+// Curves of the other kind contribute no tasks to the count, so over the
+// ordered list the offsets of one kind never decrease, and the largest position
+// whose offset is <= task is the curve that owns it.
 __device__ __forceinline__ int curve_of_task(const CurvePlan* __restrict__ plan, const int* __restrict__ order,
-                                             int nc, int task) {
+                                             int nc, int task, bool fill) {
   int lo = 0, hi = nc - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (plan[order[mid]].chunk_off <= task) lo = mid; else hi = mid - 1;
+    const CurvePlan& q = plan[order[mid]];
+    const int off = (q.kind == kFill) == fill ? q.chunk_off : q.pad[0];
+    if (off <= task) lo = mid; else hi = mid - 1;
   }
   return order[lo];
 }

@@ -119,7 +119,8 @@ __global__ void __launch_bounds__(256) k_bin_count(const float4* __restrict__ re
       const int cv = gcurve[g];
       if (cv >= 0 && cv < bp.n_curves) cnt += tile_rect(r, bp, x0, y0, nx);
       prep[g] = make_float4(r.x, r.y, ncoef(r.z), r.w);
-      reach[g] = make_float2(r.z > 0.f && r.w > 0.f ? reach2(r.z, r.w, bp.log_amin) : -1.f, r.z);
+      reach[g] = make_float2(r.z > 0.f && r.w > 0.f ? reach2(r.z, r.w, bp.log_amin) : -1.f,
+                             r.z > 0.f ? 1.f / r.z : 0.f);
       culled += (r.z > 0.f && r.w < bp.alpha_min) ? 1 : 0;
     }
   }
@@ -380,7 +381,7 @@ __global__ void k_ranges(const uint32_t* __restrict__ keys, const DevState* st, 
 //
 // Per-Gaussian constants are prepared once by k_bin_count:
 //   prep  = {mu_x, mu_y, ncoef = -1/(2 sigma^2), o}
-//   reach = {squared reach, sigma}
+//   reach = {squared reach, 1/sigma}
 
 struct BlendParams {
   float alpha_min, alpha_max, t_min;
@@ -522,7 +523,7 @@ __global__ void __launch_bounds__(256, 4) k_blend_bwd(const int2* __restrict__ r
                                                    float* dgauss, DevState* st) {
   __shared__ float4 s_q[8][32];
   __shared__ float4 s_c[8][32];
-  __shared__ float s_sig[8][32];
+  __shared__ float s_isig[8][32];
   __shared__ uint32_t s_id[8][32];
   int s, px, py;
   WarpRect wr;
@@ -554,7 +555,7 @@ __global__ void __launch_bounds__(256, 4) k_blend_bwd(const int2* __restrict__ r
       if (hit) {
         s_q[w][lane] = q;
         s_c[w][lane] = color[gcurve[g]];
-        s_sig[w][lane] = rs.y;
+        s_isig[w][lane] = rs.y;
         s_id[w][lane] = g;
       }
     }
@@ -572,7 +573,7 @@ __global__ void __launch_bounds__(256, 4) k_blend_bwd(const int2* __restrict__ r
         const float a = gauss_alpha(fx, fy, q, bp.alpha_max, dx, dy, d2, e);
         if (a >= bp.alpha_min) {
           contrib = true;
-          T = T / (1.f - a);
+          T = __fdividef(T, 1.f - a);   // transmittance in front of this Gaussian
           const float wgt = a * T;
           const float4 cc = s_c[w][b];
           float da = (cc.x - Bk[0]) * dI[0];
@@ -587,13 +588,12 @@ __global__ void __launch_bounds__(256, 4) k_blend_bwd(const int2* __restrict__ r
           }
           da *= T;
           if (__fmul_rn(q.w, e) < bp.alpha_max) {
-            const float sg = s_sig[w][b];
-            const float is2 = 1.f / (sg * sg);
+            const float isg = s_isig[w][b];
             v[3] = e * da;
-            const float aa = da * a * is2;
+            const float aa = da * a * isg * isg;   // dalpha/dmu = alpha (x - mu) / sigma^2
             v[0] = aa * dx;
             v[1] = aa * dy;
-            v[2] = aa * d2 / sg;
+            v[2] = aa * d2 * isg;                  // dalpha/dsigma = alpha d^2 / sigma^3
           }
         }
       }

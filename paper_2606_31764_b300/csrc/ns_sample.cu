@@ -272,19 +272,33 @@ __global__ void __launch_bounds__(kPlanThreads) k_boundary(ns_curves cv, ns_samp
   }
 }
 
+// Gaussian offsets over all curves (front to back), and task offsets per kind:
+// chunk_off numbers a curve's tasks among the curves of its kind; pad[0] holds
+// the task count of the other kind before it, so that each kind's offsets
+// can be searched over the one ordered list (see curve_of_task).
 __global__ void k_scan_gauss(int nc, CurvePlan* plan, const int* order, DevState* st, long long gcap,
                              int* g_count_out) {
   const long long tot = block_scan_items(
       nc, [&](int f) { return plan[order[f]].count; },
       [&](int f, long long off) { plan[order[f]].g_off = int(off < 0x7fffffff ? off : 0x7fffffff); });
-  const long long tasks = block_scan_items(
-      nc, [&](int f) { return (plan[order[f]].count + kChunk - 1) / kChunk; },
-      [&](int f, long long off) { plan[order[f]].chunk_off = int(off); });
+  const long long ftasks = block_scan_items(
+      nc, [&](int f) { const CurvePlan& q = plan[order[f]]; return q.kind == kFill ? (q.count + kChunk - 1) / kChunk : 0; },
+      [&](int f, long long off) {
+        CurvePlan& q = plan[order[f]];
+        if (q.kind == kFill) q.chunk_off = int(off); else q.pad[0] = int(off);
+      });
+  const long long ctasks = block_scan_items(
+      nc, [&](int f) { const CurvePlan& q = plan[order[f]]; return q.kind != kFill ? (q.count + kChunk - 1) / kChunk : 0; },
+      [&](int f, long long off) {
+        CurvePlan& q = plan[order[f]];
+        if (q.kind != kFill) q.chunk_off = int(off); else q.pad[0] = int(off);
+      });
   if (threadIdx.x == 0) {
     st->g_total = (unsigned long long)tot;
     const int gc = int(tot < gcap ? tot : gcap);
     st->g_count = gc;
-    st->n_chunks = int(tasks);
+    st->n_chunks = int(ftasks);
+    st->n_ctasks = int(ctasks);
     if (g_count_out) *g_count_out = gc;
     if (tot > gcap) raise_status(st, NS_ERR_CAPACITY);
   }
@@ -308,10 +322,13 @@ __global__ void __launch_bounds__(256, 4) k_emit(ns_curves cv, ns_sample_params 
   __shared__ float4 seg[kSegBatch];   // {b0.x, b0.y, e.x, e.y}
   __shared__ float2 segb[kSegBatch];  // {b1.y, 1/|e|^2 (0 for a zero-length segment)}
   __shared__ float4 cbox[kSegBatch / kCluster];  // {x0, x1, y0, y1} of each segment cluster
-  const int n_tasks = st->n_chunks;
+  const int n_fill = st->n_chunks;
+  const int n_tasks = n_fill + st->n_ctasks;   // fill tasks (heavier) first
   const int nc = cv.n_curves;
-  for (int task = blockIdx.x; task < n_tasks; task += gridDim.x) {
-    const int c = curve_of_task(plan, order, nc, task);
+  for (int t = blockIdx.x; t < n_tasks; t += gridDim.x) {
+    const bool fill_task = t < n_fill;
+    const int task = fill_task ? t : t - n_fill;
+    const int c = curve_of_task(plan, order, nc, task, fill_task);
     const CurvePlan pl = plan[c];
     const CurveRef cr = curve_ref(cv, c);
     const float* U = knots + cr.knot0;
@@ -456,7 +473,7 @@ extern "C" ns_status nurbs_sample(const ns_curves* curves, const ns_sample_param
   if (nc > 0) cudaMemsetAsync(order, 0, sizeof(int) * (size_t)nc, s);   // in range even if offsets are bad
   if (nc == 0) {
     cudaMemsetAsync(out->count, 0, sizeof(int), s);
-    cudaMemsetAsync(&st->n_chunks, 0, sizeof(int), s);
+    cudaMemsetAsync(&st->n_chunks, 0, 2 * sizeof(int), s);
     cudaMemsetAsync(&st->g_count, 0, sizeof(int), s);
     return cudaGetLastError() == cudaSuccess ? NS_OK : NS_ERR_CUDA;
   }

@@ -98,3 +98,30 @@ def test_pair_capacity_overflow_reports_size():
     tid_o, _, _ = op.pairs_records(sc, g["rec"], g["curve"])
     sp, img, rep, _ = run_records(sc, g["rec"], g["curve"], capacity=(G, 100, 16))
     assert rep.status == 2 and rep.pairs == tid_o.shape[0]
+
+
+def test_adam_step_matches_oracle():
+    """ns_adam_step (with the clamps of Table S1) against the FP64 definition."""
+    import ctypes as C
+    from oracle import optim
+    from paper_2606_31764_b300 import binding as B
+    rng = np.random.default_rng(9)
+    n = 100_003
+    p = rng.uniform(0.0, 2.0, n).astype(np.float32)
+    tp = torch.as_tensor(p, device="cuda")
+    tm = torch.zeros(n, device="cuda")
+    tv = torch.zeros(n, device="cuda")
+    m = np.zeros(n)
+    v = np.zeros(n)
+    pp = p.astype(np.float64)
+    for step in range(1, 4):
+        g = rng.standard_normal(n).astype(np.float32)
+        tg = torch.as_tensor(g, device="cuda")
+        B.call("ns_adam_step", C.c_void_p(tp.data_ptr()), C.c_void_p(tg.data_ptr()), C.c_void_p(tm.data_ptr()),
+               C.c_void_p(tv.data_ptr()), C.c_int64(n), C.c_float(0.01), C.c_float(0.9), C.c_float(0.999),
+               C.c_float(1e-8), C.c_int32(step), C.c_float(0.01), C.c_float(2.0),
+               C.c_void_p(torch.cuda.current_stream().cuda_stream))
+        pp, m, v = optim.adam_step(pp, g, m, v, step, lr=0.01, lo=0.01, hi=2.0)
+        torch.cuda.synchronize()
+        assert np.abs(tp.cpu().numpy() - pp).max() <= 1e-6
+        assert np.abs(tm.cpu().numpy() - m).max() <= 1e-6
