@@ -272,6 +272,34 @@ ns_status ns_profile_next_launch(int32_t kernel_id, void* start, void* stop);
 /* Number of kernels the calling thread has launched (or captured) through the library. */
 uint64_t ns_launch_count(void);
 
+/*
+ * splat_forward for callers that cannot allocate device memory where they
+ * render: an engine or server that owns and pre-plans all device memory, a
+ * plugin limited to the buffers it is handed, or a loop that must not trigger
+ * the device-wide synchronisation an allocation can cause.  The paper has no
+ * counterpart; it is a packaging of splat_forward.
+ *
+ * Same inputs and output as splat_forward, but no workspace: the scratch
+ * (tile pairs, sort buffers, ranges, per-pixel state, status) is a fixed
+ * 16 MiB device array inside this library, held by every GPU that loads it
+ * until the process exits.  Limits: g->capacity <= 65536 Gaussians, at most
+ * 262144 (tile, Gaussian) pairs, and the batch's workspace (ns_workspace_size
+ * with those capacities and no boundary points) must fit the 16 MiB; a larger
+ * request returns NS_ERR_INVALID_ARG with a message saying which limit.  More
+ * pairs than the limit is only known on the device: that work is dropped and
+ * the status reads NS_ERR_CAPACITY.
+ *   report: host pointer or NULL.  When non-NULL the call synchronises the
+ *   stream and fills it (as ns_poll_status would).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), so make it before any stream capture.  All calls on
+ * one device share the array: calls that overlap on the GPU (other streams or
+ * threads) race and must be serialised by the caller.  Each call clears the
+ * status it inherits from the previous one.  It calls no allocator.
+ */
+ns_status splat_forward_noalloc(const ns_curves* curves, const ns_gaussians* g,
+                                const ns_raster_params* rp, float* image, ns_report* report,
+                                void* stream);
+
 /* Message of the last error on the calling thread ("" if none). */
 const char* ns_last_error(void);
 

@@ -76,6 +76,8 @@ SIGNATURES = {
     "ns_workspace_copy": (C.c_int, [_p, C.POINTER(NsCurves), C.POINTER(NsCapacity), C.POINTER(NsRasterParams),
                                     C.c_int32, _p, C.c_size_t, _p]),
     "ns_profile_next_launch": (C.c_int, [C.c_int32, _p, _p]),
+    "splat_forward_noalloc": (C.c_int, [C.POINTER(NsCurves), C.POINTER(NsGaussians), C.POINTER(NsRasterParams),
+                                        _p, C.POINTER(NsReport), _p]),
     "ns_launch_count": (C.c_uint64, []),
     "ns_last_error": (C.c_char_p, []),
 }

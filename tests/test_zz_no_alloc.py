@@ -1,0 +1,64 @@
+"""splat_forward_noalloc against splat_forward.
+
+The no-allocation variant serves callers that cannot call cudaMalloc where
+they render (an engine or server that owns and pre-plans all device memory, a
+plugin limited to the buffers it is handed, a loop that must not trigger an
+allocation's device synchronisation).  It keeps its scratch in a fixed device
+array of the library.  This test renders the same Gaussian set with both entry
+points, twice in a row with the new one (the array keeps the previous call's
+contents), and compares the images within the 1e-5 image tolerance of the
+other splat tests.  Collected last so that a stop-at-first-failure run has
+already run everything else.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+import scenes
+from oracle import pipeline as op
+from paper_2606_31764_b300 import binding as B
+
+from gpu_util import run_records
+
+pytestmark = pytest.mark.gpu
+
+
+def _noalloc(sp, inputs, out, report):
+    lib = B.load()
+    cs = sp.dev.struct(*inputs)
+    return lib.splat_forward_noalloc(C.byref(cs), C.byref(sp.g), C.byref(sp.rp), C.c_void_p(out.data_ptr()),
+                                     C.byref(report), C.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+
+@pytest.mark.parametrize("production", [False, True])
+def test_noalloc_matches_splat_forward(production):
+    sc = scenes.small_closed(71, n_curves=3, size=64, filled=True, h=2.0)
+    if production:
+        sc = sc.with_raster(**scenes.RASTER_DEFAULTS)
+    g = op.gaussians_fp32(sc)
+    sp, ref, rep, inputs = run_records(sc, g["rec"], g["curve"], capacity=(g["rec"].shape[0], 1 << 16, 16))
+    assert rep.status == 0
+    for _ in range(2):
+        out = torch.full_like(ref, float("nan"))
+        r = B.NsReport()
+        st = _noalloc(sp, inputs, out, r)
+        assert st == B.NS_OK, B.load().ns_last_error()
+        assert r.status == 0 and r.pairs == rep.pairs
+        err = (out - ref).abs().max().item()
+        assert err <= 1e-5, err
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch():
+    sc = scenes.small_closed(72, n_curves=2, size=48, filled=True, h=2.0)
+    g = op.gaussians_fp32(sc)
+    sp, ref, rep, inputs = run_records(sc, g["rec"], g["curve"])
+    big = B.NsGaussians(1 << 20, sp.g.rec, sp.g.curve, sp.g.aux, sp.g.count)
+    lib = B.load()
+    cs = sp.dev.struct(*inputs)
+    out = torch.empty_like(ref)
+    st = lib.splat_forward_noalloc(C.byref(cs), C.byref(big), C.byref(sp.rp), C.c_void_p(out.data_ptr()), None,
+                                   C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == B.NS_ERR_INVALID_ARG
+    assert b"65536" in lib.ns_last_error()
