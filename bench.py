@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-scene", action="store_true")
     ap.add_argument("--paths", type=int, default=2048, help="paths of the 1024x1024 workload (2048 = full)")
+    ap.add_argument("--tiles", default="8,16,32", help="tile sizes the autotuner tries (comma separated)")
     ap.add_argument("--cpu-sample-curves", type=int, default=64)
     ap.add_argument("--ref-sample-curves", type=int, default=8)
     return ap.parse_args()
@@ -149,12 +150,12 @@ class ClockSampler:
 class Step:
     """Preallocated buffers and the four calls of one training step."""
 
-    def __init__(self, scene, capacity):
+    def __init__(self, scene, capacity, raster=None):
         import torch
         from paper_2606_31764_b300.splat import Splatter, scene_tensors
         self.torch = torch
         self.scene = scene
-        self.sp = Splatter(scene, capacity=capacity)
+        self.sp = Splatter(scene, raster=raster, capacity=capacity)
         self.key, self.tau, self.color = scene_tensors(scene)
         self.rep = self.sp.fit(self.key, self.tau, self.color)
         self.target = torch.as_tensor(scene.target, device="cuda").contiguous()
@@ -172,6 +173,36 @@ class Step:
 
     def gaussians(self):
         return int(self.sp.count.item())
+
+
+def autotune(torch, scene, tiles, capacity, steps=3):
+    """Tile size by timing whole steps; pixels per thread of the blend kernels
+    by the library's ns_autotune_blend on each tile's workspace."""
+    best, best_ms, table = None, None, {}
+    for tile in tiles:
+        st = Step(scene, capacity, raster=dict(scene.raster, tile=tile))
+        st()
+        st.sp.autotune_blend(st.key, st.tau, st.color, st.dimage, repeats=3)
+        st()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            st()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        table[tile] = dict(ms=round(ms, 4), ppt_fwd=int(st.sp.rp.ppt_fwd), ppt_bwd=int(st.sp.rp.ppt_bwd))
+        if best_ms is None or ms < best_ms:
+            if best is not None:
+                del best
+            best, best_ms = st, ms
+        else:
+            del st
+        torch.cuda.empty_cache()
+    chosen = dict(tile=int(best.sp.rp.tile), ppt_fwd=int(best.sp.rp.ppt_fwd), ppt_bwd=int(best.sp.rp.ppt_bwd),
+                  tried=table)
+    return best, chosen
 
 
 def capture(torch, fn, n_steps=1, arm=None):
@@ -213,7 +244,8 @@ def run_gpu(args, dist, rank, world):
     lib = B.load()
     peaks = load_peaks()
     sc = scenes.config5(seed=1005 + rank, n_paths=args.paths)
-    step = Step(sc, capacity=(10_000_000, 20_000_000, 400_000))
+    step, tuning = autotune(torch, sc, [int(x) for x in args.tiles.split(",")],
+                            capacity=(10_000_000, 40_000_000, 400_000))
     step()
     torch.cuda.synchronize()
     rep = step.sp.report()
@@ -316,6 +348,7 @@ def run_gpu(args, dist, rank, world):
                            f"{(G * 32 + rep.pairs * 16) / 1e6:.0f} MB > 126 MB)",
                            timed="one CUDA-graph replay of K steps", parallelism=f"replicas x{world}"),
                gpu_launches=launches_per_step * args.steps, launches_per_step=launches_per_step,
+               autotune=tuning,
                clocks=ck, roofline=roof, kernels=kernels, e2e=e2e,
                blend=dict(evals_fwd=int(rep.blend_evals), evals_bwd=int(rep.blend_bwd_evals),
                           composited=int(rep.blend_contribs)),

@@ -91,12 +91,14 @@ typedef struct {
 
 /* Rasterizer settings (§3.4). */
 typedef struct {
-  int32_t tile;     /* tile edge in pixels: 16 */
+  int32_t tile;     /* tile edge in pixels: 8, 16 or 32 */
   float k_sigma;    /* a Gaussian is binned to the tiles of mu +- k_sigma sigma */
   float alpha_min;  /* a Gaussian with alpha < alpha_min at a pixel is skipped there */
   float alpha_max;  /* alpha is capped at alpha_max (keeps 1 - alpha > 0) */
   float t_min;      /* compositing stops before transmittance would drop below t_min */
   float bg[3];      /* background colour behind the residual transmittance (§3.4) */
+  int32_t ppt_fwd;  /* pixels per thread of the forward blend: 1, 2, 4 (4 needs tile >= 16), 0 = default */
+  int32_t ppt_bwd;  /* the same for the backward blend; neither changes any result */
 } ns_raster_params;
 
 /* Capacities that bound the data-dependent sizes. */
@@ -258,6 +260,21 @@ ns_status ns_clear_status(void* workspace, void* stream);
 ns_status ns_workspace_copy(void* workspace, const ns_curves* curves, const ns_capacity* cap,
                             const ns_raster_params* rp, int32_t which, void* dst,
                             size_t bytes, void* stream);
+
+/*
+ * Chooses the blend decomposition for this batch by timing: every valid
+ * pixels-per-thread setting of the forward and backward blend kernels is run
+ * `repeats` times on the workspace of a completed splat_forward (and, if
+ * dL_dimage is non-NULL, the backward with that upstream gradient) and the
+ * fastest is written to rp->ppt_fwd / rp->ppt_bwd.  The choice changes no
+ * result: every setting composites each pixel over the same list in the same
+ * order.  `image` is rewritten with identical values.  Synchronises the
+ * stream; call it before capturing a graph.  The tile size is fixed by the
+ * workspace layout; to choose it, size one workspace per candidate tile.
+ */
+ns_status ns_autotune_blend(const ns_curves* curves, const ns_gaussians* g, ns_raster_params* rp,
+                            const ns_capacity* cap, float* image, const float* dL_dimage,
+                            void* workspace, size_t workspace_bytes, int32_t repeats, void* stream);
 
 /*
  * Profiling aid.  The next launch of kernel `kernel_id` issued by the calling

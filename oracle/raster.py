@@ -175,8 +175,10 @@ def render_brute(g, color_t, n_scenes, H, W, C, r):
     return torch.stack(imgs)
 
 
-def render_tiled(g, color_t, n_scenes, H, W, C, r, return_flags=False):
-    """Per-tile lists from the FP32 bin rule, composited with Eq. 8 per pixel."""
+def render_tiled(g, color_t, n_scenes, H, W, C, r, return_flags=False, only_tiles=None, flag_rel=1e-4):
+    """Per-tile lists from the FP32 bin rule, composited with Eq. 8 per pixel.
+    `only_tiles` (global tile ids) restricts the work to those tiles; the
+    other pixels are left at 0."""
     T = int(r["tile"])
     tx = (W + T - 1) // T
     ty = (H + T - 1) // T
@@ -184,9 +186,12 @@ def render_tiled(g, color_t, n_scenes, H, W, C, r, return_flags=False):
     col = _colors(g, color_t, C)
     N = n_scenes * H * W
     vals, idxs, flags = [], [], []
+    wanted = None if only_tiles is None else set(int(x) for x in only_tiles)
     for s in range(n_scenes):
         for t in range(tx * ty):
             gt = s * tx * ty + t
+            if wanted is not None and gt not in wanted:
+                continue
             x0, y0 = (t % tx) * T, (t // tx) * T
             ys = torch.arange(y0, min(y0 + T, H))
             xs = torch.arange(x0, min(x0 + T, W))
@@ -199,7 +204,7 @@ def render_tiled(g, color_t, n_scenes, H, W, C, r, return_flags=False):
             vals.append(out)
             idxs.append(s * H * W + yy * W + xx)
             if return_flags:
-                flags.append(near_threshold(al, r["alpha_min"], r["t_min"]))
+                flags.append(near_threshold(al, r["alpha_min"], r["t_min"], flag_rel))
     idx = torch.cat(idxs)
     img = torch.zeros(N, C, dtype=DT).index_add(0, idx, torch.cat(vals)).reshape(n_scenes, H, W, C)
     if return_flags:

@@ -35,7 +35,7 @@ class NsSampleParams(C.Structure):
 
 class NsRasterParams(C.Structure):
     _fields_ = [("tile", C.c_int32), ("k_sigma", C.c_float), ("alpha_min", C.c_float), ("alpha_max", C.c_float),
-                ("t_min", C.c_float), ("bg", C.c_float * 3)]
+                ("t_min", C.c_float), ("bg", C.c_float * 3), ("ppt_fwd", C.c_int32), ("ppt_bwd", C.c_int32)]
 
 
 class NsCapacity(C.Structure):
@@ -75,6 +75,8 @@ SIGNATURES = {
     "ns_clear_status": (C.c_int, [_p, _p]),
     "ns_workspace_copy": (C.c_int, [_p, C.POINTER(NsCurves), C.POINTER(NsCapacity), C.POINTER(NsRasterParams),
                                     C.c_int32, _p, C.c_size_t, _p]),
+    "ns_autotune_blend": (C.c_int, [C.POINTER(NsCurves), C.POINTER(NsGaussians), C.POINTER(NsRasterParams),
+                                    C.POINTER(NsCapacity), _p, _p, _p, C.c_size_t, C.c_int32, _p]),
     "ns_profile_next_launch": (C.c_int, [C.c_int32, _p, _p]),
     "splat_forward_noalloc": (C.c_int, [C.POINTER(NsCurves), C.POINTER(NsGaussians), C.POINTER(NsRasterParams),
                                         _p, C.POINTER(NsReport), _p]),

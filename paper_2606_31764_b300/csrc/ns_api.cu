@@ -86,8 +86,8 @@ bool make_layout(const ns_curves* c, const ns_capacity* cap, const ns_raster_par
     set_error("capacities must lie in [0, 2^31)");
     return false;
   }
-  if (rp->tile != 16) {
-    set_error("tile must be 16");
+  if (rp->tile != 8 && rp->tile != 16 && rp->tile != 32) {
+    set_error("tile must be 8, 16 or 32");
     return false;
   }
   L->S = c->n_scenes;
@@ -220,6 +220,8 @@ ns_raster_params ns_default_raster_params(void) {
   r.alpha_max = 0.99f;
   r.t_min = 1e-4f;
   r.bg[0] = r.bg[1] = r.bg[2] = 1.f;
+  r.ppt_fwd = 0;
+  r.ppt_bwd = 0;
   return r;
 }
 

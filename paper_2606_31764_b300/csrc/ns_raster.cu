@@ -25,7 +25,6 @@
 
 namespace ns {
 
-constexpr int kTile = 16;
 
 __global__ void k_curve_scene(ns_curves cv, int* curve_scene) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -366,18 +365,20 @@ __global__ void k_ranges(const uint32_t* __restrict__ keys, const DevState* st, 
 // ---------------------------------------------------------------------------
 // compositing
 //
-// Thread layout: a 16x16 tile per block of 8 warps; warp w owns the 8x4
-// sub-block at ((w & 1) * 8, (w >> 1) * 4), lane l the pixel (l & 7, l >> 3)
-// inside it.  Each warp streams its tile's list on its own, 32 entries at a
+// Thread layout: one TILE x TILE tile per block.  A warp owns an 8-wide,
+// (4 PPT)-tall sub-block; lane l handles the PPT pixels (l & 7, (l >> 3) + 4k),
+// k < PPT.  Each warp streams its tile's list on its own, 32 entries at a
 // time, staged in the warp's slice of shared memory (no block barriers, so a
-// warp whose pixels are all done leaves at once).  Before the warp evaluates
-// a Gaussian it tests, one Gaussian per lane and a ballot, whether the
-// Gaussian can reach alpha_min anywhere in its 8x4 sub-block: alpha >=
-// alpha_min needs d^2 <= 2 sigma^2 ln(o / alpha_min); the test uses the
-// sub-block's nearest point with a margin of 1e-3 in the logarithm, so a
-// Gaussian it rejects would have been skipped by the alpha < alpha_min rule
-// at every pixel of the sub-block.  The result is the same as evaluating every
-// pair; only the work changes.  With alpha_min = 0 nothing is rejected.
+// warp whose pixels are all done leaves at once).  Before the warp evaluates a
+// Gaussian it tests, one Gaussian per lane and a ballot, whether the Gaussian
+// can reach alpha_min anywhere in its sub-block: alpha >= alpha_min needs
+// d^2 <= 2 sigma^2 ln(o / alpha_min); the test uses the sub-block's nearest
+// point with a margin of 1e-3 in the logarithm, so a Gaussian it rejects would
+// have been skipped by the alpha < alpha_min rule at every pixel of the
+// sub-block.  The result is the same as evaluating every pair; only the work
+// changes.  With alpha_min = 0 nothing is rejected.  TILE and PPT change only
+// the work decomposition, never the result: every pixel still walks its
+// tile's list in order.
 //
 // Per-Gaussian constants are prepared once by k_bin_count:
 //   prep  = {mu_x, mu_y, ncoef = -1/(2 sigma^2), o}
@@ -413,54 +414,73 @@ __device__ __forceinline__ void count_evals(unsigned long long* ctr, unsigned in
   if ((threadIdx.x & 31) == 0 && v) atomicAdd(ctr, (unsigned long long)v);
 }
 
-struct WarpRect {
-  float x0, x1, y0, y1;   // pixel-centre bounds of the warp's 8x4 sub-block
+template <int TILE, int PPT>
+struct BlendGeom {
+  static constexpr int kWarpsX = TILE / 8;
+  static constexpr int kWarpsY = TILE / (4 * PPT);
+  static constexpr int kWarps = kWarpsX * kWarpsY;
+  static constexpr int kThreads = 32 * kWarps;
+  static constexpr int kMinBlocks = 1024 / kThreads;   // 1024 resident threads: up to 64 registers each
+  // the adjoint with 4 pixels per thread keeps 4 x 8 floats of pixel state: allow 128 registers
+  static constexpr int kMinBlocksBwd = (PPT == 4 ? 512 : 1024) / kThreads > 0 ? (PPT == 4 ? 512 : 1024) / kThreads : 1;
+  static_assert(kWarpsY >= 1 && TILE % (4 * PPT) == 0, "sub-block taller than the tile");
 };
 
-__device__ __forceinline__ void tile_pixel(const BlendParams& bp, int& s, int& px, int& py, WarpRect& wr) {
+// Scene, pixel column and first row of this lane, and the warp's rectangle.
+template <int TILE, int PPT>
+__device__ __forceinline__ void tile_pixels(const BlendParams& bp, int& s, int& px, int& py0, float4& rect) {
+  using Gm = BlendGeom<TILE, PPT>;
   const int tile = blockIdx.x;
   s = tile / bp.tiles_per_scene;
   const int t = tile - s * bp.tiles_per_scene;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int bx = (t % bp.tiles_x) * kTile + (w & 1) * 8;
-  const int by = (t / bp.tiles_x) * kTile + (w >> 1) * 4;
+  const int bx = (t % bp.tiles_x) * TILE + (w % Gm::kWarpsX) * 8;
+  const int by = (t / bp.tiles_x) * TILE + (w / Gm::kWarpsX) * 4 * PPT;
   px = bx + (lane & 7);
-  py = by + (lane >> 3);
-  wr.x0 = bx + 0.5f;
-  wr.x1 = bx + 7.5f;
-  wr.y0 = by + 0.5f;
-  wr.y1 = by + 3.5f;
+  py0 = by + (lane >> 3);
+  rect = make_float4(bx + 0.5f, bx + 7.5f, by + 0.5f, by + 4.f * PPT - 0.5f);
 }
 
-template <int C>
-__global__ void __launch_bounds__(256, 4) k_blend_fwd(const int2* __restrict__ ranges, const uint32_t* __restrict__ gid,
-                                                   const float4* __restrict__ prep, const float2* __restrict__ reach,
-                                                   const int* __restrict__ gcurve, const float4* __restrict__ color,
-                                                   BlendParams bp, float* image, float* Tfinal, int* nlast,
-                                                   DevState* st) {
-  __shared__ float4 s_q[8][32];
-  __shared__ float4 s_c[8][32];
-  int s, px, py;
-  WarpRect wr;
-  tile_pixel(bp, s, px, py, wr);
+template <int TILE, int PPT, int C>
+__global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE, PPT>::kMinBlocks)
+    k_blend_fwd(const int2* __restrict__ ranges, const uint32_t* __restrict__ gid, const float4* __restrict__ prep,
+                const float2* __restrict__ reach, const int* __restrict__ gcurve, const float4* __restrict__ color,
+                BlendParams bp, float* image, float* Tfinal, int* nlast, DevState* st) {
+  using Gm = BlendGeom<TILE, PPT>;
+  __shared__ float4 s_q[Gm::kWarps][32];
+  __shared__ float4 s_c[Gm::kWarps][32];
+  int s, px, py0;
+  float4 wr;
+  tile_pixels<TILE, PPT>(bp, s, px, py0, wr);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bool inside = px < bp.W && py < bp.H;
-  const float fx = px + 0.5f, fy = py + 0.5f;
+  const float fx = px + 0.5f;
   const int2 rg = ranges[blockIdx.x];
   const int n = rg.y - rg.x;
-  float T = 1.f, acc[C];
+  float T[PPT], acc[PPT][C];
+  bool done[PPT];
+  int last[PPT];
 #pragma unroll
-  for (int ch = 0; ch < C; ++ch) acc[ch] = 0.f;
-  bool done = !inside;
-  int last = 0;
+  for (int k = 0; k < PPT; ++k) {
+    T[k] = 1.f;
+    done[k] = !(px < bp.W && py0 + 4 * k < bp.H);
+    last[k] = 0;
+#pragma unroll
+    for (int ch = 0; ch < C; ++ch) acc[k][ch] = 0.f;
+  }
+  auto all_done = [&]() {
+    bool d = true;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) d = d && done[k];
+    return d;
+  };
   unsigned int evals = 0, contribs = 0;
-  for (int base = 0; base < n && !__all_sync(0xffffffffu, done); base += 32) {
+  for (int base = 0; base < n && !__all_sync(0xffffffffu, all_done()); base += 32) {
     const int j = base + lane;
     bool hit = false;
     if (j < n) {
       const uint32_t g = gid[rg.x + j];
       const float4 q = prep[g];
-      hit = rect_d2(q.x, q.y, wr.x0, wr.x1, wr.y0, wr.y1) <= reach[g].x;
+      hit = rect_d2(q.x, q.y, wr.x, wr.y, wr.z, wr.w) <= reach[g].x;
       if (hit) {
         s_q[w][lane] = q;
         s_c[w][lane] = color[gcurve[g]];
@@ -471,41 +491,49 @@ __global__ void __launch_bounds__(256, 4) k_blend_fwd(const int2* __restrict__ r
     while (mask) {
       const int b = __ffs(mask) - 1;
       mask &= mask - 1;
-      if (done) continue;
-      ++evals;
-      float dx, dy, d2, e;
-      const float a = gauss_alpha(fx, fy, s_q[w][b], bp.alpha_max, dx, dy, d2, e);
-      if (a < bp.alpha_min) continue;
-      const float test = T * (1.f - a);
-      if (test < bp.t_min) {
-        done = true;
-        continue;
+      const float4 q = s_q[w][b];
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        if (done[k]) continue;
+        ++evals;
+        float dx, dy, d2, e;
+        const float a = gauss_alpha(fx, py0 + 4 * k + 0.5f, q, bp.alpha_max, dx, dy, d2, e);
+        if (a < bp.alpha_min) continue;
+        const float test = T[k] * (1.f - a);
+        if (test < bp.t_min) {
+          done[k] = true;
+          continue;
+        }
+        const float wgt = a * T[k];
+        const float4 cc = s_c[w][b];
+        acc[k][0] = fmaf(cc.x, wgt, acc[k][0]);
+        if (C == 3) {
+          acc[k][1] = fmaf(cc.y, wgt, acc[k][1]);
+          acc[k][2] = fmaf(cc.z, wgt, acc[k][2]);
+        }
+        T[k] = test;
+        last[k] = base + b + 1;
+        ++contribs;
       }
-      const float wgt = a * T;
-      const float4 cc = s_c[w][b];
-      acc[0] = fmaf(cc.x, wgt, acc[0]);
-      if (C == 3) {
-        acc[1] = fmaf(cc.y, wgt, acc[1]);
-        acc[2] = fmaf(cc.z, wgt, acc[2]);
-      }
-      T = test;
-      last = base + b + 1;
-      ++contribs;
     }
     __syncwarp();
   }
   count_evals(&st->blend_evals, evals);
   count_evals(&st->blend_contribs, contribs);
-  if (inside) {
-    const long long pix = ((long long)s * bp.H + py) * bp.W + px;
-    float* out = image + pix * C;
-    out[0] = acc[0] + T * bp.bg0;
-    if (C == 3) {
-      out[1] = acc[1] + T * bp.bg1;
-      out[2] = acc[2] + T * bp.bg2;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    const int py = py0 + 4 * k;
+    if (px < bp.W && py < bp.H) {
+      const long long pix = ((long long)s * bp.H + py) * bp.W + px;
+      float* out = image + pix * C;
+      out[0] = acc[k][0] + T[k] * bp.bg0;
+      if (C == 3) {
+        out[1] = acc[k][1] + T[k] * bp.bg1;
+        out[2] = acc[k][2] + T[k] * bp.bg2;
+      }
+      Tfinal[pix] = T[k];
+      nlast[pix] = last[k];
     }
-    Tfinal[pix] = T;
-    nlast[pix] = last;
   }
 }
 
@@ -514,34 +542,44 @@ __device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, 
                : "memory");
 }
 
-template <int C>
-__global__ void __launch_bounds__(256, 4) k_blend_bwd(const int2* __restrict__ ranges, const uint32_t* __restrict__ gid,
-                                                   const float4* __restrict__ prep, const float2* __restrict__ reach,
-                                                   const int* __restrict__ gcurve, const float4* __restrict__ color,
-                                                   BlendParams bp, const float* __restrict__ dimage,
-                                                   const float* __restrict__ Tfinal, const int* __restrict__ nlast,
-                                                   float* dgauss, DevState* st) {
-  __shared__ float4 s_q[8][32];
-  __shared__ float4 s_c[8][32];
-  __shared__ float s_isig[8][32];
-  __shared__ uint32_t s_id[8][32];
-  int s, px, py;
-  WarpRect wr;
-  tile_pixel(bp, s, px, py, wr);
+template <int TILE, int PPT, int C>
+__global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE, PPT>::kMinBlocksBwd)
+    k_blend_bwd(const int2* __restrict__ ranges, const uint32_t* __restrict__ gid, const float4* __restrict__ prep,
+                const float2* __restrict__ reach, const int* __restrict__ gcurve, const float4* __restrict__ color,
+                BlendParams bp, const float* __restrict__ dimage, const float* __restrict__ Tfinal,
+                const int* __restrict__ nlast, float* dgauss, DevState* st) {
+  using Gm = BlendGeom<TILE, PPT>;
+  __shared__ float4 s_q[Gm::kWarps][32];
+  __shared__ float4 s_c[Gm::kWarps][32];
+  __shared__ float s_isig[Gm::kWarps][32];
+  __shared__ uint32_t s_id[Gm::kWarps][32];
+  int s, px, py0;
+  float4 wr;
+  tile_pixels<TILE, PPT>(bp, s, px, py0, wr);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bool inside = px < bp.W && py < bp.H;
-  const float fx = px + 0.5f, fy = py + 0.5f;
+  const float fx = px + 0.5f;
   const int2 rg = ranges[blockIdx.x];
-  const long long pix = ((long long)s * bp.H + py) * bp.W + px;
-  float T = 1.f, dI[3] = {0.f, 0.f, 0.f}, Bk[3] = {bp.bg0, bp.bg1, bp.bg2};
-  int last = 0;
-  if (inside) {
-    T = Tfinal[pix];
-    last = nlast[pix];
+  float T[PPT], dI[PPT][3], Bk[PPT][3];
+  int last[PPT];
+  int wmax = 0;
 #pragma unroll
-    for (int ch = 0; ch < C; ++ch) dI[ch] = dimage[pix * C + ch];
+  for (int k = 0; k < PPT; ++k) {
+    const int py = py0 + 4 * k;
+    T[k] = 1.f;
+    last[k] = 0;
+    Bk[k][0] = bp.bg0;
+    Bk[k][1] = bp.bg1;
+    Bk[k][2] = bp.bg2;
+    dI[k][0] = dI[k][1] = dI[k][2] = 0.f;
+    if (px < bp.W && py < bp.H) {
+      const long long pix = ((long long)s * bp.H + py) * bp.W + px;
+      T[k] = Tfinal[pix];
+      last[k] = nlast[pix];
+#pragma unroll
+      for (int ch = 0; ch < C; ++ch) dI[k][ch] = dimage[pix * C + ch];
+    }
+    wmax = max(wmax, last[k]);
   }
-  int wmax = last;
   for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
   unsigned int evals = 0;
   for (int base = ((wmax - 1) >> 5) << 5; base >= 0 && wmax > 0; base -= 32) {
@@ -551,7 +589,7 @@ __global__ void __launch_bounds__(256, 4) k_blend_bwd(const int2* __restrict__ r
       const uint32_t g = gid[rg.x + j];
       const float4 q = prep[g];
       const float2 rs = reach[g];
-      hit = rect_d2(q.x, q.y, wr.x0, wr.x1, wr.y0, wr.y1) <= rs.x;
+      hit = rect_d2(q.x, q.y, wr.x, wr.y, wr.z, wr.w) <= rs.x;
       if (hit) {
         s_q[w][lane] = q;
         s_c[w][lane] = color[gcurve[g]];
@@ -564,37 +602,38 @@ __global__ void __launch_bounds__(256, 4) k_blend_bwd(const int2* __restrict__ r
     while (mask) {
       const int b = 31 - __clz(mask);
       mask &= ~(1u << b);
+      const float4 q = s_q[w][b];
       float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       bool contrib = false;
-      if (base + b < last) {
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        if (base + b >= last[k]) continue;
         ++evals;
-        const float4 q = s_q[w][b];
         float dx, dy, d2, e;
-        const float a = gauss_alpha(fx, fy, q, bp.alpha_max, dx, dy, d2, e);
-        if (a >= bp.alpha_min) {
-          contrib = true;
-          T = __fdividef(T, 1.f - a);   // transmittance in front of this Gaussian
-          const float wgt = a * T;
-          const float4 cc = s_c[w][b];
-          float da = (cc.x - Bk[0]) * dI[0];
-          v[4] = wgt * dI[0];
-          Bk[0] = a * cc.x + (1.f - a) * Bk[0];
-          if (C == 3) {
-            da += (cc.y - Bk[1]) * dI[1] + (cc.z - Bk[2]) * dI[2];
-            v[5] = wgt * dI[1];
-            v[6] = wgt * dI[2];
-            Bk[1] = a * cc.y + (1.f - a) * Bk[1];
-            Bk[2] = a * cc.z + (1.f - a) * Bk[2];
-          }
-          da *= T;
-          if (__fmul_rn(q.w, e) < bp.alpha_max) {
-            const float isg = s_isig[w][b];
-            v[3] = e * da;
-            const float aa = da * a * isg * isg;   // dalpha/dmu = alpha (x - mu) / sigma^2
-            v[0] = aa * dx;
-            v[1] = aa * dy;
-            v[2] = aa * d2 * isg;                  // dalpha/dsigma = alpha d^2 / sigma^3
-          }
+        const float a = gauss_alpha(fx, py0 + 4 * k + 0.5f, q, bp.alpha_max, dx, dy, d2, e);
+        if (a < bp.alpha_min) continue;
+        contrib = true;
+        T[k] = __fdividef(T[k], 1.f - a);   // transmittance in front of this Gaussian
+        const float wgt = a * T[k];
+        const float4 cc = s_c[w][b];
+        float da = (cc.x - Bk[k][0]) * dI[k][0];
+        v[4] += wgt * dI[k][0];
+        Bk[k][0] = a * cc.x + (1.f - a) * Bk[k][0];
+        if (C == 3) {
+          da += (cc.y - Bk[k][1]) * dI[k][1] + (cc.z - Bk[k][2]) * dI[k][2];
+          v[5] += wgt * dI[k][1];
+          v[6] += wgt * dI[k][2];
+          Bk[k][1] = a * cc.y + (1.f - a) * Bk[k][1];
+          Bk[k][2] = a * cc.z + (1.f - a) * Bk[k][2];
+        }
+        da *= T[k];
+        if (__fmul_rn(q.w, e) < bp.alpha_max) {
+          const float isg = s_isig[w][b];
+          v[3] += e * da;
+          const float aa = da * a * isg * isg;   // dalpha/dmu = alpha (x - mu) / sigma^2
+          v[0] += aa * dx;
+          v[1] += aa * dy;
+          v[2] += aa * d2 * isg;                  // dalpha/dsigma = alpha d^2 / sigma^3
         }
       }
       if (__any_sync(0xffffffffu, contrib)) {
@@ -613,6 +652,40 @@ __global__ void __launch_bounds__(256, 4) k_blend_bwd(const int2* __restrict__ r
     __syncwarp();
   }
   count_evals(&st->blend_bwd_evals, evals);
+}
+
+// (TILE, PPT) -> launch.  Valid: TILE 8 with PPT 1-2, TILE 16 and 32 with PPT 1-4.
+template <int C>
+static void launch_fwd(int tile, int ppt, int grid, cudaStream_t s, const int2* ranges, const uint32_t* gid,
+                       const float4* prep, const float2* reach, const int* gcurve, const float4* col,
+                       const BlendParams& bp, float* image, float* Tf, int* nl, DevState* st) {
+#define NS_FWD(TL, PP)                                                                                 \
+  {                                                                                                      \
+    auto kern = &k_blend_fwd<TL, PP, C>;                                                                 \
+    NS_LAUNCH(NS_KERNEL_BLEND_FWD, kern, grid, (BlendGeom<TL, PP>::kThreads), 0, s, ranges, gid, prep,  \
+              reach, gcurve, col, bp, image, Tf, nl, st);                                               \
+  }
+  if (tile == 8) { if (ppt == 1) NS_FWD(8, 1) else NS_FWD(8, 2) }
+  else if (tile == 16) { if (ppt == 1) NS_FWD(16, 1) else if (ppt == 2) NS_FWD(16, 2) else NS_FWD(16, 4) }
+  else { if (ppt == 1) NS_FWD(32, 1) else if (ppt == 2) NS_FWD(32, 2) else NS_FWD(32, 4) }
+#undef NS_FWD
+}
+
+template <int C>
+static void launch_bwd(int tile, int ppt, int grid, cudaStream_t s, const int2* ranges, const uint32_t* gid,
+                       const float4* prep, const float2* reach, const int* gcurve, const float4* col,
+                       const BlendParams& bp, const float* dimage, const float* Tf, const int* nl, float* dgauss,
+                       DevState* st) {
+#define NS_BWD(TL, PP)                                                                                 \
+  {                                                                                                      \
+    auto kern = &k_blend_bwd<TL, PP, C>;                                                                 \
+    NS_LAUNCH(NS_KERNEL_BLEND_BWD, kern, grid, (BlendGeom<TL, PP>::kThreads), 0, s, ranges, gid, prep,  \
+              reach, gcurve, col, bp, dimage, Tf, nl, dgauss, st);                                      \
+  }
+  if (tile == 8) { if (ppt == 1) NS_BWD(8, 1) else NS_BWD(8, 2) }
+  else if (tile == 16) { if (ppt == 1) NS_BWD(16, 1) else if (ppt == 2) NS_BWD(16, 2) else NS_BWD(16, 4) }
+  else { if (ppt == 1) NS_BWD(32, 1) else if (ppt == 2) NS_BWD(32, 2) else NS_BWD(32, 4) }
+#undef NS_BWD
 }
 
 // ---------------------------------------------------------------------------
@@ -645,10 +718,22 @@ static BlendParams blend_params(const Layout& L, const ns_raster_params* rp) {
   return bp;
 }
 
+static int resolve_ppt(int tile, int ppt) {
+  if (ppt == 0) return tile == 8 ? 1 : 2;   // library default
+  return ppt;
+}
+
+static bool ppt_ok(int tile, int ppt) { return ppt == 1 || ppt == 2 || (ppt == 4 && tile >= 16); }
+
 static bool check_raster(const ns_raster_params* rp) {
-  if (!rp || rp->tile != kTile || !(rp->k_sigma > 0.f) || !(rp->alpha_max > 0.f) || !(rp->alpha_max < 1.f) ||
-      !(rp->alpha_min >= 0.f) || !(rp->t_min >= 0.f) || !(rp->t_min < 1.f)) {
-    set_error("invalid raster parameters (tile must be 16, 0 < alpha_max < 1, k_sigma > 0)");
+  if (!rp || (rp->tile != 8 && rp->tile != 16 && rp->tile != 32) || !(rp->k_sigma > 0.f) ||
+      !(rp->alpha_max > 0.f) || !(rp->alpha_max < 1.f) || !(rp->alpha_min >= 0.f) || !(rp->t_min >= 0.f) ||
+      !(rp->t_min < 1.f)) {
+    set_error("invalid raster parameters (tile 8, 16 or 32; 0 < alpha_max < 1; k_sigma > 0)");
+    return false;
+  }
+  if (!ppt_ok(rp->tile, resolve_ppt(rp->tile, rp->ppt_fwd)) || !ppt_ok(rp->tile, resolve_ppt(rp->tile, rp->ppt_bwd))) {
+    set_error("invalid pixels per thread (1, 2, or 4 with tiles of 16 and 32; 0 = default)");
     return false;
   }
   return true;
@@ -696,7 +781,7 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
     NS_LAUNCH(NS_KERNEL_OTHER, k_curve_scene, (curves->n_curves + 255) / 256, 256, 0, s, *curves, curve_scene);
   BinParams bp;
   bp.k_sigma = rp->k_sigma;
-  bp.inv_tile = 1.f / float(kTile);
+  bp.inv_tile = 1.f / float(rp->tile);
   bp.alpha_min = rp->alpha_min;
   bp.log_amin = rp->alpha_min > 0.f ? logf(rp->alpha_min) : -INFINITY;
   bp.tiles_x = L.tiles_x;
@@ -731,12 +816,13 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
   NS_LAUNCH(NS_KERNEL_RANGES, k_ranges, num_sms() * 4, 256, 0, s, kin, st, ranges);
   const BlendParams blp = blend_params(L, rp);
   const float4* col = reinterpret_cast<const float4*>(curves->color);
+  const int ppt = resolve_ppt(rp->tile, rp->ppt_fwd);
   if (L.C == 3)
-    NS_LAUNCH(NS_KERNEL_BLEND_FWD, k_blend_fwd<3>, L.n_tiles, 256, 0, s, ranges, vin, at<float4>(ws, L.o_prep),
-              at<float2>(ws, L.o_reach), g->curve, col, blp, image, Tf, nl, st);
+    launch_fwd<3>(rp->tile, ppt, L.n_tiles, s, ranges, vin, at<float4>(ws, L.o_prep), at<float2>(ws, L.o_reach),
+                  g->curve, col, blp, image, Tf, nl, st);
   else
-    NS_LAUNCH(NS_KERNEL_BLEND_FWD, k_blend_fwd<1>, L.n_tiles, 256, 0, s, ranges, vin, at<float4>(ws, L.o_prep),
-              at<float2>(ws, L.o_reach), g->curve, col, blp, image, Tf, nl, st);
+    launch_fwd<1>(rp->tile, ppt, L.n_tiles, s, ranges, vin, at<float4>(ws, L.o_prep), at<float2>(ws, L.o_reach),
+                  g->curve, col, blp, image, Tf, nl, st);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_error(std::string("splat_forward: ") + cudaGetErrorString(e));
@@ -760,13 +846,93 @@ ns_status launch_blend_bwd(const Layout& L, const ns_curves* curves, const ns_ga
   
   DevState* st = at<DevState>(ws, L.o_state);
   cudaMemsetAsync(&st->blend_bwd_evals, 0, sizeof(unsigned long long), s);
+  const int ppt = resolve_ppt(rp->tile, rp->ppt_bwd);
   if (L.C == 3)
-    NS_LAUNCH(NS_KERNEL_BLEND_BWD, k_blend_bwd<3>, L.n_tiles, 256, 0, s, ranges, vsorted, at<float4>(ws, L.o_prep),
-              at<float2>(ws, L.o_reach), g->curve, col, blp, dimage, Tf, nl, dgauss, st);
+    launch_bwd<3>(rp->tile, ppt, L.n_tiles, s, ranges, vsorted, at<float4>(ws, L.o_prep), at<float2>(ws, L.o_reach),
+                  g->curve, col, blp, dimage, Tf, nl, dgauss, st);
   else
-    NS_LAUNCH(NS_KERNEL_BLEND_BWD, k_blend_bwd<1>, L.n_tiles, 256, 0, s, ranges, vsorted, at<float4>(ws, L.o_prep),
-              at<float2>(ws, L.o_reach), g->curve, col, blp, dimage, Tf, nl, dgauss, st);
+    launch_bwd<1>(rp->tile, ppt, L.n_tiles, s, ranges, vsorted, at<float4>(ws, L.o_prep), at<float2>(ws, L.o_reach),
+                  g->curve, col, blp, dimage, Tf, nl, dgauss, st);
   return NS_OK;
 }
 bool raster_params_ok(const ns_raster_params* rp) { return check_raster(rp); }
 }  // namespace ns
+
+extern "C" ns_status ns_autotune_blend(const ns_curves* curves, const ns_gaussians* g, ns_raster_params* rp,
+                                       const ns_capacity* cap, float* image, const float* dL_dimage, void* ws,
+                                       size_t ws_bytes, int32_t repeats, void* stream) {
+  Layout L;
+  if (!curves || !g || !rp || !cap || !image || !ws || repeats < 1) {
+    set_error("ns_autotune_blend: null argument or repeats < 1");
+    return NS_ERR_INVALID_ARG;
+  }
+  if (!check_raster(rp) || !make_layout(curves, cap, rp, &L)) return NS_ERR_INVALID_ARG;
+  if (ws_bytes < L.total) {
+    set_error("ns_autotune_blend: workspace smaller than the layout");
+    return NS_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DevState* st = at<DevState>(ws, L.o_state);
+  const RasterPlan rpn = radix_plan(L.n_tiles);
+  const uint32_t* vsorted = (rpn.passes & 1) ? at<uint32_t>(ws, L.o_v1) : at<uint32_t>(ws, L.o_v0);
+  const int2* ranges = at<int2>(ws, L.o_ranges);
+  float* Tf = at<float>(ws, L.o_T);
+  int* nl = at<int>(ws, L.o_nlast);
+  float* dg = at<float>(ws, L.o_dgauss);
+  const float4* prep = at<float4>(ws, L.o_prep);
+  const float2* reach = at<float2>(ws, L.o_reach);
+  const BlendParams blp = blend_params(L, rp);
+  const float4* col = reinterpret_cast<const float4*>(curves->color);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    set_error("ns_autotune_blend: cudaEventCreate failed");
+    return NS_ERR_CUDA;
+  }
+  auto fwd = [&](int ppt) {
+    if (L.C == 3) launch_fwd<3>(rp->tile, ppt, L.n_tiles, s, ranges, vsorted, prep, reach, g->curve, col, blp, image, Tf, nl, st);
+    else launch_fwd<1>(rp->tile, ppt, L.n_tiles, s, ranges, vsorted, prep, reach, g->curve, col, blp, image, Tf, nl, st);
+  };
+  auto bwd = [&](int ppt) {
+    if (L.C == 3) launch_bwd<3>(rp->tile, ppt, L.n_tiles, s, ranges, vsorted, prep, reach, g->curve, col, blp, dL_dimage, Tf, nl, dg, st);
+    else launch_bwd<1>(rp->tile, ppt, L.n_tiles, s, ranges, vsorted, prep, reach, g->curve, col, blp, dL_dimage, Tf, nl, dg, st);
+  };
+  auto time_best = [&](bool backward) {
+    int best = 0;
+    float best_ms = 3.4e38f;
+    for (int ppt : {1, 2, 4}) {
+      if (!ppt_ok(rp->tile, ppt)) continue;
+      float t = 3.4e38f;
+      for (int r = 0; r < repeats + 1; ++r) {   // the first run warms the variant up
+        if (backward) cudaMemsetAsync(dg, 0, sizeof(float) * 8 * (size_t)L.gcap, s);
+        cudaEventRecord(e0, s);
+        if (backward) bwd(ppt); else fwd(ppt);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0 && ms < t) t = ms;
+      }
+      if (t < best_ms) {
+        best_ms = t;
+        best = ppt;
+      }
+    }
+    return best;
+  };
+  const int bf = time_best(false);
+  const int bb = dL_dimage ? time_best(true) : resolve_ppt(rp->tile, rp->ppt_bwd);
+  rp->ppt_fwd = bf;
+  rp->ppt_bwd = bb;
+  // leave the workspace as the chosen forward leaves it (the results of all
+  // variants are identical) and the counters as one forward pass sets them
+  cudaMemsetAsync(&st->blend_evals, 0, 3 * sizeof(unsigned long long), s);
+  fwd(bf);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+    set_error(std::string("ns_autotune_blend: ") + cudaGetErrorString(e));
+    return NS_ERR_CUDA;
+  }
+  return NS_OK;
+}

@@ -41,6 +41,8 @@ def raster_params(d: dict) -> B.NsRasterParams:
     r.t_min = float(d["t_min"])
     for i in range(3):
         r.bg[i] = float(d["bg"][i])
+    r.ppt_fwd = int(d.get("ppt_fwd", 0))
+    r.ppt_bwd = int(d.get("ppt_bwd", 0))
     return r
 
 
@@ -172,6 +174,15 @@ class Splatter:
     def mse(self, image, target, dimage, loss):
         B.call("ns_mse_loss", _ptr(image), _ptr(target), C.c_int64(image.numel()), _ptr(dimage), _ptr(loss),
                _stream())
+
+    def autotune_blend(self, key, tau, color, dimage=None, repeats=3):
+        """Let the library time the blend decompositions on this batch and keep
+        the fastest (ns_autotune_blend).  Needs a completed forward; synchronises."""
+        cs = self.dev.struct(key, tau, color)
+        B.call("ns_autotune_blend", C.byref(cs), C.byref(self.g), C.byref(self.rp), C.byref(self.cap),
+               _ptr(self.image), _ptr(dimage) if dimage is not None else None, _ptr(self.ws),
+               C.c_size_t(self.ws_bytes), C.c_int32(repeats), _stream())
+        return int(self.rp.ppt_fwd), int(self.rp.ppt_bwd)
 
     # -- sizing ---------------------------------------------------------
     def fit(self, key, tau, color, headroom=1.25, max_rounds=4):

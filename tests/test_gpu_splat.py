@@ -125,3 +125,47 @@ def test_adam_step_matches_oracle():
         torch.cuda.synchronize()
         assert np.abs(tp.cpu().numpy() - pp).max() <= 1e-6
         assert np.abs(tm.cpu().numpy() - m).max() <= 1e-6
+
+
+VARIANTS = [(8, 1, 1), (8, 2, 2), (16, 1, 4), (16, 4, 1), (32, 2, 2), (32, 4, 4), (32, 1, 1)]
+
+
+@pytest.mark.parametrize("tile,pf,pb", VARIANTS, ids=[f"t{t}-f{a}-b{b}" for t, a, b in VARIANTS])
+def test_tile_and_pixels_per_thread_variants(tile, pf, pb):
+    """Every tile size and blend decomposition: bins bit-exact, image 1e-5,
+    adjoint within 1e-3 (the decomposition must not change any result)."""
+    sc = scenes.small_closed(81, n_curves=3, size=70, filled=True, h=2.0, height=53)
+    sc = sc.with_raster(tile=tile, ppt_fwd=pf, ppt_bwd=pb)
+    g = op.gaussians_fp32(sc)
+    sp, img, rep, (k, t, c) = run_records(sc, g["rec"], g["curve"])
+    assert rep.status == 0
+    tid_o, gid_o, ranges_o = op.pairs_records(sc, g["rec"], g["curve"])
+    tid, gid = sorted_pairs(sp, (k, t, c), rep.pairs)
+    np.testing.assert_array_equal(tid, tid_o)
+    np.testing.assert_array_equal(gid, gid_o)
+    ref = op.render_records(sc, g["rec"], g["curve"])
+    assert np.abs(img.cpu().numpy() - ref).max() <= 1e-5
+    rng = np.random.default_rng(3)
+    dimg = rng.standard_normal(img.shape).astype(np.float32)
+    sp.backward(k, t, c, torch.as_tensor(dimg, device="cuda"), chain=False)
+    G = g["rec"].shape[0]
+    dg = sp.dgauss[:G].cpu().numpy().astype(np.float64)
+    drec, _ = op.record_grads(sc, g["rec"], g["curve"], dimg)
+    for j in range(4):
+        ref_j = drec[:, j]
+        assert np.linalg.norm(dg[:, j] - ref_j) <= 1e-3 * np.linalg.norm(ref_j) + 1e-7
+
+
+def test_autotune_keeps_the_image():
+    from paper_2606_31764_b300.splat import Splatter, scene_tensors
+    sc = scenes.small_closed(82, n_curves=4, size=96, filled=True, h=1.0).with_raster(**scenes.RASTER_DEFAULTS)
+    sp = Splatter(sc)
+    k, t, c = scene_tensors(sc)
+    sp.fit(k, t, c)
+    before = sp.forward(k, t, c).clone()
+    dimg = torch.ones_like(before)
+    pf, pb = sp.autotune_blend(k, t, c, dimg, repeats=2)
+    assert pf in (1, 2, 4) and pb in (1, 2, 4)
+    assert torch.equal(sp.image, before)
+    after = sp.forward(k, t, c)
+    assert torch.equal(after, before)

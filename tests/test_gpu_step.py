@@ -54,3 +54,14 @@ def test_step_matches_oracle(name, make):
     assert _rel_ok(out["dtau"], ref["dtau"]), "dtau"
     for j, nm in enumerate("xysw"):
         assert _rel_ok(out["dkey"][:, j], ref["dkey"][:, j]), "dkey." + nm
+
+
+@pytest.mark.parametrize("tile", [8, 32])
+def test_step_other_tile_sizes(tile):
+    sc = scenes.small_closed(56, n_curves=3, size=48, filled=True, h=2.0).with_raster(tile=tile)
+    ref = op.loss_and_grads(sc)
+    out = run_step(sc)
+    assert out["report"].status == 0
+    assert _rel_ok(out["dcolor"], ref["dcolor"]) and _rel_ok(out["dtau"], ref["dtau"])
+    for j in range(4):
+        assert _rel_ok(out["dkey"][:, j], ref["dkey"][:, j])
