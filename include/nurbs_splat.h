@@ -161,7 +161,9 @@ ns_raster_params ns_default_raster_params(void);
  * step: it carries the per-curve plan (knot vectors, counts, offsets, boundary
  * polylines), the sorted tile lists and the per-pixel state that the backward
  * pass reuses.  The caller allocates it (256-byte aligned); its contents need
- * no initialisation.  Returns 0 for invalid sizes (see ns_last_error).
+ * no initialisation.  The part nurbs_sample uses comes first and does not
+ * depend on the raster settings, so size the workspace with the raster
+ * settings of the splat calls.  Returns 0 for invalid sizes (see ns_last_error).
  */
 size_t ns_workspace_size(const ns_curves* curves, const ns_capacity* cap,
                          const ns_raster_params* raster);

@@ -449,7 +449,7 @@ extern "C" ns_status nurbs_sample(const ns_curves* curves, const ns_sample_param
   }
   ns_raster_params rp = ns_default_raster_params();
   if (!make_layout(curves, cap, &rp, &L)) return NS_ERR_INVALID_ARG;
-  if (ws_bytes < L.total) {
+  if (ws_bytes < L.sample_total) {
     set_error("nurbs_sample: workspace too small");
     return NS_ERR_INVALID_ARG;
   }
