@@ -118,7 +118,9 @@ typedef struct {
   float* rec;       /* device [capacity*4]: {mu_x, mu_y, sigma, opacity} */
   int32_t* curve;   /* device [capacity]: owning curve (selects colour and scene) */
   int32_t* aux;     /* device [capacity]: fills: nearest boundary segment i*, as
-                       i* (inside) or ~i* (outside); contours: -1 */
+                       i* (inside) or ~i* (outside), or 0x7fffffff for a point so
+                       deep inside that its sigmoid (Eq. 7) is exactly 1 in FP32
+                       (no segment needed); contours: -1 */
   int32_t* count;   /* device scalar: records in use */
 } ns_gaussians;
 

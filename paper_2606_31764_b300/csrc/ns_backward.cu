@@ -198,9 +198,11 @@ __global__ void __launch_bounds__(256) k_chain(ns_curves cv, ChainParams cp, con
       for (int k = threadIdx.x; k < B; k += blockDim.x) s_db[k] = make_float2(0.f, 0.f);
     __syncthreads();
     float dO = 0.f;
-    if (valid && g0.w != 0.f) {   // no opacity gradient: nothing reaches the curve but its colour
+    const int aux = valid ? gaux[g] : 0;
+    if (valid && g0.w != 0.f && aux == kAuxDeep) {
+      dO = g0.w;   // sigmoid exactly 1: the opacity gradient passes through, none reaches the boundary
+    } else if (valid && g0.w != 0.f) {   // no opacity gradient: nothing reaches the curve but its colour
       const float o = cv.color[4 * c + 3];
-      const int aux = gaux[g];
       const bool inside = aux >= 0;
       const int i0 = inside ? aux : ~aux;
       const int i1 = i0 + 1 == B ? 0 : i0 + 1;

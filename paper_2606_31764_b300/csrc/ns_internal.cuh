@@ -20,6 +20,10 @@ constexpr int kKnotPad = 2 * kMaxP + 1;  // knots per curve = intervals + 2p + 1
 
 enum CurveKind : int { kNone = 0, kOpen = 1, kClosedStroke = 2, kFill = 3 };
 
+// aux code of a fill Gaussian whose grid point lies so deep inside that its
+// sigmoid is exactly 1 in FP32: no nearest segment is recorded (none is needed)
+constexpr int kAuxDeep = 0x7fffffff;
+
 // Device-side status and counters, at the start of the workspace.
 struct DevState {
   int status;          // ns_status, first error wins

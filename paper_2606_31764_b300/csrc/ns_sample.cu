@@ -314,6 +314,40 @@ __device__ void emit_contour(const ns_curves& cv, const CurveRef& cr, const floa
   rec = make_float4(e.C[0], e.C[1], e.C[2] / sp.rho, o);
 }
 
+// Nearest segment of one cluster (strict <: the first minimum wins).
+__device__ __forceinline__ void cluster_nearest(const float4* seg, const float2* segb, int cl, int nseg, int base,
+                                                float qx, float qy, float& best, int& arg) {
+  const int k1 = min(nseg, (cl + 1) * kCluster);
+  for (int k = cl * kCluster; k < k1; ++k) {
+    const float4 sg = seg[k];
+    const float rx = qx - sg.x, ry = qy - sg.y;
+    const float t = fminf(fmaxf((rx * sg.z + ry * sg.w) * segb[k].y, 0.f), 1.f);
+    const float dx = rx - t * sg.z, dy = ry - t * sg.w;
+    const float d2 = dx * dx + dy * dy;
+    if (d2 < best) { best = d2; arg = base + k; }
+  }
+}
+
+// Signed crossings of the ray from q to +x by one cluster's segments: the
+// winding number of Eq. S2, exact off the polyline.
+__device__ __forceinline__ int cluster_crossings(const float4* seg, const float2* segb, int cl, int nseg, float qx,
+                                                 float qy) {
+  int wn = 0;
+  const int k1 = min(nseg, (cl + 1) * kCluster);
+  for (int k = cl * kCluster; k < k1; ++k) {
+    const float4 sg = seg[k];
+    const float rx = qx - sg.x, ry = qy - sg.y;
+    const float y1 = segb[k].x;
+    const float isleft = sg.z * ry - rx * sg.w;
+    if (sg.y <= qy) {
+      if (y1 > qy && isleft > 0.f) ++wn;
+    } else {
+      if (y1 <= qy && isleft < 0.f) --wn;
+    }
+  }
+  return wn;
+}
+
 // Persistent: each block iteration handles one task of 256 Gaussians of one curve.
 __global__ void __launch_bounds__(256, 4) k_emit(ns_curves cv, ns_sample_params sp, const CurvePlan* __restrict__ plan,
                                               const int* __restrict__ order, const float* __restrict__ knots,
@@ -355,6 +389,11 @@ __global__ void __launch_bounds__(256, 4) k_emit(ns_curves cv, ns_sample_params 
     const int B = pl.M;
     float best = FLT_MAX;
     int arg = 0, wn = 0;
+    bool deep = false;
+    // sigmoid(z) rounds to exactly 1 in FP32 once exp(-z) <= 2^-24 (z >= 16.64);
+    // deep2 is the squared distance beyond which z >= 17 with margin
+    const float dsat = 17.f * sp.h / sp.gamma;
+    const float deep2 = dsat * dsat * 1.001f + 1e-3f;
     for (int base = 0; base < B; base += kSegBatch) {
       const int nseg = min(kSegBatch, B - base);
       const int ncl = (nseg + kCluster - 1) / kCluster;
@@ -383,7 +422,33 @@ __global__ void __launch_bounds__(256, 4) k_emit(ns_curves cv, ns_sample_params 
         cbox[cl] = make_float4(x0, x1, y0, y1);
       }
       __syncthreads();
-      if (valid) {
+      if (valid && B <= kSegBatch) {
+        // the whole polyline is staged: first the winding number and a lower
+        // bound of the distance (nearest cluster box), then the distance itself
+        // unless the point is provably deep inside, where the sigmoid of Eq. 7
+        // is exactly 1 in FP32 and the nearest segment cannot matter
+        float lbmin = FLT_MAX;
+        for (int cl = 0; cl < ncl; ++cl) {
+          const float4 bb = cbox[cl];
+          const float bx = fmaxf(fmaxf(bb.x - qx, qx - bb.y), 0.f);
+          const float by = fmaxf(fmaxf(bb.z - qy, qy - bb.w), 0.f);
+          lbmin = fminf(lbmin, bx * bx + by * by);
+          if (bb.z <= qy && bb.w > qy && bb.y >= qx - 0.01f) wn += cluster_crossings(seg, segb, cl, nseg, qx, qy);
+        }
+        const bool inside = sp.fill_rule == 0 ? wn > 0 : wn != 0;
+        if (inside && lbmin > deep2) {
+          deep = true;
+        } else {
+          for (int cl = 0; cl < ncl; ++cl) {
+            const float4 bb = cbox[cl];
+            const float bx = fmaxf(fmaxf(bb.x - qx, qx - bb.y), 0.f);
+            const float by = fmaxf(fmaxf(bb.z - qy, qy - bb.w), 0.f);
+            const float lb2 = bx * bx + by * by;
+            if (lb2 > best + 1e-3f * (lb2 + 1.f)) continue;
+            cluster_nearest(seg, segb, cl, nseg, base, qx, qy, best, arg);
+          }
+        }
+      } else if (valid) {
         for (int cl = 0; cl < ncl; ++cl) {
           const float4 bb = cbox[cl];
           // distance: a cluster whose box lies farther than the best distance so
@@ -391,47 +456,26 @@ __global__ void __launch_bounds__(256, 4) k_emit(ns_curves cv, ns_sample_params 
           const float bx = fmaxf(fmaxf(bb.x - qx, qx - bb.y), 0.f);
           const float by = fmaxf(fmaxf(bb.z - qy, qy - bb.w), 0.f);
           const float lb2 = bx * bx + by * by;
-          const bool need_d = !(lb2 > best + 1e-3f * (lb2 + 1.f));
+          if (!(lb2 > best + 1e-3f * (lb2 + 1.f))) cluster_nearest(seg, segb, cl, nseg, base, qx, qy, best, arg);
           // crossings of the ray to +x: only a cluster with vertices on both sides
           // of y = qy (same comparisons as the per-segment test) that reaches
           // x >= qx - 0.01 can contribute
-          const bool need_w = bb.z <= qy && bb.w > qy && bb.y >= qx - 0.01f;
-          if (!need_d && !need_w) continue;
-          const int k1 = min(nseg, (cl + 1) * kCluster);
-          for (int k = cl * kCluster; k < k1; ++k) {
-            const float4 sg = seg[k];
-            const float rx = qx - sg.x, ry = qy - sg.y;
-            if (need_d) {
-              const float2 sb = segb[k];
-              const float t = fminf(fmaxf((rx * sg.z + ry * sg.w) * sb.y, 0.f), 1.f);
-              const float dx = rx - t * sg.z, dy = ry - t * sg.w;
-              const float d2 = dx * dx + dy * dy;
-              if (d2 < best) { best = d2; arg = base + k; }
-            }
-            if (need_w) {
-              // winding number by signed crossings of the horizontal ray (Eq. S2
-              // is integral off the polyline; this evaluates it exactly there)
-              const float y1 = segb[k].x;
-              const float isleft = sg.z * ry - rx * sg.w;
-              if (sg.y <= qy) {
-                if (y1 > qy && isleft > 0.f) ++wn;
-              } else {
-                if (y1 <= qy && isleft < 0.f) --wn;
-              }
-            }
-          }
+          if (bb.z <= qy && bb.w > qy && bb.y >= qx - 0.01f) wn += cluster_crossings(seg, segb, cl, nseg, qx, qy);
         }
       }
     }
     if (valid) {
       const bool inside = sp.fill_rule == 0 ? wn > 0 : wn != 0;
-      const float d = sqrtf(best);
-      const float sdf = inside ? d : -d;
-      const float z = sp.gamma / sp.h * sdf;
-      const float sig = 1.f / (1.f + __expf(-z));
+      float sig = 1.f;
+      if (!deep) {
+        const float d = sqrtf(best);
+        const float sdf = inside ? d : -d;
+        const float z = sp.gamma / sp.h * sdf;
+        sig = 1.f / (1.f + __expf(-z));
+      }
       rec[g] = make_float4(qx, qy, sp.eta * sp.h / sp.rho, o * sig);
       gcurve[g] = c;
-      gaux[g] = inside ? arg : ~arg;
+      gaux[g] = deep ? kAuxDeep : (inside ? arg : ~arg);
     }
   }
 }

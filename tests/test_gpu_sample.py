@@ -109,6 +109,14 @@ def test_fill_nearest_segment_and_sign(seed, h):
         poly = sm.nb.curve_point(cp, U, p, sm.boundary_parameters(a, b, pl_o[cv].n_boundary))[:, :2]
         q = _t.as_tensor(rec[sel, :2])
         d_min, _ = sm.unsigned_distance(q, poly)
+        tol = 32 * EPS32 * (sc.width + pl_o[cv].length)
+        # points recorded as deep inside (no segment): inside, and far enough
+        # that the sigmoid of Eq. 7 is 1 in FP32 (z >= 17)
+        deep = aux[sel] == 0x7fffffff
+        wn = sm.winding_number(q, poly).numpy()
+        assert np.all(wn[deep] > 0.5)
+        assert np.all(d_min.numpy()[deep] >= 17.0 * h / sc.sample["gamma"] - tol)
+        sel, q, d_min, wn = sel[~deep], q[~deep], d_min[~deep], wn[~deep]
         ins = aux[sel] >= 0
         i0 = np.where(ins, aux[sel], ~aux[sel])
         b0 = poly[i0]
@@ -116,8 +124,6 @@ def test_fill_nearest_segment_and_sign(seed, h):
         e = b1 - b0
         tt = (((q - b0) * e).sum(1) / (e * e).sum(1)).clamp(0, 1)
         d_sel = (q - b0 - tt[:, None] * e).norm(dim=1)
-        tol = 32 * EPS32 * (sc.width + pl_o[cv].length)
         assert float((d_sel - d_min).abs().max()) <= tol
-        wn = sm.winding_number(q, poly).numpy()
         clear = d_min.numpy() > tol
         assert np.array_equal(ins[clear], (wn > 0.5)[clear])
