@@ -32,6 +32,33 @@ if ROOT not in sys.path:
 import scenes  # noqa: E402
 
 PEAKS_FALLBACK = dict(hbm_gbs=6400.0, sm_max_mhz=2032.0)
+
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# one `ncu --set full` capture of the 512-path version of the workload at tile
+# 8 (profiles/*_vectorize-512-1024.md), with the units that launch processed
+# and the hash of the kernel source it ran.  The bench scales the bytes to its
+# own launch by the units processed, and reports null if the source or tile
+# has changed since the capture.
+TRAFFIC = dict(
+    blend_bwd=dict(bytes=106232576, units=2706344, unit="pairs", tile=8,
+                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="0864786de61ebe62"),
+    blend_fwd=dict(bytes=48792576, units=2706344, unit="pairs", tile=8,
+                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="0864786de61ebe62"),
+    emit=dict(bytes=2174208, units=2027197, unit="gaussians", tile=None,
+              src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="8edc698e9ca46215"),
+)
+
+
+def traffic_per_launch(kernel, units_now, tile):
+    """Captured DRAM bytes scaled to this launch, or None when stale."""
+    import hashlib
+    t = TRAFFIC.get(kernel)
+    if t is None or (t["tile"] is not None and t["tile"] != tile):
+        return None
+    sha = hashlib.sha256(open(os.path.join(ROOT, t["src"]), "rb").read()).hexdigest()[:16]
+    if sha != t["sha"]:
+        return None
+    return int(round(t["bytes"] * units_now[t["unit"]] / t["units"]))
 METRIC = "fwd+bwd Gaussians/s at 1024^2 (batched, graph-captured step)"
 FLOP_SEGMENT = 20        # one (grid point, boundary segment) SDF test: distance 14 + crossing 6
 FLOP_EVAL = 10           # one alpha evaluation (Eq. 9): dx, dy, d^2, scale, exp arg, *o, cap, skip test
@@ -326,12 +353,16 @@ def run_gpu(args, dist, rank, world):
             ach = amount / (ms / 1e3)
             d.update(bound=bound, achieved=round(ach, 3), unit=unit, frac=round(ach / peak, 4))
         kernels[k] = d
+    units_now = dict(pairs=int(rep.pairs), gaussians=G)
+    tile_now = int(step.sp.rp.tile)
+    for k in kernels:
+        kernels[k]["traffic"] = traffic_per_launch(k, units_now, tile_now)
     roof = None
     if dom in work:
         bound, amount, unit, peak = work[dom]
         ach = amount / (per_kernel[dom] / 1e3)
         roof = dict(kernel=dom, bound=bound, achieved=round(ach, 3), peak=round(peak, 2), unit=unit,
-                    frac=round(ach / peak, 4), traffic=None,
+                    frac=round(ach / peak, 4), traffic=traffic_per_launch(dom, units_now, tile_now),
                     peak_source=("FP32 lanes x SMs x max SM clock" if bound == "alu"
                                  else f"{peaks['source']} HBM copy bandwidth"))
 

@@ -303,18 +303,30 @@ __global__ void k_chain_boundary(ns_curves cv, const CurvePlan* __restrict__ pla
 
 // dL/dU -> dL/dtau.  U_k is the sum of the intervals before k, so dL/d(interval q)
 // = sum_{k > q} dL/dU_k; interval q of the extended list maps back to tau.
+// One warp per curve: the suffix sums run 32 knots at a time, from the last
+// knot down, with a running carry.
 __global__ void k_knot_grads(ns_curves cv, const CurvePlan* __restrict__ plan, const float* __restrict__ dknots,
                              float* dtau) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (c >= cv.n_curves || plan[c].kind == kNone) return;
   const CurveRef cr = curve_ref(cv, c);
   const int t0 = cv.tau_offset[c];
   const int nt = cr.ntau, p = cr.p;
   const int n_int = nt + 2 * p;
   const float* dU = dknots + cr.knot0;
-  float acc = 0.f;
-  for (int q = n_int - 1; q >= 0; --q) {
-    acc += dU[q + 1];
+  float carry = 0.f;
+  for (int top = n_int - 1; top >= 0; top -= 32) {
+    const int q = top - lane;                       // interval handled by this lane
+    float v = q >= 0 ? dU[q + 1] : 0.f;
+    // inclusive scan from lane 0 (interval top) downwards = suffix sum over knots > q
+    for (int o = 1; o < 32; o <<= 1) {
+      const float y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
+    }
+    const float acc = carry + v;
+    carry += __shfl_sync(0xffffffffu, v, 31);
+    if (q < 0) continue;
     int k;
     if (!cr.closed) {
       if (q < p || q >= p + nt) continue;
@@ -324,7 +336,7 @@ __global__ void k_knot_grads(ns_curves cv, const CurvePlan* __restrict__ plan, c
       k %= nt;
       if (k < 0) k += nt;
     }
-    dtau[t0 + k] += acc;
+    atomicAdd(dtau + t0 + k, acc);   // closed curves: wrapped copies fold onto the same interval
   }
 }
 
@@ -385,7 +397,7 @@ extern "C" ns_status splat_backward(const ns_curves* curves, const ns_gaussians*
                                             cap->boundary, out->dkey, dknots, dbpts, out->dcolor);
       if (L.bcap > 0)
         NS_LAUNCH(NS_KERNEL_CHAIN_BOUNDARY, k_chain_boundary, num_sms() * 4, 256, 0, s, *curves, plan, knots, st, dbpts, out->dkey, dknots);
-      NS_LAUNCH(NS_KERNEL_KNOT_GRADS, k_knot_grads, (L.nc + 127) / 128, 128, 0, s, *curves, plan, dknots, out->dtau);
+      NS_LAUNCH(NS_KERNEL_KNOT_GRADS, k_knot_grads, (L.nc + 3) / 4, 128, 0, s, *curves, plan, dknots, out->dtau);
     }
   }
   const cudaError_t e = cudaGetLastError();

@@ -116,10 +116,12 @@ __global__ void __launch_bounds__(256) k_bin_count(const float4* __restrict__ re
       const float4 r = rec[g];
       int x0, y0, nx;
       const int cv = gcurve[g];
-      if (cv >= 0 && cv < bp.n_curves) cnt += tile_rect(r, bp, x0, y0, nx);
-      prep[g] = make_float4(r.x, r.y, ncoef(r.z), r.w);
-      reach[g] = make_float2(r.z > 0.f && r.w > 0.f ? reach2(r.z, r.w, bp.log_amin) : -1.f,
-                             r.z > 0.f ? 1.f / r.z : 0.f);
+      const int nt = (cv >= 0 && cv < bp.n_curves) ? tile_rect(r, bp, x0, y0, nx) : 0;
+      cnt += nt;
+      if (nt) {   // only binned Gaussians are ever read by the blend kernels
+        prep[g] = make_float4(r.x, r.y, ncoef(r.z), r.w);
+        reach[g] = make_float2(reach2(r.z, r.w, bp.log_amin), 1.f / r.z);
+      }
       culled += (r.z > 0.f && r.w < bp.alpha_min) ? 1 : 0;
     }
   }

@@ -59,16 +59,40 @@ __device__ __forceinline__ float block_reduce_minmax(float v, float* red, bool i
   return red[0];
 }
 
+// Copies a curve's knots and key points into shared memory when they fit;
+// returns the pointers (and key offset) the evaluator should use.
+constexpr int kStageKnots = 1024, kStageKeys = 1024;
+
+struct Staged {
+  const float4* key;
+  const float* U;
+  CurveRef cr;
+};
+
+__device__ __forceinline__ Staged stage_curve(const ns_curves& cv, CurveRef cr, const float* U, float* sU,
+                                              float4* sK) {
+  const int nkn = cr.ntau + 2 * cr.p + 1;
+  if (nkn > kStageKnots || cr.nk > kStageKeys) {
+    __syncthreads();
+    return Staged{reinterpret_cast<const float4*>(cv.key), U, cr};
+  }
+  const float4* key = reinterpret_cast<const float4*>(cv.key) + cr.key0;
+  for (int i = threadIdx.x; i < nkn; i += blockDim.x) sU[i] = U[i];
+  for (int i = threadIdx.x; i < cr.nk; i += blockDim.x) sK[i] = key[i];
+  __syncthreads();
+  cr.key0 = 0;
+  return Staged{sK, sU, cr};
+}
+
 template <int P>
-__device__ float arc_length_part(const ns_curves& cv, const CurveRef& cr, const float* U, float a, float b,
-                                 int NL) {
+__device__ float arc_length_part(const float4* key, const CurveRef& cr, const float* U, float a, float b, int NL) {
   const float du = (b - a) / float(NL);
   float acc = 0.f;
   for (int j = threadIdx.x; j < NL; j += blockDim.x) {
     const float u = a + (float(j) + 0.5f) * du;
     const int i = find_span(U, P, cr.n, u);
     Eval<P> e;
-    eval_curve<P>(reinterpret_cast<const float4*>(cv.key), cr, U, i, u, e);
+    eval_curve<P>(key, cr, U, i, u, e);
     acc += speed_xy<P>(e);
   }
   return acc * du;
@@ -146,8 +170,11 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(ns_curves cv, ns_sample_p
   }
   const float a = U[cr.p], b = U[cr.n + 1];
   const int NL = sp.nl_mult * max(cv.width, cv.height);
+  __shared__ float sU[kStageKnots];
+  __shared__ float4 sK[kStageKeys];
+  const Staged sg = stage_curve(cv, cr, U, sU, sK);
   float part = 0.f;
-  NS_DISPATCH_P(cr.p, part = arc_length_part<P>(cv, cr, U, a, b, NL));
+  NS_DISPATCH_P(cr.p, part = arc_length_part<P>(sg.key, sg.cr, sg.U, a, b, NL));
   const float L = block_sum(part, red);
   if (threadIdx.x == 0) {
     pl.L = L;
@@ -223,7 +250,7 @@ __global__ void k_scan_boundary(int nc, CurvePlan* plan, DevState* st, long long
 }
 
 template <int P>
-__device__ void boundary_points(const ns_curves& cv, const CurveRef& cr, const float* U, const CurvePlan& pl,
+__device__ void boundary_points(const float4* key, const CurveRef& cr, const float* U, const CurvePlan& pl,
                                 float2* bpts, long long bcap, float4& box) {
   float xmin = FLT_MAX, ymin = FLT_MAX, xmax = -FLT_MAX, ymax = -FLT_MAX;
   for (int j = threadIdx.x; j < pl.M; j += blockDim.x) {
@@ -231,7 +258,7 @@ __device__ void boundary_points(const ns_curves& cv, const CurveRef& cr, const f
     const float u = pl.a + t * (pl.b - pl.a);
     const int i = find_span(U, P, cr.n, u);
     Eval<P> e;
-    eval_curve<P>(reinterpret_cast<const float4*>(cv.key), cr, U, i, u, e);
+    eval_curve<P>(key, cr, U, i, u, e);
     const long long o = (long long)pl.b_off + j;
     if (o < bcap) bpts[o] = make_float2(e.C[0], e.C[1]);
     xmin = fminf(xmin, e.C[0]);
@@ -251,8 +278,11 @@ __global__ void __launch_bounds__(kPlanThreads) k_boundary(ns_curves cv, ns_samp
   const CurveRef cr = curve_ref(cv, c);
   const float* U = knots + cr.knot0;
   const CurvePlan pl = plan[c];
+  __shared__ float sU[kStageKnots];
+  __shared__ float4 sK[kStageKeys];
+  const Staged sg = stage_curve(cv, cr, U, sU, sK);
   float4 box = make_float4(FLT_MAX, FLT_MAX, -FLT_MAX, -FLT_MAX);
-  NS_DISPATCH_P(cr.p, boundary_points<P>(cv, cr, U, pl, bpts, bcap, box));
+  NS_DISPATCH_P(cr.p, boundary_points<P>(sg.key, sg.cr, sg.U, pl, bpts, bcap, box));
   const float xmin = block_reduce_minmax(box.x, red, false);
   const float ymin = block_reduce_minmax(box.y, red, false);
   const float xmax = block_reduce_minmax(box.z, red, true);
@@ -314,7 +344,9 @@ __device__ void emit_contour(const ns_curves& cv, const CurveRef& cr, const floa
   rec = make_float4(e.C[0], e.C[1], e.C[2] / sp.rho, o);
 }
 
-// Nearest segment of one cluster (strict <: the first minimum wins).
+// Nearest segment of one cluster.  Among equal distances the lowest segment
+// index wins, whatever order the clusters are visited in (the result of a
+// plain first-minimum loop over all segments).
 __device__ __forceinline__ void cluster_nearest(const float4* seg, const float2* segb, int cl, int nseg, int base,
                                                 float qx, float qy, float& best, int& arg) {
   const int k1 = min(nseg, (cl + 1) * kCluster);
@@ -324,7 +356,7 @@ __device__ __forceinline__ void cluster_nearest(const float4* seg, const float2*
     const float t = fminf(fmaxf((rx * sg.z + ry * sg.w) * segb[k].y, 0.f), 1.f);
     const float dx = rx - t * sg.z, dy = ry - t * sg.w;
     const float d2 = dx * dx + dy * dy;
-    if (d2 < best) { best = d2; arg = base + k; }
+    if (d2 < best || (d2 == best && base + k < arg)) { best = d2; arg = base + k; }
   }
 }
 
@@ -428,18 +460,23 @@ __global__ void __launch_bounds__(256, 4) k_emit(ns_curves cv, ns_sample_params 
         // unless the point is provably deep inside, where the sigmoid of Eq. 7
         // is exactly 1 in FP32 and the nearest segment cannot matter
         float lbmin = FLT_MAX;
+        int clmin = 0;
         for (int cl = 0; cl < ncl; ++cl) {
           const float4 bb = cbox[cl];
           const float bx = fmaxf(fmaxf(bb.x - qx, qx - bb.y), 0.f);
           const float by = fmaxf(fmaxf(bb.z - qy, qy - bb.w), 0.f);
-          lbmin = fminf(lbmin, bx * bx + by * by);
+          const float lb2 = bx * bx + by * by;
+          if (lb2 < lbmin) { lbmin = lb2; clmin = cl; }
           if (bb.z <= qy && bb.w > qy && bb.y >= qx - 0.01f) wn += cluster_crossings(seg, segb, cl, nseg, qx, qy);
         }
         const bool inside = sp.fill_rule == 0 ? wn > 0 : wn != 0;
         if (inside && lbmin > deep2) {
           deep = true;
         } else {
+          // the nearest box first: its best distance prunes most other clusters
+          cluster_nearest(seg, segb, clmin, nseg, base, qx, qy, best, arg);
           for (int cl = 0; cl < ncl; ++cl) {
+            if (cl == clmin) continue;
             const float4 bb = cbox[cl];
             const float bx = fmaxf(fmaxf(bb.x - qx, qx - bb.y), 0.f);
             const float by = fmaxf(fmaxf(bb.z - qy, qy - bb.w), 0.f);
