@@ -234,7 +234,7 @@ __device__ __forceinline__ void eval_curve(const float4* __restrict__ key, const
 #pragma unroll
   for (int l = 0; l <= P; ++l) {
     const int k = cp_to_key(i - P + l, P, cr.closed, cr.nk);
-    const float4 q = __ldg(&key[cr.key0 + k]);
+    const float4 q = key[cr.key0 + k];   // key may point to shared or global memory: plain load
     e.cp[l] = q;
     const float nw = e.t.N[l] * q.w;
     e.S[0] = fmaf(nw, q.x, e.S[0]);
