@@ -225,6 +225,15 @@ ns_status splat_backward(const ns_curves* curves, const ns_gaussians* g,
                          void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * Grid-step annealing (Eq. 14): the fill grid step for iteration t of T,
+ * h_max until t/T reaches t_b, then a cosine ramp to h_min reached at t_e,
+ * h_min afterwards:  h = h_max + (h_min - h_max) (1 + cos(pi (1 - phi))) / 2,
+ * phi = (t/T - t_b) / (t_e - t_b).  Host function; pass the result as
+ * ns_sample_params.h.
+ */
+float ns_grid_step(int32_t t, int32_t T, float h_max, float h_min, float t_b, float t_e);
+
+/*
  * L2 image loss (Eq. 10 with an L2 image term): loss = mean((image - target)^2)
  * over n values; dL_dimage = 2 (image - target) / n.  loss: device scalar,
  * overwritten.  dL_dimage may be NULL.

@@ -18,3 +18,16 @@ def adam_step(p, g, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8, lo=-np.inf, hi=n
     vh = v / (1 - b2 ** step)
     p = np.clip(p - lr * mh / (np.sqrt(vh) + eps), lo, hi)
     return p, m, v
+
+
+def grid_step(t, T, h_max, h_min, t_b, t_e):
+    """Cosine grid-step annealing (Eq. 14): h = h_max + (h_min - h_max)(1 + cos(pi (1 - phi)))/2
+    with phi = (t/T - t_b)/(t_e - t_b) inside (t_b, t_e), clamped outside."""
+    import math
+    f = t / T
+    if f <= t_b:
+        return h_max
+    if f >= t_e:
+        return h_min
+    phi = (f - t_b) / (t_e - t_b)
+    return h_max + (h_min - h_max) * (1 + math.cos(math.pi * (1 - phi))) / 2

@@ -68,6 +68,7 @@ SIGNATURES = {
     "splat_backward": (C.c_int, [C.POINTER(NsCurves), C.POINTER(NsGaussians), C.POINTER(NsSampleParams),
                                  C.POINTER(NsRasterParams), C.POINTER(NsCapacity), _p, _p,
                                  C.POINTER(NsCurveGrads), C.c_int32, _p, C.c_size_t, _p]),
+    "ns_grid_step": (C.c_float, [C.c_int32, C.c_int32, C.c_float, C.c_float, C.c_float, C.c_float]),
     "ns_mse_loss": (C.c_int, [_p, _p, C.c_int64, _p, _p, _p]),
     "ns_adam_step": (C.c_int, [_p, _p, _p, _p, C.c_int64, C.c_float, C.c_float, C.c_float, C.c_float,
                                C.c_int32, C.c_float, C.c_float, _p]),

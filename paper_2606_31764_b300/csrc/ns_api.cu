@@ -232,6 +232,14 @@ size_t ns_workspace_size(const ns_curves* curves, const ns_capacity* cap, const 
   return L.total;
 }
 
+float ns_grid_step(int32_t t, int32_t T, float h_max, float h_min, float t_b, float t_e) {
+  const double f = T > 0 ? double(t) / double(T) : 1.0;
+  if (f <= t_b) return h_max;
+  if (f >= t_e) return h_min;
+  const double phi = (f - t_b) / (double(t_e) - double(t_b));
+  return float(h_max + (double(h_min) - h_max) * (1.0 + cos(3.14159265358979323846 * (1.0 - phi))) * 0.5);
+}
+
 ns_status ns_poll_status(void* ws, ns_report* r, void* stream) {
   if (!ws || !r) {
     set_error("ns_poll_status: null argument");

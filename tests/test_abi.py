@@ -60,3 +60,11 @@ def test_host_side_argument_errors_need_no_gpu():
     assert lib.ns_workspace_size(C.byref(c), C.byref(cap), C.byref(rp)) > 0
     rp.tile = 12
     assert lib.ns_workspace_size(C.byref(c), C.byref(cap), C.byref(rp)) == 0
+
+
+def test_grid_step_schedule_matches_oracle():
+    from oracle.optim import grid_step
+    lib = binding.load()
+    for (hmax, hmin, tb, te, T) in ((4.0, 1.0, 0.1, 0.8, 300), (8.0, 1.0, 0.1, 0.8, 300), (2.0, 0.5, 0.0, 1.0, 50)):
+        for t in range(T):
+            assert abs(lib.ns_grid_step(t, T, hmax, hmin, tb, te) - grid_step(t, T, hmax, hmin, tb, te)) <= 1e-6 * hmax

@@ -65,3 +65,28 @@ def test_step_other_tile_sizes(tile):
     assert _rel_ok(out["dcolor"], ref["dcolor"]) and _rel_ok(out["dtau"], ref["dtau"])
     for j in range(4):
         assert _rel_ok(out["dkey"][:, j], ref["dkey"][:, j])
+
+
+def test_autograd_function_matches_oracle():
+    """NurbsSplatFunction: torch autograd drives splat_backward; the gradient of
+    a torch-side L2 loss matches the oracle's exact gradient."""
+    import torch
+    from paper_2606_31764_b300.splat import NurbsSplatFunction, Splatter, scene_tensors
+    sc = scenes.small_open(57, n_curves=2, size=40)
+    ref = op.loss_and_grads(sc)
+    sp = Splatter(sc)
+    k, t, c = scene_tensors(sc)
+    sp.fit(k, t, c)
+    k.requires_grad_(True)
+    t.requires_grad_(True)
+    c.requires_grad_(True)
+    img = NurbsSplatFunction.apply(k, t, c, sp)
+    tgt = torch.as_tensor(sc.target, device="cuda")
+    loss = ((img - tgt) ** 2).mean()
+    loss.backward()
+    assert abs(loss.item() - ref["loss"]) <= 1e-4 * ref["loss"]
+    assert _rel_ok(c.grad.cpu().numpy(), ref["dcolor"])
+    assert _rel_ok(t.grad.cpu().numpy(), ref["dtau"])
+    dk = k.grad.cpu().numpy().reshape(-1, 4)
+    for j in range(4):
+        assert _rel_ok(dk[:, j], ref["dkey"][:, j])

@@ -29,3 +29,14 @@ def test_clamps():
     p, _, _ = optim.adam_step(np.array([0.02, 1.99]), np.array([1.0, -1.0]), np.zeros(2), np.zeros(2), 1,
                               lr=0.5, lo=0.01, hi=2.0)
     np.testing.assert_array_equal(p, [0.01, 2.0])
+
+
+def test_grid_step_schedule_end_points_and_midpoint():
+    # Eq. 14: h_max before t_b, h_min after t_e, the mean at the middle, monotone
+    from oracle.optim import grid_step
+    args = dict(T=300, h_max=4.0, h_min=1.0, t_b=0.1, t_e=0.8)
+    assert grid_step(0, **args) == 4.0 and grid_step(30, **args) == 4.0
+    assert grid_step(240, **args) == 1.0 and grid_step(299, **args) == 1.0
+    assert abs(grid_step(135, **args) - 2.5) < 1e-12          # phi = 1/2
+    hs = [grid_step(t, **args) for t in range(300)]
+    assert all(a >= b for a, b in zip(hs, hs[1:]))
