@@ -177,11 +177,13 @@ class ClockSampler:
 class Step:
     """Preallocated buffers and the four calls of one training step."""
 
-    def __init__(self, scene, capacity, raster=None):
+    def __init__(self, scene, capacity, raster=None, adam=False):
         import torch
         from paper_2606_31764_b300.splat import Splatter, scene_tensors
         self.torch = torch
         self.scene = scene
+        self.adam = adam
+        self.adam_state = {}
         self.sp = Splatter(scene, raster=raster, capacity=capacity)
         self.key, self.tau, self.color = scene_tensors(scene)
         self.rep = self.sp.fit(self.key, self.tau, self.color)
@@ -197,6 +199,8 @@ class Step:
         sp.forward_gaussians(self.key, self.tau, self.color, self.image)
         sp.mse(self.image, self.target, self.dimage, self.loss)
         sp.backward(self.key, self.tau, self.color, self.dimage, grads=self.grads)
+        if self.adam:   # fixed step number: the captured graph replays the same bias correction
+            sp.adam(self.key, self.tau, self.color, self.grads, self.adam_state, step=10)
 
     def gaussians(self):
         return int(self.sp.count.item())
@@ -386,7 +390,32 @@ def run_gpu(args, dist, rank, world):
                sample=costs)
     if not args.no_per_scene:
         out["per_scene"] = run_per_scene(torch, step, args, value)
+        out["long_spline"] = run_long_spline(torch, args)
     return out, step
+
+
+def run_long_spline(torch, args):
+    """The contour-path workload: 256 open cubic strokes with 64-512 key points
+    (~1.5M Gaussians) on a 512x512 grayscale canvas, fwd + bwd + Adam step,
+    graph-captured, timed like the headline."""
+    sc = scenes.config3()
+    st = Step(sc, capacity=(3_000_000, 12_000_000, 16), adam=True)
+    st()
+    g = capture(torch, st)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    K = max(3, args.steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(K):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    G = st.gaussians()
+    return dict(workload="long-spline-512: 256 open cubic strokes, 64-512 key points, 512x512 gray, + Adam",
+                gaussians_per_step=G, ms_per_step=round(ms, 4), gaussians_per_s=round(G / (ms / 1e3), 1))
 
 
 def run_e2e(torch, step, g1, args):

@@ -242,13 +242,16 @@ ns_status ns_mse_loss(const float* image, const float* target, int64_t n,
                       float* dL_dimage, float* loss, void* stream);
 
 /*
- * One Adam step on n parameters in place, then a clamp of each value to
- * [lo, hi] (the paper clamps weights to [0.01, 10] and knot intervals to
- * [0, 2], Table S1).  m, v: device moment buffers of n floats.  step >= 1.
+ * One Adam step on n parameters in place, then a clamp: element i is clamped
+ * to [lo[i % group], hi[i % group]] (group 1..4; lo, hi are host arrays of
+ * `group` floats, use +-INFINITY for no bound).  The paper clamps weights to
+ * [0.01, 10] and knot intervals to [0, 2] (Table S1): for key points {x, y, s,
+ * w} use group 4 with lo = {-inf, -inf, 0, 0.01}, hi = {inf, inf, inf, 10}.
+ * m, v: device moment buffers of n floats.  step >= 1.
  */
 ns_status ns_adam_step(float* param, const float* grad, float* m, float* v, int64_t n,
                        float lr, float beta1, float beta2, float eps, int32_t step,
-                       float lo, float hi, void* stream);
+                       const float* lo, const float* hi, int32_t group, void* stream);
 
 /* Synchronises `stream`, reads the device status and counters. */
 ns_status ns_poll_status(void* workspace, ns_report* report, void* stream);

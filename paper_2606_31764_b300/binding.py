@@ -71,7 +71,7 @@ SIGNATURES = {
     "ns_grid_step": (C.c_float, [C.c_int32, C.c_int32, C.c_float, C.c_float, C.c_float, C.c_float]),
     "ns_mse_loss": (C.c_int, [_p, _p, C.c_int64, _p, _p, _p]),
     "ns_adam_step": (C.c_int, [_p, _p, _p, _p, C.c_int64, C.c_float, C.c_float, C.c_float, C.c_float,
-                               C.c_int32, C.c_float, C.c_float, _p]),
+                               C.c_int32, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int32, _p]),
     "ns_poll_status": (C.c_int, [_p, C.POINTER(NsReport), _p]),
     "ns_clear_status": (C.c_int, [_p, _p]),
     "ns_workspace_copy": (C.c_int, [_p, C.POINTER(NsCurves), C.POINTER(NsCapacity), C.POINTER(NsRasterParams),

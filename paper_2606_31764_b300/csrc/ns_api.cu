@@ -178,8 +178,12 @@ __global__ void __launch_bounds__(256) k_mse(const float* __restrict__ a, const 
   }
 }
 
+struct Clamp4 {
+  float lo[4], hi[4];
+};
+
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
-                       long long n, float lr, float b1, float b2, float eps, float c1, float c2, float lo, float hi) {
+                       long long n, float lr, float b1, float b2, float eps, float c1, float c2, Clamp4 cl, int group) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const float gi = g[i];
     const float mi = b1 * m[i] + (1.f - b1) * gi;
@@ -188,7 +192,8 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
     v[i] = vi;
     const float mh = mi / c1, vh = vi / c2;
     const float x = p[i] - lr * mh / (sqrtf(vh) + eps);
-    p[i] = fminf(fmaxf(x, lo), hi);
+    const int j = int(i % group);
+    p[i] = fminf(fmaxf(x, cl.lo[j]), cl.hi[j]);
   }
 }
 
@@ -292,18 +297,28 @@ ns_status ns_mse_loss(const float* image, const float* target, int64_t n, float*
 }
 
 ns_status ns_adam_step(float* param, const float* grad, float* m, float* v, int64_t n, float lr, float beta1,
-                       float beta2, float eps, int32_t step, float lo, float hi, void* stream) {
-  if (!param || !grad || !m || !v || n < 0 || step < 1 || !(lo <= hi)) {
+                       float beta2, float eps, int32_t step, const float* lo, const float* hi, int32_t group,
+                       void* stream) {
+  if (!param || !grad || !m || !v || n < 0 || step < 1 || !lo || !hi || group < 1 || group > 4) {
     set_error("ns_adam_step: invalid argument");
     return NS_ERR_INVALID_ARG;
+  }
+  Clamp4 cl;
+  for (int j = 0; j < 4; ++j) {
+    cl.lo[j] = j < group ? lo[j] : -INFINITY;
+    cl.hi[j] = j < group ? hi[j] : INFINITY;
+    if (!(cl.lo[j] <= cl.hi[j])) {
+      set_error("ns_adam_step: lo > hi");
+      return NS_ERR_INVALID_ARG;
+    }
   }
   if (n == 0) return NS_OK;
   const float c1 = 1.f - powf(beta1, float(step));
   const float c2 = 1.f - powf(beta2, float(step));
   const long long blocks = (n + 255) / 256;
   const int grid = int(blocks < num_sms() * 8 ? blocks : num_sms() * 8);
-  NS_LAUNCH(NS_KERNEL_ADAM, k_adam, grid, 256, 0, static_cast<cudaStream_t>(stream), param, grad, m, v, n, lr, beta1, beta2, eps, c1, c2,
-                                                               lo, hi);
+  NS_LAUNCH(NS_KERNEL_ADAM, k_adam, grid, 256, 0, static_cast<cudaStream_t>(stream), param, grad, m, v, n, lr, beta1,
+            beta2, eps, c1, c2, cl, group);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_error(std::string("ns_adam_step: ") + cudaGetErrorString(e));

@@ -184,6 +184,22 @@ class Splatter:
                C.c_size_t(self.ws_bytes), C.c_int32(repeats), _stream())
         return int(self.rp.ppt_fwd), int(self.rp.ppt_bwd)
 
+    def adam(self, key, tau, color, grads, state, step, lr=(0.1, 0.01, 0.01), betas=(0.9, 0.999), eps=1e-8):
+        """One Adam step on key points, knot intervals and colours with the clamps
+        of Table S1 (w in [0.01, 10], tau in [0, 2]; widths >= 0; colours and
+        opacities in [0, 1]).  `state` holds the moment buffers (made on first use)."""
+        inf = float("inf")
+        groups = ((key, grads[0], 4, (-inf, -inf, 0.0, 0.01), (inf, inf, inf, 10.0), lr[0]),
+                  (tau, grads[1], 1, (0.0,), (2.0,), lr[1]),
+                  (color, grads[2], 4, (0.0,) * 4, (1.0,) * 4, lr[2]))
+        for i, (p, g, grp, lo, hi, r) in enumerate(groups):
+            if i not in state:
+                state[i] = (torch.zeros_like(p), torch.zeros_like(p))
+            m, v = state[i]
+            B.call("ns_adam_step", _ptr(p), _ptr(g), _ptr(m), _ptr(v), C.c_int64(p.numel()), C.c_float(r),
+                   C.c_float(betas[0]), C.c_float(betas[1]), C.c_float(eps), C.c_int32(step),
+                   (C.c_float * grp)(*lo), (C.c_float * grp)(*hi), C.c_int32(grp), _stream())
+
     # -- sizing ---------------------------------------------------------
     def fit(self, key, tau, color, headroom=1.25, max_rounds=4):
         """Run sample + forward, read the sizes the library needed, and grow

@@ -107,21 +107,26 @@ def test_adam_step_matches_oracle():
     from paper_2606_31764_b300 import binding as B
     rng = np.random.default_rng(9)
     n = 100_003
-    p = rng.uniform(0.0, 2.0, n).astype(np.float32)
+    p = rng.uniform(-0.02, 2.0, n).astype(np.float32)
     tp = torch.as_tensor(p, device="cuda")
     tm = torch.zeros(n, device="cuda")
     tv = torch.zeros(n, device="cuda")
     m = np.zeros(n)
     v = np.zeros(n)
     pp = p.astype(np.float64)
+    # key-point layout {x, y, s, w}: unbounded x, y; s >= 0; w in [0.01, 10] (Table S1)
+    lo = (C.c_float * 4)(-np.inf, -np.inf, 0.0, 0.01)
+    hi = (C.c_float * 4)(np.inf, np.inf, np.inf, 10.0)
+    lo_np = np.tile([-np.inf, -np.inf, 0.0, 0.01], n // 4 + 1)[:n]
+    hi_np = np.tile([np.inf, np.inf, np.inf, 10.0], n // 4 + 1)[:n]
     for step in range(1, 4):
         g = rng.standard_normal(n).astype(np.float32)
         tg = torch.as_tensor(g, device="cuda")
         B.call("ns_adam_step", C.c_void_p(tp.data_ptr()), C.c_void_p(tg.data_ptr()), C.c_void_p(tm.data_ptr()),
-               C.c_void_p(tv.data_ptr()), C.c_int64(n), C.c_float(0.01), C.c_float(0.9), C.c_float(0.999),
-               C.c_float(1e-8), C.c_int32(step), C.c_float(0.01), C.c_float(2.0),
+               C.c_void_p(tv.data_ptr()), C.c_int64(n), C.c_float(0.05), C.c_float(0.9), C.c_float(0.999),
+               C.c_float(1e-8), C.c_int32(step), lo, hi, C.c_int32(4),
                C.c_void_p(torch.cuda.current_stream().cuda_stream))
-        pp, m, v = optim.adam_step(pp, g, m, v, step, lr=0.01, lo=0.01, hi=2.0)
+        pp, m, v = optim.adam_step(pp, g, m, v, step, lr=0.05, lo=lo_np, hi=hi_np)
         torch.cuda.synchronize()
         assert np.abs(tp.cpu().numpy() - pp).max() <= 1e-6
         assert np.abs(tm.cpu().numpy() - m).max() <= 1e-6
