@@ -2,16 +2,18 @@
 //
 // After the blend adjoint (ns_raster.cu) has accumulated dL/d(mu, sigma,
 // opacity, colour) per Gaussian:
-//   k_chain           persistent over the sampling tasks of nurbs_sample.
-//                     Contour task: per sample, the reverse sweep of the
+//   k_chain_contour<P> persistent over the contour tasks of nurbs_sample, one
+//                     kernel per degree.  Per sample, the reverse sweep of the
 //                     span-local Cox-de Boor triangle gives dL/dN, dL/du and
 //                     dL/d(local knots); with C = S/W (Eq. 1) this yields
 //                     dL/dP (x, y, s), dL/dw and, through u = a + t(b - a),
-//                     the domain-end terms.  The task's control-point and knot
-//                     windows are accumulated in shared memory and flushed once.
-//                     Fill task: dL/do_j -> curve opacity (times the sigmoid),
-//                     and dL/dsdf -> the two end points of the nearest segment
-//                     (Eq. 7, S1), accumulated per boundary point in shared memory.
+//                     the domain-end terms.  Sums stay in registers while the
+//                     span is unchanged, then go to the task's shared-memory
+//                     window, which is flushed once per task.
+//   k_chain           persistent over the fill tasks: dL/do_j -> curve opacity
+//                     (times the sigmoid), and dL/dsdf -> the two end points of
+//                     the nearest segment (Eq. 7, S1), accumulated per boundary
+//                     point in shared memory.
 //   k_chain_boundary  per boundary point: dL/db_i -> control points, weights
 //                     and knots through C(u_i), as for contours.
 //   k_knot_grads      per curve: dL/dU -> dL/dtau by suffix sums over the
@@ -30,7 +32,7 @@ ns_status launch_blend_bwd(const Layout& L, const ns_curves* curves, const ns_ga
 bool raster_params_ok(const ns_raster_params* rp);
 
 constexpr int kWin = 1024;   // control points (and knots) per task window in shared memory
-constexpr int kWinB = 2 * kWin;  // boundary points per fill task window (float2, aliases s_cp)
+constexpr int kWinB = 2 * kWin;  // boundary points per fill task window
 
 // Reverse of one curve point: gC = dL/dC (x, y, s) at parameter u (span i,
 // domain fraction t).  Adds to the control-point and knot accumulators.
@@ -60,69 +62,58 @@ __device__ __forceinline__ void curve_point_bwd(const ns_curves& cv, const Curve
   dB += du * t;
 }
 
+// Reverse of one curve point into arrays: dcp[l] = dL/d{x, y, s, w} of the
+// span's control point i-P+l, dkn[k] = dL/dU[i-P+1+k], du = dL/du.
+template <int P>
+__device__ __forceinline__ void curve_point_bwd_local(const float4* key, const CurveRef& cr, const float* U, int i,
+                                                      float u, const float gC[3], float dcp[P + 1][4],
+                                                      float dkn[2 * P], float& du) {
+  Eval<P> e;
+  eval_curve<P>(key, cr, U, i, u, e);
+  const float iw = 1.f / e.W;
+  float gN[P + 1];
+#pragma unroll
+  for (int l = 0; l <= P; ++l) {
+    const float4 q = e.cp[l];
+    const float R = e.t.N[l] * q.w * iw;
+    const float proj = gC[0] * (q.x - e.C[0]) + gC[1] * (q.y - e.C[1]) + gC[2] * (q.z - e.C[2]);
+    gN[l] = q.w * proj * iw;
+    dcp[l][0] += gC[0] * R;
+    dcp[l][1] += gC[1] * R;
+    dcp[l][2] += gC[2] * R;
+    dcp[l][3] += e.t.N[l] * proj * iw;
+  }
+  float d = 0.f;
+  basis_bwd<P>(e.t, gN, &d, dkn);
+  du = d;
+}
+
 struct ChainParams {
   float rho, h, gamma;
   int kappa;
 };
 
 template <int P>
-__device__ void chain_contour_sample(const ns_curves& cv, const CurveRef& cr, const float* U, const CurvePlan& pl,
-                                     int l, const ChainParams& cp, const float4 g0, float* s_cp, float* s_kn,
-                                     int cp_lo, int kn_lo, bool use_smem, float* dkey, float* dknots, float& dA,
-                                     float& dB) {
-  const float u = contour_u(pl, l, cp.kappa);
-  const float t = contour_t(pl, l, cp.kappa);
-  const int i = find_span(U, P, cr.n, u);
-  const float gC[3] = {g0.x, g0.y, g0.z / cp.rho};
-  auto add_cp = [&](int cpi, float dx, float dy, float ds, float dw) {
-    if (use_smem && cpi >= cp_lo && cpi - cp_lo < kWin) {
-      float* a = s_cp + 4 * (cpi - cp_lo);
-      atomicAdd(a + 0, dx);
-      atomicAdd(a + 1, dy);
-      atomicAdd(a + 2, ds);
-      atomicAdd(a + 3, dw);
-    } else {
-      float* a = dkey + 4 * (long long)(cr.key0 + cp_to_key(cpi, P, cr.closed, cr.nk));
-      atomicAdd(a + 0, dx);
-      atomicAdd(a + 1, dy);
-      atomicAdd(a + 2, ds);
-      atomicAdd(a + 3, dw);
-    }
-  };
-  auto add_knot = [&](int k, float v) {
-    if (use_smem && k >= kn_lo && k - kn_lo < kWin + 2 * kMaxP) atomicAdd(s_kn + (k - kn_lo), v);
-    else atomicAdd(dknots + cr.knot0 + k, v);
-  };
-  curve_point_bwd<P>(cv, cr, U, i, u, t, gC, add_cp, add_knot, dA, dB);
-}
-
-template <int P>
 __device__ __forceinline__ int span_at(const CurveRef& cr, const float* U, float u) {
   return find_span(U, P, cr.n, u);
 }
 
-// kFillTasks selects the tasks a launch handles: contour tasks need the
-// degree-templated reverse sweep (many registers), fill tasks only load and
-// combine a few values (latency-bound, so they run in a lean kernel of their own).
-template <bool kFillTasks>
+// Fill tasks: each thread one fill Gaussian (latency-bound loads and a few
+// arithmetic steps; the contour tasks have a kernel of their own).
 __global__ void __launch_bounds__(256) k_chain(ns_curves cv, ChainParams cp, const CurvePlan* __restrict__ plan,
                                                const int* __restrict__ order, const float* __restrict__ knots,
                                                const float2* __restrict__ bpts, const DevState* __restrict__ st,
                                                const float4* __restrict__ rec, const int* __restrict__ gaux,
                                                const float* __restrict__ dgauss, long long gcap, long long bcap,
                                                float* dkey, float* dknots, float2* dbpts, float* dcolor) {
-  __shared__ float s_cp[kFillTasks ? 2 * kWinB : 4 * kWin];
-  __shared__ float s_kn[kFillTasks ? 1 : kWin + 2 * kMaxP];
+  __shared__ float2 s_db[kWinB];
   __shared__ float s_red[8];
-  __shared__ int s_span[2];
-  float2* s_db = reinterpret_cast<float2*>(s_cp);
-  const int n_tasks = kFillTasks ? st->n_chunks : st->n_ctasks;
+  const int n_tasks = st->n_chunks;
   const int nc = cv.n_curves;
   for (int task = blockIdx.x; task < n_tasks; task += gridDim.x) {
-    const int c = curve_of_task(plan, order, nc, task, kFillTasks);
+    const int c = curve_of_task(plan, order, nc, task, true);
     const CurvePlan pl = plan[c];
     const CurveRef cr = curve_ref(cv, c);
-    const float* U = knots + cr.knot0;
     const int l0 = (task - pl.chunk_off) * kChunk;
     const int l = l0 + threadIdx.x;
     const long long g = (long long)pl.g_off + l;
@@ -134,62 +125,7 @@ __global__ void __launch_bounds__(256) k_chain(ns_curves cv, ChainParams cp, con
       g0 = reinterpret_cast<const float4*>(dgauss)[2 * g];
       g1 = reinterpret_cast<const float4*>(dgauss)[2 * g + 1];
     }
-    if constexpr (!kFillTasks) {
-      // window of control points [span(first) - p, span(last)], knots
-      // [span(first) - p + 1, span(last) + p]
-      if (threadIdx.x == 0) {
-        const int lf = l0, ll = min(l0 + kChunk, pl.count) - 1;
-        int sf = 0, sl = 0;
-        NS_DISPATCH_P(cr.p, sf = span_at<P>(cr, U, contour_u(pl, lf, cp.kappa));
-                      sl = span_at<P>(cr, U, contour_u(pl, ll, cp.kappa)));
-        s_span[0] = sf;
-        s_span[1] = sl;
-      }
-      __syncthreads();
-      const int cp_lo = s_span[0] - cr.p;
-      const int ncp = s_span[1] - s_span[0] + cr.p + 1;
-      const int kn_lo = s_span[0] - cr.p + 1;
-      const int nkn = s_span[1] - s_span[0] + 2 * cr.p;
-      const bool use_smem = ncp <= kWin && nkn <= kWin + 2 * kMaxP && s_span[1] >= s_span[0];
-      if (use_smem) {
-        for (int k = threadIdx.x; k < 4 * ncp; k += blockDim.x) s_cp[k] = 0.f;
-        for (int k = threadIdx.x; k < nkn; k += blockDim.x) s_kn[k] = 0.f;
-      }
-      __syncthreads();
-      float dA = 0.f, dB = 0.f;
-      if (valid) {
-        NS_DISPATCH_P(cr.p, chain_contour_sample<P>(cv, cr, U, pl, l, cp, g0, s_cp, s_kn, cp_lo, kn_lo, use_smem,
-                                                     dkey, dknots, dA, dB));
-      }
-      {
-        const float v[8] = {dA, dB, g1.x, g1.y, g1.z, g0.w, 0.f, 0.f};
-        const float tot = warp_sum8(v);
-        const int lane = threadIdx.x & 31;
-        if ((lane & 3) == 0 && (lane >> 2) < 6 && tot != 0.f) atomicAdd(&s_red[lane >> 2], tot);
-      }
-      __syncthreads();
-      if (use_smem) {
-        for (int k = threadIdx.x; k < ncp; k += blockDim.x) {
-          const int key = cr.key0 + cp_to_key(cp_lo + k, cr.p, cr.closed, cr.nk);
-          float* a = dkey + 4 * (long long)key;
-          const float* v = s_cp + 4 * k;
-          if (v[0] != 0.f) atomicAdd(a + 0, v[0]);
-          if (v[1] != 0.f) atomicAdd(a + 1, v[1]);
-          if (v[2] != 0.f) atomicAdd(a + 2, v[2]);
-          if (v[3] != 0.f) atomicAdd(a + 3, v[3]);
-        }
-        for (int k = threadIdx.x; k < nkn; k += blockDim.x)
-          if (s_kn[k] != 0.f) atomicAdd(dknots + cr.knot0 + kn_lo + k, s_kn[k]);
-      }
-      if (threadIdx.x == 0) {
-        atomicAdd(dknots + cr.knot0 + cr.p, s_red[0]);
-        atomicAdd(dknots + cr.knot0 + cr.n + 1, s_red[1]);
-        atomicAdd(dcolor + 4 * c + 0, s_red[2]);
-        atomicAdd(dcolor + 4 * c + 1, s_red[3]);
-        atomicAdd(dcolor + 4 * c + 2, s_red[4]);
-        atomicAdd(dcolor + 4 * c + 3, s_red[5]);
-      }
-    } else {
+    {
     // fill task (skipped when its polyline overflowed the boundary capacity)
     if ((long long)pl.b_off + pl.M > bcap) continue;
     const int B = pl.M;
@@ -256,6 +192,147 @@ __global__ void __launch_bounds__(256) k_chain(ns_curves cv, ChainParams cp, con
       atomicAdd(dcolor + 4 * c + 2, s_red[4]);
       atomicAdd(dcolor + 4 * c + 3, s_red[5]);
     }
+    }
+  }
+}
+
+// Contour tasks: 64 threads per task of 256 samples, 4 consecutive samples per
+// thread.  Consecutive samples mostly share a knot span, so a thread sums its
+// samples' control-point and knot gradients in registers and writes them once
+// per span (into the task's shared-memory window), instead of once per sample.
+constexpr int kContourThreads = 64;
+constexpr int kContourPer = kChunk / kContourThreads;
+
+template <int P>
+__device__ void chain_contour_run(const ns_curves& cv, const CurveRef& cr, const float* U, const CurvePlan& pl,
+                                  int l0, const ChainParams& cp, const float* __restrict__ dgauss, long long gcap,
+                                  float* s_cp, float* s_kn, int cp_lo, int kn_lo, int ncp, int nkn, float* dkey,
+                                  float* dknots, float& dA, float& dB, float4& dcol) {
+  const float4* key = reinterpret_cast<const float4*>(cv.key);
+  float acc[P + 1][4], akn[2 * P];
+  int cur = -1;
+  auto flush = [&]() {
+    if (cur < 0) return;
+#pragma unroll
+    for (int l = 0; l <= P; ++l) {
+      const int cpi = cur - P + l;
+      if (cpi >= cp_lo && cpi - cp_lo < ncp) {
+        float* a = s_cp + 4 * (cpi - cp_lo);
+        atomicAdd(a + 0, acc[l][0]);
+        atomicAdd(a + 1, acc[l][1]);
+        atomicAdd(a + 2, acc[l][2]);
+        atomicAdd(a + 3, acc[l][3]);
+      } else {
+        float* a = dkey + 4 * (long long)(cr.key0 + cp_to_key(cpi, P, cr.closed, cr.nk));
+        atomicAdd(a + 0, acc[l][0]);
+        atomicAdd(a + 1, acc[l][1]);
+        atomicAdd(a + 2, acc[l][2]);
+        atomicAdd(a + 3, acc[l][3]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 2 * P; ++k) {
+      const int kk = cur - P + 1 + k;
+      if (kk >= kn_lo && kk - kn_lo < nkn) atomicAdd(s_kn + (kk - kn_lo), akn[k]);
+      else atomicAdd(dknots + cr.knot0 + kk, akn[k]);
+    }
+  };
+  for (int j = 0; j < kContourPer; ++j) {
+    const int l = l0 + threadIdx.x * kContourPer + j;
+    const long long g = (long long)pl.g_off + l;
+    if (l >= pl.count || g >= gcap) break;
+    const float4 g0 = reinterpret_cast<const float4*>(dgauss)[2 * g];
+    const float4 g1 = reinterpret_cast<const float4*>(dgauss)[2 * g + 1];
+    dcol.x += g1.x;
+    dcol.y += g1.y;
+    dcol.z += g1.z;
+    dcol.w += g0.w;
+    if (g0.x == 0.f && g0.y == 0.f && g0.z == 0.f) continue;   // no geometric gradient
+    const float u = contour_u(pl, l, cp.kappa);
+    const float t = contour_t(pl, l, cp.kappa);
+    const int i = find_span(U, P, cr.n, u);
+    if (i != cur) {
+      flush();
+      cur = i;
+#pragma unroll
+      for (int a = 0; a <= P; ++a) acc[a][0] = acc[a][1] = acc[a][2] = acc[a][3] = 0.f;
+#pragma unroll
+      for (int k = 0; k < 2 * P; ++k) akn[k] = 0.f;
+    }
+    const float gC[3] = {g0.x, g0.y, g0.z / cp.rho};
+    float du;
+    curve_point_bwd_local<P>(key, cr, U, i, u, gC, acc, akn, du);
+    dA += du * (1.f - t);   // u = a + t (b - a)
+    dB += du * t;
+  }
+  flush();
+}
+
+// One kernel per degree (the degree-5 registers would otherwise set the
+// occupancy of every task); each skips the tasks of other degrees.
+template <int P>
+__global__ void __launch_bounds__(kContourThreads) k_chain_contour(
+    ns_curves cv, ChainParams cp, const CurvePlan* __restrict__ plan, const int* __restrict__ order,
+    const float* __restrict__ knots, const DevState* __restrict__ st, const float* __restrict__ dgauss,
+    long long gcap, float* dkey, float* dknots, float* dcolor) {
+  __shared__ float s_cp[4 * kWin];
+  __shared__ float s_kn[kWin + 2 * kMaxP];
+  __shared__ float s_red[8];
+  __shared__ int s_span[2];
+  const int n_tasks = st->n_ctasks;
+  const int nc = cv.n_curves;
+  for (int task = blockIdx.x; task < n_tasks; task += gridDim.x) {
+    const int c = curve_of_task(plan, order, nc, task, false);
+    if (cv.degree[c] != P) continue;
+    const CurvePlan pl = plan[c];
+    const CurveRef cr = curve_ref(cv, c);
+    const float* U = knots + cr.knot0;
+    const int l0 = (task - pl.chunk_off) * kChunk;
+    __syncthreads();
+    if (threadIdx.x < 8) s_red[threadIdx.x] = 0.f;
+    if (threadIdx.x == 0) {
+      const int lf = l0, ll = min(l0 + kChunk, pl.count) - 1;
+      s_span[0] = span_at<P>(cr, U, contour_u(pl, lf, cp.kappa));
+      s_span[1] = span_at<P>(cr, U, contour_u(pl, ll, cp.kappa));
+    }
+    __syncthreads();
+    const int cp_lo = s_span[0] - cr.p;
+    int ncp = s_span[1] - s_span[0] + cr.p + 1;
+    const int kn_lo = s_span[0] - cr.p + 1;
+    int nkn = s_span[1] - s_span[0] + 2 * cr.p;
+    if (!(ncp <= kWin && nkn <= kWin + 2 * kMaxP && s_span[1] >= s_span[0])) ncp = nkn = 0;   // global fallback
+    for (int k = threadIdx.x; k < 4 * ncp; k += blockDim.x) s_cp[k] = 0.f;
+    for (int k = threadIdx.x; k < nkn; k += blockDim.x) s_kn[k] = 0.f;
+    __syncthreads();
+    float dA = 0.f, dB = 0.f;
+    float4 dcol = make_float4(0.f, 0.f, 0.f, 0.f);
+    chain_contour_run<P>(cv, cr, U, pl, l0, cp, dgauss, gcap, s_cp, s_kn, cp_lo, kn_lo, ncp, nkn, dkey, dknots, dA,
+                         dB, dcol);
+    {
+      const float v[8] = {dA, dB, dcol.x, dcol.y, dcol.z, dcol.w, 0.f, 0.f};
+      const float tot = warp_sum8(v);
+      const int lane = threadIdx.x & 31;
+      if ((lane & 3) == 0 && (lane >> 2) < 6 && tot != 0.f) atomicAdd(&s_red[lane >> 2], tot);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < ncp; k += blockDim.x) {
+      const int key = cr.key0 + cp_to_key(cp_lo + k, cr.p, cr.closed, cr.nk);
+      float* a = dkey + 4 * (long long)key;
+      const float* v = s_cp + 4 * k;
+      if (v[0] != 0.f) atomicAdd(a + 0, v[0]);
+      if (v[1] != 0.f) atomicAdd(a + 1, v[1]);
+      if (v[2] != 0.f) atomicAdd(a + 2, v[2]);
+      if (v[3] != 0.f) atomicAdd(a + 3, v[3]);
+    }
+    for (int k = threadIdx.x; k < nkn; k += blockDim.x)
+      if (s_kn[k] != 0.f) atomicAdd(dknots + cr.knot0 + kn_lo + k, s_kn[k]);
+    if (threadIdx.x == 0) {
+      atomicAdd(dknots + cr.knot0 + cr.p, s_red[0]);
+      atomicAdd(dknots + cr.knot0 + cr.n + 1, s_red[1]);
+      atomicAdd(dcolor + 4 * c + 0, s_red[2]);
+      atomicAdd(dcolor + 4 * c + 1, s_red[3]);
+      atomicAdd(dcolor + 4 * c + 2, s_red[4]);
+      atomicAdd(dcolor + 4 * c + 3, s_red[5]);
     }
   }
 }
@@ -389,12 +466,30 @@ extern "C" ns_status splat_backward(const ns_curves* curves, const ns_gaussians*
       cp.h = sp->h;
       cp.gamma = sp->gamma;
       cp.kappa = sp->kappa;
-      NS_LAUNCH(NS_KERNEL_CHAIN, k_chain<true>, num_sms() * 8, 256, 0, s, *curves, cp, plan, order, knots, bpts, st,
+      NS_LAUNCH(NS_KERNEL_CHAIN, k_chain, num_sms() * 8, 256, 0, s, *curves, cp, plan, order, knots, bpts, st,
                 reinterpret_cast<const float4*>(g->rec), g->aux, dg, cap->gaussians,
                 cap->boundary, out->dkey, dknots, dbpts, out->dcolor);
-      NS_LAUNCH(NS_KERNEL_CHAIN_CONTOUR, k_chain<false>, num_sms() * 8, 256, 0, s, *curves, cp, plan, order, knots, bpts, st,
-                                            reinterpret_cast<const float4*>(g->rec), g->aux, dg, cap->gaussians,
-                                            cap->boundary, out->dkey, dknots, dbpts, out->dcolor);
+      {
+        // one launch per degree present among the curves (the host knows the
+        // degrees only on the device, so all five are launched; a launch with
+        // no task of its degree exits after scanning the task list)
+        auto k1 = &k_chain_contour<1>;
+        auto k2 = &k_chain_contour<2>;
+        auto k3 = &k_chain_contour<3>;
+        auto k4 = &k_chain_contour<4>;
+        auto k5 = &k_chain_contour<5>;
+        const int grid = num_sms() * 16;
+        NS_LAUNCH(NS_KERNEL_CHAIN_CONTOUR, k1, grid, kContourThreads, 0, s, *curves, cp, plan, order, knots, st, dg,
+                  cap->gaussians, out->dkey, dknots, out->dcolor);
+        NS_LAUNCH(NS_KERNEL_CHAIN_CONTOUR, k2, grid, kContourThreads, 0, s, *curves, cp, plan, order, knots, st, dg,
+                  cap->gaussians, out->dkey, dknots, out->dcolor);
+        NS_LAUNCH(NS_KERNEL_CHAIN_CONTOUR, k3, grid, kContourThreads, 0, s, *curves, cp, plan, order, knots, st, dg,
+                  cap->gaussians, out->dkey, dknots, out->dcolor);
+        NS_LAUNCH(NS_KERNEL_CHAIN_CONTOUR, k4, grid, kContourThreads, 0, s, *curves, cp, plan, order, knots, st, dg,
+                  cap->gaussians, out->dkey, dknots, out->dcolor);
+        NS_LAUNCH(NS_KERNEL_CHAIN_CONTOUR, k5, grid, kContourThreads, 0, s, *curves, cp, plan, order, knots, st, dg,
+                  cap->gaussians, out->dkey, dknots, out->dcolor);
+      }
       if (L.bcap > 0)
         NS_LAUNCH(NS_KERNEL_CHAIN_BOUNDARY, k_chain_boundary, num_sms() * 4, 256, 0, s, *curves, plan, knots, st, dbpts, out->dkey, dknots);
       NS_LAUNCH(NS_KERNEL_KNOT_GRADS, k_knot_grads, (L.nc + 3) / 4, 128, 0, s, *curves, plan, dknots, out->dtau);
