@@ -206,12 +206,12 @@ class Step:
         return int(self.sp.count.item())
 
 
-def autotune(torch, scene, tiles, capacity, steps=3):
+def autotune(torch, scene, tiles, capacity, steps=3, adam=False):
     """Tile size by timing whole steps; pixels per thread of the blend kernels
     by the library's ns_autotune_blend on each tile's workspace."""
     best, best_ms, table = None, None, {}
     for tile in tiles:
-        st = Step(scene, capacity, raster=dict(scene.raster, tile=tile))
+        st = Step(scene, capacity, raster=dict(scene.raster, tile=tile), adam=adam)
         st()
         st.sp.autotune_blend(st.key, st.tau, st.color, st.dimage, repeats=3)
         st()
@@ -401,7 +401,8 @@ def run_long_spline(torch, args):
     events)."""
     from paper_2606_31764_b300 import binding as B
     sc = scenes.config3()
-    st = Step(sc, capacity=(3_000_000, 12_000_000, 16), adam=True)
+    st, tuning = autotune(torch, sc, [int(x) for x in args.tiles.split(",")], capacity=(3_000_000, 24_000_000, 16),
+                          adam=True)
     st()
     K = max(3, args.steps)
     prof = ["emit", "bin_emit", "radix_scatter", "blend_fwd", "blend_bwd", "chain_contour"]
@@ -432,7 +433,7 @@ def run_long_spline(torch, args):
     rep = st.sp.report()
     return dict(workload="long-spline-512: 256 open cubic strokes, 64-512 key points, 512x512 gray, + Adam",
                 gaussians_per_step=G, pairs_per_step=int(rep.pairs), ms_per_step=round(ms, 4),
-                gaussians_per_s=round(G / (ms / 1e3), 1),
+                gaussians_per_s=round(G / (ms / 1e3), 1), autotune=tuning,
                 kernels={k: round(float(np.mean([a.elapsed_time(b) for a, b in ev[k]])), 4) for k in prof})
 
 
