@@ -214,8 +214,11 @@ ns_status splat_forward(const ns_curves* curves, const ns_gaussians* g,
  * the key points, knot intervals, colours and opacities; counts, spans, grid
  * placement, nearest segments and winding signs are held fixed.
  *   dL_dimage: device, same layout as the image.
- *   dgauss: device [g->capacity*8] or NULL: {dmu_x, dmu_y, dsigma, dopacity,
- *     dr, dg, db, 0} per Gaussian, zeroed and written by this call.
+ *   dgauss: device [g->capacity*8] or NULL: {dmu_x, dmu_y, dsigma, 0,
+ *     dopacity, dr, dg, db} per Gaussian, zeroed and written by this call.
+ *     When dgauss is NULL and `out` is given, the workspace holds them and the
+ *     centre and sigma gradients of fill Gaussians, which the chain does not
+ *     use (their grid is fixed), are not computed.
  *   zero_outputs: 1 zeroes *out before accumulating, 0 adds to it.
  */
 ns_status splat_backward(const ns_curves* curves, const ns_gaussians* g,

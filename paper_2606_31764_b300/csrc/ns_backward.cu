@@ -28,7 +28,7 @@ namespace ns {
 
 ns_status launch_blend_bwd(const Layout& L, const ns_curves* curves, const ns_gaussians* g,
                            const ns_raster_params* rp, const float* dimage, float* dgauss, void* ws,
-                           cudaStream_t s);
+                           cudaStream_t s, int full_grads);
 bool raster_params_ok(const ns_raster_params* rp);
 
 constexpr int kWin = 1024;   // control points (and knots) per task window in shared memory
@@ -135,9 +135,10 @@ __global__ void __launch_bounds__(256) k_chain(ns_curves cv, ChainParams cp, con
     __syncthreads();
     float dO = 0.f;
     const int aux = valid ? gaux[g] : 0;
-    if (valid && g0.w != 0.f && aux == kAuxDeep) {
-      dO = g0.w;   // sigmoid exactly 1: the opacity gradient passes through, none reaches the boundary
-    } else if (valid && g0.w != 0.f) {   // no opacity gradient: nothing reaches the curve but its colour
+    const float gop = g1.x;   // row layout {dmu_x, dmu_y, dsigma, 0, do, dr, dg, db}
+    if (valid && gop != 0.f && aux == kAuxDeep) {
+      dO = gop;   // sigmoid exactly 1: the opacity gradient passes through, none reaches the boundary
+    } else if (valid && gop != 0.f) {   // no opacity gradient: nothing reaches the curve but its colour
       const float o = cv.color[4 * c + 3];
       const bool inside = aux >= 0;
       const int i0 = inside ? aux : ~aux;
@@ -152,8 +153,8 @@ __global__ void __launch_bounds__(256) k_chain(ns_curves cv, ChainParams cp, con
       const float d = sqrtf(dx * dx + dy * dy);
       const float sdf = inside ? d : -d;
       const float sig = 1.f / (1.f + __expf(-(cp.gamma / cp.h * sdf)));
-      dO = sig * g0.w;
-      const float dsdf = g0.w * o * sig * (1.f - sig) * (cp.gamma / cp.h);
+      dO = sig * gop;
+      const float dsdf = gop * o * sig * (1.f - sig) * (cp.gamma / cp.h);
       const float dd = inside ? dsdf : -dsdf;
       if (d > 0.f && dd != 0.f) {
         // d = |q - b0 - t e|, t at its optimum: dd/db0 = -(1-t) n, dd/db1 = -t n
@@ -173,7 +174,7 @@ __global__ void __launch_bounds__(256) k_chain(ns_curves cv, ChainParams cp, con
       }
     }
     {
-      const float v[8] = {0.f, 0.f, g1.x, g1.y, g1.z, dO, 0.f, 0.f};
+      const float v[8] = {0.f, 0.f, g1.y, g1.z, g1.w, dO, 0.f, 0.f};
       const float tot = warp_sum8(v);
       const int lane = threadIdx.x & 31;
       if ((lane & 3) == 0 && (lane >> 2) >= 2 && (lane >> 2) < 6 && tot != 0.f) atomicAdd(&s_red[lane >> 2], tot);
@@ -243,10 +244,10 @@ __device__ void chain_contour_run(const ns_curves& cv, const CurveRef& cr, const
     if (l >= pl.count || g >= gcap) break;
     const float4 g0 = reinterpret_cast<const float4*>(dgauss)[2 * g];
     const float4 g1 = reinterpret_cast<const float4*>(dgauss)[2 * g + 1];
-    dcol.x += g1.x;
-    dcol.y += g1.y;
-    dcol.z += g1.z;
-    dcol.w += g0.w;
+    dcol.x += g1.y;   // row layout {dmu_x, dmu_y, dsigma, 0, do, dr, dg, db}
+    dcol.y += g1.z;
+    dcol.z += g1.w;
+    dcol.w += g1.x;
     if (g0.x == 0.f && g0.y == 0.f && g0.z == 0.f) continue;   // no geometric gradient
     const float u = contour_u(pl, l, cp.kappa);
     const float t = contour_t(pl, l, cp.kappa);
@@ -443,7 +444,9 @@ extern "C" ns_status splat_backward(const ns_curves* curves, const ns_gaussians*
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   float* dg = dgauss ? dgauss : at<float>(ws, L.o_dgauss);
   cudaMemsetAsync(dg, 0, sizeof(float) * 8 * (size_t)L.gcap, s);
-  launch_blend_bwd(L, curves, g, rp, dL_dimage, dg, ws, s);
+  // the centre and sigma gradients of fill Gaussians are needed only when the
+  // caller asked for the per-Gaussian gradients themselves
+  launch_blend_bwd(L, curves, g, rp, dL_dimage, dg, ws, s, dgauss != nullptr || out == nullptr);
   if (out) {
     DevState* st = at<DevState>(ws, L.o_state);
     const CurvePlan* plan = at<CurvePlan>(ws, L.o_plan);

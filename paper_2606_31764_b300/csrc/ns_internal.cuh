@@ -292,6 +292,25 @@ __device__ __forceinline__ float warp_sum8(const float v[8]) {
   return d;
 }
 
+// Sum of 4 values over the 32 lanes in 6 shuffles (the same exchange scheme):
+// on return value k of the total sits in the lanes with (lane >> 3) == k.
+__device__ __forceinline__ float warp_sum4(const float v[4]) {
+  const int lane = threadIdx.x & 31;
+  const bool h16 = lane & 16, h8 = lane & 8;
+  float b[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float send = h16 ? v[i] : v[i + 2];
+    const float keep = h16 ? v[i + 2] : v[i];
+    b[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  float d = (h8 ? b[1] : b[0]) + __shfl_xor_sync(0xffffffffu, h8 ? b[0] : b[1], 8);
+  d += __shfl_xor_sync(0xffffffffu, d, 4);
+  d += __shfl_xor_sync(0xffffffffu, d, 2);
+  d += __shfl_xor_sync(0xffffffffu, d, 1);
+  return d;
+}
+
 // Runtime degree -> template dispatch.
 #define NS_DISPATCH_P(p, ...)                     \
   switch (p) {                                    \

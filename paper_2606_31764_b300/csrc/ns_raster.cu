@@ -102,8 +102,9 @@ __device__ __forceinline__ float reach2(float sigma, float o, float log_amin) {
 
 // Counts tiles per Gaussian and prepares the per-Gaussian blend constants.
 __global__ void __launch_bounds__(256) k_bin_count(const float4* __restrict__ rec, const int* __restrict__ gcurve,
-                                                   const int* __restrict__ gcount, BinParams bp, int* bsum,
-                                                   DevState* st, float4* prep, float2* reach) {
+                                                   const int* __restrict__ gaux, const int* __restrict__ gcount,
+                                                   BinParams bp, int* bsum, DevState* st, float4* prep,
+                                                   float2* reach) {
   __shared__ int s_warp[32];
   const int G = min(*gcount, bp.gcap);
   const long long base = (long long)blockIdx.x * kBinItems;
@@ -120,7 +121,10 @@ __global__ void __launch_bounds__(256) k_bin_count(const float4* __restrict__ re
       cnt += nt;
       if (nt) {   // only binned Gaussians are ever read by the blend kernels
         prep[g] = make_float4(r.x, r.y, ncoef(r.z), r.w);
-        reach[g] = make_float2(reach2(r.z, r.w, bp.log_amin), 1.f / r.z);
+        // 1/sigma, negative for fill Gaussians (their centre and sigma get no
+        // gradient through the chain, so the adjoint may skip them)
+        const float isg = 1.f / r.z;
+        reach[g] = make_float2(reach2(r.z, r.w, bp.log_amin), gaux && gaux[g] != -1 ? -isg : isg);
       }
       culled += (r.z > 0.f && r.w < bp.alpha_min) ? 1 : 0;
     }
@@ -384,7 +388,7 @@ __global__ void k_ranges(const uint32_t* __restrict__ keys, const DevState* st, 
 //
 // Per-Gaussian constants are prepared once by k_bin_count:
 //   prep  = {mu_x, mu_y, ncoef = -1/(2 sigma^2), o}
-//   reach = {squared reach, 1/sigma}
+//   reach = {squared reach, 1/sigma, negative for fill Gaussians}
 
 struct BlendParams {
   float alpha_min, alpha_max, t_min;
@@ -549,7 +553,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
     k_blend_bwd(const int2* __restrict__ ranges, const uint32_t* __restrict__ gid, const float4* __restrict__ prep,
                 const float2* __restrict__ reach, const int* __restrict__ gcurve, const float4* __restrict__ color,
                 BlendParams bp, const float* __restrict__ dimage, const float* __restrict__ Tfinal,
-                const int* __restrict__ nlast, float* dgauss, DevState* st) {
+                const int* __restrict__ nlast, float* dgauss, DevState* st, int full_grads) {
   using Gm = BlendGeom<TILE, PPT>;
   __shared__ float4 s_q[Gm::kWarps][32];
   __shared__ float4 s_c[Gm::kWarps][32];
@@ -605,6 +609,11 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
       const int b = 31 - __clz(mask);
       mask &= ~(1u << b);
       const float4 q = s_q[w][b];
+      const float isg_raw = s_isig[w][b];
+      // fill Gaussians (negative 1/sigma) need only the opacity and colour
+      // gradients unless the caller asked for every per-Gaussian gradient
+      const bool geo = full_grads || isg_raw > 0.f;
+      const float isg = fabsf(isg_raw);
       float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       bool contrib = false;
 #pragma unroll
@@ -619,35 +628,45 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
         const float wgt = a * T[k];
         const float4 cc = s_c[w][b];
         float da = (cc.x - Bk[k][0]) * dI[k][0];
-        v[4] += wgt * dI[k][0];
+        v[5] += wgt * dI[k][0];
         Bk[k][0] = a * cc.x + (1.f - a) * Bk[k][0];
         if (C == 3) {
           da += (cc.y - Bk[k][1]) * dI[k][1] + (cc.z - Bk[k][2]) * dI[k][2];
-          v[5] += wgt * dI[k][1];
-          v[6] += wgt * dI[k][2];
+          v[6] += wgt * dI[k][1];
+          v[7] += wgt * dI[k][2];
           Bk[k][1] = a * cc.y + (1.f - a) * Bk[k][1];
           Bk[k][2] = a * cc.z + (1.f - a) * Bk[k][2];
         }
         da *= T[k];
         if (__fmul_rn(q.w, e) < bp.alpha_max) {
-          const float isg = s_isig[w][b];
-          v[3] += e * da;
-          const float aa = da * a * isg * isg;   // dalpha/dmu = alpha (x - mu) / sigma^2
-          v[0] += aa * dx;
-          v[1] += aa * dy;
-          v[2] += aa * d2 * isg;                  // dalpha/dsigma = alpha d^2 / sigma^3
+          v[4] += e * da;
+          if (geo) {
+            const float aa = da * a * isg * isg;   // dalpha/dmu = alpha (x - mu) / sigma^2
+            v[0] += aa * dx;
+            v[1] += aa * dy;
+            v[2] += aa * d2 * isg;                  // dalpha/dsigma = alpha d^2 / sigma^3
+          }
         }
       }
       if (__any_sync(0xffffffffu, contrib)) {
-        // value k of the warp total sits in lane 4k; gather 0..3 into lane 0
-        // and 4..7 into lane 16, one 16-byte vector reduction each
-        const float t = warp_sum8(v);
-        const float t1 = __shfl_down_sync(0xffffffffu, t, 4);
-        const float t2 = __shfl_down_sync(0xffffffffu, t, 8);
-        const float t3 = __shfl_down_sync(0xffffffffu, t, 12);
-        if ((lane & 15) == 0) {
-          float* d = dgauss + (long long)s_id[w][b] * 8 + (lane >> 2);
-          red_add_v4(d, t, t1, t2, t3);
+        if (geo) {
+          // value k of the warp total sits in lane 4k; gather 0..3 into lane 0
+          // and 4..7 into lane 16, one 16-byte vector reduction each
+          const float t = warp_sum8(v);
+          const float t1 = __shfl_down_sync(0xffffffffu, t, 4);
+          const float t2 = __shfl_down_sync(0xffffffffu, t, 8);
+          const float t3 = __shfl_down_sync(0xffffffffu, t, 12);
+          if ((lane & 15) == 0) {
+            float* d = dgauss + (long long)s_id[w][b] * 8 + (lane >> 2);
+            red_add_v4(d, t, t1, t2, t3);
+          }
+        } else {
+          // only {do, dr, dg, db}: value k of the warp total sits in lane 8k
+          const float t = warp_sum4(v + 4);
+          const float t1 = __shfl_down_sync(0xffffffffu, t, 8);
+          const float t2 = __shfl_down_sync(0xffffffffu, t, 16);
+          const float t3 = __shfl_down_sync(0xffffffffu, t, 24);
+          if (lane == 0) red_add_v4(dgauss + (long long)s_id[w][b] * 8 + 4, t, t1, t2, t3);
         }
       }
     }
@@ -677,12 +696,12 @@ template <int C>
 static void launch_bwd(int tile, int ppt, int grid, cudaStream_t s, const int2* ranges, const uint32_t* gid,
                        const float4* prep, const float2* reach, const int* gcurve, const float4* col,
                        const BlendParams& bp, const float* dimage, const float* Tf, const int* nl, float* dgauss,
-                       DevState* st) {
+                       DevState* st, int full_grads) {
 #define NS_BWD(TL, PP)                                                                                 \
   {                                                                                                      \
     auto kern = &k_blend_bwd<TL, PP, C>;                                                                 \
     NS_LAUNCH(NS_KERNEL_BLEND_BWD, kern, grid, (BlendGeom<TL, PP>::kThreads), 0, s, ranges, gid, prep,  \
-              reach, gcurve, col, bp, dimage, Tf, nl, dgauss, st);                                      \
+              reach, gcurve, col, bp, dimage, Tf, nl, dgauss, st, full_grads);                          \
   }
   if (tile == 8) { if (ppt == 1) NS_BWD(8, 1) else NS_BWD(8, 2) }
   else if (tile == 16) { if (ppt == 1) NS_BWD(16, 1) else if (ppt == 2) NS_BWD(16, 2) else NS_BWD(16, 4) }
@@ -793,7 +812,7 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
   bp.gcap = int(L.gcap);
   const int bin_blocks = int(L.bin_blocks);
   if (bin_blocks > 0) {
-    NS_LAUNCH(NS_KERNEL_BIN_COUNT, k_bin_count, bin_blocks, 256, 0, s, rec, g->curve, g->count, bp, bsum, st,
+    NS_LAUNCH(NS_KERNEL_BIN_COUNT, k_bin_count, bin_blocks, 256, 0, s, rec, g->curve, g->aux, g->count, bp, bsum, st,
               at<float4>(ws, L.o_prep), at<float2>(ws, L.o_reach));
   }
   NS_LAUNCH(NS_KERNEL_SCAN, k_scan_small, 1, 1024, 0, s, bsum, g->count, int(L.gcap), kBinItems, st, cap->pairs);
@@ -837,7 +856,7 @@ namespace ns {
 // Blend adjoint, used by splat_backward (ns_backward.cu).
 ns_status launch_blend_bwd(const Layout& L, const ns_curves* curves, const ns_gaussians* g,
                            const ns_raster_params* rp, const float* dimage, float* dgauss, void* ws,
-                           cudaStream_t s) {
+                           cudaStream_t s, int full_grads) {
   const RasterPlan rpn = radix_plan(L.n_tiles);
   const uint32_t* vsorted = (rpn.passes & 1) ? at<uint32_t>(ws, L.o_v1) : at<uint32_t>(ws, L.o_v0);
   const int2* ranges = at<int2>(ws, L.o_ranges);
@@ -851,10 +870,10 @@ ns_status launch_blend_bwd(const Layout& L, const ns_curves* curves, const ns_ga
   const int ppt = resolve_ppt(rp->tile, rp->ppt_bwd);
   if (L.C == 3)
     launch_bwd<3>(rp->tile, ppt, L.n_tiles, s, ranges, vsorted, at<float4>(ws, L.o_prep), at<float2>(ws, L.o_reach),
-                  g->curve, col, blp, dimage, Tf, nl, dgauss, st);
+                  g->curve, col, blp, dimage, Tf, nl, dgauss, st, full_grads);
   else
     launch_bwd<1>(rp->tile, ppt, L.n_tiles, s, ranges, vsorted, at<float4>(ws, L.o_prep), at<float2>(ws, L.o_reach),
-                  g->curve, col, blp, dimage, Tf, nl, dgauss, st);
+                  g->curve, col, blp, dimage, Tf, nl, dgauss, st, full_grads);
   return NS_OK;
 }
 bool raster_params_ok(const ns_raster_params* rp) { return check_raster(rp); }
@@ -895,8 +914,8 @@ extern "C" ns_status ns_autotune_blend(const ns_curves* curves, const ns_gaussia
     else launch_fwd<1>(rp->tile, ppt, L.n_tiles, s, ranges, vsorted, prep, reach, g->curve, col, blp, image, Tf, nl, st);
   };
   auto bwd = [&](int ppt) {
-    if (L.C == 3) launch_bwd<3>(rp->tile, ppt, L.n_tiles, s, ranges, vsorted, prep, reach, g->curve, col, blp, dL_dimage, Tf, nl, dg, st);
-    else launch_bwd<1>(rp->tile, ppt, L.n_tiles, s, ranges, vsorted, prep, reach, g->curve, col, blp, dL_dimage, Tf, nl, dg, st);
+    if (L.C == 3) launch_bwd<3>(rp->tile, ppt, L.n_tiles, s, ranges, vsorted, prep, reach, g->curve, col, blp, dL_dimage, Tf, nl, dg, st, 0);
+    else launch_bwd<1>(rp->tile, ppt, L.n_tiles, s, ranges, vsorted, prep, reach, g->curve, col, blp, dL_dimage, Tf, nl, dg, st, 0);
   };
   auto time_best = [&](bool backward) {
     int best = 0;

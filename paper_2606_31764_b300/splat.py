@@ -165,8 +165,11 @@ class Splatter:
         if grads is None:
             grads = (torch.empty_like(key), torch.empty_like(tau), torch.empty_like(color))
         out = B.NsCurveGrads(_ptr(grads[0]), _ptr(grads[1]), _ptr(grads[2])) if chain else None
+        # per-Gaussian gradients (rows {dmu_x, dmu_y, dsigma, 0, do, dr, dg, db}) go
+        # to self.dgauss when no chain is asked for; with the chain the workspace
+        # holds them and the library skips what the chain does not use
         B.call("splat_backward", C.byref(cs), C.byref(self.g), C.byref(self.sp), C.byref(self.rp),
-               C.byref(self.cap), _ptr(dimage.contiguous()), _ptr(self.dgauss),
+               C.byref(self.cap), _ptr(dimage.contiguous()), None if chain else _ptr(self.dgauss),
                C.byref(out) if out is not None else None, C.c_int32(1), _ptr(self.ws),
                C.c_size_t(self.ws_bytes), _stream())
         return grads

@@ -90,3 +90,36 @@ def test_autograd_function_matches_oracle():
     dk = k.grad.cpu().numpy().reshape(-1, 4)
     for j in range(4):
         assert _rel_ok(dk[:, j], ref["dkey"][:, j])
+
+
+def test_empty_scenes_and_empty_batch():
+    """A batch whose middle scene has no curves renders that scene as the
+    background and gets the other scenes right; a batch with no curves at all
+    renders only background and gives empty gradients."""
+    import torch
+    from paper_2606_31764_b300.splat import Splatter, scene_tensors
+    base = scenes.small_closed(58, n_curves=2, size=40, filled=True, h=2.0, n_scenes=3)
+    b = scenes._Builder(3, base.height, base.width, base.channels)
+    for s in (0, 2):
+        for cv in range(base.scene_curve_offset[s], base.scene_curve_offset[s + 1]):
+            k0, k1 = base.key_offset[cv], base.key_offset[cv + 1]
+            t0, t1 = base.tau_offset[cv], base.tau_offset[cv + 1]
+            b.add(s, int(base.degree[cv]), base.key[k0:k1], base.tau[t0:t1], base.color[cv], True, True)
+    sc = b.build("gap", base.target, dict(base.sample), dict(base.raster))
+    assert sc.scene_curve_offset[1] == sc.scene_curve_offset[2]
+    ref = op.loss_and_grads(sc)
+    out = run_step(sc)
+    assert out["report"].status == 0
+    bg = np.asarray(sc.raster["bg"], np.float32)
+    assert np.array_equal(out["image"][1], np.broadcast_to(bg, out["image"][1].shape))
+    assert np.abs(out["image"] - ref["image"]).max() <= 1e-3
+    assert _rel_ok(out["dkey"][:, 0], ref["dkey"][:, 0]) and _rel_ok(out["dcolor"], ref["dcolor"])
+    # no curves at all
+    e = scenes._Builder(1, 24, 24, 3).build("empty", np.ones((1, 24, 24, 3), np.float32), dict(base.sample),
+                                             dict(base.raster))
+    sp = Splatter(e)
+    k, t, c = (torch.zeros(0, device="cuda"),) * 3
+    img = sp.forward(k, t, c)
+    torch.cuda.synchronize()
+    assert sp.report().status == 0 and int(sp.count.item()) == 0
+    assert torch.equal(img, torch.ones_like(img))
