@@ -87,6 +87,9 @@ typedef struct {
   int32_t kappa;    /* endpoint replicas of open curves (§3.2, last paragraph) */
   int32_t nl_mult;  /* N_L = nl_mult * max(width, height) arc-length nodes (Eq. 3) */
   int32_t fill_rule;/* 0: inside iff winding number > 0.5 (Eq. S3); 1: nonzero */
+  float fill_cull;  /* > 0: fill points provably outside with opacity below this
+                       value (pass the rasterizer's alpha_min) get opacity 0 without
+                       an exact distance; they bin to no tile either way.  0: off */
 } ns_sample_params;
 
 /* Rasterizer settings (§3.4). */
@@ -119,8 +122,9 @@ typedef struct {
   int32_t* curve;   /* device [capacity]: owning curve (selects colour and scene) */
   int32_t* aux;     /* device [capacity]: fills: nearest boundary segment i*, as
                        i* (inside) or ~i* (outside), or 0x7fffffff for a point so
-                       deep inside that its sigmoid (Eq. 7) is exactly 1 in FP32
-                       (no segment needed); contours: -1 */
+                       deep inside that its sigmoid (Eq. 7) is exactly 1 in FP32,
+                       or 0x80000000 for a point culled by fill_cull (no segment
+                       needed for either); contours: -1 */
   int32_t* count;   /* device scalar: records in use */
 } ns_gaussians;
 

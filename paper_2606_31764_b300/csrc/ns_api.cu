@@ -215,6 +215,7 @@ ns_sample_params ns_default_sample_params(void) {
   p.kappa = 4;
   p.nl_mult = 3;
   p.fill_rule = 0;
+  p.fill_cull = 0.f;
   return p;
 }
 

@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(256) k_chain(ns_curves cv, ChainParams cp, con
     const float gop = g1.x;   // row layout {dmu_x, dmu_y, dsigma, 0, do, dr, dg, db}
     if (valid && gop != 0.f && aux == kAuxDeep) {
       dO = gop;   // sigmoid exactly 1: the opacity gradient passes through, none reaches the boundary
-    } else if (valid && gop != 0.f) {   // no opacity gradient: nothing reaches the curve but its colour
+    } else if (valid && gop != 0.f && aux != kAuxFar) {   // no opacity gradient: only the colour
       const float o = cv.color[4 * c + 3];
       const bool inside = aux >= 0;
       const int i0 = inside ? aux : ~aux;

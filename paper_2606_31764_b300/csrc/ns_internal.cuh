@@ -23,6 +23,9 @@ enum CurveKind : int { kNone = 0, kOpen = 1, kClosedStroke = 2, kFill = 3 };
 // aux code of a fill Gaussian whose grid point lies so deep inside that its
 // sigmoid is exactly 1 in FP32: no nearest segment is recorded (none is needed)
 constexpr int kAuxDeep = 0x7fffffff;
+// aux code of a fill Gaussian provably outside with opacity below the cull
+// threshold (written with opacity 0; it bins to no tile)
+constexpr int kAuxFar = int(0x80000000u);
 
 // Device-side status and counters, at the start of the workspace.
 struct DevState {

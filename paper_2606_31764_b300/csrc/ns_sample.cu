@@ -421,11 +421,18 @@ __global__ void __launch_bounds__(256, 4) k_emit(ns_curves cv, ns_sample_params 
     const int B = pl.M;
     float best = FLT_MAX;
     int arg = 0, wn = 0;
-    bool deep = false;
+    bool deep = false, far = false;
     // sigmoid(z) rounds to exactly 1 in FP32 once exp(-z) <= 2^-24 (z >= 16.64);
     // deep2 is the squared distance beyond which z >= 17 with margin
     const float dsat = 17.f * sp.h / sp.gamma;
     const float deep2 = dsat * dsat * 1.001f + 1e-3f;
+    // outside, o sigmoid(-gamma d / h) < fill_cull once d > (h/gamma) ln(o/fill_cull - 1);
+    // far2 adds a margin of 0.1 in z (FLT_MAX: no culling)
+    float far2 = FLT_MAX;
+    if (sp.fill_cull > 0.f && o > 1.01f * sp.fill_cull) {
+      const float dcut = sp.h / sp.gamma * (logf(o / sp.fill_cull - 1.f) + 0.1f);
+      if (dcut > 0.f) far2 = dcut * dcut;
+    }
     for (int base = 0; base < B; base += kSegBatch) {
       const int nseg = min(kSegBatch, B - base);
       const int ncl = (nseg + kCluster - 1) / kCluster;
@@ -472,6 +479,8 @@ __global__ void __launch_bounds__(256, 4) k_emit(ns_curves cv, ns_sample_params 
         const bool inside = sp.fill_rule == 0 ? wn > 0 : wn != 0;
         if (inside && lbmin > deep2) {
           deep = true;
+        } else if (!inside && lbmin > far2) {
+          far = true;
         } else {
           // the nearest box first: its best distance prunes most other clusters
           cluster_nearest(seg, segb, clmin, nseg, base, qx, qy, best, arg);
@@ -504,7 +513,9 @@ __global__ void __launch_bounds__(256, 4) k_emit(ns_curves cv, ns_sample_params 
     if (valid) {
       const bool inside = sp.fill_rule == 0 ? wn > 0 : wn != 0;
       float sig = 1.f;
-      if (!deep) {
+      if (far) {
+        sig = 0.f;
+      } else if (!deep) {
         const float d = sqrtf(best);
         const float sdf = inside ? d : -d;
         const float z = sp.gamma / sp.h * sdf;
@@ -512,7 +523,7 @@ __global__ void __launch_bounds__(256, 4) k_emit(ns_curves cv, ns_sample_params 
       }
       rec[g] = make_float4(qx, qy, sp.eta * sp.h / sp.rho, o * sig);
       gcurve[g] = c;
-      gaux[g] = deep ? kAuxDeep : (inside ? arg : ~arg);
+      gaux[g] = deep ? kAuxDeep : (far ? kAuxFar : (inside ? arg : ~arg));
     }
   }
 }

@@ -29,6 +29,7 @@ def sample_params(d: dict) -> B.NsSampleParams:
     p.kappa = int(d["kappa"])
     p.nl_mult = int(d["nl_mult"])
     p.fill_rule = int(d["fill_rule"])
+    p.fill_cull = float(d.get("fill_cull", 0.0))
     return p
 
 
@@ -112,6 +113,9 @@ class Splatter:
         self.device = device
         self.sp = sample_params(sample or scene.sample)
         self.rp = raster_params(raster or scene.raster)
+        if "fill_cull" not in (sample or scene.sample):
+            # fill points that cannot reach the rasterizer's alpha_min need no exact SDF
+            self.sp.fill_cull = float(self.rp.alpha_min)
         self.cap = B.NsCapacity(*[int(x) for x in capacity])
         self.image = torch.empty(scene.n_scenes, scene.height, scene.width, scene.channels, device=device)
         self._alloc()
