@@ -381,7 +381,7 @@ __device__ __forceinline__ int cluster_crossings(const float4* seg, const float2
 }
 
 // Persistent: each block iteration handles one task of 256 Gaussians of one curve.
-__global__ void __launch_bounds__(256, 4) k_emit(ns_curves cv, ns_sample_params sp, const CurvePlan* __restrict__ plan,
+__global__ void __launch_bounds__(256, 3) k_emit(ns_curves cv, ns_sample_params sp, const CurvePlan* __restrict__ plan,
                                               const int* __restrict__ order, const float* __restrict__ knots,
                                               const float2* __restrict__ bpts, const DevState* __restrict__ st,
                                               float4* rec, int* gcurve, int* gaux, long long gcap, long long bcap) {
@@ -461,37 +461,73 @@ __global__ void __launch_bounds__(256, 4) k_emit(ns_curves cv, ns_sample_params 
         cbox[cl] = make_float4(x0, x1, y0, y1);
       }
       __syncthreads();
-      if (valid && B <= kSegBatch) {
-        // the whole polyline is staged: first the winding number and a lower
-        // bound of the distance (nearest cluster box), then the distance itself
-        // unless the point is provably deep inside, where the sigmoid of Eq. 7
-        // is exactly 1 in FP32 and the nearest segment cannot matter
-        float lbmin = FLT_MAX;
-        int clmin = 0;
-        for (int cl = 0; cl < ncl; ++cl) {
-          const float4 bb = cbox[cl];
-          const float bx = fmaxf(fmaxf(bb.x - qx, qx - bb.y), 0.f);
-          const float by = fmaxf(fmaxf(bb.z - qy, qy - bb.w), 0.f);
-          const float lb2 = bx * bx + by * by;
-          if (lb2 < lbmin) { lbmin = lb2; clmin = cl; }
-          if (bb.z <= qy && bb.w > qy && bb.y >= qx - 0.01f) wn += cluster_crossings(seg, segb, cl, nseg, qx, qy);
+      if (B <= kSegBatch) {
+        // The whole polyline is staged.  The warp first works on the box around
+        // its 32 grid points: the nearest cluster box bounds every point's
+        // distance from below, and only clusters straddling the box's rows can
+        // add crossings.  A warp that is provably deep inside (sigmoid exactly
+        // 1) or far outside (below fill_cull) needs no distance search at all.
+        const int lane = threadIdx.x & 31;
+        float wx0 = valid ? qx : FLT_MAX, wx1 = valid ? qx : -FLT_MAX;
+        float wy0 = valid ? qy : FLT_MAX, wy1 = valid ? qy : -FLT_MAX;
+        for (int o = 16; o > 0; o >>= 1) {
+          wx0 = fminf(wx0, __shfl_xor_sync(0xffffffffu, wx0, o));
+          wx1 = fmaxf(wx1, __shfl_xor_sync(0xffffffffu, wx1, o));
+          wy0 = fminf(wy0, __shfl_xor_sync(0xffffffffu, wy0, o));
+          wy1 = fmaxf(wy1, __shfl_xor_sync(0xffffffffu, wy1, o));
         }
+        float lbw = FLT_MAX;
+        for (int c0 = 0; c0 < ncl; c0 += 32) {
+          const int cl = c0 + lane;
+          bool cross = false;
+          if (cl < ncl) {
+            const float4 bb = cbox[cl];
+            const float bx = fmaxf(fmaxf(bb.x - wx1, wx0 - bb.y), 0.f);
+            const float by = fmaxf(fmaxf(bb.z - wy1, wy0 - bb.w), 0.f);
+            lbw = fminf(lbw, bx * bx + by * by);
+            cross = bb.z <= wy1 && bb.w > wy0 && bb.y >= wx0 - 0.01f;
+          }
+          unsigned int m = __ballot_sync(0xffffffffu, cross);
+          while (m) {
+            const int k = c0 + __ffs(m) - 1;
+            m &= m - 1;
+            const float4 bb = cbox[k];
+            if (valid && bb.z <= qy && bb.w > qy && bb.y >= qx - 0.01f)
+              wn += cluster_crossings(seg, segb, k, nseg, qx, qy);
+          }
+        }
+        for (int o = 16; o > 0; o >>= 1) lbw = fminf(lbw, __shfl_xor_sync(0xffffffffu, lbw, o));
         const bool inside = sp.fill_rule == 0 ? wn > 0 : wn != 0;
-        if (inside && lbmin > deep2) {
+        if (inside && lbw > deep2) {
           deep = true;
-        } else if (!inside && lbmin > far2) {
+        } else if (!inside && lbw > far2) {
           far = true;
-        } else {
-          // the nearest box first: its best distance prunes most other clusters
-          cluster_nearest(seg, segb, clmin, nseg, base, qx, qy, best, arg);
+        } else if (valid) {
+          float lbmin = FLT_MAX;
+          int clmin = 0;
           for (int cl = 0; cl < ncl; ++cl) {
-            if (cl == clmin) continue;
             const float4 bb = cbox[cl];
             const float bx = fmaxf(fmaxf(bb.x - qx, qx - bb.y), 0.f);
             const float by = fmaxf(fmaxf(bb.z - qy, qy - bb.w), 0.f);
             const float lb2 = bx * bx + by * by;
-            if (lb2 > best + 1e-3f * (lb2 + 1.f)) continue;
-            cluster_nearest(seg, segb, cl, nseg, base, qx, qy, best, arg);
+            if (lb2 < lbmin) { lbmin = lb2; clmin = cl; }
+          }
+          if (inside && lbmin > deep2) {
+            deep = true;
+          } else if (!inside && lbmin > far2) {
+            far = true;
+          } else {
+            // the nearest box first: its best distance prunes most other clusters
+            cluster_nearest(seg, segb, clmin, nseg, base, qx, qy, best, arg);
+            for (int cl = 0; cl < ncl; ++cl) {
+              if (cl == clmin) continue;
+              const float4 bb = cbox[cl];
+              const float bx = fmaxf(fmaxf(bb.x - qx, qx - bb.y), 0.f);
+              const float by = fmaxf(fmaxf(bb.z - qy, qy - bb.w), 0.f);
+              const float lb2 = bx * bx + by * by;
+              if (lb2 > best + 1e-3f * (lb2 + 1.f)) continue;
+              cluster_nearest(seg, segb, cl, nseg, base, qx, qy, best, arg);
+            }
           }
         }
       } else if (valid) {
