@@ -114,10 +114,10 @@ __global__ void __launch_bounds__(256) k_chain(ns_curves cv, ChainParams cp, con
     const int c = curve_of_task(plan, order, nc, task, true);
     const CurvePlan pl = plan[c];
     const CurveRef cr = curve_ref(cv, c);
-    int ix, iy;
-    const int l = fill_task_point(pl.nx, pl.ny, task - pl.chunk_off, ix, iy);
+    const int l0 = (task - pl.chunk_off) * kChunk;
+    const int l = l0 + threadIdx.x;
     const long long g = (long long)pl.g_off + l;
-    const bool valid = l >= 0 && l < pl.count && g < gcap;
+    const bool valid = l < pl.count && g < gcap;
     __syncthreads();
     if (threadIdx.x < 8) s_red[threadIdx.x] = 0.f;
     float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0;

@@ -346,21 +346,6 @@ __device__ __forceinline__ float contour_t(const CurvePlan& pl, int l, int kappa
   return float(l) / float(pl.M);
 }
 
-// Fill tasks cover the curve's grid in 16 x 16 tiles; in a 256-thread block
-// warp w takes the 8 x 4 points at ((w & 1) * 8, (w >> 1) * 4) of the tile and
-// lane l the point (l & 7, l >> 3) there, so a warp's points are close
-// together.  Returns the row-major sample index, or -1 outside the grid.
-__device__ __forceinline__ int fill_tiles(int nx, int ny) { return ((nx + 15) >> 4) * ((ny + 15) >> 4); }
-
-__device__ __forceinline__ int fill_task_point(int nx, int ny, int task_in_curve, int& ix, int& iy) {
-  const int tcx = (nx + 15) >> 4;
-  const int tx = task_in_curve % tcx, ty = task_in_curve / tcx;
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  ix = tx * 16 + (w & 1) * 8 + (lane & 7);
-  iy = ty * 16 + (w >> 1) * 4 + (lane >> 3);
-  return (ix < nx && iy < ny) ? iy * nx + ix : -1;
-}
-
 // Task -> curve map.  Tasks are 256 Gaussians of one curve; fill tasks and
 // contour tasks are numbered separately, each kind in front-to-back curve
 // order, and a curve's chunk_off counts the tasks of its own kind before it.

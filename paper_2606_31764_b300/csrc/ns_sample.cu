@@ -8,10 +8,9 @@
 //   k_boundary      one block per filled curve: boundary polyline b_i, its
 //                   padded and clipped box, the fill grid size
 //   k_scan_gauss    one block: Gaussian and task offsets in front-to-back order
-//   k_emit          persistent: one task per block iteration; 256 contour
-//                   samples (Eq. 4-5), or a 16 x 16 tile of fill points with the
-//                   SDF of Eq. S1-S3 against the polyline staged in shared
-//                   memory (Eq. 6-7)
+//   k_emit          persistent: one 256-Gaussian task per block iteration;
+//                   contour samples (Eq. 4-5) or fill points with the SDF of
+//                   Eq. S1-S3 against the polyline staged in shared memory (Eq. 6-7)
 #include <cuda_runtime.h>
 #include <float.h>
 
@@ -313,7 +312,7 @@ __global__ void k_scan_gauss(int nc, CurvePlan* plan, const int* order, DevState
       nc, [&](int f) { return plan[order[f]].count; },
       [&](int f, long long off) { plan[order[f]].g_off = int(off < 0x7fffffff ? off : 0x7fffffff); });
   const long long ftasks = block_scan_items(
-      nc, [&](int f) { const CurvePlan& q = plan[order[f]]; return q.kind == kFill && q.count > 0 ? fill_tiles(q.nx, q.ny) : 0; },
+      nc, [&](int f) { const CurvePlan& q = plan[order[f]]; return q.kind == kFill ? (q.count + kChunk - 1) / kChunk : 0; },
       [&](int f, long long off) {
         CurvePlan& q = plan[order[f]];
         if (q.kind == kFill) q.chunk_off = int(off); else q.pad[0] = int(off);
@@ -399,11 +398,9 @@ __global__ void __launch_bounds__(256, 3) k_emit(ns_curves cv, ns_sample_params 
     const CurvePlan pl = plan[c];
     const CurveRef cr = curve_ref(cv, c);
     const float* U = knots + cr.knot0;
-    int ix = 0, iy = 0;
-    const int l = fill_task ? fill_task_point(pl.nx, pl.ny, task - pl.chunk_off, ix, iy)
-                            : (task - pl.chunk_off) * kChunk + threadIdx.x;
+    const int l = (task - pl.chunk_off) * kChunk + threadIdx.x;
     const long long g = (long long)pl.g_off + l;
-    const bool valid = l >= 0 && l < pl.count && g < gcap;
+    const bool valid = l < pl.count && g < gcap;
     const float o = cv.color[4 * c + 3];
     if (pl.kind != kFill) {
       if (valid) {
@@ -418,8 +415,9 @@ __global__ void __launch_bounds__(256, 3) k_emit(ns_curves cv, ns_sample_params 
     // fill point: grid row-major over the padded box; a curve whose polyline
     // did not fit the boundary capacity emits nothing (NS_ERR_CAPACITY is set)
     if ((long long)pl.b_off + pl.M > bcap) continue;
-    const float qx = pl.x0 + (float(ix) + 0.5f) * sp.h;
-    const float qy = pl.y0 + (float(iy) + 0.5f) * sp.h;
+    const int nxx = max(pl.nx, 1);
+    const float qx = pl.x0 + (float(l % nxx) + 0.5f) * sp.h;
+    const float qy = pl.y0 + (float(l / nxx) + 0.5f) * sp.h;
     const int B = pl.M;
     float best = FLT_MAX;
     int arg = 0, wn = 0;
