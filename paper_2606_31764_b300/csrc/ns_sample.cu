@@ -446,17 +446,19 @@ __global__ void __launch_bounds__(256, 3) k_emit(ns_curves cv, ns_sample_params 
         seg[s] = make_float4(b0.x, b0.y, ex, ey);
         segb[s] = make_float2(b1.y, ee > 0.f ? 1.f / ee : 0.f);
       }
-      // bounding box of each cluster of kCluster consecutive segments
+      __syncthreads();
+      // bounding box of each cluster of kCluster consecutive segments, from the
+      // staged segments: x over b0 and b0 + e, y over b0 and b1 (the values the
+      // distance and crossing tests use)
       for (int cl = threadIdx.x; cl < ncl; cl += blockDim.x) {
         float x0 = FLT_MAX, x1 = -FLT_MAX, y0 = FLT_MAX, y1 = -FLT_MAX;
         for (int k = cl * kCluster; k < min(nseg, (cl + 1) * kCluster); ++k) {
-          const int i = base + k;
-          const float2 b0 = bpts[pl.b_off + i];
-          const float2 b1 = bpts[pl.b_off + (i + 1 == B ? 0 : i + 1)];
-          x0 = fminf(x0, fminf(b0.x, b1.x));
-          x1 = fmaxf(x1, fmaxf(b0.x, b1.x));
-          y0 = fminf(y0, fminf(b0.y, b1.y));
-          y1 = fmaxf(y1, fmaxf(b0.y, b1.y));
+          const float4 sg = seg[k];
+          const float bx1 = sg.x + sg.z, by1 = segb[k].x;
+          x0 = fminf(x0, fminf(sg.x, bx1));
+          x1 = fmaxf(x1, fmaxf(sg.x, bx1));
+          y0 = fminf(y0, fminf(sg.y, by1));
+          y1 = fmaxf(y1, fmaxf(sg.y, by1));
         }
         cbox[cl] = make_float4(x0, x1, y0, y1);
       }
