@@ -21,6 +21,8 @@ namespace ns {
 constexpr int kPlanThreads = 128;
 constexpr int kSegBatch = 1024;   // boundary segments staged in shared memory per pass
 constexpr int kCluster = 8;       // consecutive segments per bounding-box cluster
+constexpr int kMaxRows = 40;      // grid rows of one fill task with scanline crossing tables
+constexpr int kMaxCross = 32;     // crossings of one row the table holds
 
 __device__ __forceinline__ float block_sum(float v, float* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -388,6 +390,9 @@ __global__ void __launch_bounds__(256, 3) k_emit(ns_curves cv, ns_sample_params 
   __shared__ float4 seg[kSegBatch];   // {b0.x, b0.y, e.x, e.y}
   __shared__ float2 segb[kSegBatch];  // {b1.y, 1/|e|^2 (0 for a zero-length segment)}
   __shared__ float4 cbox[kSegBatch / kCluster];  // {x0, x1, y0, y1} of each segment cluster
+  __shared__ float s_cx[kMaxRows][kMaxCross];    // scanline crossings of each row of a fill task
+  __shared__ signed char s_cd[kMaxRows][kMaxCross];
+  __shared__ int s_ncross[kMaxRows];
   const int n_fill = st->n_chunks;
   const int n_tasks = n_fill + st->n_ctasks;   // fill tasks (heavier) first
   const int nc = cv.n_curves;
@@ -464,11 +469,46 @@ __global__ void __launch_bounds__(256, 3) k_emit(ns_curves cv, ns_sample_params 
       }
       __syncthreads();
       if (B <= kSegBatch) {
-        // The whole polyline is staged.  The warp first works on the box around
-        // its 32 grid points: the nearest cluster box bounds every point's
-        // distance from below, and only clusters straddling the box's rows can
-        // add crossings.  A warp that is provably deep inside (sigmoid exactly
-        // 1) or far outside (below fill_cull) needs no distance search at all.
+        // The whole polyline is staged.
+        // Winding number by scanlines: all grid points of a row share y, so the
+        // signed crossings of that row by the polyline are found once per task
+        // (x where each straddling segment meets the row, and its direction); a
+        // point then counts the crossings to its right, which is the per-segment
+        // test of Eq. S2 restated (they can differ only for a point within
+        // rounding of the polyline, where sdf ~ 0 and the sign does not matter).
+        const int lfirst = (task - pl.chunk_off) * kChunk;
+        const int llast = min(lfirst + kChunk, pl.count) - 1;
+        const int nxx = max(pl.nx, 1);
+        const int row0 = lfirst / nxx;
+        const int nrows = llast / nxx - row0 + 1;
+        bool scan = nrows <= kMaxRows;
+        if (scan) {
+          if (threadIdx.x < nrows) s_ncross[threadIdx.x] = 0;
+          __syncthreads();
+          for (int it = threadIdx.x; it < nrows * nseg; it += blockDim.x) {
+            const int j = it / nseg, k = it - j * nseg;
+            const float yq = pl.y0 + (float(row0 + j) + 0.5f) * sp.h;
+            const float4 sg = seg[k];
+            if ((sg.y <= yq) != (segb[k].x <= yq)) {
+              const int idx = atomicAdd(&s_ncross[j], 1);
+              if (idx < kMaxCross) {
+                s_cx[j][idx] = sg.x + (yq - sg.y) * (sg.z / sg.w);
+                s_cd[j][idx] = sg.y <= yq ? 1 : -1;
+              }
+            }
+          }
+          __syncthreads();
+          scan = __syncthreads_and(threadIdx.x >= nrows || s_ncross[threadIdx.x] <= kMaxCross);
+          if (scan && valid) {
+            const int j = l / nxx - row0;
+            const int nj = s_ncross[j];
+            for (int k = 0; k < nj; ++k)
+              if (s_cx[j][k] > qx) wn += s_cd[j][k];
+          }
+        }
+        // The warp then bounds the distance of its 32 grid points from below by
+        // the nearest cluster box; a warp that is provably deep inside (sigmoid
+        // exactly 1) or far outside (below fill_cull) needs no distance search.
         const int lane = threadIdx.x & 31;
         float wx0 = valid ? qx : FLT_MAX, wx1 = valid ? qx : -FLT_MAX;
         float wy0 = valid ? qy : FLT_MAX, wy1 = valid ? qy : -FLT_MAX;
@@ -487,10 +527,10 @@ __global__ void __launch_bounds__(256, 3) k_emit(ns_curves cv, ns_sample_params 
             const float bx = fmaxf(fmaxf(bb.x - wx1, wx0 - bb.y), 0.f);
             const float by = fmaxf(fmaxf(bb.z - wy1, wy0 - bb.w), 0.f);
             lbw = fminf(lbw, bx * bx + by * by);
-            cross = bb.z <= wy1 && bb.w > wy0 && bb.y >= wx0 - 0.01f;
+            cross = !scan && bb.z <= wy1 && bb.w > wy0 && bb.y >= wx0 - 0.01f;
           }
           unsigned int m = __ballot_sync(0xffffffffu, cross);
-          while (m) {
+          while (m) {   // rows the scanline tables could not hold: per-point crossings
             const int k = c0 + __ffs(m) - 1;
             m &= m - 1;
             const float4 bb = cbox[k];
