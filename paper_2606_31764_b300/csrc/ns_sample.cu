@@ -21,8 +21,6 @@ namespace ns {
 constexpr int kPlanThreads = 128;
 constexpr int kSegBatch = 1024;   // boundary segments staged in shared memory per pass
 constexpr int kCluster = 8;       // consecutive segments per bounding-box cluster
-constexpr int kMaxRows = 40;      // grid rows of one fill task with scanline crossing tables
-constexpr int kMaxCross = 32;     // crossings of one row the table holds
 
 __device__ __forceinline__ float block_sum(float v, float* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -383,16 +381,13 @@ __device__ __forceinline__ int cluster_crossings(const float4* seg, const float2
 }
 
 // Persistent: each block iteration handles one task of 256 Gaussians of one curve.
-__global__ void __launch_bounds__(256, 3) k_emit(ns_curves cv, ns_sample_params sp, const CurvePlan* __restrict__ plan,
+__global__ void __launch_bounds__(256, 4) k_emit(ns_curves cv, ns_sample_params sp, const CurvePlan* __restrict__ plan,
                                               const int* __restrict__ order, const float* __restrict__ knots,
                                               const float2* __restrict__ bpts, const DevState* __restrict__ st,
                                               float4* rec, int* gcurve, int* gaux, long long gcap, long long bcap) {
   __shared__ float4 seg[kSegBatch];   // {b0.x, b0.y, e.x, e.y}
   __shared__ float2 segb[kSegBatch];  // {b1.y, 1/|e|^2 (0 for a zero-length segment)}
   __shared__ float4 cbox[kSegBatch / kCluster];  // {x0, x1, y0, y1} of each segment cluster
-  __shared__ float s_cx[kMaxRows][kMaxCross];    // scanline crossings of each row of a fill task
-  __shared__ signed char s_cd[kMaxRows][kMaxCross];
-  __shared__ int s_ncross[kMaxRows];
   const int n_fill = st->n_chunks;
   const int n_tasks = n_fill + st->n_ctasks;   // fill tasks (heavier) first
   const int nc = cv.n_curves;
@@ -451,125 +446,52 @@ __global__ void __launch_bounds__(256, 3) k_emit(ns_curves cv, ns_sample_params 
         seg[s] = make_float4(b0.x, b0.y, ex, ey);
         segb[s] = make_float2(b1.y, ee > 0.f ? 1.f / ee : 0.f);
       }
-      __syncthreads();
-      // bounding box of each cluster of kCluster consecutive segments, from the
-      // staged segments: x over b0 and b0 + e, y over b0 and b1 (the values the
-      // distance and crossing tests use)
+      // bounding box of each cluster of kCluster consecutive segments
       for (int cl = threadIdx.x; cl < ncl; cl += blockDim.x) {
         float x0 = FLT_MAX, x1 = -FLT_MAX, y0 = FLT_MAX, y1 = -FLT_MAX;
         for (int k = cl * kCluster; k < min(nseg, (cl + 1) * kCluster); ++k) {
-          const float4 sg = seg[k];
-          const float bx1 = sg.x + sg.z, by1 = segb[k].x;
-          x0 = fminf(x0, fminf(sg.x, bx1));
-          x1 = fmaxf(x1, fmaxf(sg.x, bx1));
-          y0 = fminf(y0, fminf(sg.y, by1));
-          y1 = fmaxf(y1, fmaxf(sg.y, by1));
+          const int i = base + k;
+          const float2 b0 = bpts[pl.b_off + i];
+          const float2 b1 = bpts[pl.b_off + (i + 1 == B ? 0 : i + 1)];
+          x0 = fminf(x0, fminf(b0.x, b1.x));
+          x1 = fmaxf(x1, fmaxf(b0.x, b1.x));
+          y0 = fminf(y0, fminf(b0.y, b1.y));
+          y1 = fmaxf(y1, fmaxf(b0.y, b1.y));
         }
         cbox[cl] = make_float4(x0, x1, y0, y1);
       }
       __syncthreads();
-      if (B <= kSegBatch) {
-        // The whole polyline is staged.
-        // Winding number by scanlines: all grid points of a row share y, so the
-        // signed crossings of that row by the polyline are found once per task
-        // (x where each straddling segment meets the row, and its direction); a
-        // point then counts the crossings to its right, which is the per-segment
-        // test of Eq. S2 restated (they can differ only for a point within
-        // rounding of the polyline, where sdf ~ 0 and the sign does not matter).
-        const int lfirst = (task - pl.chunk_off) * kChunk;
-        const int llast = min(lfirst + kChunk, pl.count) - 1;
-        const int nxx = max(pl.nx, 1);
-        const int row0 = lfirst / nxx;
-        const int nrows = llast / nxx - row0 + 1;
-        bool scan = nrows <= kMaxRows;
-        if (scan) {
-          if (threadIdx.x < nrows) s_ncross[threadIdx.x] = 0;
-          __syncthreads();
-          for (int it = threadIdx.x; it < nrows * nseg; it += blockDim.x) {
-            const int j = it / nseg, k = it - j * nseg;
-            const float yq = pl.y0 + (float(row0 + j) + 0.5f) * sp.h;
-            const float4 sg = seg[k];
-            if ((sg.y <= yq) != (segb[k].x <= yq)) {
-              const int idx = atomicAdd(&s_ncross[j], 1);
-              if (idx < kMaxCross) {
-                s_cx[j][idx] = sg.x + (yq - sg.y) * (sg.z / sg.w);
-                s_cd[j][idx] = sg.y <= yq ? 1 : -1;
-              }
-            }
-          }
-          __syncthreads();
-          scan = __syncthreads_and(threadIdx.x >= nrows || s_ncross[threadIdx.x] <= kMaxCross);
-          if (scan && valid) {
-            const int j = l / nxx - row0;
-            const int nj = s_ncross[j];
-            for (int k = 0; k < nj; ++k)
-              if (s_cx[j][k] > qx) wn += s_cd[j][k];
-          }
+      if (valid && B <= kSegBatch) {
+        // the whole polyline is staged: first the winding number and a lower
+        // bound of the distance (nearest cluster box), then the distance itself
+        // unless the point is provably deep inside, where the sigmoid of Eq. 7
+        // is exactly 1 in FP32 and the nearest segment cannot matter
+        float lbmin = FLT_MAX;
+        int clmin = 0;
+        for (int cl = 0; cl < ncl; ++cl) {
+          const float4 bb = cbox[cl];
+          const float bx = fmaxf(fmaxf(bb.x - qx, qx - bb.y), 0.f);
+          const float by = fmaxf(fmaxf(bb.z - qy, qy - bb.w), 0.f);
+          const float lb2 = bx * bx + by * by;
+          if (lb2 < lbmin) { lbmin = lb2; clmin = cl; }
+          if (bb.z <= qy && bb.w > qy && bb.y >= qx - 0.01f) wn += cluster_crossings(seg, segb, cl, nseg, qx, qy);
         }
-        // The warp then bounds the distance of its 32 grid points from below by
-        // the nearest cluster box; a warp that is provably deep inside (sigmoid
-        // exactly 1) or far outside (below fill_cull) needs no distance search.
-        const int lane = threadIdx.x & 31;
-        float wx0 = valid ? qx : FLT_MAX, wx1 = valid ? qx : -FLT_MAX;
-        float wy0 = valid ? qy : FLT_MAX, wy1 = valid ? qy : -FLT_MAX;
-        for (int o = 16; o > 0; o >>= 1) {
-          wx0 = fminf(wx0, __shfl_xor_sync(0xffffffffu, wx0, o));
-          wx1 = fmaxf(wx1, __shfl_xor_sync(0xffffffffu, wx1, o));
-          wy0 = fminf(wy0, __shfl_xor_sync(0xffffffffu, wy0, o));
-          wy1 = fmaxf(wy1, __shfl_xor_sync(0xffffffffu, wy1, o));
-        }
-        float lbw = FLT_MAX;
-        for (int c0 = 0; c0 < ncl; c0 += 32) {
-          const int cl = c0 + lane;
-          bool cross = false;
-          if (cl < ncl) {
-            const float4 bb = cbox[cl];
-            const float bx = fmaxf(fmaxf(bb.x - wx1, wx0 - bb.y), 0.f);
-            const float by = fmaxf(fmaxf(bb.z - wy1, wy0 - bb.w), 0.f);
-            lbw = fminf(lbw, bx * bx + by * by);
-            cross = !scan && bb.z <= wy1 && bb.w > wy0 && bb.y >= wx0 - 0.01f;
-          }
-          unsigned int m = __ballot_sync(0xffffffffu, cross);
-          while (m) {   // rows the scanline tables could not hold: per-point crossings
-            const int k = c0 + __ffs(m) - 1;
-            m &= m - 1;
-            const float4 bb = cbox[k];
-            if (valid && bb.z <= qy && bb.w > qy && bb.y >= qx - 0.01f)
-              wn += cluster_crossings(seg, segb, k, nseg, qx, qy);
-          }
-        }
-        for (int o = 16; o > 0; o >>= 1) lbw = fminf(lbw, __shfl_xor_sync(0xffffffffu, lbw, o));
         const bool inside = sp.fill_rule == 0 ? wn > 0 : wn != 0;
-        if (inside && lbw > deep2) {
+        if (inside && lbmin > deep2) {
           deep = true;
-        } else if (!inside && lbw > far2) {
+        } else if (!inside && lbmin > far2) {
           far = true;
-        } else if (valid) {
-          float lbmin = FLT_MAX;
-          int clmin = 0;
+        } else {
+          // the nearest box first: its best distance prunes most other clusters
+          cluster_nearest(seg, segb, clmin, nseg, base, qx, qy, best, arg);
           for (int cl = 0; cl < ncl; ++cl) {
+            if (cl == clmin) continue;
             const float4 bb = cbox[cl];
             const float bx = fmaxf(fmaxf(bb.x - qx, qx - bb.y), 0.f);
             const float by = fmaxf(fmaxf(bb.z - qy, qy - bb.w), 0.f);
             const float lb2 = bx * bx + by * by;
-            if (lb2 < lbmin) { lbmin = lb2; clmin = cl; }
-          }
-          if (inside && lbmin > deep2) {
-            deep = true;
-          } else if (!inside && lbmin > far2) {
-            far = true;
-          } else {
-            // the nearest box first: its best distance prunes most other clusters
-            cluster_nearest(seg, segb, clmin, nseg, base, qx, qy, best, arg);
-            for (int cl = 0; cl < ncl; ++cl) {
-              if (cl == clmin) continue;
-              const float4 bb = cbox[cl];
-              const float bx = fmaxf(fmaxf(bb.x - qx, qx - bb.y), 0.f);
-              const float by = fmaxf(fmaxf(bb.z - qy, qy - bb.w), 0.f);
-              const float lb2 = bx * bx + by * by;
-              if (lb2 > best + 1e-3f * (lb2 + 1.f)) continue;
-              cluster_nearest(seg, segb, cl, nseg, base, qx, qy, best, arg);
-            }
+            if (lb2 > best + 1e-3f * (lb2 + 1.f)) continue;
+            cluster_nearest(seg, segb, cl, nseg, base, qx, qy, best, arg);
           }
         }
       } else if (valid) {
