@@ -40,12 +40,14 @@ PEAKS_FALLBACK = dict(hbm_gbs=6400.0, sm_max_mhz=2032.0)
 # own launch by the units processed, and reports null if the source or tile
 # has changed since the capture.
 TRAFFIC = dict(
-    blend_bwd=dict(bytes=106232576, units=2706344, unit="pairs", tile=8,
-                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="0864786de61ebe62"),
-    blend_fwd=dict(bytes=48792576, units=2706344, unit="pairs", tile=8,
-                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="0864786de61ebe62"),
-    emit=dict(bytes=2174208, units=2027197, unit="gaussians", tile=None,
-              src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="8edc698e9ca46215"),
+    blend_bwd=dict(bytes=106611200, units=2706344, unit="pairs", tile=8,
+                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="d59061f4827f403e"),
+    blend_fwd=dict(bytes=49121792, units=2706344, unit="pairs", tile=8,
+                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="d59061f4827f403e"),
+    emit=dict(bytes=2415872, units=2027197, unit="gaussians", tile=None,
+              src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="020187ed43480f94"),
+    chain=dict(bytes=88507392, units=2027197, unit="gaussians", tile=None,
+               src="paper_2606_31764_b300/csrc/ns_backward.cu", sha="44739f3991573c5e"),
 )
 
 
