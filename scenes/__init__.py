@@ -381,6 +381,18 @@ def small_open(seed, n_curves=3, size=40, p=3, nk_range=(5, 9), width=(1.5, 3.0)
     return b.build("small-open", tgt, dict(SAMPLE_DEFAULTS, delta_c=delta_c), dict(RASTER_PARITY))
 
 
+def from_curves(curves, height, width, channels=3, sample=None, raster=None, name="custom"):
+    """A one-scene batch from explicit curves: each entry is a dict with keys
+    p, key ([n_k, 4] rows {x, y, s, w}), tau, and optionally color, closed,
+    filled.  Used by tests that need hand-made inputs."""
+    b = _Builder(1, height, width, channels)
+    for cv in curves:
+        b.add(0, int(cv["p"]), cv["key"], cv["tau"], cv.get("color", (0.2, 0.4, 0.6, 0.9)),
+              bool(cv.get("closed", False)), bool(cv.get("filled", False)))
+    tgt = np.ones((1, height, width, channels), np.float32)
+    return b.build(name, tgt, dict(SAMPLE_DEFAULTS, **(sample or {})), dict(RASTER_PARITY, **(raster or {})))
+
+
 def small_closed(seed, n_curves=3, size=48, filled=True, h=2.0, degrees=(2, 3, 4, 5), n_scenes=1,
                  width=(1.0, 3.0), height=None):
     """Small closed (filled or stroked) scenes for parity tests."""
