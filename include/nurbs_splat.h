@@ -155,7 +155,7 @@ enum {
   NS_KERNEL_BIN_EMIT = 5, NS_KERNEL_RADIX_HIST = 6, NS_KERNEL_RADIX_SCATTER = 7, NS_KERNEL_RANGES = 8,
   NS_KERNEL_BLEND_FWD = 9, NS_KERNEL_BLEND_BWD = 10, NS_KERNEL_CHAIN = 11, NS_KERNEL_CHAIN_BOUNDARY = 12,
   NS_KERNEL_KNOT_GRADS = 13, NS_KERNEL_MSE = 14, NS_KERNEL_ADAM = 15, NS_KERNEL_SCAN = 16,
-  NS_KERNEL_OTHER = 17, NS_KERNEL_CHAIN_CONTOUR = 18
+  NS_KERNEL_OTHER = 17, NS_KERNEL_CHAIN_CONTOUR = 18, NS_KERNEL_DERIV_LOSS = 19, NS_KERNEL_BBOX_LOSS = 20
 };
 
 ns_sample_params ns_default_sample_params(void);
@@ -259,6 +259,52 @@ ns_status ns_mse_loss(const float* image, const float* target, int64_t n,
 ns_status ns_adam_step(float* param, const float* grad, float* m, float* v, int64_t n,
                        float lr, float beta1, float beta2, float eps, int32_t step,
                        const float* lo, const float* hi, int32_t group, void* stream);
+
+/* Penalties of the bounding-box loss (Eq. 12). */
+#define NS_PENALTY_RELU 0      /* phi(x) = max(x, 0), derivative 0 at 0 */
+#define NS_PENALTY_SOFTPLUS 1  /* phi(x) = log(1 + e^x), x in pixels */
+
+/* Weights and settings of the geometric regularisers (§3.6, Eq. 10-12). */
+typedef struct {
+  float lambda_deriv;  /* weight of the derivative loss (Eq. 11); 0 skips it */
+  int32_t order;       /* derivative order r, 1..4 (the paper uses 3) */
+  int32_t nodes;       /* midpoint nodes per curve; 0: N_L = nl_mult * max(width, height) */
+  float lambda_bbox;   /* weight of the bounding-box loss (Eq. 12); 0 skips it */
+  int32_t penalty;     /* NS_PENALTY_RELU or NS_PENALTY_SOFTPLUS */
+  float box[4];        /* x_min, y_min, x_max, y_max in pixels; an empty box
+                          (x_max <= x_min or y_max <= y_min) means the canvas
+                          [0, width] x [0, height] */
+} ns_geometry_params;
+
+/* lambda_deriv = lambda_bbox = 1, order 3, N_L nodes, ReLU, the canvas. */
+ns_geometry_params ns_default_geometry_params(void);
+
+/*
+ * Geometric regularisers of the total loss (§3.6, Eq. 10-12) and their
+ * gradients, on the plan, knot vectors and sample counts that nurbs_sample
+ * left in `workspace` (same curves and sample parameters; call it after
+ * nurbs_sample, before or after the splat calls of the same step).
+ *   Derivative loss (Eq. 11): per curve, (1/(b - a)) int_a^b |C^(r)_xy(u)|^2 du
+ *     over its domain [a, b] = [u_p, u_{m-p}], by the `nodes`-node midpoint
+ *     rule of Eq. 3, with C^(r) the exact r-th derivative of the rational
+ *     curve (Eq. 1-2 differentiated r times); averaged over all curves.
+ *   Bounding-box loss (Eq. 12): sum over the sampled curve points -- the M
+ *     contour samples of every stroke (not the endpoint copies) and the
+ *     boundary points of every filled curve -- of phi(b_min - P) + phi(P -
+ *     b_max), per axis.
+ *   loss: device float[2], overwritten with {lambda_deriv * L_deriv,
+ *     lambda_bbox * L_bbox}.
+ *   out: NULL for the values only; otherwise the gradients with respect to
+ *     the key points {x, y, w} and knot intervals are ADDED to out->dkey and
+ *     out->dtau (out->dcolor is not touched).  Knot spans of the nodes and the
+ *     sample counts are held fixed, as in splat_backward.
+ * Uses the workspace's knot-gradient scratch, so it must not run concurrently
+ * with splat_backward on the same workspace (the same stream orders them).
+ */
+ns_status ns_geometry_loss(const ns_curves* curves, const ns_sample_params* sp,
+                           const ns_raster_params* rp, const ns_geometry_params* gp,
+                           const ns_capacity* cap, float* loss, const ns_curve_grads* out,
+                           void* workspace, size_t workspace_bytes, void* stream);
 
 /* Synchronises `stream`, reads the device status and counters. */
 ns_status ns_poll_status(void* workspace, ns_report* report, void* stream);

@@ -46,6 +46,14 @@ class NsGaussians(C.Structure):
     _fields_ = [("capacity", C.c_int64), ("rec", _p), ("curve", _p), ("aux", _p), ("count", _p)]
 
 
+class NsGeometryParams(C.Structure):
+    _fields_ = [("lambda_deriv", C.c_float), ("order", C.c_int32), ("nodes", C.c_int32), ("lambda_bbox", C.c_float),
+                ("penalty", C.c_int32), ("box", C.c_float * 4)]
+
+
+NS_PENALTY_RELU, NS_PENALTY_SOFTPLUS = 0, 1
+
+
 class NsCurveGrads(C.Structure):
     _fields_ = [("dkey", _p), ("dtau", _p), ("dcolor", _p)]
 
@@ -81,13 +89,17 @@ SIGNATURES = {
     "ns_profile_next_launch": (C.c_int, [C.c_int32, _p, _p]),
     "splat_forward_noalloc": (C.c_int, [C.POINTER(NsCurves), C.POINTER(NsGaussians), C.POINTER(NsRasterParams),
                                         _p, C.POINTER(NsReport), _p]),
+    "ns_default_geometry_params": (NsGeometryParams, []),
+    "ns_geometry_loss": (C.c_int, [C.POINTER(NsCurves), C.POINTER(NsSampleParams), C.POINTER(NsRasterParams),
+                                   C.POINTER(NsGeometryParams), C.POINTER(NsCapacity), _p, C.POINTER(NsCurveGrads),
+                                   _p, C.c_size_t, _p]),
     "ns_launch_count": (C.c_uint64, []),
     "ns_last_error": (C.c_char_p, []),
 }
 
 KERNELS = dict(plan=1, boundary=2, emit=3, bin_count=4, bin_emit=5, radix_hist=6, radix_scatter=7, ranges=8,
                blend_fwd=9, blend_bwd=10, chain=11, chain_boundary=12, knot_grads=13, mse=14, adam=15, scan=16,
-               other=17, chain_contour=18)
+               other=17, chain_contour=18, deriv_loss=19, bbox_loss=20)
 
 _lib = None
 

@@ -70,22 +70,7 @@ __device__ __forceinline__ void curve_point_bwd_local(const float4* key, const C
                                                       float dkn[2 * P], float& du) {
   Eval<P> e;
   eval_curve<P>(key, cr, U, i, u, e);
-  const float iw = 1.f / e.W;
-  float gN[P + 1];
-#pragma unroll
-  for (int l = 0; l <= P; ++l) {
-    const float4 q = e.cp[l];
-    const float R = e.t.N[l] * q.w * iw;
-    const float proj = gC[0] * (q.x - e.C[0]) + gC[1] * (q.y - e.C[1]) + gC[2] * (q.z - e.C[2]);
-    gN[l] = q.w * proj * iw;
-    dcp[l][0] += gC[0] * R;
-    dcp[l][1] += gC[1] * R;
-    dcp[l][2] += gC[2] * R;
-    dcp[l][3] += e.t.N[l] * proj * iw;
-  }
-  float d = 0.f;
-  basis_bwd<P>(e.t, gN, &d, dkn);
-  du = d;
+  curve_point_adjoint<P>(e, gC, dcp, dkn, &du);
 }
 
 struct ChainParams {
@@ -416,6 +401,11 @@ __global__ void k_knot_grads(ns_curves cv, const CurvePlan* __restrict__ plan, c
     }
     atomicAdd(dtau + t0 + k, acc);   // closed curves: wrapped copies fold onto the same interval
   }
+}
+
+void launch_knot_grads(const ns_curves& cv, const CurvePlan* plan, const float* dknots, float* dtau,
+                       cudaStream_t s) {
+  NS_LAUNCH(NS_KERNEL_KNOT_GRADS, k_knot_grads, (cv.n_curves + 3) / 4, 128, 0, s, cv, plan, dknots, dtau);
 }
 
 }  // namespace ns

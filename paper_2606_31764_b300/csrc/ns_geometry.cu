@@ -1,0 +1,539 @@
+// ns_geometry_loss: the geometric regularisers of the total loss (Eq. 10),
+// with their gradients, on the plan and knots that nurbs_sample left in the
+// workspace.
+//
+//   k_deriv_loss     Eq. 11: per curve the mean of |C^(r)_xy|^2 over N
+//                    midpoint nodes u_j = a + (j + 1/2)(b - a)/N of the domain.
+//                    C^(r) comes from the homogeneous curve S_h = sum N_i w_i
+//                    (x_i, y_i, 1): its k-th derivative is a degree p-k
+//                    B-spline, S_h^(k)(u) = sum_l N_{l,p-k}(u) Q^(k)_l with
+//                    the derivative control points
+//                      Q^(k)_l = (p-k+1)/(U_{l+p-k+1} - U_l) (Q^(k-1)_l - Q^(k-1)_{l-1}),
+//                    and the lower-degree basis values are the levels of the
+//                    span's Cox-de Boor triangle.  The quotient C = S/W is then
+//                    differentiated by the Leibniz rule,
+//                      C^(k) = (S^(k) - sum_{q=1..k} binom(k,q) W^(q) C^(k-q)) / W,
+//                    which is Eq. 2 for k = 1.  The reverse sweep runs the same
+//                    steps backwards into control points, weights and knots
+//                    (the triangle's reverse sweep takes adjoints at every level).
+//                    Each thread walks a run of consecutive nodes and keeps the
+//                    span's gradients in registers until the span changes.
+//   k_bbox_contour   Eq. 12 over the contour samples of strokes (the M samples,
+//   k_bbox_boundary  not the endpoint copies) and the boundary points of fills:
+//                    per axis phi(b_min - P) + phi(P - b_max), phi ReLU or
+//                    softplus; nonzero gradients go back through C(u).
+//   k_knot_grads     (ns_backward.cu) turns the knot gradients into dtau.
+#include <cuda_runtime.h>
+
+#include "ns_internal.cuh"
+
+namespace ns {
+
+void launch_knot_grads(const ns_curves& cv, const CurvePlan* plan, const float* dknots, float* dtau,
+                       cudaStream_t s);
+
+constexpr int kMaxOrder = 4;       // highest derivative order of Eq. 11 supported
+constexpr int kDerivRun = 8;       // quadrature nodes per thread
+constexpr int kGeoThreads = 128;
+
+struct GeoParams {
+  float scale_d;      // lambda_deriv / (n_curves * nodes)
+  int order, nodes;
+  float lo[2], hi[2];
+  float scale_b;      // lambda_bbox
+  int penalty;        // NS_PENALTY_RELU / NS_PENALTY_SOFTPLUS
+  int kappa;
+};
+
+__device__ __forceinline__ float binom_small(int k, int q) {
+  // binomial coefficients up to k = kMaxOrder
+  const float row[kMaxOrder + 1][kMaxOrder + 1] = {
+      {1, 0, 0, 0, 0}, {1, 1, 0, 0, 0}, {1, 2, 1, 0, 0}, {1, 3, 3, 1, 0}, {1, 4, 6, 4, 1}};
+  return row[k][q];
+}
+
+// Reverse sweep of the span triangle with adjoints entering at every level:
+// gTop[r] = dL/dN_{i-P+r,P}, gLow[d][r] = dL/dN_{i-d+r,d} for d < P.  Same
+// recurrence as basis_bwd; the level-d adjoints join before level d is swept.
+template <int P>
+__device__ __forceinline__ void basis_bwd_levels(const Tri<P>& t, const float* gTop, const float (*gLow)[P],
+                                                 float* du, float* dU) {
+  float g[P + 1];
+#pragma unroll
+  for (int r = 0; r <= P; ++r) g[r] = gTop[r];
+#pragma unroll
+  for (int j = P; j >= 1; --j) {
+    float gp[P];
+#pragma unroll
+    for (int r = 0; r < j; ++r) {
+      const float x = t.lev[j - 1][r];
+      const float D = t.right[r + 1] + t.left[j - r];
+      const float inv = 1.f / D;
+      const float al = t.left[j - r] * inv;
+      const float be = t.right[r + 1] * inv;
+      gp[r] = be * g[r] + al * g[r + 1];
+      const float dal = x * (g[r + 1] - g[r]);
+      *du += dal * inv;
+      dU[r + P - j] += dal * (al - 1.f) * inv;
+      dU[r + P] -= dal * al * inv;
+    }
+#pragma unroll
+    for (int r = 0; r < j; ++r) g[r] = gp[r] + gLow[j - 1][r];
+  }
+}
+
+// N_{i-d+r, d}(u) from the span triangle (level P is the top row).
+template <int P>
+__device__ __forceinline__ float level_value(const Tri<P>& t, int d, int r) {
+  return d == P ? t.N[r] : t.lev[d < P ? d : 0][r];
+}
+
+// Span-local accumulators of one thread's run of nodes.
+template <int P>
+struct SpanAcc {
+  int span;
+  float cp[P + 1][3];   // dL/d{x, y, w} of control points span-P .. span
+  float kn[2 * P];      // dL/dU of knots span-P+1 .. span+P
+};
+
+template <int P>
+__device__ __forceinline__ void acc_clear(SpanAcc<P>& a, int span) {
+  a.span = span;
+#pragma unroll
+  for (int l = 0; l <= P; ++l) a.cp[l][0] = a.cp[l][1] = a.cp[l][2] = 0.f;
+#pragma unroll
+  for (int k = 0; k < 2 * P; ++k) a.kn[k] = 0.f;
+}
+
+template <int P>
+__device__ __forceinline__ void acc_flush(const CurveRef& cr, SpanAcc<P>& a, float* dkey, float* dknots) {
+  if (a.span < 0) return;
+#pragma unroll
+  for (int l = 0; l <= P; ++l) {
+    float* d = dkey + 4 * (long long)(cr.key0 + cp_to_key(a.span - P + l, P, cr.closed, cr.nk));
+    if (a.cp[l][0] != 0.f) atomicAdd(d + 0, a.cp[l][0]);
+    if (a.cp[l][1] != 0.f) atomicAdd(d + 1, a.cp[l][1]);
+    if (a.cp[l][2] != 0.f) atomicAdd(d + 3, a.cp[l][2]);
+  }
+#pragma unroll
+  for (int k = 0; k < 2 * P; ++k)
+    if (a.kn[k] != 0.f) atomicAdd(dknots + cr.knot0 + a.span - P + 1 + k, a.kn[k]);
+}
+
+// One quadrature node: returns |C^(r)_xy(u)|^2; with `acc` adds the gradient
+// of scale * |C^(r)|^2 and returns dL/du in *du.
+template <int P>
+__device__ float deriv_node(const float4* __restrict__ key, const CurveRef& cr, const float* __restrict__ U, int i,
+                            float u, int r, float scale, SpanAcc<P>* acc, float* du) {
+  constexpr int KM = P < kMaxOrder ? P : kMaxOrder;   // highest nonzero S_h derivative
+  Tri<P> t;
+  basis_fwd<P>(U, i, u, t);
+  float4 q[P + 1];
+  float Q[KM + 1][P + 1][3];
+#pragma unroll
+  for (int l = 0; l <= P; ++l) {
+    q[l] = key[cr.key0 + cp_to_key(i - P + l, P, cr.closed, cr.nk)];
+    Q[0][l][0] = q[l].w * q[l].x;
+    Q[0][l][1] = q[l].w * q[l].y;
+    Q[0][l][2] = q[l].w;
+  }
+#pragma unroll
+  for (int k = 1; k <= KM; ++k) {
+    if (k > r) break;
+#pragma unroll
+    for (int l = k; l <= P; ++l) {
+      // D >= U[i+1] - U[i] > 0: the interval [U_{i-P+l}, U_{i+l-k+1}] holds span i
+      const float c = float(P - k + 1) / (U[i + l - k + 1] - U[i - P + l]);
+#pragma unroll
+      for (int e = 0; e < 3; ++e) Q[k][l][e] = c * (Q[k - 1][l][e] - Q[k - 1][l - 1][e]);
+    }
+  }
+  // homogeneous derivatives H[k] = S_h^(k)(u), k = 0..r
+  float H[kMaxOrder + 1][3];
+#pragma unroll
+  for (int k = 0; k <= kMaxOrder; ++k) {
+    H[k][0] = H[k][1] = H[k][2] = 0.f;
+    if (k <= r && k <= KM) {
+#pragma unroll
+      for (int l = k; l <= P; ++l) {
+        const float n = level_value<P>(t, P - k, l - k);
+#pragma unroll
+        for (int e = 0; e < 3; ++e) H[k][e] = fmaf(n, Q[k][l][e], H[k][e]);
+      }
+    }
+  }
+  const float iw = 1.f / H[0][2];
+  float Cd[kMaxOrder + 1][2];
+#pragma unroll
+  for (int k = 0; k <= kMaxOrder; ++k) {
+    if (k > r) break;
+    float ax = H[k][0], ay = H[k][1];
+#pragma unroll
+    for (int qq = 1; qq <= k; ++qq) {
+      const float b = binom_small(k, qq) * H[qq][2];
+      ax -= b * Cd[k - qq][0];
+      ay -= b * Cd[k - qq][1];
+    }
+    Cd[k][0] = ax * iw;
+    Cd[k][1] = ay * iw;
+  }
+  float cx = 0.f, cy = 0.f;
+#pragma unroll
+  for (int k = 0; k <= kMaxOrder; ++k)
+    if (k == r) { cx = Cd[k][0]; cy = Cd[k][1]; }
+  const float f = cx * cx + cy * cy;
+  if (!acc) return f;
+
+  // ---- reverse sweep
+  float gC[kMaxOrder + 1][2];
+  float gH[kMaxOrder + 1][3];
+#pragma unroll
+  for (int k = 0; k <= kMaxOrder; ++k) {
+    gC[k][0] = gC[k][1] = 0.f;
+    gH[k][0] = gH[k][1] = gH[k][2] = 0.f;
+    if (k == r) {
+      gC[k][0] = 2.f * scale * cx;
+      gC[k][1] = 2.f * scale * cy;
+    }
+  }
+#pragma unroll
+  for (int k = kMaxOrder; k >= 0; --k) {
+    if (k > r) continue;
+    const float gx = gC[k][0] * iw, gy = gC[k][1] * iw;
+    gH[k][0] += gx;
+    gH[k][1] += gy;
+    gH[0][2] -= gx * Cd[k][0] + gy * Cd[k][1];   // the division by W = H[0].w
+#pragma unroll
+    for (int qq = 1; qq <= k; ++qq) {
+      const float b = binom_small(k, qq);
+      gH[qq][2] -= b * (gx * Cd[k - qq][0] + gy * Cd[k - qq][1]);
+      gC[k - qq][0] -= b * H[qq][2] * gx;
+      gC[k - qq][1] -= b * H[qq][2] * gy;
+    }
+  }
+  // H[k] = sum_l lev(P-k)[l-k] Q[k][l]: adjoints of the basis levels and of Q
+  float gTop[P + 1];
+  float gLow[P][P];
+#pragma unroll
+  for (int l = 0; l <= P; ++l) gTop[l] = 0.f;
+#pragma unroll
+  for (int d = 0; d < P; ++d)
+#pragma unroll
+    for (int l = 0; l < P; ++l) gLow[d][l] = 0.f;
+  float gQ[P + 1][3];     // adjoint of Q[k] for the level being swept
+#pragma unroll
+  for (int l = 0; l <= P; ++l) gQ[l][0] = gQ[l][1] = gQ[l][2] = 0.f;
+#pragma unroll
+  for (int k = KM; k >= 0; --k) {
+    if (k > r) continue;
+    // contributions of H[k]
+#pragma unroll
+    for (int l = k; l <= P; ++l) {
+      const float n = level_value<P>(t, P - k, l - k);
+      const float gn = gH[k][0] * Q[k][l][0] + gH[k][1] * Q[k][l][1] + gH[k][2] * Q[k][l][2];
+      if (k == 0) gTop[l] += gn; else gLow[P - k][l - k] += gn;
+#pragma unroll
+      for (int e = 0; e < 3; ++e) gQ[l][e] = fmaf(n, gH[k][e], gQ[l][e]);
+    }
+    if (k == 0) break;
+    // Q[k][l] = c (Q[k-1][l] - Q[k-1][l-1]): hand the adjoint down one level
+    float gPrev[P + 1][3];
+#pragma unroll
+    for (int l = 0; l <= P; ++l) gPrev[l][0] = gPrev[l][1] = gPrev[l][2] = 0.f;
+#pragma unroll
+    for (int l = k; l <= P; ++l) {
+      const float D = U[i + l - k + 1] - U[i - P + l];
+      const float c = float(P - k + 1) / D;
+      float gc = 0.f;
+#pragma unroll
+      for (int e = 0; e < 3; ++e) {
+        gPrev[l][e] += c * gQ[l][e];
+        gPrev[l - 1][e] -= c * gQ[l][e];
+        gc += gQ[l][e] * (Q[k - 1][l][e] - Q[k - 1][l - 1][e]);
+      }
+      const float gD = -gc * c / D;
+      acc->kn[l - k + P] += gD;   // knot i+l-k+1
+      acc->kn[l - 1] -= gD;       // knot i-P+l
+    }
+#pragma unroll
+    for (int l = 0; l <= P; ++l) {
+      gQ[l][0] = gPrev[l][0];
+      gQ[l][1] = gPrev[l][1];
+      gQ[l][2] = gPrev[l][2];
+    }
+  }
+  // Q[0][l] = (w x, w y, w)
+#pragma unroll
+  for (int l = 0; l <= P; ++l) {
+    acc->cp[l][0] += q[l].w * gQ[l][0];
+    acc->cp[l][1] += q[l].w * gQ[l][1];
+    acc->cp[l][2] += q[l].x * gQ[l][0] + q[l].y * gQ[l][1] + gQ[l][2];
+  }
+  float d = 0.f;
+  basis_bwd_levels<P>(t, gTop, gLow, &d, acc->kn);
+  *du = d;
+  return f;
+}
+
+template <int P>
+__device__ float deriv_run(const ns_curves& cv, const CurveRef& cr, const float* U, const CurvePlan& pl,
+                           const GeoParams& gp, int j0, int j1, float* dkey, float* dknots) {
+  SpanAcc<P> acc;
+  const bool grads = dkey != nullptr;
+  acc_clear<P>(acc, -1);
+  float sum = 0.f, dA = 0.f, dB = 0.f;
+  for (int j = j0; j < j1; ++j) {
+    const float t = (float(j) + 0.5f) / float(gp.nodes);
+    const float u = pl.a + t * (pl.b - pl.a);
+    const int i = find_span(U, P, cr.n, u);
+    if (grads && i != acc.span) {
+      acc_flush<P>(cr, acc, dkey, dknots);
+      acc_clear<P>(acc, i);
+    }
+    float du = 0.f;
+    sum += deriv_node<P>(reinterpret_cast<const float4*>(cv.key), cr, U, i, u, gp.order, gp.scale_d,
+                         grads ? &acc : nullptr, &du);
+    dA += du * (1.f - t);   // u = a + t (b - a)
+    dB += du * t;
+  }
+  if (grads) {
+    acc_flush<P>(cr, acc, dkey, dknots);
+    if (dA != 0.f) atomicAdd(dknots + cr.knot0 + cr.p, dA);
+    if (dB != 0.f) atomicAdd(dknots + cr.knot0 + cr.n + 1, dB);
+  }
+  return sum * gp.scale_d;
+}
+
+__device__ __forceinline__ void block_sum_add(float v, float* out) {
+  __shared__ float s_part[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) s_part[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    float x = lane < int(blockDim.x >> 5) ? s_part[lane] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0 && x != 0.f) atomicAdd(out, x);
+  }
+}
+
+__global__ void __launch_bounds__(kGeoThreads) k_deriv_loss(ns_curves cv, const CurvePlan* __restrict__ plan,
+                                                            const float* __restrict__ knots, GeoParams gp,
+                                                            float* loss, float* dkey, float* dknots) {
+  const int runs = (gp.nodes + kDerivRun - 1) / kDerivRun;
+  const long long total = (long long)cv.n_curves * runs;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  float sum = 0.f;
+  // every thread runs the same number of iterations, so the block reduction
+  // below is reached by all of them
+  const long long iters = (total + stride - 1) / stride;
+  for (long long it = 0; it < iters; ++it) {
+    const long long idx = it * stride + blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= total) continue;
+    const int c = int(idx / runs);
+    const int run = int(idx - (long long)c * runs);
+    const CurvePlan pl = plan[c];
+    if (pl.kind == kNone) continue;
+    const CurveRef cr = curve_ref(cv, c);
+    const float* U = knots + cr.knot0;
+    const int j0 = run * kDerivRun, j1 = min(j0 + kDerivRun, gp.nodes);
+    NS_DISPATCH_P(cr.p, sum += deriv_run<P>(cv, cr, U, pl, gp, j0, j1, dkey, dknots));
+  }
+  block_sum_add(sum, loss);
+}
+
+// Penalty of one point and its gradient dL/dP (before the lambda scale).
+__device__ __forceinline__ float box_penalty(const GeoParams& gp, float x, float y, float* gx, float* gy) {
+  const float v[4] = {gp.lo[0] - x, gp.lo[1] - y, x - gp.hi[0], y - gp.hi[1]};
+  float f = 0.f, d[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (gp.penalty == NS_PENALTY_SOFTPLUS) {
+      // log(1 + e^v) = max(v, 0) + log(1 + e^-|v|), derivative the logistic function
+      f += fmaxf(v[k], 0.f) + log1pf(expf(-fabsf(v[k])));
+      d[k] = 1.f / (1.f + expf(-v[k]));
+    } else {
+      f += fmaxf(v[k], 0.f);
+      d[k] = v[k] > 0.f ? 1.f : 0.f;
+    }
+  }
+  *gx = d[2] - d[0];
+  *gy = d[3] - d[1];
+  return f;
+}
+
+template <int P>
+__device__ float bbox_point(const ns_curves& cv, const CurveRef& cr, const float* U, const CurvePlan& pl,
+                            const GeoParams& gp, float u, float t, float* dkey, float* dknots) {
+  const int i = find_span(U, P, cr.n, u);
+  Eval<P> e;
+  eval_curve<P>(reinterpret_cast<const float4*>(cv.key), cr, U, i, u, e);
+  float gx, gy;
+  const float f = box_penalty(gp, e.C[0], e.C[1], &gx, &gy);
+  if (dkey && (gx != 0.f || gy != 0.f)) {
+    const float gC[3] = {gp.scale_b * gx, gp.scale_b * gy, 0.f};
+    float dcp[P + 1][4], dkn[2 * P], du = 0.f;
+#pragma unroll
+    for (int l = 0; l <= P; ++l) dcp[l][0] = dcp[l][1] = dcp[l][2] = dcp[l][3] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 2 * P; ++k) dkn[k] = 0.f;
+    curve_point_adjoint<P>(e, gC, dcp, dkn, &du);
+#pragma unroll
+    for (int l = 0; l <= P; ++l) {
+      float* d = dkey + 4 * (long long)(cr.key0 + cp_to_key(i - P + l, P, cr.closed, cr.nk));
+      if (dcp[l][0] != 0.f) atomicAdd(d + 0, dcp[l][0]);
+      if (dcp[l][1] != 0.f) atomicAdd(d + 1, dcp[l][1]);
+      if (dcp[l][3] != 0.f) atomicAdd(d + 3, dcp[l][3]);
+    }
+#pragma unroll
+    for (int k = 0; k < 2 * P; ++k)
+      if (dkn[k] != 0.f) atomicAdd(dknots + cr.knot0 + i - P + 1 + k, dkn[k]);
+    const float dA = du * (1.f - t), dB = du * t;   // u = a + t (b - a)
+    if (dA != 0.f) atomicAdd(dknots + cr.knot0 + cr.p, dA);
+    if (dB != 0.f) atomicAdd(dknots + cr.knot0 + cr.n + 1, dB);
+  }
+  return f;
+}
+
+// Contour samples of strokes: one thread per sample of a contour task.
+__global__ void __launch_bounds__(kChunk) k_bbox_contour(ns_curves cv, const CurvePlan* __restrict__ plan,
+                                                         const int* __restrict__ order,
+                                                         const float* __restrict__ knots,
+                                                         const DevState* __restrict__ st, GeoParams gp,
+                                                         float* loss, float* dkey, float* dknots) {
+  const int n_tasks = st->n_ctasks;
+  const int nc = cv.n_curves;
+  float sum = 0.f;
+  for (int task = blockIdx.x; task < n_tasks; task += gridDim.x) {
+    const int c = curve_of_task(plan, order, nc, task, false);
+    const CurvePlan pl = plan[c];
+    const int l = (task - pl.chunk_off) * kChunk + threadIdx.x;
+    if (l >= pl.count) continue;
+    if (pl.kind == kOpen && (l < gp.kappa || l >= gp.kappa + pl.M)) continue;   // endpoint copies
+    const CurveRef cr = curve_ref(cv, c);
+    const float* U = knots + cr.knot0;
+    const float t = contour_t(pl, l, gp.kappa);
+    const float u = contour_u(pl, l, gp.kappa);
+    NS_DISPATCH_P(cr.p, sum += bbox_point<P>(cv, cr, U, pl, gp, u, t, dkey, dknots));
+  }
+  block_sum_add(sum * gp.scale_b, loss);
+}
+
+// Boundary points of filled curves.
+__global__ void __launch_bounds__(kGeoThreads) k_bbox_boundary(ns_curves cv, const CurvePlan* __restrict__ plan,
+                                                               const float* __restrict__ knots,
+                                                               const DevState* __restrict__ st, GeoParams gp,
+                                                               float* loss, float* dkey, float* dknots) {
+  const int nb = st->b_count;
+  const int nc = cv.n_curves;
+  const int stride = gridDim.x * blockDim.x;
+  const int iters = (nb + stride - 1) / stride;
+  float sum = 0.f;
+  for (int it = 0; it < iters; ++it) {
+    const int j = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nb) continue;
+    int lo = 0, hi = nc - 1;   // largest curve with b_off <= j
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (plan[mid].b_off <= j) lo = mid; else hi = mid - 1;
+    }
+    const CurvePlan pl = plan[lo];
+    if (pl.kind != kFill) continue;
+    const int jj = j - pl.b_off;
+    if (jj >= pl.M) continue;
+    const CurveRef cr = curve_ref(cv, lo);
+    const float* U = knots + cr.knot0;
+    const float t = float(jj) / float(pl.M);
+    const float u = pl.a + t * (pl.b - pl.a);
+    NS_DISPATCH_P(cr.p, sum += bbox_point<P>(cv, cr, U, pl, gp, u, t, dkey, dknots));
+  }
+  block_sum_add(sum * gp.scale_b, loss);
+}
+
+}  // namespace ns
+
+using namespace ns;
+
+extern "C" ns_geometry_params ns_default_geometry_params(void) {
+  ns_geometry_params g;
+  g.lambda_deriv = 1.f;
+  g.order = 3;
+  g.nodes = 0;
+  g.lambda_bbox = 1.f;
+  g.penalty = NS_PENALTY_RELU;
+  g.box[0] = g.box[1] = g.box[2] = g.box[3] = 0.f;
+  return g;
+}
+
+extern "C" ns_status ns_geometry_loss(const ns_curves* curves, const ns_sample_params* sp,
+                                      const ns_raster_params* rp, const ns_geometry_params* gpar,
+                                      const ns_capacity* cap, float* loss, const ns_curve_grads* out,
+                                      void* ws, size_t ws_bytes, void* stream) {
+  if (!curves || !sp || !rp || !gpar || !cap || !loss || !ws) {
+    set_error("ns_geometry_loss: null argument");
+    return NS_ERR_INVALID_ARG;
+  }
+  if (out && (!out->dkey || !out->dtau)) {
+    set_error("ns_geometry_loss: gradients need dkey and dtau");
+    return NS_ERR_INVALID_ARG;
+  }
+  if (gpar->order < 1 || gpar->order > kMaxOrder) {
+    set_error("ns_geometry_loss: order must be 1..4");
+    return NS_ERR_INVALID_ARG;
+  }
+  if (gpar->penalty != NS_PENALTY_RELU && gpar->penalty != NS_PENALTY_SOFTPLUS) {
+    set_error("ns_geometry_loss: penalty must be NS_PENALTY_RELU or NS_PENALTY_SOFTPLUS");
+    return NS_ERR_INVALID_ARG;
+  }
+  if (gpar->nodes < 0 || sp->nl_mult < 1 || sp->kappa < 0) {
+    set_error("ns_geometry_loss: nodes must be >= 0 (0: N_L), nl_mult >= 1, kappa >= 0");
+    return NS_ERR_INVALID_ARG;
+  }
+  Layout L;
+  if (!make_layout(curves, cap, rp, &L)) return NS_ERR_INVALID_ARG;
+  if (ws_bytes < L.total) {
+    set_error("ns_geometry_loss: workspace smaller than ns_workspace_size");
+    return NS_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaMemsetAsync(loss, 0, 2 * sizeof(float), s);
+  if (L.nc > 0) {
+    GeoParams gp;
+    gp.order = gpar->order;
+    gp.nodes = gpar->nodes > 0 ? gpar->nodes : sp->nl_mult * (L.W > L.H ? L.W : L.H);
+    gp.scale_d = gpar->lambda_deriv / (float(L.nc) * float(gp.nodes));
+    const bool canvas = !(gpar->box[2] > gpar->box[0] && gpar->box[3] > gpar->box[1]);
+    gp.lo[0] = canvas ? 0.f : gpar->box[0];
+    gp.lo[1] = canvas ? 0.f : gpar->box[1];
+    gp.hi[0] = canvas ? float(L.W) : gpar->box[2];
+    gp.hi[1] = canvas ? float(L.H) : gpar->box[3];
+    gp.scale_b = gpar->lambda_bbox;
+    gp.penalty = gpar->penalty;
+    gp.kappa = sp->kappa;
+    const CurvePlan* plan = at<const CurvePlan>(ws, L.o_plan);
+    const float* knots = at<const float>(ws, L.o_knots);
+    const int* order = at<const int>(ws, L.o_order);
+    const DevState* st = at<const DevState>(ws, L.o_state);
+    float* dknots = out ? at<float>(ws, L.o_dknots) : nullptr;
+    float* dkey = out ? out->dkey : nullptr;
+    if (out) cudaMemsetAsync(dknots, 0, sizeof(float) * ((size_t)L.nt + (size_t)kKnotPad * L.nc), s);
+    if (gpar->lambda_deriv != 0.f)
+      NS_LAUNCH(NS_KERNEL_DERIV_LOSS, k_deriv_loss, num_sms() * 8, kGeoThreads, 0, s, *curves, plan, knots, gp,
+                loss, dkey, dknots);
+    if (gpar->lambda_bbox != 0.f) {
+      NS_LAUNCH(NS_KERNEL_BBOX_LOSS, k_bbox_contour, num_sms() * 4, kChunk, 0, s, *curves, plan, order, knots, st,
+                gp, loss + 1, dkey, dknots);
+      NS_LAUNCH(NS_KERNEL_BBOX_LOSS, k_bbox_boundary, num_sms() * 4, kGeoThreads, 0, s, *curves, plan, knots, st,
+                gp, loss + 1, dkey, dknots);
+    }
+    if (out) launch_knot_grads(*curves, plan, dknots, out->dtau, s);
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string("ns_geometry_loss: ") + cudaGetErrorString(e));
+    return NS_ERR_CUDA;
+  }
+  return NS_OK;
+}

@@ -270,6 +270,30 @@ __device__ __forceinline__ float speed_xy(const Eval<P>& e) {
   return sqrtf(dx * dx + dy * dy);
 }
 
+// Reverse of C = S/W at one evaluated point: given gC = dL/dC (x, y, s), adds
+// dL/d{x, y, s, w} of the span's control points to dcp[l], dL/dU of its 2P
+// knots to dkn (as basis_bwd) and returns dL/du in *du.
+template <int P>
+__device__ __forceinline__ void curve_point_adjoint(const Eval<P>& e, const float gC[3], float dcp[P + 1][4],
+                                                    float dkn[2 * P], float* du) {
+  const float iw = 1.f / e.W;
+  float gN[P + 1];
+#pragma unroll
+  for (int l = 0; l <= P; ++l) {
+    const float4 q = e.cp[l];
+    const float R = e.t.N[l] * q.w * iw;              // rational basis N w / W
+    const float proj = gC[0] * (q.x - e.C[0]) + gC[1] * (q.y - e.C[1]) + gC[2] * (q.z - e.C[2]);
+    gN[l] = q.w * proj * iw;                            // dL/dN_l
+    dcp[l][0] += gC[0] * R;
+    dcp[l][1] += gC[1] * R;
+    dcp[l][2] += gC[2] * R;
+    dcp[l][3] += e.t.N[l] * proj * iw;
+  }
+  float d = 0.f;
+  basis_bwd<P>(e.t, gN, &d, dkn);
+  *du = d;
+}
+
 // Sum of 8 values over the 32 lanes of a warp in 9 shuffles: each exchange
 // step hands half of the remaining values to the partner lane.  On return the
 // lanes with (lane & 3) == 0 hold the totals, value (lane >> 2) in lane.

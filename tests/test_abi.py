@@ -68,3 +68,27 @@ def test_grid_step_schedule_matches_oracle():
     for (hmax, hmin, tb, te, T) in ((4.0, 1.0, 0.1, 0.8, 300), (8.0, 1.0, 0.1, 0.8, 300), (2.0, 0.5, 0.0, 1.0, 50)):
         for t in range(T):
             assert abs(lib.ns_grid_step(t, T, hmax, hmin, tb, te) - grid_step(t, T, hmax, hmin, tb, te)) <= 1e-6 * hmax
+
+
+def test_geometry_loss_argument_errors_need_no_gpu():
+    """ns_geometry_loss rejects a bad order or penalty on the host, before any
+    device work."""
+    import ctypes as C
+    lib = binding.load()
+    c = binding.NsCurves()
+    c.n_scenes, c.n_curves, c.height, c.width, c.channels = 1, 0, 32, 32, 3
+    cap = binding.NsCapacity(16, 16, 16)
+    sp = lib.ns_default_sample_params()
+    rp = lib.ns_default_raster_params()
+    gp = lib.ns_default_geometry_params()
+    assert (gp.order, gp.penalty, gp.nodes) == (3, binding.NS_PENALTY_RELU, 0)
+    loss = C.c_void_p(16)   # never dereferenced: the checks fail first
+    ws = C.c_void_p(256)
+    for field, bad, word in (("order", 5, b"order"), ("order", 0, b"order"), ("penalty", 7, b"penalty"),
+                             ("nodes", -1, b"nodes")):
+        g = lib.ns_default_geometry_params()
+        setattr(g, field, bad)
+        st = lib.ns_geometry_loss(C.byref(c), C.byref(sp), C.byref(rp), C.byref(g), C.byref(cap), loss, None, ws,
+                                  C.c_size_t(1 << 20), None)
+        assert st == binding.NS_ERR_INVALID_ARG
+        assert word in lib.ns_last_error()
