@@ -179,12 +179,13 @@ class ClockSampler:
 class Step:
     """Preallocated buffers and the four calls of one training step."""
 
-    def __init__(self, scene, capacity, raster=None, adam=False):
+    def __init__(self, scene, capacity, raster=None, adam=False, geometry=None):
         import torch
         from paper_2606_31764_b300.splat import Splatter, scene_tensors
         self.torch = torch
         self.scene = scene
         self.adam = adam
+        self.geometry = geometry
         self.adam_state = {}
         self.sp = Splatter(scene, raster=raster, capacity=capacity)
         self.key, self.tau, self.color = scene_tensors(scene)
@@ -194,6 +195,7 @@ class Step:
         self.dimage = torch.empty_like(self.image)
         self.loss = torch.zeros(1, device="cuda")
         self.grads = (torch.empty_like(self.key), torch.empty_like(self.tau), torch.empty_like(self.color))
+        self.geo_loss = torch.zeros(2, device="cuda")
 
     def __call__(self):
         sp = self.sp
@@ -201,6 +203,8 @@ class Step:
         sp.forward_gaussians(self.key, self.tau, self.color, self.image)
         sp.mse(self.image, self.target, self.dimage, self.loss)
         sp.backward(self.key, self.tau, self.color, self.dimage, grads=self.grads)
+        if self.geometry is not None:   # regularisers (Eq. 11-12) add their gradients
+            sp.geometry(self.key, self.tau, self.color, self.geo_loss, self.grads, **self.geometry)
         if self.adam:   # fixed step number: the captured graph replays the same bias correction
             sp.adam(self.key, self.tau, self.color, self.grads, self.adam_state, step=10)
 
@@ -208,12 +212,12 @@ class Step:
         return int(self.sp.count.item())
 
 
-def autotune(torch, scene, tiles, capacity, steps=3, adam=False):
+def autotune(torch, scene, tiles, capacity, steps=3, adam=False, geometry=None):
     """Tile size by timing whole steps; pixels per thread of the blend kernels
     by the library's ns_autotune_blend on each tile's workspace."""
     best, best_ms, table = None, None, {}
     for tile in tiles:
-        st = Step(scene, capacity, raster=dict(scene.raster, tile=tile), adam=adam)
+        st = Step(scene, capacity, raster=dict(scene.raster, tile=tile), adam=adam, geometry=geometry)
         st()
         st.sp.autotune_blend(st.key, st.tau, st.color, st.dimage, repeats=3)
         st()
@@ -390,24 +394,54 @@ def run_gpu(args, dist, rank, world):
                blend=dict(evals_fwd=int(rep.blend_evals), evals_bwd=int(rep.blend_bwd_evals),
                           composited=int(rep.blend_contribs)),
                sample=costs)
+    out["geometry"] = run_geometry(torch, step, args)
     if not args.no_per_scene:
         out["per_scene"] = run_per_scene(torch, step, args, value)
         out["long_spline"] = run_long_spline(torch, args)
     return out, step
 
 
+def run_geometry(torch, step, args):
+    """The regularisers (Eq. 11 with r = 3 over N_L midpoint nodes per curve,
+    Eq. 12 over the boundary points) with gradients, on the headline batch's
+    sampling plan: K calls timed with CUDA events, not part of the headline
+    step."""
+    sc = step.scene
+    grads = (torch.zeros_like(step.key), torch.zeros_like(step.tau))
+    loss = torch.zeros(2, device="cuda")
+    for _ in range(2):
+        step.sp.geometry(step.key, step.tau, step.color, loss, grads)
+    K = max(3, args.steps)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(K):
+        step.sp.geometry(step.key, step.tau, step.color, loss, grads)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    nodes = sc.n_curves * int(sc.sample["nl_mult"]) * max(sc.width, sc.height)
+    rep = step.sp.report()
+    return dict(what="ns_geometry_loss with gradients: derivative loss (r = 3) + box loss, Table S1 weights",
+                ms=round(ms, 4), nodes=nodes, boundary_points=int(rep.boundary),
+                nodes_per_s=round(nodes / (ms / 1e3), 1), loss=[round(float(v), 4) for v in loss.cpu()])
+
+
 def run_long_spline(torch, args):
     """The contour-path workload: 256 open cubic strokes with 64-512 key points
-    (~1.5M Gaussians) on a 512x512 grayscale canvas, fwd + bwd + Adam step,
-    graph-captured, timed like the headline (K steps in one graph, per-kernel
-    events)."""
+    (~1.5M Gaussians) on a 512x512 grayscale canvas, fwd + bwd + the
+    calligraphy regularisers (Eq. 11 with r = 3, Eq. 12, Table S1 weights) +
+    Adam step, graph-captured, timed like the headline (K steps in one graph,
+    per-kernel events)."""
     from paper_2606_31764_b300 import binding as B
     sc = scenes.config3()
+    geo = dict(lambda_deriv=1.0, lambda_bbox=5.0, order=3)
     st, tuning = autotune(torch, sc, [int(x) for x in args.tiles.split(",")], capacity=(3_000_000, 24_000_000, 16),
-                          adam=True)
+                          adam=True, geometry=geo)
     st()
     K = max(3, args.steps)
-    prof = ["emit", "bin_emit", "radix_scatter", "blend_fwd", "blend_bwd", "chain_contour"]
+    prof = ["emit", "bin_emit", "radix_scatter", "blend_fwd", "blend_bwd", "chain_contour", "deriv_loss",
+            "bbox_loss"]
     ev = {k: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
           for k in prof}
     for k in prof:
@@ -433,7 +467,9 @@ def run_long_spline(torch, args):
     ms = e0.elapsed_time(e1) / K
     G = st.gaussians()
     rep = st.sp.report()
-    return dict(workload="long-spline-512: 256 open cubic strokes, 64-512 key points, 512x512 gray, + Adam",
+    return dict(workload="long-spline-512: 256 open cubic strokes, 64-512 key points, 512x512 gray, "
+                         "+ derivative and box losses + Adam",
+                geometry_nodes_per_step=sc.n_curves * int(sc.sample["nl_mult"]) * max(sc.width, sc.height),
                 gaussians_per_step=G, pairs_per_step=int(rep.pairs), ms_per_step=round(ms, 4),
                 gaussians_per_s=round(G / (ms / 1e3), 1), autotune=tuning,
                 kernels={k: round(float(np.mean([a.elapsed_time(b) for a, b in ev[k]])), 4) for k in prof})

@@ -276,22 +276,24 @@ typedef struct {
                           [0, width] x [0, height] */
 } ns_geometry_params;
 
-/* lambda_deriv = lambda_bbox = 1, order 3, N_L nodes, ReLU, the canvas. */
+/* Table S1's calligraphy weights lambda_deriv = 1, lambda_bbox = 5; order 3,
+ * N_L nodes, ReLU, the canvas. */
 ns_geometry_params ns_default_geometry_params(void);
 
 /*
  * Geometric regularisers of the total loss (§3.6, Eq. 10-12) and their
- * gradients, on the plan, knot vectors and sample counts that nurbs_sample
- * left in `workspace` (same curves and sample parameters; call it after
- * nurbs_sample, before or after the splat calls of the same step).
+ * gradients, on the plan, knot vectors, boundary polylines and Gaussian set
+ * `g` that nurbs_sample left in `workspace` and wrote to `g` (same curves and
+ * sample parameters; call it after nurbs_sample, before or after the splat
+ * calls of the same step).
  *   Derivative loss (Eq. 11): per curve, (1/(b - a)) int_a^b |C^(r)_xy(u)|^2 du
  *     over its domain [a, b] = [u_p, u_{m-p}], by the `nodes`-node midpoint
  *     rule of Eq. 3, with C^(r) the exact r-th derivative of the rational
  *     curve (Eq. 1-2 differentiated r times); averaged over all curves.
  *   Bounding-box loss (Eq. 12): sum over the sampled curve points -- the M
- *     contour samples of every stroke (not the endpoint copies) and the
+ *     contour centres of every stroke (not the endpoint copies) and the
  *     boundary points of every filled curve -- of phi(b_min - P) + phi(P -
- *     b_max), per axis.
+ *     b_max), per axis.  g->rec, g->curve and g->count are read for it.
  *   loss: device float[2], overwritten with {lambda_deriv * L_deriv,
  *     lambda_bbox * L_bbox}.
  *   out: NULL for the values only; otherwise the gradients with respect to
@@ -301,8 +303,9 @@ ns_geometry_params ns_default_geometry_params(void);
  * Uses the workspace's knot-gradient scratch, so it must not run concurrently
  * with splat_backward on the same workspace (the same stream orders them).
  */
-ns_status ns_geometry_loss(const ns_curves* curves, const ns_sample_params* sp,
-                           const ns_raster_params* rp, const ns_geometry_params* gp,
+ns_status ns_geometry_loss(const ns_curves* curves, const ns_gaussians* g,
+                           const ns_sample_params* sp, const ns_raster_params* rp,
+                           const ns_geometry_params* gp,
                            const ns_capacity* cap, float* loss, const ns_curve_grads* out,
                            void* workspace, size_t workspace_bytes, void* stream);
 

@@ -90,7 +90,8 @@ SIGNATURES = {
     "splat_forward_noalloc": (C.c_int, [C.POINTER(NsCurves), C.POINTER(NsGaussians), C.POINTER(NsRasterParams),
                                         _p, C.POINTER(NsReport), _p]),
     "ns_default_geometry_params": (NsGeometryParams, []),
-    "ns_geometry_loss": (C.c_int, [C.POINTER(NsCurves), C.POINTER(NsSampleParams), C.POINTER(NsRasterParams),
+    "ns_geometry_loss": (C.c_int, [C.POINTER(NsCurves), C.POINTER(NsGaussians), C.POINTER(NsSampleParams),
+                                   C.POINTER(NsRasterParams),
                                    C.POINTER(NsGeometryParams), C.POINTER(NsCapacity), _p, C.POINTER(NsCurveGrads),
                                    _p, C.c_size_t, _p]),
     "ns_launch_count": (C.c_uint64, []),

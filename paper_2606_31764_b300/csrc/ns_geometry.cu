@@ -2,7 +2,7 @@
 // with their gradients, on the plan and knots that nurbs_sample left in the
 // workspace.
 //
-//   k_deriv_loss     Eq. 11: per curve the mean of |C^(r)_xy|^2 over N
+//   k_deriv_loss<P,R> Eq. 11: per curve the mean of |C^(r)_xy|^2 over N
 //                    midpoint nodes u_j = a + (j + 1/2)(b - a)/N of the domain.
 //                    C^(r) comes from the homogeneous curve S_h = sum N_i w_i
 //                    (x_i, y_i, 1): its k-th derivative is a degree p-k
@@ -18,10 +18,12 @@
 //                    (the triangle's reverse sweep takes adjoints at every level).
 //                    Each thread walks a run of consecutive nodes and keeps the
 //                    span's gradients in registers until the span changes.
-//   k_bbox_contour   Eq. 12 over the contour samples of strokes (the M samples,
-//   k_bbox_boundary  not the endpoint copies) and the boundary points of fills:
-//                    per axis phi(b_min - P) + phi(P - b_max), phi ReLU or
-//                    softplus; nonzero gradients go back through C(u).
+//   k_bbox_contour   Eq. 12 over the contour samples of strokes (the M sampled
+//   k_bbox_boundary  centres, not the endpoint copies) and the boundary points
+//                    of fills, both read from what nurbs_sample wrote: per axis
+//                    phi(b_min - P) + phi(P - b_max), phi ReLU or softplus;
+//                    where the slope is nonzero the gradient goes back through
+//                    C(u).
 //   k_knot_grads     (ns_backward.cu) turns the knot gradients into dtau.
 #include <cuda_runtime.h>
 
@@ -120,11 +122,12 @@ __device__ __forceinline__ void acc_flush(const CurveRef& cr, SpanAcc<P>& a, flo
     if (a.kn[k] != 0.f) atomicAdd(dknots + cr.knot0 + a.span - P + 1 + k, a.kn[k]);
 }
 
-// One quadrature node: returns |C^(r)_xy(u)|^2; with `acc` adds the gradient
-// of scale * |C^(r)|^2 and returns dL/du in *du.
-template <int P>
+// One quadrature node: returns |C^(R)_xy(u)|^2; with `acc` adds the gradient
+// of scale * |C^(R)|^2 and returns dL/du in *du.
+template <int P, int R>
 __device__ float deriv_node(const float4* __restrict__ key, const CurveRef& cr, const float* __restrict__ U, int i,
-                            float u, int r, float scale, SpanAcc<P>* acc, float* du) {
+                            float u, float scale, SpanAcc<P>* acc, float* du) {
+  constexpr int r = R;
   constexpr int KM = P < kMaxOrder ? P : kMaxOrder;   // highest nonzero S_h derivative
   Tri<P> t;
   basis_fwd<P>(U, i, u, t);
@@ -275,7 +278,7 @@ __device__ float deriv_node(const float4* __restrict__ key, const CurveRef& cr, 
   return f;
 }
 
-template <int P>
+template <int P, int R>
 __device__ float deriv_run(const ns_curves& cv, const CurveRef& cr, const float* U, const CurvePlan& pl,
                            const GeoParams& gp, int j0, int j1, float* dkey, float* dknots) {
   SpanAcc<P> acc;
@@ -291,8 +294,8 @@ __device__ float deriv_run(const ns_curves& cv, const CurveRef& cr, const float*
       acc_clear<P>(acc, i);
     }
     float du = 0.f;
-    sum += deriv_node<P>(reinterpret_cast<const float4*>(cv.key), cr, U, i, u, gp.order, gp.scale_d,
-                         grads ? &acc : nullptr, &du);
+    sum += deriv_node<P, R>(reinterpret_cast<const float4*>(cv.key), cr, U, i, u, gp.scale_d,
+                            grads ? &acc : nullptr, &du);
     dA += du * (1.f - t);   // u = a + t (b - a)
     dB += du * t;
   }
@@ -319,6 +322,9 @@ __device__ __forceinline__ void block_sum_add(float v, float* out) {
   }
 }
 
+// One kernel per (degree, order): each handles the curves of its degree (the
+// degree-5 register count would otherwise set the occupancy of every curve).
+template <int P, int R>
 __global__ void __launch_bounds__(kGeoThreads) k_deriv_loss(ns_curves cv, const CurvePlan* __restrict__ plan,
                                                             const float* __restrict__ knots, GeoParams gp,
                                                             float* loss, float* dkey, float* dknots) {
@@ -333,15 +339,35 @@ __global__ void __launch_bounds__(kGeoThreads) k_deriv_loss(ns_curves cv, const 
     const long long idx = it * stride + blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= total) continue;
     const int c = int(idx / runs);
+    if (cv.degree[c] != P) continue;
     const int run = int(idx - (long long)c * runs);
     const CurvePlan pl = plan[c];
     if (pl.kind == kNone) continue;
     const CurveRef cr = curve_ref(cv, c);
     const float* U = knots + cr.knot0;
     const int j0 = run * kDerivRun, j1 = min(j0 + kDerivRun, gp.nodes);
-    NS_DISPATCH_P(cr.p, sum += deriv_run<P>(cv, cr, U, pl, gp, j0, j1, dkey, dknots));
+    sum += deriv_run<P, R>(cv, cr, U, pl, gp, j0, j1, dkey, dknots);
   }
   block_sum_add(sum, loss);
+}
+
+template <int R>
+void launch_deriv_loss(const ns_curves& cv, const CurvePlan* plan, const float* knots, const GeoParams& gp,
+                       float* loss, float* dkey, float* dknots, cudaStream_t s) {
+  const int grid = num_sms() * 8;
+  // the five launches form one profiled range (armed events bracket the first
+  // and the last)
+  auto run = [&](void (*k)(ns_curves, const CurvePlan*, const float*, GeoParams, float*, float*, float*),
+                 int first_id, int last_id) {
+    before_launch(first_id, s);
+    k<<<grid, kGeoThreads, 0, s>>>(cv, plan, knots, gp, loss, dkey, dknots);
+    after_launch(last_id, s);
+  };
+  run(k_deriv_loss<1, R>, NS_KERNEL_DERIV_LOSS, -1);
+  run(k_deriv_loss<2, R>, -1, -1);
+  run(k_deriv_loss<3, R>, -1, -1);
+  run(k_deriv_loss<4, R>, -1, -1);
+  run(k_deriv_loss<5, R>, -1, NS_KERNEL_DERIV_LOSS);
 }
 
 // Penalty of one point and its gradient dL/dP (before the lambda scale).
@@ -364,66 +390,80 @@ __device__ __forceinline__ float box_penalty(const GeoParams& gp, float x, float
   return f;
 }
 
+// Gradient of the penalty at one curve point C(u), u = a + t (b - a): back
+// through C(u) (Eq. 1) into control points, weights and knots.
 template <int P>
-__device__ float bbox_point(const ns_curves& cv, const CurveRef& cr, const float* U, const CurvePlan& pl,
-                            const GeoParams& gp, float u, float t, float* dkey, float* dknots) {
+__device__ void bbox_grad(const ns_curves& cv, const CurveRef& cr, const float* U, float u, float t, float gx,
+                          float gy, float* dkey, float* dknots) {
   const int i = find_span(U, P, cr.n, u);
   Eval<P> e;
   eval_curve<P>(reinterpret_cast<const float4*>(cv.key), cr, U, i, u, e);
-  float gx, gy;
-  const float f = box_penalty(gp, e.C[0], e.C[1], &gx, &gy);
-  if (dkey && (gx != 0.f || gy != 0.f)) {
-    const float gC[3] = {gp.scale_b * gx, gp.scale_b * gy, 0.f};
-    float dcp[P + 1][4], dkn[2 * P], du = 0.f;
+  const float gC[3] = {gx, gy, 0.f};
+  float dcp[P + 1][4], dkn[2 * P], du = 0.f;
 #pragma unroll
-    for (int l = 0; l <= P; ++l) dcp[l][0] = dcp[l][1] = dcp[l][2] = dcp[l][3] = 0.f;
+  for (int l = 0; l <= P; ++l) dcp[l][0] = dcp[l][1] = dcp[l][2] = dcp[l][3] = 0.f;
 #pragma unroll
-    for (int k = 0; k < 2 * P; ++k) dkn[k] = 0.f;
-    curve_point_adjoint<P>(e, gC, dcp, dkn, &du);
+  for (int k = 0; k < 2 * P; ++k) dkn[k] = 0.f;
+  curve_point_adjoint<P>(e, gC, dcp, dkn, &du);
 #pragma unroll
-    for (int l = 0; l <= P; ++l) {
-      float* d = dkey + 4 * (long long)(cr.key0 + cp_to_key(i - P + l, P, cr.closed, cr.nk));
-      if (dcp[l][0] != 0.f) atomicAdd(d + 0, dcp[l][0]);
-      if (dcp[l][1] != 0.f) atomicAdd(d + 1, dcp[l][1]);
-      if (dcp[l][3] != 0.f) atomicAdd(d + 3, dcp[l][3]);
-    }
-#pragma unroll
-    for (int k = 0; k < 2 * P; ++k)
-      if (dkn[k] != 0.f) atomicAdd(dknots + cr.knot0 + i - P + 1 + k, dkn[k]);
-    const float dA = du * (1.f - t), dB = du * t;   // u = a + t (b - a)
-    if (dA != 0.f) atomicAdd(dknots + cr.knot0 + cr.p, dA);
-    if (dB != 0.f) atomicAdd(dknots + cr.knot0 + cr.n + 1, dB);
+  for (int l = 0; l <= P; ++l) {
+    float* d = dkey + 4 * (long long)(cr.key0 + cp_to_key(i - P + l, P, cr.closed, cr.nk));
+    if (dcp[l][0] != 0.f) atomicAdd(d + 0, dcp[l][0]);
+    if (dcp[l][1] != 0.f) atomicAdd(d + 1, dcp[l][1]);
+    if (dcp[l][3] != 0.f) atomicAdd(d + 3, dcp[l][3]);
   }
-  return f;
+#pragma unroll
+  for (int k = 0; k < 2 * P; ++k)
+    if (dkn[k] != 0.f) atomicAdd(dknots + cr.knot0 + i - P + 1 + k, dkn[k]);
+  const float dA = du * (1.f - t), dB = du * t;
+  if (dA != 0.f) atomicAdd(dknots + cr.knot0 + cr.p, dA);
+  if (dB != 0.f) atomicAdd(dknots + cr.knot0 + cr.n + 1, dB);
 }
 
-// Contour samples of strokes: one thread per sample of a contour task.
-__global__ void __launch_bounds__(kChunk) k_bbox_contour(ns_curves cv, const CurvePlan* __restrict__ plan,
-                                                         const int* __restrict__ order,
-                                                         const float* __restrict__ knots,
-                                                         const DevState* __restrict__ st, GeoParams gp,
-                                                         float* loss, float* dkey, float* dknots) {
-  const int n_tasks = st->n_ctasks;
+// Contour samples of strokes, read from the sampled records: a contour
+// Gaussian's centre is C(u_j) (Eq. 4).  Fill Gaussians and the endpoint
+// copies of open curves are skipped.
+__global__ void __launch_bounds__(kGeoThreads) k_bbox_contour(ns_curves cv, const CurvePlan* __restrict__ plan,
+                                                              const float* __restrict__ knots,
+                                                              const float4* __restrict__ rec,
+                                                              const int* __restrict__ gcurve,
+                                                              const int* __restrict__ gcount, GeoParams gp,
+                                                              float* loss, float* dkey, float* dknots) {
+  const int n = *gcount;
   const int nc = cv.n_curves;
+  const int stride = gridDim.x * blockDim.x;
+  const int iters = (n + stride - 1) / stride;
   float sum = 0.f;
-  for (int task = blockIdx.x; task < n_tasks; task += gridDim.x) {
-    const int c = curve_of_task(plan, order, nc, task, false);
-    const CurvePlan pl = plan[c];
-    const int l = (task - pl.chunk_off) * kChunk + threadIdx.x;
-    if (l >= pl.count) continue;
-    if (pl.kind == kOpen && (l < gp.kappa || l >= gp.kappa + pl.M)) continue;   // endpoint copies
-    const CurveRef cr = curve_ref(cv, c);
-    const float* U = knots + cr.knot0;
-    const float t = contour_t(pl, l, gp.kappa);
-    const float u = contour_u(pl, l, gp.kappa);
-    NS_DISPATCH_P(cr.p, sum += bbox_point<P>(cv, cr, U, pl, gp, u, t, dkey, dknots));
+  for (int it = 0; it < iters; ++it) {
+    const int gi = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= n) continue;
+    const int c = gcurve[gi];
+    if (c < 0 || c >= nc) continue;
+    const CurvePlan& pl = plan[c];
+    const int kind = pl.kind;
+    if (kind != kOpen && kind != kClosedStroke) continue;
+    const int l = gi - pl.g_off;
+    if (l < 0 || l >= pl.count) continue;
+    if (kind == kOpen && (l < gp.kappa || l >= gp.kappa + pl.M)) continue;   // endpoint copies
+    const float4 r = rec[gi];
+    float gx, gy;
+    sum += box_penalty(gp, r.x, r.y, &gx, &gy);
+    if (dkey && (gx != 0.f || gy != 0.f)) {
+      const CurvePlan q = pl;
+      const CurveRef cr = curve_ref(cv, c);
+      const float* U = knots + cr.knot0;
+      const float t = contour_t(q, l, gp.kappa);
+      const float u = contour_u(q, l, gp.kappa);
+      NS_DISPATCH_P(cr.p, bbox_grad<P>(cv, cr, U, u, t, gp.scale_b * gx, gp.scale_b * gy, dkey, dknots));
+    }
   }
   block_sum_add(sum * gp.scale_b, loss);
 }
 
-// Boundary points of filled curves.
+// Boundary points of filled curves, read from the polyline nurbs_sample built.
 __global__ void __launch_bounds__(kGeoThreads) k_bbox_boundary(ns_curves cv, const CurvePlan* __restrict__ plan,
                                                                const float* __restrict__ knots,
+                                                               const float2* __restrict__ bpts,
                                                                const DevState* __restrict__ st, GeoParams gp,
                                                                float* loss, float* dkey, float* dknots) {
   const int nb = st->b_count;
@@ -434,20 +474,23 @@ __global__ void __launch_bounds__(kGeoThreads) k_bbox_boundary(ns_curves cv, con
   for (int it = 0; it < iters; ++it) {
     const int j = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= nb) continue;
+    const float2 b = bpts[j];
+    float gx, gy;
+    sum += box_penalty(gp, b.x, b.y, &gx, &gy);
+    if (!dkey || (gx == 0.f && gy == 0.f)) continue;
     int lo = 0, hi = nc - 1;   // largest curve with b_off <= j
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
       if (plan[mid].b_off <= j) lo = mid; else hi = mid - 1;
     }
     const CurvePlan pl = plan[lo];
-    if (pl.kind != kFill) continue;
     const int jj = j - pl.b_off;
-    if (jj >= pl.M) continue;
+    if (pl.kind != kFill || jj >= pl.M) continue;
     const CurveRef cr = curve_ref(cv, lo);
     const float* U = knots + cr.knot0;
     const float t = float(jj) / float(pl.M);
     const float u = pl.a + t * (pl.b - pl.a);
-    NS_DISPATCH_P(cr.p, sum += bbox_point<P>(cv, cr, U, pl, gp, u, t, dkey, dknots));
+    NS_DISPATCH_P(cr.p, bbox_grad<P>(cv, cr, U, u, t, gp.scale_b * gx, gp.scale_b * gy, dkey, dknots));
   }
   block_sum_add(sum * gp.scale_b, loss);
 }
@@ -461,17 +504,17 @@ extern "C" ns_geometry_params ns_default_geometry_params(void) {
   g.lambda_deriv = 1.f;
   g.order = 3;
   g.nodes = 0;
-  g.lambda_bbox = 1.f;
+  g.lambda_bbox = 5.f;
   g.penalty = NS_PENALTY_RELU;
   g.box[0] = g.box[1] = g.box[2] = g.box[3] = 0.f;
   return g;
 }
 
-extern "C" ns_status ns_geometry_loss(const ns_curves* curves, const ns_sample_params* sp,
+extern "C" ns_status ns_geometry_loss(const ns_curves* curves, const ns_gaussians* g, const ns_sample_params* sp,
                                       const ns_raster_params* rp, const ns_geometry_params* gpar,
                                       const ns_capacity* cap, float* loss, const ns_curve_grads* out,
                                       void* ws, size_t ws_bytes, void* stream) {
-  if (!curves || !sp || !rp || !gpar || !cap || !loss || !ws) {
+  if (!curves || !g || !sp || !rp || !gpar || !cap || !loss || !ws) {
     set_error("ns_geometry_loss: null argument");
     return NS_ERR_INVALID_ARG;
   }
@@ -497,6 +540,10 @@ extern "C" ns_status ns_geometry_loss(const ns_curves* curves, const ns_sample_p
     set_error("ns_geometry_loss: workspace smaller than ns_workspace_size");
     return NS_ERR_INVALID_ARG;
   }
+  if (gpar->lambda_bbox != 0.f && (!g->rec || !g->curve || !g->count)) {
+    set_error("ns_geometry_loss: the box loss reads the Gaussian records, curves and count");
+    return NS_ERR_INVALID_ARG;
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaMemsetAsync(loss, 0, 2 * sizeof(float), s);
   if (L.nc > 0) {
@@ -514,19 +561,29 @@ extern "C" ns_status ns_geometry_loss(const ns_curves* curves, const ns_sample_p
     gp.kappa = sp->kappa;
     const CurvePlan* plan = at<const CurvePlan>(ws, L.o_plan);
     const float* knots = at<const float>(ws, L.o_knots);
-    const int* order = at<const int>(ws, L.o_order);
     const DevState* st = at<const DevState>(ws, L.o_state);
     float* dknots = out ? at<float>(ws, L.o_dknots) : nullptr;
     float* dkey = out ? out->dkey : nullptr;
     if (out) cudaMemsetAsync(dknots, 0, sizeof(float) * ((size_t)L.nt + (size_t)kKnotPad * L.nc), s);
-    if (gpar->lambda_deriv != 0.f)
-      NS_LAUNCH(NS_KERNEL_DERIV_LOSS, k_deriv_loss, num_sms() * 8, kGeoThreads, 0, s, *curves, plan, knots, gp,
-                loss, dkey, dknots);
+    if (gpar->lambda_deriv != 0.f) {
+      switch (gp.order) {
+        case 1: launch_deriv_loss<1>(*curves, plan, knots, gp, loss, dkey, dknots, s); break;
+        case 2: launch_deriv_loss<2>(*curves, plan, knots, gp, loss, dkey, dknots, s); break;
+        case 3: launch_deriv_loss<3>(*curves, plan, knots, gp, loss, dkey, dknots, s); break;
+        default: launch_deriv_loss<4>(*curves, plan, knots, gp, loss, dkey, dknots, s); break;
+      }
+    }
     if (gpar->lambda_bbox != 0.f) {
-      NS_LAUNCH(NS_KERNEL_BBOX_LOSS, k_bbox_contour, num_sms() * 4, kChunk, 0, s, *curves, plan, order, knots, st,
-                gp, loss + 1, dkey, dknots);
-      NS_LAUNCH(NS_KERNEL_BBOX_LOSS, k_bbox_boundary, num_sms() * 4, kGeoThreads, 0, s, *curves, plan, knots, st,
-                gp, loss + 1, dkey, dknots);
+      // the two launches form one profiled range
+      const int grid = num_sms() * 8;
+      before_launch(NS_KERNEL_BBOX_LOSS, s);
+      k_bbox_contour<<<grid, kGeoThreads, 0, s>>>(*curves, plan, knots, reinterpret_cast<const float4*>(g->rec),
+                                                  g->curve, g->count, gp, loss + 1, dkey, dknots);
+      after_launch(-1, s);
+      before_launch(-1, s);
+      k_bbox_boundary<<<grid, kGeoThreads, 0, s>>>(*curves, plan, knots, at<const float2>(ws, L.o_bpts), st, gp,
+                                                   loss + 1, dkey, dknots);
+      after_launch(NS_KERNEL_BBOX_LOSS, s);
     }
     if (out) launch_knot_grads(*curves, plan, dknots, out->dtau, s);
   }

@@ -178,12 +178,13 @@ class Splatter:
                C.c_size_t(self.ws_bytes), _stream())
         return grads
 
-    def geometry(self, key, tau, color, loss, grads=None, lambda_deriv=1.0, order=3, nodes=0, lambda_bbox=1.0,
+    def geometry(self, key, tau, color, loss, grads=None, lambda_deriv=1.0, order=3, nodes=0, lambda_bbox=5.0,
                  penalty="relu", box=None):
         """Geometric regularisers (Eq. 11 derivative loss, Eq. 12 box loss) on the
         plan of the last sample() (ns_geometry_loss).  loss: device float[2],
         overwritten with the weighted terms; grads: (dkey, dtau, ...) device
         tensors the gradients are ADDED to, or None for the values only.
+        Default weights: Table S1's calligraphy setting (1 and 5).
         box: (x_min, y_min, x_max, y_max), default the canvas."""
         cs = self.dev.struct(key, tau, color)
         gp = B.NsGeometryParams()
@@ -192,7 +193,8 @@ class Splatter:
         for i, v in enumerate(box or (0.0, 0.0, 0.0, 0.0)):
             gp.box[i] = v
         out = B.NsCurveGrads(_ptr(grads[0]), _ptr(grads[1]), None) if grads is not None else None
-        B.call("ns_geometry_loss", C.byref(cs), C.byref(self.sp), C.byref(self.rp), C.byref(gp), C.byref(self.cap),
+        B.call("ns_geometry_loss", C.byref(cs), C.byref(self.g), C.byref(self.sp), C.byref(self.rp), C.byref(gp),
+               C.byref(self.cap),
                _ptr(loss), C.byref(out) if out is not None else None, _ptr(self.ws), C.c_size_t(self.ws_bytes),
                _stream())
         return loss

@@ -45,6 +45,10 @@ def test_defaults_match_table_s1():
     gold = json.load(open(os.path.join(ROOT, "tests", "golden", "table_s1_defaults.json")))
     for k in ("delta_c", "rho", "delta_b", "h", "eta", "gamma", "kappa", "nl_mult"):
         assert getattr(sp, k) == pytest.approx(gold[k]), k
+    gp = lib.ns_default_geometry_params()
+    assert gp.lambda_deriv == pytest.approx(gold["lambda_deriv_calligraphy"])
+    assert gp.lambda_bbox == pytest.approx(gold["lambda_bbox_calligraphy"])
+    assert gp.order == 3
 
 
 def test_host_side_argument_errors_need_no_gpu():
@@ -88,7 +92,8 @@ def test_geometry_loss_argument_errors_need_no_gpu():
                              ("nodes", -1, b"nodes")):
         g = lib.ns_default_geometry_params()
         setattr(g, field, bad)
-        st = lib.ns_geometry_loss(C.byref(c), C.byref(sp), C.byref(rp), C.byref(g), C.byref(cap), loss, None, ws,
-                                  C.c_size_t(1 << 20), None)
+        gs = binding.NsGaussians()
+        st = lib.ns_geometry_loss(C.byref(c), C.byref(gs), C.byref(sp), C.byref(rp), C.byref(g), C.byref(cap), loss,
+                                  None, ws, C.c_size_t(1 << 20), None)
         assert st == binding.NS_ERR_INVALID_ARG
         assert word in lib.ns_last_error()

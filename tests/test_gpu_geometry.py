@@ -85,7 +85,7 @@ def test_canvas_box_default_and_values_only():
     the same; gradients are added to what the outputs already hold."""
     sc = scenes.small_open(66, n_curves=3, size=40)
     plans = op.plan(sc)
-    ref = og.geometry_loss_and_grads(sc, plans, kind=og.SOFTPLUS)
+    ref = og.geometry_loss_and_grads(sc, plans, lambda_bbox=5.0, kind=og.SOFTPLUS)   # the library's default weights
     out = _run(sc, penalty="softplus")
     _check(sc, ref, out)
     vals = _run(sc, grads=False, penalty="softplus")
