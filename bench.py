@@ -179,13 +179,14 @@ class ClockSampler:
 class Step:
     """Preallocated buffers and the four calls of one training step."""
 
-    def __init__(self, scene, capacity, raster=None, adam=False, geometry=None):
+    def __init__(self, scene, capacity, raster=None, adam=False, geometry=None, frozen=()):
         import torch
         from paper_2606_31764_b300.splat import Splatter, scene_tensors
         self.torch = torch
         self.scene = scene
         self.adam = adam
         self.geometry = geometry
+        self.frozen = tuple(frozen)
         self.adam_state = {}
         self.sp = Splatter(scene, raster=raster, capacity=capacity)
         self.key, self.tau, self.color = scene_tensors(scene)
@@ -202,11 +203,12 @@ class Step:
         sp.sample(self.key, self.tau, self.color)
         sp.forward_gaussians(self.key, self.tau, self.color, self.image)
         sp.mse(self.image, self.target, self.dimage, self.loss)
-        sp.backward(self.key, self.tau, self.color, self.dimage, grads=self.grads)
+        sp.backward(self.key, self.tau, self.color, self.dimage, grads=self.grads, frozen=self.frozen)
         if self.geometry is not None:   # regularisers (Eq. 11-12) add their gradients
-            sp.geometry(self.key, self.tau, self.color, self.geo_loss, self.grads, **self.geometry)
+            sp.geometry(self.key, self.tau, self.color, self.geo_loss, self.grads, frozen=self.frozen,
+                        **self.geometry)
         if self.adam:   # fixed step number: the captured graph replays the same bias correction
-            sp.adam(self.key, self.tau, self.color, self.grads, self.adam_state, step=10)
+            sp.adam(self.key, self.tau, self.color, self.grads, self.adam_state, step=10, frozen=self.frozen)
 
     def gaussians(self):
         return int(self.sp.count.item())
@@ -467,12 +469,39 @@ def run_long_spline(torch, args):
     ms = e0.elapsed_time(e1) / K
     G = st.gaussians()
     rep = st.sp.report()
+    ablation = run_ablation(torch, sc, st, tuning, geo, K)
     return dict(workload="long-spline-512: 256 open cubic strokes, 64-512 key points, 512x512 gray, "
                          "+ derivative and box losses + Adam",
                 geometry_nodes_per_step=sc.n_curves * int(sc.sample["nl_mult"]) * max(sc.width, sc.height),
                 gaussians_per_step=G, pairs_per_step=int(rep.pairs), ms_per_step=round(ms, 4),
                 gaussians_per_s=round(G / (ms / 1e3), 1), autotune=tuning,
-                kernels={k: round(float(np.mean([a.elapsed_time(b) for a, b in ev[k]])), 4) for k in prof})
+                kernels={k: round(float(np.mean([a.elapsed_time(b) for a, b in ev[k]])), 4) for k in prof},
+                ablation=ablation)
+
+
+def run_ablation(torch, sc, st, tuning, geo, K):
+    """The frozen-parameter variants of Table 1 on the long-spline step (same
+    tile and blend decomposition): ms per step with rational weights, knot
+    intervals, or both held fixed (their gradients not formed, no update)."""
+    out = {"full": None}
+    for name, frozen in (("w/o weights", ("weights",)), ("w/o knots", ("knots",)),
+                         ("w/o w&k", ("weights", "knots")), ("full", ())):
+        s2 = Step(sc, capacity=(3_000_000, 24_000_000, 16), raster=dict(sc.raster, tile=tuning["tile"]), adam=True,
+                  geometry=geo, frozen=frozen)
+        s2.sp.rp.ppt_fwd, s2.sp.rp.ppt_bwd = tuning["ppt_fwd"], tuning["ppt_bwd"]
+        s2()
+        g2 = capture(torch, s2, K)
+        g2.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g2.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = round(e0.elapsed_time(e1) / K, 4)
+        del g2, s2
+        torch.cuda.empty_cache()
+    return dict(ms_per_step=out, note="same step as above; each variant captured and timed on its own")
 
 
 def run_e2e(torch, step, g1, args):

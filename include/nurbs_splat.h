@@ -128,12 +128,19 @@ typedef struct {
   int32_t* count;   /* device scalar: records in use */
 } ns_gaussians;
 
+/* Parameters held fixed (the paper's "w/o weights", "w/o knots" and "w/o
+ * w & k" variants, Table 1): their gradients are not formed. */
+#define NS_FROZEN_WEIGHTS 1  /* rational weights: nothing is added to dkey's w column */
+#define NS_FROZEN_KNOTS 2    /* knot intervals: dtau may be NULL and is not touched;
+                                the reverse sweeps that only feed knot gradients are skipped */
+
 /* Gradient outputs, caller-owned device memory, accumulated into (the caller
  * zeroes them, or passes zero_outputs = 1 to splat_backward). */
 typedef struct {
   float* dkey;      /* device [n_keys*4]: dL/d{x, y, s, w} */
-  float* dtau;      /* device [n_taus] */
+  float* dtau;      /* device [n_taus]; may be NULL with NS_FROZEN_KNOTS */
   float* dcolor;    /* device [n_curves*4]: dL/d{r, g, b, opacity} */
+  int32_t frozen;   /* NS_FROZEN_WEIGHTS | NS_FROZEN_KNOTS, or 0 */
 } ns_curve_grads;
 
 /* What ns_poll_status reads back. */
@@ -298,7 +305,7 @@ ns_geometry_params ns_default_geometry_params(void);
  *     lambda_bbox * L_bbox}.
  *   out: NULL for the values only; otherwise the gradients with respect to
  *     the key points {x, y, w} and knot intervals are ADDED to out->dkey and
- *     out->dtau (out->dcolor is not touched).  Knot spans of the nodes and the
+ *     out->dtau (out->dcolor is not touched), except those out->frozen names.  Knot spans of the nodes and the
  *     sample counts are held fixed, as in splat_backward.
  * Uses the workspace's knot-gradient scratch, so it must not run concurrently
  * with splat_backward on the same workspace (the same stream orders them).

@@ -55,7 +55,10 @@ NS_PENALTY_RELU, NS_PENALTY_SOFTPLUS = 0, 1
 
 
 class NsCurveGrads(C.Structure):
-    _fields_ = [("dkey", _p), ("dtau", _p), ("dcolor", _p)]
+    _fields_ = [("dkey", _p), ("dtau", _p), ("dcolor", _p), ("frozen", C.c_int32)]
+
+
+NS_FROZEN_WEIGHTS, NS_FROZEN_KNOTS = 1, 2
 
 
 class NsReport(C.Structure):

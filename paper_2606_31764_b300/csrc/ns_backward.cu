@@ -35,47 +35,45 @@ constexpr int kWin = 1024;   // control points (and knots) per task window in sh
 constexpr int kWinB = 2 * kWin;  // boundary points per fill task window
 
 // Reverse of one curve point: gC = dL/dC (x, y, s) at parameter u (span i,
-// domain fraction t).  Adds to the control-point and knot accumulators.
-template <int P, class AddCP, class AddKnot>
+// domain fraction t).  Hands the control-point and knot gradients to the
+// accumulators and adds the domain-end terms to dA, dB.
+template <int P, bool KNOTS, class AddCP, class AddKnot>
 __device__ __forceinline__ void curve_point_bwd(const ns_curves& cv, const CurveRef& cr, const float* U, int i,
                                                 float u, float t, const float gC[3], AddCP add_cp,
                                                 AddKnot add_knot, float& dA, float& dB) {
   Eval<P> e;
   eval_curve<P>(reinterpret_cast<const float4*>(cv.key), cr, U, i, u, e);
-  const float iw = 1.f / e.W;
-  float gN[P + 1];
+  float dcp[P + 1][4], dU[2 * P], du = 0.f;
 #pragma unroll
-  for (int l = 0; l <= P; ++l) {
-    const float4 q = e.cp[l];
-    const float R = e.t.N[l] * q.w * iw;              // rational basis N w / W
-    const float proj = gC[0] * (q.x - e.C[0]) + gC[1] * (q.y - e.C[1]) + gC[2] * (q.z - e.C[2]);
-    gN[l] = q.w * proj * iw;                            // dL/dN_l
-    add_cp(i - P + l, gC[0] * R, gC[1] * R, gC[2] * R, e.t.N[l] * proj * iw);
-  }
-  float du = 0.f, dU[2 * P];
+  for (int l = 0; l <= P; ++l) dcp[l][0] = dcp[l][1] = dcp[l][2] = dcp[l][3] = 0.f;
 #pragma unroll
   for (int k = 0; k < 2 * P; ++k) dU[k] = 0.f;
-  basis_bwd<P>(e.t, gN, &du, dU);
+  curve_point_adjoint<P, KNOTS>(e, gC, dcp, dU, &du);
 #pragma unroll
-  for (int k = 0; k < 2 * P; ++k) add_knot(i - P + 1 + k, dU[k]);
-  dA += du * (1.f - t);   // u = a + t (b - a)
-  dB += du * t;
+  for (int l = 0; l <= P; ++l) add_cp(i - P + l, dcp[l][0], dcp[l][1], dcp[l][2], dcp[l][3]);
+  if constexpr (KNOTS) {
+#pragma unroll
+    for (int k = 0; k < 2 * P; ++k) add_knot(i - P + 1 + k, dU[k]);
+    dA += du * (1.f - t);   // u = a + t (b - a)
+    dB += du * t;
+  }
 }
 
 // Reverse of one curve point into arrays: dcp[l] = dL/d{x, y, s, w} of the
 // span's control point i-P+l, dkn[k] = dL/dU[i-P+1+k], du = dL/du.
-template <int P>
+template <int P, bool KNOTS>
 __device__ __forceinline__ void curve_point_bwd_local(const float4* key, const CurveRef& cr, const float* U, int i,
                                                       float u, const float gC[3], float dcp[P + 1][4],
                                                       float dkn[2 * P], float& du) {
   Eval<P> e;
   eval_curve<P>(key, cr, U, i, u, e);
-  curve_point_adjoint<P>(e, gC, dcp, dkn, &du);
+  curve_point_adjoint<P, KNOTS>(e, gC, dcp, dkn, &du);
 }
 
 struct ChainParams {
   float rho, h, gamma;
   int kappa;
+  int freeze_w;   // rational weights frozen: no dL/dw is written
 };
 
 template <int P>
@@ -189,7 +187,7 @@ __global__ void __launch_bounds__(256) k_chain(ns_curves cv, ChainParams cp, con
 constexpr int kContourThreads = 64;
 constexpr int kContourPer = kChunk / kContourThreads;
 
-template <int P>
+template <int P, bool KNOTS>
 __device__ void chain_contour_run(const ns_curves& cv, const CurveRef& cr, const float* U, const CurvePlan& pl,
                                   int l0, const ChainParams& cp, const float* __restrict__ dgauss, long long gcap,
                                   float* s_cp, float* s_kn, int cp_lo, int kn_lo, int ncp, int nkn, float* dkey,
@@ -207,20 +205,22 @@ __device__ void chain_contour_run(const ns_curves& cv, const CurveRef& cr, const
         atomicAdd(a + 0, acc[l][0]);
         atomicAdd(a + 1, acc[l][1]);
         atomicAdd(a + 2, acc[l][2]);
-        atomicAdd(a + 3, acc[l][3]);
+        if (!cp.freeze_w) atomicAdd(a + 3, acc[l][3]);
       } else {
         float* a = dkey + 4 * (long long)(cr.key0 + cp_to_key(cpi, P, cr.closed, cr.nk));
         atomicAdd(a + 0, acc[l][0]);
         atomicAdd(a + 1, acc[l][1]);
         atomicAdd(a + 2, acc[l][2]);
-        atomicAdd(a + 3, acc[l][3]);
+        if (!cp.freeze_w) atomicAdd(a + 3, acc[l][3]);
       }
     }
+    if constexpr (KNOTS) {
 #pragma unroll
-    for (int k = 0; k < 2 * P; ++k) {
-      const int kk = cur - P + 1 + k;
-      if (kk >= kn_lo && kk - kn_lo < nkn) atomicAdd(s_kn + (kk - kn_lo), akn[k]);
-      else atomicAdd(dknots + cr.knot0 + kk, akn[k]);
+      for (int k = 0; k < 2 * P; ++k) {
+        const int kk = cur - P + 1 + k;
+        if (kk >= kn_lo && kk - kn_lo < nkn) atomicAdd(s_kn + (kk - kn_lo), akn[k]);
+        else atomicAdd(dknots + cr.knot0 + kk, akn[k]);
+      }
     }
   };
   for (int j = 0; j < kContourPer; ++j) {
@@ -247,16 +247,17 @@ __device__ void chain_contour_run(const ns_curves& cv, const CurveRef& cr, const
     }
     const float gC[3] = {g0.x, g0.y, g0.z / cp.rho};
     float du;
-    curve_point_bwd_local<P>(key, cr, U, i, u, gC, acc, akn, du);
-    dA += du * (1.f - t);   // u = a + t (b - a)
+    curve_point_bwd_local<P, KNOTS>(key, cr, U, i, u, gC, acc, akn, du);
+    dA += du * (1.f - t);   // u = a + t (b - a); 0 without KNOTS
     dB += du * t;
   }
   flush();
 }
 
 // One kernel per degree (the degree-5 registers would otherwise set the
-// occupancy of every task); each skips the tasks of other degrees.
-template <int P>
+// occupancy of every task); each skips the tasks of other degrees.  KNOTS
+// false: knot intervals frozen, no knot gradient is formed.
+template <int P, bool KNOTS>
 __global__ void __launch_bounds__(kContourThreads) k_chain_contour(
     ns_curves cv, ChainParams cp, const CurvePlan* __restrict__ plan, const int* __restrict__ order,
     const float* __restrict__ knots, const DevState* __restrict__ st, const float* __restrict__ dgauss,
@@ -292,8 +293,8 @@ __global__ void __launch_bounds__(kContourThreads) k_chain_contour(
     __syncthreads();
     float dA = 0.f, dB = 0.f;
     float4 dcol = make_float4(0.f, 0.f, 0.f, 0.f);
-    chain_contour_run<P>(cv, cr, U, pl, l0, cp, dgauss, gcap, s_cp, s_kn, cp_lo, kn_lo, ncp, nkn, dkey, dknots, dA,
-                         dB, dcol);
+    chain_contour_run<P, KNOTS>(cv, cr, U, pl, l0, cp, dgauss, gcap, s_cp, s_kn, cp_lo, kn_lo, ncp, nkn, dkey,
+                                dknots, dA, dB, dcol);
     {
       const float v[8] = {dA, dB, dcol.x, dcol.y, dcol.z, dcol.w, 0.f, 0.f};
       const float tot = warp_sum8(v);
@@ -310,11 +311,14 @@ __global__ void __launch_bounds__(kContourThreads) k_chain_contour(
       if (v[2] != 0.f) atomicAdd(a + 2, v[2]);
       if (v[3] != 0.f) atomicAdd(a + 3, v[3]);
     }
-    for (int k = threadIdx.x; k < nkn; k += blockDim.x)
-      if (s_kn[k] != 0.f) atomicAdd(dknots + cr.knot0 + kn_lo + k, s_kn[k]);
+    if (KNOTS)
+      for (int k = threadIdx.x; k < nkn; k += blockDim.x)
+        if (s_kn[k] != 0.f) atomicAdd(dknots + cr.knot0 + kn_lo + k, s_kn[k]);
     if (threadIdx.x == 0) {
-      atomicAdd(dknots + cr.knot0 + cr.p, s_red[0]);
-      atomicAdd(dknots + cr.knot0 + cr.n + 1, s_red[1]);
+      if (KNOTS) {
+        atomicAdd(dknots + cr.knot0 + cr.p, s_red[0]);
+        atomicAdd(dknots + cr.knot0 + cr.n + 1, s_red[1]);
+      }
       atomicAdd(dcolor + 4 * c + 0, s_red[2]);
       atomicAdd(dcolor + 4 * c + 1, s_red[3]);
       atomicAdd(dcolor + 4 * c + 2, s_red[4]);
@@ -323,9 +327,9 @@ __global__ void __launch_bounds__(kContourThreads) k_chain_contour(
   }
 }
 
-template <int P>
+template <int P, bool KNOTS>
 __device__ void chain_boundary_point(const ns_curves& cv, const CurveRef& cr, const float* U, const CurvePlan& pl,
-                                     int j, float2 db, float* dkey, float* dknots) {
+                                     int j, float2 db, int freeze_w, float* dkey, float* dknots) {
   const float t = float(j) / float(pl.M);
   const float u = pl.a + t * (pl.b - pl.a);
   const int i = find_span(U, P, cr.n, u);
@@ -334,18 +338,21 @@ __device__ void chain_boundary_point(const ns_curves& cv, const CurveRef& cr, co
     float* a = dkey + 4 * (long long)(cr.key0 + cp_to_key(cpi, P, cr.closed, cr.nk));
     atomicAdd(a + 0, dx);
     atomicAdd(a + 1, dy);
-    atomicAdd(a + 3, dw);
+    if (!freeze_w) atomicAdd(a + 3, dw);
   };
   auto add_knot = [&](int k, float v) { atomicAdd(dknots + cr.knot0 + k, v); };
   float dA = 0.f, dB = 0.f;
-  curve_point_bwd<P>(cv, cr, U, i, u, t, gC, add_cp, add_knot, dA, dB);
-  atomicAdd(dknots + cr.knot0 + cr.p, dA);
-  atomicAdd(dknots + cr.knot0 + cr.n + 1, dB);
+  curve_point_bwd<P, KNOTS>(cv, cr, U, i, u, t, gC, add_cp, add_knot, dA, dB);
+  if (KNOTS) {
+    atomicAdd(dknots + cr.knot0 + cr.p, dA);
+    atomicAdd(dknots + cr.knot0 + cr.n + 1, dB);
+  }
 }
 
+template <bool KNOTS>
 __global__ void k_chain_boundary(ns_curves cv, const CurvePlan* __restrict__ plan, const float* __restrict__ knots,
-                                 const DevState* __restrict__ st, const float2* __restrict__ dbpts, float* dkey,
-                                 float* dknots) {
+                                 const DevState* __restrict__ st, const float2* __restrict__ dbpts, int freeze_w,
+                                 float* dkey, float* dknots) {
   const int nb = st->b_count;
   const int nc = cv.n_curves;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nb; j += gridDim.x * blockDim.x) {
@@ -360,7 +367,7 @@ __global__ void k_chain_boundary(ns_curves cv, const CurvePlan* __restrict__ pla
     if (pl.kind != kFill) continue;
     const CurveRef cr = curve_ref(cv, lo);
     const float* U = knots + cr.knot0;
-    NS_DISPATCH_P(cr.p, chain_boundary_point<P>(cv, cr, U, pl, j - pl.b_off, db, dkey, dknots));
+    NS_DISPATCH_P(cr.p, chain_boundary_point<P, KNOTS>(cv, cr, U, pl, j - pl.b_off, db, freeze_w, dkey, dknots));
   }
 }
 
@@ -427,8 +434,10 @@ extern "C" ns_status splat_backward(const ns_curves* curves, const ns_gaussians*
     set_error("splat_backward: workspace or Gaussian arrays smaller than the capacities");
     return NS_ERR_INVALID_ARG;
   }
-  if (out && (!sp || !out->dkey || !out->dtau || !out->dcolor || !g->aux)) {
-    set_error("splat_backward: curve gradients need sample parameters, aux and all three outputs");
+  const bool knots_on = out && !(out->frozen & NS_FROZEN_KNOTS);
+  if (out && (!sp || !out->dkey || (knots_on && !out->dtau) || !out->dcolor || !g->aux)) {
+    set_error("splat_backward: curve gradients need sample parameters, aux, dkey, dcolor and (unless the knots "
+              "are frozen) dtau");
     return NS_ERR_INVALID_ARG;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -446,11 +455,11 @@ extern "C" ns_status splat_backward(const ns_curves* curves, const ns_gaussians*
     const float2* bpts = at<float2>(ws, L.o_bpts);
     float2* dbpts = at<float2>(ws, L.o_dbpts);
     const size_t n_knots = (size_t)L.nt + (size_t)kKnotPad * L.nc;
-    cudaMemsetAsync(dknots, 0, sizeof(float) * n_knots, s);
+    if (knots_on) cudaMemsetAsync(dknots, 0, sizeof(float) * n_knots, s);
     cudaMemsetAsync(dbpts, 0, sizeof(float2) * (size_t)L.bcap, s);
     if (zero_outputs) {
       cudaMemsetAsync(out->dkey, 0, sizeof(float) * 4 * (size_t)L.nk, s);
-      cudaMemsetAsync(out->dtau, 0, sizeof(float) * (size_t)L.nt, s);
+      if (out->dtau) cudaMemsetAsync(out->dtau, 0, sizeof(float) * (size_t)L.nt, s);
       cudaMemsetAsync(out->dcolor, 0, sizeof(float) * 4 * (size_t)L.nc, s);
     }
     if (L.nc > 0) {
@@ -459,6 +468,7 @@ extern "C" ns_status splat_backward(const ns_curves* curves, const ns_gaussians*
       cp.h = sp->h;
       cp.gamma = sp->gamma;
       cp.kappa = sp->kappa;
+      cp.freeze_w = (out->frozen & NS_FROZEN_WEIGHTS) != 0;
       NS_LAUNCH(NS_KERNEL_CHAIN, k_chain, num_sms() * 8, 256, 0, s, *curves, cp, plan, order, knots, bpts, st,
                 reinterpret_cast<const float4*>(g->rec), g->aux, dg, cap->gaussians,
                 cap->boundary, out->dkey, dknots, dbpts, out->dcolor);
@@ -466,11 +476,11 @@ extern "C" ns_status splat_backward(const ns_curves* curves, const ns_gaussians*
         // one launch per degree present among the curves (the host knows the
         // degrees only on the device, so all five are launched; a launch with
         // no task of its degree exits after scanning the task list)
-        auto k1 = &k_chain_contour<1>;
-        auto k2 = &k_chain_contour<2>;
-        auto k3 = &k_chain_contour<3>;
-        auto k4 = &k_chain_contour<4>;
-        auto k5 = &k_chain_contour<5>;
+        auto k1 = knots_on ? &k_chain_contour<1, true> : &k_chain_contour<1, false>;
+        auto k2 = knots_on ? &k_chain_contour<2, true> : &k_chain_contour<2, false>;
+        auto k3 = knots_on ? &k_chain_contour<3, true> : &k_chain_contour<3, false>;
+        auto k4 = knots_on ? &k_chain_contour<4, true> : &k_chain_contour<4, false>;
+        auto k5 = knots_on ? &k_chain_contour<5, true> : &k_chain_contour<5, false>;
         const int grid = num_sms() * 16;
         // the five launches form one profiled range (armed events bracket
         // the first and the last)
@@ -488,9 +498,13 @@ extern "C" ns_status splat_backward(const ns_curves* curves, const ns_gaussians*
         run(k4, -1, -1);
         run(k5, -1, NS_KERNEL_CHAIN_CONTOUR);
       }
-      if (L.bcap > 0)
-        NS_LAUNCH(NS_KERNEL_CHAIN_BOUNDARY, k_chain_boundary, num_sms() * 4, 256, 0, s, *curves, plan, knots, st, dbpts, out->dkey, dknots);
-      NS_LAUNCH(NS_KERNEL_KNOT_GRADS, k_knot_grads, (L.nc + 3) / 4, 128, 0, s, *curves, plan, dknots, out->dtau);
+      if (L.bcap > 0) {
+        auto kb = knots_on ? &k_chain_boundary<true> : &k_chain_boundary<false>;
+        NS_LAUNCH(NS_KERNEL_CHAIN_BOUNDARY, kb, num_sms() * 4, 256, 0, s, *curves, plan, knots, st, dbpts,
+                  cp.freeze_w, out->dkey, dknots);
+      }
+      if (knots_on)
+        NS_LAUNCH(NS_KERNEL_KNOT_GRADS, k_knot_grads, (L.nc + 3) / 4, 128, 0, s, *curves, plan, dknots, out->dtau);
     }
   }
   const cudaError_t e = cudaGetLastError();

@@ -45,6 +45,7 @@ struct GeoParams {
   float scale_b;      // lambda_bbox
   int penalty;        // NS_PENALTY_RELU / NS_PENALTY_SOFTPLUS
   int kappa;
+  int freeze_w;       // rational weights frozen: no dL/dw is written
 };
 
 __device__ __forceinline__ float binom_small(int k, int q) {
@@ -107,19 +108,23 @@ __device__ __forceinline__ void acc_clear(SpanAcc<P>& a, int span) {
   for (int k = 0; k < 2 * P; ++k) a.kn[k] = 0.f;
 }
 
+// dknots NULL: knot intervals frozen, their gradients are dropped.
 template <int P>
-__device__ __forceinline__ void acc_flush(const CurveRef& cr, SpanAcc<P>& a, float* dkey, float* dknots) {
+__device__ __forceinline__ void acc_flush(const CurveRef& cr, SpanAcc<P>& a, int freeze_w, float* dkey,
+                                          float* dknots) {
   if (a.span < 0) return;
 #pragma unroll
   for (int l = 0; l <= P; ++l) {
     float* d = dkey + 4 * (long long)(cr.key0 + cp_to_key(a.span - P + l, P, cr.closed, cr.nk));
     if (a.cp[l][0] != 0.f) atomicAdd(d + 0, a.cp[l][0]);
     if (a.cp[l][1] != 0.f) atomicAdd(d + 1, a.cp[l][1]);
-    if (a.cp[l][2] != 0.f) atomicAdd(d + 3, a.cp[l][2]);
+    if (!freeze_w && a.cp[l][2] != 0.f) atomicAdd(d + 3, a.cp[l][2]);
   }
+  if (dknots) {
 #pragma unroll
-  for (int k = 0; k < 2 * P; ++k)
-    if (a.kn[k] != 0.f) atomicAdd(dknots + cr.knot0 + a.span - P + 1 + k, a.kn[k]);
+    for (int k = 0; k < 2 * P; ++k)
+      if (a.kn[k] != 0.f) atomicAdd(dknots + cr.knot0 + a.span - P + 1 + k, a.kn[k]);
+  }
 }
 
 // One quadrature node: returns |C^(R)_xy(u)|^2; with `acc` adds the gradient
@@ -290,7 +295,7 @@ __device__ float deriv_run(const ns_curves& cv, const CurveRef& cr, const float*
     const float u = pl.a + t * (pl.b - pl.a);
     const int i = find_span(U, P, cr.n, u);
     if (grads && i != acc.span) {
-      acc_flush<P>(cr, acc, dkey, dknots);
+      acc_flush<P>(cr, acc, gp.freeze_w, dkey, dknots);
       acc_clear<P>(acc, i);
     }
     float du = 0.f;
@@ -300,9 +305,9 @@ __device__ float deriv_run(const ns_curves& cv, const CurveRef& cr, const float*
     dB += du * t;
   }
   if (grads) {
-    acc_flush<P>(cr, acc, dkey, dknots);
-    if (dA != 0.f) atomicAdd(dknots + cr.knot0 + cr.p, dA);
-    if (dB != 0.f) atomicAdd(dknots + cr.knot0 + cr.n + 1, dB);
+    acc_flush<P>(cr, acc, gp.freeze_w, dkey, dknots);
+    if (dknots && dA != 0.f) atomicAdd(dknots + cr.knot0 + cr.p, dA);
+    if (dknots && dB != 0.f) atomicAdd(dknots + cr.knot0 + cr.n + 1, dB);
   }
   return sum * gp.scale_d;
 }
@@ -394,7 +399,7 @@ __device__ __forceinline__ float box_penalty(const GeoParams& gp, float x, float
 // through C(u) (Eq. 1) into control points, weights and knots.
 template <int P>
 __device__ void bbox_grad(const ns_curves& cv, const CurveRef& cr, const float* U, float u, float t, float gx,
-                          float gy, float* dkey, float* dknots) {
+                          float gy, int freeze_w, float* dkey, float* dknots) {
   const int i = find_span(U, P, cr.n, u);
   Eval<P> e;
   eval_curve<P>(reinterpret_cast<const float4*>(cv.key), cr, U, i, u, e);
@@ -410,8 +415,9 @@ __device__ void bbox_grad(const ns_curves& cv, const CurveRef& cr, const float* 
     float* d = dkey + 4 * (long long)(cr.key0 + cp_to_key(i - P + l, P, cr.closed, cr.nk));
     if (dcp[l][0] != 0.f) atomicAdd(d + 0, dcp[l][0]);
     if (dcp[l][1] != 0.f) atomicAdd(d + 1, dcp[l][1]);
-    if (dcp[l][3] != 0.f) atomicAdd(d + 3, dcp[l][3]);
+    if (!freeze_w && dcp[l][3] != 0.f) atomicAdd(d + 3, dcp[l][3]);
   }
+  if (!dknots) return;
 #pragma unroll
   for (int k = 0; k < 2 * P; ++k)
     if (dkn[k] != 0.f) atomicAdd(dknots + cr.knot0 + i - P + 1 + k, dkn[k]);
@@ -454,7 +460,7 @@ __global__ void __launch_bounds__(kGeoThreads) k_bbox_contour(ns_curves cv, cons
       const float* U = knots + cr.knot0;
       const float t = contour_t(q, l, gp.kappa);
       const float u = contour_u(q, l, gp.kappa);
-      NS_DISPATCH_P(cr.p, bbox_grad<P>(cv, cr, U, u, t, gp.scale_b * gx, gp.scale_b * gy, dkey, dknots));
+      NS_DISPATCH_P(cr.p, bbox_grad<P>(cv, cr, U, u, t, gp.scale_b * gx, gp.scale_b * gy, gp.freeze_w, dkey, dknots));
     }
   }
   block_sum_add(sum * gp.scale_b, loss);
@@ -490,7 +496,7 @@ __global__ void __launch_bounds__(kGeoThreads) k_bbox_boundary(ns_curves cv, con
     const float* U = knots + cr.knot0;
     const float t = float(jj) / float(pl.M);
     const float u = pl.a + t * (pl.b - pl.a);
-    NS_DISPATCH_P(cr.p, bbox_grad<P>(cv, cr, U, u, t, gp.scale_b * gx, gp.scale_b * gy, dkey, dknots));
+    NS_DISPATCH_P(cr.p, bbox_grad<P>(cv, cr, U, u, t, gp.scale_b * gx, gp.scale_b * gy, gp.freeze_w, dkey, dknots));
   }
   block_sum_add(sum * gp.scale_b, loss);
 }
@@ -518,8 +524,9 @@ extern "C" ns_status ns_geometry_loss(const ns_curves* curves, const ns_gaussian
     set_error("ns_geometry_loss: null argument");
     return NS_ERR_INVALID_ARG;
   }
-  if (out && (!out->dkey || !out->dtau)) {
-    set_error("ns_geometry_loss: gradients need dkey and dtau");
+  const bool knots_on = out && !(out->frozen & NS_FROZEN_KNOTS);
+  if (out && (!out->dkey || (knots_on && !out->dtau))) {
+    set_error("ns_geometry_loss: gradients need dkey and (unless the knots are frozen) dtau");
     return NS_ERR_INVALID_ARG;
   }
   if (gpar->order < 1 || gpar->order > kMaxOrder) {
@@ -559,12 +566,13 @@ extern "C" ns_status ns_geometry_loss(const ns_curves* curves, const ns_gaussian
     gp.scale_b = gpar->lambda_bbox;
     gp.penalty = gpar->penalty;
     gp.kappa = sp->kappa;
+    gp.freeze_w = out && (out->frozen & NS_FROZEN_WEIGHTS) != 0;
     const CurvePlan* plan = at<const CurvePlan>(ws, L.o_plan);
     const float* knots = at<const float>(ws, L.o_knots);
     const DevState* st = at<const DevState>(ws, L.o_state);
-    float* dknots = out ? at<float>(ws, L.o_dknots) : nullptr;
+    float* dknots = knots_on ? at<float>(ws, L.o_dknots) : nullptr;
     float* dkey = out ? out->dkey : nullptr;
-    if (out) cudaMemsetAsync(dknots, 0, sizeof(float) * ((size_t)L.nt + (size_t)kKnotPad * L.nc), s);
+    if (knots_on) cudaMemsetAsync(dknots, 0, sizeof(float) * ((size_t)L.nt + (size_t)kKnotPad * L.nc), s);
     if (gpar->lambda_deriv != 0.f) {
       switch (gp.order) {
         case 1: launch_deriv_loss<1>(*curves, plan, knots, gp, loss, dkey, dknots, s); break;
@@ -585,7 +593,7 @@ extern "C" ns_status ns_geometry_loss(const ns_curves* curves, const ns_gaussian
                                                    loss + 1, dkey, dknots);
       after_launch(NS_KERNEL_BBOX_LOSS, s);
     }
-    if (out) launch_knot_grads(*curves, plan, dknots, out->dtau, s);
+    if (knots_on) launch_knot_grads(*curves, plan, dknots, out->dtau, s);
   }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {

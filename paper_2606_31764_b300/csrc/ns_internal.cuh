@@ -272,8 +272,10 @@ __device__ __forceinline__ float speed_xy(const Eval<P>& e) {
 
 // Reverse of C = S/W at one evaluated point: given gC = dL/dC (x, y, s), adds
 // dL/d{x, y, s, w} of the span's control points to dcp[l], dL/dU of its 2P
-// knots to dkn (as basis_bwd) and returns dL/du in *du.
-template <int P>
+// knots to dkn (as basis_bwd) and returns dL/du in *du.  Without KNOTS (knot
+// intervals frozen) the reverse sweep of the triangle, which only feeds the
+// knot and parameter gradients, is skipped and *du is 0.
+template <int P, bool KNOTS = true>
 __device__ __forceinline__ void curve_point_adjoint(const Eval<P>& e, const float gC[3], float dcp[P + 1][4],
                                                     float dkn[2 * P], float* du) {
   const float iw = 1.f / e.W;
@@ -290,7 +292,7 @@ __device__ __forceinline__ void curve_point_adjoint(const Eval<P>& e, const floa
     dcp[l][3] += e.t.N[l] * proj * iw;
   }
   float d = 0.f;
-  basis_bwd<P>(e.t, gN, &d, dkn);
+  if constexpr (KNOTS) basis_bwd<P>(e.t, gN, &d, dkn);
   *du = d;
 }
 

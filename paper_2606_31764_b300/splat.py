@@ -164,11 +164,20 @@ class Splatter:
         self.sample(key, tau, color)
         return self.forward_gaussians(key, tau, color, image)
 
-    def backward(self, key, tau, color, dimage, grads=None, chain=True):
+    @staticmethod
+    def frozen_bits(frozen):
+        """("weights", "knots") -> NS_FROZEN_* bits (the paper's ablation variants)."""
+        bits = {"weights": B.NS_FROZEN_WEIGHTS, "knots": B.NS_FROZEN_KNOTS}
+        return sum(bits[f] for f in set(frozen))
+
+    def backward(self, key, tau, color, dimage, grads=None, chain=True, frozen=()):
+        """splat_backward; frozen may name "weights" and/or "knots": their
+        gradients are not formed (dtau is left untouched for frozen knots)."""
         cs = self.dev.struct(key, tau, color)
         if grads is None:
             grads = (torch.empty_like(key), torch.empty_like(tau), torch.empty_like(color))
-        out = B.NsCurveGrads(_ptr(grads[0]), _ptr(grads[1]), _ptr(grads[2])) if chain else None
+        out = B.NsCurveGrads(_ptr(grads[0]), None if "knots" in frozen else _ptr(grads[1]), _ptr(grads[2]),
+                             self.frozen_bits(frozen)) if chain else None
         # per-Gaussian gradients (rows {dmu_x, dmu_y, dsigma, 0, do, dr, dg, db}) go
         # to self.dgauss when no chain is asked for; with the chain the workspace
         # holds them and the library skips what the chain does not use
@@ -179,7 +188,7 @@ class Splatter:
         return grads
 
     def geometry(self, key, tau, color, loss, grads=None, lambda_deriv=1.0, order=3, nodes=0, lambda_bbox=5.0,
-                 penalty="relu", box=None):
+                 penalty="relu", box=None, frozen=()):
         """Geometric regularisers (Eq. 11 derivative loss, Eq. 12 box loss) on the
         plan of the last sample() (ns_geometry_loss).  loss: device float[2],
         overwritten with the weighted terms; grads: (dkey, dtau, ...) device
@@ -192,7 +201,8 @@ class Splatter:
         gp.penalty = {"relu": B.NS_PENALTY_RELU, "softplus": B.NS_PENALTY_SOFTPLUS}[penalty]
         for i, v in enumerate(box or (0.0, 0.0, 0.0, 0.0)):
             gp.box[i] = v
-        out = B.NsCurveGrads(_ptr(grads[0]), _ptr(grads[1]), None) if grads is not None else None
+        out = (B.NsCurveGrads(_ptr(grads[0]), None if "knots" in frozen else _ptr(grads[1]), None,
+                              self.frozen_bits(frozen)) if grads is not None else None)
         B.call("ns_geometry_loss", C.byref(cs), C.byref(self.g), C.byref(self.sp), C.byref(self.rp), C.byref(gp),
                C.byref(self.cap),
                _ptr(loss), C.byref(out) if out is not None else None, _ptr(self.ws), C.c_size_t(self.ws_bytes),
@@ -212,15 +222,20 @@ class Splatter:
                C.c_size_t(self.ws_bytes), C.c_int32(repeats), _stream())
         return int(self.rp.ppt_fwd), int(self.rp.ppt_bwd)
 
-    def adam(self, key, tau, color, grads, state, step, lr=(0.1, 0.01, 0.01), betas=(0.9, 0.999), eps=1e-8):
+    def adam(self, key, tau, color, grads, state, step, lr=(0.1, 0.01, 0.01), betas=(0.9, 0.999), eps=1e-8,
+             frozen=()):
         """One Adam step on key points, knot intervals and colours with the clamps
         of Table S1 (w in [0.01, 10], tau in [0, 2]; widths >= 0; colours and
-        opacities in [0, 1]).  `state` holds the moment buffers (made on first use)."""
+        opacities in [0, 1]).  `state` holds the moment buffers (made on first use).
+        Frozen knots skip the tau update; frozen weights get no gradient from
+        the backward, so with moments that started at zero they stay fixed."""
         inf = float("inf")
         groups = ((key, grads[0], 4, (-inf, -inf, 0.0, 0.01), (inf, inf, inf, 10.0), lr[0]),
                   (tau, grads[1], 1, (0.0,), (2.0,), lr[1]),
                   (color, grads[2], 4, (0.0,) * 4, (1.0,) * 4, lr[2]))
         for i, (p, g, grp, lo, hi, r) in enumerate(groups):
+            if i == 1 and "knots" in frozen:
+                continue
             if i not in state:
                 state[i] = (torch.zeros_like(p), torch.zeros_like(p))
             m, v = state[i]
