@@ -46,8 +46,8 @@ TRAFFIC = dict(
                    src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="d59061f4827f403e"),
     emit=dict(bytes=2415872, units=2027197, unit="gaussians", tile=None,
               src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="020187ed43480f94"),
-    chain=dict(bytes=88507392, units=2027197, unit="gaussians", tile=None,
-               src="paper_2606_31764_b300/csrc/ns_backward.cu", sha="44739f3991573c5e"),
+    chain=dict(bytes=88617472, units=2027197, unit="gaussians", tile=None,
+               src="paper_2606_31764_b300/csrc/ns_backward.cu", sha="4c7dea65ad7f2f31"),
 )
 
 
@@ -397,10 +397,44 @@ def run_gpu(args, dist, rank, world):
                           composited=int(rep.blend_contribs)),
                sample=costs)
     out["geometry"] = run_geometry(torch, step, args)
+    out["schedule"] = run_schedule(torch, step)
     if not args.no_per_scene:
         out["per_scene"] = run_per_scene(torch, step, args, value)
         out["long_spline"] = run_long_spline(torch, args)
     return out, step
+
+
+def run_schedule(torch, step):
+    """Grid-step annealing (Eq. 14) on the headline batch: h(t) for T = 300
+    iterations from h_max = 8 to h_min = 1 between t/T = 0.1 and 0.8, sampled at
+    11 evenly spaced iterations.  Each sampled step is captured as a graph of
+    its own (the grid step is a launch parameter) and timed; the schedule
+    average is the sum of Gaussians over the sum of times."""
+    from paper_2606_31764_b300 import binding as B
+    lib = B.load()
+    T, h0 = 300, float(step.sp.sp.h)
+    rows = []
+    for i in range(11):
+        t = int(round(i * (T - 1) / 10))
+        h = float(lib.ns_grid_step(t, T, 8.0, 1.0, 0.1, 0.8))
+        step.sp.sp.h = h
+        g = capture(torch, step, 3)
+        g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        rows.append(dict(t=t, h=round(h, 4), gaussians=step.gaussians(), ms=round(e0.elapsed_time(e1) / 3, 4)))
+        del g
+    step.sp.sp.h = h0
+    step()
+    torch.cuda.synchronize()
+    G = sum(r["gaussians"] for r in rows)
+    ms = sum(r["ms"] for r in rows)
+    return dict(what="grid-step annealing 8 -> 1 px (Eq. 14, T = 300, t_b = 0.1, t_e = 0.8), 11 sampled iterations",
+                gaussians_per_s=round(G / (ms / 1e3), 1), ms_per_iteration=round(ms / len(rows), 4), steps=rows)
 
 
 def run_geometry(torch, step, args):
