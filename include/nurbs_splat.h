@@ -261,11 +261,15 @@ ns_status ns_mse_loss(const float* image, const float* target, int64_t n,
  * `group` floats, use +-INFINITY for no bound).  The paper clamps weights to
  * [0.01, 10] and knot intervals to [0, 2] (Table S1): for key points {x, y, s,
  * w} use group 4 with lo = {-inf, -inf, 0, 0.01}, hi = {inf, inf, inf, 10}.
+ * Element i uses the learning rate lr * lr_scale[i % group] (lr_scale: host
+ * array of `group` floats, or NULL for lr everywhere; the layer-wise loop of
+ * §5 uses 2.0 for positions and 0.01 for the rest).
  * m, v: device moment buffers of n floats.  step >= 1.
  */
 ns_status ns_adam_step(float* param, const float* grad, float* m, float* v, int64_t n,
                        float lr, float beta1, float beta2, float eps, int32_t step,
-                       const float* lo, const float* hi, int32_t group, void* stream);
+                       const float* lo, const float* hi, int32_t group,
+                       const float* lr_scale, void* stream);
 
 /* Penalties of the bounding-box loss (Eq. 12). */
 #define NS_PENALTY_RELU 0      /* phi(x) = max(x, 0), derivative 0 at 0 */
@@ -315,6 +319,56 @@ ns_status ns_geometry_loss(const ns_curves* curves, const ns_gaussians* g,
                            const ns_geometry_params* gp,
                            const ns_capacity* cap, float* loss, const ns_curve_grads* out,
                            void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Layer-wise vectorisation (§4.2, the LIVE adaptation): the image term of its
+ * loss (Eq. 15), L_img, a distance-weighted mean square error.  For every
+ * scene s, new_curve[s] names the filled path the scene received this round
+ * (or -1).  Per pixel centre, d is the distance to that path's closed
+ * boundary polyline (§3.3, the points nurbs_sample left in `workspace`) and
+ * w = max(0, tau - d); the scene's loss is sum w sum_c (I - I*)^2 / (C sum w).
+ * A scene without a new path, or with no pixel within tau, takes the plain
+ * mean square error.  loss = mean over scenes; the weights are constants.
+ *   new_curve: device int32 [n_scenes]; an index that is not a filled curve
+ *     counts as -1.
+ *   image, target: device, image layout; dL_dimage: device, overwritten (or NULL).
+ *   loss: device scalar, overwritten.
+ * Uses the same workspace as the splat calls of the step (after nurbs_sample).
+ */
+ns_status ns_udf_mse_loss(const ns_curves* curves, const ns_sample_params* sp,
+                          const ns_raster_params* rp, const ns_capacity* cap,
+                          const int32_t* new_curve, float tau, const float* image,
+                          const float* target, float* dL_dimage, float* loss,
+                          void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Self-crossing penalty L_xing of the same loss (Eq. 15): for every curve, the
+ * legs a_i = K_{i+1} - K_i of its key-point polygon (cyclic for closed curves),
+ * the sine of each turn sin_i = (a_i x a_{i+1}) / (|a_i| |a_{i+1}|) and the
+ * curve's winding sign sigma = sign(sum_i a_i x a_{i+1}) (held fixed):
+ *   loss = lambda * sum over curves and turns of max(0, -sigma sin_i).
+ * loss: device scalar, overwritten.  dkey: device [n_keys*4] or NULL; the
+ * gradient with respect to x and y is ADDED to it.
+ */
+ns_status ns_xing_loss(const ns_curves* curves, float lambda, float* loss, float* dkey, void* stream);
+
+/* Bytes of scratch ns_seed_windows needs (0 for invalid sizes). */
+size_t ns_seed_scratch_size(int32_t n_scenes, int32_t height, int32_t width);
+
+/*
+ * Where the layer-wise loop starts a new path (§4.2: at the region of highest
+ * reconstruction error): per scene, the pixel whose (2 radius + 1)^2 window
+ * (clipped to the image) holds the largest sum of the squared error
+ * sum_c (I - I*)^2, the first in row-major order on ties.
+ *   image, target: device [n_scenes, height, width, channels] float32.
+ *   scratch: device, ns_seed_scratch_size bytes, 256-byte aligned.
+ *   seed_xy: device int32 [n_scenes*2] (x, y); seed_value: device float
+ *   [n_scenes] (the window sum) or NULL.
+ */
+ns_status ns_seed_windows(const float* image, const float* target, int32_t n_scenes,
+                          int32_t height, int32_t width, int32_t channels, int32_t radius,
+                          void* scratch, size_t scratch_bytes, int32_t* seed_xy,
+                          float* seed_value, void* stream);
 
 /* Synchronises `stream`, reads the device status and counters. */
 ns_status ns_poll_status(void* workspace, ns_report* report, void* stream);

@@ -82,7 +82,8 @@ SIGNATURES = {
     "ns_grid_step": (C.c_float, [C.c_int32, C.c_int32, C.c_float, C.c_float, C.c_float, C.c_float]),
     "ns_mse_loss": (C.c_int, [_p, _p, C.c_int64, _p, _p, _p]),
     "ns_adam_step": (C.c_int, [_p, _p, _p, _p, C.c_int64, C.c_float, C.c_float, C.c_float, C.c_float,
-                               C.c_int32, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int32, _p]),
+                               C.c_int32, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int32,
+                               C.POINTER(C.c_float), _p]),
     "ns_poll_status": (C.c_int, [_p, C.POINTER(NsReport), _p]),
     "ns_clear_status": (C.c_int, [_p, _p]),
     "ns_workspace_copy": (C.c_int, [_p, C.POINTER(NsCurves), C.POINTER(NsCapacity), C.POINTER(NsRasterParams),
@@ -97,6 +98,12 @@ SIGNATURES = {
                                    C.POINTER(NsRasterParams),
                                    C.POINTER(NsGeometryParams), C.POINTER(NsCapacity), _p, C.POINTER(NsCurveGrads),
                                    _p, C.c_size_t, _p]),
+    "ns_udf_mse_loss": (C.c_int, [C.POINTER(NsCurves), C.POINTER(NsSampleParams), C.POINTER(NsRasterParams),
+                                  C.POINTER(NsCapacity), _p, C.c_float, _p, _p, _p, _p, _p, C.c_size_t, _p]),
+    "ns_xing_loss": (C.c_int, [C.POINTER(NsCurves), C.c_float, _p, _p, _p]),
+    "ns_seed_scratch_size": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32]),
+    "ns_seed_windows": (C.c_int, [_p, _p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _p, C.c_size_t,
+                                  _p, _p, _p]),
     "ns_launch_count": (C.c_uint64, []),
     "ns_last_error": (C.c_char_p, []),
 }

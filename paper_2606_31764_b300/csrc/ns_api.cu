@@ -140,6 +140,7 @@ bool make_layout(const ns_curves* c, const ns_capacity* cap, const ns_raster_par
   L->o_dgauss = take(sizeof(float) * 8 * (size_t)L->gcap);
   L->o_prep = take(sizeof(float4) * (size_t)L->gcap);
   L->o_reach = take(sizeof(float2) * (size_t)L->gcap);
+  L->o_live = take(sizeof(float) * 4 * (size_t)L->S);
   L->total = o;
   return true;
 }
@@ -179,11 +180,11 @@ __global__ void __launch_bounds__(256) k_mse(const float* __restrict__ a, const 
 }
 
 struct Clamp4 {
-  float lo[4], hi[4];
+  float lo[4], hi[4], lr[4];   // per component of the group: clamp bounds and learning rate
 };
 
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
-                       long long n, float lr, float b1, float b2, float eps, float c1, float c2, Clamp4 cl, int group) {
+                       long long n, float b1, float b2, float eps, float c1, float c2, Clamp4 cl, int group) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const float gi = g[i];
     const float mi = b1 * m[i] + (1.f - b1) * gi;
@@ -191,8 +192,8 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
     m[i] = mi;
     v[i] = vi;
     const float mh = mi / c1, vh = vi / c2;
-    const float x = p[i] - lr * mh / (sqrtf(vh) + eps);
     const int j = int(i % group);
+    const float x = p[i] - cl.lr[j] * mh / (sqrtf(vh) + eps);
     p[i] = fminf(fmaxf(x, cl.lo[j]), cl.hi[j]);
   }
 }
@@ -299,7 +300,7 @@ ns_status ns_mse_loss(const float* image, const float* target, int64_t n, float*
 
 ns_status ns_adam_step(float* param, const float* grad, float* m, float* v, int64_t n, float lr, float beta1,
                        float beta2, float eps, int32_t step, const float* lo, const float* hi, int32_t group,
-                       void* stream) {
+                       const float* lr_scale, void* stream) {
   if (!param || !grad || !m || !v || n < 0 || step < 1 || !lo || !hi || group < 1 || group > 4) {
     set_error("ns_adam_step: invalid argument");
     return NS_ERR_INVALID_ARG;
@@ -308,6 +309,7 @@ ns_status ns_adam_step(float* param, const float* grad, float* m, float* v, int6
   for (int j = 0; j < 4; ++j) {
     cl.lo[j] = j < group ? lo[j] : -INFINITY;
     cl.hi[j] = j < group ? hi[j] : INFINITY;
+    cl.lr[j] = lr * (lr_scale && j < group ? lr_scale[j] : 1.f);
     if (!(cl.lo[j] <= cl.hi[j])) {
       set_error("ns_adam_step: lo > hi");
       return NS_ERR_INVALID_ARG;
@@ -318,7 +320,7 @@ ns_status ns_adam_step(float* param, const float* grad, float* m, float* v, int6
   const float c2 = 1.f - powf(beta2, float(step));
   const long long blocks = (n + 255) / 256;
   const int grid = int(blocks < num_sms() * 8 ? blocks : num_sms() * 8);
-  NS_LAUNCH(NS_KERNEL_ADAM, k_adam, grid, 256, 0, static_cast<cudaStream_t>(stream), param, grad, m, v, n, lr, beta1,
+  NS_LAUNCH(NS_KERNEL_ADAM, k_adam, grid, 256, 0, static_cast<cudaStream_t>(stream), param, grad, m, v, n, beta1,
             beta2, eps, c1, c2, cl, group);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {

@@ -209,6 +209,23 @@ class Splatter:
                _stream())
         return loss
 
+    def udf_mse(self, key, tau, color, image, target, new_curve, tau_w, dimage, loss):
+        """Distance-weighted image loss of the layer-wise loop (ns_udf_mse_loss):
+        new_curve is a device int32 tensor [n_scenes] naming each scene's new
+        filled path (or -1); tau_w the weight radius in pixels."""
+        cs = self.dev.struct(key, tau, color)
+        B.call("ns_udf_mse_loss", C.byref(cs), C.byref(self.sp), C.byref(self.rp), C.byref(self.cap),
+               _ptr(new_curve), C.c_float(tau_w), _ptr(image), _ptr(target), _ptr(dimage), _ptr(loss),
+               _ptr(self.ws), C.c_size_t(self.ws_bytes), _stream())
+        return loss
+
+    def xing(self, key, tau, color, loss, dkey=None, lam=0.01):
+        """Self-crossing penalty of the key-point polygons (ns_xing_loss); its
+        gradient is added to dkey when given."""
+        cs = self.dev.struct(key, tau, color)
+        B.call("ns_xing_loss", C.byref(cs), C.c_float(lam), _ptr(loss), _ptr(dkey), _stream())
+        return loss
+
     def mse(self, image, target, dimage, loss):
         B.call("ns_mse_loss", _ptr(image), _ptr(target), C.c_int64(image.numel()), _ptr(dimage), _ptr(loss),
                _stream())
@@ -227,6 +244,8 @@ class Splatter:
         """One Adam step on key points, knot intervals and colours with the clamps
         of Table S1 (w in [0.01, 10], tau in [0, 2]; widths >= 0; colours and
         opacities in [0, 1]).  `state` holds the moment buffers (made on first use).
+        lr: (key, tau, color) learning rates; the key and colour entries may be
+        4-tuples, one rate per component ({x, y, s, w}, {r, g, b, o}).
         Frozen knots skip the tau update; frozen weights get no gradient from
         the backward, so with moments that started at zero they stay fixed."""
         inf = float("inf")
@@ -239,9 +258,13 @@ class Splatter:
             if i not in state:
                 state[i] = (torch.zeros_like(p), torch.zeros_like(p))
             m, v = state[i]
-            B.call("ns_adam_step", _ptr(p), _ptr(g), _ptr(m), _ptr(v), C.c_int64(p.numel()), C.c_float(r),
+            rates = tuple(r) if isinstance(r, (tuple, list)) else (float(r),) * grp
+            if len(rates) != grp:
+                raise ValueError("a per-component learning rate needs one value per component")
+            B.call("ns_adam_step", _ptr(p), _ptr(g), _ptr(m), _ptr(v), C.c_int64(p.numel()), C.c_float(1.0),
                    C.c_float(betas[0]), C.c_float(betas[1]), C.c_float(eps), C.c_int32(step),
-                   (C.c_float * grp)(*lo), (C.c_float * grp)(*hi), C.c_int32(grp), _stream())
+                   (C.c_float * grp)(*lo), (C.c_float * grp)(*hi), C.c_int32(grp), (C.c_float * grp)(*rates),
+                   _stream())
 
     # -- sizing ---------------------------------------------------------
     def fit(self, key, tau, color, headroom=1.25, max_rounds=4):
@@ -290,6 +313,23 @@ class NurbsSplatFunction(torch.autograd.Function):
         key, tau, color = ctx.saved_tensors
         dk, dt, dc = ctx.splatter.backward(key, tau, color, dimage.contiguous())
         return dk, dt, dc, None
+
+
+def seed_windows(image, target, radius, scratch=None):
+    """Per scene the pixel whose (2 radius + 1)^2 window holds the largest
+    squared error (ns_seed_windows): returns (xy int32 [S, 2], value [S]) on the
+    device."""
+    S, H, W, Cc = image.shape
+    lib = B.load()
+    n = lib.ns_seed_scratch_size(S, H, W)
+    if scratch is None or scratch.numel() < n:
+        scratch = torch.empty(n, dtype=torch.uint8, device=image.device)
+    xy = torch.empty(S, 2, dtype=torch.int32, device=image.device)
+    val = torch.empty(S, device=image.device)
+    B.call("ns_seed_windows", _ptr(image.contiguous()), _ptr(target.contiguous()), C.c_int32(S), C.c_int32(H),
+           C.c_int32(W), C.c_int32(Cc), C.c_int32(radius), _ptr(scratch), C.c_size_t(scratch.numel()), _ptr(xy),
+           _ptr(val), _stream())
+    return xy, val
 
 
 def scene_tensors(scene, device="cuda"):

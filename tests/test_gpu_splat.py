@@ -125,7 +125,7 @@ def test_adam_step_matches_oracle():
         tg = torch.as_tensor(g, device="cuda")
         B.call("ns_adam_step", C.c_void_p(tp.data_ptr()), C.c_void_p(tg.data_ptr()), C.c_void_p(tm.data_ptr()),
                C.c_void_p(tv.data_ptr()), C.c_int64(n), C.c_float(0.05), C.c_float(0.9), C.c_float(0.999),
-               C.c_float(1e-8), C.c_int32(step), lo, hi, C.c_int32(4),
+               C.c_float(1e-8), C.c_int32(step), lo, hi, C.c_int32(4), None,
                C.c_void_p(torch.cuda.current_stream().cuda_stream))
         pp, m, v = optim.adam_step(pp, g, m, v, step, lr=0.05, lo=lo_np, hi=hi_np)
         torch.cuda.synchronize()
