@@ -131,39 +131,54 @@ class LayerwiseVectorizer:
         # the index of each scene's new path: the last curve of the scene
         return np.asarray(self.batch.scene_curve_offset[1:] - 1, np.int32)
 
-    def optimise(self, new_curve):
+    def prepare(self, new_curve):
+        """Device tables, buffers sized at the finest grid step, loss buffers."""
         b = self.batch
-        k, t, c = self._device_params()
+        self.params = self._device_params()
+        k, t, c = self.params
         self.sp = Splatter(b, capacity=self.capacity)
-        self.sp.sp.h = float(self.sched[1])   # size the buffers at the finest grid step
+        self.sp.sp.h = float(self.sched[1])
         self.sp.fit(k, t, c)
+        self.newc = torch.as_tensor(new_curve, dtype=torch.int32, device="cuda")
+        self.image = torch.empty_like(self.target)
+        self.dimage = torch.empty_like(self.target)
+        self.loss = torch.zeros(1, device="cuda")
+        self.xloss = torch.zeros(1, device="cuda")
+        self.geo_loss = torch.zeros(2, device="cuda")
+        self.grads = (torch.empty_like(k), torch.empty_like(t), torch.empty_like(c))
+        self.state = {}
+
+    def iterate(self):
+        """The round's iterations (all on the device, no host synchronisation)."""
         lib = B.load()
-        newc = torch.as_tensor(new_curve, dtype=torch.int32, device="cuda")
-        image = torch.empty_like(self.target)
-        dimage = torch.empty_like(self.target)
-        loss = torch.zeros(1, device="cuda")
-        xloss = torch.zeros(1, device="cuda")
-        geo_loss = torch.zeros(2, device="cuda")
-        grads = (torch.empty_like(k), torch.empty_like(t), torch.empty_like(c))
-        state = {}
+        k, t, c = self.params
         h_max, h_min, t_b, t_e = self.sched
         T = self.iters
         for it in range(T):
             self.sp.sp.h = float(lib.ns_grid_step(it, T, h_max, h_min, t_b, t_e))
             self.sp.sample(k, t, c)
-            self.sp.forward_gaussians(k, t, c, image)
-            self.sp.udf_mse(k, t, c, image, self.target, newc, self.tau_udf, dimage, loss)
-            self.sp.backward(k, t, c, dimage, grads=grads)
+            self.sp.forward_gaussians(k, t, c, self.image)
+            self.sp.udf_mse(k, t, c, self.image, self.target, self.newc, self.tau_udf, self.dimage, self.loss)
+            self.sp.backward(k, t, c, self.dimage, grads=self.grads)
             if self.lambda_xing:
-                self.sp.xing(k, t, c, xloss, grads[0], self.lambda_xing)
+                self.sp.xing(k, t, c, self.xloss, self.grads[0], self.lambda_xing)
             if self.lambda_deriv:
-                self.sp.geometry(k, t, c, geo_loss, grads, lambda_deriv=self.lambda_deriv, lambda_bbox=0.0)
+                self.sp.geometry(k, t, c, self.geo_loss, self.grads, lambda_deriv=self.lambda_deriv,
+                                 lambda_bbox=0.0)
             decay = self.lr_end ** (it / max(1, T - 1))
             lr = tuple(tuple(y * decay for y in x) if isinstance(x, tuple) else x * decay for x in self.lr)
-            self.sp.adam(k, t, c, grads, state, it + 1, lr=lr)
-        self.losses.append(float(loss.item()))
-        self._pull(k, t, c)
-        return image
+            self.sp.adam(k, t, c, self.grads, self.state, it + 1, lr=lr)
+
+    def finish(self):
+        """Record the round's last loss and copy the parameters to the host."""
+        self.losses.append(float(self.loss.item()))
+        self._pull(*self.params)
+        return self.image
+
+    def optimise(self, new_curve):
+        self.prepare(new_curve)
+        self.iterate()
+        return self.finish()
 
     def run(self):
         bg = torch.as_tensor(list(self.batch.raster.get("bg", (1.0, 1.0, 1.0)))[:self.batch.channels],
