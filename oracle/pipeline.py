@@ -105,15 +105,21 @@ def gaussians_fp32(scene, plans=None):
     rec[:, 0:2] = g["mu"].numpy()[order]
     rec[:, 2] = g["sigma"].numpy()[order]
     rec[:, 3] = g["o"].numpy()[order]
-    return dict(rec=rec, curve=g["curve"].numpy()[order].astype(np.int32),
-                layer=g["layer"].numpy()[order], sample=g["sample"].numpy()[order],
-                scene=g["scene"].numpy()[order], order=order, plans=g["plans"])
+    out = dict(rec=rec, curve=g["curve"].numpy()[order].astype(np.int32),
+               layer=g["layer"].numpy()[order], sample=g["sample"].numpy()[order],
+               scene=g["scene"].numpy()[order], order=order, plans=g["plans"])
+    if "shape" in g:
+        shape = np.zeros((order.shape[0], 4), np.float32)   # {sigma_t, cos, sin, 0}
+        shape[:, 0:3] = g["shape"].numpy()[order]
+        out["shape"] = shape
+    return out
 
 
-def render_records(scene, rec, curve, mode="tiled", return_flags=False):
+def render_records(scene, rec, curve, mode="tiled", return_flags=False, shape=None):
     """Render a given FP32 Gaussian set (front to back per scene, as produced
     by `gaussians_fp32`) in FP64.  Layer and sample are re-derived from the
-    position in that order, so the sort key is the same one the set came in."""
+    position in that order, so the sort key is the same one the set came in.
+    shape: [G, 4] {sigma_t, cos, sin, 0} for tangent-aligned records."""
     cs = scene.curve_scene()
     rec64 = torch.as_tensor(rec.astype(np.float64))
     curve_t = torch.as_tensor(curve.astype(np.int64))
@@ -124,6 +130,8 @@ def render_records(scene, rec, curve, mode="tiled", return_flags=False):
     sample = torch.arange(G)   # position order inside each (scene, layer) group
     g = dict(mu=rec64[:, 0:2], sigma=rec64[:, 2], o=rec64[:, 3], curve=curve_t, sample=sample,
              layer=layer, scene=scene_of)
+    if shape is not None:
+        g["shape"] = torch.as_tensor(np.asarray(shape)[:, :3].astype(np.float64))
     color_t = torch.as_tensor(scene.color, dtype=DT)
     args = (g, color_t, scene.n_scenes, scene.height, scene.width, scene.channels, scene.raster)
     if mode == "brute":
@@ -134,30 +142,39 @@ def render_records(scene, rec, curve, mode="tiled", return_flags=False):
     return rs.render_tiled(*args).numpy()
 
 
-def _records_g(scene, rec, curve, requires_grad=False):
+def _records_g(scene, rec, curve, requires_grad=False, shape=None):
     cs = scene.curve_scene()
     rec64 = torch.tensor(rec.astype(np.float64), requires_grad=requires_grad)
     off = scene.scene_curve_offset
-    return rec64, dict(mu=rec64[:, 0:2], sigma=rec64[:, 2], o=rec64[:, 3],
-                       curve=torch.as_tensor(curve.astype(np.int64)), sample=torch.arange(rec.shape[0]),
-                       layer=torch.as_tensor((off[cs[curve] + 1] - 1 - curve).astype(np.int64)),
-                       scene=torch.as_tensor(cs[curve].astype(np.int64)))
+    g = dict(mu=rec64[:, 0:2], sigma=rec64[:, 2], o=rec64[:, 3],
+             curve=torch.as_tensor(curve.astype(np.int64)), sample=torch.arange(rec.shape[0]),
+             layer=torch.as_tensor((off[cs[curve] + 1] - 1 - curve).astype(np.int64)),
+             scene=torch.as_tensor(cs[curve].astype(np.int64)))
+    shape64 = None
+    if shape is not None:
+        shape64 = torch.tensor(np.asarray(shape)[:, :3].astype(np.float64), requires_grad=requires_grad)
+        g["shape"] = shape64
+    return rec64, g, shape64
 
 
-def pairs_records(scene, rec, curve):
+def pairs_records(scene, rec, curve, shape=None):
     """Sorted (tile, Gaussian) pairs of a given FP32 Gaussian set in the
     documented order; Gaussian ids are positions in that set."""
-    _, g = _records_g(scene, rec, curve)
+    _, g, _ = _records_g(scene, rec, curve, shape=shape)
     r = scene.raster
     return rs.sorted_pairs(g, scene.height, scene.width, int(r["tile"]), r["k_sigma"], r["alpha_min"],
                            scene.n_scenes)
 
 
-def record_grads(scene, rec, curve, dimage):
+def record_grads(scene, rec, curve, dimage, shape=None):
     """Gradient of sum(image * dimage) with respect to each record's
-    (mu_x, mu_y, sigma, o) and each curve's colour, for a given FP32 set."""
-    rec64, g = _records_g(scene, rec, curve, requires_grad=True)
+    (mu_x, mu_y, sigma, o) and each curve's colour, for a given FP32 set;
+    with tangent-aligned records also with respect to (sigma_t, cos, sin),
+    returned as a third array."""
+    rec64, g, shape64 = _records_g(scene, rec, curve, requires_grad=True, shape=shape)
     color_t = torch.tensor(scene.color.astype(np.float64), requires_grad=True)
     img = rs.render_tiled(g, color_t, scene.n_scenes, scene.height, scene.width, scene.channels, scene.raster)
     (img * torch.as_tensor(dimage, dtype=DT)).sum().backward()
+    if shape64 is not None:
+        return rec64.grad.numpy(), color_t.grad.numpy(), shape64.grad.numpy()
     return rec64.grad.numpy(), color_t.grad.numpy()

@@ -8,6 +8,10 @@ over the Gaussians in depth order (front first).  Pixel (x, y) is sampled at
 with alpha < alpha_min is skipped, and compositing stops before a Gaussian
 that would take the transmittance below t_min.
 
+The tangent-aligned variant (the paper's anisotropic prototype, §3.2 and the
+supplement's comparison with Bezier Splatting) replaces the isotropic exponent
+by -(along^2 / sigma_t^2 + across^2 / sigma_n^2) / 2 in the tangent frame.
+
 Two renders are provided: brute force over every Gaussian of a scene, and the
 tiled render over per-tile lists built with the FP32 bin rule.  The bin rule
 and the sort order are computed in IEEE float32 (numpy, one rounding per
@@ -21,11 +25,22 @@ import torch
 DT = torch.float64
 
 
-def alpha(px, py, mu, sigma, o, alpha_max):
-    """Eq. 9 with the cap alpha_max: [P] pixels x [G] Gaussians."""
+def alpha(px, py, mu, sigma, o, alpha_max, shape=None):
+    """Eq. 9 with the cap alpha_max: [P] pixels x [G] Gaussians.
+
+    shape [G, 3] = (sigma_t, cos theta, sin theta) gives the tangent-aligned
+    (anisotropic) variant: the offset is written in the frame of the unit
+    tangent (cos, sin) and its normal, with deviations sigma_t along the
+    tangent and sigma (= sigma_n) across it."""
     dx = px[:, None] - mu[None, :, 0]
     dy = py[:, None] - mu[None, :, 1]
-    a = o[None, :] * torch.exp(-(dx * dx + dy * dy) / (2.0 * sigma * sigma)[None, :])
+    if shape is None:
+        a = o[None, :] * torch.exp(-(dx * dx + dy * dy) / (2.0 * sigma * sigma)[None, :])
+    else:
+        st, c, s = shape[:, 0][None, :], shape[:, 1][None, :], shape[:, 2][None, :]
+        along = dx * c + dy * s
+        across = -dx * s + dy * c
+        a = o[None, :] * torch.exp(-0.5 * (along * along / (st * st) + across * across / (sigma * sigma)[None, :]))
     return torch.clamp(a, max=alpha_max)
 
 
@@ -89,23 +104,39 @@ def near_threshold(al, alpha_min, t_min, rel=1e-4):
 # ----------------------------------------------------------------------------
 # binning (FP32, bit-exact rule)
 
-def tile_rects(mu, sigma, o, tile, k_sigma, alpha_min, tiles_x, tiles_y):
+def tile_rects(mu, sigma, o, tile, k_sigma, alpha_min, tiles_x, tiles_y, shape=None):
     """Per-Gaussian inclusive tile rectangle [x_lo, x_hi] x [y_lo, y_hi], or an
     empty one.  Every step is one IEEE float32 operation rounded to nearest:
         ks = k_sigma * sigma;  x_lo = floor((mu_x - ks) * (1/tile));
         x_hi = floor((mu_x + ks) * (1/tile)); the same in y; clipped to the grid.
+    With a tangent-aligned shape (sigma_t, c, s) the half widths are those of
+    the k_sigma ellipse's bounding box,
+        kx = k_sigma * sqrt(sigma_t^2 c^2 + sigma^2 s^2),
+        ky = k_sigma * sqrt(sigma_t^2 s^2 + sigma^2 c^2),
+    each square, product, sum and the (correctly rounded) square root one
+    float32 operation, in that order.
     A Gaussian with sigma <= 0, o <= 0 or o < alpha_min covers no tile (it
     cannot reach alpha_min anywhere)."""
     mu = np.asarray(mu, np.float32)
     s = np.asarray(sigma, np.float32)
     o = np.asarray(o, np.float32)
-    ks = np.float32(k_sigma) * s
     inv = np.float32(1.0 / tile)
-    xlo = np.floor((mu[:, 0] - ks) * inv)
-    xhi = np.floor((mu[:, 0] + ks) * inv)
-    ylo = np.floor((mu[:, 1] - ks) * inv)
-    yhi = np.floor((mu[:, 1] + ks) * inv)
-    valid = (s > 0) & (o > 0) & (o >= np.float32(alpha_min))
+    k = np.float32(k_sigma)
+    if shape is None:
+        kx = ky = k * s
+        ok = s > 0
+    else:
+        sh = np.asarray(shape, np.float32)
+        st, cs, sn = sh[:, 0], sh[:, 1], sh[:, 2]
+        st2, cs2, sn2, sg2 = st * st, cs * cs, sn * sn, s * s
+        kx = k * np.sqrt(st2 * cs2 + sg2 * sn2)
+        ky = k * np.sqrt(st2 * sn2 + sg2 * cs2)
+        ok = (s > 0) & (st > 0)
+    xlo = np.floor((mu[:, 0] - kx) * inv)
+    xhi = np.floor((mu[:, 0] + kx) * inv)
+    ylo = np.floor((mu[:, 1] - ky) * inv)
+    yhi = np.floor((mu[:, 1] + ky) * inv)
+    valid = ok & (o > 0) & (o >= np.float32(alpha_min))
     valid &= (xhi >= 0) & (yhi >= 0) & (xlo <= tiles_x - 1) & (ylo <= tiles_y - 1)
     xlo = np.clip(xlo, 0, tiles_x - 1).astype(np.int64)
     xhi = np.clip(xhi, 0, tiles_x - 1).astype(np.int64)
@@ -123,7 +154,9 @@ def sorted_pairs(g, H, W, tile, k_sigma, alpha_min, n_scenes):
     mu = g["mu"].detach().numpy()
     sg = g["sigma"].detach().numpy()
     o = g["o"].detach().numpy()
-    xlo, xhi, ylo, yhi, valid = tile_rects(mu, sg, o, tile, k_sigma, alpha_min, tx, ty)
+    shape = g.get("shape")
+    shape = None if shape is None else shape.detach().numpy()
+    xlo, xhi, ylo, yhi, valid = tile_rects(mu, sg, o, tile, k_sigma, alpha_min, tx, ty, shape)
     layer = g["layer"].numpy()
     sample = g["sample"].numpy()
     scene = g["scene"].numpy()
@@ -169,7 +202,9 @@ def render_brute(g, color_t, n_scenes, H, W, C, r):
         sel = torch.nonzero(g["scene"] == s).reshape(-1)
         key = g["layer"][sel] * (1 << 32) + g["sample"][sel]
         sel = sel[torch.argsort(key)]
-        al = alpha(px, py, g["mu"][sel], g["sigma"][sel], g["o"][sel], r["alpha_max"])
+        shp = g.get("shape")
+        al = alpha(px, py, g["mu"][sel], g["sigma"][sel], g["o"][sel], r["alpha_max"],
+                   None if shp is None else shp[sel])
         out, _, _ = composite_sequential(al, col[sel], r["bg"][:C], r["alpha_min"], r["t_min"])
         imgs.append(out.reshape(H, W, C))
     return torch.stack(imgs)
@@ -198,8 +233,9 @@ def render_tiled(g, color_t, n_scenes, H, W, C, r, return_flags=False, only_tile
             yy, xx = torch.meshgrid(ys, xs, indexing="ij")
             yy, xx = yy.reshape(-1), xx.reshape(-1)
             lst = torch.as_tensor(gid[ranges[gt, 0]:ranges[gt, 1]], dtype=torch.long)
+            shp = g.get("shape")
             al = alpha(xx.to(DT) + 0.5, yy.to(DT) + 0.5, g["mu"][lst], g["sigma"][lst], g["o"][lst],
-                       r["alpha_max"])
+                       r["alpha_max"], None if shp is None else shp[lst])
             out, _ = composite_cumprod(al, col[lst], r["bg"][:C], r["alpha_min"], r["t_min"])
             vals.append(out)
             idxs.append(s * H * W + yy * W + xx)

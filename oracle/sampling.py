@@ -190,11 +190,33 @@ def curve_gaussians(scene, c, key_t, tau_t, color_t, pl: CurvePlan):
         sdf = sgn * d
         oj = o * sigmoid(sp["gamma"] / h * sdf)
         sigma = torch.full((q.shape[0],), sp["eta"] * h / sp["rho"], dtype=DT)
-        return q, sigma, oj, (arg, sgn)
+        return q, sigma, oj, (arg, sgn)   # fills stay isotropic in every contour mode
     closed = pl.kind == "closed"
     u = contour_parameters(a, b, pl.m_contour, int(sp["kappa"]), closed)
     C = nb.curve_point(cp, U, p, u)
-    return C[:, :2], C[:, 2] / sp["rho"], o.expand(u.shape[0]), None
+    sigma = C[:, 2] / sp["rho"]
+    if int(sp.get("contour_mode", 0)) == 1:
+        return C[:, :2], sigma, o.expand(u.shape[0]), tangent_shape(cp, U, p, u, a, b, pl, sp, sigma)
+    return C[:, :2], sigma, o.expand(u.shape[0]), None
+
+
+def tangent_shape(cp, U, p, u, a, b, pl, sp, sigma_n):
+    """Tangent-aligned contour Gaussians (the anisotropic prototype): the unit
+    tangent (cos, sin) = C'_xy/|C'_xy| (Eq. 2) and sigma_t = |C'_xy| du / rho,
+    du the parameter step between consecutive samples ((b - a)/(M - 1) open,
+    (b - a)/M closed): the arc length between samples over the same ratio rho
+    as the width.  Where C' vanishes: tangent (1, 0) and sigma_t = sigma_n.
+    Returns [G, 3] = (sigma_t, cos, sin)."""
+    d = nb.curve_derivative(cp, U, p, u)
+    v = d[:, :2]
+    n = torch.sqrt((v * v).sum(1))
+    step = (b - a) / (pl.m_contour - 1 if pl.kind == "open" else pl.m_contour)
+    ok = n > 0
+    nn = torch.where(ok, n, torch.ones_like(n))
+    cs = torch.where(ok, v[:, 0] / nn, torch.ones_like(n))
+    sn = torch.where(ok, v[:, 1] / nn, torch.zeros_like(n))
+    st = torch.where(ok, n * step / sp["rho"], sigma_n)
+    return torch.stack([st, cs, sn], 1)
 
 
 def sample_scene(scene, key_t, tau_t, color_t, plans=None):
@@ -203,20 +225,30 @@ def sample_scene(scene, key_t, tau_t, color_t, plans=None):
     plus the plans used.  Pass `plans` to freeze the discrete structure."""
     if plans is None:
         plans = [plan_curve(scene, c, key_t, tau_t) for c in range(scene.n_curves)]
-    mus, sigmas, ops, curves, samples, layers, scenes_ = [], [], [], [], [], [], []
+    mus, sigmas, ops, curves, samples, layers, scenes_, shapes = [], [], [], [], [], [], [], []
     cs = scene.curve_scene()
+    aniso = int(scene.sample.get("contour_mode", 0)) == 1
     for c in range(scene.n_curves):
-        mu, sg, oj, _ = curve_gaussians(scene, c, key_t, tau_t, color_t, plans[c])
+        mu, sg, oj, extra = curve_gaussians(scene, c, key_t, tau_t, color_t, plans[c])
         G = mu.shape[0]
         s = int(cs[c])
         mus.append(mu)
         sigmas.append(sg)
+        if aniso:
+            if plans[c].kind == "fill" or extra is None:
+                ones = torch.ones(G, dtype=DT)
+                shapes.append(torch.stack([sg, ones, torch.zeros(G, dtype=DT)], 1))
+            else:
+                shapes.append(extra)
         ops.append(oj)
         curves.append(torch.full((G,), c, dtype=torch.long))
         samples.append(torch.arange(G))
         layers.append(torch.full((G,), int(scene.scene_curve_offset[s + 1]) - 1 - c, dtype=torch.long))
         scenes_.append(torch.full((G,), s, dtype=torch.long))
     cat = lambda xs, shape: torch.cat(xs) if xs else torch.zeros(shape)
-    return dict(mu=cat(mus, (0, 2)), sigma=cat(sigmas, (0,)), o=cat(ops, (0,)),
-                curve=cat(curves, (0,)).long(), sample=cat(samples, (0,)).long(),
-                layer=cat(layers, (0,)).long(), scene=cat(scenes_, (0,)).long(), plans=plans)
+    out = dict(mu=cat(mus, (0, 2)), sigma=cat(sigmas, (0,)), o=cat(ops, (0,)),
+               curve=cat(curves, (0,)).long(), sample=cat(samples, (0,)).long(),
+               layer=cat(layers, (0,)).long(), scene=cat(scenes_, (0,)).long(), plans=plans)
+    if aniso:
+        out["shape"] = cat(shapes, (0, 3))
+    return out
