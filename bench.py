@@ -536,13 +536,40 @@ def run_long_spline(torch, args):
     G = st.gaussians()
     rep = st.sp.report()
     ablation = run_ablation(torch, sc, st, tuning, geo, K)
+    aniso = run_tangent_variant(torch, sc, tuning, geo, K)
     return dict(workload="long-spline-512: 256 open cubic strokes, 64-512 key points, 512x512 gray, "
                          "+ derivative and box losses + Adam",
                 geometry_nodes_per_step=sc.n_curves * int(sc.sample["nl_mult"]) * max(sc.width, sc.height),
                 gaussians_per_step=G, pairs_per_step=int(rep.pairs), ms_per_step=round(ms, 4),
                 gaussians_per_s=round(G / (ms / 1e3), 1), autotune=tuning,
                 kernels={k: round(float(np.mean([a.elapsed_time(b) for a, b in ev[k]])), 4) for k in prof},
-                ablation=ablation)
+                ablation=ablation, tangent_aligned=aniso)
+
+
+def run_tangent_variant(torch, sc, tuning, geo, K, delta_c=1.0):
+    """The anisotropic prototype on the same strokes: tangent-aligned contour
+    Gaussians at a tenth of the contour density (sigma_t spans the larger
+    sample spacing), same step otherwise."""
+    sc2 = sc.with_sample(contour_mode=1, delta_c=delta_c)
+    s2 = Step(sc2, capacity=(3_000_000, 24_000_000, 16), raster=dict(sc2.raster, tile=tuning["tile"]), adam=True,
+              geometry=geo)
+    s2.sp.autotune_blend(s2.key, s2.tau, s2.color, s2.dimage, repeats=3)
+    s2()
+    g2 = capture(torch, s2, K)
+    g2.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    g2.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    G = s2.gaussians()
+    out = dict(delta_c=delta_c, gaussians_per_step=G, ms_per_step=round(ms, 4),
+               gaussians_per_s=round(G / (ms / 1e3), 1), ppt=(int(s2.sp.rp.ppt_fwd), int(s2.sp.rp.ppt_bwd)))
+    del g2, s2
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_ablation(torch, sc, st, tuning, geo, K):

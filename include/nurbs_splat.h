@@ -90,6 +90,12 @@ typedef struct {
   float fill_cull;  /* > 0: fill points provably outside with opacity below this
                        value (pass the rasterizer's alpha_min) get opacity 0 without
                        an exact distance; they bin to no tile either way.  0: off */
+  int32_t contour_mode; /* 0: isotropic contour Gaussians (Eq. 5, the paper's method);
+                       1: tangent-aligned (the paper's anisotropic prototype): each
+                       contour Gaussian is stretched along the unit tangent
+                       C'_xy/|C'_xy| (Eq. 2) with sigma_t = |C'_xy| du / rho, du the
+                       parameter step between samples, and keeps sigma_n = s / rho
+                       across; the Gaussian set then needs `shape` */
 } ns_sample_params;
 
 /* Rasterizer settings (§3.4). */
@@ -126,6 +132,12 @@ typedef struct {
                        or 0x80000000 for a point culled by fill_cull (no segment
                        needed for either); contours: -1 */
   int32_t* count;   /* device scalar: records in use */
+  float* shape;     /* device [capacity*4] or NULL.  Non-NULL marks a tangent-
+                       aligned set: {sigma_t, cos, sin, 0} per record, whose
+                       rec.sigma is the deviation across the tangent; isotropic
+                       records in it (fills) hold {sigma, 1, 0, 0}.  Written by
+                       nurbs_sample with contour_mode 1; the splat calls then use
+                       the exponent -(along^2/sigma_t^2 + across^2/sigma^2)/2 */
 } ns_gaussians;
 
 /* Parameters held fixed (the paper's "w/o weights", "w/o knots" and "w/o
@@ -227,6 +239,9 @@ ns_status splat_forward(const ns_curves* curves, const ns_gaussians* g,
  *   dL_dimage: device, same layout as the image.
  *   dgauss: device [g->capacity*8] or NULL: {dmu_x, dmu_y, dsigma, 0,
  *     dopacity, dr, dg, db} per Gaussian, zeroed and written by this call.
+ *     For a tangent-aligned set (g->shape non-NULL) rows are 12 floats,
+ *     {dmu_x, dmu_y, dA, dB2, dopacity, dr, dg, db, dC, 0, 0, 0}, the
+ *     gradients of the exponent A dx^2 + B2 dx dy + C dy^2's coefficients.
  *     When dgauss is NULL and `out` is given, the workspace holds them and the
  *     centre and sigma gradients of fill Gaussians, which the chain does not
  *     use (their grid is fixed), are not computed.

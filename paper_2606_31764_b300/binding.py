@@ -30,7 +30,8 @@ class NsCurves(C.Structure):
 class NsSampleParams(C.Structure):
     _fields_ = [("delta_c", C.c_float), ("rho", C.c_float), ("delta_b", C.c_float), ("h", C.c_float),
                 ("eta", C.c_float), ("gamma", C.c_float), ("pad_frac", C.c_float), ("kappa", C.c_int32),
-                ("nl_mult", C.c_int32), ("fill_rule", C.c_int32), ("fill_cull", C.c_float)]
+                ("nl_mult", C.c_int32), ("fill_rule", C.c_int32), ("fill_cull", C.c_float),
+                ("contour_mode", C.c_int32)]
 
 
 class NsRasterParams(C.Structure):
@@ -43,7 +44,7 @@ class NsCapacity(C.Structure):
 
 
 class NsGaussians(C.Structure):
-    _fields_ = [("capacity", C.c_int64), ("rec", _p), ("curve", _p), ("aux", _p), ("count", _p)]
+    _fields_ = [("capacity", C.c_int64), ("rec", _p), ("curve", _p), ("aux", _p), ("count", _p), ("shape", _p)]
 
 
 class NsGeometryParams(C.Structure):

@@ -137,8 +137,9 @@ bool make_layout(const ns_curves* c, const ns_capacity* cap, const ns_raster_par
   L->o_ranges = take(sizeof(int2) * (size_t)L->n_tiles);
   L->o_T = take(sizeof(float) * (size_t)L->n_pix);
   L->o_nlast = take(sizeof(int) * (size_t)L->n_pix);
-  L->o_dgauss = take(sizeof(float) * 8 * (size_t)L->gcap);
+  L->o_dgauss = take(sizeof(float) * 12 * (size_t)L->gcap);   // 8 per Gaussian, 12 when tangent-aligned
   L->o_prep = take(sizeof(float4) * (size_t)L->gcap);
+  L->o_prep2 = take(sizeof(float2) * (size_t)L->gcap);
   L->o_reach = take(sizeof(float2) * (size_t)L->gcap);
   L->o_live = take(sizeof(float) * 4 * (size_t)L->S);
   L->total = o;
@@ -217,6 +218,7 @@ ns_sample_params ns_default_sample_params(void) {
   p.nl_mult = 3;
   p.fill_rule = 0;
   p.fill_cull = 0.f;
+  p.contour_mode = 0;  // isotropic contour Gaussians (Eq. 5)
   return p;
 }
 

@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(256) k_chain(ns_curves cv, ChainParams cp, con
                                                const float2* __restrict__ bpts, const DevState* __restrict__ st,
                                                const float4* __restrict__ rec, const int* __restrict__ gaux,
                                                const float* __restrict__ dgauss, long long gcap, long long bcap,
-                                               float* dkey, float* dknots, float2* dbpts, float* dcolor) {
+                                               float* dkey, float* dknots, float2* dbpts, float* dcolor, int row4) {
   __shared__ float2 s_db[kWinB];
   __shared__ float s_red[8];
   const int n_tasks = st->n_chunks;
@@ -105,8 +105,8 @@ __global__ void __launch_bounds__(256) k_chain(ns_curves cv, ChainParams cp, con
     if (threadIdx.x < 8) s_red[threadIdx.x] = 0.f;
     float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0;
     if (valid) {
-      g0 = reinterpret_cast<const float4*>(dgauss)[2 * g];
-      g1 = reinterpret_cast<const float4*>(dgauss)[2 * g + 1];
+      g0 = reinterpret_cast<const float4*>(dgauss)[row4 * g];
+      g1 = reinterpret_cast<const float4*>(dgauss)[row4 * g + 1];
     }
     {
     // fill task (skipped when its polyline overflowed the boundary capacity)
@@ -187,7 +187,56 @@ __global__ void __launch_bounds__(256) k_chain(ns_curves cv, ChainParams cp, con
 constexpr int kContourThreads = 64;
 constexpr int kContourPer = kChunk / kContourThreads;
 
+// Tangent-aligned sample: the gradient of its exponent's conic {dA, dB2, dC}
+// (rows of k_blend_bwd) -> dL/dsigma_n, dL/dC'_xy (through the unit tangent and
+// sigma_t = |C'| du / rho) and dL/d(du), then both back through C(u) and C'(u).
+// With (c, s) the tangent, it = 1/sigma_t^2, in = 1/sigma_n^2:
+//   A = -(c^2 it + s^2 in)/2,  B2 = -c s (it - in),  C = -(s^2 it + c^2 in)/2.
 template <int P, bool KNOTS>
+__device__ __forceinline__ void tangent_sample_bwd(const float4* key, const CurveRef& cr, const float* U, int i,
+                                                   float u, float rho, float step, float4 g0, float dC,
+                                                   float dcp[P + 1][4], float dkn[2 * P], float& du, float& dstep) {
+  Eval<P> e;
+  eval_curve<P>(key, cr, U, i, u, e);
+  float dN[P + 1];
+  basis_deriv<P>(e.t, dN);
+  float dSx = 0.f, dSy = 0.f, dW = 0.f;
+#pragma unroll
+  for (int l = 0; l <= P; ++l) {
+    const float nw = dN[l] * e.cp[l].w;
+    dSx = fmaf(nw, e.cp[l].x, dSx);
+    dSy = fmaf(nw, e.cp[l].y, dSy);
+    dW += nw;
+  }
+  const float iw = 1.f / e.W;
+  const float vx = (dSx - e.C[0] * dW) * iw, vy = (dSy - e.C[1] * dW) * iw;
+  const float n = sqrtf(vx * vx + vy * vy);
+  const float sn = e.C[2] / rho;
+  const float dA = g0.z, dB2 = g0.w;
+  float gD[2] = {0.f, 0.f};
+  float dsn;
+  dstep = 0.f;
+  if (n > 0.f) {
+    const float c = vx / n, s = vy / n, st = n * step / rho;
+    const float it = 1.f / (st * st), in = 1.f / (sn * sn);
+    const float g_it = -0.5f * c * c * dA - c * s * dB2 - 0.5f * s * s * dC;
+    const float g_in = -0.5f * s * s * dA + c * s * dB2 - 0.5f * c * c * dC;
+    const float g_c = -c * it * dA - s * (it - in) * dB2 - c * in * dC;
+    const float g_s = -s * in * dA - c * (it - in) * dB2 - s * it * dC;
+    const float dst = -2.f * g_it / (st * st * st);
+    dsn = -2.f * g_in / (sn * sn * sn);
+    const float in_n = 1.f / n;
+    gD[0] = dst * step / rho * c + (g_c * (1.f - c * c) - g_s * c * s) * in_n;
+    gD[1] = dst * step / rho * s + (g_s * (1.f - s * s) - g_c * c * s) * in_n;
+    dstep = dst * n / rho;
+  } else {   // no tangent: the record is isotropic, sigma_t = sigma_n, tangent (1, 0): A = C = -1/(2 sigma_n^2)
+    dsn = (dA + dC) / (sn * sn * sn);
+  }
+  const float gC[3] = {g0.x, g0.y, dsn / rho};
+  curve_tangent_adjoint<P, KNOTS>(e, dN, gC, gD, dcp, dkn, &du);
+}
+
+template <int P, bool KNOTS, bool ANISO>
 __device__ void chain_contour_run(const ns_curves& cv, const CurveRef& cr, const float* U, const CurvePlan& pl,
                                   int l0, const ChainParams& cp, const float* __restrict__ dgauss, long long gcap,
                                   float* s_cp, float* s_kn, int cp_lo, int kn_lo, int ncp, int nkn, float* dkey,
@@ -227,13 +276,15 @@ __device__ void chain_contour_run(const ns_curves& cv, const CurveRef& cr, const
     const int l = l0 + threadIdx.x * kContourPer + j;
     const long long g = (long long)pl.g_off + l;
     if (l >= pl.count || g >= gcap) break;
-    const float4 g0 = reinterpret_cast<const float4*>(dgauss)[2 * g];
-    const float4 g1 = reinterpret_cast<const float4*>(dgauss)[2 * g + 1];
-    dcol.x += g1.y;   // row layout {dmu_x, dmu_y, dsigma, 0, do, dr, dg, db}
+    constexpr int kRow4 = ANISO ? 3 : 2;   // float4 per gradient row
+    const float4 g0 = reinterpret_cast<const float4*>(dgauss)[kRow4 * g];
+    const float4 g1 = reinterpret_cast<const float4*>(dgauss)[kRow4 * g + 1];
+    const float gCc = ANISO ? dgauss[kRow4 * 4 * g + 8] : 0.f;
+    dcol.x += g1.y;   // row layout {dmu_x, dmu_y, dsigma, 0, do, dr, dg, db} (tangent-aligned: dA, dB2, ..., dC)
     dcol.y += g1.z;
     dcol.z += g1.w;
     dcol.w += g1.x;
-    if (g0.x == 0.f && g0.y == 0.f && g0.z == 0.f) continue;   // no geometric gradient
+    if (g0.x == 0.f && g0.y == 0.f && g0.z == 0.f && g0.w == 0.f && gCc == 0.f) continue;   // no geometric gradient
     const float u = contour_u(pl, l, cp.kappa);
     const float t = contour_t(pl, l, cp.kappa);
     const int i = find_span(U, P, cr.n, u);
@@ -245,9 +296,20 @@ __device__ void chain_contour_run(const ns_curves& cv, const CurveRef& cr, const
 #pragma unroll
       for (int k = 0; k < 2 * P; ++k) akn[k] = 0.f;
     }
-    const float gC[3] = {g0.x, g0.y, g0.z / cp.rho};
     float du;
-    curve_point_bwd_local<P, KNOTS>(key, cr, U, i, u, gC, acc, akn, du);
+    if constexpr (ANISO) {
+      const int K = pl.kind == kOpen ? pl.M - 1 : pl.M;   // du = (b - a) / K between samples
+      const float step = (pl.b - pl.a) / float(K);
+      float dstep;
+      tangent_sample_bwd<P, KNOTS>(key, cr, U, i, u, cp.rho, step, g0, gCc, acc, akn, du, dstep);
+      if (KNOTS) {
+        dA -= dstep / float(K);
+        dB += dstep / float(K);
+      }
+    } else {
+      const float gC[3] = {g0.x, g0.y, g0.z / cp.rho};
+      curve_point_bwd_local<P, KNOTS>(key, cr, U, i, u, gC, acc, akn, du);
+    }
     dA += du * (1.f - t);   // u = a + t (b - a); 0 without KNOTS
     dB += du * t;
   }
@@ -257,7 +319,7 @@ __device__ void chain_contour_run(const ns_curves& cv, const CurveRef& cr, const
 // One kernel per degree (the degree-5 registers would otherwise set the
 // occupancy of every task); each skips the tasks of other degrees.  KNOTS
 // false: knot intervals frozen, no knot gradient is formed.
-template <int P, bool KNOTS>
+template <int P, bool KNOTS, bool ANISO>
 __global__ void __launch_bounds__(kContourThreads) k_chain_contour(
     ns_curves cv, ChainParams cp, const CurvePlan* __restrict__ plan, const int* __restrict__ order,
     const float* __restrict__ knots, const DevState* __restrict__ st, const float* __restrict__ dgauss,
@@ -293,8 +355,8 @@ __global__ void __launch_bounds__(kContourThreads) k_chain_contour(
     __syncthreads();
     float dA = 0.f, dB = 0.f;
     float4 dcol = make_float4(0.f, 0.f, 0.f, 0.f);
-    chain_contour_run<P, KNOTS>(cv, cr, U, pl, l0, cp, dgauss, gcap, s_cp, s_kn, cp_lo, kn_lo, ncp, nkn, dkey,
-                                dknots, dA, dB, dcol);
+    chain_contour_run<P, KNOTS, ANISO>(cv, cr, U, pl, l0, cp, dgauss, gcap, s_cp, s_kn, cp_lo, kn_lo, ncp, nkn, dkey,
+                                       dknots, dA, dB, dcol);
     {
       const float v[8] = {dA, dB, dcol.x, dcol.y, dcol.z, dcol.w, 0.f, 0.f};
       const float tot = warp_sum8(v);
@@ -441,8 +503,10 @@ extern "C" ns_status splat_backward(const ns_curves* curves, const ns_gaussians*
     return NS_ERR_INVALID_ARG;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool aniso = g->shape != nullptr;
+  const int row = aniso ? 12 : 8;   // floats per per-Gaussian gradient row
   float* dg = dgauss ? dgauss : at<float>(ws, L.o_dgauss);
-  cudaMemsetAsync(dg, 0, sizeof(float) * 8 * (size_t)L.gcap, s);
+  cudaMemsetAsync(dg, 0, sizeof(float) * row * (size_t)L.gcap, s);
   // the centre and sigma gradients of fill Gaussians are needed only when the
   // caller asked for the per-Gaussian gradients themselves
   launch_blend_bwd(L, curves, g, rp, dL_dimage, dg, ws, s, dgauss != nullptr || out == nullptr);
@@ -471,16 +535,19 @@ extern "C" ns_status splat_backward(const ns_curves* curves, const ns_gaussians*
       cp.freeze_w = (out->frozen & NS_FROZEN_WEIGHTS) != 0;
       NS_LAUNCH(NS_KERNEL_CHAIN, k_chain, num_sms() * 8, 256, 0, s, *curves, cp, plan, order, knots, bpts, st,
                 reinterpret_cast<const float4*>(g->rec), g->aux, dg, cap->gaussians,
-                cap->boundary, out->dkey, dknots, dbpts, out->dcolor);
+                cap->boundary, out->dkey, dknots, dbpts, out->dcolor, row / 4);
       {
         // one launch per degree present among the curves (the host knows the
         // degrees only on the device, so all five are launched; a launch with
         // no task of its degree exits after scanning the task list)
-        auto k1 = knots_on ? &k_chain_contour<1, true> : &k_chain_contour<1, false>;
-        auto k2 = knots_on ? &k_chain_contour<2, true> : &k_chain_contour<2, false>;
-        auto k3 = knots_on ? &k_chain_contour<3, true> : &k_chain_contour<3, false>;
-        auto k4 = knots_on ? &k_chain_contour<4, true> : &k_chain_contour<4, false>;
-        auto k5 = knots_on ? &k_chain_contour<5, true> : &k_chain_contour<5, false>;
+#define NS_CC(P) (aniso ? (knots_on ? &k_chain_contour<P, true, true> : &k_chain_contour<P, false, true>) \
+                         : (knots_on ? &k_chain_contour<P, true, false> : &k_chain_contour<P, false, false>))
+        auto k1 = NS_CC(1);
+        auto k2 = NS_CC(2);
+        auto k3 = NS_CC(3);
+        auto k4 = NS_CC(4);
+        auto k5 = NS_CC(5);
+#undef NS_CC
         const int grid = num_sms() * 16;
         // the five launches form one profiled range (armed events bracket
         // the first and the last)

@@ -55,36 +55,6 @@ __device__ __forceinline__ float binom_small(int k, int q) {
   return row[k][q];
 }
 
-// Reverse sweep of the span triangle with adjoints entering at every level:
-// gTop[r] = dL/dN_{i-P+r,P}, gLow[d][r] = dL/dN_{i-d+r,d} for d < P.  Same
-// recurrence as basis_bwd; the level-d adjoints join before level d is swept.
-template <int P>
-__device__ __forceinline__ void basis_bwd_levels(const Tri<P>& t, const float* gTop, const float (*gLow)[P],
-                                                 float* du, float* dU) {
-  float g[P + 1];
-#pragma unroll
-  for (int r = 0; r <= P; ++r) g[r] = gTop[r];
-#pragma unroll
-  for (int j = P; j >= 1; --j) {
-    float gp[P];
-#pragma unroll
-    for (int r = 0; r < j; ++r) {
-      const float x = t.lev[j - 1][r];
-      const float D = t.right[r + 1] + t.left[j - r];
-      const float inv = 1.f / D;
-      const float al = t.left[j - r] * inv;
-      const float be = t.right[r + 1] * inv;
-      gp[r] = be * g[r] + al * g[r + 1];
-      const float dal = x * (g[r + 1] - g[r]);
-      *du += dal * inv;
-      dU[r + P - j] += dal * (al - 1.f) * inv;
-      dU[r + P] -= dal * al * inv;
-    }
-#pragma unroll
-    for (int r = 0; r < j; ++r) g[r] = gp[r] + gLow[j - 1][r];
-  }
-}
-
 // N_{i-d+r, d}(u) from the span triangle (level P is the top row).
 template <int P>
 __device__ __forceinline__ float level_value(const Tri<P>& t, int d, int r) {

@@ -70,7 +70,8 @@ struct Layout {
   int64_t bin_blocks = 0, sort_blocks = 0;
   size_t o_state = 0, o_plan = 0, o_knots = 0, o_dknots = 0, o_bpts = 0, o_dbpts = 0, o_bsum = 0,
          o_k0 = 0, o_v0 = 0, o_k1 = 0, o_v1 = 0, o_hist = 0, o_ranges = 0, o_T = 0, o_nlast = 0,
-         o_dgauss = 0, o_curve_scene = 0, o_order = 0, o_prep = 0, o_reach = 0, o_live = 0, total = 0;
+         o_dgauss = 0, o_curve_scene = 0, o_order = 0, o_prep = 0, o_prep2 = 0, o_reach = 0, o_live = 0,
+         total = 0;
   size_t sample_total = 0;   // bytes of the prefix nurbs_sample uses (independent of the raster settings)
 };
 
@@ -293,6 +294,99 @@ __device__ __forceinline__ void curve_point_adjoint(const Eval<P>& e, const floa
   }
   float d = 0.f;
   if constexpr (KNOTS) basis_bwd<P>(e.t, gN, &d, dkn);
+  *du = d;
+}
+
+// Reverse sweep of the span triangle with adjoints entering at every level:
+// gTop[r] = dL/dN_{i-P+r,P}, gLow[d][r] = dL/dN_{i-d+r,d} for d < P.  Same
+// recurrence as basis_bwd; the level-d adjoints join before level d is swept.
+template <int P>
+__device__ __forceinline__ void basis_bwd_levels(const Tri<P>& t, const float* gTop, const float (*gLow)[P],
+                                                 float* du, float* dU) {
+  float g[P + 1];
+#pragma unroll
+  for (int r = 0; r <= P; ++r) g[r] = gTop[r];
+#pragma unroll
+  for (int j = P; j >= 1; --j) {
+    float gp[P];
+#pragma unroll
+    for (int r = 0; r < j; ++r) {
+      const float x = t.lev[j - 1][r];
+      const float D = t.right[r + 1] + t.left[j - r];
+      const float inv = 1.f / D;
+      const float al = t.left[j - r] * inv;
+      const float be = t.right[r + 1] * inv;
+      gp[r] = be * g[r] + al * g[r + 1];
+      const float dal = x * (g[r + 1] - g[r]);
+      *du += dal * inv;
+      dU[r + P - j] += dal * (al - 1.f) * inv;
+      dU[r + P] -= dal * al * inv;
+    }
+#pragma unroll
+    for (int r = 0; r < j; ++r) g[r] = gp[r] + gLow[j - 1][r];
+  }
+}
+
+// Reverse of a curve point and of its tangent at one evaluated point: given
+// gC = dL/dC (x, y, s) and gD = dL/dC'_xy, with C' = (S' - C_xy W') / W (Eq. 2)
+// and the basis derivatives dN from level P-1 of the triangle, adds
+// dL/d{x, y, s, w} of the span's control points to dcp, dL/dU of its 2P knots
+// to dkn and returns dL/du in *du (0 without KNOTS).
+template <int P, bool KNOTS>
+__device__ __forceinline__ void curve_tangent_adjoint(const Eval<P>& e, const float* dN, const float gC[3],
+                                                      const float gD[2], float dcp[P + 1][4], float dkn[2 * P],
+                                                      float* du) {
+  const float iw = 1.f / e.W;
+  float dSx = 0.f, dSy = 0.f, dW = 0.f;
+#pragma unroll
+  for (int l = 0; l <= P; ++l) {
+    const float nw = dN[l] * e.cp[l].w;
+    dSx = fmaf(nw, e.cp[l].x, dSx);
+    dSy = fmaf(nw, e.cp[l].y, dSy);
+    dW += nw;
+  }
+  const float Dx = (dSx - e.C[0] * dW) * iw, Dy = (dSy - e.C[1] * dW) * iw;
+  // C' = (S' - C W') / W
+  const float gSp0 = gD[0] * iw, gSp1 = gD[1] * iw;
+  const float gWp = -(gD[0] * e.C[0] + gD[1] * e.C[1]) * iw;
+  const float gc0 = gC[0] - gD[0] * dW * iw, gc1 = gC[1] - gD[1] * dW * iw, gc2 = gC[2];
+  // C = S / W
+  const float gS0 = gc0 * iw, gS1 = gc1 * iw, gS2 = gc2 * iw;
+  const float gW = -(gc0 * e.C[0] + gc1 * e.C[1] + gc2 * e.C[2]) * iw - (gD[0] * Dx + gD[1] * Dy) * iw;
+  float gN[P + 1], gNp[P + 1];
+#pragma unroll
+  for (int l = 0; l <= P; ++l) {
+    const float4 q = e.cp[l];
+    const float N = e.t.N[l], Np = dN[l];
+    const float g_nw = gS0 * q.x + gS1 * q.y + gS2 * q.z + gW;    // d/d(N w)
+    const float g_npw = gSp0 * q.x + gSp1 * q.y + gWp;             // d/d(N' w)
+    dcp[l][0] += q.w * (N * gS0 + Np * gSp0);
+    dcp[l][1] += q.w * (N * gS1 + Np * gSp1);
+    dcp[l][2] += q.w * N * gS2;
+    dcp[l][3] += g_nw * N + g_npw * Np;
+    gN[l] = g_nw * q.w;
+    gNp[l] = g_npw * q.w;
+  }
+  float d = 0.f;
+  if constexpr (KNOTS) {
+    // N'_r = P (tmp[r-1] - tmp[r]), tmp[r] = lev[P-1][r] / D_r, D_r = U[i+r+1] - U[i+r+1-P]
+    float gLow[P][P];
+#pragma unroll
+    for (int a = 0; a < P; ++a)
+#pragma unroll
+      for (int b = 0; b < P; ++b) gLow[a][b] = 0.f;
+#pragma unroll
+    for (int r = 0; r < P; ++r) {
+      const float D = e.t.right[r + 1] + e.t.left[P - r];
+      const float tmp = e.t.lev[P - 1][r] / D;
+      const float gt = float(P) * (gNp[r + 1] - gNp[r]);
+      gLow[P - 1][r] += gt / D;
+      const float gDr = -gt * tmp / D;
+      dkn[r + P] += gDr;
+      dkn[r] -= gDr;
+    }
+    basis_bwd_levels<P>(e.t, gN, gLow, &d, dkn);
+  }
   *du = d;
 }
 

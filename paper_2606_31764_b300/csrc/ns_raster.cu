@@ -66,6 +66,38 @@ __device__ __forceinline__ int tile_rect(const float4 r, const BinParams& bp, in
   return nx * (y1 - y0 + 1);
 }
 
+// The same for a tangent-aligned Gaussian, sh = {sigma_t, cos, sin, 0} and
+// r.z = sigma_n: the half widths of the k_sigma ellipse's bounding box,
+// k sqrt(sigma_t^2 c^2 + sigma_n^2 s^2) in x and k sqrt(sigma_t^2 s^2 + sigma_n^2 c^2)
+// in y, each operation rounded to nearest in this order.
+__device__ __forceinline__ int tile_rect_aniso(const float4 r, const float4 sh, const BinParams& bp, int& x0,
+                                               int& y0, int& nx) {
+  const float st2 = __fmul_rn(sh.x, sh.x), cs2 = __fmul_rn(sh.y, sh.y), sn2 = __fmul_rn(sh.z, sh.z);
+  const float sg2 = __fmul_rn(r.z, r.z);
+  const float kx = __fmul_rn(bp.k_sigma, __fsqrt_rn(__fadd_rn(__fmul_rn(st2, cs2), __fmul_rn(sg2, sn2))));
+  const float ky = __fmul_rn(bp.k_sigma, __fsqrt_rn(__fadd_rn(__fmul_rn(st2, sn2), __fmul_rn(sg2, cs2))));
+  const float xlo = floorf(__fmul_rn(__fsub_rn(r.x, kx), bp.inv_tile));
+  const float xhi = floorf(__fmul_rn(__fadd_rn(r.x, kx), bp.inv_tile));
+  const float ylo = floorf(__fmul_rn(__fsub_rn(r.y, ky), bp.inv_tile));
+  const float yhi = floorf(__fmul_rn(__fadd_rn(r.y, ky), bp.inv_tile));
+  const bool ok = r.z > 0.f && sh.x > 0.f && r.w > 0.f && r.w >= bp.alpha_min && xhi >= 0.f && yhi >= 0.f &&
+                  xlo <= float(bp.tiles_x - 1) && ylo <= float(bp.tiles_y - 1);
+  if (!ok) return 0;
+  x0 = int(fmaxf(xlo, 0.f));
+  const int x1 = int(fminf(xhi, float(bp.tiles_x - 1)));
+  y0 = int(fmaxf(ylo, 0.f));
+  const int y1 = int(fminf(yhi, float(bp.tiles_y - 1)));
+  nx = x1 - x0 + 1;
+  return nx * (y1 - y0 + 1);
+}
+
+template <bool ANISO>
+__device__ __forceinline__ int tile_rect_of(const float4* __restrict__ rec, const float4* __restrict__ shape,
+                                            long long g, const BinParams& bp, int& x0, int& y0, int& nx) {
+  if constexpr (ANISO) return tile_rect_aniso(rec[g], shape[g], bp, x0, y0, nx);
+  else return tile_rect(rec[g], bp, x0, y0, nx);
+}
+
 __device__ __forceinline__ int block_excl_scan_int(int v, int* s_warp, int& total) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   int x = v;
@@ -101,10 +133,14 @@ __device__ __forceinline__ float reach2(float sigma, float o, float log_amin) {
 }
 
 // Counts tiles per Gaussian and prepares the per-Gaussian blend constants.
-__global__ void __launch_bounds__(256) k_bin_count(const float4* __restrict__ rec, const int* __restrict__ gcurve,
+// Tangent-aligned Gaussians keep the exponent's conic: prep = {mu_x, mu_y, A,
+// o}, prep2 = {B2, C} with exponent A dx^2 + B2 dx dy + C dy^2.
+template <bool ANISO>
+__global__ void __launch_bounds__(256) k_bin_count(const float4* __restrict__ rec, const float4* __restrict__ shape,
+                                                   const int* __restrict__ gcurve,
                                                    const int* __restrict__ gaux, const int* __restrict__ gcount,
                                                    BinParams bp, int* bsum, DevState* st, float4* prep,
-                                                   float2* reach) {
+                                                   float2* prep2, float2* reach) {
   __shared__ int s_warp[32];
   const int G = min(*gcount, bp.gcap);
   const long long base = (long long)blockIdx.x * kBinItems;
@@ -117,14 +153,26 @@ __global__ void __launch_bounds__(256) k_bin_count(const float4* __restrict__ re
       const float4 r = rec[g];
       int x0, y0, nx;
       const int cv = gcurve[g];
-      const int nt = (cv >= 0 && cv < bp.n_curves) ? tile_rect(r, bp, x0, y0, nx) : 0;
+      const int nt = (cv >= 0 && cv < bp.n_curves) ? tile_rect_of<ANISO>(rec, shape, g, bp, x0, y0, nx) : 0;
       cnt += nt;
       if (nt) {   // only binned Gaussians are ever read by the blend kernels
-        prep[g] = make_float4(r.x, r.y, ncoef(r.z), r.w);
         // 1/sigma, negative for fill Gaussians (their centre and sigma get no
         // gradient through the chain, so the adjoint may skip them)
         const float isg = 1.f / r.z;
-        reach[g] = make_float2(reach2(r.z, r.w, bp.log_amin), gaux && gaux[g] != -1 ? -isg : isg);
+        const float sgn_isg = gaux && gaux[g] != -1 ? -isg : isg;
+        if constexpr (ANISO) {
+          const float4 sh = shape[g];
+          const float it = 1.f / (sh.x * sh.x), in = 1.f / (r.z * r.z);
+          const float A = -0.5f * (sh.y * sh.y * it + sh.z * sh.z * in);
+          const float B2 = -sh.y * sh.z * (it - in);
+          const float Cc = -0.5f * (sh.z * sh.z * it + sh.y * sh.y * in);
+          prep[g] = make_float4(r.x, r.y, A, r.w);
+          prep2[g] = make_float2(B2, Cc);
+          reach[g] = make_float2(reach2(fmaxf(sh.x, r.z), r.w, bp.log_amin), sgn_isg);
+        } else {
+          prep[g] = make_float4(r.x, r.y, ncoef(r.z), r.w);
+          reach[g] = make_float2(reach2(r.z, r.w, bp.log_amin), sgn_isg);
+        }
       }
       culled += (r.z > 0.f && r.w < bp.alpha_min) ? 1 : 0;
     }
@@ -181,7 +229,9 @@ __global__ void k_scan_small(int* vals, const int* gcount, int gcap, int items_p
   }
 }
 
-__global__ void __launch_bounds__(256) k_bin_emit(const float4* __restrict__ rec, const int* __restrict__ gcurve,
+template <bool ANISO>
+__global__ void __launch_bounds__(256) k_bin_emit(const float4* __restrict__ rec, const float4* __restrict__ shape,
+                                                  const int* __restrict__ gcurve,
                                                   const int* __restrict__ gcount, const int* __restrict__ curve_scene,
                                                   BinParams bp, const int* __restrict__ boff, uint32_t* keys,
                                                   uint32_t* vals, long long pcap) {
@@ -197,7 +247,7 @@ __global__ void __launch_bounds__(256) k_bin_emit(const float4* __restrict__ rec
     cnt[k] = 0;
     if (g < G) {
       const int cv = gcurve[g];
-      if (cv >= 0 && cv < bp.n_curves) cnt[k] = tile_rect(rec[g], bp, x0[k], y0[k], nx[k]);
+      if (cv >= 0 && cv < bp.n_curves) cnt[k] = tile_rect_of<ANISO>(rec, shape, g, bp, x0[k], y0[k], nx[k]);
     }
     tot += cnt[k];
   }
@@ -407,6 +457,18 @@ __device__ __forceinline__ float gauss_alpha(float fx, float fy, float4 q, float
   return fminf(__fmul_rn(q.w, e), amax);
 }
 
+// Alpha of a tangent-aligned Gaussian from its conic (prep {mu_x, mu_y, A, o},
+// q2 = {B2, C}): exponent A dx^2 + B2 dx dy + C dy^2, the same roundings in the
+// forward and the backward kernels.
+__device__ __forceinline__ float gauss_alpha_aniso(float fx, float fy, float4 q, float2 q2, float amax, float& dx,
+                                                   float& dy, float& e) {
+  dx = __fsub_rn(fx, q.x);
+  dy = __fsub_rn(fy, q.y);
+  const float E = __fmaf_rn(q.z, __fmul_rn(dx, dx), __fmaf_rn(q2.x, __fmul_rn(dx, dy), __fmul_rn(q2.y, __fmul_rn(dy, dy))));
+  e = __expf(E);
+  return fminf(__fmul_rn(q.w, e), amax);
+}
+
 // Squared distance from (x, y) to the rectangle [x0, x1] x [y0, y1].
 __device__ __forceinline__ float rect_d2(float x, float y, float x0, float x1, float y0, float y1) {
   const float dx = fmaxf(fmaxf(x0 - x, x - x1), 0.f);
@@ -447,14 +509,16 @@ __device__ __forceinline__ void tile_pixels(const BlendParams& bp, int& s, int& 
   rect = make_float4(bx + 0.5f, bx + 7.5f, by + 0.5f, by + 4.f * PPT - 0.5f);
 }
 
-template <int TILE, int PPT, int C>
+template <int TILE, int PPT, int C, bool ANISO>
 __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE, PPT>::kMinBlocks)
     k_blend_fwd(const int2* __restrict__ ranges, const uint32_t* __restrict__ gid, const float4* __restrict__ prep,
-                const float2* __restrict__ reach, const int* __restrict__ gcurve, const float4* __restrict__ color,
-                BlendParams bp, float* image, float* Tfinal, int* nlast, DevState* st) {
+                const float2* __restrict__ prep2, const float2* __restrict__ reach, const int* __restrict__ gcurve,
+                const float4* __restrict__ color, BlendParams bp, float* image, float* Tfinal, int* nlast,
+                DevState* st) {
   using Gm = BlendGeom<TILE, PPT>;
   __shared__ float4 s_q[Gm::kWarps][32];
   __shared__ float4 s_c[Gm::kWarps][32];
+  __shared__ float2 s_q2[ANISO ? Gm::kWarps : 1][32];
   int s, px, py0;
   float4 wr;
   tile_pixels<TILE, PPT>(bp, s, px, py0, wr);
@@ -490,6 +554,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
       if (hit) {
         s_q[w][lane] = q;
         s_c[w][lane] = color[gcurve[g]];
+        if (ANISO) s_q2[ANISO ? w : 0][lane] = prep2[g];
       }
     }
     unsigned int mask = __ballot_sync(0xffffffffu, hit);
@@ -498,12 +563,14 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
       const int b = __ffs(mask) - 1;
       mask &= mask - 1;
       const float4 q = s_q[w][b];
+      const float2 q2 = ANISO ? s_q2[ANISO ? w : 0][b] : make_float2(0.f, 0.f);
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
         if (done[k]) continue;
         ++evals;
         float dx, dy, d2, e;
-        const float a = gauss_alpha(fx, py0 + 4 * k + 0.5f, q, bp.alpha_max, dx, dy, d2, e);
+        const float a = ANISO ? gauss_alpha_aniso(fx, py0 + 4 * k + 0.5f, q, q2, bp.alpha_max, dx, dy, e)
+                              : gauss_alpha(fx, py0 + 4 * k + 0.5f, q, bp.alpha_max, dx, dy, d2, e);
         if (a < bp.alpha_min) continue;
         const float test = T[k] * (1.f - a);
         if (test < bp.t_min) {
@@ -548,17 +615,28 @@ __device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, 
                : "memory");
 }
 
-template <int TILE, int PPT, int C>
+// Rows of the per-Gaussian gradients: {dmu_x, dmu_y, dsigma, 0, do, dr, dg, db};
+// tangent-aligned: {dmu_x, dmu_y, dA, dB2, do, dr, dg, db, dC, 0, 0, 0} (the
+// conic of gauss_alpha_aniso).
+template <bool ANISO>
+struct GradRow {
+  static constexpr int kFloats = ANISO ? 12 : 8;
+};
+
+template <int TILE, int PPT, int C, bool ANISO>
 __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE, PPT>::kMinBlocksBwd)
     k_blend_bwd(const int2* __restrict__ ranges, const uint32_t* __restrict__ gid, const float4* __restrict__ prep,
-                const float2* __restrict__ reach, const int* __restrict__ gcurve, const float4* __restrict__ color,
-                BlendParams bp, const float* __restrict__ dimage, const float* __restrict__ Tfinal,
-                const int* __restrict__ nlast, float* dgauss, DevState* st, int full_grads) {
+                const float2* __restrict__ prep2, const float2* __restrict__ reach, const int* __restrict__ gcurve,
+                const float4* __restrict__ color, BlendParams bp, const float* __restrict__ dimage,
+                const float* __restrict__ Tfinal, const int* __restrict__ nlast, float* dgauss, DevState* st,
+                int full_grads) {
   using Gm = BlendGeom<TILE, PPT>;
+  constexpr int kRow = GradRow<ANISO>::kFloats;
   __shared__ float4 s_q[Gm::kWarps][32];
   __shared__ float4 s_c[Gm::kWarps][32];
   __shared__ float s_isig[Gm::kWarps][32];
   __shared__ uint32_t s_id[Gm::kWarps][32];
+  __shared__ float2 s_q2[ANISO ? Gm::kWarps : 1][32];
   int s, px, py0;
   float4 wr;
   tile_pixels<TILE, PPT>(bp, s, px, py0, wr);
@@ -601,6 +679,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
         s_c[w][lane] = color[gcurve[g]];
         s_isig[w][lane] = rs.y;
         s_id[w][lane] = g;
+        if (ANISO) s_q2[ANISO ? w : 0][lane] = prep2[g];
       }
     }
     unsigned int mask = __ballot_sync(0xffffffffu, hit);
@@ -609,19 +688,22 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
       const int b = 31 - __clz(mask);
       mask &= ~(1u << b);
       const float4 q = s_q[w][b];
+      const float2 q2 = ANISO ? s_q2[ANISO ? w : 0][b] : make_float2(0.f, 0.f);
       const float isg_raw = s_isig[w][b];
       // fill Gaussians (negative 1/sigma) need only the opacity and colour
       // gradients unless the caller asked for every per-Gaussian gradient
       const bool geo = full_grads || isg_raw > 0.f;
       const float isg = fabsf(isg_raw);
       float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      float vC = 0.f;   // dC of a tangent-aligned Gaussian
       bool contrib = false;
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
         if (base + b >= last[k]) continue;
         ++evals;
-        float dx, dy, d2, e;
-        const float a = gauss_alpha(fx, py0 + 4 * k + 0.5f, q, bp.alpha_max, dx, dy, d2, e);
+        float dx, dy, d2 = 0.f, e;
+        const float a = ANISO ? gauss_alpha_aniso(fx, py0 + 4 * k + 0.5f, q, q2, bp.alpha_max, dx, dy, e)
+                              : gauss_alpha(fx, py0 + 4 * k + 0.5f, q, bp.alpha_max, dx, dy, d2, e);
         if (a < bp.alpha_min) continue;
         contrib = true;
         T[k] = __fdividef(T[k], 1.f - a);   // transmittance in front of this Gaussian
@@ -641,10 +723,20 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
         if (__fmul_rn(q.w, e) < bp.alpha_max) {
           v[4] += e * da;
           if (geo) {
-            const float aa = da * a * isg * isg;   // dalpha/dmu = alpha (x - mu) / sigma^2
-            v[0] += aa * dx;
-            v[1] += aa * dy;
-            v[2] += aa * d2 * isg;                  // dalpha/dsigma = alpha d^2 / sigma^3
+            if (ANISO) {
+              // dalpha/dE = alpha; dE/dmu = -(2A dx + B2 dy, B2 dx + 2C dy), dE/d{A, B2, C} = {dx^2, dx dy, dy^2}
+              const float ga = da * a;
+              v[0] -= ga * (2.f * q.z * dx + q2.x * dy);
+              v[1] -= ga * (q2.x * dx + 2.f * q2.y * dy);
+              v[2] += ga * dx * dx;
+              v[3] += ga * dx * dy;
+              vC += ga * dy * dy;
+            } else {
+              const float aa = da * a * isg * isg;   // dalpha/dmu = alpha (x - mu) / sigma^2
+              v[0] += aa * dx;
+              v[1] += aa * dy;
+              v[2] += aa * d2 * isg;                  // dalpha/dsigma = alpha d^2 / sigma^3
+            }
           }
         }
       }
@@ -657,8 +749,13 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
           const float t2 = __shfl_down_sync(0xffffffffu, t, 8);
           const float t3 = __shfl_down_sync(0xffffffffu, t, 12);
           if ((lane & 15) == 0) {
-            float* d = dgauss + (long long)s_id[w][b] * 8 + (lane >> 2);
+            float* d = dgauss + (long long)s_id[w][b] * kRow + (lane >> 2);
             red_add_v4(d, t, t1, t2, t3);
+          }
+          if (ANISO) {
+            float tc = vC;
+            for (int o = 16; o > 0; o >>= 1) tc += __shfl_xor_sync(0xffffffffu, tc, o);
+            if (lane == 0 && tc != 0.f) atomicAdd(dgauss + (long long)s_id[w][b] * kRow + 8, tc);
           }
         } else {
           // only {do, dr, dg, db}: value k of the warp total sits in lane 8k
@@ -666,7 +763,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
           const float t1 = __shfl_down_sync(0xffffffffu, t, 8);
           const float t2 = __shfl_down_sync(0xffffffffu, t, 16);
           const float t3 = __shfl_down_sync(0xffffffffu, t, 24);
-          if (lane == 0) red_add_v4(dgauss + (long long)s_id[w][b] * 8 + 4, t, t1, t2, t3);
+          if (lane == 0) red_add_v4(dgauss + (long long)s_id[w][b] * kRow + 4, t, t1, t2, t3);
         }
       }
     }
@@ -676,15 +773,15 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
 }
 
 // (TILE, PPT) -> launch.  Valid: TILE 8 with PPT 1-2, TILE 16 and 32 with PPT 1-4.
-template <int C>
+template <int C, bool ANISO>
 static void launch_fwd(int tile, int ppt, int grid, cudaStream_t s, const int2* ranges, const uint32_t* gid,
-                       const float4* prep, const float2* reach, const int* gcurve, const float4* col,
-                       const BlendParams& bp, float* image, float* Tf, int* nl, DevState* st) {
+                       const float4* prep, const float2* prep2, const float2* reach, const int* gcurve,
+                       const float4* col, const BlendParams& bp, float* image, float* Tf, int* nl, DevState* st) {
 #define NS_FWD(TL, PP)                                                                                 \
   {                                                                                                      \
-    auto kern = &k_blend_fwd<TL, PP, C>;                                                                 \
+    auto kern = &k_blend_fwd<TL, PP, C, ANISO>;                                                          \
     NS_LAUNCH(NS_KERNEL_BLEND_FWD, kern, grid, (BlendGeom<TL, PP>::kThreads), 0, s, ranges, gid, prep,  \
-              reach, gcurve, col, bp, image, Tf, nl, st);                                               \
+              prep2, reach, gcurve, col, bp, image, Tf, nl, st);                                        \
   }
   if (tile == 8) { if (ppt == 1) NS_FWD(8, 1) else NS_FWD(8, 2) }
   else if (tile == 16) { if (ppt == 1) NS_FWD(16, 1) else if (ppt == 2) NS_FWD(16, 2) else NS_FWD(16, 4) }
@@ -692,21 +789,58 @@ static void launch_fwd(int tile, int ppt, int grid, cudaStream_t s, const int2* 
 #undef NS_FWD
 }
 
-template <int C>
+template <int C, bool ANISO>
 static void launch_bwd(int tile, int ppt, int grid, cudaStream_t s, const int2* ranges, const uint32_t* gid,
-                       const float4* prep, const float2* reach, const int* gcurve, const float4* col,
-                       const BlendParams& bp, const float* dimage, const float* Tf, const int* nl, float* dgauss,
-                       DevState* st, int full_grads) {
+                       const float4* prep, const float2* prep2, const float2* reach, const int* gcurve,
+                       const float4* col, const BlendParams& bp, const float* dimage, const float* Tf, const int* nl,
+                       float* dgauss, DevState* st, int full_grads) {
 #define NS_BWD(TL, PP)                                                                                 \
   {                                                                                                      \
-    auto kern = &k_blend_bwd<TL, PP, C>;                                                                 \
+    auto kern = &k_blend_bwd<TL, PP, C, ANISO>;                                                          \
     NS_LAUNCH(NS_KERNEL_BLEND_BWD, kern, grid, (BlendGeom<TL, PP>::kThreads), 0, s, ranges, gid, prep,  \
-              reach, gcurve, col, bp, dimage, Tf, nl, dgauss, st, full_grads);                          \
+              prep2, reach, gcurve, col, bp, dimage, Tf, nl, dgauss, st, full_grads);                   \
   }
   if (tile == 8) { if (ppt == 1) NS_BWD(8, 1) else NS_BWD(8, 2) }
   else if (tile == 16) { if (ppt == 1) NS_BWD(16, 1) else if (ppt == 2) NS_BWD(16, 2) else NS_BWD(16, 4) }
   else { if (ppt == 1) NS_BWD(32, 1) else if (ppt == 2) NS_BWD(32, 2) else NS_BWD(32, 4) }
 #undef NS_BWD
+}
+
+// Runtime (channels, tangent-aligned) -> template.
+struct BlendArgs {
+  const int2* ranges;
+  const uint32_t* gid;
+  const float4* prep;
+  const float2* prep2;
+  const float2* reach;
+  const int* gcurve;
+  const float4* col;
+  BlendParams bp;
+  float* Tf;
+  int* nl;
+  DevState* st;
+};
+
+static void dispatch_fwd(int C, bool aniso, int tile, int ppt, int grid, cudaStream_t s, const BlendArgs& a,
+                         float* image) {
+  if (C == 3) {
+    if (aniso) launch_fwd<3, true>(tile, ppt, grid, s, a.ranges, a.gid, a.prep, a.prep2, a.reach, a.gcurve, a.col, a.bp, image, a.Tf, a.nl, a.st);
+    else launch_fwd<3, false>(tile, ppt, grid, s, a.ranges, a.gid, a.prep, a.prep2, a.reach, a.gcurve, a.col, a.bp, image, a.Tf, a.nl, a.st);
+  } else {
+    if (aniso) launch_fwd<1, true>(tile, ppt, grid, s, a.ranges, a.gid, a.prep, a.prep2, a.reach, a.gcurve, a.col, a.bp, image, a.Tf, a.nl, a.st);
+    else launch_fwd<1, false>(tile, ppt, grid, s, a.ranges, a.gid, a.prep, a.prep2, a.reach, a.gcurve, a.col, a.bp, image, a.Tf, a.nl, a.st);
+  }
+}
+
+static void dispatch_bwd(int C, bool aniso, int tile, int ppt, int grid, cudaStream_t s, const BlendArgs& a,
+                         const float* dimage, float* dgauss, int full_grads) {
+  if (C == 3) {
+    if (aniso) launch_bwd<3, true>(tile, ppt, grid, s, a.ranges, a.gid, a.prep, a.prep2, a.reach, a.gcurve, a.col, a.bp, dimage, a.Tf, a.nl, dgauss, a.st, full_grads);
+    else launch_bwd<3, false>(tile, ppt, grid, s, a.ranges, a.gid, a.prep, a.prep2, a.reach, a.gcurve, a.col, a.bp, dimage, a.Tf, a.nl, dgauss, a.st, full_grads);
+  } else {
+    if (aniso) launch_bwd<1, true>(tile, ppt, grid, s, a.ranges, a.gid, a.prep, a.prep2, a.reach, a.gcurve, a.col, a.bp, dimage, a.Tf, a.nl, dgauss, a.st, full_grads);
+    else launch_bwd<1, false>(tile, ppt, grid, s, a.ranges, a.gid, a.prep, a.prep2, a.reach, a.gcurve, a.col, a.bp, dimage, a.Tf, a.nl, dgauss, a.st, full_grads);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -811,13 +945,18 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
   bp.n_curves = L.nc;
   bp.gcap = int(L.gcap);
   const int bin_blocks = int(L.bin_blocks);
+  const bool aniso = g->shape != nullptr;
+  const float4* shape = reinterpret_cast<const float4*>(g->shape);
   if (bin_blocks > 0) {
-    NS_LAUNCH(NS_KERNEL_BIN_COUNT, k_bin_count, bin_blocks, 256, 0, s, rec, g->curve, g->aux, g->count, bp, bsum, st,
-              at<float4>(ws, L.o_prep), at<float2>(ws, L.o_reach));
+    auto kc = aniso ? &k_bin_count<true> : &k_bin_count<false>;
+    NS_LAUNCH(NS_KERNEL_BIN_COUNT, kc, bin_blocks, 256, 0, s, rec, shape, g->curve, g->aux, g->count, bp, bsum, st,
+              at<float4>(ws, L.o_prep), at<float2>(ws, L.o_prep2), at<float2>(ws, L.o_reach));
   }
   NS_LAUNCH(NS_KERNEL_SCAN, k_scan_small, 1, 1024, 0, s, bsum, g->count, int(L.gcap), kBinItems, st, cap->pairs);
   if (bin_blocks > 0) {
-    NS_LAUNCH(NS_KERNEL_BIN_EMIT, k_bin_emit, bin_blocks, 256, 0, s, rec, g->curve, g->count, curve_scene, bp, bsum, k0, v0, cap->pairs);
+    auto ke = aniso ? &k_bin_emit<true> : &k_bin_emit<false>;
+    NS_LAUNCH(NS_KERNEL_BIN_EMIT, ke, bin_blocks, 256, 0, s, rec, shape, g->curve, g->count, curve_scene, bp, bsum,
+              k0, v0, cap->pairs);
   }
   const RasterPlan rpn = radix_plan(L.n_tiles);
   const int sort_blocks = int(L.sort_blocks);
@@ -835,15 +974,9 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
   }
   cudaMemsetAsync(ranges, 0, sizeof(int2) * (size_t)L.n_tiles, s);
   NS_LAUNCH(NS_KERNEL_RANGES, k_ranges, num_sms() * 4, 256, 0, s, kin, st, ranges);
-  const BlendParams blp = blend_params(L, rp);
-  const float4* col = reinterpret_cast<const float4*>(curves->color);
-  const int ppt = resolve_ppt(rp->tile, rp->ppt_fwd);
-  if (L.C == 3)
-    launch_fwd<3>(rp->tile, ppt, L.n_tiles, s, ranges, vin, at<float4>(ws, L.o_prep), at<float2>(ws, L.o_reach),
-                  g->curve, col, blp, image, Tf, nl, st);
-  else
-    launch_fwd<1>(rp->tile, ppt, L.n_tiles, s, ranges, vin, at<float4>(ws, L.o_prep), at<float2>(ws, L.o_reach),
-                  g->curve, col, blp, image, Tf, nl, st);
+  const BlendArgs ba{ranges, vin, at<float4>(ws, L.o_prep), at<float2>(ws, L.o_prep2), at<float2>(ws, L.o_reach),
+                     g->curve, reinterpret_cast<const float4*>(curves->color), blend_params(L, rp), Tf, nl, st};
+  dispatch_fwd(L.C, aniso, rp->tile, resolve_ppt(rp->tile, rp->ppt_fwd), L.n_tiles, s, ba, image);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_error(std::string("splat_forward: ") + cudaGetErrorString(e));
@@ -859,21 +992,13 @@ ns_status launch_blend_bwd(const Layout& L, const ns_curves* curves, const ns_ga
                            cudaStream_t s, int full_grads) {
   const RasterPlan rpn = radix_plan(L.n_tiles);
   const uint32_t* vsorted = (rpn.passes & 1) ? at<uint32_t>(ws, L.o_v1) : at<uint32_t>(ws, L.o_v0);
-  const int2* ranges = at<int2>(ws, L.o_ranges);
-  const float* Tf = at<float>(ws, L.o_T);
-  const int* nl = at<int>(ws, L.o_nlast);
-  const BlendParams blp = blend_params(L, rp);
-  const float4* col = reinterpret_cast<const float4*>(curves->color);
-  
   DevState* st = at<DevState>(ws, L.o_state);
   cudaMemsetAsync(&st->blend_bwd_evals, 0, sizeof(unsigned long long), s);
-  const int ppt = resolve_ppt(rp->tile, rp->ppt_bwd);
-  if (L.C == 3)
-    launch_bwd<3>(rp->tile, ppt, L.n_tiles, s, ranges, vsorted, at<float4>(ws, L.o_prep), at<float2>(ws, L.o_reach),
-                  g->curve, col, blp, dimage, Tf, nl, dgauss, st, full_grads);
-  else
-    launch_bwd<1>(rp->tile, ppt, L.n_tiles, s, ranges, vsorted, at<float4>(ws, L.o_prep), at<float2>(ws, L.o_reach),
-                  g->curve, col, blp, dimage, Tf, nl, dgauss, st, full_grads);
+  const BlendArgs ba{at<int2>(ws, L.o_ranges), vsorted, at<float4>(ws, L.o_prep), at<float2>(ws, L.o_prep2),
+                     at<float2>(ws, L.o_reach), g->curve, reinterpret_cast<const float4*>(curves->color),
+                     blend_params(L, rp), at<float>(ws, L.o_T), at<int>(ws, L.o_nlast), st};
+  dispatch_bwd(L.C, g->shape != nullptr, rp->tile, resolve_ppt(rp->tile, rp->ppt_bwd), L.n_tiles, s, ba, dimage,
+               dgauss, full_grads);
   return NS_OK;
 }
 bool raster_params_ok(const ns_raster_params* rp) { return check_raster(rp); }
@@ -896,27 +1021,19 @@ extern "C" ns_status ns_autotune_blend(const ns_curves* curves, const ns_gaussia
   DevState* st = at<DevState>(ws, L.o_state);
   const RasterPlan rpn = radix_plan(L.n_tiles);
   const uint32_t* vsorted = (rpn.passes & 1) ? at<uint32_t>(ws, L.o_v1) : at<uint32_t>(ws, L.o_v0);
-  const int2* ranges = at<int2>(ws, L.o_ranges);
-  float* Tf = at<float>(ws, L.o_T);
-  int* nl = at<int>(ws, L.o_nlast);
   float* dg = at<float>(ws, L.o_dgauss);
-  const float4* prep = at<float4>(ws, L.o_prep);
-  const float2* reach = at<float2>(ws, L.o_reach);
-  const BlendParams blp = blend_params(L, rp);
-  const float4* col = reinterpret_cast<const float4*>(curves->color);
+  const bool aniso = g->shape != nullptr;
+  const int row = aniso ? 12 : 8;
+  const BlendArgs ba{at<int2>(ws, L.o_ranges), vsorted, at<float4>(ws, L.o_prep), at<float2>(ws, L.o_prep2),
+                     at<float2>(ws, L.o_reach), g->curve, reinterpret_cast<const float4*>(curves->color),
+                     blend_params(L, rp), at<float>(ws, L.o_T), at<int>(ws, L.o_nlast), st};
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     set_error("ns_autotune_blend: cudaEventCreate failed");
     return NS_ERR_CUDA;
   }
-  auto fwd = [&](int ppt) {
-    if (L.C == 3) launch_fwd<3>(rp->tile, ppt, L.n_tiles, s, ranges, vsorted, prep, reach, g->curve, col, blp, image, Tf, nl, st);
-    else launch_fwd<1>(rp->tile, ppt, L.n_tiles, s, ranges, vsorted, prep, reach, g->curve, col, blp, image, Tf, nl, st);
-  };
-  auto bwd = [&](int ppt) {
-    if (L.C == 3) launch_bwd<3>(rp->tile, ppt, L.n_tiles, s, ranges, vsorted, prep, reach, g->curve, col, blp, dL_dimage, Tf, nl, dg, st, 0);
-    else launch_bwd<1>(rp->tile, ppt, L.n_tiles, s, ranges, vsorted, prep, reach, g->curve, col, blp, dL_dimage, Tf, nl, dg, st, 0);
-  };
+  auto fwd = [&](int ppt) { dispatch_fwd(L.C, aniso, rp->tile, ppt, L.n_tiles, s, ba, image); };
+  auto bwd = [&](int ppt) { dispatch_bwd(L.C, aniso, rp->tile, ppt, L.n_tiles, s, ba, dL_dimage, dg, 0); };
   auto time_best = [&](bool backward) {
     int best = 0;
     float best_ms = 3.4e38f;
@@ -924,7 +1041,7 @@ extern "C" ns_status ns_autotune_blend(const ns_curves* curves, const ns_gaussia
       if (!ppt_ok(rp->tile, ppt)) continue;
       float t = 3.4e38f;
       for (int r = 0; r < repeats + 1; ++r) {   // the first run warms the variant up
-        if (backward) cudaMemsetAsync(dg, 0, sizeof(float) * 8 * (size_t)L.gcap, s);
+        if (backward) cudaMemsetAsync(dg, 0, sizeof(float) * row * (size_t)L.gcap, s);
         cudaEventRecord(e0, s);
         if (backward) bwd(ppt); else fwd(ppt);
         cudaEventRecord(e1, s);

@@ -344,6 +344,64 @@ __device__ void emit_contour(const ns_curves& cv, const CurveRef& cr, const floa
   rec = make_float4(e.C[0], e.C[1], e.C[2] / sp.rho, o);
 }
 
+// Shape of a tangent-aligned contour Gaussian at sample l: {sigma_t, cos,
+// sin, 0} with (cos, sin) = C'_xy/|C'_xy| (Eq. 2) and sigma_t = |C'_xy| du / rho,
+// du = (b - a)/(M - 1) for open curves and (b - a)/M for closed ones (the
+// parameter step between samples).  Where C'_xy vanishes the Gaussian stays
+// isotropic: {sigma_n, 1, 0, 0}.  An isotropic contour set (contour_mode 0)
+// gets {sigma_n, 1, 0, 0} everywhere.
+template <int P>
+__device__ float4 contour_shape(const ns_curves& cv, const CurveRef& cr, const float* U, const CurvePlan& pl, int l,
+                                const ns_sample_params& sp) {
+  const float u = contour_u(pl, l, sp.kappa);
+  const int i = find_span(U, P, cr.n, u);
+  Eval<P> e;
+  eval_curve<P>(reinterpret_cast<const float4*>(cv.key), cr, U, i, u, e);
+  const float sn = e.C[2] / sp.rho;
+  if (sp.contour_mode != 1) return make_float4(sn, 1.f, 0.f, 0.f);
+  float dN[P + 1];
+  basis_deriv<P>(e.t, dN);
+  float dS0 = 0.f, dS1 = 0.f, dW = 0.f;
+#pragma unroll
+  for (int k = 0; k <= P; ++k) {
+    const float nw = dN[k] * e.cp[k].w;
+    dS0 = fmaf(nw, e.cp[k].x, dS0);
+    dS1 = fmaf(nw, e.cp[k].y, dS1);
+    dW += nw;
+  }
+  const float iw = 1.f / e.W;
+  const float vx = (dS0 - e.C[0] * dW) * iw, vy = (dS1 - e.C[1] * dW) * iw;
+  const float n = sqrtf(vx * vx + vy * vy);
+  if (!(n > 0.f)) return make_float4(sn, 1.f, 0.f, 0.f);
+  const float step = (pl.b - pl.a) / float(pl.kind == kOpen ? pl.M - 1 : pl.M);
+  return make_float4(n * step / sp.rho, vx / n, vy / n, 0.f);
+}
+
+__global__ void __launch_bounds__(256) k_emit_shape(ns_curves cv, ns_sample_params sp,
+                                                    const CurvePlan* __restrict__ plan,
+                                                    const float* __restrict__ knots,
+                                                    const DevState* __restrict__ st,
+                                                    const float4* __restrict__ rec, const int* __restrict__ gcurve,
+                                                    float4* shape) {
+  const int G = st->g_count;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+    const int c = gcurve[g];
+    if (c < 0 || c >= cv.n_curves) continue;
+    const CurvePlan pl = plan[c];
+    if (pl.kind == kFill || pl.kind == kNone) {
+      shape[g] = make_float4(rec[g].z, 1.f, 0.f, 0.f);
+      continue;
+    }
+    const int l = g - pl.g_off;
+    if (l < 0 || l >= pl.count) continue;
+    const CurveRef cr = curve_ref(cv, c);
+    const float* U = knots + cr.knot0;
+    float4 sh = make_float4(rec[g].z, 1.f, 0.f, 0.f);
+    NS_DISPATCH_P(cr.p, sh = contour_shape<P>(cv, cr, U, pl, l, sp));
+    shape[g] = sh;
+  }
+}
+
 // Nearest segment of one cluster.  Among equal distances the lowest segment
 // index wins, whatever order the clusters are visited in (the result of a
 // plain first-minimum loop over all segments).
@@ -554,6 +612,10 @@ extern "C" ns_status nurbs_sample(const ns_curves* curves, const ns_sample_param
     set_error("nurbs_sample: output arrays missing or smaller than the Gaussian capacity");
     return NS_ERR_INVALID_ARG;
   }
+  if (sp->contour_mode < 0 || sp->contour_mode > 1 || (sp->contour_mode == 1 && !out->shape)) {
+    set_error("nurbs_sample: contour_mode must be 0 or 1, and 1 needs the Gaussian set's shape array");
+    return NS_ERR_INVALID_ARG;
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   DevState* st = at<DevState>(ws, L.o_state);
   CurvePlan* plan = at<CurvePlan>(ws, L.o_plan);
@@ -576,6 +638,9 @@ extern "C" ns_status nurbs_sample(const ns_curves* curves, const ns_sample_param
   const int grid = num_sms() * 8;
   NS_LAUNCH(NS_KERNEL_EMIT, k_emit, grid, 256, 0, s, *curves, *sp, plan, order, knots, bpts, st, reinterpret_cast<float4*>(out->rec),
                               out->curve, out->aux, cap->gaussians, cap->boundary);
+  if (out->shape)
+    NS_LAUNCH(NS_KERNEL_OTHER, k_emit_shape, grid, 256, 0, s, *curves, *sp, plan, knots, st,
+              reinterpret_cast<const float4*>(out->rec), out->curve, reinterpret_cast<float4*>(out->shape));
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_error(std::string("nurbs_sample: ") + cudaGetErrorString(e));

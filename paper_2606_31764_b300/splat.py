@@ -30,6 +30,7 @@ def sample_params(d: dict) -> B.NsSampleParams:
     p.nl_mult = int(d["nl_mult"])
     p.fill_rule = int(d["fill_rule"])
     p.fill_cull = float(d.get("fill_cull", 0.0))
+    p.contour_mode = int(d.get("contour_mode", 0))
     return p
 
 
@@ -127,14 +128,16 @@ class Splatter:
         self.curve = torch.empty(G, dtype=torch.int32, device=self.device)
         self.aux = torch.empty(G, dtype=torch.int32, device=self.device)
         self.count = torch.zeros(1, dtype=torch.int32, device=self.device)
-        self.dgauss = torch.empty(G, 8, device=self.device)
+        self.aniso = int(self.sp.contour_mode) == 1
+        self.shape = torch.empty(G, 4, device=self.device) if self.aniso else None
+        self.dgauss = torch.empty(G, 12 if self.aniso else 8, device=self.device)
         cs = self.dev.struct_sizes()
         n = lib.ns_workspace_size(C.byref(cs), C.byref(self.cap), C.byref(self.rp))
         if n == 0:
             raise B.NsError("ns_workspace_size", B.NS_ERR_INVALID_ARG, lib.ns_last_error().decode())
         self.ws = torch.empty(n, dtype=torch.uint8, device=self.device)
         self.g = B.NsGaussians(int(self.cap.gaussians), _ptr(self.rec), _ptr(self.curve), _ptr(self.aux),
-                               _ptr(self.count))
+                               _ptr(self.count), _ptr(self.shape))
         B.call("ns_clear_status", _ptr(self.ws), _stream())
 
     @property

@@ -6,14 +6,17 @@ from paper_2606_31764_b300 import binding as B
 from paper_2606_31764_b300.splat import Splatter, scene_tensors
 
 
-def run_records(scene, rec, curve, capacity=None):
-    """splat_forward on a given FP32 Gaussian set.  Returns the splatter, the
-    image, the report and the device inputs."""
+def run_records(scene, rec, curve, capacity=None, shape=None):
+    """splat_forward on a given FP32 Gaussian set (with its tangent-aligned
+    shapes when the scene samples in contour_mode 1).  Returns the splatter,
+    the image, the report and the device inputs."""
     G = rec.shape[0]
     cap = capacity or (max(G, 1), max(64 * G, 1024), 16)
     sp = Splatter(scene, capacity=cap)
     sp.rec[:G] = torch.as_tensor(rec, device="cuda")
     sp.curve[:G] = torch.as_tensor(curve, device="cuda")
+    if shape is not None:
+        sp.shape[:G] = torch.as_tensor(shape, device="cuda")
     sp.aux[:G] = -1
     sp.count.fill_(G)
     k, t, c = scene_tensors(scene)
