@@ -73,7 +73,9 @@ __device__ __forceinline__ void curve_point_bwd_local(const float4* key, const C
 struct ChainParams {
   float rho, h, gamma;
   int kappa;
-  int freeze_w;   // rational weights frozen: no dL/dw is written
+  int freeze_w;         // rational weights frozen: no dL/dw is written
+  const int* tmap;      // task -> curve table of nurbs_sample
+  long long tcap;       // its entries
 };
 
 template <int P>
@@ -94,7 +96,7 @@ __global__ void __launch_bounds__(256) k_chain(ns_curves cv, ChainParams cp, con
   const int n_tasks = st->n_chunks;
   const int nc = cv.n_curves;
   for (int task = blockIdx.x; task < n_tasks; task += gridDim.x) {
-    const int c = curve_of_task(plan, order, nc, task, true);
+    const int c = task_curve(cp.tmap, cp.tcap, n_tasks, plan, order, nc, task, true);
     const CurvePlan pl = plan[c];
     const CurveRef cr = curve_ref(cv, c);
     const int l0 = (task - pl.chunk_off) * kChunk;
@@ -331,7 +333,7 @@ __global__ void __launch_bounds__(kContourThreads) k_chain_contour(
   const int n_tasks = st->n_ctasks;
   const int nc = cv.n_curves;
   for (int task = blockIdx.x; task < n_tasks; task += gridDim.x) {
-    const int c = curve_of_task(plan, order, nc, task, false);
+    const int c = task_curve(cp.tmap, cp.tcap, st->n_chunks, plan, order, nc, task, false);
     if (cv.degree[c] != P) continue;
     const CurvePlan pl = plan[c];
     const CurveRef cr = curve_ref(cv, c);
@@ -533,6 +535,8 @@ extern "C" ns_status splat_backward(const ns_curves* curves, const ns_gaussians*
       cp.gamma = sp->gamma;
       cp.kappa = sp->kappa;
       cp.freeze_w = (out->frozen & NS_FROZEN_WEIGHTS) != 0;
+      cp.tmap = at<const int>(ws, L.o_tasks);
+      cp.tcap = L.tcap;
       NS_LAUNCH(NS_KERNEL_CHAIN, k_chain, num_sms() * 8, 256, 0, s, *curves, cp, plan, order, knots, bpts, st,
                 reinterpret_cast<const float4*>(g->rec), g->aux, dg, cap->gaussians,
                 cap->boundary, out->dkey, dknots, dbpts, out->dcolor, row / 4);

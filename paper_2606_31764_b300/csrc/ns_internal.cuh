@@ -73,6 +73,8 @@ struct Layout {
          o_dgauss = 0, o_curve_scene = 0, o_order = 0, o_prep = 0, o_prep2 = 0, o_reach = 0, o_live = 0,
          total = 0;
   size_t sample_total = 0;   // bytes of the prefix nurbs_sample uses (independent of the raster settings)
+  size_t o_tasks = 0;        // task -> curve table (fill tasks first, then contour tasks)
+  int64_t tcap = 0;          // entries of that table
 };
 
 // Host helpers (ns_api.cu).
@@ -464,6 +466,18 @@ __device__ __forceinline__ float contour_t(const CurvePlan& pl, int l, int kappa
     return j <= 0 ? 0.f : (j >= pl.M - 1 ? 1.f : float(j) / float(pl.M - 1));
   }
   return float(l) / float(pl.M);
+}
+
+// Task -> curve from the table nurbs_sample writes (fill tasks first, then the
+// contour tasks); tasks beyond the table (only when the Gaussian capacity
+// overflowed) fall back to the search below.
+__device__ __forceinline__ int curve_of_task(const CurvePlan* __restrict__ plan, const int* __restrict__ order,
+                                             int nc, int task, bool fill);
+__device__ __forceinline__ int task_curve(const int* __restrict__ tmap, long long tcap, int n_fill,
+                                          const CurvePlan* __restrict__ plan, const int* __restrict__ order, int nc,
+                                          int task, bool fill) {
+  const long long t = fill ? task : (long long)n_fill + task;
+  return t < tcap ? tmap[t] : curve_of_task(plan, order, nc, task, fill);
 }
 
 // Task -> curve map.  Tasks are 256 Gaussians of one curve; fill tasks and

@@ -138,7 +138,7 @@ __device__ __forceinline__ float reach2(float sigma, float o, float log_amin) {
 template <bool ANISO>
 __global__ void __launch_bounds__(256) k_bin_count(const float4* __restrict__ rec, const float4* __restrict__ shape,
                                                    const int* __restrict__ gcurve,
-                                                   const int* __restrict__ gaux, const int* __restrict__ gcount,
+                                                   const int* __restrict__ cflags, const int* __restrict__ gcount,
                                                    BinParams bp, int* bsum, DevState* st, float4* prep,
                                                    float2* prep2, float2* reach) {
   __shared__ int s_warp[32];
@@ -156,10 +156,12 @@ __global__ void __launch_bounds__(256) k_bin_count(const float4* __restrict__ re
       const int nt = (cv >= 0 && cv < bp.n_curves) ? tile_rect_of<ANISO>(rec, shape, g, bp, x0, y0, nx) : 0;
       cnt += nt;
       if (nt) {   // only binned Gaussians are ever read by the blend kernels
-        // 1/sigma, negative for fill Gaussians (their centre and sigma get no
-        // gradient through the chain, so the adjoint may skip them)
+        // 1/sigma, negative for the Gaussians of filled curves (their centre and
+        // sigma get no gradient through the chain, so the adjoint may skip
+        // them).  The curve's flag decides: a fill point's aux can equal the
+        // contour marker -1 (~0: outside, nearest segment 0).
         const float isg = 1.f / r.z;
-        const float sgn_isg = gaux && gaux[g] != -1 ? -isg : isg;
+        const float sgn_isg = (cflags[cv] & NS_FILLED) ? -isg : isg;
         if constexpr (ANISO) {
           const float4 sh = shape[g];
           const float it = 1.f / (sh.x * sh.x), in = 1.f / (r.z * r.z);
@@ -949,7 +951,7 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
   const float4* shape = reinterpret_cast<const float4*>(g->shape);
   if (bin_blocks > 0) {
     auto kc = aniso ? &k_bin_count<true> : &k_bin_count<false>;
-    NS_LAUNCH(NS_KERNEL_BIN_COUNT, kc, bin_blocks, 256, 0, s, rec, shape, g->curve, g->aux, g->count, bp, bsum, st,
+    NS_LAUNCH(NS_KERNEL_BIN_COUNT, kc, bin_blocks, 256, 0, s, rec, shape, g->curve, curves->flags, g->count, bp, bsum, st,
               at<float4>(ws, L.o_prep), at<float2>(ws, L.o_prep2), at<float2>(ws, L.o_reach));
   }
   NS_LAUNCH(NS_KERNEL_SCAN, k_scan_small, 1, 1024, 0, s, bsum, g->count, int(L.gcap), kBinItems, st, cap->pairs);

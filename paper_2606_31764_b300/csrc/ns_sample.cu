@@ -334,6 +334,23 @@ __global__ void k_scan_gauss(int nc, CurvePlan* plan, const int* order, DevState
   }
 }
 
+// Task -> curve table: one warp per curve writes the index of each of its
+// tasks (fill tasks numbered first, contour tasks after them).
+__global__ void k_task_map(int nc, const CurvePlan* __restrict__ plan, const DevState* __restrict__ st, int* tmap,
+                           long long tcap) {
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= nc) return;
+  const CurvePlan pl = plan[c];
+  if (pl.kind == kNone) return;
+  const int ntask = (pl.count + kChunk - 1) / kChunk;
+  const long long base = pl.kind == kFill ? pl.chunk_off : (long long)st->n_chunks + pl.chunk_off;
+  for (int j = lane; j < ntask; j += 32) {
+    const long long t = base + j;
+    if (t < tcap) tmap[t] = c;
+  }
+}
+
 template <int P>
 __device__ void emit_contour(const ns_curves& cv, const CurveRef& cr, const float* U, const CurvePlan& pl, int l,
                              const ns_sample_params& sp, float o, float4& rec) {
@@ -442,7 +459,8 @@ __device__ __forceinline__ int cluster_crossings(const float4* seg, const float2
 __global__ void __launch_bounds__(256, 4) k_emit(ns_curves cv, ns_sample_params sp, const CurvePlan* __restrict__ plan,
                                               const int* __restrict__ order, const float* __restrict__ knots,
                                               const float2* __restrict__ bpts, const DevState* __restrict__ st,
-                                              float4* rec, int* gcurve, int* gaux, long long gcap, long long bcap) {
+                                              float4* rec, int* gcurve, int* gaux, long long gcap, long long bcap,
+                                              const int* __restrict__ tmap, long long tcap) {
   __shared__ float4 seg[kSegBatch];   // {b0.x, b0.y, e.x, e.y}
   __shared__ float2 segb[kSegBatch];  // {b1.y, 1/|e|^2 (0 for a zero-length segment)}
   __shared__ float4 cbox[kSegBatch / kCluster];  // {x0, x1, y0, y1} of each segment cluster
@@ -452,7 +470,7 @@ __global__ void __launch_bounds__(256, 4) k_emit(ns_curves cv, ns_sample_params 
   for (int t = blockIdx.x; t < n_tasks; t += gridDim.x) {
     const bool fill_task = t < n_fill;
     const int task = fill_task ? t : t - n_fill;
-    const int c = curve_of_task(plan, order, nc, task, fill_task);
+    const int c = task_curve(tmap, tcap, n_fill, plan, order, nc, task, fill_task);
     const CurvePlan pl = plan[c];
     const CurveRef cr = curve_ref(cv, c);
     const float* U = knots + cr.knot0;
@@ -635,9 +653,11 @@ extern "C" ns_status nurbs_sample(const ns_curves* curves, const ns_sample_param
   NS_LAUNCH(NS_KERNEL_SCAN, k_scan_boundary, 1, 1024, 0, s, nc, plan, st, cap->boundary);
   NS_LAUNCH(NS_KERNEL_BOUNDARY, k_boundary, nc, kPlanThreads, 0, s, *curves, *sp, plan, knots, bpts, cap->boundary);
   NS_LAUNCH(NS_KERNEL_SCAN, k_scan_gauss, 1, 1024, 0, s, nc, plan, order, st, cap->gaussians, out->count);
+  int* tmap = at<int>(ws, L.o_tasks);
+  NS_LAUNCH(NS_KERNEL_SCAN, k_task_map, (nc + 7) / 8, 256, 0, s, nc, plan, st, tmap, (long long)L.tcap);
   const int grid = num_sms() * 8;
   NS_LAUNCH(NS_KERNEL_EMIT, k_emit, grid, 256, 0, s, *curves, *sp, plan, order, knots, bpts, st, reinterpret_cast<float4*>(out->rec),
-                              out->curve, out->aux, cap->gaussians, cap->boundary);
+                              out->curve, out->aux, cap->gaussians, cap->boundary, tmap, (long long)L.tcap);
   if (out->shape)
     NS_LAUNCH(NS_KERNEL_OTHER, k_emit_shape, grid, 256, 0, s, *curves, *sp, plan, knots, st,
               reinterpret_cast<const float4*>(out->rec), out->curve, reinterpret_cast<float4*>(out->shape));
