@@ -303,7 +303,8 @@ def run_gpu(args, dist, rank, world):
     torch.cuda.synchronize()
 
     # K-step graph with per-kernel events armed in every step
-    prof = ["emit", "bin_emit", "radix_scatter", "blend_fwd", "blend_bwd", "chain", "chain_contour", "chain_boundary"]
+    prof = ["plan", "emit", "bin_count", "bin_emit", "radix_scatter", "ranges", "blend_fwd", "mse", "blend_bwd",
+            "chain", "chain_contour", "chain_boundary", "knot_grads"]
     ev = {k: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)] for k in prof}
     for k in prof:                      # torch creates the CUDA events on first record

@@ -103,9 +103,19 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(ns_curves cv, ns_sample_p
                                                        float* knots, int* order, DevState* st) {
   __shared__ float red[32];
   __shared__ int s_ok;
+  __shared__ float sU[kStageKnots];   // the intervals first, then the knot vector (stage_curve)
+  __shared__ float4 sK[kStageKeys];
+  float* s_tau = sU;
   const int c = blockIdx.x;
   const CurveRef cr = curve_ref(cv, c);
   float* U = knots + cr.knot0;
+  // the intervals go to shared memory first (all threads), so that the serial
+  // cumulative sum below reads them without a global-memory round trip each
+  const int t0 = cv.tau_offset[c];
+  const bool tau_staged = cr.ntau >= 0 && cr.ntau <= kStageKnots && t0 >= 0 && cv.tau_offset[c + 1] <= cv.n_taus;
+  if (tau_staged)
+    for (int q = threadIdx.x; q < cr.ntau; q += blockDim.x) s_tau[q] = cv.tau[t0 + q];
+  __syncthreads();
   if (threadIdx.x == 0) {
     int ok = cr.p >= 1 && cr.p <= kMaxP && cr.key0 >= 0 && cr.nk >= 0 && cv.tau_offset[c] >= 0 &&
              cr.ntau >= 0 && cv.key_offset[c + 1] <= cv.n_keys && cv.tau_offset[c + 1] <= cv.n_taus;
@@ -130,7 +140,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(ns_curves cv, ns_sample_p
     // knot vector (§3.1): open -> p zero intervals on both sides; closed ->
     // last p core intervals before, first p after; cumulative sum from 0.
     if (ok) {
-      const float* tau = cv.tau + cv.tau_offset[c];
+      const float* tau = tau_staged ? s_tau : cv.tau + cv.tau_offset[c];
       const int p = cr.p, nt = cr.ntau;
       const int n_int = nt + 2 * p;
       double acc = 0.0;
@@ -170,8 +180,6 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(ns_curves cv, ns_sample_p
   }
   const float a = U[cr.p], b = U[cr.n + 1];
   const int NL = sp.nl_mult * max(cv.width, cv.height);
-  __shared__ float sU[kStageKnots];
-  __shared__ float4 sK[kStageKeys];
   const Staged sg = stage_curve(cv, cr, U, sU, sK);
   float part = 0.f;
   NS_DISPATCH_P(cr.p, part = arc_length_part<P>(sg.key, sg.cr, sg.U, a, b, NL));
