@@ -159,17 +159,59 @@ __device__ __forceinline__ float span_speed(const SpanPoly<P>& sp, float u) {
   return sqrtf(dx * dx + dy * dy);
 }
 
-// Each thread sums a contiguous run of the N_L midpoint nodes (Eq. 3), building
-// the span's Taylor form whenever the run enters a new span.
+// Each thread sums a contiguous run of the N_L midpoint nodes (Eq. 3).  With at
+// most kSmemSpans spans the block first builds every span's Taylor form once
+// (one thread per span) in shared memory; otherwise each thread builds the form
+// whenever its run enters a new span.
+constexpr int kSmemSpans = 128;
+
 template <int P>
-__device__ float arc_length_part(const float4* key, const CurveRef& cr, const float* U, float a, float b, int NL) {
+__device__ float arc_length_part(const float4* key, const CurveRef& cr, const float* U, float a, float b, int NL,
+                                 float* s_poly) {
   const float du = (b - a) / float(NL);
   const int per = (NL + blockDim.x - 1) / blockDim.x;
   const int j0 = threadIdx.x * per, j1 = min(NL, j0 + per);
+  const int nspan = cr.n - P + 1;
+  constexpr int kPoly = 1 + 3 * (P + 1);   // {m, A[0..P][3]}
   float acc = 0.f;
+  SpanPoly<P> sp;
+  if (nspan <= kSmemSpans) {
+    for (int sidx = threadIdx.x; sidx < nspan; sidx += blockDim.x) {
+      const int i = P + sidx;
+      if (!(U[i] < U[i + 1])) continue;   // empty span: never the span of a node
+      span_poly<P>(key, cr, U, i, sp);
+      float* d = s_poly + sidx * kPoly;
+      d[0] = sp.m;
+#pragma unroll
+      for (int k = 0; k <= P; ++k) {
+        d[1 + 3 * k] = sp.A[k][0];
+        d[2 + 3 * k] = sp.A[k][1];
+        d[3 + 3 * k] = sp.A[k][2];
+      }
+    }
+    __syncthreads();
+    int span = -1;
+    float hi = 0.f;
+    for (int j = j0; j < j1; ++j) {
+      const float u = a + (float(j) + 0.5f) * du;
+      if (span < 0 || !(u < hi)) {
+        span = find_span(U, P, cr.n, u);
+        hi = span < cr.n ? U[span + 1] : 3.0e38f;
+        const float* d = s_poly + (span - P) * kPoly;
+        sp.m = d[0];
+#pragma unroll
+        for (int k = 0; k <= P; ++k) {
+          sp.A[k][0] = d[1 + 3 * k];
+          sp.A[k][1] = d[2 + 3 * k];
+          sp.A[k][2] = d[3 + 3 * k];
+        }
+      }
+      acc += span_speed<P>(sp, u);
+    }
+    return acc * du;
+  }
   int span = -1;
   float hi = 0.f;
-  SpanPoly<P> sp;
   for (int j = j0; j < j1; ++j) {
     const float u = a + (float(j) + 0.5f) * du;
     if (span < 0 || !(u < hi)) {
@@ -186,7 +228,7 @@ __device__ float arc_length_part(const float4* key, const CurveRef& cr, const fl
 }
 
 // One block per curve.
-__global__ void __launch_bounds__(kPlanThreads) k_plan(ns_curves cv, ns_sample_params sp, CurvePlan* plan,
+__global__ void __launch_bounds__(kPlanThreads, 7) k_plan(ns_curves cv, ns_sample_params sp, CurvePlan* plan,
                                                        float* knots, int* order, DevState* st) {
   __shared__ float red[32];
   __shared__ int s_ok;
@@ -269,7 +311,8 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(ns_curves cv, ns_sample_p
   const int NL = sp.nl_mult * max(cv.width, cv.height);
   const Staged sg = stage_curve(cv, cr, U, sU, sK);
   float part = 0.f;
-  NS_DISPATCH_P(cr.p, part = arc_length_part<P>(sg.key, sg.cr, sg.U, a, b, NL));
+  __shared__ float s_poly[kSmemSpans * (1 + 3 * (kMaxP + 1))];
+  NS_DISPATCH_P(cr.p, part = arc_length_part<P>(sg.key, sg.cr, sg.U, a, b, NL, s_poly));
   const float L = block_sum(part, red);
   if (threadIdx.x == 0) {
     pl.L = L;
