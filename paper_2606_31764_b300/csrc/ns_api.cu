@@ -98,8 +98,8 @@ bool make_layout(const ns_curves* c, const ns_capacity* cap, const ns_raster_par
   L->tiles_x = (c->width + rp->tile - 1) / rp->tile;
   L->tiles_y = (c->height + rp->tile - 1) / rp->tile;
   const long long nt = (long long)L->S * L->tiles_x * L->tiles_y;
-  if (nt >= (1LL << 31)) {
-    set_error("too many tiles");
+  if (nt >= (1LL << 31) || L->tiles_x > 32767 || L->tiles_y > 32767) {
+    set_error("too many tiles (at most 32767 per image side and 2^31 in all)");
     return false;
   }
   L->n_tiles = int(nt);

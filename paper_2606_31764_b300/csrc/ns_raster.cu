@@ -146,9 +146,11 @@ __global__ void __launch_bounds__(256) k_bin_count(const float4* __restrict__ re
   const long long base = (long long)blockIdx.x * kBinItems;
   if (base >= G) return;
   int cnt = 0, culled = 0;
+  // the block total is all that is kept, so consecutive threads take
+  // consecutive Gaussians (coalesced loads and stores)
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    const long long g = base + threadIdx.x * 8 + k;
+    const long long g = base + k * 256 + threadIdx.x;
     if (g < G) {
       const float4 r = rec[g];
       int x0, y0, nx;
@@ -238,32 +240,58 @@ __global__ void __launch_bounds__(256) k_bin_emit(const float4* __restrict__ rec
                                                   BinParams bp, const int* __restrict__ boff, uint32_t* keys,
                                                   uint32_t* vals, long long pcap) {
   __shared__ int s_warp[32];
+  __shared__ int s_off[kBinItems];    // tile count, then exclusive offset in Gaussian order
+  __shared__ int2 s_rect[kBinItems];  // {x0 | nx << 16, y0 | ny << 16}
   const int G = min(*gcount, bp.gcap);
   const long long base = (long long)blockIdx.x * kBinItems;
   if (base >= G) return;
-  int cnt[8], x0[8], y0[8], nx[8];
-  int tot = 0;
+  // 1. rectangles, consecutive threads on consecutive Gaussians (coalesced)
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    const long long g = base + threadIdx.x * 8 + k;
-    cnt[k] = 0;
+    const int gl = k * 256 + threadIdx.x;
+    const long long g = base + gl;
+    int c = 0, x0 = 0, y0 = 0, nx = 1;
     if (g < G) {
       const int cv = gcurve[g];
-      if (cv >= 0 && cv < bp.n_curves) cnt[k] = tile_rect_of<ANISO>(rec, shape, g, bp, x0[k], y0[k], nx[k]);
+      if (cv >= 0 && cv < bp.n_curves) c = tile_rect_of<ANISO>(rec, shape, g, bp, x0, y0, nx);
     }
+    s_off[gl] = c;
+    s_rect[gl] = make_int2(x0 | (nx << 16), y0 | ((c ? c / nx : 0) << 16));
+  }
+  __syncthreads();
+  // 2. exclusive offsets in Gaussian order (each thread 8 consecutive)
+  int cnt[8], tot = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    cnt[k] = s_off[threadIdx.x * 8 + k];
     tot += cnt[k];
   }
   int btot;
-  long long off = (long long)boff[blockIdx.x] + block_excl_scan_int(tot, s_warp, btot);
+  int run = block_excl_scan_int(tot, s_warp, btot);
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    if (!cnt[k]) continue;
-    const long long g = base + threadIdx.x * 8 + k;
+    s_off[threadIdx.x * 8 + k] = run;
+    run += cnt[k];
+  }
+  __syncthreads();
+  // 3. pairs, consecutive threads on consecutive Gaussians again
+  const long long boff0 = boff[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int gl = k * 256 + threadIdx.x;
+    const long long g = base + gl;
+    if (g >= G) continue;
+    const int2 rr = s_rect[gl];
+    const int nx = rr.x >> 16, ny = rr.y >> 16;
+    const int c = nx * ny;
+    if (!c) continue;
+    const int x0 = rr.x & 0xffff, y0 = rr.y & 0xffff;
     const int sbase = curve_scene[gcurve[g]] * bp.tiles_per_scene;
-    for (int j = 0; j < cnt[k]; ++j, ++off) {
+    long long off = boff0 + s_off[gl];
+    for (int j = 0; j < c; ++j, ++off) {
       if (off >= pcap) break;
-      const int tx = x0[k] + j % nx[k];
-      const int ty = y0[k] + j / nx[k];
+      const int tx = x0 + j % nx;
+      const int ty = y0 + j / nx;
       keys[off] = uint32_t(sbase + ty * bp.tiles_x + tx);
       vals[off] = uint32_t(g);
     }
