@@ -19,6 +19,8 @@
 //                   composited entry, transmittance recovered by division,
 //                   warp-reduced per-Gaussian gradients
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <float.h>
 
 #include "ns_internal.cuh"
@@ -390,6 +392,10 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const uint32_t* __restric
                                                        const DevState* st, int shift, int bits) {
   constexpr int kWarps = 8, kPerWarp = kSortItems / kWarps, kRounds = kPerWarp / 32;
   __shared__ uint32_t wcnt[kWarps][256];
+  __shared__ uint32_t dstart[256];        // first position of each digit in the block's sorted order
+  __shared__ uint32_t gbase[256];         // global position of each digit's first item of this block
+  __shared__ uint32_t s_key[kSortItems];  // the block's items in digit order (stable)
+  __shared__ uint32_t s_val[kSortItems];
   const int n = st->pair_count;
   const int nb = (n + kSortItems - 1) / kSortItems;
   if ((int)blockIdx.x >= nb) return;
@@ -397,7 +403,9 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const uint32_t* __restric
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int d = lane; d < nd; d += 32) wcnt[w][d] = 0;
   __syncwarp();
-  const long long base = (long long)blockIdx.x * kSortItems + (long long)w * kPerWarp;
+  const long long blk0 = (long long)blockIdx.x * kSortItems;
+  const int nblk = (int)min((long long)kSortItems, n - blk0);
+  const long long base = blk0 + (long long)w * kPerWarp;
   uint32_t key[kRounds], val[kRounds];
   uint32_t rank[kRounds];
 #pragma unroll
@@ -416,29 +424,56 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const uint32_t* __restric
     __syncwarp();
   }
   __syncthreads();
-  // exclusive prefix over warps per digit, plus the global base of (digit, block)
+  // per digit: offsets of the warps inside the block's digit run, the run's
+  // start in the block's sorted order, and its global position
   for (int d = threadIdx.x; d < nd; d += blockDim.x) {
-    uint32_t acc = hist[(long long)d * nb + blockIdx.x];
+    uint32_t acc = 0;
 #pragma unroll
     for (int ww = 0; ww < kWarps; ++ww) {
       const uint32_t c = wcnt[ww][d];
       wcnt[ww][d] = acc;
       acc += c;
     }
+    dstart[d] = acc;   // the digit's count for now
+    gbase[d] = hist[(long long)d * nb + blockIdx.x];
   }
   __syncthreads();
+  if (threadIdx.x < 32) {   // exclusive scan of the digit counts (nd <= 256)
+    uint32_t run = 0;
+    for (int c0 = 0; c0 < nd; c0 += 32) {
+      const int d = c0 + lane;
+      uint32_t v = d < nd ? dstart[d] : 0u;
+      uint32_t x = v;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (d < nd) dstart[d] = run + x - v;
+      run += __shfl_sync(0xffffffffu, x, 31);
+    }
+  }
+  __syncthreads();
+  // stable local placement in shared memory
 #pragma unroll
   for (int r = 0; r < kRounds; ++r) {
     const long long i = base + r * 32 + lane;
     if (i < n) {
       const uint32_t d = (key[r] >> shift) & (nd - 1);
-      const uint32_t pos = wcnt[w][d] + rank[r];
-      kout[pos] = key[r];
-      vout[pos] = val[r];
+      const uint32_t pos = dstart[d] + wcnt[w][d] + rank[r];
+      s_key[pos] = key[r];
+      s_val[pos] = val[r];
     }
   }
+  __syncthreads();
+  // contiguous runs per digit: consecutive threads write consecutive positions
+  for (int j = threadIdx.x; j < nblk; j += blockDim.x) {
+    const uint32_t k = s_key[j];
+    const uint32_t d = (k >> shift) & (nd - 1);
+    const uint32_t pos = gbase[d] + (uint32_t(j) - dstart[d]);
+    kout[pos] = k;
+    vout[pos] = s_val[j];
+  }
 }
-
 __global__ void k_ranges(const uint32_t* __restrict__ keys, const DevState* st, int2* ranges) {
   const int n = st->pair_count;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -1003,7 +1038,7 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
     std::swap(vin, vout);
   }
   cudaMemsetAsync(ranges, 0, sizeof(int2) * (size_t)L.n_tiles, s);
-  NS_LAUNCH(NS_KERNEL_RANGES, k_ranges, num_sms() * 4, 256, 0, s, kin, st, ranges);
+  NS_LAUNCH(NS_KERNEL_RANGES, k_ranges, num_sms() * 16, 256, 0, s, kin, st, ranges);
   const BlendArgs ba{ranges, vin, at<float4>(ws, L.o_prep), at<float2>(ws, L.o_prep2), at<float2>(ws, L.o_reach),
                      g->curve, reinterpret_cast<const float4*>(curves->color), blend_params(L, rp), Tf, nl, st};
   dispatch_fwd(L.C, aniso, rp->tile, resolve_ppt(rp->tile, rp->ppt_fwd), L.n_tiles, s, ba, image);
