@@ -127,6 +127,7 @@ bool make_layout(const ns_curves* c, const ns_capacity* cap, const ns_raster_par
   L->o_curve_scene = take(sizeof(int) * (size_t)L->nc);
   L->o_bpts = take(sizeof(float2) * (size_t)L->bcap);
   L->o_dbpts = take(sizeof(float2) * (size_t)L->bcap);
+  L->o_bcurve = take(sizeof(int) * (size_t)L->bcap);
   // each curve's tasks cover its Gaussians in chunks of kChunk: within the
   // Gaussian capacity there are at most gcap/kChunk + n_curves of them
   L->tcap = L->gcap / kChunk + L->nc + 1;

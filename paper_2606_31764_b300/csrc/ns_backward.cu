@@ -415,18 +415,15 @@ __device__ void chain_boundary_point(const ns_curves& cv, const CurveRef& cr, co
 
 template <bool KNOTS>
 __global__ void k_chain_boundary(ns_curves cv, const CurvePlan* __restrict__ plan, const float* __restrict__ knots,
-                                 const DevState* __restrict__ st, const float2* __restrict__ dbpts, int freeze_w,
-                                 float* dkey, float* dknots) {
+                                 const DevState* __restrict__ st, const float2* __restrict__ dbpts,
+                                 const int* __restrict__ bcurve, int freeze_w, float* dkey, float* dknots) {
   const int nb = st->b_count;
   const int nc = cv.n_curves;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nb; j += gridDim.x * blockDim.x) {
     const float2 db = dbpts[j];
     if (db.x == 0.f && db.y == 0.f) continue;
-    int lo = 0, hi = nc - 1;   // largest curve with b_off <= j (offsets increase with the curve index)
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (plan[mid].b_off <= j) lo = mid; else hi = mid - 1;
-    }
+    const int lo = bcurve[j];   // the curve that owns boundary point j
+    if (lo < 0 || lo >= nc) continue;
     const CurvePlan pl = plan[lo];
     if (pl.kind != kFill) continue;
     const CurveRef cr = curve_ref(cv, lo);
@@ -572,7 +569,7 @@ extern "C" ns_status splat_backward(const ns_curves* curves, const ns_gaussians*
       if (L.bcap > 0) {
         auto kb = knots_on ? &k_chain_boundary<true> : &k_chain_boundary<false>;
         NS_LAUNCH(NS_KERNEL_CHAIN_BOUNDARY, kb, num_sms() * 4, 256, 0, s, *curves, plan, knots, st, dbpts,
-                  cp.freeze_w, out->dkey, dknots);
+                  at<const int>(ws, L.o_bcurve), cp.freeze_w, out->dkey, dknots);
       }
       if (knots_on)
         NS_LAUNCH(NS_KERNEL_KNOT_GRADS, k_knot_grads, (L.nc + 3) / 4, 128, 0, s, *curves, plan, dknots, out->dtau);

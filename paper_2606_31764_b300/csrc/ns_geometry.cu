@@ -440,6 +440,7 @@ __global__ void __launch_bounds__(kGeoThreads) k_bbox_contour(ns_curves cv, cons
 __global__ void __launch_bounds__(kGeoThreads) k_bbox_boundary(ns_curves cv, const CurvePlan* __restrict__ plan,
                                                                const float* __restrict__ knots,
                                                                const float2* __restrict__ bpts,
+                                                               const int* __restrict__ bcurve,
                                                                const DevState* __restrict__ st, GeoParams gp,
                                                                float* loss, float* dkey, float* dknots) {
   const int nb = st->b_count;
@@ -454,11 +455,8 @@ __global__ void __launch_bounds__(kGeoThreads) k_bbox_boundary(ns_curves cv, con
     float gx, gy;
     sum += box_penalty(gp, b.x, b.y, &gx, &gy);
     if (!dkey || (gx == 0.f && gy == 0.f)) continue;
-    int lo = 0, hi = nc - 1;   // largest curve with b_off <= j
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (plan[mid].b_off <= j) lo = mid; else hi = mid - 1;
-    }
+    const int lo = bcurve[j];   // the curve that owns boundary point j
+    if (lo < 0 || lo >= nc) continue;
     const CurvePlan pl = plan[lo];
     const int jj = j - pl.b_off;
     if (pl.kind != kFill || jj >= pl.M) continue;
@@ -559,8 +557,8 @@ extern "C" ns_status ns_geometry_loss(const ns_curves* curves, const ns_gaussian
                                                   g->curve, g->count, gp, loss + 1, dkey, dknots);
       after_launch(-1, s);
       before_launch(-1, s);
-      k_bbox_boundary<<<grid, kGeoThreads, 0, s>>>(*curves, plan, knots, at<const float2>(ws, L.o_bpts), st, gp,
-                                                   loss + 1, dkey, dknots);
+      k_bbox_boundary<<<grid, kGeoThreads, 0, s>>>(*curves, plan, knots, at<const float2>(ws, L.o_bpts),
+                                                   at<const int>(ws, L.o_bcurve), st, gp, loss + 1, dkey, dknots);
       after_launch(NS_KERNEL_BBOX_LOSS, s);
     }
     if (knots_on) launch_knot_grads(*curves, plan, dknots, out->dtau, s);

@@ -389,7 +389,7 @@ __global__ void k_scan_boundary(int nc, CurvePlan* plan, DevState* st, long long
 
 template <int P>
 __device__ void boundary_points(const float4* key, const CurveRef& cr, const float* U, const CurvePlan& pl,
-                                float2* bpts, long long bcap, float4& box) {
+                                float2* bpts, int* bcurve, int c, long long bcap, float4& box) {
   float xmin = FLT_MAX, ymin = FLT_MAX, xmax = -FLT_MAX, ymax = -FLT_MAX;
   for (int j = threadIdx.x; j < pl.M; j += blockDim.x) {
     const float t = float(j) / float(pl.M);
@@ -398,7 +398,10 @@ __device__ void boundary_points(const float4* key, const CurveRef& cr, const flo
     Eval<P> e;
     eval_curve<P>(key, cr, U, i, u, e);
     const long long o = (long long)pl.b_off + j;
-    if (o < bcap) bpts[o] = make_float2(e.C[0], e.C[1]);
+    if (o < bcap) {
+      bpts[o] = make_float2(e.C[0], e.C[1]);
+      bcurve[o] = c;
+    }
     xmin = fminf(xmin, e.C[0]);
     xmax = fmaxf(xmax, e.C[0]);
     ymin = fminf(ymin, e.C[1]);
@@ -409,7 +412,8 @@ __device__ void boundary_points(const float4* key, const CurveRef& cr, const flo
 
 // One block per curve; filled curves only.
 __global__ void __launch_bounds__(kPlanThreads) k_boundary(ns_curves cv, ns_sample_params sp, CurvePlan* plan,
-                                                           const float* knots, float2* bpts, long long bcap) {
+                                                           const float* knots, float2* bpts, int* bcurve,
+                                                           long long bcap) {
   __shared__ float red[32];
   const int c = blockIdx.x;
   if (plan[c].kind != kFill) return;
@@ -420,7 +424,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_boundary(ns_curves cv, ns_samp
   __shared__ float4 sK[kStageKeys];
   const Staged sg = stage_curve(cv, cr, U, sU, sK);
   float4 box = make_float4(FLT_MAX, FLT_MAX, -FLT_MAX, -FLT_MAX);
-  NS_DISPATCH_P(cr.p, boundary_points<P>(sg.key, sg.cr, sg.U, pl, bpts, bcap, box));
+  NS_DISPATCH_P(cr.p, boundary_points<P>(sg.key, sg.cr, sg.U, pl, bpts, bcurve, c, bcap, box));
   const float xmin = block_reduce_minmax(box.x, red, false);
   const float ymin = block_reduce_minmax(box.y, red, false);
   const float xmax = block_reduce_minmax(box.z, red, true);
@@ -789,7 +793,8 @@ extern "C" ns_status nurbs_sample(const ns_curves* curves, const ns_sample_param
   }
   NS_LAUNCH(NS_KERNEL_PLAN, k_plan, nc, kPlanThreads, 0, s, *curves, *sp, plan, knots, order, st);
   NS_LAUNCH(NS_KERNEL_SCAN, k_scan_boundary, 1, 1024, 0, s, nc, plan, st, cap->boundary);
-  NS_LAUNCH(NS_KERNEL_BOUNDARY, k_boundary, nc, kPlanThreads, 0, s, *curves, *sp, plan, knots, bpts, cap->boundary);
+  NS_LAUNCH(NS_KERNEL_BOUNDARY, k_boundary, nc, kPlanThreads, 0, s, *curves, *sp, plan, knots, bpts,
+            at<int>(ws, L.o_bcurve), cap->boundary);
   NS_LAUNCH(NS_KERNEL_SCAN, k_scan_gauss, 1, 1024, 0, s, nc, plan, order, st, cap->gaussians, out->count);
   int* tmap = at<int>(ws, L.o_tasks);
   NS_LAUNCH(NS_KERNEL_SCAN, k_task_map, (nc + 7) / 8, 256, 0, s, nc, plan, st, tmap, (long long)L.tcap);
