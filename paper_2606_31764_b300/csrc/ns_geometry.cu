@@ -35,6 +35,17 @@ void launch_knot_grads(const ns_curves& cv, const CurvePlan* plan, const float* 
                        cudaStream_t s);
 
 constexpr int kMaxOrder = 4;       // highest derivative order of Eq. 11 supported
+constexpr int kGeoCurveThreads = 128;
+constexpr int kGeoMaxSpans = 256;  // curves with more spans take the per-node kernel
+constexpr int kGeoStage = 256;     // knots and key points staged per curve
+
+// Curves whose spans hold many nodes each (the Taylor forms' set-up is then
+// shared by many nodes) and fit the per-curve shared memory take
+// k_deriv_curve; the others the per-node kernel.
+__device__ __forceinline__ bool taylor_path(const CurveRef& cr, int p, int nodes) {
+  const int nspan = cr.n - p + 1;
+  return nspan <= kGeoMaxSpans && cr.ntau + 2 * p + 1 <= kGeoStage && cr.nk <= kGeoStage && nodes >= 16 * nspan;
+}
 constexpr int kDerivRun = 8;       // quadrature nodes per thread
 constexpr int kGeoThreads = 128;
 
@@ -46,7 +57,15 @@ struct GeoParams {
   int penalty;        // NS_PENALTY_RELU / NS_PENALTY_SOFTPLUS
   int kappa;
   int freeze_w;       // rational weights frozen: no dL/dw is written
+  int taylor;         // the per-curve Taylor kernels run (the batch's curves are short against the nodes)
 };
+
+// binomial coefficients up to k = kMaxP
+__device__ __forceinline__ float binom_pascal(int k, int q) {
+  const float row[kMaxP + 1][kMaxP + 1] = {{1, 0, 0, 0, 0, 0}, {1, 1, 0, 0, 0, 0}, {1, 2, 1, 0, 0, 0},
+                                           {1, 3, 3, 1, 0, 0}, {1, 4, 6, 4, 1, 0}, {1, 5, 10, 10, 5, 1}};
+  return row[k][q];
+}
 
 __device__ __forceinline__ float binom_small(int k, int q) {
   // binomial coefficients up to k = kMaxOrder
@@ -319,11 +338,329 @@ __global__ void __launch_bounds__(kGeoThreads) k_deriv_loss(ns_curves cv, const 
     const CurvePlan pl = plan[c];
     if (pl.kind == kNone) continue;
     const CurveRef cr = curve_ref(cv, c);
+    if (gp.taylor && taylor_path(cr, P, gp.nodes)) continue;   // done by k_deriv_curve
     const float* U = knots + cr.knot0;
     const int j0 = run * kDerivRun, j1 = min(j0 + kDerivRun, gp.nodes);
     sum += deriv_run<P, R>(cv, cr, U, pl, gp, j0, j1, dkey, dknots);
   }
   block_sum_add(sum, loss);
+}
+
+// ---------------------------------------------------------------------------
+// Derivative loss per curve from the spans' Taylor forms.  One block per curve
+// (with at most kGeoMaxSpans spans): the block builds every span's Taylor form
+// S_h(u) = sum_k A[k] (u - m)^k once; each node then needs only the first r + 1
+// derivatives of three polynomials (Horner with derivatives) and the Leibniz
+// quotient.  The reverse sweep of a node stops at the span's coefficients A[k]
+// and its centre m; the sums over the span's nodes then go once per span
+// through the reverse of the Taylor form's construction (derivative control
+// points and span triangle at m) into control points, weights and knots.
+// Reverse of span_poly: gA[k][e] = dL/dA[k][e] and gm = dL/dm (from the nodes).
+template <int P>
+__device__ void span_poly_bwd(const float4* key, const CurveRef& cr, const float* U, int i, const float* gA,
+                              float gm, float dcp[P + 1][3], float dkn[2 * P]) {
+  const float m = 0.5f * (U[i] + U[i + 1]);
+  Tri<P> t;
+  basis_fwd<P>(U, i, m, t);
+  float Q[P + 1][P + 1][3];
+#pragma unroll
+  for (int l = 0; l <= P; ++l) {
+    const float4 q = key[cr.key0 + cp_to_key(i - P + l, P, cr.closed, cr.nk)];
+    Q[0][l][0] = q.w * q.x;
+    Q[0][l][1] = q.w * q.y;
+    Q[0][l][2] = q.w;
+  }
+#pragma unroll
+  for (int k = 1; k <= P; ++k)
+#pragma unroll
+    for (int l = k; l <= P; ++l) {
+      const float c = float(P - k + 1) / (U[i + l - k + 1] - U[i - P + l]);
+#pragma unroll
+      for (int e = 0; e < 3; ++e) Q[k][l][e] = c * (Q[k - 1][l][e] - Q[k - 1][l - 1][e]);
+    }
+  float gTop[P + 1];
+  float gLow[P][P];
+#pragma unroll
+  for (int l = 0; l <= P; ++l) gTop[l] = 0.f;
+#pragma unroll
+  for (int d = 0; d < P; ++d)
+#pragma unroll
+    for (int l = 0; l < P; ++l) gLow[d][l] = 0.f;
+  float gQ[P + 1][3];
+#pragma unroll
+  for (int l = 0; l <= P; ++l) gQ[l][0] = gQ[l][1] = gQ[l][2] = 0.f;
+  float fact = 1.f;
+#pragma unroll
+  for (int k = 1; k <= P; ++k) fact *= float(k);   // P!
+#pragma unroll
+  for (int k = P; k >= 0; --k) {
+    // A[k] = (1/k!) sum_l lev(P-k)[l-k] Q[k][l]
+    const float inv = 1.f / fact;
+    const float g0 = gA[3 * k] * inv, g1 = gA[3 * k + 1] * inv, g2 = gA[3 * k + 2] * inv;
+#pragma unroll
+    for (int l = k; l <= P; ++l) {
+      const float n = (k == 0) ? t.N[l] : t.lev[P - k < P ? P - k : 0][l - k];
+      const float gn = g0 * Q[k][l][0] + g1 * Q[k][l][1] + g2 * Q[k][l][2];
+      if (k == 0) gTop[l] += gn; else gLow[P - k < P ? P - k : 0][l - k] += gn;
+      gQ[l][0] = fmaf(n, g0, gQ[l][0]);
+      gQ[l][1] = fmaf(n, g1, gQ[l][1]);
+      gQ[l][2] = fmaf(n, g2, gQ[l][2]);
+    }
+    if (k > 0) fact /= float(k);
+    if (k == 0) break;
+    // Q[k][l] = c (Q[k-1][l] - Q[k-1][l-1])
+    float gPrev[P + 1][3];
+#pragma unroll
+    for (int l = 0; l <= P; ++l) gPrev[l][0] = gPrev[l][1] = gPrev[l][2] = 0.f;
+#pragma unroll
+    for (int l = k; l <= P; ++l) {
+      const float D = U[i + l - k + 1] - U[i - P + l];
+      const float c = float(P - k + 1) / D;
+      float gc = 0.f;
+#pragma unroll
+      for (int e = 0; e < 3; ++e) {
+        gPrev[l][e] += c * gQ[l][e];
+        gPrev[l - 1][e] -= c * gQ[l][e];
+        gc += gQ[l][e] * (Q[k - 1][l][e] - Q[k - 1][l - 1][e]);
+      }
+      const float gD = -gc * c / D;
+      dkn[l - k + P] += gD;   // knot i+l-k+1
+      dkn[l - 1] -= gD;       // knot i-P+l
+    }
+#pragma unroll
+    for (int l = 0; l <= P; ++l) {
+      gQ[l][0] = gPrev[l][0];
+      gQ[l][1] = gPrev[l][1];
+      gQ[l][2] = gPrev[l][2];
+    }
+  }
+#pragma unroll
+  for (int l = 0; l <= P; ++l) {
+    const float4 q = key[cr.key0 + cp_to_key(i - P + l, P, cr.closed, cr.nk)];
+    dcp[l][0] += q.w * gQ[l][0];
+    dcp[l][1] += q.w * gQ[l][1];
+    dcp[l][2] += q.x * gQ[l][0] + q.y * gQ[l][1] + gQ[l][2];
+  }
+  float dm = 0.f;
+  basis_bwd_levels<P>(t, gTop, gLow, &dm, dkn);
+  dm += gm;
+  dkn[P - 1] += 0.5f * dm;   // m = (U_i + U_{i+1}) / 2
+  dkn[P] += 0.5f * dm;
+}
+
+template <int P, int R>
+__global__ void __launch_bounds__(kGeoCurveThreads) k_deriv_curve(ns_curves cv, const CurvePlan* __restrict__ plan,
+                                                                  const float* __restrict__ knots, GeoParams gp,
+                                                                  float* loss, float* dkey, float* dknots) {
+  constexpr int kPoly = 1 + 3 * (P + 1);   // {m, A[0..P][3]}
+  constexpr int KD = R + 1;                // derivatives needed: up to R + 1 (the last for d/du)
+  __shared__ float sU[kGeoStage];
+  __shared__ float4 sK[kGeoStage];
+  __shared__ float s_poly[kGeoMaxSpans * kPoly];
+  __shared__ float s_grad[kGeoMaxSpans * kPoly];   // {dL/dm, dL/dA[0..P][3]} per span
+  __shared__ float s_red[2];
+  const int c = blockIdx.x;
+  if (cv.degree[c] != P) return;
+  const CurvePlan pl = plan[c];
+  if (pl.kind == kNone) return;
+  CurveRef cr = curve_ref(cv, c);
+  const int nspan = cr.n - P + 1;
+  const int nkn = cr.ntau + 2 * P + 1;
+  if (!gp.taylor || !taylor_path(cr, P, gp.nodes)) return;   // left to k_deriv_loss
+  const float* Ug = knots + cr.knot0;
+  const float4* keyg = reinterpret_cast<const float4*>(cv.key) + cr.key0;
+  for (int q = threadIdx.x; q < nkn; q += blockDim.x) sU[q] = Ug[q];
+  for (int q = threadIdx.x; q < cr.nk; q += blockDim.x) sK[q] = keyg[q];
+  for (int q = threadIdx.x; q < nspan * kPoly; q += blockDim.x) s_grad[q] = 0.f;
+  if (threadIdx.x < 2) s_red[threadIdx.x] = 0.f;
+  __syncthreads();
+  const int key0 = cr.key0;
+  cr.key0 = 0;   // key points now in sK
+  for (int sidx = threadIdx.x; sidx < nspan; sidx += blockDim.x) {
+    const int i = P + sidx;
+    if (!(sU[i] < sU[i + 1])) continue;
+    SpanPoly<P> sp;
+    span_poly<P>(sK, cr, sU, i, sp);
+    float* d = s_poly + sidx * kPoly;
+    d[0] = sp.m;
+#pragma unroll
+    for (int k = 0; k <= P; ++k) {
+      d[1 + 3 * k] = sp.A[k][0];
+      d[2 + 3 * k] = sp.A[k][1];
+      d[3 + 3 * k] = sp.A[k][2];
+    }
+  }
+  __syncthreads();
+  const bool grads = dkey != nullptr;
+  const int N = gp.nodes;
+  const int per = (N + blockDim.x - 1) / blockDim.x;
+  const int j0 = threadIdx.x * per, j1 = min(N, j0 + per);
+  float sum = 0.f, dA = 0.f, dB = 0.f;
+  int span = -1;
+  float hi = 0.f, m = 0.f;
+  float A[P + 1][3], gAcc[P + 1][3], gmAcc = 0.f;
+  auto flush = [&]() {
+    if (!grads || span < 0) return;
+    float* g = s_grad + (span - P) * kPoly;
+    if (gmAcc != 0.f) atomicAdd(g, gmAcc);
+#pragma unroll
+    for (int k = 0; k <= P; ++k)
+#pragma unroll
+      for (int e = 0; e < 3; ++e)
+        if (gAcc[k][e] != 0.f) atomicAdd(g + 1 + 3 * k + e, gAcc[k][e]);
+  };
+  for (int j = j0; j < j1; ++j) {
+    const float tn = (float(j) + 0.5f) / float(N);
+    const float u = pl.a + tn * (pl.b - pl.a);
+    if (span < 0 || !(u < hi)) {
+      const int i = find_span(sU, P, cr.n, u);
+      if (i != span) {
+        flush();
+        span = i;
+        hi = i < cr.n ? sU[i + 1] : 3.0e38f;
+        const float* d = s_poly + (i - P) * kPoly;
+        m = d[0];
+#pragma unroll
+        for (int k = 0; k <= P; ++k) {
+          A[k][0] = d[1 + 3 * k];
+          A[k][1] = d[2 + 3 * k];
+          A[k][2] = d[3 + 3 * k];
+          gAcc[k][0] = gAcc[k][1] = gAcc[k][2] = 0.f;
+        }
+        gmAcc = 0.f;
+      }
+    }
+    const float t = u - m;
+    // Taylor coefficients at t: dd[e][q] = S_h^(q)(u) / q!, q = 0..KD
+    float dd[3][KD + 1];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+#pragma unroll
+      for (int q = 0; q <= KD; ++q) dd[e][q] = 0.f;
+      dd[e][0] = A[P][e];
+#pragma unroll
+      for (int k = P - 1; k >= 0; --k) {
+#pragma unroll
+        for (int q = KD; q >= 1; --q)
+          if (q <= P - k) dd[e][q] = fmaf(dd[e][q], t, dd[e][q - 1]);
+        dd[e][0] = fmaf(dd[e][0], t, A[k][e]);
+      }
+    }
+    // H[q] = S_h^(q), q = 0..R
+    float H[R + 1][3];
+    float qf = 1.f;
+#pragma unroll
+    for (int q = 0; q <= R; ++q) {
+      if (q > 0) qf *= float(q);
+#pragma unroll
+      for (int e = 0; e < 3; ++e) H[q][e] = qf * dd[e][q];
+    }
+    const float iw = 1.f / H[0][2];
+    float Cd[R + 1][2];
+#pragma unroll
+    for (int k = 0; k <= R; ++k) {
+      float ax = H[k][0], ay = H[k][1];
+#pragma unroll
+      for (int q = 1; q <= k; ++q) {
+        const float bq = binom_small(k, q) * H[q][2];
+        ax -= bq * Cd[k - q][0];
+        ay -= bq * Cd[k - q][1];
+      }
+      Cd[k][0] = ax * iw;
+      Cd[k][1] = ay * iw;
+    }
+    const float cx = Cd[R][0], cy = Cd[R][1];
+    sum += cx * cx + cy * cy;
+    if (!grads) continue;
+    // reverse of the Leibniz quotient -> gH[q][e]
+    float gC[R + 1][2], gH[R + 1][3];
+#pragma unroll
+    for (int k = 0; k <= R; ++k) {
+      gC[k][0] = gC[k][1] = 0.f;
+      gH[k][0] = gH[k][1] = gH[k][2] = 0.f;
+    }
+    gC[R][0] = 2.f * gp.scale_d * cx;
+    gC[R][1] = 2.f * gp.scale_d * cy;
+#pragma unroll
+    for (int k = R; k >= 0; --k) {
+      const float gx = gC[k][0] * iw, gy = gC[k][1] * iw;
+      gH[k][0] += gx;
+      gH[k][1] += gy;
+      gH[0][2] -= gx * Cd[k][0] + gy * Cd[k][1];
+#pragma unroll
+      for (int q = 1; q <= k; ++q) {
+        const float bq = binom_small(k, q);
+        gH[q][2] -= bq * (gx * Cd[k - q][0] + gy * Cd[k - q][1]);
+        gC[k - q][0] -= bq * H[q][2] * gx;
+        gC[k - q][1] -= bq * H[q][2] * gy;
+      }
+    }
+    // H[q] = q! sum_k A[k] binom(k, q) t^(k-q): adjoints of A and of t (= of u)
+    float gt = 0.f;
+    qf = 1.f;
+#pragma unroll
+    for (int q = 0; q <= R; ++q) {
+      if (q > 0) qf *= float(q);
+#pragma unroll
+      for (int e = 0; e < 3; ++e) {
+        const float g = gH[q][e] * qf;   // dL/d dd[e][q]
+        // dd[q] = sum_{k >= q} A[k] binom(k, q) t^(k-q); d dd[q]/dt = (q + 1) dd[q + 1]
+        gt += g * float(q + 1) * dd[e][q + 1];
+        float tp = 1.f;
+#pragma unroll
+        for (int k = q; k <= P; ++k) {
+          gAcc[k][e] = fmaf(g * binom_pascal(k, q), tp, gAcc[k][e]);
+          tp *= t;
+        }
+      }
+    }
+    gmAcc -= gt;                 // t = u - m
+    dA += gt * (1.f - tn);       // u = a + tn (b - a)
+    dB += gt * tn;
+  }
+  flush();
+  // loss
+  float v = sum * gp.scale_d;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v != 0.f) atomicAdd(&s_red[0], v);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_red[0] != 0.f) atomicAdd(loss, s_red[0]);
+  if (!grads) return;
+  // domain ends
+  if (dknots) {
+    float x = dA, y = dB;
+    for (int o = 16; o > 0; o >>= 1) {
+      x += __shfl_xor_sync(0xffffffffu, x, o);
+      y += __shfl_xor_sync(0xffffffffu, y, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      if (x != 0.f) atomicAdd(dknots + cr.knot0 + P, x);
+      if (y != 0.f) atomicAdd(dknots + cr.knot0 + cr.n + 1, y);
+    }
+  }
+  // each span: the reverse of its Taylor form's construction
+  for (int sidx = threadIdx.x; sidx < nspan; sidx += blockDim.x) {
+    const int i = P + sidx;
+    if (!(sU[i] < sU[i + 1])) continue;
+    const float* g = s_grad + sidx * kPoly;
+    float dcp[P + 1][3], dkn[2 * P];
+#pragma unroll
+    for (int l = 0; l <= P; ++l) dcp[l][0] = dcp[l][1] = dcp[l][2] = 0.f;
+#pragma unroll
+    for (int q = 0; q < 2 * P; ++q) dkn[q] = 0.f;
+    span_poly_bwd<P>(sK, cr, sU, i, g + 1, g[0], dcp, dkn);
+#pragma unroll
+    for (int l = 0; l <= P; ++l) {
+      float* dk = dkey + 4 * (long long)(key0 + cp_to_key(i - P + l, P, cr.closed, cr.nk));
+      if (dcp[l][0] != 0.f) atomicAdd(dk + 0, dcp[l][0]);
+      if (dcp[l][1] != 0.f) atomicAdd(dk + 1, dcp[l][1]);
+      if (!gp.freeze_w && dcp[l][2] != 0.f) atomicAdd(dk + 3, dcp[l][2]);
+    }
+    if (dknots)
+#pragma unroll
+      for (int q = 0; q < 2 * P; ++q)
+        if (dkn[q] != 0.f) atomicAdd(dknots + cr.knot0 + i - P + 1 + q, dkn[q]);
+  }
 }
 
 template <int R>
@@ -338,7 +675,23 @@ void launch_deriv_loss(const ns_curves& cv, const CurvePlan* plan, const float* 
     k<<<grid, kGeoThreads, 0, s>>>(cv, plan, knots, gp, loss, dkey, dknots);
     after_launch(last_id, s);
   };
-  run(k_deriv_loss<1, R>, NS_KERNEL_DERIV_LOSS, -1);
+  auto run_curve = [&](void (*k)(ns_curves, const CurvePlan*, const float*, GeoParams, float*, float*, float*),
+                       int first_id, int last_id) {
+    before_launch(first_id, s);
+    k<<<cv.n_curves, kGeoCurveThreads, 0, s>>>(cv, plan, knots, gp, loss, dkey, dknots);
+    after_launch(last_id, s);
+  };
+  // curves within the shared-memory limits with many nodes per span: one block
+  // each, per degree (launched only when the batch's mean key count makes that
+  // the common case); the others: per-node kernels
+  if (gp.taylor) {
+    run_curve(k_deriv_curve<1, R>, NS_KERNEL_DERIV_LOSS, -1);
+    run_curve(k_deriv_curve<2, R>, -1, -1);
+    run_curve(k_deriv_curve<3, R>, -1, -1);
+    run_curve(k_deriv_curve<4, R>, -1, -1);
+    run_curve(k_deriv_curve<5, R>, -1, -1);
+  }
+  run(k_deriv_loss<1, R>, gp.taylor ? -1 : NS_KERNEL_DERIV_LOSS, -1);
   run(k_deriv_loss<2, R>, -1, -1);
   run(k_deriv_loss<3, R>, -1, -1);
   run(k_deriv_loss<4, R>, -1, -1);
@@ -535,6 +888,9 @@ extern "C" ns_status ns_geometry_loss(const ns_curves* curves, const ns_gaussian
     gp.penalty = gpar->penalty;
     gp.kappa = sp->kappa;
     gp.freeze_w = out && (out->frozen & NS_FROZEN_WEIGHTS) != 0;
+    // the per-curve Taylor kernels pay off when spans hold many nodes: decided
+    // from the batch's mean key count
+    gp.taylor = (long long)gp.nodes >= 16LL * ((long long)L.nk / L.nc + 6);
     const CurvePlan* plan = at<const CurvePlan>(ws, L.o_plan);
     const float* knots = at<const float>(ws, L.o_knots);
     const DevState* st = at<const DevState>(ws, L.o_state);

@@ -393,6 +393,61 @@ __device__ __forceinline__ void curve_tangent_adjoint(const Eval<P>& e, const fl
   *du = d;
 }
 
+// Taylor (power-basis) form of the homogeneous curve S_h = sum_l N_l w_l (x_l,
+// y_l, 1) on one knot span, about the span's midpoint m:
+// S_h(u) = sum_k A[k] (u - m)^k with A[k] = S_h^(k)(m) / k!.  The k-th derivative
+// is the degree p-k B-spline of the derivative control points
+//   Q^(k)_l = (p-k+1)/(U_{l+p-k+1} - U_l) (Q^(k-1)_l - Q^(k-1)_{l-1})
+// over the level p-k functions of the span triangle at m.
+template <int P>
+struct SpanPoly {
+  float m;
+  float A[P + 1][3];
+};
+
+template <int P>
+__device__ __forceinline__ void span_poly(const float4* key, const CurveRef& cr, const float* U, int i,
+                                          SpanPoly<P>& sp) {
+  const float m = 0.5f * (U[i] + U[i + 1]);
+  Tri<P> t;
+  basis_fwd<P>(U, i, m, t);
+  float Q[P + 1][3];
+#pragma unroll
+  for (int l = 0; l <= P; ++l) {
+    const float4 q = key[cr.key0 + cp_to_key(i - P + l, P, cr.closed, cr.nk)];
+    Q[l][0] = q.w * q.x;
+    Q[l][1] = q.w * q.y;
+    Q[l][2] = q.w;
+  }
+  sp.m = m;
+  float fact = 1.f;
+#pragma unroll
+  for (int k = 0; k <= P; ++k) {
+    if (k > 0) {
+      fact *= float(k);
+      // Q^(k) from Q^(k-1), highest l first so that Q[l - 1] still holds level k-1
+#pragma unroll
+      for (int l = P; l >= k; --l) {
+        const float c = float(P - k + 1) / (U[i + l - k + 1] - U[i - P + l]);
+#pragma unroll
+        for (int e = 0; e < 3; ++e) Q[l][e] = c * (Q[l][e] - Q[l - 1][e]);
+      }
+    }
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll
+    for (int l = k; l <= P; ++l) {
+      const float n = (k == 0) ? t.N[l] : t.lev[P - k < P ? P - k : 0][l - k];
+      a0 = fmaf(n, Q[l][0], a0);
+      a1 = fmaf(n, Q[l][1], a1);
+      a2 = fmaf(n, Q[l][2], a2);
+    }
+    const float inv = 1.f / fact;
+    sp.A[k][0] = a0 * inv;
+    sp.A[k][1] = a1 * inv;
+    sp.A[k][2] = a2 * inv;
+  }
+}
+
 // Sum of 8 values over the 32 lanes of a warp in 9 shuffles: each exchange
 // step hands half of the remaining values to the partner lane.  On return the
 // lanes with (lane & 3) == 0 hold the totals, value (lane >> 2) in lane.

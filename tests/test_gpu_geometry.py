@@ -99,3 +99,20 @@ def test_canvas_box_default_and_values_only():
     sp.geometry(k, t, c, loss, g, penalty="softplus")
     assert _rel_ok(g[0].cpu().numpy(), 2 * out["dkey"].reshape(-1), 1e-5)
     assert _rel_ok(g[1].cpu().numpy(), 2 * out["dtau"], 1e-5)
+
+
+@pytest.mark.parametrize("order", [1, 2, 3, 4])
+@pytest.mark.parametrize("make", ["open", "closed", "filled"])
+def test_taylor_span_kernel_matches_oracle(make, order):
+    """Enough quadrature nodes per knot span that the per-curve kernel (span
+    Taylor forms, the reverse once per span) takes every curve."""
+    if make == "open":
+        sc = scenes.small_open(67, n_curves=4, size=40, p=(1, 2, 3, 4, 5))
+    else:
+        sc = scenes.small_closed(68, n_curves=3, size=44, filled=make == "filled", h=2.0, degrees=(2, 3, 4, 5))
+    plans = op.plan(sc)
+    box = (5.0, 4.0, sc.width - 6.0, sc.height - 5.0)
+    ref = og.geometry_loss_and_grads(sc, plans, order=order, nodes=700, lambda_deriv=0.7, lambda_bbox=1.5,
+                                     box=box, kind=og.SOFTPLUS)
+    out = _run(sc, order=order, nodes=700, lambda_deriv=0.7, lambda_bbox=1.5, box=box, penalty="softplus")
+    _check(sc, ref, out)
