@@ -49,7 +49,7 @@ TRAFFIC = dict(
     radix_scatter=dict(bytes=22024448, units=2706344, unit="pairs", tile=8,
                        src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="13a4539eac3391b8"),
     emit=dict(bytes=2332416, units=2027197, unit="gaussians", tile=None,
-              src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="a02525e983148a1a"),
+              src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="28770a9dd684096a"),
     chain=dict(bytes=88292864, units=2027197, unit="gaussians", tile=None,
                src="paper_2606_31764_b300/csrc/ns_backward.cu", sha="95583a4bcedf5a24"),
 )
