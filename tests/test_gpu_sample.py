@@ -80,11 +80,19 @@ def test_capacity_overflow_reports_needed_sizes():
     from paper_2606_31764_b300.splat import Splatter, scene_tensors
     s = Splatter(sc, capacity=(100, 1 << 16, 8))
     k, t, c = scene_tensors(sc)
-    s.forward(k, t, c)
+    img = s.forward(k, t, c)
     r = s.report()
     assert r.status == 2
     assert r.gaussians == sum(p.count for p in pl_o)
     assert r.boundary == sum(p.n_boundary for p in pl_o)
+    # the backward on the truncated set still runs within bounds: tasks beyond
+    # the task table fall back to the plan search, work beyond the capacities
+    # is dropped, and the status stays NS_ERR_CAPACITY
+    import torch as _t
+    dk, dt, dc = s.backward(k, t, c, _t.ones_like(img))
+    _t.cuda.synchronize()
+    assert s.report().status == 2
+    assert bool(_t.isfinite(dk).all()) and bool(_t.isfinite(dt).all()) and bool(_t.isfinite(dc).all())
 
 
 @pytest.mark.parametrize("seed,h", [(61, 1.0), (62, 2.0), (63, 1.0)])
