@@ -32,7 +32,20 @@ class CurvePlan:
     nx: int = 0
     ny: int = 0
     count: int = 0                # Gaussians this curve emits
-    margin: dict = field(default_factory=dict)  # distance of each count decision from a tie
+    # distance of each discrete decision from a tie: count decisions in counts
+    # (ceil() of Eq. 3-based sizes); for fills, once their Gaussians are
+    # sampled, "sign": the smallest distance (px) of a grid point from the
+    # boundary polyline.  At such a point the winding sign of Eq. S3 can flip
+    # under rounding of the polyline, which leaves sdf ~ 0 unchanged but
+    # reverses the sign of its gradient with respect to the polyline.
+    margin: dict = field(default_factory=dict)
+
+    def well_separated(self, count_bar: float = 1e-3, sign_bar_px: float = 1e-4) -> bool:
+        """True when every discrete decision is far from a tie: each count at
+        least count_bar from an integer, and every fill grid point at least
+        sign_bar_px from the polyline (about ten times the rounding of a
+        float32 boundary point at these canvas sizes)."""
+        return all(v > (sign_bar_px if k == "sign" else count_bar) for k, v in self.margin.items())
 
 
 def curve_inputs(scene, c, key_t, tau_t):
@@ -186,6 +199,7 @@ def curve_gaussians(scene, c, key_t, tau_t, color_t, pl: CurvePlan):
                                 indexing="ij")
         q = torch.stack([pl.x0 + (ix.reshape(-1) + 0.5) * h, pl.y0 + (iy.reshape(-1) + 0.5) * h], 1)
         d, arg = unsigned_distance(q, poly)
+        pl.margin["sign"] = float(d.detach().min())
         sgn = inside_sign(winding_number(q, poly), int(sp["fill_rule"]))
         sdf = sgn * d
         oj = o * sigmoid(sp["gamma"] / h * sdf)

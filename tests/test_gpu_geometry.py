@@ -63,7 +63,7 @@ def _check(sc, ref, out):
 def test_geometry_matches_oracle(name, make, penalty):
     sc = make()
     plans = op.plan(sc)
-    assert all(m > 1e-3 for p in plans for m in p.margin.values())
+    assert all(p.well_separated() for p in plans)
     box = (6.0, 5.0, sc.width - 7.0, sc.height - 6.0)
     kind = og.RELU if penalty == "relu" else og.SOFTPLUS
     ref = og.geometry_loss_and_grads(sc, plans, order=3, lambda_deriv=0.5, lambda_bbox=2.0, box=box, kind=kind)

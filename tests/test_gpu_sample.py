@@ -27,7 +27,7 @@ CASES = [
 
 
 def _no_ties(pl):
-    return all(m > 1e-3 for p in pl for m in p.margin.values())
+    return all(p.well_separated() for p in pl)
 
 
 @pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])

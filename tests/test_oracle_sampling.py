@@ -147,3 +147,31 @@ def test_layers_painter_order():
         s = sc.curve_scene()[cv]
         lay = g["layer"][g["curve"] == cv]
         assert bool((lay == sc.scene_curve_offset[s + 1] - 1 - cv).all())
+
+
+def test_sign_margin_flags_a_grid_point_on_the_polyline():
+    """The fill plan's "sign" margin is the smallest distance of a grid point
+    from the boundary polyline (Eq. S1): it must equal a brute-force minimum
+    over every grid point and segment, and it flags a scene whose grid point
+    lies within rounding of the polyline (there the winding sign of Eq. S3,
+    and with it the sign of the sdf gradient, is not decided by the data)."""
+    from oracle import pipeline as op
+    sc = scenes.small_closed(311, n_curves=3, size=48, filled=True, h=2.0)
+    k, t, c = op.leaves(sc, False)
+    with torch.no_grad():
+        g = sm.sample_scene(sc, k, t, c)
+    pl = g["plans"][0]
+    p, fl, cp, U = sm.curve_inputs(sc, 0, k, t)
+    a, b = nb.domain(U, p)
+    poly = nb.curve_point(cp, U, p, sm.boundary_parameters(a, b, pl.n_boundary))[:, :2].detach().numpy()
+    best = np.inf
+    for iy in range(pl.ny):
+        for ix in range(pl.nx):
+            q = np.array([pl.x0 + (ix + 0.5) * 2.0, pl.y0 + (iy + 0.5) * 2.0])
+            for i in range(poly.shape[0]):
+                b0, b1 = poly[i], poly[(i + 1) % poly.shape[0]]
+                e = b1 - b0
+                tt = min(max(np.dot(q - b0, e) / np.dot(e, e), 0.0), 1.0)
+                best = min(best, np.linalg.norm(q - b0 - tt * e))
+    assert abs(pl.margin["sign"] - best) <= 1e-12
+    assert pl.margin["sign"] < 1e-4
