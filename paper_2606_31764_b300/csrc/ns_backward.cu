@@ -137,9 +137,15 @@ __global__ void __launch_bounds__(256) k_chain(ns_curves cv, ChainParams cp, con
       const float dx = rx - t * ex, dy = ry - t * ey;
       const float d = sqrtf(dx * dx + dy * dy);
       const float sdf = inside ? d : -d;
-      const float sig = 1.f / (1.f + __expf(-(cp.gamma / cp.h * sdf)));
+      // sigmoid and its slope from E = exp(-|z|): s (1 - s) = E / (1 + E)^2 has no
+      // cancellation inside the shape, where s rounds towards 1 and 1 - s in
+      // float32 would keep only a few significant bits
+      const float z = cp.gamma / cp.h * sdf;
+      const float E = __expf(-fabsf(z));
+      const float inv = 1.f / (1.f + E);
+      const float sig = z >= 0.f ? inv : E * inv;
       dO = sig * gop;
-      const float dsdf = gop * o * sig * (1.f - sig) * (cp.gamma / cp.h);
+      const float dsdf = gop * o * (E * inv * inv) * (cp.gamma / cp.h);
       const float dd = inside ? dsdf : -dsdf;
       if (d > 0.f && dd != 0.f) {
         // d = |q - b0 - t e|, t at its optimum: dd/db0 = -(1-t) n, dd/db1 = -t n
