@@ -70,6 +70,12 @@ FLOP_SEGMENT = 20        # one (grid point, boundary segment) SDF test: distance
 FLOP_EVAL = 10           # one alpha evaluation (Eq. 9): dx, dy, d^2, scale, exp arg, *o, cap, skip test
 FLOP_CONTRIB_FWD = 10    # composite one pair (Eq. 8), 3 channels
 FLOP_CONTRIB_BWD = 33    # adjoint of one composited pair, 3 channels
+# Algorithmic cost of one visited (pixel, list entry) pair of Eq. 8-9's loop, FP32
+# operations only (the exponential and the reciprocal run on the MUFU pipe):
+# forward alpha 8 + compositing 5; backward alpha 8 + division, colour and
+# alpha adjoints and the mu, sigma, opacity terms 22.
+FLOP_VISIT_FWD = 13
+FLOP_VISIT_BWD = 30
 
 
 def parse():
@@ -354,13 +360,13 @@ def run_gpu(args, dist, rank, world):
     fp32_peak = 2.0 * 128 * sms * clk / 1e12        # TFLOP/s, FMA = 2 FLOP
     work = dict(
         emit=("alu", costs["segment_tests"] * FLOP_SEGMENT / 1e12, "TFLOP/s", fp32_peak),
-        blend_fwd=("alu", (rep.blend_evals * FLOP_EVAL + rep.blend_contribs * FLOP_CONTRIB_FWD) / 1e12, "TFLOP/s",
-                   fp32_peak),
-        blend_bwd=("alu", (rep.blend_bwd_evals * FLOP_EVAL + rep.blend_contribs * FLOP_CONTRIB_BWD) / 1e12,
-                   "TFLOP/s", fp32_peak),
+        blend_fwd=("alu", rep.blend_visits * FLOP_VISIT_FWD / 1e12, "TFLOP/s", fp32_peak),
+        blend_bwd=("alu", rep.blend_bwd_visits * FLOP_VISIT_BWD / 1e12, "TFLOP/s", fp32_peak),
         radix_scatter=("hbm", rep.pairs * 16 / 1e9, "GB/s", peaks["hbm_gbs"]),
         bin_emit=("hbm", (G * 16 + G * 4 + rep.pairs * 8) / 1e9, "GB/s", peaks["hbm_gbs"]),
     )
+    performed = dict(blend_fwd=(rep.blend_evals * FLOP_EVAL + rep.blend_contribs * FLOP_CONTRIB_FWD) / 1e12,
+                     blend_bwd=(rep.blend_bwd_evals * FLOP_EVAL + rep.blend_contribs * FLOP_CONTRIB_BWD) / 1e12)
     dom = max(per_kernel, key=per_kernel.get)
     kernels = {}
     for k, ms in per_kernel.items():
@@ -369,6 +375,9 @@ def run_gpu(args, dist, rank, world):
             bound, amount, unit, peak = work[k]
             ach = amount / (ms / 1e3)
             d.update(bound=bound, achieved=round(ach, 3), unit=unit, frac=round(ach / peak, 4))
+        if k in performed:
+            # the FLOPs the kernel itself executed (its culling skips most pairs)
+            d["performed_frac"] = round(performed[k] / (ms / 1e3) / fp32_peak, 4)
         kernels[k] = d
     units_now = dict(pairs=int(rep.pairs), gaussians=G)
     tile_now = int(step.sp.rp.tile)
@@ -382,6 +391,10 @@ def run_gpu(args, dist, rank, world):
                     frac=round(ach / peak, 4), traffic=traffic_per_launch(dom, units_now, tile_now),
                     peak_source=("FP32 lanes x SMs x max SM clock" if bound == "alu"
                                  else f"{peaks['source']} HBM copy bandwidth"))
+        if dom in performed:
+            roof["work"] = ("algorithmic: visited (pixel, list entry) pairs of Eq. 8-9 with early termination x "
+                            f"{FLOP_VISIT_FWD if dom == 'blend_fwd' else FLOP_VISIT_BWD} FP32 FLOP")
+            roof["performed_frac"] = kernels[dom]["performed_frac"]
 
     # end to end through the public API with host buffers
     e2e = run_e2e(torch, step, g1, args)
@@ -401,7 +414,8 @@ def run_gpu(args, dist, rank, world):
                gpu_launches=launches_per_step * args.steps, launches_per_step=launches_per_step,
                autotune=tuning,
                clocks=ck, roofline=roof, kernels=kernels, e2e=e2e,
-               blend=dict(evals_fwd=int(rep.blend_evals), evals_bwd=int(rep.blend_bwd_evals),
+               blend=dict(visits_fwd=int(rep.blend_visits), visits_bwd=int(rep.blend_bwd_visits),
+                          evals_fwd=int(rep.blend_evals), evals_bwd=int(rep.blend_bwd_evals),
                           composited=int(rep.blend_contribs)),
                sample=costs)
     out["geometry"] = run_geometry(torch, step, args)

@@ -98,6 +98,13 @@ typedef struct {
                        across; the Gaussian set then needs `shape` */
 } ns_sample_params;
 
+/* Blend decomposition flag for ns_raster_params.ppt_fwd / ppt_bwd: with it,
+ * each warp's 8-column sub-block is split into four groups of eight lanes, two
+ * pixel columns each, and every group walks only the Gaussians that can reach
+ * its own pixels (pixels per thread 1 or 2).  Pays off for Gaussians much
+ * smaller than the sub-block, such as fill Gaussians at grid step 1 px. */
+#define NS_BLEND_LANE_GROUPS 16
+
 /* Rasterizer settings (§3.4). */
 typedef struct {
   int32_t tile;     /* tile edge in pixels: 8, 16 or 32 */
@@ -106,7 +113,8 @@ typedef struct {
   float alpha_max;  /* alpha is capped at alpha_max (keeps 1 - alpha > 0) */
   float t_min;      /* compositing stops before transmittance would drop below t_min */
   float bg[3];      /* background colour behind the residual transmittance (§3.4) */
-  int32_t ppt_fwd;  /* pixels per thread of the forward blend: 1, 2, 4 (4 needs tile >= 16), 0 = default */
+  int32_t ppt_fwd;  /* decomposition of the forward blend: pixels per thread 1, 2 or 4 (4 needs
+                       tile >= 16), or 1 or 2 plus NS_BLEND_LANE_GROUPS; 0 = default */
   int32_t ppt_bwd;  /* the same for the backward blend; neither changes any result */
 } ns_raster_params;
 
@@ -166,6 +174,11 @@ typedef struct {
   int64_t blend_evals;   /* (pixel, Gaussian) alpha evaluations of the last splat_forward */
   int64_t blend_bwd_evals; /* the same for the last splat_backward */
   int64_t blend_contribs;  /* (pixel, Gaussian) pairs composited by the last splat_forward */
+  int64_t blend_visits;    /* (pixel, list entry) pairs the last splat_forward walked: per pixel, its
+                              tile list up to and including the entry that ended it (Eq. 8-9's loop
+                              with early termination), whether or not the entry was evaluated */
+  int64_t blend_bwd_visits; /* the same for the last splat_backward: per pixel, the entries in front
+                               of its last composited one, inclusive */
 } ns_report;
 
 /* Kernel ids for ns_profile_next_launch. */
@@ -413,8 +426,9 @@ ns_status ns_workspace_copy(void* workspace, const ns_curves* curves, const ns_c
  * Chooses the blend decomposition for this batch by timing: every valid
  * pixels-per-thread setting of the forward and backward blend kernels is run
  * `repeats` times on the workspace of a completed splat_forward (and, if
- * dL_dimage is non-NULL, the backward with that upstream gradient) and the
- * fastest is written to rp->ppt_fwd / rp->ppt_bwd.  The choice changes no
+ * dL_dimage is non-NULL, the backward with that upstream gradient), with and
+ * without NS_BLEND_LANE_GROUPS, and the fastest is written to rp->ppt_fwd /
+ * rp->ppt_bwd.  The choice changes no
  * result: every setting composites each pixel over the same list in the same
  * order.  `image` is rewritten with identical values.  Synchronises the
  * stream; call it before capturing a graph.  The tile size is fixed by the

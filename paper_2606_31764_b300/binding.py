@@ -65,7 +65,8 @@ NS_FROZEN_WEIGHTS, NS_FROZEN_KNOTS = 1, 2
 class NsReport(C.Structure):
     _fields_ = [("status", C.c_int32), ("bad_curve", C.c_int32), ("gaussians", C.c_int64), ("pairs", C.c_int64),
                 ("boundary", C.c_int64), ("fill_culled", C.c_int64), ("blend_evals", C.c_int64),
-                ("blend_bwd_evals", C.c_int64), ("blend_contribs", C.c_int64)]
+                ("blend_bwd_evals", C.c_int64), ("blend_contribs", C.c_int64), ("blend_visits", C.c_int64),
+                ("blend_bwd_visits", C.c_int64)]
 
 
 # name -> (restype, argtypes); the declarations of include/nurbs_splat.h
@@ -108,6 +109,9 @@ SIGNATURES = {
     "ns_launch_count": (C.c_uint64, []),
     "ns_last_error": (C.c_char_p, []),
 }
+
+# ns_raster_params.ppt_fwd / ppt_bwd flag: lane-group blend decomposition (nurbs_splat.h)
+BLEND_LANE_GROUPS = 16
 
 KERNELS = dict(plan=1, boundary=2, emit=3, bin_count=4, bin_emit=5, radix_hist=6, radix_scatter=7, ranges=8,
                blend_fwd=9, blend_bwd=10, chain=11, chain_boundary=12, knot_grads=13, mse=14, adam=15, scan=16,

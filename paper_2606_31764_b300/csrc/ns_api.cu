@@ -161,6 +161,7 @@ __global__ void k_reset_state(DevState* st) {
   st->g_total = st->b_total = st->pair_total = st->culled = 0;
   st->g_count = st->pair_count = st->b_count = 0;
   st->blend_evals = st->blend_bwd_evals = st->blend_contribs = 0;
+  st->blend_visits = st->blend_bwd_visits = 0;
 }
 
 void launch_reset_state(DevState* st, cudaStream_t s) { NS_LAUNCH(NS_KERNEL_OTHER, k_reset_state, 1, 1, 0, s, st); }
@@ -275,6 +276,8 @@ ns_status ns_poll_status(void* ws, ns_report* r, void* stream) {
   r->blend_evals = (int64_t)st.blend_evals;
   r->blend_bwd_evals = (int64_t)st.blend_bwd_evals;
   r->blend_contribs = (int64_t)st.blend_contribs;
+  r->blend_visits = (int64_t)st.blend_visits;
+  r->blend_bwd_visits = (int64_t)st.blend_bwd_visits;
   return NS_OK;
 }
 

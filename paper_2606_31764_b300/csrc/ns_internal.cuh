@@ -45,6 +45,8 @@ struct DevState {
   unsigned long long blend_evals;      // alpha evaluations of the last forward blend
   unsigned long long blend_bwd_evals;  // alpha evaluations of the last backward blend
   unsigned long long blend_contribs;   // composited (pixel, Gaussian) pairs of the last forward blend
+  unsigned long long blend_visits;     // (pixel, list entry) pairs walked by the last forward blend
+  unsigned long long blend_bwd_visits; // the same for the last backward blend
 };
 
 // One curve's sampling plan (written by the planning kernels).

@@ -12,12 +12,17 @@
 //                   only: pairs enter in (layer, sample) order, so a stable sort
 //                   by tile yields the full (tile, layer, sample) order
 //   k_ranges        [start, end) of every tile's run
-//   k_blend_fwd     one 16x16 tile per block: the tile's list staged in shared
-//                   memory 256 records at a time, each thread composites one
-//                   pixel front to back; the block stops once every pixel is done
+//   k_blend_fwd     one tile per block, one 8 x 4 PPT sub-block per warp: each
+//                   warp streams its tile's list 32 entries at a time, culls by
+//                   ballot the entries that cannot reach its sub-block, and each
+//                   thread composites its pixels front to back; a warp stops
+//                   once all its pixels are done
 //   k_blend_bwd     the adjoint, back to front from each pixel's last
 //                   composited entry, transmittance recovered by division,
 //                   warp-reduced per-Gaussian gradients
+//   k_blend_fwd_groups / k_blend_bwd_groups
+//                   the same with each warp split into four 8-lane groups of
+//                   two pixel columns, each group walking its own hits
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -593,12 +598,13 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
   const int n = rg.y - rg.x;
   float T[PPT], acc[PPT][C];
   bool done[PPT];
-  int last[PPT];
+  int last[PPT], stop[PPT];   // stop: entries walked up to the one that ended the pixel (0 = not ended)
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
     T[k] = 1.f;
     done[k] = !(px < bp.W && py0 + 4 * k < bp.H);
     last[k] = 0;
+    stop[k] = 0;
 #pragma unroll
     for (int ch = 0; ch < C; ++ch) acc[k][ch] = 0.f;
   }
@@ -640,6 +646,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
         const float test = T[k] * (1.f - a);
         if (test < bp.t_min) {
           done[k] = true;
+          stop[k] = base + b + 1;
           continue;
         }
         const float wgt = a * T[k];
@@ -658,6 +665,11 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
   }
   count_evals(&st->blend_evals, evals);
   count_evals(&st->blend_contribs, contribs);
+  unsigned int visits = 0;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k)
+    if (px < bp.W && py0 + 4 * k < bp.H) visits += stop[k] ? stop[k] : n;
+  count_evals(&st->blend_visits, visits);
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
     const int py = py0 + 4 * k;
@@ -835,16 +847,407 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
     __syncwarp();
   }
   count_evals(&st->blend_bwd_evals, evals);
+  unsigned int visits = 0;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) visits += last[k];
+  count_evals(&st->blend_bwd_visits, visits);
 }
 
-// (TILE, PPT) -> launch.  Valid: TILE 8 with PPT 1-2, TILE 16 and 32 with PPT 1-4.
+// ---------------------------------------------------------------------------
+// Lane-group decomposition.  A fill Gaussian's reach (about 2.5 px at h = 1)
+// covers only a few of the columns of a warp's 8 x 4 PPT sub-block, so most
+// lanes idle while the warp walks a Gaussian.  Here the warp splits into four
+// groups of eight lanes, group g owning pixel columns 2g and 2g + 1 of the
+// sub-block (all its rows), and each group walks its own list: the batch's
+// Gaussians that can reach one of its pixels.  In one iteration the four
+// groups work on up to four different Gaussians.  Every pixel still visits
+// the Gaussians of its tile's list in list order (the groups differ only in
+// which entries they skip as out of reach), so the image is bit-identical to
+// the whole-warp kernels'; only the order of the gradient atomics changes.
+
+constexpr int kLaneGroups = 4;
+
+// Pixel of this lane in the lane-group layout: lane = 8 g + i, column
+// 2 g + (i & 1), row i >> 1 (+ 4 k for the k-th pixel of the thread).
+template <int TILE, int PPT>
+__device__ __forceinline__ void group_pixels(const BlendParams& bp, int& s, int& px, int& py0, float& bxf,
+                                             float& y0, float& y1) {
+  using Gm = BlendGeom<TILE, PPT>;
+  const int tile = blockIdx.x;
+  s = tile / bp.tiles_per_scene;
+  const int t = tile - s * bp.tiles_per_scene;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int bx = (t % bp.tiles_x) * TILE + (w % Gm::kWarpsX) * 8;
+  const int by = (t / bp.tiles_x) * TILE + (w / Gm::kWarpsX) * 4 * PPT;
+  px = bx + 2 * (lane >> 3) + (lane & 1);
+  py0 = by + ((lane >> 1) & 3);
+  bxf = bx + 0.5f;
+  y0 = by + 0.5f;
+  y1 = by + 4.f * PPT - 0.5f;
+}
+
+// Hit masks of the four groups for the Gaussian this lane loaded (q, squared
+// reach r2; valid = false for lanes past the list), and the mask of this
+// lane's own group.  Group g tests the rectangle of its pixel centres
+// [bxf + 2g, bxf + 2g + 1] x [y0, y1] with the same rule as the whole-warp
+// kernels.
+__device__ __forceinline__ unsigned int group_masks(bool valid, float qx, float qy, float r2, float bxf, float y0,
+                                                    float y1, bool& any_hit) {
+  const int lane = threadIdx.x & 31;
+  unsigned int mine = 0;
+  any_hit = false;
+#pragma unroll
+  for (int g = 0; g < kLaneGroups; ++g) {
+    const float x0 = bxf + 2.f * g;
+    const bool h = valid && rect_d2(qx, qy, x0, x0 + 1.f, y0, y1) <= r2;
+    any_hit = any_hit || h;
+    const unsigned int m = __ballot_sync(0xffffffffu, h);
+    if ((lane >> 3) == g) mine = m;
+  }
+  return mine;
+}
+
+// Sum of 8 values over each aligned group of 8 lanes: lane i of the group
+// receives the group total of value i (7 shuffles).
+__device__ __forceinline__ float group_sum8(const float v[8]) {
+  const int i = threadIdx.x & 7;
+  const bool h4 = i & 4, h2 = i & 2, h1 = i & 1;
+  float b[4], c[2];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float send = h4 ? v[k] : v[k + 4];
+    const float keep = h4 ? v[k + 4] : v[k];
+    b[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float send = h2 ? b[k] : b[k + 2];
+    const float keep = h2 ? b[k + 2] : b[k];
+    c[k] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+  }
+  return (h1 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, h1 ? c[0] : c[1], 1);
+}
+
+// Sum of 4 values over each aligned group of 8 lanes: lanes 0, 2, 4, 6 of the
+// group receive the totals of values 0, 1, 2, 3 (4 shuffles).
+__device__ __forceinline__ float group_sum4(const float v[4]) {
+  const int i = threadIdx.x & 7;
+  const bool h4 = i & 4, h2 = i & 2;
+  float b[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float send = h4 ? v[k] : v[k + 2];
+    const float keep = h4 ? v[k + 2] : v[k];
+    b[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  float d = (h2 ? b[1] : b[0]) + __shfl_xor_sync(0xffffffffu, h2 ? b[0] : b[1], 2);
+  return d + __shfl_xor_sync(0xffffffffu, d, 1);
+}
+
+template <int TILE, int PPT, int C, bool ANISO>
+__global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE, PPT>::kMinBlocks)
+    k_blend_fwd_groups(const int2* __restrict__ ranges, const uint32_t* __restrict__ gid,
+                       const float4* __restrict__ prep, const float2* __restrict__ prep2,
+                       const float2* __restrict__ reach, const int* __restrict__ gcurve,
+                       const float4* __restrict__ color, BlendParams bp, float* image, float* Tfinal, int* nlast,
+                       DevState* st) {
+  using Gm = BlendGeom<TILE, PPT>;
+  __shared__ float4 s_q[Gm::kWarps][32];
+  __shared__ float4 s_c[Gm::kWarps][32];
+  __shared__ float2 s_q2[ANISO ? Gm::kWarps : 1][32];
+  int s, px, py0;
+  float bxf, y0, y1;
+  group_pixels<TILE, PPT>(bp, s, px, py0, bxf, y0, y1);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float fx = px + 0.5f;
+  const int2 rg = ranges[blockIdx.x];
+  const int n = rg.y - rg.x;
+  float T[PPT], acc[PPT][C];
+  bool done[PPT];
+  int last[PPT], stop[PPT];   // stop: entries walked up to the one that ended the pixel (0 = not ended)
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    T[k] = 1.f;
+    done[k] = !(px < bp.W && py0 + 4 * k < bp.H);
+    last[k] = 0;
+    stop[k] = 0;
+#pragma unroll
+    for (int ch = 0; ch < C; ++ch) acc[k][ch] = 0.f;
+  }
+  auto all_done = [&]() {
+    bool d = true;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) d = d && done[k];
+    return d;
+  };
+  unsigned int evals = 0, contribs = 0;
+  for (int base = 0; base < n && !__all_sync(0xffffffffu, all_done()); base += 32) {
+    const int j = base + lane;
+    float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+    float r2 = -1.f;
+    uint32_t g = 0;
+    if (j < n) {
+      g = gid[rg.x + j];
+      q = prep[g];
+      r2 = reach[g].x;
+    }
+    bool hit;
+    unsigned int m = group_masks(j < n, q.x, q.y, r2, bxf, y0, y1, hit);
+    if (hit) {
+      s_q[w][lane] = q;
+      s_c[w][lane] = color[gcurve[g]];
+      if (ANISO) s_q2[ANISO ? w : 0][lane] = prep2[g];
+    }
+    if (all_done()) m = 0;
+    __syncwarp();
+    // the non-finished lanes of a group pop the same entries in the same order
+    while (__any_sync(0xffffffffu, m != 0)) {
+      if (m == 0) continue;   // back to the vote: every lane votes once per iteration
+      const int b = __ffs(m) - 1;
+      m &= m - 1;
+      const float4 qb = s_q[w][b];
+      const float2 q2 = ANISO ? s_q2[ANISO ? w : 0][b] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        if (done[k]) continue;
+        ++evals;
+        float dx, dy, d2, e;
+        const float a = ANISO ? gauss_alpha_aniso(fx, py0 + 4 * k + 0.5f, qb, q2, bp.alpha_max, dx, dy, e)
+                              : gauss_alpha(fx, py0 + 4 * k + 0.5f, qb, bp.alpha_max, dx, dy, d2, e);
+        if (a < bp.alpha_min) continue;
+        const float test = T[k] * (1.f - a);
+        if (test < bp.t_min) {
+          done[k] = true;
+          stop[k] = base + b + 1;
+          continue;
+        }
+        const float wgt = a * T[k];
+        const float4 cc = s_c[w][b];
+        acc[k][0] = fmaf(cc.x, wgt, acc[k][0]);
+        if (C == 3) {
+          acc[k][1] = fmaf(cc.y, wgt, acc[k][1]);
+          acc[k][2] = fmaf(cc.z, wgt, acc[k][2]);
+        }
+        T[k] = test;
+        last[k] = base + b + 1;
+        ++contribs;
+      }
+      if (all_done()) m = 0;
+    }
+    __syncwarp();
+  }
+  count_evals(&st->blend_evals, evals);
+  count_evals(&st->blend_contribs, contribs);
+  unsigned int visits = 0;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k)
+    if (px < bp.W && py0 + 4 * k < bp.H) visits += stop[k] ? stop[k] : n;
+  count_evals(&st->blend_visits, visits);
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    const int py = py0 + 4 * k;
+    if (px < bp.W && py < bp.H) {
+      const long long pix = ((long long)s * bp.H + py) * bp.W + px;
+      float* out = image + pix * C;
+      out[0] = acc[k][0] + T[k] * bp.bg0;
+      if (C == 3) {
+        out[1] = acc[k][1] + T[k] * bp.bg1;
+        out[2] = acc[k][2] + T[k] * bp.bg2;
+      }
+      Tfinal[pix] = T[k];
+      nlast[pix] = last[k];
+    }
+  }
+}
+
+template <int TILE, int PPT, int C, bool ANISO>
+__global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE, PPT>::kMinBlocksBwd)
+    k_blend_bwd_groups(const int2* __restrict__ ranges, const uint32_t* __restrict__ gid,
+                       const float4* __restrict__ prep, const float2* __restrict__ prep2,
+                       const float2* __restrict__ reach, const int* __restrict__ gcurve,
+                       const float4* __restrict__ color, BlendParams bp, const float* __restrict__ dimage,
+                       const float* __restrict__ Tfinal, const int* __restrict__ nlast, float* dgauss, DevState* st,
+                       int full_grads) {
+  using Gm = BlendGeom<TILE, PPT>;
+  constexpr int kRow = GradRow<ANISO>::kFloats;
+  __shared__ float4 s_q[Gm::kWarps][32];
+  __shared__ float4 s_c[Gm::kWarps][32];
+  __shared__ float s_isig[Gm::kWarps][32];
+  __shared__ uint32_t s_id[Gm::kWarps][32];
+  __shared__ float2 s_q2[ANISO ? Gm::kWarps : 1][32];
+  int s, px, py0;
+  float bxf, y0, y1;
+  group_pixels<TILE, PPT>(bp, s, px, py0, bxf, y0, y1);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, gi = lane & 7;
+  const float fx = px + 0.5f;
+  const int2 rg = ranges[blockIdx.x];
+  float T[PPT], dI[PPT][3], Bk[PPT][3];
+  int last[PPT];
+  int gmax = 0;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    const int py = py0 + 4 * k;
+    T[k] = 1.f;
+    last[k] = 0;
+    Bk[k][0] = bp.bg0;
+    Bk[k][1] = bp.bg1;
+    Bk[k][2] = bp.bg2;
+    dI[k][0] = dI[k][1] = dI[k][2] = 0.f;
+    if (px < bp.W && py < bp.H) {
+      const long long pix = ((long long)s * bp.H + py) * bp.W + px;
+      T[k] = Tfinal[pix];
+      last[k] = nlast[pix];
+#pragma unroll
+      for (int ch = 0; ch < C; ++ch) dI[k][ch] = dimage[pix * C + ch];
+    }
+    gmax = max(gmax, last[k]);
+  }
+  // list length of the group (its masks are trimmed to it, so that all eight
+  // lanes pop the same entries) and of the warp
+  for (int o = 4; o > 0; o >>= 1) gmax = max(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+  int wmax = gmax;
+  for (int o = 16; o > 4; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+  unsigned int evals = 0;
+  for (int base = ((wmax - 1) >> 5) << 5; base >= 0 && wmax > 0; base -= 32) {
+    const int j = base + lane;
+    float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 rs = make_float2(-1.f, 0.f);
+    uint32_t g = 0;
+    if (j < wmax) {
+      g = gid[rg.x + j];
+      q = prep[g];
+      rs = reach[g];
+    }
+    bool hit;
+    unsigned int m = group_masks(j < wmax, q.x, q.y, rs.x, bxf, y0, y1, hit);
+    if (hit) {
+      s_q[w][lane] = q;
+      s_c[w][lane] = color[gcurve[g]];
+      s_isig[w][lane] = rs.y;
+      s_id[w][lane] = g;
+      if (ANISO) s_q2[ANISO ? w : 0][lane] = prep2[g];
+    }
+    const int lim = gmax - base;
+    m &= lim >= 32 ? 0xffffffffu : (lim <= 0 ? 0u : ((1u << lim) - 1u));
+    __syncwarp();
+    while (__any_sync(0xffffffffu, m != 0)) {
+      const bool act = m != 0;
+      int b = 0;
+      float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      float vC = 0.f;   // dC of a tangent-aligned Gaussian
+      bool contrib = false, geo = false;
+      if (act) {
+        b = 31 - __clz(m);
+        m &= ~(1u << b);
+        const float4 qb = s_q[w][b];
+        const float2 q2 = ANISO ? s_q2[ANISO ? w : 0][b] : make_float2(0.f, 0.f);
+        const float isg_raw = s_isig[w][b];
+        // fill Gaussians (negative 1/sigma) need only the opacity and colour
+        // gradients unless the caller asked for every per-Gaussian gradient
+        geo = full_grads || isg_raw > 0.f;
+        const float isg = fabsf(isg_raw);
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+          if (base + b >= last[k]) continue;
+          ++evals;
+          float dx, dy, d2 = 0.f, e;
+          const float a = ANISO ? gauss_alpha_aniso(fx, py0 + 4 * k + 0.5f, qb, q2, bp.alpha_max, dx, dy, e)
+                                : gauss_alpha(fx, py0 + 4 * k + 0.5f, qb, bp.alpha_max, dx, dy, d2, e);
+          if (a < bp.alpha_min) continue;
+          contrib = true;
+          T[k] = __fdividef(T[k], 1.f - a);   // transmittance in front of this Gaussian
+          const float wgt = a * T[k];
+          const float4 cc = s_c[w][b];
+          float da = (cc.x - Bk[k][0]) * dI[k][0];
+          v[5] += wgt * dI[k][0];
+          Bk[k][0] = a * cc.x + (1.f - a) * Bk[k][0];
+          if (C == 3) {
+            da += (cc.y - Bk[k][1]) * dI[k][1] + (cc.z - Bk[k][2]) * dI[k][2];
+            v[6] += wgt * dI[k][1];
+            v[7] += wgt * dI[k][2];
+            Bk[k][1] = a * cc.y + (1.f - a) * Bk[k][1];
+            Bk[k][2] = a * cc.z + (1.f - a) * Bk[k][2];
+          }
+          da *= T[k];
+          if (__fmul_rn(qb.w, e) < bp.alpha_max) {
+            v[4] += e * da;
+            if (geo) {
+              if (ANISO) {
+                const float ga = da * a;
+                v[0] -= ga * (2.f * qb.z * dx + q2.x * dy);
+                v[1] -= ga * (q2.x * dx + 2.f * q2.y * dy);
+                v[2] += ga * dx * dx;
+                v[3] += ga * dx * dy;
+                vC += ga * dy * dy;
+              } else {
+                const float aa = da * a * isg * isg;
+                v[0] += aa * dx;
+                v[1] += aa * dy;
+                v[2] += aa * d2 * isg;
+              }
+            }
+          }
+        }
+      }
+      // per-group reductions: every lane takes part in the shuffles, the
+      // group's lanes 0 (and 4) write its Gaussian's row
+      const unsigned int cb = __ballot_sync(0xffffffffu, contrib);
+      const bool gcontrib = ((cb >> (lane & 24)) & 0xffu) != 0u;
+      if (cb == 0u) continue;   // no group composited anything: nothing to reduce
+      if (__any_sync(0xffffffffu, contrib && geo)) {
+        const float t = group_sum8(v);
+        const float t1 = __shfl_down_sync(0xffffffffu, t, 1, 8);
+        const float t2 = __shfl_down_sync(0xffffffffu, t, 2, 8);
+        const float t3 = __shfl_down_sync(0xffffffffu, t, 3, 8);
+        if (ANISO) {
+          float tc = vC;
+          for (int o = 4; o > 0; o >>= 1) tc += __shfl_xor_sync(0xffffffffu, tc, o);
+          if (gcontrib && geo && gi == 0 && tc != 0.f) atomicAdd(dgauss + (long long)s_id[w][b] * kRow + 8, tc);
+        }
+        if (gcontrib && (gi == 4 || (gi == 0 && geo)))
+          red_add_v4(dgauss + (long long)s_id[w][b] * kRow + gi, t, t1, t2, t3);
+      } else {
+        const float t = group_sum4(v + 4);
+        const float t1 = __shfl_down_sync(0xffffffffu, t, 2, 8);
+        const float t2 = __shfl_down_sync(0xffffffffu, t, 4, 8);
+        const float t3 = __shfl_down_sync(0xffffffffu, t, 6, 8);
+        if (gcontrib && gi == 0) red_add_v4(dgauss + (long long)s_id[w][b] * kRow + 4, t, t1, t2, t3);
+      }
+    }
+    __syncwarp();
+  }
+  count_evals(&st->blend_bwd_evals, evals);
+  unsigned int visits = 0;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) visits += last[k];
+  count_evals(&st->blend_bwd_visits, visits);
+}
+
+// (TILE, decomposition) -> launch.  Valid: TILE 8 with PPT 1-2, TILE 16 and 32 with PPT 1-4; lane groups
+// with PPT 1-2 at every tile.
+// Kernel of a decomposition: whole-warp sub-blocks, or lane groups (PPT 1-2).
+template <int TL, int PP, int C, bool ANISO, bool GRP>
+static auto fwd_kernel() {
+  if constexpr (GRP && PP <= 2) return &k_blend_fwd_groups<TL, PP, C, ANISO>;
+  else return &k_blend_fwd<TL, PP, C, ANISO>;
+}
+template <int TL, int PP, int C, bool ANISO, bool GRP>
+static auto bwd_kernel() {
+  if constexpr (GRP && PP <= 2) return &k_blend_bwd_groups<TL, PP, C, ANISO>;
+  else return &k_blend_bwd<TL, PP, C, ANISO>;
+}
+
+// `code` is a decomposition: pixels per thread, plus NS_BLEND_LANE_GROUPS for
+// the lane-group kernels.
 template <int C, bool ANISO>
-static void launch_fwd(int tile, int ppt, int grid, cudaStream_t s, const int2* ranges, const uint32_t* gid,
+static void launch_fwd(int tile, int code, int grid, cudaStream_t s, const int2* ranges, const uint32_t* gid,
                        const float4* prep, const float2* prep2, const float2* reach, const int* gcurve,
                        const float4* col, const BlendParams& bp, float* image, float* Tf, int* nl, DevState* st) {
+  const bool grp = (code & NS_BLEND_LANE_GROUPS) != 0;
+  const int ppt = code & ~NS_BLEND_LANE_GROUPS;
 #define NS_FWD(TL, PP)                                                                                 \
   {                                                                                                      \
-    auto kern = &k_blend_fwd<TL, PP, C, ANISO>;                                                          \
+    auto kern = grp ? fwd_kernel<TL, PP, C, ANISO, true>() : fwd_kernel<TL, PP, C, ANISO, false>();      \
     NS_LAUNCH(NS_KERNEL_BLEND_FWD, kern, grid, (BlendGeom<TL, PP>::kThreads), 0, s, ranges, gid, prep,  \
               prep2, reach, gcurve, col, bp, image, Tf, nl, st);                                        \
   }
@@ -855,13 +1258,15 @@ static void launch_fwd(int tile, int ppt, int grid, cudaStream_t s, const int2* 
 }
 
 template <int C, bool ANISO>
-static void launch_bwd(int tile, int ppt, int grid, cudaStream_t s, const int2* ranges, const uint32_t* gid,
+static void launch_bwd(int tile, int code, int grid, cudaStream_t s, const int2* ranges, const uint32_t* gid,
                        const float4* prep, const float2* prep2, const float2* reach, const int* gcurve,
                        const float4* col, const BlendParams& bp, const float* dimage, const float* Tf, const int* nl,
                        float* dgauss, DevState* st, int full_grads) {
+  const bool grp = (code & NS_BLEND_LANE_GROUPS) != 0;
+  const int ppt = code & ~NS_BLEND_LANE_GROUPS;
 #define NS_BWD(TL, PP)                                                                                 \
   {                                                                                                      \
-    auto kern = &k_blend_bwd<TL, PP, C, ANISO>;                                                          \
+    auto kern = grp ? bwd_kernel<TL, PP, C, ANISO, true>() : bwd_kernel<TL, PP, C, ANISO, false>();      \
     NS_LAUNCH(NS_KERNEL_BLEND_BWD, kern, grid, (BlendGeom<TL, PP>::kThreads), 0, s, ranges, gid, prep,  \
               prep2, reach, gcurve, col, bp, dimage, Tf, nl, dgauss, st, full_grads);                   \
   }
@@ -943,7 +1348,11 @@ static int resolve_ppt(int tile, int ppt) {
   return ppt;
 }
 
-static bool ppt_ok(int tile, int ppt) { return ppt == 1 || ppt == 2 || (ppt == 4 && tile >= 16); }
+static bool ppt_ok(int tile, int code) {
+  const int ppt = code & ~NS_BLEND_LANE_GROUPS;
+  if (code & NS_BLEND_LANE_GROUPS) return ppt == 1 || ppt == 2;
+  return ppt == 1 || ppt == 2 || (ppt == 4 && tile >= 16);
+}
 
 static bool check_raster(const ns_raster_params* rp) {
   if (!rp || (rp->tile != 8 && rp->tile != 16 && rp->tile != 32) || !(rp->k_sigma > 0.f) ||
@@ -953,7 +1362,8 @@ static bool check_raster(const ns_raster_params* rp) {
     return false;
   }
   if (!ppt_ok(rp->tile, resolve_ppt(rp->tile, rp->ppt_fwd)) || !ppt_ok(rp->tile, resolve_ppt(rp->tile, rp->ppt_bwd))) {
-    set_error("invalid pixels per thread (1, 2, or 4 with tiles of 16 and 32; 0 = default)");
+    set_error("invalid blend decomposition (pixels per thread 1, 2, or 4 with tiles of 16 and 32; "
+              "lane groups with 1 or 2; 0 = default)");
     return false;
   }
   return true;
@@ -997,6 +1407,7 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
   cudaMemsetAsync(&st->culled, 0, sizeof(unsigned long long), s);
   cudaMemsetAsync(&st->blend_evals, 0, sizeof(unsigned long long), s);
   cudaMemsetAsync(&st->blend_contribs, 0, sizeof(unsigned long long), s);
+  cudaMemsetAsync(&st->blend_visits, 0, sizeof(unsigned long long), s);
   if (curves->n_curves > 0)
     NS_LAUNCH(NS_KERNEL_OTHER, k_curve_scene, (curves->n_curves + 255) / 256, 256, 0, s, *curves, curve_scene);
   BinParams bp;
@@ -1059,6 +1470,7 @@ ns_status launch_blend_bwd(const Layout& L, const ns_curves* curves, const ns_ga
   const uint32_t* vsorted = (rpn.passes & 1) ? at<uint32_t>(ws, L.o_v1) : at<uint32_t>(ws, L.o_v0);
   DevState* st = at<DevState>(ws, L.o_state);
   cudaMemsetAsync(&st->blend_bwd_evals, 0, sizeof(unsigned long long), s);
+  cudaMemsetAsync(&st->blend_bwd_visits, 0, sizeof(unsigned long long), s);
   const BlendArgs ba{at<int2>(ws, L.o_ranges), vsorted, at<float4>(ws, L.o_prep), at<float2>(ws, L.o_prep2),
                      at<float2>(ws, L.o_reach), g->curve, reinterpret_cast<const float4*>(curves->color),
                      blend_params(L, rp), at<float>(ws, L.o_T), at<int>(ws, L.o_nlast), st};
@@ -1102,7 +1514,7 @@ extern "C" ns_status ns_autotune_blend(const ns_curves* curves, const ns_gaussia
   auto time_best = [&](bool backward) {
     int best = 0;
     float best_ms = 3.4e38f;
-    for (int ppt : {1, 2, 4}) {
+    for (int ppt : {1, 2, 4, 1 | NS_BLEND_LANE_GROUPS, 2 | NS_BLEND_LANE_GROUPS}) {
       if (!ppt_ok(rp->tile, ppt)) continue;
       float t = 3.4e38f;
       for (int r = 0; r < repeats + 1; ++r) {   // the first run warms the variant up
@@ -1128,7 +1540,7 @@ extern "C" ns_status ns_autotune_blend(const ns_curves* curves, const ns_gaussia
   rp->ppt_bwd = bb;
   // leave the workspace as the chosen forward leaves it (the results of all
   // variants are identical) and the counters as one forward pass sets them
-  cudaMemsetAsync(&st->blend_evals, 0, 3 * sizeof(unsigned long long), s);
+  cudaMemsetAsync(&st->blend_evals, 0, 5 * sizeof(unsigned long long), s);
   fwd(bf);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

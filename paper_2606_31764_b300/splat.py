@@ -59,6 +59,8 @@ class Report:
     blend_evals: int
     blend_bwd_evals: int
     blend_contribs: int
+    blend_visits: int = 0
+    blend_bwd_visits: int = 0
 
 
 class DeviceCurves:
@@ -148,7 +150,7 @@ class Splatter:
         r = B.NsReport()
         B.call("ns_poll_status", _ptr(self.ws), C.byref(r), _stream())
         return Report(r.status, r.bad_curve, r.gaussians, r.pairs, r.boundary, r.fill_culled, r.blend_evals,
-                      r.blend_bwd_evals, r.blend_contribs)
+                      r.blend_bwd_evals, r.blend_contribs, r.blend_visits, r.blend_bwd_visits)
 
     # -- stages ---------------------------------------------------------
     def sample(self, key, tau, color):

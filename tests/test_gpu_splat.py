@@ -171,7 +171,9 @@ def test_autotune_keeps_the_image():
     before = sp.forward(k, t, c).clone()
     dimg = torch.ones_like(before)
     pf, pb = sp.autotune_blend(k, t, c, dimg, repeats=2)
-    assert pf in (1, 2, 4) and pb in (1, 2, 4)
+    from paper_2606_31764_b300 import binding as B
+    grp = B.BLEND_LANE_GROUPS
+    assert pf in (1, 2, 4, 1 | grp, 2 | grp) and pb in (1, 2, 4, 1 | grp, 2 | grp)
     assert torch.equal(sp.image, before)
     after = sp.forward(k, t, c)
     assert torch.equal(after, before)
