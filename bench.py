@@ -88,6 +88,8 @@ def parse():
     ap.add_argument("--no-per-scene", action="store_true")
     ap.add_argument("--paths", type=int, default=2048, help="paths of the 1024x1024 workload (2048 = full)")
     ap.add_argument("--tiles", default="8,16,32", help="tile sizes the autotuner tries (comma separated)")
+    ap.add_argument("--fill-layers", default="0,1",
+                    help="binnings the autotuner tries: 0 per Gaussian, 1 fill layers (comma separated)")
     ap.add_argument("--cpu-sample-curves", type=int, default=64)
     ap.add_argument("--ref-sample-curves", type=int, default=8)
     return ap.parse_args()
@@ -224,12 +226,14 @@ class Step:
         return int(self.sp.count.item())
 
 
-def autotune(torch, scene, tiles, capacity, steps=3, adam=False, geometry=None):
-    """Tile size by timing whole steps; pixels per thread of the blend kernels
-    by the library's ns_autotune_blend on each tile's workspace."""
+def autotune(torch, scene, tiles, capacity, steps=3, adam=False, geometry=None, layers=(0, 1)):
+    """Tile size and binning (per Gaussian, or fill layers) by timing whole
+    steps; the blend decomposition by the library's ns_autotune_blend on each
+    candidate's workspace."""
     best, best_ms, table = None, None, {}
-    for tile in tiles:
-        st = Step(scene, capacity, raster=dict(scene.raster, tile=tile), adam=adam, geometry=geometry)
+    for tile, fl in [(t, f) for t in tiles for f in layers]:
+        st = Step(scene, capacity, raster=dict(scene.raster, tile=tile, fill_layers=fl), adam=adam,
+                  geometry=geometry)
         st()
         st.sp.autotune_blend(st.key, st.tau, st.color, st.dimage, repeats=3)
         st()
@@ -241,7 +245,8 @@ def autotune(torch, scene, tiles, capacity, steps=3, adam=False, geometry=None):
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
-        table[tile] = dict(ms=round(ms, 4), ppt_fwd=int(st.sp.rp.ppt_fwd), ppt_bwd=int(st.sp.rp.ppt_bwd))
+        table[f"{tile}" + ("-layers" if fl else "")] = dict(ms=round(ms, 4), ppt_fwd=int(st.sp.rp.ppt_fwd),
+                                                             ppt_bwd=int(st.sp.rp.ppt_bwd))
         if best_ms is None or ms < best_ms:
             if best is not None:
                 del best
@@ -250,7 +255,7 @@ def autotune(torch, scene, tiles, capacity, steps=3, adam=False, geometry=None):
             del st
         torch.cuda.empty_cache()
     chosen = dict(tile=int(best.sp.rp.tile), ppt_fwd=int(best.sp.rp.ppt_fwd), ppt_bwd=int(best.sp.rp.ppt_bwd),
-                  tried=table)
+                  fill_layers=int(best.sp.rp.fill_layers), tried=table)
     return best, chosen
 
 
@@ -294,7 +299,8 @@ def run_gpu(args, dist, rank, world):
     peaks = load_peaks()
     sc = scenes.config5(seed=1005 + rank, n_paths=args.paths)
     step, tuning = autotune(torch, sc, [int(x) for x in args.tiles.split(",")],
-                            capacity=(10_000_000, 40_000_000, 400_000))
+                            capacity=(10_000_000, 40_000_000, 400_000),
+                            layers=tuple(int(x) for x in args.fill_layers.split(",")))
     step()
     torch.cuda.synchronize()
     rep = step.sp.report()
@@ -527,7 +533,7 @@ def run_long_spline(torch, args):
     sc = scenes.config3()
     geo = dict(lambda_deriv=1.0, lambda_bbox=5.0, order=3)
     st, tuning = autotune(torch, sc, [int(x) for x in args.tiles.split(",")], capacity=(3_000_000, 24_000_000, 16),
-                          adam=True, geometry=geo)
+                          adam=True, geometry=geo, layers=(0,))   # open strokes only: no fill layers
     st()
     K = max(3, args.steps)
     prof = ["emit", "bin_emit", "radix_scatter", "blend_fwd", "blend_bwd", "chain_contour", "deriv_loss",

@@ -116,6 +116,15 @@ typedef struct {
   int32_t ppt_fwd;  /* decomposition of the forward blend: pixels per thread 1, 2 or 4 (4 needs
                        tile >= 16), or 1 or 2 plus NS_BLEND_LANE_GROUPS; 0 = default */
   int32_t ppt_bwd;  /* the same for the backward blend; neither changes any result */
+  int32_t fill_layers; /* 1: the Gaussians of a filled curve, which lie on its grid (§3.3), are
+                          binned as one tile pair per tile their bin rectangles cover, and the blend
+                          kernels find the grid points that can reach a pixel by index arithmetic.
+                          Every pixel composites the same Gaussians in the same order as with 0
+                          (one pair per Gaussian and tile), so images are identical; gradients
+                          differ only in the order of float additions.  Needs a Gaussian set
+                          written by nurbs_sample into the same workspace, and tile 8 or 16 (or
+                          tile 32 with 4 pixels per thread); the decomposition falls back to one
+                          of those when needed.  0: one pair per Gaussian and tile. */
 } ns_raster_params;
 
 /* Capacities that bound the data-dependent sizes. */

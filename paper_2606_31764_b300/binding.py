@@ -36,7 +36,8 @@ class NsSampleParams(C.Structure):
 
 class NsRasterParams(C.Structure):
     _fields_ = [("tile", C.c_int32), ("k_sigma", C.c_float), ("alpha_min", C.c_float), ("alpha_max", C.c_float),
-                ("t_min", C.c_float), ("bg", C.c_float * 3), ("ppt_fwd", C.c_int32), ("ppt_bwd", C.c_int32)]
+                ("t_min", C.c_float), ("bg", C.c_float * 3), ("ppt_fwd", C.c_int32), ("ppt_bwd", C.c_int32),
+                ("fill_layers", C.c_int32)]
 
 
 class NsCapacity(C.Structure):

@@ -142,6 +142,7 @@ bool make_layout(const ns_curves* c, const ns_capacity* cap, const ns_raster_par
   L->o_ranges = take(sizeof(int2) * (size_t)L->n_tiles);
   L->o_T = take(sizeof(float) * (size_t)L->n_pix);
   L->o_nlast = take(sizeof(int) * (size_t)L->n_pix);
+  L->o_nsub = take(sizeof(int) * (size_t)L->n_pix);
   L->o_dgauss = take(sizeof(float) * 12 * (size_t)L->gcap);   // 8 per Gaussian, 12 when tangent-aligned
   L->o_prep = take(sizeof(float4) * (size_t)L->gcap);
   L->o_prep2 = take(sizeof(float2) * (size_t)L->gcap);
@@ -238,6 +239,7 @@ ns_raster_params ns_default_raster_params(void) {
   r.bg[0] = r.bg[1] = r.bg[2] = 1.f;
   r.ppt_fwd = 0;
   r.ppt_bwd = 0;
+  r.fill_layers = 0;
   return r;
 }
 

@@ -28,7 +28,7 @@ namespace ns {
 
 ns_status launch_blend_bwd(const Layout& L, const ns_curves* curves, const ns_gaussians* g,
                            const ns_raster_params* rp, const float* dimage, float* dgauss, void* ws,
-                           cudaStream_t s, int full_grads);
+                           cudaStream_t s, int full_grads, float* dcurve);
 bool raster_params_ok(const ns_raster_params* rp);
 
 constexpr int kWin = 1024;   // control points (and knots) per task window in shared memory
@@ -512,9 +512,16 @@ extern "C" ns_status splat_backward(const ns_curves* curves, const ns_gaussians*
   const int row = aniso ? 12 : 8;   // floats per per-Gaussian gradient row
   float* dg = dgauss ? dgauss : at<float>(ws, L.o_dgauss);
   cudaMemsetAsync(dg, 0, sizeof(float) * row * (size_t)L.gcap, s);
+  if (out && zero_outputs) {
+    cudaMemsetAsync(out->dkey, 0, sizeof(float) * 4 * (size_t)L.nk, s);
+    if (out->dtau) cudaMemsetAsync(out->dtau, 0, sizeof(float) * (size_t)L.nt, s);
+    cudaMemsetAsync(out->dcolor, 0, sizeof(float) * 4 * (size_t)L.nc, s);
+  }
   // the centre and sigma gradients of fill Gaussians are needed only when the
-  // caller asked for the per-Gaussian gradients themselves
-  launch_blend_bwd(L, curves, g, rp, dL_dimage, dg, ws, s, dgauss != nullptr || out == nullptr);
+  // caller asked for the per-Gaussian gradients themselves; otherwise their
+  // colour gradients may go straight to the per-curve output
+  const bool full = dgauss != nullptr || out == nullptr;
+  launch_blend_bwd(L, curves, g, rp, dL_dimage, dg, ws, s, full, full ? nullptr : out->dcolor);
   if (out) {
     DevState* st = at<DevState>(ws, L.o_state);
     const CurvePlan* plan = at<CurvePlan>(ws, L.o_plan);
@@ -526,11 +533,6 @@ extern "C" ns_status splat_backward(const ns_curves* curves, const ns_gaussians*
     const size_t n_knots = (size_t)L.nt + (size_t)kKnotPad * L.nc;
     if (knots_on) cudaMemsetAsync(dknots, 0, sizeof(float) * n_knots, s);
     cudaMemsetAsync(dbpts, 0, sizeof(float2) * (size_t)L.bcap, s);
-    if (zero_outputs) {
-      cudaMemsetAsync(out->dkey, 0, sizeof(float) * 4 * (size_t)L.nk, s);
-      if (out->dtau) cudaMemsetAsync(out->dtau, 0, sizeof(float) * (size_t)L.nt, s);
-      cudaMemsetAsync(out->dcolor, 0, sizeof(float) * 4 * (size_t)L.nc, s);
-    }
     if (L.nc > 0) {
       ChainParams cp;
       cp.rho = sp->rho;

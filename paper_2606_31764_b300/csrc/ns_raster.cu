@@ -52,7 +52,11 @@ struct BinParams {
   float k_sigma, inv_tile, alpha_min, log_amin;   // log_amin = ln(alpha_min), or -inf
   int tiles_x, tiles_y, tiles_per_scene;
   int n_curves, gcap;   // Gaussians naming a curve outside [0, n_curves) cover no tile
+  int fill_layers;      // one pair per (tile, filled curve) instead of per (tile, Gaussian)
 };
+
+// Pair values of fill layers carry this bit on the index of the layer's first Gaussian.
+constexpr uint32_t kLayerBit = 0x80000000u;
 
 // Tile rectangle of one Gaussian; every step one float32 operation rounded to
 // nearest so that the result is reproducible bit for bit.
@@ -105,6 +109,49 @@ __device__ __forceinline__ int tile_rect_of(const float4* __restrict__ rec, cons
   else return tile_rect(rec[g], bp, x0, y0, nx);
 }
 
+// Tiles of a fill layer: the union of the bin rectangles of its grid's
+// Gaussians.  They share sigma and sit on a grid, so the union runs from the
+// first record's rectangle (smallest x and y) to the last one's (largest),
+// by the same float32 rule; every grid point is counted whatever its opacity
+// (a tile whose grid points are all culled gets an entry that composites
+// nothing).  The last record is clamped to the set (g1 < G).
+__device__ __forceinline__ int layer_rect(const float4* __restrict__ rec, long long g0, long long g1,
+                                          const BinParams& bp, int& x0, int& y0, int& nx) {
+  const float4 r0 = rec[g0], r1 = rec[g1];
+  const float ks = __fmul_rn(bp.k_sigma, r0.z);
+  const float xlo = floorf(__fmul_rn(__fsub_rn(r0.x, ks), bp.inv_tile));
+  const float xhi = floorf(__fmul_rn(__fadd_rn(r1.x, ks), bp.inv_tile));
+  const float ylo = floorf(__fmul_rn(__fsub_rn(r0.y, ks), bp.inv_tile));
+  const float yhi = floorf(__fmul_rn(__fadd_rn(r1.y, ks), bp.inv_tile));
+  const bool ok = r0.z > 0.f && xhi >= 0.f && yhi >= 0.f && xlo <= float(bp.tiles_x - 1) &&
+                  ylo <= float(bp.tiles_y - 1) && xlo <= xhi && ylo <= yhi;
+  if (!ok) return 0;
+  x0 = int(fmaxf(xlo, 0.f));
+  const int x1 = int(fminf(xhi, float(bp.tiles_x - 1)));
+  y0 = int(fmaxf(ylo, 0.f));
+  const int y1 = int(fminf(yhi, float(bp.tiles_y - 1)));
+  nx = x1 - x0 + 1;
+  return nx * (y1 - y0 + 1);
+}
+
+// Tile count of Gaussian g in the pair emission, and its rectangle.  In
+// fill-layer mode a fill Gaussian counts only as its layer's first one.
+template <bool ANISO>
+__device__ __forceinline__ int gaussian_tiles(const float4* __restrict__ rec, const float4* __restrict__ shape,
+                                              const int* __restrict__ cflags, const CurvePlan* __restrict__ plan,
+                                              long long g, int cv, int G, const BinParams& bp, bool& layer,
+                                              int& x0, int& y0, int& nx) {
+  layer = false;
+  if (cv < 0 || cv >= bp.n_curves) return 0;
+  if (bp.fill_layers && (cflags[cv] & NS_FILLED)) {
+    const CurvePlan& p = plan[cv];
+    if (g != p.g_off || p.count <= 0) return 0;
+    layer = true;
+    return layer_rect(rec, g, min(g + p.count, (long long)G) - 1, bp, x0, y0, nx);
+  }
+  return tile_rect_of<ANISO>(rec, shape, g, bp, x0, y0, nx);
+}
+
 __device__ __forceinline__ int block_excl_scan_int(int v, int* s_warp, int& total) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   int x = v;
@@ -147,7 +194,7 @@ __global__ void __launch_bounds__(256) k_bin_count(const float4* __restrict__ re
                                                    const int* __restrict__ gcurve,
                                                    const int* __restrict__ cflags, const int* __restrict__ gcount,
                                                    BinParams bp, int* bsum, DevState* st, float4* prep,
-                                                   float2* prep2, float2* reach) {
+                                                   float2* prep2, float2* reach, const CurvePlan* __restrict__ plan) {
   __shared__ int s_warp[32];
   const int G = min(*gcount, bp.gcap);
   const long long base = (long long)blockIdx.x * kBinItems;
@@ -162,9 +209,10 @@ __global__ void __launch_bounds__(256) k_bin_count(const float4* __restrict__ re
       const float4 r = rec[g];
       int x0, y0, nx;
       const int cv = gcurve[g];
-      const int nt = (cv >= 0 && cv < bp.n_curves) ? tile_rect_of<ANISO>(rec, shape, g, bp, x0, y0, nx) : 0;
+      bool layer;
+      const int nt = gaussian_tiles<ANISO>(rec, shape, cflags, plan, g, cv, G, bp, layer, x0, y0, nx);
       cnt += nt;
-      if (nt) {   // only binned Gaussians are ever read by the blend kernels
+      if (nt && !layer) {   // only Gaussians binned on their own are read through these
         // 1/sigma, negative for the Gaussians of filled curves (their centre and
         // sigma get no gradient through the chain, so the adjoint may skip
         // them).  The curve's flag decides: a fill point's aux can equal the
@@ -245,7 +293,8 @@ __global__ void __launch_bounds__(256) k_bin_emit(const float4* __restrict__ rec
                                                   const int* __restrict__ gcurve,
                                                   const int* __restrict__ gcount, const int* __restrict__ curve_scene,
                                                   BinParams bp, const int* __restrict__ boff, uint32_t* keys,
-                                                  uint32_t* vals, long long pcap) {
+                                                  uint32_t* vals, long long pcap, const int* __restrict__ cflags,
+                                                  const CurvePlan* __restrict__ plan) {
   __shared__ int s_warp[32];
   __shared__ int s_off[kBinItems];    // tile count, then exclusive offset in Gaussian order
   __shared__ int2 s_rect[kBinItems];  // {x0 | nx << 16, y0 | ny << 16}
@@ -259,8 +308,8 @@ __global__ void __launch_bounds__(256) k_bin_emit(const float4* __restrict__ rec
     const long long g = base + gl;
     int c = 0, x0 = 0, y0 = 0, nx = 1;
     if (g < G) {
-      const int cv = gcurve[g];
-      if (cv >= 0 && cv < bp.n_curves) c = tile_rect_of<ANISO>(rec, shape, g, bp, x0, y0, nx);
+      bool layer;
+      c = gaussian_tiles<ANISO>(rec, shape, cflags, plan, g, gcurve[g], G, bp, layer, x0, y0, nx);
     }
     s_off[gl] = c;
     s_rect[gl] = make_int2(x0 | (nx << 16), y0 | ((c ? c / nx : 0) << 16));
@@ -293,14 +342,16 @@ __global__ void __launch_bounds__(256) k_bin_emit(const float4* __restrict__ rec
     const int c = nx * ny;
     if (!c) continue;
     const int x0 = rr.x & 0xffff, y0 = rr.y & 0xffff;
-    const int sbase = curve_scene[gcurve[g]] * bp.tiles_per_scene;
+    const int cv = gcurve[g];
+    const int sbase = curve_scene[cv] * bp.tiles_per_scene;
+    const uint32_t val = uint32_t(g) | ((bp.fill_layers && (cflags[cv] & NS_FILLED)) ? kLayerBit : 0u);
     long long off = boff0 + s_off[gl];
     for (int j = 0; j < c; ++j, ++off) {
       if (off >= pcap) break;
       const int tx = x0 + j % nx;
       const int ty = y0 + j / nx;
       keys[off] = uint32_t(sbase + ty * bp.tiles_x + tx);
-      vals[off] = uint32_t(g);
+      vals[off] = val;
     }
   }
 }
@@ -706,7 +757,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
                 const float2* __restrict__ prep2, const float2* __restrict__ reach, const int* __restrict__ gcurve,
                 const float4* __restrict__ color, BlendParams bp, const float* __restrict__ dimage,
                 const float* __restrict__ Tfinal, const int* __restrict__ nlast, float* dgauss, DevState* st,
-                int full_grads) {
+                int full_grads, float* /* per-curve colour gradients: unused, the rows carry them */) {
   using Gm = BlendGeom<TILE, PPT>;
   constexpr int kRow = GradRow<ANISO>::kFloats;
   __shared__ float4 s_q[Gm::kWarps][32];
@@ -1067,7 +1118,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
                        const float2* __restrict__ reach, const int* __restrict__ gcurve,
                        const float4* __restrict__ color, BlendParams bp, const float* __restrict__ dimage,
                        const float* __restrict__ Tfinal, const int* __restrict__ nlast, float* dgauss, DevState* st,
-                       int full_grads) {
+                       int full_grads, float* /* per-curve colour gradients: unused, the rows carry them */) {
   using Gm = BlendGeom<TILE, PPT>;
   constexpr int kRow = GradRow<ANISO>::kFloats;
   __shared__ float4 s_q[Gm::kWarps][32];
@@ -1225,6 +1276,577 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
 
 // (TILE, decomposition) -> launch.  Valid: TILE 8 with PPT 1-2, TILE 16 and 32 with PPT 1-4; lane groups
 // with PPT 1-2 at every tile.
+// ---------------------------------------------------------------------------
+// Fill layers (ns_raster_params.fill_layers, isotropic sets).  The Gaussians
+// of a filled curve sit on its grid (§3.3): record g_off + iy nx + ix is grid
+// point (ix, iy), and all share one sigma.  The binning then emits one pair
+// per tile of the whole layer (value g_off | kLayerBit).  On such an entry
+// each lane walks, in sample order, the grid points that can reach its pixel:
+//   - the columns and rows whose bin rectangle covers this tile, by the exact
+//     float32 rule of tile_rect (the Gaussians per-Gaussian pairs would list),
+//   - narrowed, when alpha_min > 0, to |q - p| <= R per axis, R the reach of
+//     the layer's most opaque Gaussian (beyond it alpha < alpha_min),
+//   - skipping the grid points tile_rect would not bin (culled opacity).
+// A pixel thus composites exactly the Gaussians, in the order and with the
+// arithmetic of the per-Gaussian lists, and the image is the same bit for
+// bit.  The adjoint also needs, per pixel, the sample index of the last
+// composited Gaussian inside its layer (nsub) besides the list position.
+
+constexpr int kLayerRegion = 512;   // floats of a warp's opacity-gradient region per layer
+
+struct LayerArgs {
+  const CurvePlan* plan;
+  const float4* rec;
+  const int* gcount;
+  int gcap, tile;
+  float k_sigma, inv_tile, log_amin;
+  int* nsub;   // per pixel: 1 + sample index of the last composited fill Gaussian (0: none)
+};
+
+// One layer as a warp sees it on one tile (the same in every lane).
+struct LayerView {
+  long long g_off, G;   // first Gaussian; Gaussians in the set (the walk never reads past G)
+  int nx, ny;
+  float x0, y0, inv_h, sig, nc, R;
+  int cx0, cx1, cy0, cy1;   // columns and rows binned to this tile (empty when cx0 > cx1)
+};
+
+__device__ __forceinline__ bool bin_covers(float v, float ks, float inv_tile, int t) {
+  return floorf(__fmul_rn(__fsub_rn(v, ks), inv_tile)) <= float(t) &&
+         float(t) <= floorf(__fmul_rn(__fadd_rn(v, ks), inv_tile));
+}
+
+// The run of indices in [0, n) where ok() holds (contiguous: a bin
+// rectangle moves with its centre), found from a guess inside or near it.
+template <typename F>
+__device__ __forceinline__ void covered_run(int n, float guess, F ok, int& lo, int& hi) {
+  lo = 0;
+  hi = -1;
+  if (n <= 0) return;
+  int i = int(fminf(fmaxf(guess, 0.f), float(n - 1)));
+  if (!ok(i)) {
+    int a = i - 1, b = i + 1;
+    bool found = false;
+    while (!found && (a >= 0 || b < n)) {
+      if (b < n && ok(b)) {
+        i = b;
+        found = true;
+      } else if (a >= 0 && ok(a)) {
+        i = a;
+        found = true;
+      }
+      --a;
+      ++b;
+    }
+    if (!found) return;
+  }
+  lo = hi = i;
+  while (lo > 0 && ok(lo - 1)) --lo;
+  while (hi + 1 < n && ok(hi + 1)) ++hi;
+}
+
+__device__ __forceinline__ LayerView layer_view(const LayerArgs& la, int c, int tx, int ty, float o_c) {
+  LayerView v;
+  const CurvePlan p = la.plan[c];
+  v.G = min((long long)*la.gcount, (long long)la.gcap);
+  v.g_off = p.g_off;
+  v.nx = p.nx;
+  v.ny = p.ny;
+  v.cx0 = v.cy0 = 0;
+  v.cx1 = v.cy1 = -1;
+  v.x0 = p.x0;
+  v.y0 = p.y0;
+  v.inv_h = 0.f;
+  v.sig = v.nc = v.R = 0.f;
+  if (v.g_off < 0 || v.g_off >= v.G || v.nx <= 0 || v.ny <= 0 || !(p.h > 0.f) || !(o_c > 0.f)) return v;
+  v.inv_h = 1.f / p.h;
+  const float4 r0 = la.rec[v.g_off];
+  v.sig = r0.z;
+  v.nc = ncoef(r0.z);
+  v.R = la.log_amin > -1e30f ? sqrtf(reach2(r0.z, o_c, la.log_amin)) + 0.01f * p.h : FLT_MAX;
+  const float ks = __fmul_rn(la.k_sigma, r0.z);
+  const long long lastg = v.G - 1;
+  const float T = float(la.tile);
+  covered_run(v.nx, (tx * T - ks - v.x0) * v.inv_h - 0.5f,
+              [&](int ix) { return bin_covers(la.rec[min(v.g_off + ix, lastg)].x, ks, la.inv_tile, tx); },
+              v.cx0, v.cx1);
+  covered_run(v.ny, (ty * T - ks - v.y0) * v.inv_h - 0.5f,
+              [&](int iy) {
+                return bin_covers(la.rec[min(v.g_off + (long long)iy * v.nx, lastg)].y, ks, la.inv_tile, ty);
+              },
+              v.cy0, v.cy1);
+  return v;
+}
+
+// The grid points of the layer one pixel (centre fx, fy) may see.
+__device__ __forceinline__ void layer_window(const LayerView& v, float fx, float fy, int& ix0, int& ix1, int& iy0,
+                                             int& iy1) {
+  ix0 = v.cx0;
+  ix1 = v.cx1;
+  iy0 = v.cy0;
+  iy1 = v.cy1;
+  if (v.R < FLT_MAX) {
+    ix0 = max(ix0, int(ceilf(fmaxf((fx - v.R - v.x0) * v.inv_h - 0.5f, -1.f))));
+    ix1 = min(ix1, int(floorf(fminf((fx + v.R - v.x0) * v.inv_h - 0.5f, 2e9f))));
+    iy0 = max(iy0, int(ceilf(fmaxf((fy - v.R - v.y0) * v.inv_h - 0.5f, -1.f))));
+    iy1 = min(iy1, int(floorf(fminf((fy + v.R - v.y0) * v.inv_h - 0.5f, 2e9f))));
+  }
+}
+
+// A grid point the per-Gaussian binning would have listed (tile_rect's
+// per-Gaussian conditions; the tile itself is covered by construction).
+__device__ __forceinline__ bool layer_point_binned(const float4& r, float alpha_min) {
+  return r.z > 0.f && r.w > 0.f && r.w >= alpha_min;
+}
+
+template <int TILE, int PPT, int C>
+__global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE, PPT>::kMinBlocks)
+    k_blend_fwd_layers(const int2* __restrict__ ranges, const uint32_t* __restrict__ gid,
+                       const float4* __restrict__ prep, const float2* __restrict__ reach,
+                       const int* __restrict__ gcurve, const float4* __restrict__ color, BlendParams bp,
+                       LayerArgs la, float* image, float* Tfinal, int* nlast, DevState* st) {
+  using Gm = BlendGeom<TILE, PPT>;
+  __shared__ float4 s_q[Gm::kWarps][32];
+  __shared__ float4 s_c[Gm::kWarps][32];
+  __shared__ uint32_t s_id[Gm::kWarps][32];
+  int s, px, py0;
+  float4 wr;
+  tile_pixels<TILE, PPT>(bp, s, px, py0, wr);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x - s * bp.tiles_per_scene;
+  const int tx = t % bp.tiles_x, ty = t / bp.tiles_x;
+  const float fx = px + 0.5f;
+  const int2 rg = ranges[blockIdx.x];
+  const int n = rg.y - rg.x;
+  float T[PPT], acc[PPT][C];
+  bool done[PPT];
+  int last[PPT], lsub[PPT];
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    T[k] = 1.f;
+    done[k] = !(px < bp.W && py0 + 4 * k < bp.H);
+    last[k] = 0;
+    lsub[k] = 0;
+#pragma unroll
+    for (int ch = 0; ch < C; ++ch) acc[k][ch] = 0.f;
+  }
+  auto all_done = [&]() {
+    bool d = true;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) d = d && done[k];
+    return d;
+  };
+  unsigned int evals = 0, contribs = 0;
+  for (int base = 0; base < n && !__all_sync(0xffffffffu, all_done()); base += 32) {
+    const int j = base + lane;
+    bool hit = false;
+    if (j < n) {
+      const uint32_t g = gid[rg.x + j];
+      const uint32_t gi = g & ~kLayerBit;
+      if (g & kLayerBit) {
+        hit = true;
+        s_id[w][lane] = g;
+        s_c[w][lane] = color[gcurve[gi]];
+      } else {
+        const float4 q = prep[gi];
+        hit = rect_d2(q.x, q.y, wr.x, wr.y, wr.z, wr.w) <= reach[gi].x;
+        if (hit) {
+          s_id[w][lane] = g;
+          s_q[w][lane] = q;
+          s_c[w][lane] = color[gcurve[gi]];
+        }
+      }
+    }
+    unsigned int mask = __ballot_sync(0xffffffffu, hit);
+    __syncwarp();
+    while (mask) {
+      const int b = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const uint32_t id = s_id[w][b];
+      const float4 cc = s_c[w][b];
+      if (id & kLayerBit) {
+        if (all_done()) continue;
+        const LayerView v = layer_view(la, gcurve[id & ~kLayerBit], tx, ty, cc.w);
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+          if (done[k]) continue;
+          const float fy = py0 + 4 * k + 0.5f;
+          int ix0, ix1, iy0, iy1;
+          layer_window(v, fx, fy, ix0, ix1, iy0, iy1);
+          for (int iy = iy0; iy <= iy1 && !done[k]; ++iy) {
+            const long long rowg = v.g_off + (long long)iy * v.nx;
+            for (int ix = ix0; ix <= ix1; ++ix) {
+              const long long g = rowg + ix;
+              if (g >= v.G) break;
+              const float4 r = la.rec[g];
+              if (!layer_point_binned(r, bp.alpha_min)) continue;
+              ++evals;
+              float dx, dy, d2, e;
+              const float a = gauss_alpha(fx, fy, make_float4(r.x, r.y, r.z == v.sig ? v.nc : ncoef(r.z), r.w),
+                                          bp.alpha_max, dx, dy, d2, e);
+              if (a < bp.alpha_min) continue;
+              const float test = T[k] * (1.f - a);
+              if (test < bp.t_min) {
+                done[k] = true;
+                break;
+              }
+              const float wgt = a * T[k];
+              acc[k][0] = fmaf(cc.x, wgt, acc[k][0]);
+              if (C == 3) {
+                acc[k][1] = fmaf(cc.y, wgt, acc[k][1]);
+                acc[k][2] = fmaf(cc.z, wgt, acc[k][2]);
+              }
+              T[k] = test;
+              last[k] = base + b + 1;
+              lsub[k] = int(g - v.g_off) + 1;
+              ++contribs;
+            }
+          }
+        }
+      } else {
+        const float4 q = s_q[w][b];
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+          if (done[k]) continue;
+          ++evals;
+          float dx, dy, d2, e;
+          const float a = gauss_alpha(fx, py0 + 4 * k + 0.5f, q, bp.alpha_max, dx, dy, d2, e);
+          if (a < bp.alpha_min) continue;
+          const float test = T[k] * (1.f - a);
+          if (test < bp.t_min) {
+            done[k] = true;
+            continue;
+          }
+          const float wgt = a * T[k];
+          acc[k][0] = fmaf(cc.x, wgt, acc[k][0]);
+          if (C == 3) {
+            acc[k][1] = fmaf(cc.y, wgt, acc[k][1]);
+            acc[k][2] = fmaf(cc.z, wgt, acc[k][2]);
+          }
+          T[k] = test;
+          last[k] = base + b + 1;
+          lsub[k] = 0;
+          ++contribs;
+        }
+      }
+    }
+    __syncwarp();
+  }
+  count_evals(&st->blend_evals, evals);
+  count_evals(&st->blend_contribs, contribs);
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    const int py = py0 + 4 * k;
+    if (px < bp.W && py < bp.H) {
+      const long long pix = ((long long)s * bp.H + py) * bp.W + px;
+      float* out = image + pix * C;
+      out[0] = acc[k][0] + T[k] * bp.bg0;
+      if (C == 3) {
+        out[1] = acc[k][1] + T[k] * bp.bg1;
+        out[2] = acc[k][2] + T[k] * bp.bg2;
+      }
+      Tfinal[pix] = T[k];
+      nlast[pix] = last[k];
+      la.nsub[pix] = lsub[k];
+    }
+  }
+}
+
+// The adjoint with fill layers.  Per layer entry, the opacity gradients of
+// the grid points the warp's pixels see gather in a per-warp region of
+// shared memory (shared atomics: at grid steps above 1 px neighbouring
+// pixels see the same grid points) and go to the per-Gaussian rows once per
+// layer; the colour gradients of the layer are summed over the warp and added
+// to the curve's.  When every per-Gaussian gradient is asked for, or no
+// per-curve output is given, each composited pair adds its row directly.
+template <int TILE, int PPT, int C>
+__global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE, PPT>::kMinBlocksBwd)
+    k_blend_bwd_layers(const int2* __restrict__ ranges, const uint32_t* __restrict__ gid,
+                       const float4* __restrict__ prep, const float2* __restrict__ reach,
+                       const int* __restrict__ gcurve, const float4* __restrict__ color, BlendParams bp,
+                       LayerArgs la, const float* __restrict__ dimage, const float* __restrict__ Tfinal,
+                       const int* __restrict__ nlast, float* dgauss, DevState* st, int full_grads, float* dcurve) {
+  using Gm = BlendGeom<TILE, PPT>;
+  constexpr int kRow = 8;
+  __shared__ float4 s_q[Gm::kWarps][32];
+  __shared__ float4 s_c[Gm::kWarps][32];
+  __shared__ float s_isig[Gm::kWarps][32];
+  __shared__ uint32_t s_id[Gm::kWarps][32];
+  __shared__ float s_reg[Gm::kWarps][kLayerRegion];
+  int s, px, py0;
+  float4 wr;
+  tile_pixels<TILE, PPT>(bp, s, px, py0, wr);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x - s * bp.tiles_per_scene;
+  const int tx = t % bp.tiles_x, ty = t / bp.tiles_x;
+  const float fx = px + 0.5f;
+  const int2 rg = ranges[blockIdx.x];
+  const bool per_pair = full_grads || dcurve == nullptr;
+  float T[PPT], dI[PPT][3], Bk[PPT][3];
+  int last[PPT], lsub[PPT];
+  int wmax = 0;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    const int py = py0 + 4 * k;
+    T[k] = 1.f;
+    last[k] = 0;
+    lsub[k] = 0;
+    Bk[k][0] = bp.bg0;
+    Bk[k][1] = bp.bg1;
+    Bk[k][2] = bp.bg2;
+    dI[k][0] = dI[k][1] = dI[k][2] = 0.f;
+    if (px < bp.W && py < bp.H) {
+      const long long pix = ((long long)s * bp.H + py) * bp.W + px;
+      T[k] = Tfinal[pix];
+      last[k] = nlast[pix];
+      lsub[k] = la.nsub[pix];
+#pragma unroll
+      for (int ch = 0; ch < C; ++ch) dI[k][ch] = dimage[pix * C + ch];
+    }
+    wmax = max(wmax, last[k]);
+  }
+  for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+  unsigned int evals = 0;
+  for (int base = ((wmax - 1) >> 5) << 5; base >= 0 && wmax > 0; base -= 32) {
+    const int j = base + lane;
+    bool hit = false;
+    if (j < wmax) {
+      const uint32_t g = gid[rg.x + j];
+      const uint32_t gi = g & ~kLayerBit;
+      if (g & kLayerBit) {
+        hit = true;
+        s_id[w][lane] = g;
+        s_c[w][lane] = color[gcurve[gi]];
+      } else {
+        const float4 q = prep[gi];
+        const float2 rs = reach[gi];
+        hit = rect_d2(q.x, q.y, wr.x, wr.y, wr.z, wr.w) <= rs.x;
+        if (hit) {
+          s_q[w][lane] = q;
+          s_c[w][lane] = color[gcurve[gi]];
+          s_isig[w][lane] = rs.y;
+          s_id[w][lane] = g;
+        }
+      }
+    }
+    unsigned int mask = __ballot_sync(0xffffffffu, hit);
+    __syncwarp();
+    while (mask) {
+      const int b = 31 - __clz(mask);
+      mask &= ~(1u << b);
+      const int jpos = base + b;
+      const uint32_t id = s_id[w][b];
+      const float4 cc = s_c[w][b];
+      if (id & kLayerBit) {
+        {
+          // skip an entry no pixel of the warp reaches (each walks up to its last)
+          bool any = false;
+#pragma unroll
+          for (int k = 0; k < PPT; ++k) any = any || jpos < last[k];
+          if (!__any_sync(0xffffffffu, any)) continue;
+        }
+        const int c = gcurve[id & ~kLayerBit];
+        const LayerView v = layer_view(la, c, tx, ty, cc.w);
+        // the warp's region of grid points
+        int rx0 = 0x7fffffff, rx1 = -1, ry0 = 0x7fffffff, ry1 = -1;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+          if (jpos >= last[k]) continue;
+          int ix0, ix1, iy0, iy1;
+          layer_window(v, fx, py0 + 4 * k + 0.5f, ix0, ix1, iy0, iy1);
+          if (ix0 > ix1 || iy0 > iy1) continue;
+          rx0 = min(rx0, ix0);
+          rx1 = max(rx1, ix1);
+          ry0 = min(ry0, iy0);
+          ry1 = max(ry1, iy1);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          rx0 = min(rx0, __shfl_xor_sync(0xffffffffu, rx0, o));
+          rx1 = max(rx1, __shfl_xor_sync(0xffffffffu, rx1, o));
+          ry0 = min(ry0, __shfl_xor_sync(0xffffffffu, ry0, o));
+          ry1 = max(ry1, __shfl_xor_sync(0xffffffffu, ry1, o));
+        }
+        if (rx1 < rx0 || ry1 < ry0) continue;   // the layer misses every pixel of the warp
+        const int rw = rx1 - rx0 + 1, rh = ry1 - ry0 + 1;
+        const bool regional = !per_pair && (long long)rw * rh <= kLayerRegion;
+        if (regional) {
+          for (int i = lane; i < rw * rh; i += 32) s_reg[w][i] = 0.f;
+          __syncwarp();
+        }
+        float col[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+          if (jpos >= last[k]) continue;
+          const float fy = py0 + 4 * k + 0.5f;
+          const int sstart = (jpos == last[k] - 1) ? lsub[k] - 1 : 0x7fffffff;
+          int ix0, ix1, iy0, iy1;
+          layer_window(v, fx, fy, ix0, ix1, iy0, iy1);
+          for (int iy = iy1; iy >= iy0; --iy) {
+            const long long rowg = v.g_off + (long long)iy * v.nx;
+            for (int ix = ix1; ix >= ix0; --ix) {
+              const long long g = rowg + ix;
+              if (g - v.g_off > sstart || g >= v.G) continue;
+              const float4 r = la.rec[g];
+              if (!layer_point_binned(r, bp.alpha_min)) continue;
+              ++evals;
+              const float isg = 1.f / r.z;
+              float dx, dy, d2, e;
+              const float a = gauss_alpha(fx, fy, make_float4(r.x, r.y, r.z == v.sig ? v.nc : ncoef(r.z), r.w),
+                                          bp.alpha_max, dx, dy, d2, e);
+              if (a < bp.alpha_min) continue;
+              T[k] = __fdividef(T[k], 1.f - a);   // transmittance in front of this Gaussian
+              const float wgt = a * T[k];
+              float da = (cc.x - Bk[k][0]) * dI[k][0];
+              float g5 = wgt * dI[k][0], g6 = 0.f, g7 = 0.f;
+              Bk[k][0] = a * cc.x + (1.f - a) * Bk[k][0];
+              if (C == 3) {
+                da += (cc.y - Bk[k][1]) * dI[k][1] + (cc.z - Bk[k][2]) * dI[k][2];
+                g6 = wgt * dI[k][1];
+                g7 = wgt * dI[k][2];
+                Bk[k][1] = a * cc.y + (1.f - a) * Bk[k][1];
+                Bk[k][2] = a * cc.z + (1.f - a) * Bk[k][2];
+              }
+              da *= T[k];
+              const bool uncapped = __fmul_rn(r.w, e) < bp.alpha_max;
+              const float dO = uncapped ? e * da : 0.f;
+              if (!per_pair) {
+                col[0] += g5;
+                col[1] += g6;
+                col[2] += g7;
+                if (dO != 0.f) {
+                  if (regional) atomicAdd(&s_reg[w][(iy - ry0) * rw + (ix - rx0)], dO);
+                  else atomicAdd(dgauss + g * kRow + 4, dO);
+                }
+              } else {
+                if (full_grads && uncapped) {
+                  const float aa = da * a * isg * isg;
+                  red_add_v4(dgauss + g * kRow, aa * dx, aa * dy, aa * d2 * isg, 0.f);
+                }
+                red_add_v4(dgauss + g * kRow + 4, dO, g5, g6, g7);
+              }
+            }
+          }
+        }
+        if (!per_pair) {
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            col[0] += __shfl_xor_sync(0xffffffffu, col[0], o);
+            col[1] += __shfl_xor_sync(0xffffffffu, col[1], o);
+            col[2] += __shfl_xor_sync(0xffffffffu, col[2], o);
+          }
+          if (lane == 0 && (col[0] != 0.f || col[1] != 0.f || col[2] != 0.f))
+            red_add_v4(dcurve + 4 * (long long)c, col[0], col[1], col[2], 0.f);
+        }
+        if (regional) {
+          __syncwarp();
+          for (int i = lane; i < rw * rh; i += 32) {
+            const float val = s_reg[w][i];
+            if (val != 0.f) {
+              const int iy = ry0 + i / rw, ix = rx0 + i % rw;
+              atomicAdd(dgauss + (v.g_off + (long long)iy * v.nx + ix) * kRow + 4, val);
+            }
+          }
+          __syncwarp();
+        }
+      } else {
+        const float4 q = s_q[w][b];
+        const float isg_raw = s_isig[w][b];
+        const bool geo = full_grads || isg_raw > 0.f;
+        const float isg = fabsf(isg_raw);
+        float vv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        bool contrib = false;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+          if (jpos >= last[k]) continue;
+          ++evals;
+          float dx, dy, d2, e;
+          const float a = gauss_alpha(fx, py0 + 4 * k + 0.5f, q, bp.alpha_max, dx, dy, d2, e);
+          if (a < bp.alpha_min) continue;
+          contrib = true;
+          T[k] = __fdividef(T[k], 1.f - a);
+          const float wgt = a * T[k];
+          float da = (cc.x - Bk[k][0]) * dI[k][0];
+          vv[5] += wgt * dI[k][0];
+          Bk[k][0] = a * cc.x + (1.f - a) * Bk[k][0];
+          if (C == 3) {
+            da += (cc.y - Bk[k][1]) * dI[k][1] + (cc.z - Bk[k][2]) * dI[k][2];
+            vv[6] += wgt * dI[k][1];
+            vv[7] += wgt * dI[k][2];
+            Bk[k][1] = a * cc.y + (1.f - a) * Bk[k][1];
+            Bk[k][2] = a * cc.z + (1.f - a) * Bk[k][2];
+          }
+          da *= T[k];
+          if (__fmul_rn(q.w, e) < bp.alpha_max) {
+            vv[4] += e * da;
+            if (geo) {
+              const float aa = da * a * isg * isg;
+              vv[0] += aa * dx;
+              vv[1] += aa * dy;
+              vv[2] += aa * d2 * isg;
+            }
+          }
+        }
+        if (__any_sync(0xffffffffu, contrib)) {
+          const uint32_t gg = id & ~kLayerBit;
+          if (geo) {
+            const float tt = warp_sum8(vv);
+            const float t1 = __shfl_down_sync(0xffffffffu, tt, 4);
+            const float t2 = __shfl_down_sync(0xffffffffu, tt, 8);
+            const float t3 = __shfl_down_sync(0xffffffffu, tt, 12);
+            if ((lane & 15) == 0) red_add_v4(dgauss + (long long)gg * kRow + (lane >> 2), tt, t1, t2, t3);
+          } else {
+            const float tt = warp_sum4(vv + 4);
+            const float t1 = __shfl_down_sync(0xffffffffu, tt, 8);
+            const float t2 = __shfl_down_sync(0xffffffffu, tt, 16);
+            const float t3 = __shfl_down_sync(0xffffffffu, tt, 24);
+            if (lane == 0) red_add_v4(dgauss + (long long)gg * kRow + 4, tt, t1, t2, t3);
+          }
+        }
+      }
+    }
+    __syncwarp();
+  }
+  count_evals(&st->blend_bwd_evals, evals);
+}
+
+// Layer kernels exist for blocks of at most 8 warps (the per-warp regions
+// live in static shared memory): tiles 8 and 16, and tile 32 with 4 pixels
+// per thread.
+static int layer_ppt(int tile, int code) {
+  const int ppt = code & ~NS_BLEND_LANE_GROUPS;
+  if (tile == 32) return 4;
+  if (tile == 8) return ppt >= 2 ? 2 : 1;
+  return ppt == 4 ? 4 : (ppt == 2 ? 2 : 1);
+}
+
+template <int C>
+static void launch_fwd_layers(int tile, int ppt, int grid, cudaStream_t s, const int2* ranges, const uint32_t* gid,
+                              const float4* prep, const float2* reach, const int* gcurve, const float4* col,
+                              const BlendParams& bp, const LayerArgs& la, float* image, float* Tf, int* nl,
+                              DevState* st) {
+#define NS_FWDL(TL, PP)                                                                                   \
+  NS_LAUNCH(NS_KERNEL_BLEND_FWD, (k_blend_fwd_layers<TL, PP, C>), grid, (BlendGeom<TL, PP>::kThreads), 0, s, \
+            ranges, gid, prep, reach, gcurve, col, bp, la, image, Tf, nl, st)
+  if (tile == 8) { if (ppt == 1) NS_FWDL(8, 1); else NS_FWDL(8, 2); }
+  else if (tile == 16) { if (ppt == 1) NS_FWDL(16, 1); else if (ppt == 2) NS_FWDL(16, 2); else NS_FWDL(16, 4); }
+  else NS_FWDL(32, 4);
+#undef NS_FWDL
+}
+
+template <int C>
+static void launch_bwd_layers(int tile, int ppt, int grid, cudaStream_t s, const int2* ranges, const uint32_t* gid,
+                              const float4* prep, const float2* reach, const int* gcurve, const float4* col,
+                              const BlendParams& bp, const LayerArgs& la, const float* dimage, const float* Tf,
+                              const int* nl, float* dgauss, DevState* st, int full_grads, float* dcurve) {
+#define NS_BWDL(TL, PP)                                                                                   \
+  NS_LAUNCH(NS_KERNEL_BLEND_BWD, (k_blend_bwd_layers<TL, PP, C>), grid, (BlendGeom<TL, PP>::kThreads), 0, s, \
+            ranges, gid, prep, reach, gcurve, col, bp, la, dimage, Tf, nl, dgauss, st, full_grads, dcurve)
+  if (tile == 8) { if (ppt == 1) NS_BWDL(8, 1); else NS_BWDL(8, 2); }
+  else if (tile == 16) { if (ppt == 1) NS_BWDL(16, 1); else if (ppt == 2) NS_BWDL(16, 2); else NS_BWDL(16, 4); }
+  else NS_BWDL(32, 4);
+#undef NS_BWDL
+}
+
 // Kernel of a decomposition: whole-warp sub-blocks, or lane groups (PPT 1-2).
 template <int TL, int PP, int C, bool ANISO, bool GRP>
 static auto fwd_kernel() {
@@ -1261,14 +1883,14 @@ template <int C, bool ANISO>
 static void launch_bwd(int tile, int code, int grid, cudaStream_t s, const int2* ranges, const uint32_t* gid,
                        const float4* prep, const float2* prep2, const float2* reach, const int* gcurve,
                        const float4* col, const BlendParams& bp, const float* dimage, const float* Tf, const int* nl,
-                       float* dgauss, DevState* st, int full_grads) {
+                       float* dgauss, DevState* st, int full_grads, float* dcurve) {
   const bool grp = (code & NS_BLEND_LANE_GROUPS) != 0;
   const int ppt = code & ~NS_BLEND_LANE_GROUPS;
 #define NS_BWD(TL, PP)                                                                                 \
   {                                                                                                      \
     auto kern = grp ? bwd_kernel<TL, PP, C, ANISO, true>() : bwd_kernel<TL, PP, C, ANISO, false>();      \
     NS_LAUNCH(NS_KERNEL_BLEND_BWD, kern, grid, (BlendGeom<TL, PP>::kThreads), 0, s, ranges, gid, prep,  \
-              prep2, reach, gcurve, col, bp, dimage, Tf, nl, dgauss, st, full_grads);                   \
+              prep2, reach, gcurve, col, bp, dimage, Tf, nl, dgauss, st, full_grads, dcurve);           \
   }
   if (tile == 8) { if (ppt == 1) NS_BWD(8, 1) else NS_BWD(8, 2) }
   else if (tile == 16) { if (ppt == 1) NS_BWD(16, 1) else if (ppt == 2) NS_BWD(16, 2) else NS_BWD(16, 4) }
@@ -1289,10 +1911,18 @@ struct BlendArgs {
   float* Tf;
   int* nl;
   DevState* st;
+  bool layers;    // fill layers (isotropic sets only)
+  LayerArgs la;
 };
 
 static void dispatch_fwd(int C, bool aniso, int tile, int ppt, int grid, cudaStream_t s, const BlendArgs& a,
                          float* image) {
+  if (a.layers) {
+    const int lp = layer_ppt(tile, ppt);
+    if (C == 3) launch_fwd_layers<3>(tile, lp, grid, s, a.ranges, a.gid, a.prep, a.reach, a.gcurve, a.col, a.bp, a.la, image, a.Tf, a.nl, a.st);
+    else launch_fwd_layers<1>(tile, lp, grid, s, a.ranges, a.gid, a.prep, a.reach, a.gcurve, a.col, a.bp, a.la, image, a.Tf, a.nl, a.st);
+    return;
+  }
   if (C == 3) {
     if (aniso) launch_fwd<3, true>(tile, ppt, grid, s, a.ranges, a.gid, a.prep, a.prep2, a.reach, a.gcurve, a.col, a.bp, image, a.Tf, a.nl, a.st);
     else launch_fwd<3, false>(tile, ppt, grid, s, a.ranges, a.gid, a.prep, a.prep2, a.reach, a.gcurve, a.col, a.bp, image, a.Tf, a.nl, a.st);
@@ -1303,13 +1933,19 @@ static void dispatch_fwd(int C, bool aniso, int tile, int ppt, int grid, cudaStr
 }
 
 static void dispatch_bwd(int C, bool aniso, int tile, int ppt, int grid, cudaStream_t s, const BlendArgs& a,
-                         const float* dimage, float* dgauss, int full_grads) {
+                         const float* dimage, float* dgauss, int full_grads, float* dcurve) {
+  if (a.layers) {
+    const int lp = layer_ppt(tile, ppt);
+    if (C == 3) launch_bwd_layers<3>(tile, lp, grid, s, a.ranges, a.gid, a.prep, a.reach, a.gcurve, a.col, a.bp, a.la, dimage, a.Tf, a.nl, dgauss, a.st, full_grads, dcurve);
+    else launch_bwd_layers<1>(tile, lp, grid, s, a.ranges, a.gid, a.prep, a.reach, a.gcurve, a.col, a.bp, a.la, dimage, a.Tf, a.nl, dgauss, a.st, full_grads, dcurve);
+    return;
+  }
   if (C == 3) {
-    if (aniso) launch_bwd<3, true>(tile, ppt, grid, s, a.ranges, a.gid, a.prep, a.prep2, a.reach, a.gcurve, a.col, a.bp, dimage, a.Tf, a.nl, dgauss, a.st, full_grads);
-    else launch_bwd<3, false>(tile, ppt, grid, s, a.ranges, a.gid, a.prep, a.prep2, a.reach, a.gcurve, a.col, a.bp, dimage, a.Tf, a.nl, dgauss, a.st, full_grads);
+    if (aniso) launch_bwd<3, true>(tile, ppt, grid, s, a.ranges, a.gid, a.prep, a.prep2, a.reach, a.gcurve, a.col, a.bp, dimage, a.Tf, a.nl, dgauss, a.st, full_grads, dcurve);
+    else launch_bwd<3, false>(tile, ppt, grid, s, a.ranges, a.gid, a.prep, a.prep2, a.reach, a.gcurve, a.col, a.bp, dimage, a.Tf, a.nl, dgauss, a.st, full_grads, dcurve);
   } else {
-    if (aniso) launch_bwd<1, true>(tile, ppt, grid, s, a.ranges, a.gid, a.prep, a.prep2, a.reach, a.gcurve, a.col, a.bp, dimage, a.Tf, a.nl, dgauss, a.st, full_grads);
-    else launch_bwd<1, false>(tile, ppt, grid, s, a.ranges, a.gid, a.prep, a.prep2, a.reach, a.gcurve, a.col, a.bp, dimage, a.Tf, a.nl, dgauss, a.st, full_grads);
+    if (aniso) launch_bwd<1, true>(tile, ppt, grid, s, a.ranges, a.gid, a.prep, a.prep2, a.reach, a.gcurve, a.col, a.bp, dimage, a.Tf, a.nl, dgauss, a.st, full_grads, dcurve);
+    else launch_bwd<1, false>(tile, ppt, grid, s, a.ranges, a.gid, a.prep, a.prep2, a.reach, a.gcurve, a.col, a.bp, dimage, a.Tf, a.nl, dgauss, a.st, full_grads, dcurve);
   }
 }
 
@@ -1341,6 +1977,25 @@ static BlendParams blend_params(const Layout& L, const ns_raster_params* rp) {
   bp.tiles_x = L.tiles_x;
   bp.tiles_per_scene = L.tiles_x * L.tiles_y;
   return bp;
+}
+
+// Whether a Gaussian set is binned by fill layers, and what the layer kernels read.
+static bool use_layers(const ns_raster_params* rp, const ns_gaussians* g) {
+  return rp->fill_layers != 0 && g->shape == nullptr;
+}
+
+static LayerArgs layer_args(const Layout& L, const ns_raster_params* rp, const ns_gaussians* g, void* ws) {
+  LayerArgs la;
+  la.plan = at<CurvePlan>(ws, L.o_plan);
+  la.rec = reinterpret_cast<const float4*>(g->rec);
+  la.gcount = g->count;
+  la.gcap = int(L.gcap);
+  la.tile = rp->tile;
+  la.k_sigma = rp->k_sigma;
+  la.inv_tile = 1.f / float(rp->tile);
+  la.log_amin = rp->alpha_min > 0.f ? logf(rp->alpha_min) : -INFINITY;
+  la.nsub = at<int>(ws, L.o_nsub);
+  return la;
 }
 
 static int resolve_ppt(int tile, int ppt) {
@@ -1420,19 +2075,21 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
   bp.tiles_per_scene = L.tiles_x * L.tiles_y;
   bp.n_curves = L.nc;
   bp.gcap = int(L.gcap);
+  bp.fill_layers = use_layers(rp, g) ? 1 : 0;
+  const CurvePlan* plan = at<CurvePlan>(ws, L.o_plan);
   const int bin_blocks = int(L.bin_blocks);
   const bool aniso = g->shape != nullptr;
   const float4* shape = reinterpret_cast<const float4*>(g->shape);
   if (bin_blocks > 0) {
     auto kc = aniso ? &k_bin_count<true> : &k_bin_count<false>;
     NS_LAUNCH(NS_KERNEL_BIN_COUNT, kc, bin_blocks, 256, 0, s, rec, shape, g->curve, curves->flags, g->count, bp, bsum, st,
-              at<float4>(ws, L.o_prep), at<float2>(ws, L.o_prep2), at<float2>(ws, L.o_reach));
+              at<float4>(ws, L.o_prep), at<float2>(ws, L.o_prep2), at<float2>(ws, L.o_reach), plan);
   }
   NS_LAUNCH(NS_KERNEL_SCAN, k_scan_small, 1, 1024, 0, s, bsum, g->count, int(L.gcap), kBinItems, st, cap->pairs);
   if (bin_blocks > 0) {
     auto ke = aniso ? &k_bin_emit<true> : &k_bin_emit<false>;
     NS_LAUNCH(NS_KERNEL_BIN_EMIT, ke, bin_blocks, 256, 0, s, rec, shape, g->curve, g->count, curve_scene, bp, bsum,
-              k0, v0, cap->pairs);
+              k0, v0, cap->pairs, curves->flags, plan);
   }
   const RasterPlan rpn = radix_plan(L.n_tiles);
   const int sort_blocks = int(L.sort_blocks);
@@ -1451,7 +2108,8 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
   cudaMemsetAsync(ranges, 0, sizeof(int2) * (size_t)L.n_tiles, s);
   NS_LAUNCH(NS_KERNEL_RANGES, k_ranges, num_sms() * 16, 256, 0, s, kin, st, ranges);
   const BlendArgs ba{ranges, vin, at<float4>(ws, L.o_prep), at<float2>(ws, L.o_prep2), at<float2>(ws, L.o_reach),
-                     g->curve, reinterpret_cast<const float4*>(curves->color), blend_params(L, rp), Tf, nl, st};
+                     g->curve, reinterpret_cast<const float4*>(curves->color), blend_params(L, rp), Tf, nl, st,
+                     use_layers(rp, g), layer_args(L, rp, g, ws)};
   dispatch_fwd(L.C, aniso, rp->tile, resolve_ppt(rp->tile, rp->ppt_fwd), L.n_tiles, s, ba, image);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -1462,10 +2120,13 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
 }
 
 namespace ns {
-// Blend adjoint, used by splat_backward (ns_backward.cu).
+// Blend adjoint, used by splat_backward (ns_backward.cu).  With full_grads = 0
+// the caller's per-curve colour gradients `dcurve` ({r, g, b, o} per curve,
+// already zeroed or accumulating) may receive the colour gradients of fill
+// Gaussians directly instead of their per-Gaussian rows.
 ns_status launch_blend_bwd(const Layout& L, const ns_curves* curves, const ns_gaussians* g,
                            const ns_raster_params* rp, const float* dimage, float* dgauss, void* ws,
-                           cudaStream_t s, int full_grads) {
+                           cudaStream_t s, int full_grads, float* dcurve) {
   const RasterPlan rpn = radix_plan(L.n_tiles);
   const uint32_t* vsorted = (rpn.passes & 1) ? at<uint32_t>(ws, L.o_v1) : at<uint32_t>(ws, L.o_v0);
   DevState* st = at<DevState>(ws, L.o_state);
@@ -1473,9 +2134,10 @@ ns_status launch_blend_bwd(const Layout& L, const ns_curves* curves, const ns_ga
   cudaMemsetAsync(&st->blend_bwd_visits, 0, sizeof(unsigned long long), s);
   const BlendArgs ba{at<int2>(ws, L.o_ranges), vsorted, at<float4>(ws, L.o_prep), at<float2>(ws, L.o_prep2),
                      at<float2>(ws, L.o_reach), g->curve, reinterpret_cast<const float4*>(curves->color),
-                     blend_params(L, rp), at<float>(ws, L.o_T), at<int>(ws, L.o_nlast), st};
+                     blend_params(L, rp), at<float>(ws, L.o_T), at<int>(ws, L.o_nlast), st,
+                     use_layers(rp, g), layer_args(L, rp, g, ws)};
   dispatch_bwd(L.C, g->shape != nullptr, rp->tile, resolve_ppt(rp->tile, rp->ppt_bwd), L.n_tiles, s, ba, dimage,
-               dgauss, full_grads);
+               dgauss, full_grads, full_grads ? nullptr : dcurve);
   return NS_OK;
 }
 bool raster_params_ok(const ns_raster_params* rp) { return check_raster(rp); }
@@ -1503,19 +2165,26 @@ extern "C" ns_status ns_autotune_blend(const ns_curves* curves, const ns_gaussia
   const int row = aniso ? 12 : 8;
   const BlendArgs ba{at<int2>(ws, L.o_ranges), vsorted, at<float4>(ws, L.o_prep), at<float2>(ws, L.o_prep2),
                      at<float2>(ws, L.o_reach), g->curve, reinterpret_cast<const float4*>(curves->color),
-                     blend_params(L, rp), at<float>(ws, L.o_T), at<int>(ws, L.o_nlast), st};
+                     blend_params(L, rp), at<float>(ws, L.o_T), at<int>(ws, L.o_nlast), st,
+                     use_layers(rp, g), layer_args(L, rp, g, ws)};
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     set_error("ns_autotune_blend: cudaEventCreate failed");
     return NS_ERR_CUDA;
   }
   auto fwd = [&](int ppt) { dispatch_fwd(L.C, aniso, rp->tile, ppt, L.n_tiles, s, ba, image); };
-  auto bwd = [&](int ppt) { dispatch_bwd(L.C, aniso, rp->tile, ppt, L.n_tiles, s, ba, dL_dimage, dg, 0); };
+  // the per-curve colour gradients of the timed adjoint go to the knot-gradient
+  // scratch (at least 11 floats per curve; splat_backward clears it before use)
+  float* dcurve_scratch = at<float>(ws, L.o_dknots);
+  auto bwd = [&](int ppt) {
+    dispatch_bwd(L.C, aniso, rp->tile, ppt, L.n_tiles, s, ba, dL_dimage, dg, 0, dcurve_scratch);
+  };
   auto time_best = [&](bool backward) {
     int best = 0;
     float best_ms = 3.4e38f;
     for (int ppt : {1, 2, 4, 1 | NS_BLEND_LANE_GROUPS, 2 | NS_BLEND_LANE_GROUPS}) {
-      if (!ppt_ok(rp->tile, ppt)) continue;
+      if (!ppt_ok(rp->tile, ppt) && !(ba.layers && ppt == 4)) continue;
+      if (ba.layers && layer_ppt(rp->tile, ppt) != ppt) continue;   // the layer kernels' own settings
       float t = 3.4e38f;
       for (int r = 0; r < repeats + 1; ++r) {   // the first run warms the variant up
         if (backward) cudaMemsetAsync(dg, 0, sizeof(float) * row * (size_t)L.gcap, s);

@@ -265,6 +265,7 @@ __global__ void __launch_bounds__(kPlanThreads, 7) k_plan(ns_curves cv, ns_sampl
     pl.b = b;
     pl.x0 = pl.y0 = 0.f;
     pl.nx = pl.ny = 0;
+    pl.h = 0.f;
     if (cr.filled) {
       pl.kind = kFill;
       pl.M = max(3, int(ceilf(sp.delta_b * L)));
@@ -385,6 +386,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_boundary(ns_curves cv, ns_samp
     plan[c].y0 = y0;
     plan[c].nx = nx;
     plan[c].ny = ny;
+    plan[c].h = sp.h;
     plan[c].count = nx * ny;   // counted even when the polyline overflowed (sizing)
   }
 }

@@ -45,6 +45,7 @@ def raster_params(d: dict) -> B.NsRasterParams:
         r.bg[i] = float(d["bg"][i])
     r.ppt_fwd = int(d.get("ppt_fwd", 0))
     r.ppt_bwd = int(d.get("ppt_bwd", 0))
+    r.fill_layers = int(d.get("fill_layers", 0))
     return r
 
 

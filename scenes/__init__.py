@@ -395,17 +395,19 @@ def from_curves(curves, height, width, channels=3, sample=None, raster=None, nam
 
 def small_closed(seed, n_curves=3, size=48, filled=True, h=2.0, degrees=(2, 3, 4, 5), n_scenes=1,
                  width=(1.0, 3.0), height=None):
-    """Small closed (filled or stroked) scenes for parity tests."""
+    """Small closed (filled or stroked) scenes for parity tests; filled =
+    "alternate" makes every second path a stroke."""
     rng = np.random.default_rng(seed)
     H = height or size
     W = size
     b = _Builder(n_scenes, H, W, 3)
     for s in range(n_scenes):
-        for _ in range(n_curves):
+        for i in range(n_curves):
             p = int(rng.choice(degrees))
             nk = int(rng.integers(max(p, 6), 12))
             r = rng.uniform(0.15, 0.3) * min(W, H)
             cx, cy = rng.uniform(0.3 * W, 0.7 * W), rng.uniform(0.3 * H, 0.7 * H)
-            _closed_path(rng, b, s, cx, cy, r, p, nk, filled, *width)
+            fill = (i % 2 == 0) if filled == "alternate" else filled
+            _closed_path(rng, b, s, cx, cy, r, p, nk, fill, *width)
     tgt = blob_target(rng, n_scenes, H, W, 3, 6)
     return b.build("small-closed", tgt, dict(SAMPLE_DEFAULTS, h=h, delta_c=2.0), dict(RASTER_PARITY))

@@ -1,0 +1,100 @@
+"""Fill layers (ns_raster_params.fill_layers = 1): the Gaussians of a filled
+curve are binned as one tile pair per tile of the whole grid, and the blend
+kernels find the grid points that reach each pixel by index arithmetic.
+
+Every pixel composites the same Gaussians in the same order with the same
+arithmetic as with one pair per Gaussian, so the image must be bit-identical
+to the per-Gaussian path's at every tile size and decomposition.  Gradients
+differ only in the order of float additions (1e-5 of their norm), and the
+whole step is checked against the oracle (1e-3)."""
+import numpy as np
+import pytest
+import torch
+
+import scenes
+from oracle import pipeline as op
+
+from gpu_util import run_scene, run_step
+
+pytestmark = pytest.mark.gpu
+
+SCENES = [
+    ("filled-h1-production", lambda: scenes.small_closed(331, n_curves=3, size=70, filled=True, h=1.0, height=53)
+     .with_raster(**scenes.RASTER_DEFAULTS)),
+    ("filled-h2-parity", lambda: scenes.small_closed(332, n_curves=3, size=64, filled=True, h=2.0)),
+    ("fills-and-strokes-production", lambda: scenes.small_closed(333, n_curves=4, size=60, filled="alternate",
+                                                                 h=1.0).with_raster(**scenes.RASTER_DEFAULTS)),
+    ("fills-and-strokes-parity", lambda: scenes.small_closed(334, n_curves=4, size=52, filled="alternate", h=1.5)),
+    ("batched-h1", lambda: scenes.small_closed(335, n_curves=3, size=44, filled=True, h=1.0, n_scenes=3)
+     .with_raster(**scenes.RASTER_DEFAULTS)),
+    ("coarse-grid-h6", lambda: scenes.small_closed(336, n_curves=2, size=72, filled=True, h=6.0)
+     .with_raster(**scenes.RASTER_DEFAULTS)),
+    ("open-strokes-only", lambda: scenes.small_open(337, n_curves=3, size=48, p=(2, 3, 5))),
+]
+DECOMP = [(8, 1), (8, 2), (16, 1), (16, 2), (16, 4), (32, 4), (32, 1)]
+
+
+def _rel(a, b):
+    a = np.asarray(a, np.float64).reshape(-1)
+    b = np.asarray(b, np.float64).reshape(-1)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+
+
+@pytest.mark.parametrize("name,make", SCENES, ids=[s[0] for s in SCENES])
+def test_layers_match_per_gaussian_pairs(name, make):
+    sc = make()
+    for tile, ppt in DECOMP:
+        base = run_step(sc.with_raster(tile=tile, ppt_fwd=ppt, ppt_bwd=ppt, fill_layers=0))
+        lay = run_step(sc.with_raster(tile=tile, ppt_fwd=ppt, ppt_bwd=ppt, fill_layers=1))
+        assert base["report"].status == 0 and lay["report"].status == 0
+        assert np.array_equal(lay["image"], base["image"]), (tile, ppt)
+        assert lay["report"].blend_contribs == base["report"].blend_contribs
+        assert lay["report"].pairs <= base["report"].pairs
+        for nm in ("dkey", "dtau", "dcolor"):
+            assert _rel(lay[nm], base[nm]) <= 1e-5, (tile, ppt, nm)
+
+
+@pytest.mark.parametrize("name,make", SCENES[:4], ids=[s[0] for s in SCENES[:4]])
+def test_layers_per_gaussian_rows(name, make):
+    """Without the chain the adjoint returns every per-Gaussian row."""
+    sc = make()
+    rows = {}
+    for fl in (0, 1):
+        s2 = sc.with_raster(tile=8, fill_layers=fl)
+        sp, img, rep, (k, t, c), G = run_scene(s2)
+        dimg = np.random.default_rng(338).standard_normal(tuple(img.shape)).astype(np.float32)
+        sp.backward(k, t, c, torch.as_tensor(dimg, device="cuda"), chain=False)
+        torch.cuda.synchronize()
+        rows[fl] = sp.dgauss[:G].cpu().numpy().astype(np.float64)
+    scale = max(np.abs(rows[0]).max(), 1e-30)
+    assert np.abs(rows[1] - rows[0]).max() <= 1e-5 * scale
+
+
+@pytest.mark.parametrize("tile", [8, 16])
+def test_layers_step_matches_oracle(tile):
+    sc = scenes.small_closed(321, n_curves=3, size=48, filled=True, h=2.0).with_raster(tile=tile, fill_layers=1)
+    ref = op.loss_and_grads(sc)
+    assert all(p.well_separated() for p in ref["plans"])
+    out = run_step(sc)
+    assert out["report"].status == 0
+    assert abs(out["loss"] - ref["loss"]) <= 1e-4 * ref["loss"] + 1e-7
+    for nm in ("dcolor", "dtau"):
+        assert _rel(out[nm], ref[nm]) <= 1e-3, nm
+    for j in range(4):
+        assert _rel(out["dkey"][:, j], ref["dkey"][:, j]) <= 1e-3
+
+
+def test_tangent_aligned_sets_keep_per_gaussian_pairs():
+    """Tangent-aligned sets are binned per Gaussian whatever fill_layers says."""
+    sc = scenes.small_closed(339, n_curves=4, size=52, filled="alternate", h=2.0).with_sample(contour_mode=1)
+    a = run_step(sc.with_raster(tile=8, fill_layers=0))
+    b = run_step(sc.with_raster(tile=8, fill_layers=1))
+    assert np.array_equal(a["image"], b["image"])
+    assert a["report"].pairs == b["report"].pairs
+
+
+def test_layers_need_far_fewer_pairs():
+    sc = scenes.small_closed(331, n_curves=3, size=70, filled=True, h=1.0).with_raster(**scenes.RASTER_DEFAULTS)
+    a = run_step(sc.with_raster(tile=8, fill_layers=0))
+    b = run_step(sc.with_raster(tile=8, fill_layers=1))
+    assert b["report"].pairs * 20 < a["report"].pairs

@@ -80,6 +80,9 @@ STEPS = [
     ("filled", lambda: scenes.small_closed(321, n_curves=3, size=48, filled=True, h=2.0)),
     ("open", lambda: scenes.small_open(312, n_curves=3, size=48, p=(2, 3, 5))),
     ("filled-h1-batched", lambda: scenes.small_closed(55, n_curves=2, size=40, filled=True, h=1.0, n_scenes=2)),
+    ("fills-and-strokes", lambda: scenes.small_closed(322, n_curves=4, size=52, filled="alternate", h=1.0)),
+    ("tangent-aligned-mixed", lambda: scenes.small_closed(323, n_curves=4, size=52, filled="alternate", h=2.0)
+     .with_sample(contour_mode=1, delta_c=0.8)),
 ]
 
 
@@ -93,6 +96,11 @@ def test_step_with_groups_matches_oracle(name, make, tile, ppt):
     assert out["report"].status == 0
     base = run_step(sc.with_raster(ppt_fwd=ppt, ppt_bwd=ppt))
     assert np.array_equal(out["image"], base["image"])
+    # against the whole-warp kernels: only the order of the float atomics differs
+    for nm in ("dkey", "dtau", "dcolor"):
+        a = np.asarray(out[nm], np.float64)
+        b = np.asarray(base[nm], np.float64)
+        assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b) + 1e-12, nm
     assert abs(out["loss"] - ref["loss"]) <= 1e-4 * ref["loss"] + 1e-7
     assert _rel_ok(out["dcolor"], ref["dcolor"]), "dcolor"
     assert _rel_ok(out["dtau"], ref["dtau"]), "dtau"
