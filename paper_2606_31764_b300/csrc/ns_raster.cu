@@ -1280,32 +1280,36 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
 // Fill layers (ns_raster_params.fill_layers, isotropic sets).  The Gaussians
 // of a filled curve sit on its grid (§3.3): record g_off + iy nx + ix is grid
 // point (ix, iy), and all share one sigma.  The binning then emits one pair
-// per tile of the whole layer (value g_off | kLayerBit).  On such an entry
-// each lane walks, in sample order, the grid points that can reach its pixel:
+// per tile of the whole layer (value g_off | kLayerBit).  On such an entry a
+// pixel composites, in sample order, the grid points that can reach it:
 //   - the columns and rows whose bin rectangle covers this tile, by the exact
-//     float32 rule of tile_rect (the Gaussians per-Gaussian pairs would list),
+//     float32 rule of tile_rect (the Gaussians per-Gaussian pairs would list);
+//     k_layer_runs finds these runs once per forward, per curve and tile
+//     column or row;
 //   - narrowed, when alpha_min > 0, to |q - p| <= R per axis, R the reach of
-//     the layer's most opaque Gaussian (beyond it alpha < alpha_min),
+//     the layer's most opaque Gaussian (beyond it alpha < alpha_min);
 //   - skipping the grid points tile_rect would not bin (culled opacity).
 // A pixel thus composites exactly the Gaussians, in the order and with the
 // arithmetic of the per-Gaussian lists, and the image is the same bit for
-// bit.  The adjoint also needs, per pixel, the sample index of the last
-// composited Gaussian inside its layer (nsub) besides the list position.
-
-constexpr int kLayerRegion = 512;   // floats of a warp's opacity-gradient region per layer
+// bit.  Each warp stages the records of the grid points its pixels can see
+// (its region) in shared memory with coalesced loads, culled points marked,
+// and skips a layer whose region holds no live point.  The adjoint also
+// needs, per pixel, the sample index of the last composited Gaussian inside
+// its layer (nsub) besides the list position.
 
 struct LayerArgs {
   const CurvePlan* plan;
   const float4* rec;
   const int* gcount;
-  int gcap, tile;
+  const int2* runs;   // per curve: covered column run per tile column, then row run per tile row
+  int gcap, tile, tiles_x, runs_stride;
   float k_sigma, inv_tile, log_amin;
   int* nsub;   // per pixel: 1 + sample index of the last composited fill Gaussian (0: none)
 };
 
 // One layer as a warp sees it on one tile (the same in every lane).
 struct LayerView {
-  long long g_off, G;   // first Gaussian; Gaussians in the set (the walk never reads past G)
+  long long g_off, G;   // first Gaussian; Gaussians in the set (nothing at or past G is read)
   int nx, ny;
   float x0, y0, inv_h, sig, nc, R;
   int cx0, cx1, cy0, cy1;   // columns and rows binned to this tile (empty when cx0 > cx1)
@@ -1345,6 +1349,46 @@ __device__ __forceinline__ void covered_run(int n, float guess, F ok, int& lo, i
   while (hi + 1 < n && ok(hi + 1)) ++hi;
 }
 
+// One block per curve: for each tile column (row) of a fill layer's tile
+// rectangle, the run of grid columns (rows) the bin rule puts on it.
+__global__ void __launch_bounds__(128) k_layer_runs(ns_curves cv, const CurvePlan* __restrict__ plan,
+                                                    const float4* __restrict__ rec, const int* __restrict__ gcount,
+                                                    BinParams bp, int2* runs, int stride) {
+  const int c = blockIdx.x;
+  if (!(cv.flags[c] & NS_FILLED)) return;
+  const CurvePlan p = plan[c];
+  const long long G = min((long long)*gcount, (long long)bp.gcap);
+  if (p.g_off < 0 || p.g_off >= G || p.count <= 0 || p.nx <= 0 || p.ny <= 0 || !(p.h > 0.f)) return;
+  int tx0, ty0, ntx;
+  const long long g1 = min((long long)p.g_off + p.count, G) - 1;
+  const int nt = layer_rect(rec, p.g_off, g1, bp, tx0, ty0, ntx);
+  if (!nt) return;
+  const int nty = nt / ntx;
+  const float ks = __fmul_rn(bp.k_sigma, rec[p.g_off].z);
+  const float inv_h = 1.f / p.h, T = 1.f / bp.inv_tile;
+  const long long lastg = G - 1;
+  int2* out = runs + (long long)c * stride;
+  for (int k = threadIdx.x; k < ntx + nty; k += blockDim.x) {
+    int lo, hi;
+    if (k < ntx) {
+      const int tx = tx0 + k;
+      covered_run(p.nx, (tx * T - ks - p.x0) * inv_h - 0.5f,
+                  [&](int ix) { return bin_covers(rec[min((long long)p.g_off + ix, lastg)].x, ks, bp.inv_tile, tx); },
+                  lo, hi);
+      out[tx] = make_int2(lo, hi);
+    } else {
+      const int ty = ty0 + (k - ntx);
+      covered_run(p.ny, (ty * T - ks - p.y0) * inv_h - 0.5f,
+                  [&](int iy) {
+                    return bin_covers(rec[min((long long)p.g_off + (long long)iy * p.nx, lastg)].y, ks,
+                                      bp.inv_tile, ty);
+                  },
+                  lo, hi);
+      out[bp.tiles_x + ty] = make_int2(lo, hi);
+    }
+  }
+}
+
 __device__ __forceinline__ LayerView layer_view(const LayerArgs& la, int c, int tx, int ty, float o_c) {
   LayerView v;
   const CurvePlan p = la.plan[c];
@@ -1360,21 +1404,15 @@ __device__ __forceinline__ LayerView layer_view(const LayerArgs& la, int c, int 
   v.sig = v.nc = v.R = 0.f;
   if (v.g_off < 0 || v.g_off >= v.G || v.nx <= 0 || v.ny <= 0 || !(p.h > 0.f) || !(o_c > 0.f)) return v;
   v.inv_h = 1.f / p.h;
-  const float4 r0 = la.rec[v.g_off];
-  v.sig = r0.z;
-  v.nc = ncoef(r0.z);
-  v.R = la.log_amin > -1e30f ? sqrtf(reach2(r0.z, o_c, la.log_amin)) + 0.01f * p.h : FLT_MAX;
-  const float ks = __fmul_rn(la.k_sigma, r0.z);
-  const long long lastg = v.G - 1;
-  const float T = float(la.tile);
-  covered_run(v.nx, (tx * T - ks - v.x0) * v.inv_h - 0.5f,
-              [&](int ix) { return bin_covers(la.rec[min(v.g_off + ix, lastg)].x, ks, la.inv_tile, tx); },
-              v.cx0, v.cx1);
-  covered_run(v.ny, (ty * T - ks - v.y0) * v.inv_h - 0.5f,
-              [&](int iy) {
-                return bin_covers(la.rec[min(v.g_off + (long long)iy * v.nx, lastg)].y, ks, la.inv_tile, ty);
-              },
-              v.cy0, v.cy1);
+  v.sig = la.rec[v.g_off].z;
+  v.nc = ncoef(v.sig);
+  v.R = la.log_amin > -1e30f ? sqrtf(reach2(v.sig, o_c, la.log_amin)) + 0.01f * p.h : FLT_MAX;
+  const int2* r = la.runs + (long long)c * la.runs_stride;
+  const int2 rx = r[tx], ry = r[la.tiles_x + ty];
+  v.cx0 = rx.x;
+  v.cx1 = rx.y;
+  v.cy0 = ry.x;
+  v.cy1 = ry.y;
   return v;
 }
 
@@ -1399,6 +1437,71 @@ __device__ __forceinline__ bool layer_point_binned(const float4& r, float alpha_
   return r.z > 0.f && r.w > 0.f && r.w >= alpha_min;
 }
 
+// The warp's region of a layer: the union of the windows of the pixels that
+// take part (want[k]), identical in every lane; false if empty.
+template <int PPT>
+__device__ __forceinline__ bool layer_region(const LayerView& v, float fx, int py0, const bool want[PPT], int& rx0,
+                                             int& rx1, int& ry0, int& ry1) {
+  rx0 = 0x7fffffff;
+  rx1 = -1;
+  ry0 = 0x7fffffff;
+  ry1 = -1;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    if (!want[k]) continue;
+    int ix0, ix1, iy0, iy1;
+    layer_window(v, fx, py0 + 4 * k + 0.5f, ix0, ix1, iy0, iy1);
+    if (ix0 > ix1 || iy0 > iy1) continue;
+    rx0 = min(rx0, ix0);
+    rx1 = max(rx1, ix1);
+    ry0 = min(ry0, iy0);
+    ry1 = max(ry1, iy1);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    rx0 = min(rx0, __shfl_xor_sync(0xffffffffu, rx0, o));
+    rx1 = max(rx1, __shfl_xor_sync(0xffffffffu, rx1, o));
+    ry0 = min(ry0, __shfl_xor_sync(0xffffffffu, ry0, o));
+    ry1 = max(ry1, __shfl_xor_sync(0xffffffffu, ry1, o));
+  }
+  return rx1 >= rx0 && ry1 >= ry0;
+}
+
+// Stages the region's points as the blend constants {mu_x, mu_y, ncoef, o}
+// the per-Gaussian binning would prepare; points it would not bin get
+// o = -1.  Returns whether any point is live (the same in every lane).
+__device__ __forceinline__ bool layer_stage(const LayerArgs& la, const LayerView& v, int rx0, int ry0, int rw,
+                                            int rh, float alpha_min, float4* pts) {
+  const int lane = threadIdx.x & 31;
+  const int npt = rw * rh;
+  const float inv_rw = 1.f / float(rw);
+  bool live = false;
+  for (int i = lane; i < npt; i += 32) {
+    int iyr = int((float(i) + 0.5f) * inv_rw);   // exact for the region sizes staged here
+    int ixr = i - iyr * rw;
+    const long long g = v.g_off + (long long)(ry0 + iyr) * v.nx + (rx0 + ixr);
+    float4 q = make_float4(0.f, 0.f, 0.f, -1.f);
+    if (g < v.G) {
+      const float4 r = la.rec[g];
+      if (layer_point_binned(r, alpha_min)) {
+        q = make_float4(r.x, r.y, r.z == v.sig ? v.nc : ncoef(r.z), r.w);
+        live = true;
+      }
+    }
+    pts[i] = q;
+  }
+  return __any_sync(0xffffffffu, live);
+}
+
+template <int TILE, int PPT>
+struct LayerGeom {
+  // staged points per warp; the forward and the adjoint share a budget of
+  // shared memory per block that keeps every instantiation under 48 KB
+  static constexpr int kPts = BlendGeom<TILE, PPT>::kWarps <= 2 ? 256 : 192;
+  // the adjoint keeps more live state per pixel than the forward: 768
+  // resident threads leave it up to 85 registers instead of spilling
+  static constexpr int kMinBlocksBwd = 768 / BlendGeom<TILE, PPT>::kThreads;
+};
+
 template <int TILE, int PPT, int C>
 __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE, PPT>::kMinBlocks)
     k_blend_fwd_layers(const int2* __restrict__ ranges, const uint32_t* __restrict__ gid,
@@ -1406,9 +1509,11 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
                        const int* __restrict__ gcurve, const float4* __restrict__ color, BlendParams bp,
                        LayerArgs la, float* image, float* Tfinal, int* nlast, DevState* st) {
   using Gm = BlendGeom<TILE, PPT>;
+  constexpr int kPts = LayerGeom<TILE, PPT>::kPts;
   __shared__ float4 s_q[Gm::kWarps][32];
   __shared__ float4 s_c[Gm::kWarps][32];
   __shared__ uint32_t s_id[Gm::kWarps][32];
+  __shared__ float4 s_pt[Gm::kWarps][kPts];
   int s, px, py0;
   float4 wr;
   tile_pixels<TILE, PPT>(bp, s, px, py0, wr);
@@ -1437,6 +1542,28 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
     return d;
   };
   unsigned int evals = 0, contribs = 0;
+  // composite one Gaussian (blend constants q) into pixel k; false once the pixel is done
+  auto composite = [&](int k, float fy, const float4& q, const float4& cc, int pos, int sub) {
+    ++evals;
+    float dx, dy, d2, e;
+    const float a = gauss_alpha(fx, fy, q, bp.alpha_max, dx, dy, d2, e);
+    if (a < bp.alpha_min) return;
+    const float test = T[k] * (1.f - a);
+    if (test < bp.t_min) {
+      done[k] = true;
+      return;
+    }
+    const float wgt = a * T[k];
+    acc[k][0] = fmaf(cc.x, wgt, acc[k][0]);
+    if (C == 3) {
+      acc[k][1] = fmaf(cc.y, wgt, acc[k][1]);
+      acc[k][2] = fmaf(cc.z, wgt, acc[k][2]);
+    }
+    T[k] = test;
+    last[k] = pos;
+    lsub[k] = sub;
+    ++contribs;
+  };
   for (int base = 0; base < n && !__all_sync(0xffffffffu, all_done()); base += 32) {
     const int j = base + lane;
     bool hit = false;
@@ -1465,8 +1592,23 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
       const uint32_t id = s_id[w][b];
       const float4 cc = s_c[w][b];
       if (id & kLayerBit) {
-        if (all_done()) continue;
+        bool want[PPT];
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) want[k] = !done[k];
+        if (!__any_sync(0xffffffffu, !all_done())) break;
         const LayerView v = layer_view(la, gcurve[id & ~kLayerBit], tx, ty, cc.w);
+        int rx0, rx1, ry0, ry1;
+        if (!layer_region<PPT>(v, fx, py0, want, rx0, rx1, ry0, ry1)) continue;
+        const int rw = rx1 - rx0 + 1, rh = ry1 - ry0 + 1;
+        const bool staged = (long long)rw * rh <= kPts;
+        if (staged) {
+          const bool live = layer_stage(la, v, rx0, ry0, rw, rh, bp.alpha_min, s_pt[w]);
+          __syncwarp();
+          if (!live) {
+            __syncwarp();
+            continue;
+          }
+        }
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
           if (done[k]) continue;
@@ -1474,59 +1616,30 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
           int ix0, ix1, iy0, iy1;
           layer_window(v, fx, fy, ix0, ix1, iy0, iy1);
           for (int iy = iy0; iy <= iy1 && !done[k]; ++iy) {
-            const long long rowg = v.g_off + (long long)iy * v.nx;
-            for (int ix = ix0; ix <= ix1; ++ix) {
-              const long long g = rowg + ix;
-              if (g >= v.G) break;
-              const float4 r = la.rec[g];
-              if (!layer_point_binned(r, bp.alpha_min)) continue;
-              ++evals;
-              float dx, dy, d2, e;
-              const float a = gauss_alpha(fx, fy, make_float4(r.x, r.y, r.z == v.sig ? v.nc : ncoef(r.z), r.w),
-                                          bp.alpha_max, dx, dy, d2, e);
-              if (a < bp.alpha_min) continue;
-              const float test = T[k] * (1.f - a);
-              if (test < bp.t_min) {
-                done[k] = true;
-                break;
+            const int rowsub = iy * v.nx;
+            for (int ix = ix0; ix <= ix1 && !done[k]; ++ix) {
+              float4 q;
+              if (staged) {
+                q = s_pt[w][(iy - ry0) * rw + (ix - rx0)];
+                if (q.w < 0.f) continue;
+              } else {
+                const long long g = v.g_off + rowsub + ix;
+                if (g >= v.G) break;
+                const float4 r = la.rec[g];
+                if (!layer_point_binned(r, bp.alpha_min)) continue;
+                q = make_float4(r.x, r.y, r.z == v.sig ? v.nc : ncoef(r.z), r.w);
               }
-              const float wgt = a * T[k];
-              acc[k][0] = fmaf(cc.x, wgt, acc[k][0]);
-              if (C == 3) {
-                acc[k][1] = fmaf(cc.y, wgt, acc[k][1]);
-                acc[k][2] = fmaf(cc.z, wgt, acc[k][2]);
-              }
-              T[k] = test;
-              last[k] = base + b + 1;
-              lsub[k] = int(g - v.g_off) + 1;
-              ++contribs;
+              composite(k, fy, q, cc, base + b + 1, rowsub + ix + 1);
             }
           }
         }
+        if (staged) __syncwarp();
       } else {
         const float4 q = s_q[w][b];
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
           if (done[k]) continue;
-          ++evals;
-          float dx, dy, d2, e;
-          const float a = gauss_alpha(fx, py0 + 4 * k + 0.5f, q, bp.alpha_max, dx, dy, d2, e);
-          if (a < bp.alpha_min) continue;
-          const float test = T[k] * (1.f - a);
-          if (test < bp.t_min) {
-            done[k] = true;
-            continue;
-          }
-          const float wgt = a * T[k];
-          acc[k][0] = fmaf(cc.x, wgt, acc[k][0]);
-          if (C == 3) {
-            acc[k][1] = fmaf(cc.y, wgt, acc[k][1]);
-            acc[k][2] = fmaf(cc.z, wgt, acc[k][2]);
-          }
-          T[k] = test;
-          last[k] = base + b + 1;
-          lsub[k] = 0;
-          ++contribs;
+          composite(k, py0 + 4 * k + 0.5f, q, cc, base + b + 1, 0);
         }
       }
     }
@@ -1552,15 +1665,16 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
   }
 }
 
-// The adjoint with fill layers.  Per layer entry, the opacity gradients of
-// the grid points the warp's pixels see gather in a per-warp region of
-// shared memory (shared atomics: at grid steps above 1 px neighbouring
-// pixels see the same grid points) and go to the per-Gaussian rows once per
-// layer; the colour gradients of the layer are summed over the warp and added
-// to the curve's.  When every per-Gaussian gradient is asked for, or no
-// per-curve output is given, each composited pair adds its row directly.
+// The adjoint with fill layers.  Per layer entry the warp stages its region
+// as the forward does; the opacity gradients of its grid points gather in a
+// per-warp array of shared memory (shared atomics: at grid steps above 1 px
+// neighbouring pixels see the same grid points) and go to the per-Gaussian
+// rows once per layer, and the colour gradients of the layer are summed over
+// the warp and added to the curve's.  When every per-Gaussian gradient is
+// asked for, no per-curve output is given, or the region is too large to
+// stage, each composited pair reads its record and adds its row directly.
 template <int TILE, int PPT, int C>
-__global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE, PPT>::kMinBlocksBwd)
+__global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE, PPT>::kMinBlocksBwd)
     k_blend_bwd_layers(const int2* __restrict__ ranges, const uint32_t* __restrict__ gid,
                        const float4* __restrict__ prep, const float2* __restrict__ reach,
                        const int* __restrict__ gcurve, const float4* __restrict__ color, BlendParams bp,
@@ -1568,11 +1682,13 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
                        const int* __restrict__ nlast, float* dgauss, DevState* st, int full_grads, float* dcurve) {
   using Gm = BlendGeom<TILE, PPT>;
   constexpr int kRow = 8;
+  constexpr int kPts = LayerGeom<TILE, PPT>::kPts;
   __shared__ float4 s_q[Gm::kWarps][32];
   __shared__ float4 s_c[Gm::kWarps][32];
   __shared__ float s_isig[Gm::kWarps][32];
   __shared__ uint32_t s_id[Gm::kWarps][32];
-  __shared__ float s_reg[Gm::kWarps][kLayerRegion];
+  __shared__ float4 s_pt[Gm::kWarps][kPts];
+  __shared__ float s_reg[Gm::kWarps][kPts];
   int s, px, py0;
   float4 wr;
   tile_pixels<TILE, PPT>(bp, s, px, py0, wr);
@@ -1607,6 +1723,34 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
   }
   for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
   unsigned int evals = 0;
+  // the adjoint of one pair of pixel k (blend constants q, colour cc):
+  // returns false below alpha_min; else the opacity gradient dO, the colour
+  // gradient col and, for the centre and sigma, da a and the offsets
+  auto adjoint = [&](int k, float fy, const float4& q, const float4& cc, float& dO, float col[3], float& daa,
+                     float& dx, float& dy, float& d2) {
+    ++evals;
+    float e;
+    const float a = gauss_alpha(fx, fy, q, bp.alpha_max, dx, dy, d2, e);
+    if (a < bp.alpha_min) return false;
+    T[k] = __fdividef(T[k], 1.f - a);   // transmittance in front of this Gaussian
+    const float wgt = a * T[k];
+    float da = (cc.x - Bk[k][0]) * dI[k][0];
+    col[0] = wgt * dI[k][0];
+    col[1] = col[2] = 0.f;
+    Bk[k][0] = a * cc.x + (1.f - a) * Bk[k][0];
+    if (C == 3) {
+      da += (cc.y - Bk[k][1]) * dI[k][1] + (cc.z - Bk[k][2]) * dI[k][2];
+      col[1] = wgt * dI[k][1];
+      col[2] = wgt * dI[k][2];
+      Bk[k][1] = a * cc.y + (1.f - a) * Bk[k][1];
+      Bk[k][2] = a * cc.z + (1.f - a) * Bk[k][2];
+    }
+    da *= T[k];
+    const bool uncapped = __fmul_rn(q.w, e) < bp.alpha_max;
+    dO = uncapped ? e * da : 0.f;
+    daa = uncapped ? da * a : 0.f;
+    return true;
+  };
   for (int base = ((wmax - 1) >> 5) << 5; base >= 0 && wmax > 0; base -= 32) {
     const int j = base + lane;
     bool hit = false;
@@ -1638,91 +1782,70 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
       const uint32_t id = s_id[w][b];
       const float4 cc = s_c[w][b];
       if (id & kLayerBit) {
-        {
-          // skip an entry no pixel of the warp reaches (each walks up to its last)
-          bool any = false;
+        bool want[PPT], any = false;
 #pragma unroll
-          for (int k = 0; k < PPT; ++k) any = any || jpos < last[k];
-          if (!__any_sync(0xffffffffu, any)) continue;
+        for (int k = 0; k < PPT; ++k) {
+          want[k] = jpos < last[k];
+          any = any || want[k];
         }
+        if (!__any_sync(0xffffffffu, any)) continue;   // no pixel of the warp walks this far back
         const int c = gcurve[id & ~kLayerBit];
         const LayerView v = layer_view(la, c, tx, ty, cc.w);
-        // the warp's region of grid points
-        int rx0 = 0x7fffffff, rx1 = -1, ry0 = 0x7fffffff, ry1 = -1;
-#pragma unroll
-        for (int k = 0; k < PPT; ++k) {
-          if (jpos >= last[k]) continue;
-          int ix0, ix1, iy0, iy1;
-          layer_window(v, fx, py0 + 4 * k + 0.5f, ix0, ix1, iy0, iy1);
-          if (ix0 > ix1 || iy0 > iy1) continue;
-          rx0 = min(rx0, ix0);
-          rx1 = max(rx1, ix1);
-          ry0 = min(ry0, iy0);
-          ry1 = max(ry1, iy1);
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          rx0 = min(rx0, __shfl_xor_sync(0xffffffffu, rx0, o));
-          rx1 = max(rx1, __shfl_xor_sync(0xffffffffu, rx1, o));
-          ry0 = min(ry0, __shfl_xor_sync(0xffffffffu, ry0, o));
-          ry1 = max(ry1, __shfl_xor_sync(0xffffffffu, ry1, o));
-        }
-        if (rx1 < rx0 || ry1 < ry0) continue;   // the layer misses every pixel of the warp
+        int rx0, rx1, ry0, ry1;
+        if (!layer_region<PPT>(v, fx, py0, want, rx0, rx1, ry0, ry1)) continue;
         const int rw = rx1 - rx0 + 1, rh = ry1 - ry0 + 1;
-        const bool regional = !per_pair && (long long)rw * rh <= kLayerRegion;
-        if (regional) {
+        const bool staged = !per_pair && (long long)rw * rh <= kPts;
+        if (staged) {
           for (int i = lane; i < rw * rh; i += 32) s_reg[w][i] = 0.f;
+          const bool live = layer_stage(la, v, rx0, ry0, rw, rh, bp.alpha_min, s_pt[w]);
           __syncwarp();
+          if (!live) {
+            __syncwarp();
+            continue;
+          }
         }
-        float col[3] = {0.f, 0.f, 0.f};
+        float csum[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
-          if (jpos >= last[k]) continue;
+          if (!want[k]) continue;
           const float fy = py0 + 4 * k + 0.5f;
           const int sstart = (jpos == last[k] - 1) ? lsub[k] - 1 : 0x7fffffff;
           int ix0, ix1, iy0, iy1;
           layer_window(v, fx, fy, ix0, ix1, iy0, iy1);
           for (int iy = iy1; iy >= iy0; --iy) {
-            const long long rowg = v.g_off + (long long)iy * v.nx;
+            const int rowsub = iy * v.nx;
             for (int ix = ix1; ix >= ix0; --ix) {
-              const long long g = rowg + ix;
-              if (g - v.g_off > sstart || g >= v.G) continue;
-              const float4 r = la.rec[g];
-              if (!layer_point_binned(r, bp.alpha_min)) continue;
-              ++evals;
-              const float isg = 1.f / r.z;
-              float dx, dy, d2, e;
-              const float a = gauss_alpha(fx, fy, make_float4(r.x, r.y, r.z == v.sig ? v.nc : ncoef(r.z), r.w),
-                                          bp.alpha_max, dx, dy, d2, e);
-              if (a < bp.alpha_min) continue;
-              T[k] = __fdividef(T[k], 1.f - a);   // transmittance in front of this Gaussian
-              const float wgt = a * T[k];
-              float da = (cc.x - Bk[k][0]) * dI[k][0];
-              float g5 = wgt * dI[k][0], g6 = 0.f, g7 = 0.f;
-              Bk[k][0] = a * cc.x + (1.f - a) * Bk[k][0];
-              if (C == 3) {
-                da += (cc.y - Bk[k][1]) * dI[k][1] + (cc.z - Bk[k][2]) * dI[k][2];
-                g6 = wgt * dI[k][1];
-                g7 = wgt * dI[k][2];
-                Bk[k][1] = a * cc.y + (1.f - a) * Bk[k][1];
-                Bk[k][2] = a * cc.z + (1.f - a) * Bk[k][2];
-              }
-              da *= T[k];
-              const bool uncapped = __fmul_rn(r.w, e) < bp.alpha_max;
-              const float dO = uncapped ? e * da : 0.f;
-              if (!per_pair) {
-                col[0] += g5;
-                col[1] += g6;
-                col[2] += g7;
-                if (dO != 0.f) {
-                  if (regional) atomicAdd(&s_reg[w][(iy - ry0) * rw + (ix - rx0)], dO);
-                  else atomicAdd(dgauss + g * kRow + 4, dO);
-                }
+              if (rowsub + ix > sstart) continue;
+              float4 q;
+              long long g = v.g_off + rowsub + ix;
+              if (staged) {
+                q = s_pt[w][(iy - ry0) * rw + (ix - rx0)];
+                if (q.w < 0.f) continue;
               } else {
-                if (full_grads && uncapped) {
-                  const float aa = da * a * isg * isg;
+                if (g >= v.G) continue;
+                const float4 r = la.rec[g];
+                if (!layer_point_binned(r, bp.alpha_min)) continue;
+                q = make_float4(r.x, r.y, r.z == v.sig ? v.nc : ncoef(r.z), r.w);
+              }
+              float dO, col[3], daa, dx, dy, d2;
+              if (!adjoint(k, fy, q, cc, dO, col, daa, dx, dy, d2)) continue;
+              if (staged) {
+                csum[0] += col[0];
+                csum[1] += col[1];
+                csum[2] += col[2];
+                if (dO != 0.f) atomicAdd(&s_reg[w][(iy - ry0) * rw + (ix - rx0)], dO);
+              } else if (!per_pair) {
+                csum[0] += col[0];
+                csum[1] += col[1];
+                csum[2] += col[2];
+                if (dO != 0.f) atomicAdd(dgauss + g * kRow + 4, dO);
+              } else {
+                if (full_grads && daa != 0.f) {
+                  const float isg = 1.f / la.rec[g].z;
+                  const float aa = daa * isg * isg;
                   red_add_v4(dgauss + g * kRow, aa * dx, aa * dy, aa * d2 * isg, 0.f);
                 }
-                red_add_v4(dgauss + g * kRow + 4, dO, g5, g6, g7);
+                red_add_v4(dgauss + g * kRow + 4, dO, col[0], col[1], col[2]);
               }
             }
           }
@@ -1730,20 +1853,22 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
         if (!per_pair) {
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) {
-            col[0] += __shfl_xor_sync(0xffffffffu, col[0], o);
-            col[1] += __shfl_xor_sync(0xffffffffu, col[1], o);
-            col[2] += __shfl_xor_sync(0xffffffffu, col[2], o);
+            csum[0] += __shfl_xor_sync(0xffffffffu, csum[0], o);
+            csum[1] += __shfl_xor_sync(0xffffffffu, csum[1], o);
+            csum[2] += __shfl_xor_sync(0xffffffffu, csum[2], o);
           }
-          if (lane == 0 && (col[0] != 0.f || col[1] != 0.f || col[2] != 0.f))
-            red_add_v4(dcurve + 4 * (long long)c, col[0], col[1], col[2], 0.f);
+          if (lane == 0 && (csum[0] != 0.f || csum[1] != 0.f || csum[2] != 0.f))
+            red_add_v4(dcurve + 4 * (long long)c, csum[0], csum[1], csum[2], 0.f);
         }
-        if (regional) {
+        if (staged) {
           __syncwarp();
+          const float inv_rw = 1.f / float(rw);
           for (int i = lane; i < rw * rh; i += 32) {
             const float val = s_reg[w][i];
             if (val != 0.f) {
-              const int iy = ry0 + i / rw, ix = rx0 + i % rw;
-              atomicAdd(dgauss + (v.g_off + (long long)iy * v.nx + ix) * kRow + 4, val);
+              const int iyr = int((float(i) + 0.5f) * inv_rw);
+              const int ixr = i - iyr * rw;
+              atomicAdd(dgauss + (v.g_off + (long long)(ry0 + iyr) * v.nx + rx0 + ixr) * kRow + 4, val);
             }
           }
           __syncwarp();
@@ -1758,32 +1883,18 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
           if (jpos >= last[k]) continue;
-          ++evals;
-          float dx, dy, d2, e;
-          const float a = gauss_alpha(fx, py0 + 4 * k + 0.5f, q, bp.alpha_max, dx, dy, d2, e);
-          if (a < bp.alpha_min) continue;
+          float dO, col[3], daa, dx, dy, d2;
+          if (!adjoint(k, py0 + 4 * k + 0.5f, q, cc, dO, col, daa, dx, dy, d2)) continue;
           contrib = true;
-          T[k] = __fdividef(T[k], 1.f - a);
-          const float wgt = a * T[k];
-          float da = (cc.x - Bk[k][0]) * dI[k][0];
-          vv[5] += wgt * dI[k][0];
-          Bk[k][0] = a * cc.x + (1.f - a) * Bk[k][0];
-          if (C == 3) {
-            da += (cc.y - Bk[k][1]) * dI[k][1] + (cc.z - Bk[k][2]) * dI[k][2];
-            vv[6] += wgt * dI[k][1];
-            vv[7] += wgt * dI[k][2];
-            Bk[k][1] = a * cc.y + (1.f - a) * Bk[k][1];
-            Bk[k][2] = a * cc.z + (1.f - a) * Bk[k][2];
-          }
-          da *= T[k];
-          if (__fmul_rn(q.w, e) < bp.alpha_max) {
-            vv[4] += e * da;
-            if (geo) {
-              const float aa = da * a * isg * isg;
-              vv[0] += aa * dx;
-              vv[1] += aa * dy;
-              vv[2] += aa * d2 * isg;
-            }
+          vv[4] += dO;
+          vv[5] += col[0];
+          vv[6] += col[1];
+          vv[7] += col[2];
+          if (geo) {
+            const float aa = daa * isg * isg;   // dalpha/dmu = alpha (x - mu) / sigma^2
+            vv[0] += aa * dx;
+            vv[1] += aa * dy;
+            vv[2] += aa * d2 * isg;              // dalpha/dsigma = alpha d^2 / sigma^3
           }
         }
         if (__any_sync(0xffffffffu, contrib)) {
@@ -1995,6 +2106,9 @@ static LayerArgs layer_args(const Layout& L, const ns_raster_params* rp, const n
   la.inv_tile = 1.f / float(rp->tile);
   la.log_amin = rp->alpha_min > 0.f ? logf(rp->alpha_min) : -INFINITY;
   la.nsub = at<int>(ws, L.o_nsub);
+  la.runs = at<int2>(ws, L.o_lruns);
+  la.tiles_x = L.tiles_x;
+  la.runs_stride = L.tiles_x + L.tiles_y;
   return la;
 }
 
@@ -2105,6 +2219,9 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
     std::swap(kin, kout);
     std::swap(vin, vout);
   }
+  if (bp.fill_layers && L.nc > 0)
+    NS_LAUNCH(NS_KERNEL_OTHER, k_layer_runs, L.nc, 128, 0, s, *curves, plan, rec, g->count, bp,
+              at<int2>(ws, L.o_lruns), L.tiles_x + L.tiles_y);
   cudaMemsetAsync(ranges, 0, sizeof(int2) * (size_t)L.n_tiles, s);
   NS_LAUNCH(NS_KERNEL_RANGES, k_ranges, num_sms() * 16, 256, 0, s, kin, st, ranges);
   const BlendArgs ba{ranges, vin, at<float4>(ws, L.o_prep), at<float2>(ws, L.o_prep2), at<float2>(ws, L.o_reach),
