@@ -1302,6 +1302,7 @@ struct LayerArgs {
   const float4* rec;
   const int* gcount;
   const int2* runs;   // per curve: covered column run per tile column, then row run per tile row
+  const float4* lconst;   // per curve: {x0, y0, 1/h, R}, {sigma, ncoef, nx bits, ny bits} (k_layer_runs)
   int gcap, tile, tiles_x, runs_stride;
   float k_sigma, inv_tile, log_amin;
   int* nsub;   // per pixel: 1 + sample index of the last composited fill Gaussian (0: none)
@@ -1351,14 +1352,25 @@ __device__ __forceinline__ void covered_run(int n, float guess, F ok, int& lo, i
 
 // One block per curve: for each tile column (row) of a fill layer's tile
 // rectangle, the run of grid columns (rows) the bin rule puts on it.
+// Thread 0 also writes the layer's constants: origin, 1/h, the reach bound R
+// of its most opaque Gaussian (+inf when alpha_min = 0), sigma and the
+// exponent coefficient the per-Gaussian binning would prepare.
 __global__ void __launch_bounds__(128) k_layer_runs(ns_curves cv, const CurvePlan* __restrict__ plan,
                                                     const float4* __restrict__ rec, const int* __restrict__ gcount,
-                                                    BinParams bp, int2* runs, int stride) {
+                                                    BinParams bp, int2* runs, int stride, float4* lconst) {
   const int c = blockIdx.x;
   if (!(cv.flags[c] & NS_FILLED)) return;
   const CurvePlan p = plan[c];
   const long long G = min((long long)*gcount, (long long)bp.gcap);
   if (p.g_off < 0 || p.g_off >= G || p.count <= 0 || p.nx <= 0 || p.ny <= 0 || !(p.h > 0.f)) return;
+  if (threadIdx.x == 0) {
+    const float sig = rec[p.g_off].z;
+    const float o_c = cv.color[4 * c + 3];
+    const float R = !(o_c > 0.f) ? 0.f
+                    : (bp.log_amin > -1e30f ? sqrtf(reach2(sig, o_c, bp.log_amin)) + 0.01f * p.h : FLT_MAX);
+    lconst[2 * c] = make_float4(p.x0, p.y0, 1.f / p.h, R);
+    lconst[2 * c + 1] = make_float4(sig, ncoef(sig), __int_as_float(p.nx), __int_as_float(p.ny));
+  }
   int tx0, ty0, ntx;
   const long long g1 = min((long long)p.g_off + p.count, G) - 1;
   const int nt = layer_rect(rec, p.g_off, g1, bp, tx0, ty0, ntx);
@@ -1389,30 +1401,31 @@ __global__ void __launch_bounds__(128) k_layer_runs(ns_curves cv, const CurvePla
   }
 }
 
-__device__ __forceinline__ LayerView layer_view(const LayerArgs& la, int c, int tx, int ty, float o_c) {
+// The layer of curve c (first Gaussian g_off) on tile (tx, ty); empty when
+// the curve's constants were not written (nothing to composite).
+__device__ __forceinline__ LayerView layer_view(const LayerArgs& la, int c, long long g_off, int tx, int ty) {
   LayerView v;
-  const CurvePlan p = la.plan[c];
-  v.G = min((long long)*la.gcount, (long long)la.gcap);
-  v.g_off = p.g_off;
-  v.nx = p.nx;
-  v.ny = p.ny;
-  v.cx0 = v.cy0 = 0;
-  v.cx1 = v.cy1 = -1;
-  v.x0 = p.x0;
-  v.y0 = p.y0;
-  v.inv_h = 0.f;
-  v.sig = v.nc = v.R = 0.f;
-  if (v.g_off < 0 || v.g_off >= v.G || v.nx <= 0 || v.ny <= 0 || !(p.h > 0.f) || !(o_c > 0.f)) return v;
-  v.inv_h = 1.f / p.h;
-  v.sig = la.rec[v.g_off].z;
-  v.nc = ncoef(v.sig);
-  v.R = la.log_amin > -1e30f ? sqrtf(reach2(v.sig, o_c, la.log_amin)) + 0.01f * p.h : FLT_MAX;
+  const float4 k0 = la.lconst[2 * c], k1 = la.lconst[2 * c + 1];
   const int2* r = la.runs + (long long)c * la.runs_stride;
   const int2 rx = r[tx], ry = r[la.tiles_x + ty];
+  v.G = min((long long)*la.gcount, (long long)la.gcap);
+  v.g_off = g_off;
+  v.x0 = k0.x;
+  v.y0 = k0.y;
+  v.inv_h = k0.z;
+  v.R = k0.w;
+  v.sig = k1.x;
+  v.nc = k1.y;
+  v.nx = __float_as_int(k1.z);
+  v.ny = __float_as_int(k1.w);
   v.cx0 = rx.x;
   v.cx1 = rx.y;
   v.cy0 = ry.x;
   v.cy1 = ry.y;
+  if (!(v.R > 0.f) || v.nx <= 0 || v.ny <= 0) {
+    v.cx0 = v.cy0 = 0;
+    v.cx1 = v.cy1 = -1;
+  }
   return v;
 }
 
@@ -1437,31 +1450,20 @@ __device__ __forceinline__ bool layer_point_binned(const float4& r, float alpha_
   return r.z > 0.f && r.w > 0.f && r.w >= alpha_min;
 }
 
-// The warp's region of a layer: the union of the windows of the pixels that
-// take part (want[k]), identical in every lane; false if empty.
-template <int PPT>
-__device__ __forceinline__ bool layer_region(const LayerView& v, float fx, int py0, const bool want[PPT], int& rx0,
-                                             int& rx1, int& ry0, int& ry1) {
-  rx0 = 0x7fffffff;
-  rx1 = -1;
-  ry0 = 0x7fffffff;
-  ry1 = -1;
-#pragma unroll
-  for (int k = 0; k < PPT; ++k) {
-    if (!want[k]) continue;
-    int ix0, ix1, iy0, iy1;
-    layer_window(v, fx, py0 + 4 * k + 0.5f, ix0, ix1, iy0, iy1);
-    if (ix0 > ix1 || iy0 > iy1) continue;
-    rx0 = min(rx0, ix0);
-    rx1 = max(rx1, ix1);
-    ry0 = min(ry0, iy0);
-    ry1 = max(ry1, iy1);
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    rx0 = min(rx0, __shfl_xor_sync(0xffffffffu, rx0, o));
-    rx1 = max(rx1, __shfl_xor_sync(0xffffffffu, rx1, o));
-    ry0 = min(ry0, __shfl_xor_sync(0xffffffffu, ry0, o));
-    ry1 = max(ry1, __shfl_xor_sync(0xffffffffu, ry1, o));
+// The warp's region of a layer: the grid points the pixel centres of its
+// rectangle wr = (x0, x1, y0, y1) can see.  It contains every pixel's
+// window (the bounds are monotone in the pixel position); false if empty.
+__device__ __forceinline__ bool layer_region(const LayerView& v, const float4& wr, int& rx0, int& rx1, int& ry0,
+                                             int& ry1) {
+  rx0 = v.cx0;
+  rx1 = v.cx1;
+  ry0 = v.cy0;
+  ry1 = v.cy1;
+  if (v.R < FLT_MAX) {
+    rx0 = max(rx0, int(ceilf(fmaxf((wr.x - v.R - v.x0) * v.inv_h - 0.5f, -1.f))));
+    rx1 = min(rx1, int(floorf(fminf((wr.y + v.R - v.x0) * v.inv_h - 0.5f, 2e9f))));
+    ry0 = max(ry0, int(ceilf(fmaxf((wr.z - v.R - v.y0) * v.inv_h - 0.5f, -1.f))));
+    ry1 = min(ry1, int(floorf(fminf((wr.w + v.R - v.y0) * v.inv_h - 0.5f, 2e9f))));
   }
   return rx1 >= rx0 && ry1 >= ry0;
 }
@@ -1592,13 +1594,11 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
       const uint32_t id = s_id[w][b];
       const float4 cc = s_c[w][b];
       if (id & kLayerBit) {
-        bool want[PPT];
-#pragma unroll
-        for (int k = 0; k < PPT; ++k) want[k] = !done[k];
         if (!__any_sync(0xffffffffu, !all_done())) break;
-        const LayerView v = layer_view(la, gcurve[id & ~kLayerBit], tx, ty, cc.w);
+        const uint32_t g0 = id & ~kLayerBit;
+        const LayerView v = layer_view(la, gcurve[g0], g0, tx, ty);
         int rx0, rx1, ry0, ry1;
-        if (!layer_region<PPT>(v, fx, py0, want, rx0, rx1, ry0, ry1)) continue;
+        if (!layer_region(v, wr, rx0, rx1, ry0, ry1)) continue;
         const int rw = rx1 - rx0 + 1, rh = ry1 - ry0 + 1;
         const bool staged = (long long)rw * rh <= kPts;
         if (staged) {
@@ -1789,10 +1789,11 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
           any = any || want[k];
         }
         if (!__any_sync(0xffffffffu, any)) continue;   // no pixel of the warp walks this far back
-        const int c = gcurve[id & ~kLayerBit];
-        const LayerView v = layer_view(la, c, tx, ty, cc.w);
+        const uint32_t g0 = id & ~kLayerBit;
+        const int c = gcurve[g0];
+        const LayerView v = layer_view(la, c, g0, tx, ty);
         int rx0, rx1, ry0, ry1;
-        if (!layer_region<PPT>(v, fx, py0, want, rx0, rx1, ry0, ry1)) continue;
+        if (!layer_region(v, wr, rx0, rx1, ry0, ry1)) continue;
         const int rw = rx1 - rx0 + 1, rh = ry1 - ry0 + 1;
         const bool staged = !per_pair && (long long)rw * rh <= kPts;
         if (staged) {
@@ -2107,6 +2108,7 @@ static LayerArgs layer_args(const Layout& L, const ns_raster_params* rp, const n
   la.log_amin = rp->alpha_min > 0.f ? logf(rp->alpha_min) : -INFINITY;
   la.nsub = at<int>(ws, L.o_nsub);
   la.runs = at<int2>(ws, L.o_lruns);
+  la.lconst = at<float4>(ws, L.o_lconst);
   la.tiles_x = L.tiles_x;
   la.runs_stride = L.tiles_x + L.tiles_y;
   return la;
@@ -2221,7 +2223,7 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
   }
   if (bp.fill_layers && L.nc > 0)
     NS_LAUNCH(NS_KERNEL_OTHER, k_layer_runs, L.nc, 128, 0, s, *curves, plan, rec, g->count, bp,
-              at<int2>(ws, L.o_lruns), L.tiles_x + L.tiles_y);
+              at<int2>(ws, L.o_lruns), L.tiles_x + L.tiles_y, at<float4>(ws, L.o_lconst));
   cudaMemsetAsync(ranges, 0, sizeof(int2) * (size_t)L.n_tiles, s);
   NS_LAUNCH(NS_KERNEL_RANGES, k_ranges, num_sms() * 16, 256, 0, s, kin, st, ranges);
   const BlendArgs ba{ranges, vin, at<float4>(ws, L.o_prep), at<float2>(ws, L.o_prep2), at<float2>(ws, L.o_reach),
