@@ -146,6 +146,8 @@ bool make_layout(const ns_curves* c, const ns_capacity* cap, const ns_raster_par
   // fill layers: per curve, the grid run of each tile column and row
   L->o_lruns = take(sizeof(int2) * (size_t)L->nc * (size_t)(L->tiles_x + L->tiles_y));
   L->o_lconst = take(sizeof(float4) * 2 * (size_t)L->nc);   // per layer {x0, y0, 1/h, R}, {sigma, ncoef, nx, ny}
+  L->o_lmin = take(sizeof(int2) * (size_t)L->nc);   // per layer: smallest live grid column and row
+  L->o_lmax = take(sizeof(int2) * (size_t)L->nc);   // largest
   L->o_dgauss = take(sizeof(float) * 12 * (size_t)L->gcap);   // 8 per Gaussian, 12 when tangent-aligned
   L->o_prep = take(sizeof(float4) * (size_t)L->gcap);
   L->o_prep2 = take(sizeof(float2) * (size_t)L->gcap);

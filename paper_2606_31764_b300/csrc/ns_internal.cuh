@@ -72,7 +72,7 @@ struct Layout {
   int64_t gcap = 0, pcap = 0, bcap = 0;
   int64_t bin_blocks = 0, sort_blocks = 0;
   size_t o_state = 0, o_plan = 0, o_knots = 0, o_dknots = 0, o_bpts = 0, o_dbpts = 0, o_bsum = 0,
-         o_k0 = 0, o_v0 = 0, o_k1 = 0, o_v1 = 0, o_hist = 0, o_ranges = 0, o_T = 0, o_nlast = 0, o_nsub = 0, o_lruns = 0, o_lconst = 0,
+         o_k0 = 0, o_v0 = 0, o_k1 = 0, o_v1 = 0, o_hist = 0, o_ranges = 0, o_T = 0, o_nlast = 0, o_nsub = 0, o_lruns = 0, o_lconst = 0, o_lmin = 0, o_lmax = 0,
          o_dgauss = 0, o_curve_scene = 0, o_order = 0, o_prep = 0, o_prep2 = 0, o_reach = 0, o_live = 0,
          total = 0;
   size_t sample_total = 0;   // bytes of the prefix nurbs_sample uses (independent of the raster settings)

@@ -53,6 +53,8 @@ struct BinParams {
   int tiles_x, tiles_y, tiles_per_scene;
   int n_curves, gcap;   // Gaussians naming a curve outside [0, n_curves) cover no tile
   int fill_layers;      // one pair per (tile, filled curve) instead of per (tile, Gaussian)
+  int2* lmin;           // fill layers: per curve the smallest / largest grid column and row of a
+  int2* lmax;           // live Gaussian (one the per-Gaussian rule would bin); empty: lmax < lmin
 };
 
 // Pair values of fill layers carry this bit on the index of the layer's first Gaussian.
@@ -109,15 +111,12 @@ __device__ __forceinline__ int tile_rect_of(const float4* __restrict__ rec, cons
   else return tile_rect(rec[g], bp, x0, y0, nx);
 }
 
-// Tiles of a fill layer: the union of the bin rectangles of its grid's
-// Gaussians.  They share sigma and sit on a grid, so the union runs from the
-// first record's rectangle (smallest x and y) to the last one's (largest),
-// by the same float32 rule; every grid point is counted whatever its opacity
-// (a tile whose grid points are all culled gets an entry that composites
-// nothing).  The last record is clamped to the set (g1 < G).
-__device__ __forceinline__ int layer_rect(const float4* __restrict__ rec, long long g0, long long g1,
-                                          const BinParams& bp, int& x0, int& y0, int& nx) {
-  const float4 r0 = rec[g0], r1 = rec[g1];
+// Tiles of a fill layer: the union of the bin rectangles of a block of its
+// grid's Gaussians.  They share sigma and sit on a grid, so the union runs
+// from the rectangle of the block's corner with the smallest x and y (r0) to
+// that of the corner with the largest (r1), by the same float32 rule.
+__device__ __forceinline__ int layer_rect(const float4 r0, const float4 r1, const BinParams& bp, int& x0, int& y0,
+                                          int& nx) {
   const float ks = __fmul_rn(bp.k_sigma, r0.z);
   const float xlo = floorf(__fmul_rn(__fsub_rn(r0.x, ks), bp.inv_tile));
   const float xhi = floorf(__fmul_rn(__fadd_rn(r1.x, ks), bp.inv_tile));
@@ -134,20 +133,37 @@ __device__ __forceinline__ int layer_rect(const float4* __restrict__ rec, long l
   return nx * (y1 - y0 + 1);
 }
 
+// Tiles of a fill layer restricted to its live grid points: the layer rule
+// above applied to the columns and rows between the live extremes (the
+// x of a column is that of its record in the first row, the y of a row that
+// of its first record).  Live points are the only ones per-Gaussian pairs
+// would list, so nothing that composites is left out.
+__device__ __forceinline__ int layer_rect_live(const float4* __restrict__ rec, const CurvePlan& p, long long G,
+                                               const BinParams& bp, int c, int& x0, int& y0, int& nx) {
+  const int2 lo = bp.lmin[c], hi = bp.lmax[c];
+  if (hi.x < lo.x || hi.y < lo.y || lo.x < 0 || lo.y < 0 || hi.x >= p.nx || hi.y >= p.ny) return 0;
+  const long long last = G - 1;
+  const float4 rx0 = rec[min((long long)p.g_off + lo.x, last)], rx1 = rec[min((long long)p.g_off + hi.x, last)];
+  const float4 ry0 = rec[min((long long)p.g_off + (long long)lo.y * p.nx, last)];
+  const float4 ry1 = rec[min((long long)p.g_off + (long long)hi.y * p.nx, last)];
+  return layer_rect(make_float4(rx0.x, ry0.y, rx0.z, rx0.w), make_float4(rx1.x, ry1.y, rx1.z, rx1.w), bp, x0, y0, nx);
+}
+
 // Tile count of Gaussian g in the pair emission, and its rectangle.  In
-// fill-layer mode a fill Gaussian counts only as its layer's first one.
+// fill-layer mode a fill Gaussian counts only as its layer's first one, and
+// only when count_layers is set (the binning counts layers separately).
 template <bool ANISO>
 __device__ __forceinline__ int gaussian_tiles(const float4* __restrict__ rec, const float4* __restrict__ shape,
                                               const int* __restrict__ cflags, const CurvePlan* __restrict__ plan,
-                                              long long g, int cv, int G, const BinParams& bp, bool& layer,
-                                              int& x0, int& y0, int& nx) {
+                                              long long g, int cv, int G, const BinParams& bp, bool count_layers,
+                                              bool& layer, int& x0, int& y0, int& nx) {
   layer = false;
   if (cv < 0 || cv >= bp.n_curves) return 0;
   if (bp.fill_layers && (cflags[cv] & NS_FILLED)) {
     const CurvePlan& p = plan[cv];
     if (g != p.g_off || p.count <= 0) return 0;
     layer = true;
-    return layer_rect(rec, g, min(g + p.count, (long long)G) - 1, bp, x0, y0, nx);
+    return count_layers ? layer_rect_live(rec, p, G, bp, cv, x0, y0, nx) : 0;
   }
   return tile_rect_of<ANISO>(rec, shape, g, bp, x0, y0, nx);
 }
@@ -205,13 +221,22 @@ __global__ void __launch_bounds__(256) k_bin_count(const float4* __restrict__ re
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     const long long g = base + k * 256 + threadIdx.x;
+    int live_key = -1, live_ix = 0, live_iy = 0;   // fill layers: live grid point of curve live_key
     if (g < G) {
       const float4 r = rec[g];
       int x0, y0, nx;
       const int cv = gcurve[g];
       bool layer;
-      const int nt = gaussian_tiles<ANISO>(rec, shape, cflags, plan, g, cv, G, bp, layer, x0, y0, nx);
+      const int nt = gaussian_tiles<ANISO>(rec, shape, cflags, plan, g, cv, G, bp, false, layer, x0, y0, nx);
       cnt += nt;
+      if (bp.fill_layers && cv >= 0 && cv < bp.n_curves && (cflags[cv] & NS_FILLED) && r.z > 0.f && r.w > 0.f &&
+          r.w >= bp.alpha_min) {
+        const CurvePlan& p = plan[cv];
+        const float ih = 1.f / p.h;
+        live_key = cv;
+        live_ix = __float2int_rn((r.x - p.x0) * ih - 0.5f);
+        live_iy = __float2int_rn((r.y - p.y0) * ih - 0.5f);
+      }
       if (nt && !layer) {   // only Gaussians binned on their own are read through these
         // 1/sigma, negative for the Gaussians of filled curves (their centre and
         // sigma get no gradient through the chain, so the adjoint may skip
@@ -235,6 +260,20 @@ __global__ void __launch_bounds__(256) k_bin_count(const float4* __restrict__ re
       }
       culled += (r.z > 0.f && r.w < bp.alpha_min) ? 1 : 0;
     }
+    if (bp.fill_layers) {
+      // extremes of the live grid points per curve: lanes of one curve reduce, one lane adds
+      const unsigned int peers = __match_any_sync(0xffffffffu, live_key);
+      if (live_key >= 0) {
+        const int mnx = __reduce_min_sync(peers, live_ix), mxx = __reduce_max_sync(peers, live_ix);
+        const int mny = __reduce_min_sync(peers, live_iy), mxy = __reduce_max_sync(peers, live_iy);
+        if ((threadIdx.x & 31) == __ffs(peers) - 1) {
+          atomicMin(&bp.lmin[live_key].x, mnx);
+          atomicMax(&bp.lmax[live_key].x, mxx);
+          atomicMin(&bp.lmin[live_key].y, mny);
+          atomicMax(&bp.lmax[live_key].y, mxy);
+        }
+      }
+    }
   }
   int total;
   block_excl_scan_int(cnt, s_warp, total);
@@ -244,6 +283,21 @@ __global__ void __launch_bounds__(256) k_bin_count(const float4* __restrict__ re
     bsum[blockIdx.x] = total;
     if (ctot) atomicAdd(&st->culled, (unsigned long long)ctot);
   }
+}
+
+// Fill layers: each filled curve's tile count (from its live grid points)
+// joins the count of the binning block that holds its first Gaussian, where
+// k_bin_emit writes the layer's pairs.
+__global__ void k_layer_count(ns_curves cv, const CurvePlan* __restrict__ plan, const float4* __restrict__ rec,
+                              const int* __restrict__ gcount, BinParams bp, int* bsum) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cv.n_curves || !(cv.flags[c] & NS_FILLED)) return;
+  const CurvePlan p = plan[c];
+  const long long G = min((long long)*gcount, (long long)bp.gcap);
+  if (p.g_off < 0 || p.g_off >= G || p.count <= 0) return;
+  int x0, y0, nx;
+  const int nt = layer_rect_live(rec, p, G, bp, c, x0, y0, nx);
+  if (nt) atomicAdd(&bsum[p.g_off / kBinItems], nt);
 }
 
 __global__ void k_scan_small(int* vals, const int* gcount, int gcap, int items_per_block, DevState* st,
@@ -309,7 +363,7 @@ __global__ void __launch_bounds__(256) k_bin_emit(const float4* __restrict__ rec
     int c = 0, x0 = 0, y0 = 0, nx = 1;
     if (g < G) {
       bool layer;
-      c = gaussian_tiles<ANISO>(rec, shape, cflags, plan, g, gcurve[g], G, bp, layer, x0, y0, nx);
+      c = gaussian_tiles<ANISO>(rec, shape, cflags, plan, g, gcurve[g], G, bp, true, layer, x0, y0, nx);
     }
     s_off[gl] = c;
     s_rect[gl] = make_int2(x0 | (nx << 16), y0 | ((c ? c / nx : 0) << 16));
@@ -1372,9 +1426,9 @@ __global__ void __launch_bounds__(128) k_layer_runs(ns_curves cv, const CurvePla
     lconst[2 * c + 1] = make_float4(sig, ncoef(sig), __int_as_float(p.nx), __int_as_float(p.ny));
   }
   int tx0, ty0, ntx;
-  const long long g1 = min((long long)p.g_off + p.count, G) - 1;
-  const int nt = layer_rect(rec, p.g_off, g1, bp, tx0, ty0, ntx);
+  const int nt = layer_rect_live(rec, p, G, bp, c, tx0, ty0, ntx);
   if (!nt) return;
+  const int2 live0 = bp.lmin[c], live1 = bp.lmax[c];   // runs keep to the live columns and rows
   const int nty = nt / ntx;
   const float ks = __fmul_rn(bp.k_sigma, rec[p.g_off].z);
   const float inv_h = 1.f / p.h, T = 1.f / bp.inv_tile;
@@ -1387,7 +1441,7 @@ __global__ void __launch_bounds__(128) k_layer_runs(ns_curves cv, const CurvePla
       covered_run(p.nx, (tx * T - ks - p.x0) * inv_h - 0.5f,
                   [&](int ix) { return bin_covers(rec[min((long long)p.g_off + ix, lastg)].x, ks, bp.inv_tile, tx); },
                   lo, hi);
-      out[tx] = make_int2(lo, hi);
+      out[tx] = make_int2(max(lo, live0.x), min(hi, live1.x));
     } else {
       const int ty = ty0 + (k - ntx);
       covered_run(p.ny, (ty * T - ks - p.y0) * inv_h - 0.5f,
@@ -1396,7 +1450,7 @@ __global__ void __launch_bounds__(128) k_layer_runs(ns_curves cv, const CurvePla
                                       bp.inv_tile, ty);
                   },
                   lo, hi);
-      out[bp.tiles_x + ty] = make_int2(lo, hi);
+      out[bp.tiles_x + ty] = make_int2(max(lo, live0.y), min(hi, live1.y));
     }
   }
 }
@@ -2192,7 +2246,13 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
   bp.n_curves = L.nc;
   bp.gcap = int(L.gcap);
   bp.fill_layers = use_layers(rp, g) ? 1 : 0;
+  bp.lmin = at<int2>(ws, L.o_lmin);
+  bp.lmax = at<int2>(ws, L.o_lmax);
   const CurvePlan* plan = at<CurvePlan>(ws, L.o_plan);
+  if (bp.fill_layers && L.nc > 0) {
+    cudaMemsetAsync(bp.lmin, 0x7f, sizeof(int2) * (size_t)L.nc, s);   // 0x7f7f7f7f: above every index
+    cudaMemsetAsync(bp.lmax, 0xff, sizeof(int2) * (size_t)L.nc, s);   // -1
+  }
   const int bin_blocks = int(L.bin_blocks);
   const bool aniso = g->shape != nullptr;
   const float4* shape = reinterpret_cast<const float4*>(g->shape);
@@ -2201,6 +2261,8 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
     NS_LAUNCH(NS_KERNEL_BIN_COUNT, kc, bin_blocks, 256, 0, s, rec, shape, g->curve, curves->flags, g->count, bp, bsum, st,
               at<float4>(ws, L.o_prep), at<float2>(ws, L.o_prep2), at<float2>(ws, L.o_reach), plan);
   }
+  if (bp.fill_layers && L.nc > 0 && bin_blocks > 0)
+    NS_LAUNCH(NS_KERNEL_OTHER, k_layer_count, (L.nc + 127) / 128, 128, 0, s, *curves, plan, rec, g->count, bp, bsum);
   NS_LAUNCH(NS_KERNEL_SCAN, k_scan_small, 1, 1024, 0, s, bsum, g->count, int(L.gcap), kBinItems, st, cap->pairs);
   if (bin_blocks > 0) {
     auto ke = aniso ? &k_bin_emit<true> : &k_bin_emit<false>;
