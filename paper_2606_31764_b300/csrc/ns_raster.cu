@@ -355,6 +355,9 @@ __global__ void __launch_bounds__(256) k_bin_emit(const float4* __restrict__ rec
   const int G = min(*gcount, bp.gcap);
   const long long base = (long long)blockIdx.x * kBinItems;
   if (base >= G) return;
+  // a block whose Gaussians emit no pair (the inside of a fill layer, culled
+  // points) has the same offset as the next block
+  if (base + kBinItems < G && boff[blockIdx.x + 1] == boff[blockIdx.x]) return;
   // 1. rectangles, consecutive threads on consecutive Gaussians (coalesced)
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
@@ -1552,7 +1555,7 @@ template <int TILE, int PPT>
 struct LayerGeom {
   // staged points per warp; the forward and the adjoint share a budget of
   // shared memory per block that keeps every instantiation under 48 KB
-  static constexpr int kPts = BlendGeom<TILE, PPT>::kWarps <= 2 ? 256 : 192;
+  static constexpr int kPts = BlendGeom<TILE, PPT>::kWarps <= 2 ? 192 : 128;
   // the adjoint keeps more live state per pixel than the forward: 768
   // resident threads leave it up to 85 registers instead of spilling
   static constexpr int kMinBlocksBwd = 768 / BlendGeom<TILE, PPT>::kThreads;
@@ -1599,10 +1602,9 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
   };
   unsigned int evals = 0, contribs = 0;
   // composite one Gaussian (blend constants q) into pixel k; false once the pixel is done
-  auto composite = [&](int k, float fy, const float4& q, const float4& cc, int pos, int sub) {
+  // the compositing step of Eq. 8 once alpha is known
+  auto composite_alpha = [&](int k, float a, const float4& cc, int pos, int sub) {
     ++evals;
-    float dx, dy, d2, e;
-    const float a = gauss_alpha(fx, fy, q, bp.alpha_max, dx, dy, d2, e);
     if (a < bp.alpha_min) return;
     const float test = T[k] * (1.f - a);
     if (test < bp.t_min) {
@@ -1619,6 +1621,10 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
     last[k] = pos;
     lsub[k] = sub;
     ++contribs;
+  };
+  auto composite = [&](int k, float fy, const float4& q, const float4& cc, int pos, int sub) {
+    float dx, dy, d2, e;
+    composite_alpha(k, gauss_alpha(fx, fy, q, bp.alpha_max, dx, dy, d2, e), cc, pos, sub);
   };
   for (int base = 0; base < n && !__all_sync(0xffffffffu, all_done()); base += 32) {
     const int j = base + lane;
@@ -1669,21 +1675,35 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
           const float fy = py0 + 4 * k + 0.5f;
           int ix0, ix1, iy0, iy1;
           layer_window(v, fx, fy, ix0, ix1, iy0, iy1);
+          const int pos = base + b + 1;
           for (int iy = iy0; iy <= iy1 && !done[k]; ++iy) {
             const int rowsub = iy * v.nx;
-            for (int ix = ix0; ix <= ix1 && !done[k]; ++ix) {
-              float4 q;
-              if (staged) {
-                q = s_pt[w][(iy - ry0) * rw + (ix - rx0)];
-                if (q.w < 0.f) continue;
-              } else {
+            if (staged) {
+              // two points per step: both alphas are independent of the
+              // compositing state, which then takes them in order
+              const float4* prow = &s_pt[w][(iy - ry0) * rw - rx0];
+              int ix = ix0;
+              for (; ix + 1 <= ix1 && !done[k]; ix += 2) {
+                const float4 qa = prow[ix], qb = prow[ix + 1];
+                float dx, dy, d2, ea, eb;
+                const float aa = gauss_alpha(fx, fy, qa, bp.alpha_max, dx, dy, d2, ea);
+                const float ab = gauss_alpha(fx, fy, qb, bp.alpha_max, dx, dy, d2, eb);
+                if (qa.w >= 0.f) composite_alpha(k, aa, cc, pos, rowsub + ix + 1);
+                if (qb.w >= 0.f && !done[k]) composite_alpha(k, ab, cc, pos, rowsub + ix + 2);
+              }
+              if (ix <= ix1 && !done[k]) {
+                const float4 q = prow[ix];
+                if (q.w >= 0.f) composite(k, fy, q, cc, pos, rowsub + ix + 1);
+              }
+            } else {
+              for (int ix = ix0; ix <= ix1 && !done[k]; ++ix) {
                 const long long g = v.g_off + rowsub + ix;
                 if (g >= v.G) break;
                 const float4 r = la.rec[g];
                 if (!layer_point_binned(r, bp.alpha_min)) continue;
-                q = make_float4(r.x, r.y, r.z == v.sig ? v.nc : ncoef(r.z), r.w);
+                composite(k, fy, make_float4(r.x, r.y, r.z == v.sig ? v.nc : ncoef(r.z), r.w), cc, pos,
+                          rowsub + ix + 1);
               }
-              composite(k, fy, q, cc, base + b + 1, rowsub + ix + 1);
             }
           }
         }
@@ -1780,11 +1800,9 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
   // the adjoint of one pair of pixel k (blend constants q, colour cc):
   // returns false below alpha_min; else the opacity gradient dO, the colour
   // gradient col and, for the centre and sigma, da a and the offsets
-  auto adjoint = [&](int k, float fy, const float4& q, const float4& cc, float& dO, float col[3], float& daa,
-                     float& dx, float& dy, float& d2) {
+  auto adjoint_alpha = [&](int k, float a, float e, float ow, const float4& cc, float& dO, float col[3],
+                           float& daa) {
     ++evals;
-    float e;
-    const float a = gauss_alpha(fx, fy, q, bp.alpha_max, dx, dy, d2, e);
     if (a < bp.alpha_min) return false;
     T[k] = __fdividef(T[k], 1.f - a);   // transmittance in front of this Gaussian
     const float wgt = a * T[k];
@@ -1800,10 +1818,16 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
       Bk[k][2] = a * cc.z + (1.f - a) * Bk[k][2];
     }
     da *= T[k];
-    const bool uncapped = __fmul_rn(q.w, e) < bp.alpha_max;
+    const bool uncapped = __fmul_rn(ow, e) < bp.alpha_max;
     dO = uncapped ? e * da : 0.f;
     daa = uncapped ? da * a : 0.f;
     return true;
+  };
+  auto adjoint = [&](int k, float fy, const float4& q, const float4& cc, float& dO, float col[3], float& daa,
+                     float& dx, float& dy, float& d2) {
+    float e;
+    const float a = gauss_alpha(fx, fy, q, bp.alpha_max, dx, dy, d2, e);
+    return adjoint_alpha(k, a, e, q.w, cc, dO, col, daa);
   };
   for (int base = ((wmax - 1) >> 5) << 5; base >= 0 && wmax > 0; base -= 32) {
     const int j = base + lane;
@@ -1867,29 +1891,59 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
           const int sstart = (jpos == last[k] - 1) ? lsub[k] - 1 : 0x7fffffff;
           int ix0, ix1, iy0, iy1;
           layer_window(v, fx, fy, ix0, ix1, iy0, iy1);
+          if (staged) {
+            for (int iy = iy1; iy >= iy0; --iy) {
+              const int rowsub = iy * v.nx;
+              const int ridx = (iy - ry0) * rw - rx0;
+              const float4* prow = &s_pt[w][ridx];
+              float* rreg = &s_reg[w][ridx];
+              // the last layer of the pixel starts at its last composited point
+              int ix = min(ix1, sstart - rowsub);
+              // two points per step: both alphas first, then the adjoint in order
+              for (; ix - 1 >= ix0; ix -= 2) {
+                const float4 qa = prow[ix], qb = prow[ix - 1];
+                float dxa, dya, d2a, ea, dxb, dyb, d2b, eb;
+                const float aa = gauss_alpha(fx, fy, qa, bp.alpha_max, dxa, dya, d2a, ea);
+                const float ab = gauss_alpha(fx, fy, qb, bp.alpha_max, dxb, dyb, d2b, eb);
+                float dO, col[3], daa;
+                if (qa.w >= 0.f && adjoint_alpha(k, aa, ea, qa.w, cc, dO, col, daa)) {
+                  csum[0] += col[0];
+                  csum[1] += col[1];
+                  csum[2] += col[2];
+                  if (dO != 0.f) atomicAdd(&rreg[ix], dO);
+                }
+                if (qb.w >= 0.f && adjoint_alpha(k, ab, eb, qb.w, cc, dO, col, daa)) {
+                  csum[0] += col[0];
+                  csum[1] += col[1];
+                  csum[2] += col[2];
+                  if (dO != 0.f) atomicAdd(&rreg[ix - 1], dO);
+                }
+              }
+              if (ix == ix0) {
+                const float4 q = prow[ix];
+                float dO, col[3], daa, dx, dy, d2;
+                if (q.w >= 0.f && adjoint(k, fy, q, cc, dO, col, daa, dx, dy, d2)) {
+                  csum[0] += col[0];
+                  csum[1] += col[1];
+                  csum[2] += col[2];
+                  if (dO != 0.f) atomicAdd(&rreg[ix], dO);
+                }
+              }
+            }
+            continue;
+          }
           for (int iy = iy1; iy >= iy0; --iy) {
             const int rowsub = iy * v.nx;
             for (int ix = ix1; ix >= ix0; --ix) {
               if (rowsub + ix > sstart) continue;
-              float4 q;
-              long long g = v.g_off + rowsub + ix;
-              if (staged) {
-                q = s_pt[w][(iy - ry0) * rw + (ix - rx0)];
-                if (q.w < 0.f) continue;
-              } else {
-                if (g >= v.G) continue;
-                const float4 r = la.rec[g];
-                if (!layer_point_binned(r, bp.alpha_min)) continue;
-                q = make_float4(r.x, r.y, r.z == v.sig ? v.nc : ncoef(r.z), r.w);
-              }
+              const long long g = v.g_off + rowsub + ix;
+              if (g >= v.G) continue;
+              const float4 r = la.rec[g];
+              if (!layer_point_binned(r, bp.alpha_min)) continue;
+              const float4 q = make_float4(r.x, r.y, r.z == v.sig ? v.nc : ncoef(r.z), r.w);
               float dO, col[3], daa, dx, dy, d2;
               if (!adjoint(k, fy, q, cc, dO, col, daa, dx, dy, d2)) continue;
-              if (staged) {
-                csum[0] += col[0];
-                csum[1] += col[1];
-                csum[2] += col[2];
-                if (dO != 0.f) atomicAdd(&s_reg[w][(iy - ry0) * rw + (ix - rx0)], dO);
-              } else if (!per_pair) {
+              if (!per_pair) {
                 csum[0] += col[0];
                 csum[1] += col[1];
                 csum[2] += col[2];
@@ -1906,14 +1960,13 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
           }
         }
         if (!per_pair) {
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            csum[0] += __shfl_xor_sync(0xffffffffu, csum[0], o);
-            csum[1] += __shfl_xor_sync(0xffffffffu, csum[1], o);
-            csum[2] += __shfl_xor_sync(0xffffffffu, csum[2], o);
-          }
-          if (lane == 0 && (csum[0] != 0.f || csum[1] != 0.f || csum[2] != 0.f))
-            red_add_v4(dcurve + 4 * (long long)c, csum[0], csum[1], csum[2], 0.f);
+          // the layer's colour gradient: value k of the warp total sits in lane 8k
+          const float cv4[4] = {csum[0], csum[1], csum[2], 0.f};
+          const float t0 = warp_sum4(cv4);
+          const float t1 = __shfl_down_sync(0xffffffffu, t0, 8);
+          const float t2 = __shfl_down_sync(0xffffffffu, t0, 16);
+          if (lane == 0 && (t0 != 0.f || t1 != 0.f || t2 != 0.f))
+            red_add_v4(dcurve + 4 * (long long)c, t0, t1, t2, 0.f);
         }
         if (staged) {
           __syncwarp();
