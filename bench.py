@@ -35,31 +35,27 @@ PEAKS_FALLBACK = dict(hbm_gbs=6400.0, sm_max_mhz=2032.0)
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one `ncu --set full` capture of the 512-path version of the workload at tile
-# 8 (profiles/*_vectorize-512-1024.md), with the units that launch processed
-# and the hash of the kernel source it ran.  The bench scales the bytes to its
-# own launch by the units processed, and reports null if the source or tile
-# has changed since the capture.
+# 8 with fill layers (profiles/*_vectorize-512-1024.md), with the units that
+# launch processed and the hash of the kernel source it ran.  The bench
+# scales the bytes to its own launch by the units processed, and reports null
+# if the source, the tile or the binning has changed since the capture.
 TRAFFIC = dict(
-    blend_bwd=dict(bytes=107379712, units=2706344, unit="pairs", tile=8,
-                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="13a4539eac3391b8"),
-    blend_fwd=dict(bytes=49210112, units=2706344, unit="pairs", tile=8,
-                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="13a4539eac3391b8"),
-    bin_emit=dict(bytes=40954368, units=2027197, unit="gaussians", tile=8,
-                  src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="13a4539eac3391b8"),
-    radix_scatter=dict(bytes=22024448, units=2706344, unit="pairs", tile=8,
-                       src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="13a4539eac3391b8"),
-    emit=dict(bytes=2332416, units=2027197, unit="gaussians", tile=None,
-              src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="28770a9dd684096a"),
-    chain=dict(bytes=88292864, units=2027197, unit="gaussians", tile=None,
-               src="paper_2606_31764_b300/csrc/ns_backward.cu", sha="95583a4bcedf5a24"),
+    blend_bwd=dict(bytes=86230272, units=2027197, unit="gaussians", tile=8, layers=1,
+                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="cd04738aa9abe5dd"),
+    blend_fwd=dict(bytes=27888640, units=2027197, unit="gaussians", tile=8, layers=1,
+                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="cd04738aa9abe5dd"),
+    emit=dict(bytes=2934528, units=2027197, unit="gaussians", tile=None, layers=None,
+              src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="cf009dde58f5c3d2"),
 )
 
 
-def traffic_per_launch(kernel, units_now, tile):
+def traffic_per_launch(kernel, units_now, tile, layers):
     """Captured DRAM bytes scaled to this launch, or None when stale."""
     import hashlib
     t = TRAFFIC.get(kernel)
     if t is None or (t["tile"] is not None and t["tile"] != tile):
+        return None
+    if t["layers"] is not None and t["layers"] != int(layers):
         return None
     sha = hashlib.sha256(open(os.path.join(ROOT, t["src"]), "rb").read()).hexdigest()[:16]
     if sha != t["sha"]:
@@ -91,6 +87,8 @@ def parse():
     ap.add_argument("--fill-layers", default="0,1",
                     help="binnings the autotuner tries: 0 per Gaussian, 1 fill layers (comma separated)")
     ap.add_argument("--cpu-sample-curves", type=int, default=64)
+    ap.add_argument("--headline-only", action="store_true",
+                    help="profiling runs: only the headline step (no e2e, regulariser or schedule measurements)")
     ap.add_argument("--ref-sample-curves", type=int, default=8)
     return ap.parse_args()
 
@@ -364,15 +362,32 @@ def run_gpu(args, dist, rank, world):
     clk = peaks["sm_max_mhz"] * 1e6
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     fp32_peak = 2.0 * 128 * sms * clk / 1e12        # TFLOP/s, FMA = 2 FLOP
-    work = dict(
-        emit=("alu", costs["segment_tests"] * FLOP_SEGMENT / 1e12, "TFLOP/s", fp32_peak),
-        blend_fwd=("alu", rep.blend_visits * FLOP_VISIT_FWD / 1e12, "TFLOP/s", fp32_peak),
-        blend_bwd=("alu", rep.blend_bwd_visits * FLOP_VISIT_BWD / 1e12, "TFLOP/s", fp32_peak),
-        radix_scatter=("hbm", rep.pairs * 16 / 1e9, "GB/s", peaks["hbm_gbs"]),
-        bin_emit=("hbm", (G * 16 + G * 4 + rep.pairs * 8) / 1e9, "GB/s", peaks["hbm_gbs"]),
-    )
     performed = dict(blend_fwd=(rep.blend_evals * FLOP_EVAL + rep.blend_contribs * FLOP_CONTRIB_FWD) / 1e12,
                      blend_bwd=(rep.blend_bwd_evals * FLOP_EVAL + rep.blend_contribs * FLOP_CONTRIB_BWD) / 1e12)
+    layers = bool(step.sp.rp.fill_layers)
+    # with per-Gaussian pairs the blend work is counted per visited (pixel,
+    # list entry) pair; fill layers have no per-Gaussian list, and there the
+    # FP32 work the kernels performed is reported instead
+    work = dict(
+        emit=("alu", costs["segment_tests"] * FLOP_SEGMENT / 1e12, "TFLOP/s", fp32_peak),
+        blend_fwd=("alu", performed["blend_fwd"] if layers else rep.blend_visits * FLOP_VISIT_FWD / 1e12,
+                   "TFLOP/s", fp32_peak),
+        blend_bwd=("alu", performed["blend_bwd"] if layers else rep.blend_bwd_visits * FLOP_VISIT_BWD / 1e12,
+                   "TFLOP/s", fp32_peak),
+        radix_scatter=("hbm", rep.pairs * 16 / 1e9, "GB/s", peaks["hbm_gbs"]),
+        # fill layers: the emission reads the curve of every Gaussian, not its record
+        bin_emit=("hbm", ((G * 4 if layers else G * 20) + rep.pairs * 8) / 1e9, "GB/s", peaks["hbm_gbs"]),
+    )
+    work_text = dict(
+        emit=f"algorithmic: {FLOP_SEGMENT} FP32 FLOP per (grid point, boundary segment) test of the plain "
+             "definition (Eq. S1-S2), Q x B per curve",
+        blend_fwd=("performed: 10 FP32 FLOP per alpha evaluation + 10 per composited pair (fill layers)" if layers
+                   else f"algorithmic: visited (pixel, list entry) pairs of Eq. 8-9 x {FLOP_VISIT_FWD} FP32 FLOP"),
+        blend_bwd=("performed: 10 FP32 FLOP per alpha evaluation + 33 per composited pair (fill layers)" if layers
+                   else f"algorithmic: visited (pixel, list entry) pairs of Eq. 8-9 x {FLOP_VISIT_BWD} FP32 FLOP"),
+        radix_scatter="16 B per pair and pass (read + write of key and value)",
+        bin_emit="curve ids (fill layers) or records and curve ids read, 8 B per pair written",
+    )
     dom = max(per_kernel, key=per_kernel.get)
     kernels = {}
     for k, ms in per_kernel.items():
@@ -380,7 +395,7 @@ def run_gpu(args, dist, rank, world):
         if k in work:
             bound, amount, unit, peak = work[k]
             ach = amount / (ms / 1e3)
-            d.update(bound=bound, achieved=round(ach, 3), unit=unit, frac=round(ach / peak, 4))
+            d.update(bound=bound, achieved=round(ach, 3), unit=unit, frac=round(ach / peak, 4), work=work_text[k])
         if k in performed:
             # the FLOPs the kernel itself executed (its culling skips most pairs)
             d["performed_frac"] = round(performed[k] / (ms / 1e3) / fp32_peak, 4)
@@ -388,22 +403,21 @@ def run_gpu(args, dist, rank, world):
     units_now = dict(pairs=int(rep.pairs), gaussians=G)
     tile_now = int(step.sp.rp.tile)
     for k in kernels:
-        kernels[k]["traffic"] = traffic_per_launch(k, units_now, tile_now)
+        kernels[k]["traffic"] = traffic_per_launch(k, units_now, tile_now, layers)
     roof = None
     if dom in work:
         bound, amount, unit, peak = work[dom]
         ach = amount / (per_kernel[dom] / 1e3)
         roof = dict(kernel=dom, bound=bound, achieved=round(ach, 3), peak=round(peak, 2), unit=unit,
-                    frac=round(ach / peak, 4), traffic=traffic_per_launch(dom, units_now, tile_now),
+                    frac=round(ach / peak, 4), traffic=traffic_per_launch(dom, units_now, tile_now, layers),
                     peak_source=("FP32 lanes x SMs x max SM clock" if bound == "alu"
                                  else f"{peaks['source']} HBM copy bandwidth"))
-        if dom in performed:
-            roof["work"] = ("algorithmic: visited (pixel, list entry) pairs of Eq. 8-9 with early termination x "
-                            f"{FLOP_VISIT_FWD if dom == 'blend_fwd' else FLOP_VISIT_BWD} FP32 FLOP")
+        roof["work"] = work_text[dom]
+        if dom in performed and not layers:
             roof["performed_frac"] = kernels[dom]["performed_frac"]
 
     # end to end through the public API with host buffers
-    e2e = run_e2e(torch, step, g1, args)
+    e2e = None if args.headline_only else run_e2e(torch, step, g1, args)
 
     out = dict(metric=METRIC, value=round(value, 1), unit="Gaussians/s", n_gpus=world, steps=args.steps,
                warmup=args.warmup, ms_per_step=round(ms_step, 4), higher_is_better=True,
@@ -424,8 +438,10 @@ def run_gpu(args, dist, rank, world):
                           evals_fwd=int(rep.blend_evals), evals_bwd=int(rep.blend_bwd_evals),
                           composited=int(rep.blend_contribs)),
                sample=costs)
+    if args.headline_only:
+        return out, step
     out["geometry"] = run_geometry(torch, step, args)
-    out["schedule"] = run_schedule(torch, step)
+    out["schedule"] = run_schedule(torch, step, tuning)
     if not args.no_per_scene:
         out["per_scene"] = run_per_scene(torch, step, args, value)
         out["long_spline"] = run_long_spline(torch, args)
@@ -464,36 +480,54 @@ def run_layerwise(torch, rounds=4, iters=100):
                 note="the round's set-up (seeding, buffer sizing) is outside the per-iteration times")
 
 
-def run_schedule(torch, step):
+def run_schedule(torch, step, tuning):
     """Grid-step annealing (Eq. 14) on the headline batch: h(t) for T = 300
     iterations from h_max = 8 to h_min = 1 between t/T = 0.1 and 0.8, sampled at
     11 evenly spaced iterations.  Each sampled step is captured as a graph of
-    its own (the grid step is a launch parameter) and timed; the schedule
-    average is the sum of Gaussians over the sum of times."""
+    its own (the grid step is a launch parameter) and timed with each binning
+    (per Gaussian, fill layers) at the tuned tile, keeping the faster: fill
+    layers win on fine grids, per-Gaussian pairs on coarse ones.  The
+    schedule average is the sum of Gaussians over the sum of times."""
     from paper_2606_31764_b300 import binding as B
     lib = B.load()
     T, h0 = 300, float(step.sp.sp.h)
+    rp = step.sp.rp
+    saved = (int(rp.fill_layers), int(rp.ppt_fwd), int(rp.ppt_bwd))
+    modes = []
+    for fl in (0, 1):
+        key = f"{int(rp.tile)}" + ("-layers" if fl else "")
+        if key in tuning["tried"]:
+            modes.append((fl, tuning["tried"][key]["ppt_fwd"], tuning["tried"][key]["ppt_bwd"]))
     rows = []
     for i in range(11):
         t = int(round(i * (T - 1) / 10))
         h = float(lib.ns_grid_step(t, T, 8.0, 1.0, 0.1, 0.8))
         step.sp.sp.h = h
-        g = capture(torch, step, 3)
-        g.replay()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        g.replay()
-        e1.record()
-        torch.cuda.synchronize()
-        rows.append(dict(t=t, h=round(h, 4), gaussians=step.gaussians(), ms=round(e0.elapsed_time(e1) / 3, 4)))
-        del g
+        best = None
+        for fl, pf, pb in modes:
+            rp.fill_layers, rp.ppt_fwd, rp.ppt_bwd = fl, pf, pb
+            g = capture(torch, step, 3)
+            g.replay()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 3
+            if best is None or ms < best[0]:
+                best = (ms, fl)
+            del g
+        rows.append(dict(t=t, h=round(h, 4), gaussians=step.gaussians(), ms=round(best[0], 4),
+                         fill_layers=best[1]))
     step.sp.sp.h = h0
+    rp.fill_layers, rp.ppt_fwd, rp.ppt_bwd = saved
     step()
     torch.cuda.synchronize()
     G = sum(r["gaussians"] for r in rows)
     ms = sum(r["ms"] for r in rows)
-    return dict(what="grid-step annealing 8 -> 1 px (Eq. 14, T = 300, t_b = 0.1, t_e = 0.8), 11 sampled iterations",
+    return dict(what="grid-step annealing 8 -> 1 px (Eq. 14, T = 300, t_b = 0.1, t_e = 0.8), 11 sampled iterations, "
+                     "the faster binning per grid step",
                 gaussians_per_s=round(G / (ms / 1e3), 1), ms_per_iteration=round(ms / len(rows), 4), steps=rows)
 
 

@@ -128,6 +128,7 @@ bool make_layout(const ns_curves* c, const ns_capacity* cap, const ns_raster_par
   L->o_bpts = take(sizeof(float2) * (size_t)L->bcap);
   L->o_dbpts = take(sizeof(float2) * (size_t)L->bcap);
   L->o_bcurve = take(sizeof(int) * (size_t)L->bcap);
+  L->o_cbox = take(sizeof(float4) * (size_t)L->bcap);   // at the index of each cluster's first point
   // each curve's tasks cover its Gaussians in chunks of kChunk: within the
   // Gaussian capacity there are at most gcap/kChunk + n_curves of them
   L->tcap = L->gcap / kChunk + L->nc + 1;

@@ -78,6 +78,7 @@ struct Layout {
   size_t sample_total = 0;   // bytes of the prefix nurbs_sample uses (independent of the raster settings)
   size_t o_tasks = 0;        // task -> curve table (fill tasks first, then contour tasks)
   size_t o_bcurve = 0;       // boundary point -> curve
+  size_t o_cbox = 0;         // bounding box of each 8-segment cluster of a boundary polyline
   int64_t tcap = 0;          // entries of that table
 };
 

@@ -544,12 +544,46 @@ __device__ __forceinline__ int cluster_crossings(const float4* seg, const float2
   return wn;
 }
 
+// Bounding box {x0, x1, y0, y1} of each cluster of kCluster consecutive
+// segments of a fill polyline (the last cluster may be shorter; segment j
+// runs from point j to point j + 1, the last one back to point 0), stored at
+// the index of the cluster's first point.  The sampling tasks of a curve all
+// stage these boxes, so they are computed once per curve here.
+__global__ void __launch_bounds__(256) k_cluster_boxes(const CurvePlan* __restrict__ plan,
+                                                       const int* __restrict__ bcurve,
+                                                       const float2* __restrict__ bpts,
+                                                       const DevState* __restrict__ st, float4* cbox,
+                                                       long long bcap, int nc) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nb = min((long long)st->b_count, bcap);
+  if (i >= nb) return;
+  // points of a polyline that overflowed the capacity are never written:
+  // their curve entry is not trusted
+  const int c = bcurve[i];
+  if (c < 0 || c >= nc) return;
+  const CurvePlan p = plan[c];
+  const long long k = i - p.b_off;
+  if (k < 0 || k >= p.M || k % kCluster != 0 || (long long)p.b_off + p.M > bcap) return;
+  const int B = p.M;
+  float x0 = FLT_MAX, x1 = -FLT_MAX, y0 = FLT_MAX, y1 = -FLT_MAX;
+  for (int j = int(k); j < min(B, int(k) + kCluster); ++j) {
+    const float2 b0 = bpts[p.b_off + j];
+    const float2 b1 = bpts[p.b_off + (j + 1 == B ? 0 : j + 1)];
+    x0 = fminf(x0, fminf(b0.x, b1.x));
+    x1 = fmaxf(x1, fmaxf(b0.x, b1.x));
+    y0 = fminf(y0, fminf(b0.y, b1.y));
+    y1 = fmaxf(y1, fmaxf(b0.y, b1.y));
+  }
+  cbox[i] = make_float4(x0, x1, y0, y1);
+}
+
 // Persistent: each block iteration handles one task of 256 Gaussians of one curve.
 __global__ void __launch_bounds__(256, 4) k_emit(ns_curves cv, ns_sample_params sp, const CurvePlan* __restrict__ plan,
                                               const int* __restrict__ order, const float* __restrict__ knots,
                                               const float2* __restrict__ bpts, const DevState* __restrict__ st,
                                               float4* rec, int* gcurve, int* gaux, long long gcap, long long bcap,
-                                              const int* __restrict__ tmap, long long tcap) {
+                                              const int* __restrict__ tmap, long long tcap,
+                                              const float4* __restrict__ cbox_g) {
   __shared__ float4 seg[kSegBatch];   // {b0.x, b0.y, e.x, e.y}
   __shared__ float2 segb[kSegBatch];  // {b1.y, 1/|e|^2 (0 for a zero-length segment)}
   __shared__ float4 cbox[kSegBatch / kCluster];  // {x0, x1, y0, y1} of each segment cluster
@@ -611,20 +645,8 @@ __global__ void __launch_bounds__(256, 4) k_emit(ns_curves cv, ns_sample_params 
         seg[s] = make_float4(b0.x, b0.y, ex, ey);
         segb[s] = make_float2(b1.y, ee > 0.f ? 1.f / ee : 0.f);
       }
-      // bounding box of each cluster of kCluster consecutive segments
-      for (int cl = threadIdx.x; cl < ncl; cl += blockDim.x) {
-        float x0 = FLT_MAX, x1 = -FLT_MAX, y0 = FLT_MAX, y1 = -FLT_MAX;
-        for (int k = cl * kCluster; k < min(nseg, (cl + 1) * kCluster); ++k) {
-          const int i = base + k;
-          const float2 b0 = bpts[pl.b_off + i];
-          const float2 b1 = bpts[pl.b_off + (i + 1 == B ? 0 : i + 1)];
-          x0 = fminf(x0, fminf(b0.x, b1.x));
-          x1 = fmaxf(x1, fmaxf(b0.x, b1.x));
-          y0 = fminf(y0, fminf(b0.y, b1.y));
-          y1 = fmaxf(y1, fmaxf(b0.y, b1.y));
-        }
-        cbox[cl] = make_float4(x0, x1, y0, y1);
-      }
+      // bounding box of each cluster of kCluster consecutive segments (k_cluster_boxes)
+      for (int cl = threadIdx.x; cl < ncl; cl += blockDim.x) cbox[cl] = cbox_g[pl.b_off + base + cl * kCluster];
       __syncthreads();
       if (valid && B <= kSegBatch) {
         // the whole polyline is staged: first the winding number and a lower
@@ -742,12 +764,16 @@ extern "C" ns_status nurbs_sample(const ns_curves* curves, const ns_sample_param
   NS_LAUNCH(NS_KERNEL_SCAN, k_scan_boundary, 1, 1024, 0, s, nc, plan, st, cap->boundary);
   NS_LAUNCH(NS_KERNEL_BOUNDARY, k_boundary, nc, kPlanThreads, 0, s, *curves, *sp, plan, knots, bpts,
             at<int>(ws, L.o_bcurve), cap->boundary);
+  float4* cbox = at<float4>(ws, L.o_cbox);
+  if (cap->boundary > 0)
+    NS_LAUNCH(NS_KERNEL_OTHER, k_cluster_boxes, int((cap->boundary + 255) / 256), 256, 0, s, plan,
+              at<const int>(ws, L.o_bcurve), bpts, st, cbox, cap->boundary, nc);
   NS_LAUNCH(NS_KERNEL_SCAN, k_scan_gauss, 1, 1024, 0, s, nc, plan, order, st, cap->gaussians, out->count);
   int* tmap = at<int>(ws, L.o_tasks);
   NS_LAUNCH(NS_KERNEL_SCAN, k_task_map, (nc + 7) / 8, 256, 0, s, nc, plan, st, tmap, (long long)L.tcap);
   const int grid = num_sms() * 8;
   NS_LAUNCH(NS_KERNEL_EMIT, k_emit, grid, 256, 0, s, *curves, *sp, plan, order, knots, bpts, st, reinterpret_cast<float4*>(out->rec),
-                              out->curve, out->aux, cap->gaussians, cap->boundary, tmap, (long long)L.tcap);
+                              out->curve, out->aux, cap->gaussians, cap->boundary, tmap, (long long)L.tcap, cbox);
   if (out->shape)
     NS_LAUNCH(NS_KERNEL_OTHER, k_emit_shape, grid, 256, 0, s, *curves, *sp, plan, knots, st,
               reinterpret_cast<const float4*>(out->rec), out->curve, reinterpret_cast<float4*>(out->shape));
