@@ -1556,9 +1556,10 @@ struct LayerGeom {
   // staged points per warp; the forward and the adjoint share a budget of
   // shared memory per block that keeps every instantiation under 48 KB
   static constexpr int kPts = BlendGeom<TILE, PPT>::kWarps <= 2 ? 192 : 128;
-  // the adjoint keeps more live state per pixel than the forward: 768
-  // resident threads leave it up to 85 registers instead of spilling
-  static constexpr int kMinBlocksBwd = 768 / BlendGeom<TILE, PPT>::kThreads;
+  // 1024 resident threads (64 registers): the adjoint is latency-bound, and
+  // 16 blocks of 2 warps per SM beat 12 blocks at 80 registers (a few bytes
+  // of spills outside the walk)
+  static constexpr int kMinBlocksBwd = 1024 / BlendGeom<TILE, PPT>::kThreads;
 };
 
 template <int TILE, int PPT, int C>
