@@ -1460,12 +1460,23 @@ __global__ void __launch_bounds__(128) k_layer_runs(ns_curves cv, const CurvePla
 
 // The layer of curve c (first Gaussian g_off) on tile (tx, ty); empty when
 // the curve's constants were not written (nothing to composite).
-__device__ __forceinline__ LayerView layer_view(const LayerArgs& la, int c, long long g_off, int tx, int ty) {
-  LayerView v;
-  const float4 k0 = la.lconst[2 * c], k1 = la.lconst[2 * c + 1];
+// What a layer entry needs from global memory, loaded by the lane that loads
+// the entry of a list batch: the layer constants and the grid runs of the
+// tile ({column run, row run}).
+__device__ __forceinline__ void layer_entry(const LayerArgs& la, int c, int tx, int ty, float4& k0, float4& k1,
+                                            int4& run) {
+  k0 = la.lconst[2 * c];
+  k1 = la.lconst[2 * c + 1];
   const int2* r = la.runs + (long long)c * la.runs_stride;
   const int2 rx = r[tx], ry = r[la.tiles_x + ty];
-  v.G = min((long long)*la.gcount, (long long)la.gcap);
+  run = make_int4(rx.x, rx.y, ry.x, ry.y);
+}
+
+__device__ __forceinline__ LayerView layer_view(const float4& k0, const float4& k1, const int4& run, long long g_off,
+                                                long long G) {
+  LayerView v;
+  const int2 rx = make_int2(run.x, run.y), ry = make_int2(run.z, run.w);
+  v.G = G;
   v.g_off = g_off;
   v.x0 = k0.x;
   v.y0 = k0.y;
@@ -1570,9 +1581,11 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
                        LayerArgs la, float* image, float* Tfinal, int* nlast, DevState* st) {
   using Gm = BlendGeom<TILE, PPT>;
   constexpr int kPts = LayerGeom<TILE, PPT>::kPts;
-  __shared__ float4 s_q[Gm::kWarps][32];
+  __shared__ float4 s_q[Gm::kWarps][32];     // blend constants, or a layer's first constants
   __shared__ float4 s_c[Gm::kWarps][32];
   __shared__ uint32_t s_id[Gm::kWarps][32];
+  __shared__ float4 s_k1[Gm::kWarps][32];    // a layer's second constants
+  __shared__ int4 s_run[Gm::kWarps][32];     // a layer's grid runs on this tile
   __shared__ float4 s_pt[Gm::kWarps][kPts];
   int s, px, py0;
   float4 wr;
@@ -1582,6 +1595,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
   const int tx = t % bp.tiles_x, ty = t / bp.tiles_x;
   const float fx = px + 0.5f;
   const int2 rg = ranges[blockIdx.x];
+  const long long Gset = min((long long)*la.gcount, (long long)la.gcap);   // Gaussians in the set
   const int n = rg.y - rg.x;
   float T[PPT], acc[PPT][C];
   bool done[PPT];
@@ -1635,8 +1649,15 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
       const uint32_t gi = g & ~kLayerBit;
       if (g & kLayerBit) {
         hit = true;
+        const int c = gcurve[gi];
+        float4 k0, k1;
+        int4 run;
+        layer_entry(la, c, tx, ty, k0, k1, run);
         s_id[w][lane] = g;
-        s_c[w][lane] = color[gcurve[gi]];
+        s_c[w][lane] = color[c];
+        s_q[w][lane] = k0;
+        s_k1[w][lane] = k1;
+        s_run[w][lane] = run;
       } else {
         const float4 q = prep[gi];
         hit = rect_d2(q.x, q.y, wr.x, wr.y, wr.z, wr.w) <= reach[gi].x;
@@ -1657,7 +1678,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
       if (id & kLayerBit) {
         if (!__any_sync(0xffffffffu, !all_done())) break;
         const uint32_t g0 = id & ~kLayerBit;
-        const LayerView v = layer_view(la, gcurve[g0], g0, tx, ty);
+        const LayerView v = layer_view(s_q[w][b], s_k1[w][b], s_run[w][b], g0, Gset);
         int rx0, rx1, ry0, ry1;
         if (!layer_region(v, wr, rx0, rx1, ry0, ry1)) continue;
         const int rw = rx1 - rx0 + 1, rh = ry1 - ry0 + 1;
@@ -1758,10 +1779,12 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
   using Gm = BlendGeom<TILE, PPT>;
   constexpr int kRow = 8;
   constexpr int kPts = LayerGeom<TILE, PPT>::kPts;
-  __shared__ float4 s_q[Gm::kWarps][32];
+  __shared__ float4 s_q[Gm::kWarps][32];     // blend constants, or a layer's first constants
   __shared__ float4 s_c[Gm::kWarps][32];
-  __shared__ float s_isig[Gm::kWarps][32];
+  __shared__ float s_isig[Gm::kWarps][32];   // +-1/sigma, or a layer's curve (int bits)
   __shared__ uint32_t s_id[Gm::kWarps][32];
+  __shared__ float4 s_k1[Gm::kWarps][32];    // a layer's second constants
+  __shared__ int4 s_run[Gm::kWarps][32];     // a layer's grid runs on this tile
   __shared__ float4 s_pt[Gm::kWarps][kPts];
   __shared__ float s_reg[Gm::kWarps][kPts];
   int s, px, py0;
@@ -1772,6 +1795,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
   const int tx = t % bp.tiles_x, ty = t / bp.tiles_x;
   const float fx = px + 0.5f;
   const int2 rg = ranges[blockIdx.x];
+  const long long Gset = min((long long)*la.gcount, (long long)la.gcap);   // Gaussians in the set
   const bool per_pair = full_grads || dcurve == nullptr;
   float T[PPT], dI[PPT][3], Bk[PPT][3];
   int last[PPT], lsub[PPT];
@@ -1838,8 +1862,16 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
       const uint32_t gi = g & ~kLayerBit;
       if (g & kLayerBit) {
         hit = true;
+        const int c = gcurve[gi];
+        float4 k0, k1;
+        int4 run;
+        layer_entry(la, c, tx, ty, k0, k1, run);
         s_id[w][lane] = g;
-        s_c[w][lane] = color[gcurve[gi]];
+        s_c[w][lane] = color[c];
+        s_q[w][lane] = k0;
+        s_k1[w][lane] = k1;
+        s_run[w][lane] = run;
+        s_isig[w][lane] = __int_as_float(c);
       } else {
         const float4 q = prep[gi];
         const float2 rs = reach[gi];
@@ -1869,8 +1901,8 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
         }
         if (!__any_sync(0xffffffffu, any)) continue;   // no pixel of the warp walks this far back
         const uint32_t g0 = id & ~kLayerBit;
-        const int c = gcurve[g0];
-        const LayerView v = layer_view(la, c, g0, tx, ty);
+        const int c = __float_as_int(s_isig[w][b]);
+        const LayerView v = layer_view(s_q[w][b], s_k1[w][b], s_run[w][b], g0, Gset);
         int rx0, rx1, ry0, ry1;
         if (!layer_region(v, wr, rx0, rx1, ry0, ry1)) continue;
         const int rw = rx1 - rx0 + 1, rh = ry1 - ry0 + 1;
@@ -2058,9 +2090,19 @@ static void launch_bwd_layers(int tile, int ppt, int grid, cudaStream_t s, const
                               const float4* prep, const float2* reach, const int* gcurve, const float4* col,
                               const BlendParams& bp, const LayerArgs& la, const float* dimage, const float* Tf,
                               const int* nl, float* dgauss, DevState* st, int full_grads, float* dcurve) {
+  // the register-limited 16 blocks per SM need most of the SM's shared memory
+  // (staged regions): ask for the largest carveout once per instantiation
 #define NS_BWDL(TL, PP)                                                                                   \
-  NS_LAUNCH(NS_KERNEL_BLEND_BWD, (k_blend_bwd_layers<TL, PP, C>), grid, (BlendGeom<TL, PP>::kThreads), 0, s, \
-            ranges, gid, prep, reach, gcurve, col, bp, la, dimage, Tf, nl, dgauss, st, full_grads, dcurve)
+  do {                                                                                                    \
+    static bool carveout = false;                                                                         \
+    if (!carveout) {                                                                                      \
+      cudaFuncSetAttribute(k_blend_bwd_layers<TL, PP, C>, cudaFuncAttributePreferredSharedMemoryCarveout,  \
+                           int(cudaSharedmemCarveoutMaxShared));                                          \
+      carveout = true;                                                                                    \
+    }                                                                                                     \
+    NS_LAUNCH(NS_KERNEL_BLEND_BWD, (k_blend_bwd_layers<TL, PP, C>), grid, (BlendGeom<TL, PP>::kThreads), 0, \
+              s, ranges, gid, prep, reach, gcurve, col, bp, la, dimage, Tf, nl, dgauss, st, full_grads, dcurve); \
+  } while (0)
   if (tile == 8) { if (ppt == 1) NS_BWDL(8, 1); else NS_BWDL(8, 2); }
   else if (tile == 16) { if (ppt == 1) NS_BWDL(16, 1); else if (ppt == 2) NS_BWDL(16, 2); else NS_BWDL(16, 4); }
   else NS_BWDL(32, 4);
