@@ -40,14 +40,12 @@ PEAKS_FALLBACK = dict(hbm_gbs=6400.0, sm_max_mhz=2032.0)
 # scales the bytes to its own launch by the units processed, and reports null
 # if the source, the tile or the binning has changed since the capture.
 TRAFFIC = dict(
-    blend_bwd=dict(bytes=86230272, units=2027197, unit="gaussians", tile=8, layers=1,
-                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="cd04738aa9abe5dd"),
-    blend_fwd=dict(bytes=27893504, units=2027197, unit="gaussians", tile=8, layers=1,
-                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="f9a11b6e411525b0"),
-    bin_count=dict(bytes=40630016, units=2027197, unit="gaussians", tile=8, layers=1,
-                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="f9a11b6e411525b0"),
-    bin_emit=dict(bytes=3822080, units=2027197, unit="gaussians", tile=8, layers=1,
-                  src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="f9a11b6e411525b0"),
+    blend_bwd=dict(bytes=86937856, units=2027197, unit="gaussians", tile=8, layers=1,
+                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="d643f6760c7636ff"),
+    blend_fwd=dict(bytes=28032000, units=2027197, unit="gaussians", tile=8, layers=1,
+                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="d643f6760c7636ff"),
+    chain=dict(bytes=88732672, units=2027197, unit="gaussians", tile=None, layers=None,
+               src="paper_2606_31764_b300/csrc/ns_backward.cu", sha="9153ecc170fdaa06"),
     emit=dict(bytes=2934528, units=2027197, unit="gaussians", tile=None, layers=None,
               src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="cf009dde58f5c3d2"),
 )

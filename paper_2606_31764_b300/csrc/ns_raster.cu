@@ -1571,10 +1571,13 @@ struct LayerGeom {
   // 16 blocks of 2 warps per SM beat 12 blocks at 80 registers (a few bytes
   // of spills outside the walk)
   static constexpr int kMinBlocksBwd = 1024 / BlendGeom<TILE, PPT>::kThreads;
+  // the forward at 56 registers: 18 blocks of 2 warps per SM (at most 32 blocks)
+  static constexpr int kMinBlocksFwd =
+      1152 / BlendGeom<TILE, PPT>::kThreads < 32 ? 1152 / BlendGeom<TILE, PPT>::kThreads : 32;
 };
 
 template <int TILE, int PPT, int C>
-__global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE, PPT>::kMinBlocks)
+__global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE, PPT>::kMinBlocksFwd)
     k_blend_fwd_layers(const int2* __restrict__ ranges, const uint32_t* __restrict__ gid,
                        const float4* __restrict__ prep, const float2* __restrict__ reach,
                        const int* __restrict__ gcurve, const float4* __restrict__ color, BlendParams bp,
@@ -2077,8 +2080,16 @@ static void launch_fwd_layers(int tile, int ppt, int grid, cudaStream_t s, const
                               const BlendParams& bp, const LayerArgs& la, float* image, float* Tf, int* nl,
                               DevState* st) {
 #define NS_FWDL(TL, PP)                                                                                   \
-  NS_LAUNCH(NS_KERNEL_BLEND_FWD, (k_blend_fwd_layers<TL, PP, C>), grid, (BlendGeom<TL, PP>::kThreads), 0, s, \
-            ranges, gid, prep, reach, gcurve, col, bp, la, image, Tf, nl, st)
+  do {                                                                                                    \
+    static bool carveout = false;                                                                         \
+    if (!carveout) {                                                                                      \
+      cudaFuncSetAttribute(k_blend_fwd_layers<TL, PP, C>, cudaFuncAttributePreferredSharedMemoryCarveout,  \
+                           int(cudaSharedmemCarveoutMaxShared));                                          \
+      carveout = true;                                                                                    \
+    }                                                                                                     \
+    NS_LAUNCH(NS_KERNEL_BLEND_FWD, (k_blend_fwd_layers<TL, PP, C>), grid, (BlendGeom<TL, PP>::kThreads), 0, \
+              s, ranges, gid, prep, reach, gcurve, col, bp, la, image, Tf, nl, st);                       \
+  } while (0)
   if (tile == 8) { if (ppt == 1) NS_FWDL(8, 1); else NS_FWDL(8, 2); }
   else if (tile == 16) { if (ppt == 1) NS_FWDL(16, 1); else if (ppt == 2) NS_FWDL(16, 2); else NS_FWDL(16, 4); }
   else NS_FWDL(32, 4);
