@@ -105,11 +105,11 @@ __global__ void __launch_bounds__(256) k_chain(ns_curves cv, ChainParams cp, con
     const bool valid = l < pl.count && g < gcap;
     __syncthreads();
     if (threadIdx.x < 8) s_red[threadIdx.x] = 0.f;
-    float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0;
-    if (valid) {
-      g0 = reinterpret_cast<const float4*>(dgauss)[row4 * g];
-      g1 = reinterpret_cast<const float4*>(dgauss)[row4 * g + 1];
-    }
+    // a culled point (opacity 0, marked far) is never composited: its row is
+    // zero and nothing of it is read
+    const int aux = valid ? gaux[g] : 0;
+    float4 g1 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid && aux != kAuxFar) g1 = reinterpret_cast<const float4*>(dgauss)[row4 * g + 1];
     {
     // fill task (skipped when its polyline overflowed the boundary capacity)
     if ((long long)pl.b_off + pl.M > bcap) continue;
@@ -119,7 +119,6 @@ __global__ void __launch_bounds__(256) k_chain(ns_curves cv, ChainParams cp, con
       for (int k = threadIdx.x; k < B; k += blockDim.x) s_db[k] = make_float2(0.f, 0.f);
     __syncthreads();
     float dO = 0.f;
-    const int aux = valid ? gaux[g] : 0;
     const float gop = g1.x;   // row layout {dmu_x, dmu_y, dsigma, 0, do, dr, dg, db}
     if (valid && gop != 0.f && aux == kAuxDeep) {
       dO = gop;   // sigmoid exactly 1: the opacity gradient passes through, none reaches the boundary

@@ -3,10 +3,16 @@
 // Kernels, in launch order:
 //   k_curve_scene   scene of every curve (binary search of the scene offsets)
 //   k_bin_count     per 2048 Gaussians: tiles overlapped by mu +- k sigma (exact
-//                   float32 rule), block sums
+//                   float32 rule), block sums; with fill layers, the live box
+//                   of every filled curve's grid
+//   k_layer_count   fill layers: each layer's tile count joins its block's sum
 //   k_scan_small    one block: block sums -> block offsets, pair total
 //   k_bin_emit      recount, block-local scan, write (tile, Gaussian) pairs in
 //                   Gaussian order, which is front to back inside each scene
+//                   (a fill layer: one pair per tile of its live grid box)
+//   k_layer_runs    fill layers: per curve and tile column (row), the grid
+//                   columns (rows) the bin rule puts on it, and the layer's
+//                   constants
 //   k_radix_hist / k_radix_scan / k_radix_scatter
 //                   stable LSD radix sort of the pairs on the tile id bits
 //                   only: pairs enter in (layer, sample) order, so a stable sort
@@ -23,6 +29,9 @@
 //   k_blend_fwd_groups / k_blend_bwd_groups
 //                   the same with each warp split into four 8-lane groups of
 //                   two pixel columns, each group walking its own hits
+//   k_blend_fwd_layers / k_blend_bwd_layers
+//                   the same lists where a fill layer's entry is walked as its
+//                   grid: each warp stages the grid points its pixels can see
 #include <cuda_runtime.h>
 
 #include <algorithm>
