@@ -482,7 +482,9 @@ uint64_t ns_launch_count(void);
  * (cudaGetSymbolAddress), so make it before any stream capture.  All calls on
  * one device share the array: calls that overlap on the GPU (other streams or
  * threads) race and must be serialised by the caller.  Each call clears the
- * status it inherits from the previous one.  It calls no allocator.
+ * status it inherits from the previous one.  It calls no allocator.  It
+ * always bins one pair per Gaussian and tile (rp->fill_layers is ignored:
+ * fill layers need the sampling plans of a workspace, which it has none of).
  */
 ns_status splat_forward_noalloc(const ns_curves* curves, const ns_gaussians* g,
                                 const ns_raster_params* rp, float* image, ns_report* report,

@@ -61,6 +61,10 @@ extern "C" ns_status splat_forward_noalloc(const ns_curves* curves, const ns_gau
     set_error("splat_forward_noalloc: the Gaussian set's capacity exceeds the fixed scratch limit of 65536");
     return NS_ERR_INVALID_ARG;
   }
+  // no sampling plans live in the scratch: bin one pair per Gaussian and tile
+  ns_raster_params rpn = *rp;
+  rpn.fill_layers = 0;
+  rp = &rpn;
   ns_capacity cap;
   cap.gaussians = g->capacity;
   cap.pairs = kNoAllocMaxPairs;

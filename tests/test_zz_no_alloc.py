@@ -62,3 +62,19 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
                                    C.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == B.NS_ERR_INVALID_ARG
     assert b"65536" in lib.ns_last_error()
+
+
+def test_noalloc_ignores_fill_layers():
+    """Fill layers need the sampling plans of a workspace; the no-allocation
+    variant has none and bins per Gaussian whatever the raster settings say."""
+    sc = scenes.small_closed(73, n_curves=3, size=56, filled=True, h=1.0).with_raster(**scenes.RASTER_DEFAULTS)
+    g = op.gaussians_fp32(sc)
+    sp, ref, rep, inputs = run_records(sc, g["rec"], g["curve"], capacity=(g["rec"].shape[0], 1 << 16, 16))
+    assert rep.status == 0
+    sp.rp.fill_layers = 1
+    out = torch.full_like(ref, float("nan"))
+    r = B.NsReport()
+    st = _noalloc(sp, inputs, out, r)
+    assert st == B.NS_OK, B.load().ns_last_error()
+    assert r.status == 0 and r.pairs == rep.pairs
+    assert torch.equal(out, ref)
