@@ -77,6 +77,11 @@ FLOP_VISIT_FWD = 13
 FLOP_VISIT_BWD = 30
 
 
+def workload_name(paths=2048):
+    return (f"vectorize-{paths}-1024: 1024x1024 RGB, {paths} closed filled NURBS paths p in {{2,3,4,5}}, "
+            "8-64 key points, fill grid step h=1")
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -425,8 +430,7 @@ def run_gpu(args, dist, rank, world):
     out = dict(metric=METRIC, value=round(value, 1), unit="Gaussians/s", n_gpus=world, steps=args.steps,
                warmup=args.warmup, ms_per_step=round(ms_step, 4), higher_is_better=True,
                scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
-               config=dict(workload=f"vectorize-{args.paths}-1024: 1024x1024 RGB, {args.paths} closed filled NURBS "
-                                    "paths p in {2,3,4,5}, 8-64 key points, fill grid step h=1",
+               config=dict(workload=workload_name(args.paths),
                            gaussians_per_step=G, pairs_per_step=int(rep.pairs), curves=sc.n_curves,
                            fill_culled=int(rep.fill_culled),
                            l2=(f"inputs larger than L2 (records+pairs {(G * 32 + rep.pairs * 16) / 1e6:.0f} MB "
@@ -800,7 +804,7 @@ def main():
         print(json.dumps(dict(impl="reference", metric=METRIC, value=round(val, 1), unit="Gaussians/s",
                               n_gpus=world, steps=args.steps, warmup=args.warmup, ms_per_step=round(ms, 2),
                               higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
-                              data="synthetic", config=dict(workload="vectorize-2048-1024 (bounded sample)"),
+                              data="synthetic", config=dict(workload=workload_name(), sample=sample),
                               cpu_baseline=dict(value=round(val, 1), unit="Gaussians/s", cores=cores,
                                                 kind="oracle", sample=sample),
                               e2e=dict(value=round(val, 1), unit="Gaussians/s", h2d_bytes_per_step=0,
