@@ -185,9 +185,10 @@ typedef struct {
   int64_t blend_contribs;  /* (pixel, Gaussian) pairs composited by the last splat_forward */
   int64_t blend_visits;    /* (pixel, list entry) pairs the last splat_forward walked: per pixel, its
                               tile list up to and including the entry that ended it (Eq. 8-9's loop
-                              with early termination), whether or not the entry was evaluated */
+                              with early termination), whether or not the entry was evaluated; 0 with
+                              fill layers, whose lists hold one entry per layer, not per Gaussian */
   int64_t blend_bwd_visits; /* the same for the last splat_backward: per pixel, the entries in front
-                               of its last composited one, inclusive */
+                               of its last composited one, inclusive (0 with fill layers) */
 } ns_report;
 
 /* Kernel ids for ns_profile_next_launch. */
