@@ -259,6 +259,10 @@ ns_status splat_forward(const ns_curves* curves, const ns_gaussians* g,
  * through the sampling of nurbs_sample (same workspace, same settings) into
  * the key points, knot intervals, colours and opacities; counts, spans, grid
  * placement, nearest segments and winding signs are held fixed.
+ *   rp: the raster settings of the splat_forward this call follows (the
+ *     lists and per-pixel state it left in the workspace).  With other
+ *     settings the gradients are wrong (a per-Gaussian adjoint skips the
+ *     entries of fill layers), though nothing is read out of bounds.
  *   dL_dimage: device, same layout as the image.
  *   dgauss: device [g->capacity*8] or NULL: {dmu_x, dmu_y, dsigma, 0,
  *     dopacity, dr, dg, db} per Gaussian, zeroed and written by this call.

@@ -735,8 +735,8 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
   for (int base = 0; base < n && !__all_sync(0xffffffffu, all_done()); base += 32) {
     const int j = base + lane;
     bool hit = false;
-    if (j < n) {
-      const uint32_t g = gid[rg.x + j];
+    const uint32_t g = j < n ? gid[rg.x + j] : kLayerBit;
+    if (!(g & kLayerBit)) {   // fill-layer entries (settings of another pass) are never read here
       const float4 q = prep[g];
       hit = rect_d2(q.x, q.y, wr.x, wr.y, wr.z, wr.w) <= reach[g].x;
       if (hit) {
@@ -863,8 +863,8 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
   for (int base = ((wmax - 1) >> 5) << 5; base >= 0 && wmax > 0; base -= 32) {
     const int j = base + lane;
     bool hit = false;
-    if (j < wmax) {
-      const uint32_t g = gid[rg.x + j];
+    const uint32_t g = j < wmax ? gid[rg.x + j] : kLayerBit;
+    if (!(g & kLayerBit)) {   // fill-layer entries (settings of another pass) are never read here
       const float4 q = prep[g];
       const float2 rs = reach[g];
       hit = rect_d2(q.x, q.y, wr.x, wr.y, wr.z, wr.w) <= rs.x;
@@ -1105,8 +1105,10 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
     uint32_t g = 0;
     if (j < n) {
       g = gid[rg.x + j];
-      q = prep[g];
-      r2 = reach[g].x;
+      if (!(g & kLayerBit)) {   // fill-layer entries (settings of another pass) are never read here
+        q = prep[g];
+        r2 = reach[g].x;
+      }
     }
     bool hit;
     unsigned int m = group_masks(j < n, q.x, q.y, r2, bxf, y0, y1, hit);
@@ -1232,8 +1234,10 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
     uint32_t g = 0;
     if (j < wmax) {
       g = gid[rg.x + j];
-      q = prep[g];
-      rs = reach[g];
+      if (!(g & kLayerBit)) {   // fill-layer entries (settings of another pass) are never read here
+        q = prep[g];
+        rs = reach[g];
+      }
     }
     bool hit;
     unsigned int m = group_masks(j < wmax, q.x, q.y, rs.x, bxf, y0, y1, hit);
