@@ -36,15 +36,16 @@ PEAKS_FALLBACK = dict(hbm_gbs=6400.0, sm_max_mhz=2032.0)
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one `ncu --set full` capture of the 512-path version of the workload at tile
 # 8 with fill layers (profiles/*_vectorize-512-1024.md), with the units that
-# launch processed and the hash of the kernel source it ran (for the blend
-# kernels, the source after a comment-only edit made since the capture).  The bench
+# launch processed and the hash of the kernel source it ran (for the
+# fill-layer blend kernels, the file after later edits that left those
+# kernels unchanged: comments, and a guard in the per-Gaussian kernels).  The bench
 # scales the bytes to its own launch by the units processed, and reports null
 # if the source, the tile or the binning has changed since the capture.
 TRAFFIC = dict(
     blend_bwd=dict(bytes=86937856, units=2027197, unit="gaussians", tile=8, layers=1,
-                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="23c413e0cbeb8fd8"),
+                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="01705d0bf105706e"),
     blend_fwd=dict(bytes=28032000, units=2027197, unit="gaussians", tile=8, layers=1,
-                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="23c413e0cbeb8fd8"),
+                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="01705d0bf105706e"),
     chain=dict(bytes=88732672, units=2027197, unit="gaussians", tile=None, layers=None,
                src="paper_2606_31764_b300/csrc/ns_backward.cu", sha="9153ecc170fdaa06"),
     emit=dict(bytes=2934528, units=2027197, unit="gaussians", tile=None, layers=None,
