@@ -578,7 +578,7 @@ __global__ void __launch_bounds__(256) k_cluster_boxes(const CurvePlan* __restri
 }
 
 // Persistent: each block iteration handles one task of 256 Gaussians of one curve.
-__global__ void __launch_bounds__(256, 4) k_emit(ns_curves cv, ns_sample_params sp, const CurvePlan* __restrict__ plan,
+__global__ void __launch_bounds__(256, 5) k_emit(ns_curves cv, ns_sample_params sp, const CurvePlan* __restrict__ plan,
                                               const int* __restrict__ order, const float* __restrict__ knots,
                                               const float2* __restrict__ bpts, const DevState* __restrict__ st,
                                               float4* rec, int* gcurve, int* gaux, long long gcap, long long bcap,
