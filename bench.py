@@ -34,13 +34,11 @@ import scenes  # noqa: E402
 PEAKS_FALLBACK = dict(hbm_gbs=6400.0, sm_max_mhz=2032.0)
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
-# one `ncu --set full` capture of the 512-path version of the workload at tile
-# 8 with fill layers (profiles/*_vectorize-512-1024.md), with the units that
-# launch processed and the hash of the kernel source it ran (for the
-# fill-layer blend kernels, the file after later edits that left those
-# kernels unchanged: comments, and a guard in the per-Gaussian kernels).  The bench
-# scales the bytes to its own launch by the units processed, and reports null
-# if the source, the tile or the binning has changed since the capture.
+# one ncu capture per kernel of the 512-path version of the workload at tile 8
+# with fill layers, with the units that launch processed and the hash of the
+# kernel source it ran.  The bench scales the bytes to its own launch by the
+# units processed, and reports null if the source, the tile or the binning has
+# changed since the capture.
 TRAFFIC = dict(
     blend_bwd=dict(bytes=86937856, units=2027197, unit="gaussians", tile=8, layers=1,
                    src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="01705d0bf105706e"),
@@ -253,7 +251,8 @@ def autotune(torch, scene, tiles, capacity, steps=3, adam=False, geometry=None, 
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
         table[f"{tile}" + ("-layers" if fl else "")] = dict(ms=round(ms, 4), ppt_fwd=int(st.sp.rp.ppt_fwd),
-                                                             ppt_bwd=int(st.sp.rp.ppt_bwd))
+                                                             ppt_bwd=int(st.sp.rp.ppt_bwd),
+                                                             pairs=int(st.sp.report().pairs))
         if best_ms is None or ms < best_ms:
             if best is not None:
                 del best
@@ -326,7 +325,7 @@ def run_gpu(args, dist, rank, world):
     torch.cuda.synchronize()
 
     # K-step graph with per-kernel events armed in every step
-    prof = ["plan", "emit", "bin_count", "bin_emit", "radix_scatter", "ranges", "blend_fwd", "mse", "blend_bwd",
+    prof = ["plan", "boundary", "emit", "bin_count", "bin_emit", "radix_scatter", "ranges", "blend_fwd", "mse", "blend_bwd",
             "chain", "chain_contour", "chain_boundary", "knot_grads"]
     ev = {k: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)] for k in prof}
@@ -442,9 +441,8 @@ def run_gpu(args, dist, rank, world):
                gpu_launches=launches_per_step * args.steps, launches_per_step=launches_per_step,
                autotune=tuning,
                clocks=ck, roofline=roof, kernels=kernels, e2e=e2e,
-               blend=dict(visits_fwd=int(rep.blend_visits), visits_bwd=int(rep.blend_bwd_visits),
-                          evals_fwd=int(rep.blend_evals), evals_bwd=int(rep.blend_bwd_evals),
-                          composited=int(rep.blend_contribs)),
+               live_gaussians_per_s=round(world * (G - int(rep.fill_culled)) * args.steps / (ms_total / 1e3), 1),
+               blend=blend_units(rep, tuning, per_kernel, layers),
                sample=costs)
     if args.headline_only:
         return out, step
@@ -455,6 +453,28 @@ def run_gpu(args, dist, rank, world):
         out["long_spline"] = run_long_spline(torch, args)
         out["layerwise"] = run_layerwise(torch)
     return out, step
+
+
+def blend_units(rep, tuning, per_kernel, layers):
+    """Blend work in the unit of the scope table: pair-evals = sum over tiles
+    of |list| x tile pixels, the (pixel, Gaussian) pairs Eq. 8-9's loop would
+    walk before early termination, with |list| the per-Gaussian tile lists
+    (with fill layers, those the per-Gaussian binning of the same tile size
+    produced in the autotuner's trial); besides the alpha evaluations the
+    kernels performed and the pairs composited."""
+    tile = int(tuning["tile"])
+    pg = rep.pairs if not layers else tuning["tried"].get(str(tile), {}).get("pairs")
+    out = dict(visits_fwd=int(rep.blend_visits), visits_bwd=int(rep.blend_bwd_visits),
+               evals_fwd=int(rep.blend_evals), evals_bwd=int(rep.blend_bwd_evals),
+               composited=int(rep.blend_contribs), per_gaussian_pairs=None if pg is None else int(pg))
+    if pg is not None:
+        pe = int(pg) * tile * tile
+        out.update(pair_evals_listed=pe,
+                   pair_evals_per_s_fwd=round(pe / (per_kernel["blend_fwd"] / 1e3), 1),
+                   pair_evals_per_s_bwd=round(pe / (per_kernel["blend_bwd"] / 1e3), 1))
+    out["evals_per_s_fwd"] = round(rep.blend_evals / (per_kernel["blend_fwd"] / 1e3), 1)
+    out["evals_per_s_bwd"] = round(rep.blend_bwd_evals / (per_kernel["blend_bwd"] / 1e3), 1)
+    return out
 
 
 def run_layerwise(torch, rounds=4, iters=100):
@@ -758,21 +778,69 @@ def oracle_sample_scene(n_curves, seed=1005):
     return b.build("vectorize-sample", sc.target, dict(sc.sample), dict(sc.raster))
 
 
-def run_oracle_sample(n_curves):
+def run_oracle_sample(n_curves, threads=None):
+    """The oracle's fwd+bwd on the first n_curves paths, timed on `threads`
+    host threads (default: every core of the machine)."""
     import torch
     from oracle import pipeline as op
     sub = oracle_sample_scene(n_curves)
-    t0 = time.perf_counter()
-    ref = op.loss_and_grads(sub)
-    dt = time.perf_counter() - t0
+    old = torch.get_num_threads()
+    torch.set_num_threads(threads or os.cpu_count() or old)
+    try:
+        t0 = time.perf_counter()
+        ref = op.loss_and_grads(sub)
+        dt = time.perf_counter() - t0
+        used = torch.get_num_threads()
+    finally:
+        torch.set_num_threads(old)
     G = int(sum(p.count for p in ref["plans"]))
-    return sub, ref, dt, G, torch.get_num_threads()
+    return sub, ref, dt, G, used
 
 
-def grad_rel_err(sub, ref):
-    """GPU step on the oracle's sample; max over tensors of ||g - g_ref|| / ||g_ref||."""
+def oracle_context(n_curves_1t=8, n_scenes_cfg4=4):
+    """Oracle timings beside the headline: one thread on a small sample of the
+    1024x1024 workload, and the batched 64-scene workload's first scenes on
+    every core, with the full workload's time extrapolated per scene."""
     import torch
-    step = Step(sub, capacity=(200_000, 800_000, 20_000))
+    from oracle import pipeline as op
+    _, _, dt1, G1, _ = run_oracle_sample(n_curves_1t, threads=1)
+    sc4 = scenes.config4().subset(list(range(n_scenes_cfg4)))
+    old = torch.get_num_threads()
+    torch.set_num_threads(os.cpu_count() or old)
+    try:
+        t0 = time.perf_counter()
+        ref4 = op.loss_and_grads(sc4)
+        dt4 = time.perf_counter() - t0
+        th = torch.get_num_threads()
+    finally:
+        torch.set_num_threads(old)
+    G4 = int(sum(p.count for p in ref4["plans"]))
+    full4 = scenes.config4()
+    return dict(
+        one_thread=dict(value=round(G1 / dt1, 1), unit="Gaussians/s", cores=1, seconds=round(dt1, 2),
+                        sample=f"first {n_curves_1t} of the 2048 paths of the 1024x1024 workload, {G1} Gaussians, "
+                               "one fwd+bwd"),
+        batched_64x256=dict(value=round(G4 / dt4, 1), unit="Gaussians/s", cores=th, seconds=round(dt4, 2),
+                            sample=f"first {n_scenes_cfg4} of the 64 scenes of the batched 256x256 workload, "
+                                   f"{G4} Gaussians, one fwd+bwd",
+                            extrapolated_full_s=round(dt4 * full4.n_scenes / n_scenes_cfg4, 1),
+                            extrapolation="per-scene cost of the sample times 64 scenes"))
+
+
+def parity_at_timed_config(sub, ref, tuning):
+    """The GPU step in the configuration the bench times (the autotuner's tile,
+    binning and decompositions) on the oracle's sample of the workload:
+    gradient errors (max over tensors of ||g - g_ref|| / ||g_ref||) and the
+    image error in three forms: at the parity thresholds; at the production
+    thresholds outside pixels whose threshold decision lies within 1e-4 of its
+    tie in the oracle; and at the production thresholds unfiltered (where a
+    flipped alpha_min decision moves a pixel by up to alpha_min times a colour
+    difference)."""
+    import torch
+    from oracle import pipeline as op
+    tuned = {k: int(tuning[k]) for k in ("tile", "fill_layers", "ppt_fwd", "ppt_bwd")}
+    cap = (300_000, 1_600_000, 20_000)
+    step = Step(sub, capacity=cap, raster=dict(sub.raster, **tuned))
     step()
     torch.cuda.synchronize()
     errs = {}
@@ -781,8 +849,26 @@ def grad_rel_err(sub, ref):
         gg = g.cpu().numpy().astype(np.float64).reshape(-1)
         rr = np.asarray(r, np.float64).reshape(-1)
         errs[nm] = float(np.linalg.norm(gg - rr) / max(np.linalg.norm(rr), 1e-30))
-    img_err = float(np.abs(step.image.cpu().numpy() - ref["image"]).max())
-    return max(errs.values()), errs, img_err
+    img = step.image.cpu().numpy().astype(np.float64)
+    del step
+    k, t, c = op.leaves(sub, False)
+    with torch.no_grad():
+        _, _, flags = op.render(sub, k, t, c, plans=ref["plans"], return_flags=True)
+    flags = flags.numpy()
+    d = np.abs(img - ref["image"])
+    ok = np.broadcast_to(~flags[..., None], d.shape)
+    subp = sub.with_raster(**scenes.RASTER_PARITY)
+    with torch.no_grad():
+        refp, _ = op.render(subp, k, t, c, plans=ref["plans"])
+    stepp = Step(subp, capacity=cap, raster=dict(subp.raster, **tuned))
+    stepp()
+    torch.cuda.synchronize()
+    dp = float(np.abs(stepp.image.cpu().numpy().astype(np.float64) - refp.numpy()).max())
+    del stepp
+    image = dict(parity_thresholds=dp, production_outside_near_threshold=float(d[ok].max(initial=0.0)),
+                 production_unfiltered=float(d.max()), near_threshold_pixels=int(flags.sum()),
+                 pixels=int(flags.size), flag_rel=1e-4, gate=1e-5, raster=tuned)
+    return max(errs.values()), errs, image
 
 
 def main():
@@ -817,11 +903,15 @@ def main():
         out["cpu_baseline"] = dict(value=round(G / dt, 1), unit="Gaussians/s", cores=cores, kind="oracle",
                                    sample=f"first {args.cpu_sample_curves} of the 2048 paths of the 1024x1024 "
                                           f"workload on the full canvas, {G} Gaussians, one fwd+bwd",
-                                   seconds=round(dt, 2))
-        gre, errs, img_err = grad_rel_err(sub, ref)
+                                   seconds=round(dt, 2),
+                                   extrapolated_full_s=round(dt * 2048 / args.cpu_sample_curves, 1),
+                                   extrapolation="per-path cost of the sample times 2048 paths")
+        out["cpu_baseline"].update(oracle_context())
+        gre, errs, image = parity_at_timed_config(sub, ref, out["autotune"])
         out["grad_rel_err"] = round(gre, 7)
         out["grad_rel_err_detail"] = {k: round(v, 7) for k, v in errs.items()}
-        out["image_max_abs_err_vs_oracle"] = img_err
+        out["image_err_vs_oracle"] = image
+        out["image_max_abs_err_vs_oracle"] = image["parity_thresholds"]
     if rank == 0:
         print(json.dumps(out))
     if dist is not None:

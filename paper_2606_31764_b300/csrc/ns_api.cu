@@ -129,6 +129,10 @@ bool make_layout(const ns_curves* c, const ns_capacity* cap, const ns_raster_par
   L->o_dbpts = take(sizeof(float2) * (size_t)L->bcap);
   L->o_bcurve = take(sizeof(int) * (size_t)L->bcap);
   L->o_cbox = take(sizeof(float4) * (size_t)L->bcap);   // at the index of each cluster's first point
+  L->o_bloc = take(sizeof(float4) * (size_t)L->bcap);
+  L->o_glo = take(sizeof(float2) * (size_t)L->nc);
+  L->o_knots_lo = take(sizeof(float) * nkn);
+  L->o_krcp = take(sizeof(float2) * kMaxP * nkn);
   // each curve's tasks cover its Gaussians in chunks of kChunk: within the
   // Gaussian capacity there are at most gcap/kChunk + n_curves of them
   L->tcap = L->gcap / kChunk + L->nc + 1;
@@ -146,7 +150,7 @@ bool make_layout(const ns_curves* c, const ns_capacity* cap, const ns_raster_par
   L->o_nsub = take(sizeof(int) * (size_t)L->n_pix);
   // fill layers: per curve, the grid run of each tile column and row
   L->o_lruns = take(sizeof(int2) * (size_t)L->nc * (size_t)(L->tiles_x + L->tiles_y));
-  L->o_lconst = take(sizeof(float4) * 2 * (size_t)L->nc);   // per layer {x0, y0, 1/h, R}, {sigma, ncoef, nx, ny}
+  L->o_lconst = take(sizeof(float4) * 3 * (size_t)L->nc);   // per layer {X0, Y0, xoff, yoff}, {sigma, ncoef, nx, ny}, {h, 1/h, R, 0}
   L->o_lmin = take(sizeof(int2) * (size_t)L->nc);   // per layer: smallest live grid column and row
   L->o_lmax = take(sizeof(int2) * (size_t)L->nc);   // largest
   L->o_dgauss = take(sizeof(float) * 12 * (size_t)L->gcap);   // 8 per Gaussian, 12 when tangent-aligned

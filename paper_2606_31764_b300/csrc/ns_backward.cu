@@ -85,9 +85,9 @@ __device__ __forceinline__ int span_at(const CurveRef& cr, const float* U, float
 
 // Fill tasks: each thread one fill Gaussian (latency-bound loads and a few
 // arithmetic steps; the contour tasks have a kernel of their own).
-__global__ void __launch_bounds__(256) k_chain(ns_curves cv, ChainParams cp, const CurvePlan* __restrict__ plan,
+__global__ void __launch_bounds__(256, 8) k_chain(ns_curves cv, ChainParams cp, const CurvePlan* __restrict__ plan,
                                                const int* __restrict__ order, const float* __restrict__ knots,
-                                               const float2* __restrict__ bpts, const DevState* __restrict__ st,
+                                               const float4* __restrict__ bloc, const DevState* __restrict__ st,
                                                const float4* __restrict__ rec, const int* __restrict__ gaux,
                                                const float* __restrict__ dgauss, long long gcap, long long bcap,
                                                float* dkey, float* dknots, float2* dbpts, float* dcolor, int row4) {
@@ -127,10 +127,14 @@ __global__ void __launch_bounds__(256) k_chain(ns_curves cv, ChainParams cp, con
       const bool inside = aux >= 0;
       const int i0 = inside ? aux : ~aux;
       const int i1 = i0 + 1 == B ? 0 : i0 + 1;
-      const float4 r = rec[g];
-      const float2 b0 = bpts[pl.b_off + i0], b1 = bpts[pl.b_off + i1];
-      const float ex = b1.x - b0.x, ey = b1.y - b0.y;
-      const float rx = r.x - b0.x, ry = r.y - b0.y;
+      // in grid-local coordinates with the polyline's low parts, as nurbs_sample
+      // formed the distance (the direction below stays exact near the polyline)
+      const int nxx = max(pl.nx, 1);
+      const float qx = (float(l % nxx) + 0.5f) * pl.h, qy = (float(l / nxx) + 0.5f) * pl.h;
+      const float4 b0 = bloc[pl.b_off + i0], b1 = bloc[pl.b_off + i1];
+      const float ex = __fadd_rn(__fsub_rn(b1.x, b0.x), __fsub_rn(b1.z, b0.z));
+      const float ey = __fadd_rn(__fsub_rn(b1.y, b0.y), __fsub_rn(b1.w, b0.w));
+      const float rx = __fsub_rn(__fsub_rn(qx, b0.x), b0.z), ry = __fsub_rn(__fsub_rn(qy, b0.y), b0.w);
       const float ee = ex * ex + ey * ey;
       const float t = ee > 0.f ? fminf(fmaxf((rx * ex + ry * ey) / ee, 0.f), 1.f) : 0.f;
       const float dx = rx - t * ex, dy = ry - t * ey;
@@ -541,7 +545,8 @@ extern "C" ns_status splat_backward(const ns_curves* curves, const ns_gaussians*
       cp.freeze_w = (out->frozen & NS_FROZEN_WEIGHTS) != 0;
       cp.tmap = at<const int>(ws, L.o_tasks);
       cp.tcap = L.tcap;
-      NS_LAUNCH(NS_KERNEL_CHAIN, k_chain, num_sms() * 8, 256, 0, s, *curves, cp, plan, order, knots, bpts, st,
+      NS_LAUNCH(NS_KERNEL_CHAIN, k_chain, num_sms() * 8, 256, 0, s, *curves, cp, plan, order, knots,
+                at<const float4>(ws, L.o_bloc), st,
                 reinterpret_cast<const float4*>(g->rec), g->aux, dg, cap->gaussians,
                 cap->boundary, out->dkey, dknots, dbpts, out->dcolor, row / 4);
       {

@@ -79,6 +79,10 @@ struct Layout {
   size_t o_tasks = 0;        // task -> curve table (fill tasks first, then contour tasks)
   size_t o_bcurve = 0;       // boundary point -> curve
   size_t o_cbox = 0;         // bounding box of each 8-segment cluster of a boundary polyline
+  size_t o_bloc = 0;         // boundary points relative to their curve's fill grid origin, {x_hi, y_hi, x_lo, y_lo}
+  size_t o_glo = 0;          // per curve: the low parts {x0_lo, y0_lo} of the fill grid origin (plan x0, y0 = high parts)
+  size_t o_knots_lo = 0;     // low parts of the knot vectors (knots = their high parts, the exact sums rounded)
+  size_t o_krcp = 0;         // per knot slot k and width j = 1..kMaxP: 1 / (U[k + j] - U[k]) as {hi, lo} (filled curves)
   int64_t tcap = 0;          // entries of that table
 };
 

@@ -1372,7 +1372,8 @@ struct LayerArgs {
   const float4* rec;
   const int* gcount;
   const int2* runs;   // per curve: covered column run per tile column, then row run per tile row
-  const float4* lconst;   // per curve: {x0, y0, 1/h, R}, {sigma, ncoef, nx bits, ny bits} (k_layer_runs)
+  const float4* lconst;   // per curve: {X0, Y0, xoff, yoff}, {sigma, ncoef, nx bits, ny bits}, {h, 1/h, R, 0}
+                          // with the grid origin X0 + xoff (X0 an integer), from k_layer_runs
   int gcap, tile, tiles_x, runs_stride;
   float k_sigma, inv_tile, log_amin;
   int* nsub;   // per pixel: 1 + sample index of the last composited fill Gaussian (0: none)
@@ -1382,7 +1383,8 @@ struct LayerArgs {
 struct LayerView {
   long long g_off, G;   // first Gaussian; Gaussians in the set (nothing at or past G is read)
   int nx, ny;
-  float x0, y0, inv_h, sig, nc, R;
+  float x0, y0, inv_h, sig, nc, R;   // x0, y0: the grid origin rounded to float (windows only)
+  float X0, Y0, xoff, yoff, h;       // the origin as integer + offset, for the exact local offsets
   int cx0, cx1, cy0, cy1;   // columns and rows binned to this tile (empty when cx0 > cx1)
 };
 
@@ -1427,7 +1429,8 @@ __device__ __forceinline__ void covered_run(int n, float guess, F ok, int& lo, i
 // exponent coefficient the per-Gaussian binning would prepare.
 __global__ void __launch_bounds__(128) k_layer_runs(ns_curves cv, const CurvePlan* __restrict__ plan,
                                                     const float4* __restrict__ rec, const int* __restrict__ gcount,
-                                                    BinParams bp, int2* runs, int stride, float4* lconst) {
+                                                    BinParams bp, int2* runs, int stride, float4* lconst,
+                                                    const float2* __restrict__ glo) {
   const int c = blockIdx.x;
   if (!(cv.flags[c] & NS_FILLED)) return;
   const CurvePlan p = plan[c];
@@ -1438,8 +1441,14 @@ __global__ void __launch_bounds__(128) k_layer_runs(ns_curves cv, const CurvePla
     const float o_c = cv.color[4 * c + 3];
     const float R = !(o_c > 0.f) ? 0.f
                     : (bp.log_amin > -1e30f ? sqrtf(reach2(sig, o_c, bp.log_amin)) + 0.01f * p.h : FLT_MAX);
-    lconst[2 * c] = make_float4(p.x0, p.y0, 1.f / p.h, R);
-    lconst[2 * c + 1] = make_float4(sig, ncoef(sig), __int_as_float(p.nx), __int_as_float(p.ny));
+    // origin = X0 + xoff with X0 an integer: pixel centre - X0 is exact, and
+    // xoff (the fraction plus the low part of nurbs_sample's FP64 origin) keeps
+    // the offset of a pixel from a grid point exact to ~1e-7 px at any canvas size
+    const float2 lo = glo[c];
+    const float X0 = floorf(p.x0), Y0 = floorf(p.y0);
+    lconst[3 * c] = make_float4(X0, Y0, __fadd_rn(__fsub_rn(p.x0, X0), lo.x), __fadd_rn(__fsub_rn(p.y0, Y0), lo.y));
+    lconst[3 * c + 1] = make_float4(sig, ncoef(sig), __int_as_float(p.nx), __int_as_float(p.ny));
+    lconst[3 * c + 2] = make_float4(p.h, 1.f / p.h, R, 0.f);
   }
   int tx0, ty0, ntx;
   const int nt = layer_rect_live(rec, p, G, bp, c, tx0, ty0, ntx);
@@ -1477,24 +1486,30 @@ __global__ void __launch_bounds__(128) k_layer_runs(ns_curves cv, const CurvePla
 // the entry of a list batch: the layer constants and the grid runs of the
 // tile ({column run, row run}).
 __device__ __forceinline__ void layer_entry(const LayerArgs& la, int c, int tx, int ty, float4& k0, float4& k1,
-                                            int4& run) {
-  k0 = la.lconst[2 * c];
-  k1 = la.lconst[2 * c + 1];
+                                            float4& k2, int4& run) {
+  k0 = la.lconst[3 * c];
+  k1 = la.lconst[3 * c + 1];
+  k2 = la.lconst[3 * c + 2];
   const int2* r = la.runs + (long long)c * la.runs_stride;
   const int2 rx = r[tx], ry = r[la.tiles_x + ty];
   run = make_int4(rx.x, rx.y, ry.x, ry.y);
 }
 
-__device__ __forceinline__ LayerView layer_view(const float4& k0, const float4& k1, const int4& run, long long g_off,
-                                                long long G) {
+__device__ __forceinline__ LayerView layer_view(const float4& k0, const float4& k1, const float4& k2,
+                                                const int4& run, long long g_off, long long G) {
   LayerView v;
   const int2 rx = make_int2(run.x, run.y), ry = make_int2(run.z, run.w);
   v.G = G;
   v.g_off = g_off;
-  v.x0 = k0.x;
-  v.y0 = k0.y;
-  v.inv_h = k0.z;
-  v.R = k0.w;
+  v.X0 = k0.x;
+  v.Y0 = k0.y;
+  v.xoff = k0.z;
+  v.yoff = k0.w;
+  v.x0 = k0.x + k0.z;
+  v.y0 = k0.y + k0.w;
+  v.h = k2.x;
+  v.inv_h = k2.y;
+  v.R = k2.z;
   v.sig = k1.x;
   v.nc = k1.y;
   v.nx = __float_as_int(k1.z);
@@ -1529,6 +1544,21 @@ __device__ __forceinline__ void layer_window(const LayerView& v, float fx, float
 // per-Gaussian conditions; the tile itself is covered by construction).
 __device__ __forceinline__ bool layer_point_binned(const float4& r, float alpha_min) {
   return r.z > 0.f && r.w > 0.f && r.w >= alpha_min;
+}
+
+// Grid-local coordinate of grid column (row) i, as nurbs_sample placed it.
+__device__ __forceinline__ float layer_qx(const LayerView& v, int i) { return (float(i) + 0.5f) * v.h; }
+
+// alpha of a layer's grid point (staged {qx, qy, ncoef, o} in grid-local
+// coordinates) at the pixel whose centre minus the integer origin is (fxl,
+// fyl): the offset (fxl - qx) - xoff is exact to ~1e-7 px, then as gauss_alpha.
+__device__ __forceinline__ float layer_alpha(const LayerView& v, float fxl, float fyl, const float4& q, float amax,
+                                             float& dx, float& dy, float& d2, float& e) {
+  dx = __fsub_rn(__fsub_rn(fxl, q.x), v.xoff);
+  dy = __fsub_rn(__fsub_rn(fyl, q.y), v.yoff);
+  d2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
+  e = __expf(__fmul_rn(q.z, d2));
+  return fminf(__fmul_rn(q.w, e), amax);
 }
 
 // The warp's region of a layer: the grid points the pixel centres of its
@@ -1566,7 +1596,7 @@ __device__ __forceinline__ bool layer_stage(const LayerArgs& la, const LayerView
     if (g < v.G) {
       const float4 r = la.rec[g];
       if (layer_point_binned(r, alpha_min)) {
-        q = make_float4(r.x, r.y, r.z == v.sig ? v.nc : ncoef(r.z), r.w);
+        q = make_float4(layer_qx(v, rx0 + ixr), layer_qx(v, ry0 + iyr), r.z == v.sig ? v.nc : ncoef(r.z), r.w);
         live = true;
       }
     }
@@ -1601,6 +1631,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
   __shared__ float4 s_c[Gm::kWarps][32];
   __shared__ uint32_t s_id[Gm::kWarps][32];
   __shared__ float4 s_k1[Gm::kWarps][32];    // a layer's second constants
+  __shared__ float4 s_k2[Gm::kWarps][32];    // a layer's third constants
   __shared__ int4 s_run[Gm::kWarps][32];     // a layer's grid runs on this tile
   __shared__ float4 s_pt[Gm::kWarps][kPts];
   int s, px, py0;
@@ -1666,13 +1697,14 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
       if (g & kLayerBit) {
         hit = true;
         const int c = gcurve[gi];
-        float4 k0, k1;
+        float4 k0, k1, k2;
         int4 run;
-        layer_entry(la, c, tx, ty, k0, k1, run);
+        layer_entry(la, c, tx, ty, k0, k1, k2, run);
         s_id[w][lane] = g;
         s_c[w][lane] = color[c];
         s_q[w][lane] = k0;
         s_k1[w][lane] = k1;
+        s_k2[w][lane] = k2;
         s_run[w][lane] = run;
       } else {
         const float4 q = prep[gi];
@@ -1694,7 +1726,8 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
       if (id & kLayerBit) {
         if (!__any_sync(0xffffffffu, !all_done())) break;
         const uint32_t g0 = id & ~kLayerBit;
-        const LayerView v = layer_view(s_q[w][b], s_k1[w][b], s_run[w][b], g0, Gset);
+        const LayerView v = layer_view(s_q[w][b], s_k1[w][b], s_k2[w][b], s_run[w][b], g0, Gset);
+        const float fxl = __fsub_rn(fx, v.X0);
         int rx0, rx1, ry0, ry1;
         if (!layer_region(v, wr, rx0, rx1, ry0, ry1)) continue;
         const int rw = rx1 - rx0 + 1, rh = ry1 - ry0 + 1;
@@ -1711,6 +1744,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
         for (int k = 0; k < PPT; ++k) {
           if (done[k]) continue;
           const float fy = py0 + 4 * k + 0.5f;
+          const float fyl = __fsub_rn(fy, v.Y0);
           int ix0, ix1, iy0, iy1;
           layer_window(v, fx, fy, ix0, ix1, iy0, iy1);
           const int pos = base + b + 1;
@@ -1724,14 +1758,17 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
               for (; ix + 1 <= ix1 && !done[k]; ix += 2) {
                 const float4 qa = prow[ix], qb = prow[ix + 1];
                 float dx, dy, d2, ea, eb;
-                const float aa = gauss_alpha(fx, fy, qa, bp.alpha_max, dx, dy, d2, ea);
-                const float ab = gauss_alpha(fx, fy, qb, bp.alpha_max, dx, dy, d2, eb);
+                const float aa = layer_alpha(v, fxl, fyl, qa, bp.alpha_max, dx, dy, d2, ea);
+                const float ab = layer_alpha(v, fxl, fyl, qb, bp.alpha_max, dx, dy, d2, eb);
                 if (qa.w >= 0.f) composite_alpha(k, aa, cc, pos, rowsub + ix + 1);
                 if (qb.w >= 0.f && !done[k]) composite_alpha(k, ab, cc, pos, rowsub + ix + 2);
               }
               if (ix <= ix1 && !done[k]) {
                 const float4 q = prow[ix];
-                if (q.w >= 0.f) composite(k, fy, q, cc, pos, rowsub + ix + 1);
+                float dx, dy, d2, e;
+                if (q.w >= 0.f)
+                  composite_alpha(k, layer_alpha(v, fxl, fyl, q, bp.alpha_max, dx, dy, d2, e), cc, pos,
+                                  rowsub + ix + 1);
               }
             } else {
               for (int ix = ix0; ix <= ix1 && !done[k]; ++ix) {
@@ -1739,8 +1776,10 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
                 if (g >= v.G) break;
                 const float4 r = la.rec[g];
                 if (!layer_point_binned(r, bp.alpha_min)) continue;
-                composite(k, fy, make_float4(r.x, r.y, r.z == v.sig ? v.nc : ncoef(r.z), r.w), cc, pos,
-                          rowsub + ix + 1);
+                const float4 q = make_float4(layer_qx(v, ix), layer_qx(v, iy), r.z == v.sig ? v.nc : ncoef(r.z), r.w);
+                float dx, dy, d2, e;
+                composite_alpha(k, layer_alpha(v, fxl, fyl, q, bp.alpha_max, dx, dy, d2, e), cc, pos,
+                                rowsub + ix + 1);
               }
             }
           }
@@ -1800,6 +1839,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
   __shared__ float s_isig[Gm::kWarps][32];   // +-1/sigma, or a layer's curve (int bits)
   __shared__ uint32_t s_id[Gm::kWarps][32];
   __shared__ float4 s_k1[Gm::kWarps][32];    // a layer's second constants
+  __shared__ float4 s_k2[Gm::kWarps][32];    // a layer's third constants
   __shared__ int4 s_run[Gm::kWarps][32];     // a layer's grid runs on this tile
   __shared__ float4 s_pt[Gm::kWarps][kPts];
   __shared__ float s_reg[Gm::kWarps][kPts];
@@ -1879,13 +1919,14 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
       if (g & kLayerBit) {
         hit = true;
         const int c = gcurve[gi];
-        float4 k0, k1;
+        float4 k0, k1, k2;
         int4 run;
-        layer_entry(la, c, tx, ty, k0, k1, run);
+        layer_entry(la, c, tx, ty, k0, k1, k2, run);
         s_id[w][lane] = g;
         s_c[w][lane] = color[c];
         s_q[w][lane] = k0;
         s_k1[w][lane] = k1;
+        s_k2[w][lane] = k2;
         s_run[w][lane] = run;
         s_isig[w][lane] = __int_as_float(c);
       } else {
@@ -1918,7 +1959,8 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
         if (!__any_sync(0xffffffffu, any)) continue;   // no pixel of the warp walks this far back
         const uint32_t g0 = id & ~kLayerBit;
         const int c = __float_as_int(s_isig[w][b]);
-        const LayerView v = layer_view(s_q[w][b], s_k1[w][b], s_run[w][b], g0, Gset);
+        const LayerView v = layer_view(s_q[w][b], s_k1[w][b], s_k2[w][b], s_run[w][b], g0, Gset);
+        const float fxl = __fsub_rn(fx, v.X0);
         int rx0, rx1, ry0, ry1;
         if (!layer_region(v, wr, rx0, rx1, ry0, ry1)) continue;
         const int rw = rx1 - rx0 + 1, rh = ry1 - ry0 + 1;
@@ -1937,6 +1979,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
         for (int k = 0; k < PPT; ++k) {
           if (!want[k]) continue;
           const float fy = py0 + 4 * k + 0.5f;
+          const float fyl = __fsub_rn(fy, v.Y0);
           const int sstart = (jpos == last[k] - 1) ? lsub[k] - 1 : 0x7fffffff;
           int ix0, ix1, iy0, iy1;
           layer_window(v, fx, fy, ix0, ix1, iy0, iy1);
@@ -1952,8 +1995,8 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
               for (; ix - 1 >= ix0; ix -= 2) {
                 const float4 qa = prow[ix], qb = prow[ix - 1];
                 float dxa, dya, d2a, ea, dxb, dyb, d2b, eb;
-                const float aa = gauss_alpha(fx, fy, qa, bp.alpha_max, dxa, dya, d2a, ea);
-                const float ab = gauss_alpha(fx, fy, qb, bp.alpha_max, dxb, dyb, d2b, eb);
+                const float aa = layer_alpha(v, fxl, fyl, qa, bp.alpha_max, dxa, dya, d2a, ea);
+                const float ab = layer_alpha(v, fxl, fyl, qb, bp.alpha_max, dxb, dyb, d2b, eb);
                 float dO, col[3], daa;
                 if (qa.w >= 0.f && adjoint_alpha(k, aa, ea, qa.w, cc, dO, col, daa)) {
                   csum[0] += col[0];
@@ -1970,8 +2013,10 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
               }
               if (ix == ix0) {
                 const float4 q = prow[ix];
-                float dO, col[3], daa, dx, dy, d2;
-                if (q.w >= 0.f && adjoint(k, fy, q, cc, dO, col, daa, dx, dy, d2)) {
+                float dO, col[3], daa, dx, dy, d2, e;
+                if (q.w >= 0.f &&
+                    adjoint_alpha(k, layer_alpha(v, fxl, fyl, q, bp.alpha_max, dx, dy, d2, e), e, q.w, cc, dO, col,
+                                  daa)) {
                   csum[0] += col[0];
                   csum[1] += col[1];
                   csum[2] += col[2];
@@ -1989,9 +2034,11 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
               if (g >= v.G) continue;
               const float4 r = la.rec[g];
               if (!layer_point_binned(r, bp.alpha_min)) continue;
-              const float4 q = make_float4(r.x, r.y, r.z == v.sig ? v.nc : ncoef(r.z), r.w);
-              float dO, col[3], daa, dx, dy, d2;
-              if (!adjoint(k, fy, q, cc, dO, col, daa, dx, dy, d2)) continue;
+              const float4 q = make_float4(layer_qx(v, ix), layer_qx(v, iy), r.z == v.sig ? v.nc : ncoef(r.z), r.w);
+              float dO, col[3], daa, dx, dy, d2, e;
+              if (!adjoint_alpha(k, layer_alpha(v, fxl, fyl, q, bp.alpha_max, dx, dy, d2, e), e, q.w, cc, dO, col,
+                                 daa))
+                continue;
               if (!per_pair) {
                 csum[0] += col[0];
                 csum[1] += col[1];
@@ -2405,7 +2452,8 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
   }
   if (bp.fill_layers && L.nc > 0)
     NS_LAUNCH(NS_KERNEL_OTHER, k_layer_runs, L.nc, 128, 0, s, *curves, plan, rec, g->count, bp,
-              at<int2>(ws, L.o_lruns), L.tiles_x + L.tiles_y, at<float4>(ws, L.o_lconst));
+              at<int2>(ws, L.o_lruns), L.tiles_x + L.tiles_y, at<float4>(ws, L.o_lconst),
+              at<const float2>(ws, L.o_glo));
   cudaMemsetAsync(ranges, 0, sizeof(int2) * (size_t)L.n_tiles, s);
   NS_LAUNCH(NS_KERNEL_RANGES, k_ranges, num_sms() * 16, 256, 0, s, kin, st, ranges);
   const BlendArgs ba{ranges, vin, at<float4>(ws, L.o_prep), at<float2>(ws, L.o_prep2), at<float2>(ws, L.o_reach),

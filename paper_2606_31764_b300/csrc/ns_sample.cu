@@ -2,11 +2,14 @@
 //
 // Kernels, in launch order:
 //   k_plan          one block per curve: validation, knot vector (FP64 running
-//                   sum, stored FP32), arc length by N_L-node midpoint
+//                   sum, stored as FP32 high and low parts), arc length by N_L-node midpoint
 //                   quadrature of |C'| (Eq. 2-3, block reduction), counts
 //   k_scan_boundary one block: boundary-point offsets of filled curves
-//   k_boundary      one block per filled curve: boundary polyline b_i, its
-//                   padded and clipped box, the fill grid size
+//   k_boundary      one thread per boundary point b_i of the filled curves,
+//                   evaluated in double-float arithmetic
+//   k_boundary_box  one warp per filled curve: the polyline's padded and
+//                   clipped box, the fill grid origin (high and low parts) and
+//                   size, the points made relative to the origin
 //   k_scan_gauss    one block: Gaussian and task offsets in front-to-back order
 //   k_emit          persistent: one 256-Gaussian task per block iteration;
 //                   contour samples (Eq. 4-5) or fill points with the SDF of
@@ -14,9 +17,59 @@
 #include <cuda_runtime.h>
 #include <float.h>
 
+#include <algorithm>
+
 #include "ns_internal.cuh"
 
 namespace ns {
+
+// Boundary points are evaluated in double-float arithmetic: every value is an
+// unevaluated sum hi + lo of two floats (about 48 significant bits), built
+// from the error-free transformations TwoSum (Knuth) and TwoProduct (Dekker;
+// here with the fused multiply-add, as Ogita, Rump and Oishi write it).  The
+// knot vector (the same sums as k_plan), the parameters, the Cox-de Boor
+// triangle and the rational quotient of Eq. 1 all carry that precision.
+// FP32 evaluation at pixel coordinates near 1000 has errors of about 1e-4 px,
+// which the grid origin and, through the sigmoid of Eq. 7, the fill opacities
+// inherit; FP64 gives the same precision as double-float but runs far slower
+// on this part.
+struct df {
+  float h, l;
+};
+__device__ __forceinline__ df df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return df{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ df df_fast_two_sum(float a, float b) {   // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return df{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df df_add(df x, df y) {
+  df s = df_two_sum(x.h, y.h);
+  const df t = df_two_sum(x.l, y.l);
+  s = df_fast_two_sum(s.h, __fadd_rn(s.l, t.h));
+  return df_fast_two_sum(s.h, __fadd_rn(s.l, t.l));
+}
+__device__ __forceinline__ df df_sub(df x, df y) { return df_add(x, df{-y.h, -y.l}); }
+__device__ __forceinline__ df df_mul(df x, df y) {
+  const float p = __fmul_rn(x.h, y.h);
+  const float e = __fmaf_rn(x.h, y.h, -p);   // exact error of the product
+  return df_fast_two_sum(p, __fmaf_rn(x.h, y.l, __fmaf_rn(x.l, y.h, e)));
+}
+__device__ __forceinline__ df df_mulf(df x, float y) {
+  const float p = __fmul_rn(x.h, y);
+  return df_fast_two_sum(p, __fmaf_rn(x.l, y, __fmaf_rn(x.h, y, -p)));
+}
+// 1/d: the float reciprocal q refined by one Newton step, q + q (1 - d q),
+// with the residual 1 - d q formed exactly enough in double-float.
+__device__ __forceinline__ df df_rcp(df d) {
+  const float q = 1.f / d.h;
+  const df r = df_sub(df{1.f, 0.f}, df_mulf(d, q));
+  return df_fast_two_sum(q, __fmul_rn(q, r.h));
+}
+__device__ __forceinline__ bool df_less(df a, df b) { return a.h < b.h || (a.h == b.h && a.l < b.l); }
+__device__ __forceinline__ double df_to_double(df a) { return double(a.h) + double(a.l); }
 
 constexpr int kPlanThreads = 128;
 constexpr int kSegBatch = 1024;   // boundary segments staged in shared memory per pass
@@ -174,7 +227,8 @@ __device__ float arc_length_part(const float4* key, const CurveRef& cr, const fl
 
 // One block per curve.
 __global__ void __launch_bounds__(kPlanThreads, 7) k_plan(ns_curves cv, ns_sample_params sp, CurvePlan* plan,
-                                                       float* knots, int* order, DevState* st) {
+                                                       float* knots, float* knots_lo, float2* krcp, int* order,
+                                                       DevState* st) {
   __shared__ float red[32];
   __shared__ int s_ok;
   __shared__ float sU[kStageKnots];   // the intervals first, then the knot vector (stage_curve)
@@ -217,8 +271,13 @@ __global__ void __launch_bounds__(kPlanThreads, 7) k_plan(ns_curves cv, ns_sampl
       const float* tau = tau_staged ? s_tau : cv.tau + cv.tau_offset[c];
       const int p = cr.p, nt = cr.ntau;
       const int n_int = nt + 2 * p;
-      double acc = 0.0;
+      // exact running sum as hi + lo: TwoSum keeps each addition's rounding
+      // error, which the low part collects (the sums of float intervals need
+      // far fewer than 48 bits)
+      float acc_h = 0.f, acc_l = 0.f;
+      float* Ulo = knots_lo + cr.knot0;
       U[0] = 0.f;
+      Ulo[0] = 0.f;
       for (int q = 0; q < n_int; ++q) {
         float v;
         if (!cr.closed) {
@@ -230,8 +289,12 @@ __global__ void __launch_bounds__(kPlanThreads, 7) k_plan(ns_curves cv, ns_sampl
           v = tau[k];
         }
         if (!(v >= 0.f)) ok = 0;   // negative or NaN interval
-        acc += double(v);
-        U[q + 1] = float(acc);
+        const df t = df_two_sum(acc_h, v);
+        acc_h = t.h;
+        acc_l = __fadd_rn(acc_l, t.l);
+        const df u = df_fast_two_sum(acc_h, acc_l);
+        U[q + 1] = u.h;
+        Ulo[q + 1] = u.l;
       }
       if (ok && !(U[cr.n + 1] > U[p])) ok = 0;   // empty domain
     }
@@ -242,6 +305,20 @@ __global__ void __launch_bounds__(kPlanThreads, 7) k_plan(ns_curves cv, ns_sampl
     s_ok = ok;
   }
   __syncthreads();
+  if (s_ok && cr.filled) {
+    // reciprocals of the knot differences of width 1..p (double-float), for
+    // the boundary points' Cox-de Boor triangle (k_boundary)
+    const int nkn = cr.ntau + 2 * cr.p + 1;
+    const float* Uh = U;
+    const float* Ul = knots_lo + cr.knot0;
+    float2* rc = krcp + (long long)kMaxP * cr.knot0;
+    for (int q = threadIdx.x; q < cr.p * nkn; q += blockDim.x) {
+      const int j = q / nkn + 1, k = q - (j - 1) * nkn;
+      const df d = k + j < nkn ? df_sub(df{Uh[k + j], Ul[k + j]}, df{Uh[k], Ul[k]}) : df{0.f, 0.f};
+      const df r = d.h > 0.f ? df_rcp(d) : df{0.f, 0.f};
+      rc[(j - 1) * nkn + k] = make_float2(r.h, r.l);
+    }
+  }
   CurvePlan pl;
   if (!s_ok) {
     if (threadIdx.x == 0) {
@@ -269,7 +346,7 @@ __global__ void __launch_bounds__(kPlanThreads, 7) k_plan(ns_curves cv, ns_sampl
     if (cr.filled) {
       pl.kind = kFill;
       pl.M = max(3, int(ceilf(sp.delta_b * L)));
-      pl.count = 0;   // set by k_boundary
+      pl.count = 0;   // set by k_boundary_box
     } else if (cr.closed) {
       pl.kind = kClosedStroke;
       pl.M = max(1, int(ceilf(sp.delta_c * L)));
@@ -333,61 +410,166 @@ __global__ void k_scan_boundary(int nc, CurvePlan* plan, DevState* st, long long
   }
 }
 
+// C_xy(u) on span i in double-float, the knots U given as high and low parts.
 template <int P>
-__device__ void boundary_points(const float4* key, const CurveRef& cr, const float* U, const CurvePlan& pl,
-                                float2* bpts, int* bcurve, int c, long long bcap, float4& box) {
-  float xmin = FLT_MAX, ymin = FLT_MAX, xmax = -FLT_MAX, ymax = -FLT_MAX;
-  for (int j = threadIdx.x; j < pl.M; j += blockDim.x) {
-    const float t = float(j) / float(pl.M);
-    const float u = pl.a + t * (pl.b - pl.a);
-    const int i = find_span(U, P, cr.n, u);
-    Eval<P> e;
-    eval_curve<P>(key, cr, U, i, u, e);
-    const long long o = (long long)pl.b_off + j;
-    if (o < bcap) {
-      bpts[o] = make_float2(e.C[0], e.C[1]);
-      bcurve[o] = c;
+__device__ __forceinline__ void curve_xy_df(const float4* __restrict__ key, const CurveRef& cr,
+                                            const float* __restrict__ Uh, const float* __restrict__ Ul,
+                                            const float2* __restrict__ rc, int ld, int i, df u, df& x, df& y) {
+  df N[P + 1], left[P + 1], right[P + 1];
+  N[0] = df{1.f, 0.f};
+#pragma unroll
+  for (int j = 1; j <= P; ++j) {
+    left[j] = df_sub(u, df{Uh[i + 1 - j], Ul[i + 1 - j]});
+    right[j] = df_sub(df{Uh[i + j], Ul[i + j]}, u);
+    df saved = df{0.f, 0.f};
+#pragma unroll
+    for (int r = 0; r < j; ++r) {
+      // 1 / (U[i+r+1] - U[i+1-j+r]), positive on a non-empty span
+      const float2 inv = rc[(j - 1) * ld + i + 1 - j + r];
+      const df temp = df_mul(N[r], df{inv.x, inv.y});
+      N[r] = df_add(saved, df_mul(right[r + 1], temp));
+      saved = df_mul(left[j - r], temp);
     }
-    xmin = fminf(xmin, e.C[0]);
-    xmax = fmaxf(xmax, e.C[0]);
-    ymin = fminf(ymin, e.C[1]);
-    ymax = fmaxf(ymax, e.C[1]);
+    N[j] = saved;
   }
-  box = make_float4(xmin, ymin, xmax, ymax);
+  df Sx{0.f, 0.f}, Sy{0.f, 0.f}, W{0.f, 0.f};
+#pragma unroll
+  for (int l = 0; l <= P; ++l) {
+    const float4 q = key[cr.key0 + cp_to_key(i - P + l, P, cr.closed, cr.nk)];
+    const df nw = df_mulf(N[l], q.w);
+    Sx = df_add(Sx, df_mulf(nw, q.x));
+    Sy = df_add(Sy, df_mulf(nw, q.y));
+    W = df_add(W, nw);
+  }
+  const df iw = df_rcp(W);
+  x = df_mul(Sx, iw);
+  y = df_mul(Sy, iw);
 }
 
-// One block per curve; filled curves only.
-__global__ void __launch_bounds__(kPlanThreads) k_boundary(ns_curves cv, ns_sample_params sp, CurvePlan* plan,
-                                                           const float* knots, float2* bpts, int* bcurve,
-                                                           long long bcap) {
-  __shared__ float red[32];
-  const int c = blockIdx.x;
-  if (plan[c].kind != kFill) return;
-  const CurveRef cr = curve_ref(cv, c);
-  const float* U = knots + cr.knot0;
+// One thread per boundary point of every filled curve: b_j = C_xy(a + (j/B)
+// (b - a)), j < B (closed rule), evaluated in double-float; writes the
+// absolute FP32 copy, the curve table and, in the local array, the
+// double-float pair {x.h, y.h, x.l, y.l} (k_boundary_box makes it relative to
+// the grid origin).  The span is searched on the FP32 knots and settled on
+// the double-float ones.
+__global__ void __launch_bounds__(256) k_boundary(ns_curves cv, const CurvePlan* __restrict__ plan,
+                                                  const float* __restrict__ knots, const float* __restrict__ knots_lo,
+                                                  const float2* __restrict__ krcp,
+                                                  const DevState* __restrict__ st, float2* bpts, int* bcurve,
+                                                  float4* bloc, long long bcap) {
+  const long long nb = min((long long)st->b_count, bcap);
+  const int nc = cv.n_curves;
+  for (long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x; o < nb;
+       o += (long long)gridDim.x * blockDim.x) {
+    // the curve: the largest c with b_off <= o (curves without points share
+    // the offset of the next one, and the largest index is the filled curve)
+    int lo = 0, hi = nc - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (plan[mid].b_off <= o) lo = mid; else hi = mid - 1;
+    }
+    const int c = lo;
+    const CurvePlan pl = plan[c];
+    const int j = int(o - pl.b_off);
+    if (pl.kind != kFill || j < 0 || j >= pl.M) continue;
+    const CurveRef cr = curve_ref(cv, c);
+    const float* Uh = knots + cr.knot0;
+    const float* Ul = knots_lo + cr.knot0;
+    const df a{Uh[cr.p], Ul[cr.p]}, b{Uh[cr.n + 1], Ul[cr.n + 1]};
+    // t = j / B as a double-float: the float quotient plus the exact remainder over B
+    const float B = float(pl.M);
+    const float q = float(j) / B;
+    const df t = df_fast_two_sum(q, __fmaf_rn(-q, B, float(j)) / B);
+    const df u = df_add(a, df_mul(t, df_sub(b, a)));
+    const int p = cr.p;
+    int i = find_span(Uh, p, cr.n, u.h);
+    while (i < cr.n && !df_less(u, df{Uh[i + 1], Ul[i + 1]})) ++i;
+    while (i > p && df_less(u, df{Uh[i], Ul[i]})) --i;
+    while (i > p && !df_less(df{Uh[i], Ul[i]}, df{Uh[i + 1], Ul[i + 1]})) --i;
+    df x{0.f, 0.f}, y{0.f, 0.f};
+    NS_DISPATCH_P(p, curve_xy_df<P>(reinterpret_cast<const float4*>(cv.key), cr, Uh, Ul,
+                                    krcp + (long long)kMaxP * cr.knot0, cr.ntau + 2 * p + 1, i, u, x, y));
+    bpts[o] = make_float2(x.h, y.h);
+    bloc[o] = make_float4(x.h, y.h, x.l, y.l);
+    bcurve[o] = c;
+  }
+}
+
+// One warp per filled curve: the box of its boundary points (double-float
+// comparisons), the grid origin and size decided in double precision (a
+// handful of scalar operations), the origin stored as a high part (plan) and
+// a low part (glo), and the points rewritten relative to it as high and low
+// floats (bloc) -- what the signed distance of Eq. S1-S3, the fill chain and
+// the fill-layer blend work with.
+__global__ void __launch_bounds__(256) k_boundary_box(ns_curves cv, ns_sample_params sp, CurvePlan* plan,
+                                                      const float* __restrict__ knots, float4* bloc, float2* glo,
+                                                      long long bcap) {
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= cv.n_curves) return;
   const CurvePlan pl = plan[c];
-  __shared__ float sU[kStageKnots];
-  __shared__ float4 sK[kStageKeys];
-  const Staged sg = stage_curve(cv, cr, U, sU, sK);
-  float4 box = make_float4(FLT_MAX, FLT_MAX, -FLT_MAX, -FLT_MAX);
-  NS_DISPATCH_P(cr.p, boundary_points<P>(sg.key, sg.cr, sg.U, pl, bpts, bcurve, c, bcap, box));
-  const float xmin = block_reduce_minmax(box.x, red, false);
-  const float ymin = block_reduce_minmax(box.y, red, false);
-  const float xmax = block_reduce_minmax(box.z, red, true);
-  const float ymax = block_reduce_minmax(box.w, red, true);
-  if (threadIdx.x == 0) {
-    const float padx = sp.pad_frac * (xmax - xmin);
-    const float pady = sp.pad_frac * (ymax - ymin);
-    const float x0 = fmaxf(0.f, xmin - padx), x1 = fminf(float(cv.width), xmax + padx);
-    const float y0 = fmaxf(0.f, ymin - pady), y1 = fminf(float(cv.height), ymax + pady);
-    const int nx = x1 > x0 ? int(ceilf((x1 - x0) / sp.h)) : 0;
-    const int ny = y1 > y0 ? int(ceilf((y1 - y0) / sp.h)) : 0;
-    plan[c].x0 = x0;
-    plan[c].y0 = y0;
+  if (pl.kind != kFill) return;
+  const bool whole = (long long)pl.b_off + pl.M <= bcap;   // else the polyline overflowed: box from what exists
+  const int M = whole ? pl.M : int(max(0LL, min((long long)pl.M, bcap - pl.b_off)));
+  df box[4] = {df{FLT_MAX, 0.f}, df{FLT_MAX, 0.f}, df{-FLT_MAX, 0.f}, df{-FLT_MAX, 0.f}};
+  for (int j = lane; j < pl.M; j += 32) {
+    df x, y;
+    if (j < M) {
+      const float4 v = bloc[pl.b_off + j];
+      x = df{v.x, v.z};
+      y = df{v.y, v.w};
+    } else {
+      // past the boundary capacity: evaluated in FP32 only to size the grid
+      // (NS_ERR_CAPACITY is raised, the curve emits nothing)
+      const CurveRef cr = curve_ref(cv, c);
+      const float* U = knots + cr.knot0;
+      const float u = pl.a + (float(j) / float(pl.M)) * (pl.b - pl.a);
+      float2 q = make_float2(0.f, 0.f);
+      NS_DISPATCH_P(cr.p, {
+        Eval<P> e;
+        eval_curve<P>(reinterpret_cast<const float4*>(cv.key), cr, U, find_span(U, P, cr.n, u), u, e);
+        q = make_float2(e.C[0], e.C[1]);
+      });
+      x = df{q.x, 0.f};
+      y = df{q.y, 0.f};
+    }
+    if (df_less(x, box[0])) box[0] = x;
+    if (df_less(y, box[1])) box[1] = y;
+    if (df_less(box[2], x)) box[2] = x;
+    if (df_less(box[3], y)) box[3] = y;
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    for (int o = 16; o > 0; o >>= 1) {
+      const df x{__shfl_xor_sync(0xffffffffu, box[k].h, o), __shfl_xor_sync(0xffffffffu, box[k].l, o)};
+      if (k < 2 ? df_less(x, box[k]) : df_less(box[k], x)) box[k] = x;
+    }
+  }
+  const double xmin = df_to_double(box[0]), ymin = df_to_double(box[1]);
+  const double xmax = df_to_double(box[2]), ymax = df_to_double(box[3]);
+  const double padx = double(sp.pad_frac) * (xmax - xmin);
+  const double pady = double(sp.pad_frac) * (ymax - ymin);
+  const double x0 = fmax(0.0, xmin - padx), x1 = fmin(double(cv.width), xmax + padx);
+  const double y0 = fmax(0.0, ymin - pady), y1 = fmin(double(cv.height), ymax + pady);
+  const float x0h = float(x0), y0h = float(y0);
+  const df ox{x0h, float(x0 - double(x0h))}, oy{y0h, float(y0 - double(y0h))};
+  __syncwarp();
+  for (int j = lane; j < M; j += 32) {
+    const float4 v = bloc[pl.b_off + j];
+    const df lx = df_sub(df{v.x, v.z}, ox), ly = df_sub(df{v.y, v.w}, oy);
+    bloc[pl.b_off + j] = make_float4(lx.h, ly.h, lx.l, ly.l);
+  }
+  if (lane == 0) {
+    const double h = double(sp.h);
+    const int nx = x1 > x0 ? int(ceil((x1 - x0) / h)) : 0;
+    const int ny = y1 > y0 ? int(ceil((y1 - y0) / h)) : 0;
+    plan[c].x0 = x0h;
+    plan[c].y0 = y0h;
+    glo[c] = make_float2(ox.l, oy.l);
     plan[c].nx = nx;
     plan[c].ny = ny;
     plan[c].h = sp.h;
-    plan[c].count = nx * ny;   // counted even when the polyline overflowed (sizing)
+    plan[c].count = nx * ny;
   }
 }
 
@@ -546,12 +728,13 @@ __device__ __forceinline__ int cluster_crossings(const float4* seg, const float2
 
 // Bounding box {x0, x1, y0, y1} of each cluster of kCluster consecutive
 // segments of a fill polyline (the last cluster may be shorter; segment j
-// runs from point j to point j + 1, the last one back to point 0), stored at
-// the index of the cluster's first point.  The sampling tasks of a curve all
-// stage these boxes, so they are computed once per curve here.
+// runs from point j to point j + 1, the last one back to point 0), in the
+// curve's grid-local coordinates (high parts), stored at the index of the
+// cluster's first point.  The sampling tasks of a curve all stage these
+// boxes, so they are computed once per curve here.
 __global__ void __launch_bounds__(256) k_cluster_boxes(const CurvePlan* __restrict__ plan,
                                                        const int* __restrict__ bcurve,
-                                                       const float2* __restrict__ bpts,
+                                                       const float4* __restrict__ bloc,
                                                        const DevState* __restrict__ st, float4* cbox,
                                                        long long bcap, int nc) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -567,8 +750,8 @@ __global__ void __launch_bounds__(256) k_cluster_boxes(const CurvePlan* __restri
   const int B = p.M;
   float x0 = FLT_MAX, x1 = -FLT_MAX, y0 = FLT_MAX, y1 = -FLT_MAX;
   for (int j = int(k); j < min(B, int(k) + kCluster); ++j) {
-    const float2 b0 = bpts[p.b_off + j];
-    const float2 b1 = bpts[p.b_off + (j + 1 == B ? 0 : j + 1)];
+    const float4 b0 = bloc[p.b_off + j];
+    const float4 b1 = bloc[p.b_off + (j + 1 == B ? 0 : j + 1)];
     x0 = fminf(x0, fminf(b0.x, b1.x));
     x1 = fmaxf(x1, fmaxf(b0.x, b1.x));
     y0 = fminf(y0, fminf(b0.y, b1.y));
@@ -577,10 +760,25 @@ __global__ void __launch_bounds__(256) k_cluster_boxes(const CurvePlan* __restri
   cbox[i] = make_float4(x0, x1, y0, y1);
 }
 
+// Distance from grid-local point q to the segment p0 -> p1 given as high and
+// low parts {x_hi, y_hi, x_lo, y_lo} (Eq. S1): q - p0 and p1 - p0 are formed
+// from the high parts first (exact for nearby points) and corrected by the
+// low parts, so a point near the polyline gets its distance to about 1e-7 px.
+__device__ __forceinline__ float seg_distance_hl(float qx, float qy, const float4& p0, const float4& p1) {
+  const float rx = __fsub_rn(__fsub_rn(qx, p0.x), p0.z), ry = __fsub_rn(__fsub_rn(qy, p0.y), p0.w);
+  const float ex = __fadd_rn(__fsub_rn(p1.x, p0.x), __fsub_rn(p1.z, p0.z));
+  const float ey = __fadd_rn(__fsub_rn(p1.y, p0.y), __fsub_rn(p1.w, p0.w));
+  const float ee = ex * ex + ey * ey;
+  const float t = ee > 0.f ? fminf(fmaxf((rx * ex + ry * ey) / ee, 0.f), 1.f) : 0.f;
+  const float dx = rx - t * ex, dy = ry - t * ey;
+  return sqrtf(dx * dx + dy * dy);
+}
+
 // Persistent: each block iteration handles one task of 256 Gaussians of one curve.
 __global__ void __launch_bounds__(256, 5) k_emit(ns_curves cv, ns_sample_params sp, const CurvePlan* __restrict__ plan,
                                               const int* __restrict__ order, const float* __restrict__ knots,
-                                              const float2* __restrict__ bpts, const DevState* __restrict__ st,
+                                              const float4* __restrict__ bloc, const float2* __restrict__ glo,
+                                              const DevState* __restrict__ st,
                                               float4* rec, int* gcurve, int* gaux, long long gcap, long long bcap,
                                               const int* __restrict__ tmap, long long tcap,
                                               const float4* __restrict__ cbox_g) {
@@ -612,11 +810,14 @@ __global__ void __launch_bounds__(256, 5) k_emit(ns_curves cv, ns_sample_params 
       continue;
     }
     // fill point: grid row-major over the padded box; a curve whose polyline
-    // did not fit the boundary capacity emits nothing (NS_ERR_CAPACITY is set)
+    // did not fit the boundary capacity emits nothing (NS_ERR_CAPACITY is set).
+    // The distance search runs in grid-local coordinates (the polyline's high
+    // parts; the grid origin is 0), the nearest segment's distance is then
+    // recomputed with the low parts as well.
     if ((long long)pl.b_off + pl.M > bcap) continue;
     const int nxx = max(pl.nx, 1);
-    const float qx = pl.x0 + (float(l % nxx) + 0.5f) * sp.h;
-    const float qy = pl.y0 + (float(l / nxx) + 0.5f) * sp.h;
+    const float qx = (float(l % nxx) + 0.5f) * sp.h;
+    const float qy = (float(l / nxx) + 0.5f) * sp.h;
     const int B = pl.M;
     float best = FLT_MAX;
     int arg = 0, wn = 0;
@@ -638,8 +839,8 @@ __global__ void __launch_bounds__(256, 5) k_emit(ns_curves cv, ns_sample_params 
       __syncthreads();
       for (int s = threadIdx.x; s < nseg; s += blockDim.x) {
         const int i = base + s;
-        const float2 b0 = bpts[pl.b_off + i];
-        const float2 b1 = bpts[pl.b_off + (i + 1 == B ? 0 : i + 1)];
+        const float4 b0 = bloc[pl.b_off + i];
+        const float4 b1 = bloc[pl.b_off + (i + 1 == B ? 0 : i + 1)];
         const float ex = b1.x - b0.x, ey = b1.y - b0.y;
         const float ee = ex * ex + ey * ey;
         seg[s] = make_float4(b0.x, b0.y, ex, ey);
@@ -703,12 +904,16 @@ __global__ void __launch_bounds__(256, 5) k_emit(ns_curves cv, ns_sample_params 
       if (far) {
         sig = 0.f;
       } else if (!deep) {
-        const float d = sqrtf(best);
+        const float4 p0 = bloc[pl.b_off + arg];
+        const float4 p1 = bloc[pl.b_off + (arg + 1 == B ? 0 : arg + 1)];
+        const float d = seg_distance_hl(qx, qy, p0, p1);
         const float sdf = inside ? d : -d;
         const float z = sp.gamma / sp.h * sdf;
         sig = 1.f / (1.f + __expf(-z));
       }
-      rec[g] = make_float4(qx, qy, sp.eta * sp.h / sp.rho, o * sig);
+      const float2 lo = glo[c];
+      rec[g] = make_float4(__fadd_rn(pl.x0, __fadd_rn(qx, lo.x)), __fadd_rn(pl.y0, __fadd_rn(qy, lo.y)),
+                           sp.eta * sp.h / sp.rho, o * sig);
       gcurve[g] = c;
       gaux[g] = deep ? kAuxDeep : (far ? kAuxFar : (inside ? arg : ~arg));
     }
@@ -760,19 +965,28 @@ extern "C" ns_status nurbs_sample(const ns_curves* curves, const ns_sample_param
     cudaMemsetAsync(&st->g_count, 0, sizeof(int), s);
     return cudaGetLastError() == cudaSuccess ? NS_OK : NS_ERR_CUDA;
   }
-  NS_LAUNCH(NS_KERNEL_PLAN, k_plan, nc, kPlanThreads, 0, s, *curves, *sp, plan, knots, order, st);
+  float2* krcp = at<float2>(ws, L.o_krcp);
+  NS_LAUNCH(NS_KERNEL_PLAN, k_plan, nc, kPlanThreads, 0, s, *curves, *sp, plan, knots, at<float>(ws, L.o_knots_lo),
+            krcp, order, st);
   NS_LAUNCH(NS_KERNEL_SCAN, k_scan_boundary, 1, 1024, 0, s, nc, plan, st, cap->boundary);
-  NS_LAUNCH(NS_KERNEL_BOUNDARY, k_boundary, nc, kPlanThreads, 0, s, *curves, *sp, plan, knots, bpts,
-            at<int>(ws, L.o_bcurve), cap->boundary);
+  float4* bloc = at<float4>(ws, L.o_bloc);
+  if (cap->boundary > 0)
+    NS_LAUNCH(NS_KERNEL_BOUNDARY, k_boundary, int(std::min<long long>((cap->boundary + 255) / 256, num_sms() * 16LL)),
+              256, 0, s, *curves, plan, knots, at<const float>(ws, L.o_knots_lo), krcp, st, bpts,
+              at<int>(ws, L.o_bcurve),
+              bloc, cap->boundary);
+  NS_LAUNCH(NS_KERNEL_OTHER, k_boundary_box, (nc + 7) / 8, 256, 0, s, *curves, *sp, plan, knots, bloc,
+            at<float2>(ws, L.o_glo), cap->boundary);
   float4* cbox = at<float4>(ws, L.o_cbox);
   if (cap->boundary > 0)
     NS_LAUNCH(NS_KERNEL_OTHER, k_cluster_boxes, int((cap->boundary + 255) / 256), 256, 0, s, plan,
-              at<const int>(ws, L.o_bcurve), bpts, st, cbox, cap->boundary, nc);
+              at<const int>(ws, L.o_bcurve), bloc, st, cbox, cap->boundary, nc);
   NS_LAUNCH(NS_KERNEL_SCAN, k_scan_gauss, 1, 1024, 0, s, nc, plan, order, st, cap->gaussians, out->count);
   int* tmap = at<int>(ws, L.o_tasks);
   NS_LAUNCH(NS_KERNEL_SCAN, k_task_map, (nc + 7) / 8, 256, 0, s, nc, plan, st, tmap, (long long)L.tcap);
   const int grid = num_sms() * 8;
-  NS_LAUNCH(NS_KERNEL_EMIT, k_emit, grid, 256, 0, s, *curves, *sp, plan, order, knots, bpts, st, reinterpret_cast<float4*>(out->rec),
+  NS_LAUNCH(NS_KERNEL_EMIT, k_emit, grid, 256, 0, s, *curves, *sp, plan, order, knots, bloc,
+            at<const float2>(ws, L.o_glo), st, reinterpret_cast<float4*>(out->rec),
                               out->curve, out->aux, cap->gaussians, cap->boundary, tmap, (long long)L.tcap, cbox);
   if (out->shape)
     NS_LAUNCH(NS_KERNEL_OTHER, k_emit_shape, grid, 256, 0, s, *curves, *sp, plan, knots, st,

@@ -2,11 +2,18 @@
 curve are binned as one tile pair per tile of the whole grid, and the blend
 kernels find the grid points that reach each pixel by index arithmetic.
 
-Every pixel composites the same Gaussians in the same order with the same
-arithmetic as with one pair per Gaussian, so the image must be bit-identical
-to the per-Gaussian path's at every tile size and decomposition.  Gradients
-differ only in the order of float additions (1e-5 of their norm), and the
-whole step is checked against the oracle (1e-3)."""
+Every pixel composites the same Gaussians in the same order as with one pair
+per Gaussian.  The two paths differ in one rounding: per-Gaussian pairs read
+the records' absolute FP32 centres, while fill layers form the offset of a
+pixel from a grid point in grid-local coordinates, exact to about 1e-7 px.
+So the fill-layer image is checked against the FP64 oracle at the 1e-5 gate
+(outside pixels where a production threshold decision lies within 1e-4 of its
+tie), and against the per-Gaussian image within the rounding of the records'
+centres, 32 eps32 max(W, H) / (sigma_min sqrt(e)) + 1e-5.  Gradients of the
+two paths agree within 1e-4 of their norm, and the whole step is checked
+against the oracle (1e-3)."""
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -17,6 +24,7 @@ from oracle import pipeline as op
 from gpu_util import run_scene, run_step
 
 pytestmark = pytest.mark.gpu
+EPS32 = float(np.finfo(np.float32).eps)
 
 SCENES = [
     ("filled-h1-production", lambda: scenes.small_closed(331, n_curves=3, size=70, filled=True, h=1.0, height=53)
@@ -41,17 +49,26 @@ def _rel(a, b):
 
 
 @pytest.mark.parametrize("name,make", SCENES, ids=[s[0] for s in SCENES])
-def test_layers_match_per_gaussian_pairs(name, make):
+def test_layers_match_oracle_and_per_gaussian_pairs(name, make):
     sc = make()
+    k, t, c = op.leaves(sc, False)
+    with torch.no_grad():
+        ref, g, flags = op.render(sc, k, t, c, return_flags=True)
+    ref = ref.numpy()
+    ok = np.broadcast_to(~flags.numpy()[..., None], ref.shape)
+    smin = float(g["sigma"].min()) if g["sigma"].numel() else 1.0
+    tol_rec = 32 * EPS32 * max(sc.width, sc.height) / (smin * math.sqrt(math.e)) + 1e-5
     for tile, ppt in DECOMP:
         base = run_step(sc.with_raster(tile=tile, ppt_fwd=ppt, ppt_bwd=ppt, fill_layers=0))
         lay = run_step(sc.with_raster(tile=tile, ppt_fwd=ppt, ppt_bwd=ppt, fill_layers=1))
         assert base["report"].status == 0 and lay["report"].status == 0
-        assert np.array_equal(lay["image"], base["image"]), (tile, ppt)
-        assert lay["report"].blend_contribs == base["report"].blend_contribs
+        assert np.abs(lay["image"] - ref)[ok].max() <= 1e-5, (tile, ppt)
+        assert np.abs(lay["image"] - base["image"])[ok].max() <= tol_rec, (tile, ppt)
+        nb, nl = base["report"].blend_contribs, lay["report"].blend_contribs
+        assert abs(nl - nb) <= 1e-3 * nb + 2, (tile, ppt, nb, nl)
         assert lay["report"].pairs <= base["report"].pairs
         for nm in ("dkey", "dtau", "dcolor"):
-            assert _rel(lay[nm], base[nm]) <= 1e-5, (tile, ppt, nm)
+            assert _rel(lay[nm], base[nm]) <= 1e-4, (tile, ppt, nm)
 
 
 @pytest.mark.parametrize("name,make", SCENES[:4], ids=[s[0] for s in SCENES[:4]])
