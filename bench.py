@@ -325,7 +325,7 @@ def run_gpu(args, dist, rank, world):
     torch.cuda.synchronize()
 
     # K-step graph with per-kernel events armed in every step
-    prof = ["plan", "boundary", "emit", "bin_count", "bin_emit", "radix_scatter", "ranges", "blend_fwd", "mse", "blend_bwd",
+    prof = ["plan", "boundary", "fill_sdf", "emit", "bin_count", "bin_emit", "radix_scatter", "ranges", "blend_fwd", "mse", "blend_bwd",
             "chain", "chain_contour", "chain_boundary", "knot_grads"]
     ev = {k: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)] for k in prof}

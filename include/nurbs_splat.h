@@ -197,7 +197,8 @@ enum {
   NS_KERNEL_BIN_EMIT = 5, NS_KERNEL_RADIX_HIST = 6, NS_KERNEL_RADIX_SCATTER = 7, NS_KERNEL_RANGES = 8,
   NS_KERNEL_BLEND_FWD = 9, NS_KERNEL_BLEND_BWD = 10, NS_KERNEL_CHAIN = 11, NS_KERNEL_CHAIN_BOUNDARY = 12,
   NS_KERNEL_KNOT_GRADS = 13, NS_KERNEL_MSE = 14, NS_KERNEL_ADAM = 15, NS_KERNEL_SCAN = 16,
-  NS_KERNEL_OTHER = 17, NS_KERNEL_CHAIN_CONTOUR = 18, NS_KERNEL_DERIV_LOSS = 19, NS_KERNEL_BBOX_LOSS = 20
+  NS_KERNEL_OTHER = 17, NS_KERNEL_CHAIN_CONTOUR = 18, NS_KERNEL_DERIV_LOSS = 19, NS_KERNEL_BBOX_LOSS = 20,
+  NS_KERNEL_FILL_SDF = 21
 };
 
 ns_sample_params ns_default_sample_params(void);

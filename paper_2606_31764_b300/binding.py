@@ -116,7 +116,7 @@ BLEND_LANE_GROUPS = 16
 
 KERNELS = dict(plan=1, boundary=2, emit=3, bin_count=4, bin_emit=5, radix_hist=6, radix_scatter=7, ranges=8,
                blend_fwd=9, blend_bwd=10, chain=11, chain_boundary=12, knot_grads=13, mse=14, adam=15, scan=16,
-               other=17, chain_contour=18, deriv_loss=19, bbox_loss=20)
+               other=17, chain_contour=18, deriv_loss=19, bbox_loss=20, fill_sdf=21)
 
 _lib = None
 

@@ -133,9 +133,11 @@ bool make_layout(const ns_curves* c, const ns_capacity* cap, const ns_raster_par
   L->o_glo = take(sizeof(float2) * (size_t)L->nc);
   L->o_knots_lo = take(sizeof(float) * nkn);
   L->o_krcp = take(sizeof(float2) * kMaxP * nkn);
-  // each curve's tasks cover its Gaussians in chunks of kChunk: within the
-  // Gaussian capacity there are at most gcap/kChunk + n_curves of them
-  L->tcap = L->gcap / kChunk + L->nc + 1;
+  // contour tasks cover a curve's samples in chunks of kChunk, fill tasks its
+  // grid in 16 x 16 tiles (at most (nx ny + 15 (nx + ny) + 225) / 256 of them):
+  // within the Gaussian capacity this table holds them all (past it the task
+  // -> curve search takes over)
+  L->tcap = L->gcap / kChunk + L->gcap / kFillTile + 2LL * L->nc + 1;
   L->o_tasks = take(sizeof(int) * (size_t)L->tcap);
   L->sample_total = o;   // everything above depends on the curves and capacities only
   L->o_bsum = take(sizeof(int) * (size_t)(L->bin_blocks + 1));

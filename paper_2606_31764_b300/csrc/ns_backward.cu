@@ -99,10 +99,11 @@ __global__ void __launch_bounds__(256, 8) k_chain(ns_curves cv, ChainParams cp, 
     const int c = task_curve(cp.tmap, cp.tcap, n_tasks, plan, order, nc, task, true);
     const CurvePlan pl = plan[c];
     const CurveRef cr = curve_ref(cv, c);
-    const int l0 = (task - pl.chunk_off) * kChunk;
-    const int l = l0 + threadIdx.x;
-    const long long g = (long long)pl.g_off + l;
-    const bool valid = l < pl.count && g < gcap;
+    // a fill task is a 16 x 16 tile of the curve's grid
+    int ix, iy;
+    const bool in_grid = fill_task_point(task - pl.chunk_off, pl.nx, pl.ny, threadIdx.x, ix, iy);
+    const long long g = (long long)pl.g_off + (long long)iy * pl.nx + ix;
+    const bool valid = in_grid && g < gcap;
     __syncthreads();
     if (threadIdx.x < 8) s_red[threadIdx.x] = 0.f;
     // a culled point (opacity 0, marked far) is never composited: its row is
@@ -129,8 +130,7 @@ __global__ void __launch_bounds__(256, 8) k_chain(ns_curves cv, ChainParams cp, 
       const int i1 = i0 + 1 == B ? 0 : i0 + 1;
       // in grid-local coordinates with the polyline's low parts, as nurbs_sample
       // formed the distance (the direction below stays exact near the polyline)
-      const int nxx = max(pl.nx, 1);
-      const float qx = (float(l % nxx) + 0.5f) * pl.h, qy = (float(l / nxx) + 0.5f) * pl.h;
+      const float qx = (float(ix) + 0.5f) * pl.h, qy = (float(iy) + 0.5f) * pl.h;
       const float4 b0 = bloc[pl.b_off + i0], b1 = bloc[pl.b_off + i1];
       const float ex = __fadd_rn(__fsub_rn(b1.x, b0.x), __fsub_rn(b1.z, b0.z));
       const float ey = __fadd_rn(__fsub_rn(b1.y, b0.y), __fsub_rn(b1.w, b0.w));

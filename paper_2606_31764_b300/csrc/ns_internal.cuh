@@ -14,6 +14,7 @@ namespace ns {
 
 constexpr int kMaxP = NS_MAX_DEGREE;
 constexpr int kChunk = 256;          // Gaussians per sampling / chain task (one block)
+constexpr int kFillTile = 16;        // a fill task: a 16 x 16 tile of its curve's grid (kChunk points)
 constexpr int kBinItems = 2048;      // Gaussians per binning block (256 threads x 8)
 constexpr int kSortItems = 4096;     // pairs per radix-sort block (256 threads x 16)
 constexpr int kKnotPad = 2 * kMaxP + 1;  // knots per curve = intervals + 2p + 1
@@ -544,7 +545,22 @@ __device__ __forceinline__ int task_curve(const int* __restrict__ tmap, long lon
   return t < tcap ? tmap[t] : curve_of_task(plan, order, nc, task, fill);
 }
 
-// Task -> curve map.  Tasks are 256 Gaussians of one curve; fill tasks and
+// Fill tasks of a curve's nx x ny grid: its 16 x 16 tiles, row-major.
+__host__ __device__ __forceinline__ int fill_task_count(int nx, int ny) {
+  return ((nx + kFillTile - 1) / kFillTile) * ((ny + kFillTile - 1) / kFillTile);
+}
+
+// Grid point (ix, iy) of thread t (0..255) in fill task k of a curve with an
+// nx x ny grid; false past the grid.
+__device__ __forceinline__ bool fill_task_point(int k, int nx, int ny, int t, int& ix, int& iy) {
+  const int tcols = (nx + kFillTile - 1) / kFillTile;
+  ix = (k % tcols) * kFillTile + (t % kFillTile);
+  iy = (k / tcols) * kFillTile + (t / kFillTile);
+  return ix < nx && iy < ny;
+}
+
+// Task -> curve map.  Contour tasks are 256 samples of one curve, fill tasks
+// 16 x 16 tiles of one curve's grid; fill tasks and
 // contour tasks are numbered separately, each kind in front-to-back curve
 // order, and a curve's chunk_off counts the tasks of its own kind before it.
 // Curves of the other kind contribute no tasks to the count, so over the

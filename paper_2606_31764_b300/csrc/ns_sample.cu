@@ -11,9 +11,12 @@
 //                   clipped box, the fill grid origin (high and low parts) and
 //                   size, the points made relative to the origin
 //   k_scan_gauss    one block: Gaussian and task offsets in front-to-back order
-//   k_emit          persistent: one 256-Gaussian task per block iteration;
-//                   contour samples (Eq. 4-5) or fill points with the SDF of
-//                   Eq. S1-S3 against the polyline staged in shared memory (Eq. 6-7)
+//   k_fill_sdf      persistent over the fill tasks (16 x 16 tiles of a curve's
+//                   grid): the SDF of Eq. S1-S3 from the band of segments
+//                   near the tile and per-row crossing lists, the fill
+//                   opacity of Eq. 7 and the records (Eq. 6)
+//   k_emit          persistent over the contour tasks: 256 samples of a
+//                   stroke per block iteration (Eq. 4-5)
 #include <cuda_runtime.h>
 #include <float.h>
 
@@ -72,7 +75,6 @@ __device__ __forceinline__ bool df_less(df a, df b) { return a.h < b.h || (a.h =
 __device__ __forceinline__ double df_to_double(df a) { return double(a.h) + double(a.l); }
 
 constexpr int kPlanThreads = 128;
-constexpr int kSegBatch = 1024;   // boundary segments staged in shared memory per pass
 constexpr int kCluster = 8;       // consecutive segments per bounding-box cluster
 
 __device__ __forceinline__ float block_sum(float v, float* red) {
@@ -583,7 +585,7 @@ __global__ void k_scan_gauss(int nc, CurvePlan* plan, const int* order, DevState
       nc, [&](int f) { return plan[order[f]].count; },
       [&](int f, long long off) { plan[order[f]].g_off = int(off < 0x7fffffff ? off : 0x7fffffff); });
   const long long ftasks = block_scan_items(
-      nc, [&](int f) { const CurvePlan& q = plan[order[f]]; return q.kind == kFill ? (q.count + kChunk - 1) / kChunk : 0; },
+      nc, [&](int f) { const CurvePlan& q = plan[order[f]]; return q.kind == kFill ? fill_task_count(q.nx, q.ny) : 0; },
       [&](int f, long long off) {
         CurvePlan& q = plan[order[f]];
         if (q.kind == kFill) q.chunk_off = int(off); else q.pad[0] = int(off);
@@ -614,7 +616,7 @@ __global__ void k_task_map(int nc, const CurvePlan* __restrict__ plan, const Dev
   if (c >= nc) return;
   const CurvePlan pl = plan[c];
   if (pl.kind == kNone) return;
-  const int ntask = (pl.count + kChunk - 1) / kChunk;
+  const int ntask = pl.kind == kFill ? fill_task_count(pl.nx, pl.ny) : (pl.count + kChunk - 1) / kChunk;
   const long long base = pl.kind == kFill ? pl.chunk_off : (long long)st->n_chunks + pl.chunk_off;
   for (int j = lane; j < ntask; j += 32) {
     const long long t = base + j;
@@ -690,41 +692,7 @@ __global__ void __launch_bounds__(256) k_emit_shape(ns_curves cv, ns_sample_para
   }
 }
 
-// Nearest segment of one cluster.  Among equal distances the lowest segment
-// index wins, whatever order the clusters are visited in (the result of a
-// plain first-minimum loop over all segments).
-__device__ __forceinline__ void cluster_nearest(const float4* seg, const float2* segb, int cl, int nseg, int base,
-                                                float qx, float qy, float& best, int& arg) {
-  const int k1 = min(nseg, (cl + 1) * kCluster);
-  for (int k = cl * kCluster; k < k1; ++k) {
-    const float4 sg = seg[k];
-    const float rx = qx - sg.x, ry = qy - sg.y;
-    const float t = fminf(fmaxf((rx * sg.z + ry * sg.w) * segb[k].y, 0.f), 1.f);
-    const float dx = rx - t * sg.z, dy = ry - t * sg.w;
-    const float d2 = dx * dx + dy * dy;
-    if (d2 < best || (d2 == best && base + k < arg)) { best = d2; arg = base + k; }
-  }
-}
 
-// Signed crossings of the ray from q to +x by one cluster's segments: the
-// winding number of Eq. S2, exact off the polyline.
-__device__ __forceinline__ int cluster_crossings(const float4* seg, const float2* segb, int cl, int nseg, float qx,
-                                                 float qy) {
-  int wn = 0;
-  const int k1 = min(nseg, (cl + 1) * kCluster);
-  for (int k = cl * kCluster; k < k1; ++k) {
-    const float4 sg = seg[k];
-    const float rx = qx - sg.x, ry = qy - sg.y;
-    const float y1 = segb[k].x;
-    const float isleft = sg.z * ry - rx * sg.w;
-    if (sg.y <= qy) {
-      if (y1 > qy && isleft > 0.f) ++wn;
-    } else {
-      if (y1 <= qy && isleft < 0.f) --wn;
-    }
-  }
-  return wn;
-}
 
 // Bounding box {x0, x1, y0, y1} of each cluster of kCluster consecutive
 // segments of a fill polyline (the last cluster may be shorter; segment j
@@ -774,149 +742,305 @@ __device__ __forceinline__ float seg_distance_hl(float qx, float qy, const float
   return sqrtf(dx * dx + dy * dy);
 }
 
-// Persistent: each block iteration handles one task of 256 Gaussians of one curve.
+// Persistent over the contour tasks: each block iteration handles 256 samples
+// of one open or closed stroke (Eq. 4-5).
 __global__ void __launch_bounds__(256, 5) k_emit(ns_curves cv, ns_sample_params sp, const CurvePlan* __restrict__ plan,
                                               const int* __restrict__ order, const float* __restrict__ knots,
-                                              const float4* __restrict__ bloc, const float2* __restrict__ glo,
-                                              const DevState* __restrict__ st,
-                                              float4* rec, int* gcurve, int* gaux, long long gcap, long long bcap,
-                                              const int* __restrict__ tmap, long long tcap,
-                                              const float4* __restrict__ cbox_g) {
-  __shared__ float4 seg[kSegBatch];   // {b0.x, b0.y, e.x, e.y}
-  __shared__ float2 segb[kSegBatch];  // {b1.y, 1/|e|^2 (0 for a zero-length segment)}
-  __shared__ float4 cbox[kSegBatch / kCluster];  // {x0, x1, y0, y1} of each segment cluster
+                                              const DevState* __restrict__ st, float4* rec, int* gcurve, int* gaux,
+                                              long long gcap, const int* __restrict__ tmap, long long tcap) {
   const int n_fill = st->n_chunks;
-  const int n_tasks = n_fill + st->n_ctasks;   // fill tasks (heavier) first
+  const int n_tasks = st->n_ctasks;
   const int nc = cv.n_curves;
-  for (int t = blockIdx.x; t < n_tasks; t += gridDim.x) {
-    const bool fill_task = t < n_fill;
-    const int task = fill_task ? t : t - n_fill;
-    const int c = task_curve(tmap, tcap, n_fill, plan, order, nc, task, fill_task);
+  for (int task = blockIdx.x; task < n_tasks; task += gridDim.x) {
+    const int c = task_curve(tmap, tcap, n_fill, plan, order, nc, task, false);
     const CurvePlan pl = plan[c];
+    if (pl.kind == kFill || pl.kind == kNone) continue;
     const CurveRef cr = curve_ref(cv, c);
     const float* U = knots + cr.knot0;
     const int l = (task - pl.chunk_off) * kChunk + threadIdx.x;
     const long long g = (long long)pl.g_off + l;
-    const bool valid = l < pl.count && g < gcap;
-    const float o = cv.color[4 * c + 3];
-    if (pl.kind != kFill) {
-      if (valid) {
-        float4 r;
-        NS_DISPATCH_P(cr.p, emit_contour<P>(cv, cr, U, pl, l, sp, o, r));
-        rec[g] = r;
-        gcurve[g] = c;
-        gaux[g] = -1;
-      }
-      continue;
+    if (l < pl.count && g < gcap) {
+      float4 r;
+      NS_DISPATCH_P(cr.p, emit_contour<P>(cv, cr, U, pl, l, sp, cv.color[4 * c + 3], r));
+      rec[g] = r;
+      gcurve[g] = c;
+      gaux[g] = -1;
     }
-    // fill point: grid row-major over the padded box; a curve whose polyline
-    // did not fit the boundary capacity emits nothing (NS_ERR_CAPACITY is set).
-    // The distance search runs in grid-local coordinates (the polyline's high
-    // parts; the grid origin is 0), the nearest segment's distance is then
-    // recomputed with the low parts as well.
-    if ((long long)pl.b_off + pl.M > bcap) continue;
-    const int nxx = max(pl.nx, 1);
-    const float qx = (float(l % nxx) + 0.5f) * sp.h;
-    const float qy = (float(l / nxx) + 0.5f) * sp.h;
-    const int B = pl.M;
-    float best = FLT_MAX;
-    int arg = 0, wn = 0;
-    bool deep = false, far = false;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fill points (§3.3, Eq. 6-7 and S1-S3).  A fill point's opacity only needs
+// the exact distance to the polyline inside a band around it: deeper inside,
+// the sigmoid of Eq. 7 is exactly 1 in FP32 (R21), and farther outside the
+// opacity stays below the cull threshold (R22).  So each task, a 16 x 16
+// tile of one curve's grid, works from the segments instead of the points:
+//   - the clusters of 8 segments whose boxes come within the band of the
+//     tile list their segments, and every segment offers its distance to the
+//     tile points within the band, kept per point as the smallest (squared
+//     distance, segment index) by a 64-bit atomic minimum in shared memory --
+//     the nearest segment of Eq. S1 with the lowest index among equal
+//     distances, the same as a first-minimum loop over all segments;
+//   - the segments that straddle a tile row are listed per row, and each point
+//     counts their signed crossings of its ray to +x (Eq. S2, exact off the
+//     polyline);
+//   - a point in the band gets its distance recomputed from the high and low
+//     parts of its nearest segment; a point outside it is deep (inside) or
+//     culled (outside).  Where the band is not enough (no cull threshold, as at
+//     the parity thresholds, or a cull distance beyond the band) an outside
+//     point, and every point of a tile whose lists overflow, searches all
+//     clusters with box lower bounds.
+// All coordinates are grid-local (origin 0): the polyline's high parts.
+constexpr int kNearCap = 384;   // band segments listed per tile
+constexpr int kCandCl = 128;    // candidate clusters listed per tile
+
+__device__ __forceinline__ float xmax_of(const float4& sg) { return fmaxf(sg.x, sg.x + sg.z); }
+constexpr int kRowX = 12;       // crossing segments listed per tile row
+
+// Squared distance from q to segment {b0, e} (1/|e|^2 given), as in Eq. S1.
+__device__ __forceinline__ float seg_d2(float qx, float qy, float4 sg, float inv_ee) {
+  const float rx = qx - sg.x, ry = qy - sg.y;
+  const float t = fminf(fmaxf((rx * sg.z + ry * sg.w) * inv_ee, 0.f), 1.f);
+  const float dx = rx - t * sg.z, dy = ry - t * sg.w;
+  return dx * dx + dy * dy;
+}
+
+// Segment k of a polyline of B points (high parts): {b0, b1 - b0}, b1.y, 1/|e|^2.
+__device__ __forceinline__ float4 seg_at(const float4* __restrict__ bl, int B, int k, float& y1, float& inv_ee) {
+  const float4 b0 = bl[k];
+  const float4 b1 = bl[k + 1 == B ? 0 : k + 1];
+  const float ex = b1.x - b0.x, ey = b1.y - b0.y;
+  const float ee = ex * ex + ey * ey;
+  inv_ee = ee > 0.f ? 1.f / ee : 0.f;
+  y1 = b1.y;
+  return make_float4(b0.x, b0.y, ex, ey);
+}
+
+// Signed crossing of segment {b0, e} (ending at height y1) by the ray from q to +x.
+__device__ __forceinline__ int seg_crossing(float qx, float qy, float4 sg, float y1) {
+  const float isleft = sg.z * (qy - sg.y) - (qx - sg.x) * sg.w;
+  if (sg.y <= qy) return (y1 > qy && isleft > 0.f) ? 1 : 0;
+  return (y1 <= qy && isleft < 0.f) ? -1 : 0;
+}
+
+// Nearest segment over the whole polyline (cluster boxes as lower bounds,
+// lowest index among equal distances), and optionally the winding number.
+__device__ void polyline_scan(const float4* __restrict__ bl, const float4* __restrict__ cb, int B, float qx, float qy,
+                              bool want_d, float& best, int& arg, bool want_wn, int& wn) {
+  const int ncl = (B + kCluster - 1) / kCluster;
+  for (int cl = 0; cl < ncl; ++cl) {
+    const float4 bb = cb[cl * kCluster];
+    const int k1 = min(B, (cl + 1) * kCluster);
+    const float bx = fmaxf(fmaxf(bb.x - qx, qx - bb.y), 0.f);
+    const float by = fmaxf(fmaxf(bb.z - qy, qy - bb.w), 0.f);
+    const float lb2 = bx * bx + by * by;
+    const bool near = want_d && !(lb2 > best + 1e-3f * (lb2 + 1.f));
+    const bool cross = want_wn && bb.z <= qy && bb.w > qy && bb.y >= qx - 0.01f;
+    if (!near && !cross) continue;
+    for (int k = cl * kCluster; k < k1; ++k) {
+      float y1, inv_ee;
+      const float4 sg = seg_at(bl, B, k, y1, inv_ee);
+      if (near) {
+        const float d2 = seg_d2(qx, qy, sg, inv_ee);
+        if (d2 < best || (d2 == best && k < arg)) {
+          best = d2;
+          arg = k;
+        }
+      }
+      if (cross) wn += seg_crossing(qx, qy, sg, y1);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256, 4) k_fill_sdf(ns_curves cv, ns_sample_params sp,
+                                                  const CurvePlan* __restrict__ plan, const int* __restrict__ order,
+                                                  const float4* __restrict__ bloc, const float2* __restrict__ glo,
+                                                  const float4* __restrict__ cbox, const DevState* __restrict__ st,
+                                                  float4* rec, int* gcurve, int* gaux, long long gcap,
+                                                  long long bcap, const int* __restrict__ tmap, long long tcap) {
+  __shared__ unsigned long long s_key[kChunk];
+  __shared__ float4 s_nseg[kNearCap];         // band segments {b0, e}
+  __shared__ float2 s_ninfo[kNearCap];        // {index bits, 1/|e|^2}
+  __shared__ float s_ny1[kNearCap];           // and their end heights
+  __shared__ int s_ccl[kCandCl];              // candidate clusters: 4 index + near + 2 crossing
+  __shared__ int s_nccl;
+  __shared__ float4 s_xs[kFillTile][kRowX];   // crossing segments per tile row {b0, e}
+  __shared__ float s_xy1[kFillTile][kRowX];   // and their end heights
+  __shared__ int s_xcnt[kFillTile];
+  __shared__ int s_nnear;
+  const int n_fill = st->n_chunks;
+  const int nc = cv.n_curves;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int task = blockIdx.x; task < n_fill; task += gridDim.x) {
+    const int c = task_curve(tmap, tcap, n_fill, plan, order, nc, task, true);
+    const CurvePlan pl = plan[c];
+    // a curve whose polyline did not fit the boundary capacity emits nothing
+    if (pl.kind != kFill || (long long)pl.b_off + pl.M > bcap) continue;
+    const int k = task - pl.chunk_off;
+    int ix, iy;
+    const bool in_grid = fill_task_point(k, pl.nx, pl.ny, tid, ix, iy);
+    const long long g = (long long)pl.g_off + (long long)iy * pl.nx + ix;
+    const bool valid = in_grid && g < gcap;
+    const int tix0 = ix - (tid % kFillTile), tiy0 = iy - (tid / kFillTile);   // the tile's first column and row
+    const float h = sp.h;
+    const float qx = (float(ix) + 0.5f) * h, qy = (float(iy) + 0.5f) * h;
+    // the tile's point box
+    const float tx0 = (float(tix0) + 0.5f) * h, tx1 = (float(min(pl.nx, tix0 + kFillTile)) - 0.5f) * h;
+    const float ty0 = (float(tiy0) + 0.5f) * h, ty1 = (float(min(pl.ny, tiy0 + kFillTile)) - 0.5f) * h;
+    const float o = cv.color[4 * c + 3];
     // sigmoid(z) rounds to exactly 1 in FP32 once exp(-z) <= 2^-24 (z >= 16.64);
-    // deep2 is the squared distance beyond which z >= 17 with margin
-    const float dsat = 17.f * sp.h / sp.gamma;
+    // deep2 is the squared distance beyond which z >= 17 with margin: the band
+    const float dsat = 17.f * h / sp.gamma;
     const float deep2 = dsat * dsat * 1.001f + 1e-3f;
+    const float band = sqrtf(deep2);
     // outside, o sigmoid(-gamma d / h) < fill_cull once d > (h/gamma) ln(o/fill_cull - 1);
     // far2 adds a margin of 0.1 in z (FLT_MAX: no culling)
     float far2 = FLT_MAX;
     if (sp.fill_cull > 0.f && o > 1.01f * sp.fill_cull) {
-      const float dcut = sp.h / sp.gamma * (logf(o / sp.fill_cull - 1.f) + 0.1f);
+      const float dcut = h / sp.gamma * (logf(o / sp.fill_cull - 1.f) + 0.1f);
       if (dcut > 0.f) far2 = dcut * dcut;
     }
-    for (int base = 0; base < B; base += kSegBatch) {
-      const int nseg = min(kSegBatch, B - base);
-      const int ncl = (nseg + kCluster - 1) / kCluster;
-      __syncthreads();
-      for (int s = threadIdx.x; s < nseg; s += blockDim.x) {
-        const int i = base + s;
-        const float4 b0 = bloc[pl.b_off + i];
-        const float4 b1 = bloc[pl.b_off + (i + 1 == B ? 0 : i + 1)];
-        const float ex = b1.x - b0.x, ey = b1.y - b0.y;
-        const float ee = ex * ex + ey * ey;
-        seg[s] = make_float4(b0.x, b0.y, ex, ey);
-        segb[s] = make_float2(b1.y, ee > 0.f ? 1.f / ee : 0.f);
+    const float4* bl = bloc + pl.b_off;
+    const float4* cb = cbox + pl.b_off;
+    const int B = pl.M;
+    const int ncl = (B + kCluster - 1) / kCluster;
+    __syncthreads();   // the previous task's lists are read
+    s_key[tid] = ~0ull;
+    if (tid < kFillTile) s_xcnt[tid] = 0;
+    if (tid == 0) {
+      s_nnear = 0;
+      s_nccl = 0;
+    }
+    __syncthreads();
+    // clusters near the tile (their segments join the band list) and clusters
+    // straddling a tile row to the right of its first column (crossings)
+    for (int cl = tid; cl < ncl; cl += blockDim.x) {
+      const float4 bb = cb[cl * kCluster];
+      const float gx = fmaxf(fmaxf(bb.x - tx1, tx0 - bb.y), 0.f);
+      const float gy = fmaxf(fmaxf(bb.z - ty1, ty0 - bb.w), 0.f);
+      const int near = gx * gx + gy * gy <= deep2 * 1.001f + 1e-3f;
+      const int cross = bb.z <= ty1 && bb.w > ty0 && bb.y >= tx0 - 0.01f;
+      if (near | cross) {
+        const int slot = atomicAdd(&s_nccl, 1);
+        if (slot < kCandCl) s_ccl[slot] = cl * 4 + near + 2 * cross;
       }
-      // bounding box of each cluster of kCluster consecutive segments (k_cluster_boxes)
-      for (int cl = threadIdx.x; cl < ncl; cl += blockDim.x) cbox[cl] = cbox_g[pl.b_off + base + cl * kCluster];
-      __syncthreads();
-      if (valid && B <= kSegBatch) {
-        // the whole polyline is staged: first the winding number and a lower
-        // bound of the distance (nearest cluster box), then the distance itself
-        // unless the point is provably deep inside, where the sigmoid of Eq. 7
-        // is exactly 1 in FP32 and the nearest segment cannot matter
-        float lbmin = FLT_MAX;
-        int clmin = 0;
-        for (int cl = 0; cl < ncl; ++cl) {
-          const float4 bb = cbox[cl];
-          const float bx = fmaxf(fmaxf(bb.x - qx, qx - bb.y), 0.f);
-          const float by = fmaxf(fmaxf(bb.z - qy, qy - bb.w), 0.f);
-          const float lb2 = bx * bx + by * by;
-          if (lb2 < lbmin) { lbmin = lb2; clmin = cl; }
-          if (bb.z <= qy && bb.w > qy && bb.y >= qx - 0.01f) wn += cluster_crossings(seg, segb, cl, nseg, qx, qy);
-        }
-        const bool inside = sp.fill_rule == 0 ? wn > 0 : wn != 0;
-        if (inside && lbmin > deep2) {
-          deep = true;
-        } else if (!inside && lbmin > far2) {
-          far = true;
-        } else {
-          // the nearest box first: its best distance prunes most other clusters
-          cluster_nearest(seg, segb, clmin, nseg, base, qx, qy, best, arg);
-          for (int cl = 0; cl < ncl; ++cl) {
-            if (cl == clmin) continue;
-            const float4 bb = cbox[cl];
-            const float bx = fmaxf(fmaxf(bb.x - qx, qx - bb.y), 0.f);
-            const float by = fmaxf(fmaxf(bb.z - qy, qy - bb.w), 0.f);
-            const float lb2 = bx * bx + by * by;
-            if (lb2 > best + 1e-3f * (lb2 + 1.f)) continue;
-            cluster_nearest(seg, segb, cl, nseg, base, qx, qy, best, arg);
+    }
+    __syncthreads();
+    const int nccl = s_nccl;
+    const bool ovf_cl = nccl > kCandCl;
+    // their segments, one thread each
+    for (int i = tid; !ovf_cl && i < nccl * kCluster; i += blockDim.x) {
+      const int e = s_ccl[i / kCluster];
+      const int kseg = (e >> 2) * kCluster + i % kCluster;
+      if (kseg >= B) continue;
+      float y1, inv_ee;
+      const float4 sg = seg_at(bl, B, kseg, y1, inv_ee);
+      const float ylo = fminf(sg.y, y1), yhi = fmaxf(sg.y, y1);
+      if (e & 1) {
+        const float xlo = fminf(sg.x, sg.x + sg.z), xhi = fmaxf(sg.x, sg.x + sg.z);
+        const float gx = fmaxf(fmaxf(xlo - tx1, tx0 - xhi), 0.f);
+        const float gy = fmaxf(fmaxf(ylo - ty1, ty0 - yhi), 0.f);
+        if (gx * gx + gy * gy <= deep2 * 1.001f + 1e-3f) {
+          const int slot = atomicAdd(&s_nnear, 1);
+          if (slot < kNearCap) {
+            s_nseg[slot] = sg;
+            s_ninfo[slot] = make_float2(__int_as_float(kseg), inv_ee);
+            s_ny1[slot] = y1;
           }
         }
-      } else if (valid) {
-        for (int cl = 0; cl < ncl; ++cl) {
-          const float4 bb = cbox[cl];
-          // distance: a cluster whose box lies farther than the best distance so
-          // far cannot hold a nearer segment (margin covers the rounding of d^2)
-          const float bx = fmaxf(fmaxf(bb.x - qx, qx - bb.y), 0.f);
-          const float by = fmaxf(fmaxf(bb.z - qy, qy - bb.w), 0.f);
-          const float lb2 = bx * bx + by * by;
-          if (!(lb2 > best + 1e-3f * (lb2 + 1.f))) cluster_nearest(seg, segb, cl, nseg, base, qx, qy, best, arg);
-          // crossings of the ray to +x: only a cluster with vertices on both sides
-          // of y = qy (same comparisons as the per-segment test) that reaches
-          // x >= qx - 0.01 can contribute
-          if (bb.z <= qy && bb.w > qy && bb.y >= qx - 0.01f) wn += cluster_crossings(seg, segb, cl, nseg, qx, qy);
+      }
+      if ((e & 2) && xmax_of(sg) >= tx0 - 0.01f) {
+        // rows r of the tile with ylo <= qy_r < yhi (the straddle rule of the crossing test)
+        const int r0 = max(0, int(ceilf(ylo / h - 0.5f)) - tiy0 - 1);
+        const int r1 = min(kFillTile - 1, int(ceilf(yhi / h - 0.5f)) - tiy0);
+        for (int r = r0; r <= r1; ++r) {
+          const float qyr = (float(tiy0 + r) + 0.5f) * h;
+          if (ylo <= qyr && qyr < yhi) {
+            const int slot = atomicAdd(&s_xcnt[r], 1);
+            if (slot < kRowX) {
+              s_xs[r][slot] = sg;
+              s_xy1[r][slot] = y1;
+            }
+          }
         }
       }
     }
-    if (valid) {
-      const bool inside = sp.fill_rule == 0 ? wn > 0 : wn != 0;
-      float sig = 1.f;
-      if (far) {
-        sig = 0.f;
-      } else if (!deep) {
-        const float4 p0 = bloc[pl.b_off + arg];
-        const float4 p1 = bloc[pl.b_off + (arg + 1 == B ? 0 : arg + 1)];
-        const float d = seg_distance_hl(qx, qy, p0, p1);
-        const float sdf = inside ? d : -d;
-        const float z = sp.gamma / sp.h * sdf;
-        sig = 1.f / (1.f + __expf(-z));
+    __syncthreads();
+    const int nnear = s_nnear;
+    const bool near_ovf = ovf_cl || nnear > kNearCap;
+    if (!near_ovf) {
+      // band: one warp per listed segment, its lanes over the tile points
+      // within the band of the segment's box
+      for (int i = warp; i < nnear; i += blockDim.x >> 5) {
+        const float4 sg = s_nseg[i];
+        const float2 info = s_ninfo[i];
+        const int kseg = __float_as_int(info.x);
+        const float y1 = s_ny1[i];
+        const float xlo = fminf(sg.x, sg.x + sg.z) - band, xhi = fmaxf(sg.x, sg.x + sg.z) + band;
+        const float ylo = fminf(sg.y, y1) - band, yhi = fmaxf(sg.y, y1) + band;
+        const int ia = max(tix0, int(ceilf(xlo / h - 0.5f))), ib = min(tix0 + kFillTile - 1, int(floorf(xhi / h - 0.5f)));
+        const int ja = max(tiy0, int(ceilf(ylo / h - 0.5f))), jb = min(tiy0 + kFillTile - 1, int(floorf(yhi / h - 0.5f)));
+        if (ia > ib || ja > jb) continue;
+        const int w = ib - ia + 1, npts = w * (jb - ja + 1);
+        for (int p = lane; p < npts; p += 32) {
+          const int jx = ia + p % w, jy = ja + p / w;
+          const float d2 = seg_d2((float(jx) + 0.5f) * h, (float(jy) + 0.5f) * h, sg, info.y);
+          if (d2 <= deep2)
+            atomicMin(&s_key[(jy - tiy0) * kFillTile + (jx - tix0)],
+                      ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned int)kseg);
+        }
       }
-      const float2 lo = glo[c];
-      rec[g] = make_float4(__fadd_rn(pl.x0, __fadd_rn(qx, lo.x)), __fadd_rn(pl.y0, __fadd_rn(qy, lo.y)),
-                           sp.eta * sp.h / sp.rho, o * sig);
-      gcurve[g] = c;
-      gaux[g] = deep ? kAuxDeep : (far ? kAuxFar : (inside ? arg : ~arg));
     }
+    __syncthreads();
+    if (!valid) continue;
+    // winding number from the row's crossing list (or the whole polyline)
+    int wn = 0;
+    const int r = iy - tiy0;
+    const int nx_r = s_xcnt[r];
+    if (!ovf_cl && nx_r <= kRowX) {
+      for (int q = 0; q < nx_r; ++q) wn += seg_crossing(qx, qy, s_xs[r][q], s_xy1[r][q]);
+    } else {
+      float b_unused = FLT_MAX;
+      int a_unused = 0;
+      polyline_scan(bl, cb, B, qx, qy, false, b_unused, a_unused, true, wn);
+    }
+    const bool inside = sp.fill_rule == 0 ? wn > 0 : wn != 0;
+    float best = FLT_MAX;
+    int arg = 0;
+    if (!near_ovf) {
+      const unsigned long long key = s_key[tid];
+      if (key != ~0ull) {
+        best = __uint_as_float(unsigned(key >> 32));
+        arg = int(key & 0xffffffffu);
+      }
+    }
+    bool deep = false, far = false;
+    if (near_ovf || (!inside && best > deep2 && far2 > deep2)) {
+      // exact nearest segment over the whole polyline
+      int w_unused = 0;
+      best = FLT_MAX;
+      arg = 0;
+      polyline_scan(bl, cb, B, qx, qy, true, best, arg, false, w_unused);
+    }
+    if (inside) {
+      deep = best > deep2;
+    } else {
+      far = best > far2;
+    }
+    float sig = 1.f;
+    if (far) {
+      sig = 0.f;
+    } else if (!deep) {
+      const float d = seg_distance_hl(qx, qy, bl[arg], bl[arg + 1 == B ? 0 : arg + 1]);
+      const float sdf = inside ? d : -d;
+      const float z = sp.gamma / h * sdf;
+      sig = 1.f / (1.f + __expf(-z));
+    }
+    const float2 lo = glo[c];
+    rec[g] = make_float4(__fadd_rn(pl.x0, __fadd_rn(qx, lo.x)), __fadd_rn(pl.y0, __fadd_rn(qy, lo.y)),
+                         sp.eta * h / sp.rho, o * sig);
+    gcurve[g] = c;
+    gaux[g] = deep ? kAuxDeep : (far ? kAuxFar : (inside ? arg : ~arg));
   }
 }
 
@@ -985,9 +1109,11 @@ extern "C" ns_status nurbs_sample(const ns_curves* curves, const ns_sample_param
   int* tmap = at<int>(ws, L.o_tasks);
   NS_LAUNCH(NS_KERNEL_SCAN, k_task_map, (nc + 7) / 8, 256, 0, s, nc, plan, st, tmap, (long long)L.tcap);
   const int grid = num_sms() * 8;
-  NS_LAUNCH(NS_KERNEL_EMIT, k_emit, grid, 256, 0, s, *curves, *sp, plan, order, knots, bloc,
-            at<const float2>(ws, L.o_glo), st, reinterpret_cast<float4*>(out->rec),
-                              out->curve, out->aux, cap->gaussians, cap->boundary, tmap, (long long)L.tcap, cbox);
+  NS_LAUNCH(NS_KERNEL_FILL_SDF, k_fill_sdf, num_sms() * 16, 256, 0, s, *curves, *sp, plan, order, bloc, at<const float2>(ws, L.o_glo),
+            cbox, st, reinterpret_cast<float4*>(out->rec), out->curve, out->aux, cap->gaussians, cap->boundary, tmap,
+            (long long)L.tcap);
+  NS_LAUNCH(NS_KERNEL_EMIT, k_emit, grid, 256, 0, s, *curves, *sp, plan, order, knots, st,
+            reinterpret_cast<float4*>(out->rec), out->curve, out->aux, cap->gaussians, tmap, (long long)L.tcap);
   if (out->shape)
     NS_LAUNCH(NS_KERNEL_OTHER, k_emit_shape, grid, 256, 0, s, *curves, *sp, plan, knots, st,
               reinterpret_cast<const float4*>(out->rec), out->curve, reinterpret_cast<float4*>(out->shape));
