@@ -791,10 +791,7 @@ __global__ void __launch_bounds__(256, 5) k_emit(ns_curves cv, ns_sample_params 
 //     point, and every point of a tile whose lists overflow, searches all
 //     clusters with box lower bounds.
 // All coordinates are grid-local (origin 0): the polyline's high parts.
-constexpr int kNearCap = 384;   // band segments listed per tile
-constexpr int kCandCl = 128;    // candidate clusters listed per tile
-
-__device__ __forceinline__ float xmax_of(const float4& sg) { return fmaxf(sg.x, sg.x + sg.z); }
+constexpr int kNearCap = 256;   // band segments listed per tile
 constexpr int kRowX = 12;       // crossing segments listed per tile row
 
 // Squared distance from q to segment {b0, e} (1/|e|^2 given), as in Eq. S1.
@@ -852,29 +849,36 @@ __device__ void polyline_scan(const float4* __restrict__ bl, const float4* __res
   }
 }
 
-__global__ void __launch_bounds__(256, 4) k_fill_sdf(ns_curves cv, ns_sample_params sp,
-                                                  const CurvePlan* __restrict__ plan, const int* __restrict__ order,
-                                                  const float4* __restrict__ bloc, const float2* __restrict__ glo,
-                                                  const float4* __restrict__ cbox, const DevState* __restrict__ st,
-                                                  float4* rec, int* gcurve, int* gaux, long long gcap,
-                                                  long long bcap, const int* __restrict__ tmap, long long tcap) {
-  __shared__ unsigned long long s_key[kChunk];
-  __shared__ float4 s_nseg[kNearCap];         // band segments {b0, e}
-  __shared__ float2 s_ninfo[kNearCap];        // {index bits, 1/|e|^2}
-  __shared__ float s_ny1[kNearCap];           // and their end heights
-  __shared__ int s_ccl[kCandCl];              // candidate clusters: 4 index + near + 2 crossing
-  __shared__ int s_nccl;
-  __shared__ float4 s_xs[kFillTile][kRowX];   // crossing segments per tile row {b0, e}
-  __shared__ float s_xy1[kFillTile][kRowX];   // and their end heights
-  __shared__ int s_xcnt[kFillTile];
-  __shared__ int s_nnear;
+__global__ void __launch_bounds__(256, 8) k_fill_sdf(ns_curves cv, ns_sample_params sp,
+                                                     const CurvePlan* __restrict__ plan, const int* __restrict__ order,
+                                                     const float4* __restrict__ bloc, const float2* __restrict__ glo,
+                                                     const float4* __restrict__ cbox, const DevState* __restrict__ st,
+                                                     float4* rec, int* gcurve, int* gaux, long long gcap,
+                                                     long long bcap, const int* __restrict__ tmap, long long tcap) {
+  // The lists and keys alternate between two buffers from task to task: the
+  // points of one task clear the other buffer, so a task takes three block
+  // barriers (after the lists, after the band, after the points).
+  __shared__ unsigned long long s_key[2][kChunk];
+  __shared__ float4 s_nseg[2][kNearCap];        // band segments {b0, e}
+  __shared__ float2 s_ninfo[2][kNearCap];       // {index bits, 1/|e|^2}
+  __shared__ float s_ny1[2][kNearCap];          // and their end heights
+  __shared__ float4 s_xs[2][kFillTile][kRowX];  // crossing segments per tile row {b0, e}
+  __shared__ float s_xy1[2][kFillTile][kRowX];  // and their end heights
+  __shared__ int s_xcnt[2][kFillTile];
+  __shared__ int s_nnear[2];
   const int n_fill = st->n_chunks;
   const int nc = cv.n_curves;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  s_key[0][tid] = ~0ull;
+  if (tid < kFillTile) s_xcnt[0][tid] = 0;
+  if (tid == 0) s_nnear[0] = 0;
+  __syncthreads();
+  int buf = 0;
   for (int task = blockIdx.x; task < n_fill; task += gridDim.x) {
     const int c = task_curve(tmap, tcap, n_fill, plan, order, nc, task, true);
     const CurvePlan pl = plan[c];
     // a curve whose polyline did not fit the boundary capacity emits nothing
+    // (block-uniform: the buffers stay as they are)
     if (pl.kind != kFill || (long long)pl.b_off + pl.M > bcap) continue;
     const int k = task - pl.chunk_off;
     int ix, iy;
@@ -893,6 +897,7 @@ __global__ void __launch_bounds__(256, 4) k_fill_sdf(ns_curves cv, ns_sample_par
     const float dsat = 17.f * h / sp.gamma;
     const float deep2 = dsat * dsat * 1.001f + 1e-3f;
     const float band = sqrtf(deep2);
+    const float near2 = deep2 * 1.001f + 1e-3f;   // box tests, with a margin for their rounding
     // outside, o sigmoid(-gamma d / h) < fill_cull once d > (h/gamma) ln(o/fill_cull - 1);
     // far2 adds a margin of 0.1 in z (FLT_MAX: no culling)
     float far2 = FLT_MAX;
@@ -903,79 +908,60 @@ __global__ void __launch_bounds__(256, 4) k_fill_sdf(ns_curves cv, ns_sample_par
     const float4* bl = bloc + pl.b_off;
     const float4* cb = cbox + pl.b_off;
     const int B = pl.M;
-    const int ncl = (B + kCluster - 1) / kCluster;
-    __syncthreads();   // the previous task's lists are read
-    s_key[tid] = ~0ull;
-    if (tid < kFillTile) s_xcnt[tid] = 0;
-    if (tid == 0) {
-      s_nnear = 0;
-      s_nccl = 0;
-    }
-    __syncthreads();
-    // clusters near the tile (their segments join the band list) and clusters
-    // straddling a tile row to the right of its first column (crossings)
-    for (int cl = tid; cl < ncl; cl += blockDim.x) {
-      const float4 bb = cb[cl * kCluster];
+    // one thread per segment: segments of clusters whose boxes come within the
+    // band of the tile join the band list, segments straddling a tile row to
+    // the right of the tile's first column join that row's crossing list
+    for (int kseg = tid; kseg < B; kseg += blockDim.x) {
+      const float4 bb = cb[(kseg / kCluster) * kCluster];
       const float gx = fmaxf(fmaxf(bb.x - tx1, tx0 - bb.y), 0.f);
       const float gy = fmaxf(fmaxf(bb.z - ty1, ty0 - bb.w), 0.f);
-      const int near = gx * gx + gy * gy <= deep2 * 1.001f + 1e-3f;
-      const int cross = bb.z <= ty1 && bb.w > ty0 && bb.y >= tx0 - 0.01f;
-      if (near | cross) {
-        const int slot = atomicAdd(&s_nccl, 1);
-        if (slot < kCandCl) s_ccl[slot] = cl * 4 + near + 2 * cross;
-      }
-    }
-    __syncthreads();
-    const int nccl = s_nccl;
-    const bool ovf_cl = nccl > kCandCl;
-    // their segments, one thread each
-    for (int i = tid; !ovf_cl && i < nccl * kCluster; i += blockDim.x) {
-      const int e = s_ccl[i / kCluster];
-      const int kseg = (e >> 2) * kCluster + i % kCluster;
-      if (kseg >= B) continue;
+      const bool ncl_near = gx * gx + gy * gy <= near2;
+      const bool ncl_cross = bb.z <= ty1 && bb.w > ty0 && bb.y >= tx0 - 0.01f;
+      if (!ncl_near && !ncl_cross) continue;
       float y1, inv_ee;
       const float4 sg = seg_at(bl, B, kseg, y1, inv_ee);
+      const float xlo = fminf(sg.x, sg.x + sg.z), xhi = fmaxf(sg.x, sg.x + sg.z);
       const float ylo = fminf(sg.y, y1), yhi = fmaxf(sg.y, y1);
-      if (e & 1) {
-        const float xlo = fminf(sg.x, sg.x + sg.z), xhi = fmaxf(sg.x, sg.x + sg.z);
-        const float gx = fmaxf(fmaxf(xlo - tx1, tx0 - xhi), 0.f);
-        const float gy = fmaxf(fmaxf(ylo - ty1, ty0 - yhi), 0.f);
-        if (gx * gx + gy * gy <= deep2 * 1.001f + 1e-3f) {
-          const int slot = atomicAdd(&s_nnear, 1);
+      if (ncl_near) {
+        const float sx = fmaxf(fmaxf(xlo - tx1, tx0 - xhi), 0.f);
+        const float sy = fmaxf(fmaxf(ylo - ty1, ty0 - yhi), 0.f);
+        if (sx * sx + sy * sy <= near2) {
+          const int slot = atomicAdd(&s_nnear[buf], 1);
           if (slot < kNearCap) {
-            s_nseg[slot] = sg;
-            s_ninfo[slot] = make_float2(__int_as_float(kseg), inv_ee);
-            s_ny1[slot] = y1;
+            s_nseg[buf][slot] = sg;
+            s_ninfo[buf][slot] = make_float2(__int_as_float(kseg), inv_ee);
+            s_ny1[buf][slot] = y1;
           }
         }
       }
-      if ((e & 2) && xmax_of(sg) >= tx0 - 0.01f) {
+      if (ncl_cross && xhi >= tx0 - 0.01f) {
         // rows r of the tile with ylo <= qy_r < yhi (the straddle rule of the crossing test)
         const int r0 = max(0, int(ceilf(ylo / h - 0.5f)) - tiy0 - 1);
         const int r1 = min(kFillTile - 1, int(ceilf(yhi / h - 0.5f)) - tiy0);
         for (int r = r0; r <= r1; ++r) {
           const float qyr = (float(tiy0 + r) + 0.5f) * h;
           if (ylo <= qyr && qyr < yhi) {
-            const int slot = atomicAdd(&s_xcnt[r], 1);
+            const int slot = atomicAdd(&s_xcnt[buf][r], 1);
             if (slot < kRowX) {
-              s_xs[r][slot] = sg;
-              s_xy1[r][slot] = y1;
+              s_xs[buf][r][slot] = sg;
+              s_xy1[buf][r][slot] = y1;
             }
           }
         }
       }
     }
     __syncthreads();
-    const int nnear = s_nnear;
-    const bool near_ovf = ovf_cl || nnear > kNearCap;
+    const int nnear = s_nnear[buf];
+    const bool near_ovf = nnear > kNearCap;
+    unsigned long long* key = s_key[buf];
     if (!near_ovf) {
       // band: one warp per listed segment, its lanes over the tile points
       // within the band of the segment's box
       for (int i = warp; i < nnear; i += blockDim.x >> 5) {
-        const float4 sg = s_nseg[i];
-        const float2 info = s_ninfo[i];
+        const float4 sg = s_nseg[buf][i];
+        const float2 info = s_ninfo[buf][i];
         const int kseg = __float_as_int(info.x);
-        const float y1 = s_ny1[i];
+        const float y1 = s_ny1[buf][i];
         const float xlo = fminf(sg.x, sg.x + sg.z) - band, xhi = fmaxf(sg.x, sg.x + sg.z) + band;
         const float ylo = fminf(sg.y, y1) - band, yhi = fmaxf(sg.y, y1) + band;
         const int ia = max(tix0, int(ceilf(xlo / h - 0.5f))), ib = min(tix0 + kFillTile - 1, int(floorf(xhi / h - 0.5f)));
@@ -986,61 +972,66 @@ __global__ void __launch_bounds__(256, 4) k_fill_sdf(ns_curves cv, ns_sample_par
           const int jx = ia + p % w, jy = ja + p / w;
           const float d2 = seg_d2((float(jx) + 0.5f) * h, (float(jy) + 0.5f) * h, sg, info.y);
           if (d2 <= deep2)
-            atomicMin(&s_key[(jy - tiy0) * kFillTile + (jx - tix0)],
+            atomicMin(&key[(jy - tiy0) * kFillTile + (jx - tix0)],
                       ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned int)kseg);
         }
       }
     }
     __syncthreads();
-    if (!valid) continue;
-    // winding number from the row's crossing list (or the whole polyline)
-    int wn = 0;
-    const int r = iy - tiy0;
-    const int nx_r = s_xcnt[r];
-    if (!ovf_cl && nx_r <= kRowX) {
-      for (int q = 0; q < nx_r; ++q) wn += seg_crossing(qx, qy, s_xs[r][q], s_xy1[r][q]);
-    } else {
-      float b_unused = FLT_MAX;
-      int a_unused = 0;
-      polyline_scan(bl, cb, B, qx, qy, false, b_unused, a_unused, true, wn);
-    }
-    const bool inside = sp.fill_rule == 0 ? wn > 0 : wn != 0;
-    float best = FLT_MAX;
-    int arg = 0;
-    if (!near_ovf) {
-      const unsigned long long key = s_key[tid];
-      if (key != ~0ull) {
-        best = __uint_as_float(unsigned(key >> 32));
-        arg = int(key & 0xffffffffu);
+    if (valid) {
+      // winding number from the row's crossing list (or the whole polyline)
+      int wn = 0;
+      const int r = iy - tiy0;
+      const int nx_r = s_xcnt[buf][r];
+      if (nx_r <= kRowX) {
+        for (int q = 0; q < nx_r; ++q) wn += seg_crossing(qx, qy, s_xs[buf][r][q], s_xy1[buf][r][q]);
+      } else {
+        float b_unused = FLT_MAX;
+        int a_unused = 0;
+        polyline_scan(bl, cb, B, qx, qy, false, b_unused, a_unused, true, wn);
       }
+      const bool inside = sp.fill_rule == 0 ? wn > 0 : wn != 0;
+      float best = FLT_MAX;
+      int arg = 0;
+      if (!near_ovf) {
+        const unsigned long long kk = key[tid];
+        if (kk != ~0ull) {
+          best = __uint_as_float(unsigned(kk >> 32));
+          arg = int(kk & 0xffffffffu);
+        }
+      }
+      if (near_ovf || (!inside && best > deep2 && far2 > deep2)) {
+        // an outside point beyond the band without a cull distance inside it,
+        // or a tile whose band list overflowed: the exact nearest segment over
+        // the whole polyline
+        int w_unused = 0;
+        best = FLT_MAX;
+        arg = 0;
+        polyline_scan(bl, cb, B, qx, qy, true, best, arg, false, w_unused);
+      }
+      const bool deep = inside && best > deep2;
+      const bool far = !inside && best > far2;
+      float sig = 1.f;
+      if (far) {
+        sig = 0.f;
+      } else if (!deep) {
+        const float d = seg_distance_hl(qx, qy, bl[arg], bl[arg + 1 == B ? 0 : arg + 1]);
+        const float sdf = inside ? d : -d;
+        const float z = sp.gamma / h * sdf;
+        sig = 1.f / (1.f + __expf(-z));
+      }
+      const float2 lo = glo[c];
+      rec[g] = make_float4(__fadd_rn(pl.x0, __fadd_rn(qx, lo.x)), __fadd_rn(pl.y0, __fadd_rn(qy, lo.y)),
+                           sp.eta * h / sp.rho, o * sig);
+      gcurve[g] = c;
+      gaux[g] = deep ? kAuxDeep : (far ? kAuxFar : (inside ? arg : ~arg));
     }
-    bool deep = false, far = false;
-    if (near_ovf || (!inside && best > deep2 && far2 > deep2)) {
-      // exact nearest segment over the whole polyline
-      int w_unused = 0;
-      best = FLT_MAX;
-      arg = 0;
-      polyline_scan(bl, cb, B, qx, qy, true, best, arg, false, w_unused);
-    }
-    if (inside) {
-      deep = best > deep2;
-    } else {
-      far = best > far2;
-    }
-    float sig = 1.f;
-    if (far) {
-      sig = 0.f;
-    } else if (!deep) {
-      const float d = seg_distance_hl(qx, qy, bl[arg], bl[arg + 1 == B ? 0 : arg + 1]);
-      const float sdf = inside ? d : -d;
-      const float z = sp.gamma / h * sdf;
-      sig = 1.f / (1.f + __expf(-z));
-    }
-    const float2 lo = glo[c];
-    rec[g] = make_float4(__fadd_rn(pl.x0, __fadd_rn(qx, lo.x)), __fadd_rn(pl.y0, __fadd_rn(qy, lo.y)),
-                         sp.eta * h / sp.rho, o * sig);
-    gcurve[g] = c;
-    gaux[g] = deep ? kAuxDeep : (far ? kAuxFar : (inside ? arg : ~arg));
+    // clear the other buffer for the next task
+    s_key[buf ^ 1][tid] = ~0ull;
+    if (tid < kFillTile) s_xcnt[buf ^ 1][tid] = 0;
+    if (tid == 0) s_nnear[buf ^ 1] = 0;
+    __syncthreads();
+    buf ^= 1;
   }
 }
 
@@ -1109,6 +1100,12 @@ extern "C" ns_status nurbs_sample(const ns_curves* curves, const ns_sample_param
   int* tmap = at<int>(ws, L.o_tasks);
   NS_LAUNCH(NS_KERNEL_SCAN, k_task_map, (nc + 7) / 8, 256, 0, s, nc, plan, st, tmap, (long long)L.tcap);
   const int grid = num_sms() * 8;
+  static bool carveout = false;   // eight resident blocks need most of the SM's shared memory
+  if (!carveout) {
+    cudaFuncSetAttribute(k_fill_sdf, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         int(cudaSharedmemCarveoutMaxShared));
+    carveout = true;
+  }
   NS_LAUNCH(NS_KERNEL_FILL_SDF, k_fill_sdf, num_sms() * 16, 256, 0, s, *curves, *sp, plan, order, bloc, at<const float2>(ws, L.o_glo),
             cbox, st, reinterpret_cast<float4*>(out->rec), out->curve, out->aux, cap->gaussians, cap->boundary, tmap,
             (long long)L.tcap);
