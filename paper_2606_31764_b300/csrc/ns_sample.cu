@@ -968,8 +968,10 @@ __global__ void __launch_bounds__(256, 8) k_fill_sdf(ns_curves cv, ns_sample_par
         const int ja = max(tiy0, int(ceilf(ylo / h - 0.5f))), jb = min(tiy0 + kFillTile - 1, int(floorf(yhi / h - 0.5f)));
         if (ia > ib || ja > jb) continue;
         const int w = ib - ia + 1, npts = w * (jb - ja + 1);
+        const float inv_w = 1.f / float(w);
         for (int p = lane; p < npts; p += 32) {
-          const int jx = ia + p % w, jy = ja + p / w;
+          const int py = int((float(p) + 0.5f) * inv_w);   // exact for the box sizes of a tile
+          const int jx = ia + (p - py * w), jy = ja + py;
           const float d2 = seg_d2((float(jx) + 0.5f) * h, (float(jy) + 0.5f) * h, sg, info.y);
           if (d2 <= deep2)
             atomicMin(&key[(jy - tiy0) * kFillTile + (jx - tix0)],
