@@ -480,17 +480,24 @@ uint64_t ns_launch_count(void);
  * 262144 (tile, Gaussian) pairs, and the batch's workspace (ns_workspace_size
  * with those capacities and no boundary points) must fit the 16 MiB; a larger
  * request returns NS_ERR_INVALID_ARG with a message saying which limit.  More
- * pairs than the limit is only known on the device: that work is dropped and
- * the status reads NS_ERR_CAPACITY.
+ * pairs than the limit is only known on the device: that work is dropped (the
+ * image stays finite but misses those pairs) and the status reads
+ * NS_ERR_CAPACITY -- visible only through a non-NULL report, since the array
+ * is private to the library and the next call clears it.
  *   report: host pointer or NULL.  When non-NULL the call synchronises the
- *   stream and fills it (as ns_poll_status would).
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress), so make it before any stream capture.  All calls on
- * one device share the array: calls that overlap on the GPU (other streams or
- * threads) race and must be serialised by the caller.  Each call clears the
- * status it inherits from the previous one.  It calls no allocator.  It
- * always bins one pair per Gaussian and tile (rp->fill_layers is ignored:
- * fill layers need the sampling plans of a workspace, which it has none of).
+ *   stream and fills it: status, pairs (needed), fill_culled and the blend
+ *   counters as ns_poll_status would, and gaussians = the set's count.  With
+ *   NULL the call only enqueues work and returns.
+ * Each call that is not being captured into a CUDA graph looks up the array's
+ * device address (cudaGetSymbolAddress), so a device reset is picked up; a
+ * call made during stream capture reuses the address found by the last
+ * uncaptured call on that device, so make one call before any capture.  All
+ * calls on one device share the array: calls that overlap on the GPU (other
+ * streams or threads) race and must be serialised by the caller.  Each call
+ * clears the status it inherits from the previous one.  It calls no
+ * allocator.  It always bins one pair per Gaussian and tile (rp->fill_layers
+ * is ignored: fill layers need the sampling plans of a workspace, which it
+ * has none of).
  */
 ns_status splat_forward_noalloc(const ns_curves* curves, const ns_gaussians* g,
                                 const ns_raster_params* rp, float* image, ns_report* report,

@@ -26,19 +26,24 @@ constexpr int64_t kNoAllocMaxPairs = 1 << 18;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-// Device address of the scratch array, looked up once per device.  In host
-// code the name g_noalloc_scratch is only a host-side stand-in, not a device
-// address, so it is never passed to a kernel directly.
+// Device address of the scratch array.  In host code the name
+// g_noalloc_scratch is only a host-side stand-in, not a device address, so it
+// is never passed to a kernel directly.  The address is looked up on every
+// call that is not being captured into a CUDA graph (so a device reset or a
+// new context on the same ordinal is picked up); a call made while its stream
+// is capturing reuses the address the last uncaptured call on that device
+// found, since the lookup may not be legal during capture.
 static std::mutex g_noalloc_mutex;
 static void* g_noalloc_ptr[64] = {nullptr};
 
-static void* noalloc_scratch(int dev) {
+static void* noalloc_scratch(int dev, bool capturing) {
   if (dev < 0 || dev >= 64) return nullptr;
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_ptr[dev]) {
+  if (!capturing) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
       cudaGetLastError();
+      g_noalloc_ptr[dev] = nullptr;
       return nullptr;
     }
     g_noalloc_ptr[dev] = p;
@@ -83,9 +88,17 @@ extern "C" ns_status splat_forward_noalloc(const ns_curves* curves, const ns_gau
     set_error("splat_forward_noalloc: no current device");
     return NS_ERR_CUDA;
   }
-  void* ws = noalloc_scratch(dev);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cs) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("splat_forward_noalloc: invalid stream");
+    return NS_ERR_CUDA;
+  }
+  void* ws = noalloc_scratch(dev, cs != cudaStreamCaptureStatusNone);
   if (!ws) {
-    set_error("splat_forward_noalloc: cudaGetSymbolAddress of the scratch array failed");
+    set_error(cs != cudaStreamCaptureStatusNone
+                  ? "splat_forward_noalloc: the first call on a device must come before any stream capture"
+                  : "splat_forward_noalloc: cudaGetSymbolAddress of the scratch array failed");
     return NS_ERR_CUDA;
   }
   // The scratch keeps the previous call's contents: start from a clear status.
@@ -93,5 +106,15 @@ extern "C" ns_status splat_forward_noalloc(const ns_curves* curves, const ns_gau
   if (st != NS_OK) return st;
   st = splat_forward(curves, g, rp, &cap, image, ws, kNoAllocBytes, stream);
   if (st != NS_OK || !report) return st;
-  return ns_poll_status(ws, report, stream);
+  st = ns_poll_status(ws, report, stream);
+  if (st != NS_OK) return st;
+  // the status word was cleared above, and with it the sampling counters:
+  // report the Gaussians the set holds (its count) instead
+  int count = 0;
+  if (cudaMemcpy(&count, g->count, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    set_error(std::string("splat_forward_noalloc: ") + cudaGetErrorString(cudaGetLastError()));
+    return NS_ERR_CUDA;
+  }
+  report->gaussians = count;
+  return NS_OK;
 }
