@@ -231,7 +231,7 @@ class Step:
         return int(self.sp.count.item())
 
 
-def autotune(torch, scene, tiles, capacity, steps=3, adam=False, geometry=None, layers=(0, 1)):
+def autotune(torch, scene, tiles, capacity, steps=3, adam=False, geometry=None, layers=(0, 1), fill_tiles=(16, 8)):
     """Tile size and binning (per Gaussian, or fill layers) by timing whole
     steps; the blend decomposition by the library's ns_autotune_blend on each
     candidate's workspace."""
@@ -250,9 +250,11 @@ def autotune(torch, scene, tiles, capacity, steps=3, adam=False, geometry=None, 
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
+        rep_t = st.sp.report()
         table[f"{tile}" + ("-layers" if fl else "")] = dict(ms=round(ms, 4), ppt_fwd=int(st.sp.rp.ppt_fwd),
-                                                             ppt_bwd=int(st.sp.rp.ppt_bwd),
-                                                             pairs=int(st.sp.report().pairs))
+                                                             ppt_bwd=int(st.sp.rp.ppt_bwd), pairs=int(rep_t.pairs),
+                                                             visits_fwd=int(rep_t.blend_visits),
+                                                             visits_bwd=int(rep_t.blend_bwd_visits))
         if best_ms is None or ms < best_ms:
             if best is not None:
                 del best
@@ -262,6 +264,33 @@ def autotune(torch, scene, tiles, capacity, steps=3, adam=False, geometry=None, 
         torch.cuda.empty_cache()
     chosen = dict(tile=int(best.sp.rp.tile), ppt_fwd=int(best.sp.rp.ppt_fwd), ppt_bwd=int(best.sp.rp.ppt_bwd),
                   fill_layers=int(best.sp.rp.fill_layers), tried=table)
+    # Gaussians per sampling block (the fill tile of the SDF and the fill
+    # chain) on the chosen raster
+    raster = dict(scene.raster, tile=chosen["tile"], fill_layers=chosen["fill_layers"], ppt_fwd=chosen["ppt_fwd"],
+                  ppt_bwd=chosen["ppt_bwd"])
+    ft_table, best_ft, best_ft_ms = {}, 16, None
+    for ft in fill_tiles:
+        st = best if ft == 16 else Step(scene.with_sample(fill_tile=ft), capacity, raster=raster, adam=adam,
+                                         geometry=geometry)
+        st()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            st()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        ft_table[str(ft * ft)] = round(ms, 4)
+        if best_ft_ms is None or ms < best_ft_ms:
+            if st is not best:
+                best = st
+            best_ft, best_ft_ms = ft, ms
+        elif st is not best:
+            del st
+        torch.cuda.empty_cache()
+    chosen["fill_gaussians_per_block"] = best_ft * best_ft
+    chosen["tried_fill_gaussians_per_block"] = ft_table
     return best, chosen
 
 
@@ -373,26 +402,35 @@ def run_gpu(args, dist, rank, world):
     performed = dict(blend_fwd=(rep.blend_evals * FLOP_EVAL + rep.blend_contribs * FLOP_CONTRIB_FWD) / 1e12,
                      blend_bwd=(rep.blend_bwd_evals * FLOP_EVAL + rep.blend_contribs * FLOP_CONTRIB_BWD) / 1e12)
     layers = bool(step.sp.rp.fill_layers)
-    # with per-Gaussian pairs the blend work is counted per visited (pixel,
-    # list entry) pair; fill layers have no per-Gaussian list, and there the
-    # FP32 work the kernels performed is reported instead
+    # the blend work is counted per visited (pixel, list entry) pair of Eq. 8-9's
+    # loop over the per-Gaussian tile lists.  Fill layers composite the same
+    # Gaussians in the same order without such lists; the visits are a property
+    # of the lists and the image, so they come from the per-Gaussian kernels'
+    # counters in the autotuner's trial at the same tile size (else the FP32
+    # work the layer kernels performed is reported)
+    pg = tuning["tried"].get(str(int(step.sp.rp.tile)), {}) if layers else {}
+    visits_fwd = pg.get("visits_fwd", 0) if layers else rep.blend_visits
+    visits_bwd = pg.get("visits_bwd", 0) if layers else rep.blend_bwd_visits
+    visit_src = ("per-Gaussian trial at this tile size" if layers else "this step's counters")
     work = dict(
-        emit=("alu", costs["segment_tests"] * FLOP_SEGMENT / 1e12, "TFLOP/s", fp32_peak),
-        blend_fwd=("alu", performed["blend_fwd"] if layers else rep.blend_visits * FLOP_VISIT_FWD / 1e12,
+        fill_sdf=("alu", costs["segment_tests"] * FLOP_SEGMENT / 1e12, "TFLOP/s", fp32_peak),
+        blend_fwd=("alu", visits_fwd * FLOP_VISIT_FWD / 1e12 if visits_fwd else performed["blend_fwd"],
                    "TFLOP/s", fp32_peak),
-        blend_bwd=("alu", performed["blend_bwd"] if layers else rep.blend_bwd_visits * FLOP_VISIT_BWD / 1e12,
+        blend_bwd=("alu", visits_bwd * FLOP_VISIT_BWD / 1e12 if visits_bwd else performed["blend_bwd"],
                    "TFLOP/s", fp32_peak),
         radix_scatter=("hbm", rep.pairs * 16 / 1e9, "GB/s", peaks["hbm_gbs"]),
         # fill layers: the emission reads the curve of every Gaussian, not its record
         bin_emit=("hbm", ((G * 4 if layers else G * 20) + rep.pairs * 8) / 1e9, "GB/s", peaks["hbm_gbs"]),
     )
     work_text = dict(
-        emit=f"algorithmic: {FLOP_SEGMENT} FP32 FLOP per (grid point, boundary segment) test of the plain "
-             "definition (Eq. S1-S2), Q x B per curve",
-        blend_fwd=("performed: 10 FP32 FLOP per alpha evaluation + 10 per composited pair (fill layers)" if layers
-                   else f"algorithmic: visited (pixel, list entry) pairs of Eq. 8-9 x {FLOP_VISIT_FWD} FP32 FLOP"),
-        blend_bwd=("performed: 10 FP32 FLOP per alpha evaluation + 33 per composited pair (fill layers)" if layers
-                   else f"algorithmic: visited (pixel, list entry) pairs of Eq. 8-9 x {FLOP_VISIT_BWD} FP32 FLOP"),
+        fill_sdf=f"algorithmic: {FLOP_SEGMENT} FP32 FLOP per (grid point, boundary segment) test of the plain "
+                 "definition (Eq. S1-S2), Q x B per curve",
+        blend_fwd=(f"algorithmic: {visits_fwd} visited (pixel, list entry) pairs of Eq. 8-9 ({visit_src}) x "
+                   f"{FLOP_VISIT_FWD} FP32 FLOP" if visits_fwd else
+                   "performed: 10 FP32 FLOP per alpha evaluation + 10 per composited pair (fill layers)"),
+        blend_bwd=(f"algorithmic: {visits_bwd} visited (pixel, list entry) pairs of Eq. 8-9 ({visit_src}) x "
+                   f"{FLOP_VISIT_BWD} FP32 FLOP" if visits_bwd else
+                   "performed: 10 FP32 FLOP per alpha evaluation + 33 per composited pair (fill layers)"),
         radix_scatter="16 B per pair and pass (read + write of key and value)",
         bin_emit="curve ids (fill layers) or records and curve ids read, 8 B per pair written",
     )
@@ -421,7 +459,7 @@ def run_gpu(args, dist, rank, world):
                     peak_source=("FP32 lanes x SMs x max SM clock" if bound == "alu"
                                  else f"{peaks['source']} HBM copy bandwidth"))
         roof["work"] = work_text[dom]
-        if dom in performed and not layers:
+        if dom in performed:
             roof["performed_frac"] = kernels[dom]["performed_frac"]
 
     # end to end through the public API with host buffers
@@ -595,7 +633,7 @@ def run_long_spline(torch, args):
     sc = scenes.config3()
     geo = dict(lambda_deriv=1.0, lambda_bbox=5.0, order=3)
     st, tuning = autotune(torch, sc, [int(x) for x in args.tiles.split(",")], capacity=(3_000_000, 24_000_000, 16),
-                          adam=True, geometry=geo, layers=(0,))   # open strokes only: no fill layers
+                          adam=True, geometry=geo, layers=(0,), fill_tiles=(16,))   # open strokes only: no fills
     st()
     K = max(3, args.steps)
     prof = ["emit", "bin_emit", "radix_scatter", "blend_fwd", "blend_bwd", "chain_contour", "deriv_loss",

@@ -96,6 +96,10 @@ typedef struct {
                        C'_xy/|C'_xy| (Eq. 2) with sigma_t = |C'_xy| du / rho, du the
                        parameter step between samples, and keeps sigma_n = s / rho
                        across; the Gaussian set then needs `shape` */
+  int32_t fill_tile;  /* fill Gaussians per sampling block: the signed distance and the
+                       fill chain run one block per fill_tile x fill_tile tile of a
+                       curve's grid, 8 or 16 (64 or 256 Gaussians); 0 = 16.  Changes
+                       no result, only the work decomposition */
 } ns_sample_params;
 
 /* Blend decomposition flag for ns_raster_params.ppt_fwd / ppt_bwd: with it,

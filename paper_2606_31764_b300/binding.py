@@ -31,7 +31,7 @@ class NsSampleParams(C.Structure):
     _fields_ = [("delta_c", C.c_float), ("rho", C.c_float), ("delta_b", C.c_float), ("h", C.c_float),
                 ("eta", C.c_float), ("gamma", C.c_float), ("pad_frac", C.c_float), ("kappa", C.c_int32),
                 ("nl_mult", C.c_int32), ("fill_rule", C.c_int32), ("fill_cull", C.c_float),
-                ("contour_mode", C.c_int32)]
+                ("contour_mode", C.c_int32), ("fill_tile", C.c_int32)]
 
 
 class NsRasterParams(C.Structure):

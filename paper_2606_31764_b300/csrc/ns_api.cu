@@ -134,10 +134,10 @@ bool make_layout(const ns_curves* c, const ns_capacity* cap, const ns_raster_par
   L->o_knots_lo = take(sizeof(float) * nkn);
   L->o_krcp = take(sizeof(float2) * kMaxP * nkn);
   // contour tasks cover a curve's samples in chunks of kChunk, fill tasks its
-  // grid in 16 x 16 tiles (at most (nx ny + 15 (nx + ny) + 225) / 256 of them):
-  // within the Gaussian capacity this table holds them all (past it the task
-  // -> curve search takes over)
-  L->tcap = L->gcap / kChunk + L->gcap / kFillTile + 2LL * L->nc + 1;
+  // grid in T x T tiles, T = 8 or 16 (at most (nx ny + (T - 1)(nx + ny) +
+  // (T - 1)^2) / T^2 of them): within the Gaussian capacity this table holds
+  // them all (past it the task -> curve search takes over)
+  L->tcap = L->gcap / kChunk + L->gcap / 64 + L->gcap / 8 + 2LL * L->nc + 1;
   L->o_tasks = take(sizeof(int) * (size_t)L->tcap);
   L->sample_total = o;   // everything above depends on the curves and capacities only
   L->o_bsum = take(sizeof(int) * (size_t)(L->bin_blocks + 1));
@@ -238,6 +238,7 @@ ns_sample_params ns_default_sample_params(void) {
   p.fill_rule = 0;
   p.fill_cull = 0.f;
   p.contour_mode = 0;  // isotropic contour Gaussians (Eq. 5)
+  p.fill_tile = 0;     // 16 x 16 fill tiles
   return p;
 }
 

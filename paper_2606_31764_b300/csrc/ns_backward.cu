@@ -73,6 +73,7 @@ __device__ __forceinline__ void curve_point_bwd_local(const float4* key, const C
 struct ChainParams {
   float rho, h, gamma;
   int kappa;
+  int ftile;            // fill tile edge of nurbs_sample (8 or 16): fill tasks are ftile x ftile tiles
   int freeze_w;         // rational weights frozen: no dL/dw is written
   const int* tmap;      // task -> curve table of nurbs_sample
   long long tcap;       // its entries
@@ -99,9 +100,9 @@ __global__ void __launch_bounds__(256, 8) k_chain(ns_curves cv, ChainParams cp, 
     const int c = task_curve(cp.tmap, cp.tcap, n_tasks, plan, order, nc, task, true);
     const CurvePlan pl = plan[c];
     const CurveRef cr = curve_ref(cv, c);
-    // a fill task is a 16 x 16 tile of the curve's grid
+    // a fill task is a tile of the curve's grid (ftile x ftile points)
     int ix, iy;
-    const bool in_grid = fill_task_point(task - pl.chunk_off, pl.nx, pl.ny, threadIdx.x, ix, iy);
+    const bool in_grid = fill_task_point(task - pl.chunk_off, pl.nx, pl.ny, threadIdx.x, cp.ftile, ix, iy);
     const long long g = (long long)pl.g_off + (long long)iy * pl.nx + ix;
     const bool valid = in_grid && g < gcap;
     __syncthreads();
@@ -542,10 +543,12 @@ extern "C" ns_status splat_backward(const ns_curves* curves, const ns_gaussians*
       cp.h = sp->h;
       cp.gamma = sp->gamma;
       cp.kappa = sp->kappa;
+      cp.ftile = fill_tile_of(sp->fill_tile);
       cp.freeze_w = (out->frozen & NS_FROZEN_WEIGHTS) != 0;
       cp.tmap = at<const int>(ws, L.o_tasks);
       cp.tcap = L.tcap;
-      NS_LAUNCH(NS_KERNEL_CHAIN, k_chain, num_sms() * 8, 256, 0, s, *curves, cp, plan, order, knots,
+      // one block per fill task: ftile x ftile threads
+      NS_LAUNCH(NS_KERNEL_CHAIN, k_chain, num_sms() * 8 * (256 / (cp.ftile * cp.ftile)), cp.ftile * cp.ftile, 0, s, *curves, cp, plan, order, knots,
                 at<const float4>(ws, L.o_bloc), st,
                 reinterpret_cast<const float4*>(g->rec), g->aux, dg, cap->gaussians,
                 cap->boundary, out->dkey, dknots, dbpts, out->dcolor, row / 4);

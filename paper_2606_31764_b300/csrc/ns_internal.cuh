@@ -14,7 +14,7 @@ namespace ns {
 
 constexpr int kMaxP = NS_MAX_DEGREE;
 constexpr int kChunk = 256;          // Gaussians per sampling / chain task (one block)
-constexpr int kFillTile = 16;        // a fill task: a 16 x 16 tile of its curve's grid (kChunk points)
+constexpr int kFillTileMax = 16;     // a fill task: a T x T tile of its curve's grid, T = 8 or 16
 constexpr int kBinItems = 2048;      // Gaussians per binning block (256 threads x 8)
 constexpr int kSortItems = 4096;     // pairs per radix-sort block (256 threads x 16)
 constexpr int kKnotPad = 2 * kMaxP + 1;  // knots per curve = intervals + 2p + 1
@@ -545,19 +545,22 @@ __device__ __forceinline__ int task_curve(const int* __restrict__ tmap, long lon
   return t < tcap ? tmap[t] : curve_of_task(plan, order, nc, task, fill);
 }
 
-// Fill tasks of a curve's nx x ny grid: its 16 x 16 tiles, row-major.
-__host__ __device__ __forceinline__ int fill_task_count(int nx, int ny) {
-  return ((nx + kFillTile - 1) / kFillTile) * ((ny + kFillTile - 1) / kFillTile);
+// Fill tasks of a curve's nx x ny grid: its T x T tiles, row-major.
+__host__ __device__ __forceinline__ int fill_task_count(int nx, int ny, int T) {
+  return ((nx + T - 1) / T) * ((ny + T - 1) / T);
 }
 
-// Grid point (ix, iy) of thread t (0..255) in fill task k of a curve with an
-// nx x ny grid; false past the grid.
-__device__ __forceinline__ bool fill_task_point(int k, int nx, int ny, int t, int& ix, int& iy) {
-  const int tcols = (nx + kFillTile - 1) / kFillTile;
-  ix = (k % tcols) * kFillTile + (t % kFillTile);
-  iy = (k / tcols) * kFillTile + (t / kFillTile);
+// Grid point (ix, iy) of thread t (0..T^2-1) in fill task k (T x T tiles) of a
+// curve with an nx x ny grid; false past the grid.
+__device__ __forceinline__ bool fill_task_point(int k, int nx, int ny, int t, int T, int& ix, int& iy) {
+  const int tcols = (nx + T - 1) / T;
+  ix = (k % tcols) * T + (t % T);
+  iy = (k / tcols) * T + (t / T);
   return ix < nx && iy < ny;
 }
+
+// The fill tile edge of a sampling setting (0 -> 16).
+__host__ __device__ __forceinline__ int fill_tile_of(int v) { return v == 8 ? 8 : 16; }
 
 // Task -> curve map.  Contour tasks are 256 samples of one curve, fill tasks
 // 16 x 16 tiles of one curve's grid; fill tasks and

@@ -580,12 +580,12 @@ __global__ void __launch_bounds__(256) k_boundary_box(ns_curves cv, ns_sample_pa
 // the task count of the other kind before it, so that each kind's offsets
 // can be searched over the one ordered list (see curve_of_task).
 __global__ void k_scan_gauss(int nc, CurvePlan* plan, const int* order, DevState* st, long long gcap,
-                             int* g_count_out) {
+                             int* g_count_out, int ftile) {
   const long long tot = block_scan_items(
       nc, [&](int f) { return plan[order[f]].count; },
       [&](int f, long long off) { plan[order[f]].g_off = int(off < 0x7fffffff ? off : 0x7fffffff); });
   const long long ftasks = block_scan_items(
-      nc, [&](int f) { const CurvePlan& q = plan[order[f]]; return q.kind == kFill ? fill_task_count(q.nx, q.ny) : 0; },
+      nc, [&](int f) { const CurvePlan& q = plan[order[f]]; return q.kind == kFill ? fill_task_count(q.nx, q.ny, ftile) : 0; },
       [&](int f, long long off) {
         CurvePlan& q = plan[order[f]];
         if (q.kind == kFill) q.chunk_off = int(off); else q.pad[0] = int(off);
@@ -610,13 +610,13 @@ __global__ void k_scan_gauss(int nc, CurvePlan* plan, const int* order, DevState
 // Task -> curve table: one warp per curve writes the index of each of its
 // tasks (fill tasks numbered first, contour tasks after them).
 __global__ void k_task_map(int nc, const CurvePlan* __restrict__ plan, const DevState* __restrict__ st, int* tmap,
-                           long long tcap) {
+                           long long tcap, int ftile) {
   const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (c >= nc) return;
   const CurvePlan pl = plan[c];
   if (pl.kind == kNone) return;
-  const int ntask = pl.kind == kFill ? fill_task_count(pl.nx, pl.ny) : (pl.count + kChunk - 1) / kChunk;
+  const int ntask = pl.kind == kFill ? fill_task_count(pl.nx, pl.ny, ftile) : (pl.count + kChunk - 1) / kChunk;
   const long long base = pl.kind == kFill ? pl.chunk_off : (long long)st->n_chunks + pl.chunk_off;
   for (int j = lane; j < ntask; j += 32) {
     const long long t = base + j;
@@ -791,7 +791,6 @@ __global__ void __launch_bounds__(256, 5) k_emit(ns_curves cv, ns_sample_params 
 //     point, and every point of a tile whose lists overflow, searches all
 //     clusters with box lower bounds.
 // All coordinates are grid-local (origin 0): the polyline's high parts.
-constexpr int kNearCap = 256;   // band segments listed per tile
 constexpr int kRowX = 12;       // crossing segments listed per tile row
 
 // Squared distance from q to segment {b0, e} (1/|e|^2 given), as in Eq. S1.
@@ -849,7 +848,8 @@ __device__ void polyline_scan(const float4* __restrict__ bl, const float4* __res
   }
 }
 
-__global__ void __launch_bounds__(256, 8) k_fill_sdf(ns_curves cv, ns_sample_params sp,
+template <int TE>
+__global__ void __launch_bounds__(TE * TE, 2048 / (TE * TE)) k_fill_sdf(ns_curves cv, ns_sample_params sp,
                                                      const CurvePlan* __restrict__ plan, const int* __restrict__ order,
                                                      const float4* __restrict__ bloc, const float2* __restrict__ glo,
                                                      const float4* __restrict__ cbox, const DevState* __restrict__ st,
@@ -858,19 +858,22 @@ __global__ void __launch_bounds__(256, 8) k_fill_sdf(ns_curves cv, ns_sample_par
   // The lists and keys alternate between two buffers from task to task: the
   // points of one task clear the other buffer, so a task takes three block
   // barriers (after the lists, after the band, after the points).
-  __shared__ unsigned long long s_key[2][kChunk];
+  // band segments listed per tile (a tile's band list beyond it falls back to
+  // the search over the whole polyline): sized so that 2048 threads per SM fit
+  constexpr int kNearCap = TE == 8 ? 64 : 256;
+  __shared__ unsigned long long s_key[2][TE * TE];
   __shared__ float4 s_nseg[2][kNearCap];        // band segments {b0, e}
   __shared__ float2 s_ninfo[2][kNearCap];       // {index bits, 1/|e|^2}
   __shared__ float s_ny1[2][kNearCap];          // and their end heights
-  __shared__ float4 s_xs[2][kFillTile][kRowX];  // crossing segments per tile row {b0, e}
-  __shared__ float s_xy1[2][kFillTile][kRowX];  // and their end heights
-  __shared__ int s_xcnt[2][kFillTile];
+  __shared__ float4 s_xs[2][TE][kRowX];  // crossing segments per tile row {b0, e}
+  __shared__ float s_xy1[2][TE][kRowX];  // and their end heights
+  __shared__ int s_xcnt[2][TE];
   __shared__ int s_nnear[2];
   const int n_fill = st->n_chunks;
   const int nc = cv.n_curves;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   s_key[0][tid] = ~0ull;
-  if (tid < kFillTile) s_xcnt[0][tid] = 0;
+  if (tid < TE) s_xcnt[0][tid] = 0;
   if (tid == 0) s_nnear[0] = 0;
   __syncthreads();
   int buf = 0;
@@ -882,15 +885,15 @@ __global__ void __launch_bounds__(256, 8) k_fill_sdf(ns_curves cv, ns_sample_par
     if (pl.kind != kFill || (long long)pl.b_off + pl.M > bcap) continue;
     const int k = task - pl.chunk_off;
     int ix, iy;
-    const bool in_grid = fill_task_point(k, pl.nx, pl.ny, tid, ix, iy);
+    const bool in_grid = fill_task_point(k, pl.nx, pl.ny, tid, TE, ix, iy);
     const long long g = (long long)pl.g_off + (long long)iy * pl.nx + ix;
     const bool valid = in_grid && g < gcap;
-    const int tix0 = ix - (tid % kFillTile), tiy0 = iy - (tid / kFillTile);   // the tile's first column and row
+    const int tix0 = ix - (tid % TE), tiy0 = iy - (tid / TE);   // the tile's first column and row
     const float h = sp.h;
     const float qx = (float(ix) + 0.5f) * h, qy = (float(iy) + 0.5f) * h;
     // the tile's point box
-    const float tx0 = (float(tix0) + 0.5f) * h, tx1 = (float(min(pl.nx, tix0 + kFillTile)) - 0.5f) * h;
-    const float ty0 = (float(tiy0) + 0.5f) * h, ty1 = (float(min(pl.ny, tiy0 + kFillTile)) - 0.5f) * h;
+    const float tx0 = (float(tix0) + 0.5f) * h, tx1 = (float(min(pl.nx, tix0 + TE)) - 0.5f) * h;
+    const float ty0 = (float(tiy0) + 0.5f) * h, ty1 = (float(min(pl.ny, tiy0 + TE)) - 0.5f) * h;
     const float o = cv.color[4 * c + 3];
     // sigmoid(z) rounds to exactly 1 in FP32 once exp(-z) <= 2^-24 (z >= 16.64);
     // deep2 is the squared distance beyond which z >= 17 with margin: the band
@@ -937,7 +940,7 @@ __global__ void __launch_bounds__(256, 8) k_fill_sdf(ns_curves cv, ns_sample_par
       if (ncl_cross && xhi >= tx0 - 0.01f) {
         // rows r of the tile with ylo <= qy_r < yhi (the straddle rule of the crossing test)
         const int r0 = max(0, int(ceilf(ylo / h - 0.5f)) - tiy0 - 1);
-        const int r1 = min(kFillTile - 1, int(ceilf(yhi / h - 0.5f)) - tiy0);
+        const int r1 = min(TE - 1, int(ceilf(yhi / h - 0.5f)) - tiy0);
         for (int r = r0; r <= r1; ++r) {
           const float qyr = (float(tiy0 + r) + 0.5f) * h;
           if (ylo <= qyr && qyr < yhi) {
@@ -964,8 +967,8 @@ __global__ void __launch_bounds__(256, 8) k_fill_sdf(ns_curves cv, ns_sample_par
         const float y1 = s_ny1[buf][i];
         const float xlo = fminf(sg.x, sg.x + sg.z) - band, xhi = fmaxf(sg.x, sg.x + sg.z) + band;
         const float ylo = fminf(sg.y, y1) - band, yhi = fmaxf(sg.y, y1) + band;
-        const int ia = max(tix0, int(ceilf(xlo / h - 0.5f))), ib = min(tix0 + kFillTile - 1, int(floorf(xhi / h - 0.5f)));
-        const int ja = max(tiy0, int(ceilf(ylo / h - 0.5f))), jb = min(tiy0 + kFillTile - 1, int(floorf(yhi / h - 0.5f)));
+        const int ia = max(tix0, int(ceilf(xlo / h - 0.5f))), ib = min(tix0 + TE - 1, int(floorf(xhi / h - 0.5f)));
+        const int ja = max(tiy0, int(ceilf(ylo / h - 0.5f))), jb = min(tiy0 + TE - 1, int(floorf(yhi / h - 0.5f)));
         if (ia > ib || ja > jb) continue;
         const int w = ib - ia + 1, npts = w * (jb - ja + 1);
         const float inv_w = 1.f / float(w);
@@ -974,7 +977,7 @@ __global__ void __launch_bounds__(256, 8) k_fill_sdf(ns_curves cv, ns_sample_par
           const int jx = ia + (p - py * w), jy = ja + py;
           const float d2 = seg_d2((float(jx) + 0.5f) * h, (float(jy) + 0.5f) * h, sg, info.y);
           if (d2 <= deep2)
-            atomicMin(&key[(jy - tiy0) * kFillTile + (jx - tix0)],
+            atomicMin(&key[(jy - tiy0) * TE + (jx - tix0)],
                       ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned int)kseg);
         }
       }
@@ -1030,7 +1033,7 @@ __global__ void __launch_bounds__(256, 8) k_fill_sdf(ns_curves cv, ns_sample_par
     }
     // clear the other buffer for the next task
     s_key[buf ^ 1][tid] = ~0ull;
-    if (tid < kFillTile) s_xcnt[buf ^ 1][tid] = 0;
+    if (tid < TE) s_xcnt[buf ^ 1][tid] = 0;
     if (tid == 0) s_nnear[buf ^ 1] = 0;
     __syncthreads();
     buf ^= 1;
@@ -1055,7 +1058,8 @@ extern "C" ns_status nurbs_sample(const ns_curves* curves, const ns_sample_param
     return NS_ERR_INVALID_ARG;
   }
   if (!(sp->h > 0.f) || !(sp->rho > 0.f) || !(sp->delta_c > 0.f) || !(sp->delta_b > 0.f) || sp->kappa < 0 ||
-      sp->nl_mult < 1 || !(sp->eta > 0.f) || !(sp->pad_frac >= 0.f) || sp->fill_rule < 0 || sp->fill_rule > 1) {
+      sp->nl_mult < 1 || !(sp->eta > 0.f) || !(sp->pad_frac >= 0.f) || sp->fill_rule < 0 || sp->fill_rule > 1 ||
+      (sp->fill_tile != 0 && sp->fill_tile != 8 && sp->fill_tile != 16)) {
     set_error("nurbs_sample: invalid sample parameters");
     return NS_ERR_INVALID_ARG;
   }
@@ -1098,19 +1102,28 @@ extern "C" ns_status nurbs_sample(const ns_curves* curves, const ns_sample_param
   if (cap->boundary > 0)
     NS_LAUNCH(NS_KERNEL_OTHER, k_cluster_boxes, int((cap->boundary + 255) / 256), 256, 0, s, plan,
               at<const int>(ws, L.o_bcurve), bloc, st, cbox, cap->boundary, nc);
-  NS_LAUNCH(NS_KERNEL_SCAN, k_scan_gauss, 1, 1024, 0, s, nc, plan, order, st, cap->gaussians, out->count);
+  const int ftile = fill_tile_of(sp->fill_tile);
+  NS_LAUNCH(NS_KERNEL_SCAN, k_scan_gauss, 1, 1024, 0, s, nc, plan, order, st, cap->gaussians, out->count, ftile);
   int* tmap = at<int>(ws, L.o_tasks);
-  NS_LAUNCH(NS_KERNEL_SCAN, k_task_map, (nc + 7) / 8, 256, 0, s, nc, plan, st, tmap, (long long)L.tcap);
+  NS_LAUNCH(NS_KERNEL_SCAN, k_task_map, (nc + 7) / 8, 256, 0, s, nc, plan, st, tmap, (long long)L.tcap, ftile);
   const int grid = num_sms() * 8;
-  static bool carveout = false;   // eight resident blocks need most of the SM's shared memory
+  // full occupancy (2048 threads per SM) needs most of the SM's shared memory
+  static bool carveout = false;
   if (!carveout) {
-    cudaFuncSetAttribute(k_fill_sdf, cudaFuncAttributePreferredSharedMemoryCarveout,
+    cudaFuncSetAttribute(k_fill_sdf<8>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         int(cudaSharedmemCarveoutMaxShared));
+    cudaFuncSetAttribute(k_fill_sdf<16>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          int(cudaSharedmemCarveoutMaxShared));
     carveout = true;
   }
-  NS_LAUNCH(NS_KERNEL_FILL_SDF, k_fill_sdf, num_sms() * 16, 256, 0, s, *curves, *sp, plan, order, bloc, at<const float2>(ws, L.o_glo),
-            cbox, st, reinterpret_cast<float4*>(out->rec), out->curve, out->aux, cap->gaussians, cap->boundary, tmap,
-            (long long)L.tcap);
+  if (ftile == 8)
+    NS_LAUNCH(NS_KERNEL_FILL_SDF, k_fill_sdf<8>, num_sms() * 64, 64, 0, s, *curves, *sp, plan, order, bloc,
+              at<const float2>(ws, L.o_glo), cbox, st, reinterpret_cast<float4*>(out->rec), out->curve, out->aux,
+              cap->gaussians, cap->boundary, tmap, (long long)L.tcap);
+  else
+    NS_LAUNCH(NS_KERNEL_FILL_SDF, k_fill_sdf<16>, num_sms() * 16, 256, 0, s, *curves, *sp, plan, order, bloc,
+              at<const float2>(ws, L.o_glo), cbox, st, reinterpret_cast<float4*>(out->rec), out->curve, out->aux,
+              cap->gaussians, cap->boundary, tmap, (long long)L.tcap);
   NS_LAUNCH(NS_KERNEL_EMIT, k_emit, grid, 256, 0, s, *curves, *sp, plan, order, knots, st,
             reinterpret_cast<float4*>(out->rec), out->curve, out->aux, cap->gaussians, tmap, (long long)L.tcap);
   if (out->shape)

@@ -31,6 +31,7 @@ def sample_params(d: dict) -> B.NsSampleParams:
     p.fill_rule = int(d["fill_rule"])
     p.fill_cull = float(d.get("fill_cull", 0.0))
     p.contour_mode = int(d.get("contour_mode", 0))
+    p.fill_tile = int(d.get("fill_tile", 0))
     return p
 
 

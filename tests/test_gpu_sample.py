@@ -135,3 +135,35 @@ def test_fill_nearest_segment_and_sign(seed, h):
         assert float((d_sel - d_min).abs().max()) <= tol
         clear = d_min.numpy() > tol
         assert np.array_equal(ins[clear], (wn > 0.5)[clear])
+
+
+@pytest.mark.parametrize("production", [False, True])
+def test_fill_tile_changes_no_record(production):
+    """The fill tile (Gaussians per sampling block, 8 x 8 or 16 x 16) is a work
+    decomposition only: every grid point takes the same minimum over the same
+    segment distances and the same crossing tests, so the records, nearest
+    segments and signs are identical bit for bit, and so are the gradients."""
+    sc = scenes.small_closed(46, n_curves=4, size=72, filled="alternate", h=1.0, n_scenes=2)
+    if production:
+        sc = sc.with_raster(**scenes.RASTER_DEFAULTS)
+    out = {}
+    for ft in (16, 8):
+        s2 = sc.with_sample(fill_tile=ft)
+        sp, img, rep, (k, t, c), G = run_scene(s2)
+        assert rep.status == 0
+        dimg = torch.as_tensor(np.random.default_rng(47).standard_normal(tuple(img.shape)).astype(np.float32),
+                               device="cuda")
+        dk, dt, dc = sp.backward(k, t, c, dimg)
+        torch.cuda.synchronize()
+        out[ft] = (sp.rec[:G].cpu().numpy(), sp.aux[:G].cpu().numpy(), img.cpu().numpy(), dk.cpu().numpy(),
+                   dt.cpu().numpy(), dc.cpu().numpy())
+    for a, b in zip(out[16][:3], out[8][:3]):
+        np.testing.assert_array_equal(a, b)
+    for a, b in zip(out[16][3:], out[8][3:]):   # float additions in another order
+        assert np.abs(a - b).max() <= 1e-5 * max(np.abs(a).max(), 1e-30)
+
+
+def test_fill_tile_is_checked():
+    sc = scenes.small_closed(48, n_curves=2, size=40, filled=True, h=2.0).with_sample(fill_tile=12)
+    with pytest.raises(Exception):
+        run_scene(sc)

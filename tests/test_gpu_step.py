@@ -28,6 +28,9 @@ CASES = [
     ("filled-deep-h1", lambda: scenes.small_closed(315, n_curves=2, size=56, filled=True, h=1.0)),
     ("filled-h1-batched", lambda: scenes.small_closed(55, n_curves=2, size=40, filled=True, h=1.0, n_scenes=2)),
     ("config1", lambda: scenes.config1().with_raster(**scenes.RASTER_PARITY)),
+    # 64 fill Gaussians per sampling block instead of 256
+    ("filled-h1-fill-tile-8", lambda: scenes.small_closed(55, n_curves=2, size=40, filled=True, h=1.0, n_scenes=2)
+     .with_sample(fill_tile=8)),
 ]
 
 
