@@ -38,16 +38,24 @@ PEAKS_FALLBACK = dict(hbm_gbs=6400.0, sm_max_mhz=2032.0)
 # with fill layers, with the units that launch processed and the hash of the
 # kernel source it ran.  The bench scales the bytes to its own launch by the
 # units processed, and reports null if the source, the tile or the binning has
-# changed since the capture.
+# changed since the capture.  The fill SDF is left out: at 512 paths the
+# records it writes stay in L2, at 2048 they do not, so its traffic does not
+# grow in proportion.
 TRAFFIC = dict(
-    blend_bwd=dict(bytes=86937856, units=2027197, unit="gaussians", tile=8, layers=1,
-                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="01705d0bf105706e"),
-    blend_fwd=dict(bytes=28032000, units=2027197, unit="gaussians", tile=8, layers=1,
-                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="01705d0bf105706e"),
-    chain=dict(bytes=88732672, units=2027197, unit="gaussians", tile=None, layers=None,
-               src="paper_2606_31764_b300/csrc/ns_backward.cu", sha="9153ecc170fdaa06"),
-    emit=dict(bytes=2934528, units=2027197, unit="gaussians", tile=None, layers=None,
-              src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="cf009dde58f5c3d2"),
+    blend_bwd=dict(bytes=86780416, units=2027197, unit="gaussians", tile=8, layers=1,
+                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="219d18604a2c9810"),
+    blend_fwd=dict(bytes=29323776, units=2027197, unit="gaussians", tile=8, layers=1,
+                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="219d18604a2c9810"),
+    chain=dict(bytes=43591424, units=2027197, unit="gaussians", tile=None, layers=None,
+               src="paper_2606_31764_b300/csrc/ns_backward.cu", sha="3d0a96c1d14d779a"),
+    bin_count=dict(bytes=40628992, units=2027197, unit="gaussians", tile=8, layers=1,
+                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="219d18604a2c9810"),
+    bin_emit=dict(bytes=3822336, units=2027197, unit="gaussians", tile=8, layers=1,
+                  src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="219d18604a2c9810"),
+    plan=dict(bytes=477440, units=512, unit="curves", tile=None, layers=None,
+              src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="f92e9b313b6601c2"),
+    boundary=dict(bytes=1273344, units=512, unit="curves", tile=None, layers=None,
+                  src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="f92e9b313b6601c2"),
 )
 
 
@@ -97,6 +105,10 @@ def parse():
     ap.add_argument("--headline-only", action="store_true",
                     help="profiling runs: only the headline step (no e2e, regulariser or schedule measurements)")
     ap.add_argument("--ref-sample-curves", type=int, default=8)
+    ap.add_argument("--ppt", default="",
+                    help="profiling runs: fixed blend decompositions 'fwd,bwd' instead of timing them")
+    ap.add_argument("--fill-tiles", default="16,8",
+                    help="fill tile edges (Gaussians per sampling block: their squares) the autotuner tries")
     return ap.parse_args()
 
 
@@ -231,7 +243,8 @@ class Step:
         return int(self.sp.count.item())
 
 
-def autotune(torch, scene, tiles, capacity, steps=3, adam=False, geometry=None, layers=(0, 1), fill_tiles=(16, 8)):
+def autotune(torch, scene, tiles, capacity, steps=3, adam=False, geometry=None, layers=(0, 1), fill_tiles=(16, 8),
+             ppt=None):
     """Tile size and binning (per Gaussian, or fill layers) by timing whole
     steps; the blend decomposition by the library's ns_autotune_blend on each
     candidate's workspace."""
@@ -240,7 +253,10 @@ def autotune(torch, scene, tiles, capacity, steps=3, adam=False, geometry=None, 
         st = Step(scene, capacity, raster=dict(scene.raster, tile=tile, fill_layers=fl), adam=adam,
                   geometry=geometry)
         st()
-        st.sp.autotune_blend(st.key, st.tau, st.color, st.dimage, repeats=3)
+        if ppt:
+            st.sp.rp.ppt_fwd, st.sp.rp.ppt_bwd = ppt
+        else:
+            st.sp.autotune_blend(st.key, st.tau, st.color, st.dimage, repeats=3)
         st()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -272,6 +288,9 @@ def autotune(torch, scene, tiles, capacity, steps=3, adam=False, geometry=None, 
     for ft in fill_tiles:
         st = best if ft == 16 else Step(scene.with_sample(fill_tile=ft), capacity, raster=raster, adam=adam,
                                          geometry=geometry)
+        if len(fill_tiles) == 1:   # nothing to choose
+            best, best_ft = st, ft
+            break
         st()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -283,10 +302,8 @@ def autotune(torch, scene, tiles, capacity, steps=3, adam=False, geometry=None, 
         ms = e0.elapsed_time(e1) / steps
         ft_table[str(ft * ft)] = round(ms, 4)
         if best_ft_ms is None or ms < best_ft_ms:
-            if st is not best:
-                best = st
-            best_ft, best_ft_ms = ft, ms
-        elif st is not best:
+            best, best_ft, best_ft_ms = st, ft, ms
+        else:
             del st
         torch.cuda.empty_cache()
     chosen["fill_gaussians_per_block"] = best_ft * best_ft
@@ -335,7 +352,9 @@ def run_gpu(args, dist, rank, world):
     sc = scenes.config5(seed=1005 + rank, n_paths=args.paths)
     step, tuning = autotune(torch, sc, [int(x) for x in args.tiles.split(",")],
                             capacity=(10_000_000, 40_000_000, 400_000),
-                            layers=tuple(int(x) for x in args.fill_layers.split(",")))
+                            layers=tuple(int(x) for x in args.fill_layers.split(",")),
+                            fill_tiles=tuple(int(x) for x in args.fill_tiles.split(",")),
+                            ppt=tuple(int(x) for x in args.ppt.split(",")) if args.ppt else None)
     step()
     torch.cuda.synchronize()
     rep = step.sp.report()
@@ -446,7 +465,7 @@ def run_gpu(args, dist, rank, world):
             # the FLOPs the kernel itself executed (its culling skips most pairs)
             d["performed_frac"] = round(performed[k] / (ms / 1e3) / fp32_peak, 4)
         kernels[k] = d
-    units_now = dict(pairs=int(rep.pairs), gaussians=G)
+    units_now = dict(pairs=int(rep.pairs), gaussians=G, curves=sc.n_curves)
     tile_now = int(step.sp.rp.tile)
     for k in kernels:
         kernels[k]["traffic"] = traffic_per_launch(k, units_now, tile_now, layers)
