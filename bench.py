@@ -44,7 +44,7 @@ PEAKS_FALLBACK = dict(hbm_gbs=6400.0, sm_max_mhz=2032.0)
 TRAFFIC = dict(
     blend_bwd=dict(bytes=86780416, units=2027197, unit="gaussians", tile=8, layers=1,
                    src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="219d18604a2c9810"),
-    blend_fwd=dict(bytes=29323776, units=2027197, unit="gaussians", tile=8, layers=1,
+    blend_fwd=dict(bytes=28441344, units=2027197, unit="gaussians", tile=8, layers=1,
                    src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="219d18604a2c9810"),
     chain=dict(bytes=43591424, units=2027197, unit="gaussians", tile=None, layers=None,
                src="paper_2606_31764_b300/csrc/ns_backward.cu", sha="3d0a96c1d14d779a"),
@@ -432,7 +432,7 @@ def run_gpu(args, dist, rank, world):
     visits_bwd = pg.get("visits_bwd", 0) if layers else rep.blend_bwd_visits
     visit_src = ("per-Gaussian trial at this tile size" if layers else "this step's counters")
     work = dict(
-        fill_sdf=("alu", costs["segment_tests"] * FLOP_SEGMENT / 1e12, "TFLOP/s", fp32_peak),
+        fill_sdf=("hbm", costs["fill_gaussians"] * 24 / 1e9, "GB/s", peaks["hbm_gbs"]),
         blend_fwd=("alu", visits_fwd * FLOP_VISIT_FWD / 1e12 if visits_fwd else performed["blend_fwd"],
                    "TFLOP/s", fp32_peak),
         blend_bwd=("alu", visits_bwd * FLOP_VISIT_BWD / 1e12 if visits_bwd else performed["blend_bwd"],
@@ -442,8 +442,9 @@ def run_gpu(args, dist, rank, world):
         bin_emit=("hbm", ((G * 4 if layers else G * 20) + rep.pairs * 8) / 1e9, "GB/s", peaks["hbm_gbs"]),
     )
     work_text = dict(
-        fill_sdf=f"algorithmic: {FLOP_SEGMENT} FP32 FLOP per (grid point, boundary segment) test of the plain "
-                 "definition (Eq. S1-S2), Q x B per curve",
+        fill_sdf="the fill records written, 24 B per grid point (record, curve, aux); the band performs about "
+                 "3 distance tests per grid point where the plain definition (Eq. S1-S2) takes Q x B "
+                 f"({costs['segment_tests']} per step, see sample.segment_tests)",
         blend_fwd=(f"algorithmic: {visits_fwd} visited (pixel, list entry) pairs of Eq. 8-9 ({visit_src}) x "
                    f"{FLOP_VISIT_FWD} FP32 FLOP" if visits_fwd else
                    "performed: 10 FP32 FLOP per alpha evaluation + 10 per composited pair (fill layers)"),
