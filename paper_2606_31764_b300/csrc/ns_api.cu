@@ -133,6 +133,7 @@ bool make_layout(const ns_curves* c, const ns_capacity* cap, const ns_raster_par
   L->o_glo = take(sizeof(float2) * (size_t)L->nc);
   L->o_knots_lo = take(sizeof(float) * nkn);
   L->o_krcp = take(sizeof(float2) * kMaxP * nkn);
+  L->o_lbox = take(sizeof(int4) * (size_t)L->nc);
   // contour tasks cover a curve's samples in chunks of kChunk, fill tasks its
   // grid in T x T tiles, T = 8 or 16 (at most (nx ny + (T - 1)(nx + ny) +
   // (T - 1)^2) / T^2 of them): within the Gaussian capacity this table holds
@@ -153,6 +154,8 @@ bool make_layout(const ns_curves* c, const ns_capacity* cap, const ns_raster_par
   // fill layers: per curve, the grid run of each tile column and row
   L->o_lruns = take(sizeof(int2) * (size_t)L->nc * (size_t)(L->tiles_x + L->tiles_y));
   L->o_lconst = take(sizeof(float4) * 3 * (size_t)L->nc);   // per layer {X0, Y0, xoff, yoff}, {sigma, ncoef, nx, ny}, {h, 1/h, R, 0}
+  L->o_bflag = take(sizeof(int) * (size_t)(L->bin_blocks + 1));
+  L->o_lcount = take(sizeof(int) * (size_t)L->nc);
   L->o_lmin = take(sizeof(int2) * (size_t)L->nc);   // per layer: smallest live grid column and row
   L->o_lmax = take(sizeof(int2) * (size_t)L->nc);   // largest
   L->o_dgauss = take(sizeof(float) * 12 * (size_t)L->gcap);   // 8 per Gaussian, 12 when tangent-aligned
@@ -175,6 +178,8 @@ __global__ void k_reset_state(DevState* st) {
   st->g_count = st->pair_count = st->b_count = 0;
   st->blend_evals = st->blend_bwd_evals = st->blend_contribs = 0;
   st->blend_visits = st->blend_bwd_visits = 0;
+  st->cull_thr = -1.f;
+  st->culled_s = 0;
 }
 
 void launch_reset_state(DevState* st, cudaStream_t s) { NS_LAUNCH(NS_KERNEL_OTHER, k_reset_state, 1, 1, 0, s, st); }

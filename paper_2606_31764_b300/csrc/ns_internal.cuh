@@ -48,6 +48,12 @@ struct DevState {
   unsigned long long blend_contribs;   // composited (pixel, Gaussian) pairs of the last forward blend
   unsigned long long blend_visits;     // (pixel, list entry) pairs walked by the last forward blend
   unsigned long long blend_bwd_visits; // the same for the last backward blend
+  // what nurbs_sample knows of its fill Gaussians for a given alpha_min (its
+  // fill_cull): the culled count, and (in the workspace) each curve's box of
+  // live grid points; the binning uses them when its alpha_min is the same
+  float cull_thr;                      // the threshold they were counted for (-1: none)
+  int pad2;
+  unsigned long long culled_s;         // fill Gaussians with opacity below cull_thr (sigma > 0)
 };
 
 // One curve's sampling plan (written by the planning kernels).
@@ -83,6 +89,9 @@ struct Layout {
   size_t o_bloc = 0;         // boundary points relative to their curve's fill grid origin, {x_hi, y_hi, x_lo, y_lo}
   size_t o_glo = 0;          // per curve: the low parts {x0_lo, y0_lo} of the fill grid origin (plan x0, y0 = high parts)
   size_t o_knots_lo = 0;     // low parts of the knot vectors (knots = their high parts, the exact sums rounded)
+  size_t o_lbox = 0;         // per curve: {min column, min row, max column, max row} of live fill grid points (nurbs_sample)
+  size_t o_bflag = 0;        // per binning block: 1 if it holds a Gaussian that is not a fill layer's (splat_forward)
+  size_t o_lcount = 0;       // per curve: tile pairs of its fill layer (splat_forward)
   size_t o_krcp = 0;         // per knot slot k and width j = 1..kMaxP: 1 / (U[k + j] - U[k]) as {hi, lo} (filled curves)
   int64_t tcap = 0;          // entries of that table
 };

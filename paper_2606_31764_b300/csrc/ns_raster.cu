@@ -64,7 +64,19 @@ struct BinParams {
   int fill_layers;      // one pair per (tile, filled curve) instead of per (tile, Gaussian)
   int2* lmin;           // fill layers: per curve the smallest / largest grid column and row of a
   int2* lmax;           // live Gaussian (one the per-Gaussian rule would bin); empty: lmax < lmin
+  // fill layers with nurbs_sample's live boxes (when its threshold is alpha_min): the boxes,
+  // per binning block whether it holds a Gaussian outside the fill layers, per curve its
+  // layer's pair count
+  const int4* lbox;
+  int* bflag;
+  int* lcount;
 };
+
+// Whether the binning may take nurbs_sample's live boxes and culled count:
+// fill layers, and the sampling counted for this alpha_min.
+__device__ __forceinline__ bool sampled_boxes(const BinParams& bp, const DevState* st) {
+  return bp.fill_layers && st->cull_thr == bp.alpha_min;
+}
 
 // Pair values of fill layers carry this bit on the index of the layer's first Gaussian.
 constexpr uint32_t kLayerBit = 0x80000000u;
@@ -219,19 +231,60 @@ __global__ void __launch_bounds__(256) k_bin_count(const float4* __restrict__ re
                                                    const int* __restrict__ gcurve,
                                                    const int* __restrict__ cflags, const int* __restrict__ gcount,
                                                    BinParams bp, int* bsum, DevState* st, float4* prep,
-                                                   float2* prep2, float2* reach, const CurvePlan* __restrict__ plan) {
+                                                   float2* prep2, float2* reach, const CurvePlan* __restrict__ plan,
+                                                   const int* __restrict__ order,
+                                                   const int* __restrict__ scene_off) {
   __shared__ int s_warp[32];
+  __shared__ int s_pure;
   const int G = min(*gcount, bp.gcap);
   const long long base = (long long)blockIdx.x * kBinItems;
   if (base >= G) return;
-  int cnt = 0, culled = 0;
+  // with nurbs_sample's live boxes and culled count a fill Gaussian needs
+  // nothing here (its layer is counted per curve): only its curve is read
+  const bool fast = sampled_boxes(bp, st);
+  if (fast && blockIdx.x == 0 && threadIdx.x == 0 && st->culled_s) atomicAdd(&st->culled, st->culled_s);
+  if (fast) {
+    // a block whose first and last Gaussians belong to filled curves, and all
+    // curves between them in front-to-back order too, holds fill Gaussians only
+    if (threadIdx.x == 0) {
+      int pure = 0;
+      const int c0 = gcurve[base], c1 = gcurve[min((long long)G, base + kBinItems) - 1];
+      if (c0 >= 0 && c0 < bp.n_curves && c1 >= 0 && c1 < bp.n_curves) {
+        auto pos = [&](int c) {
+          const int sc = plan[c].scene;
+          const int s0 = scene_off ? scene_off[sc] : 0, s1 = scene_off ? scene_off[sc + 1] : bp.n_curves;
+          return s0 + (s1 - 1 - c);
+        };
+        const int p0 = pos(c0), p1 = pos(c1);
+        pure = p0 <= p1;
+        for (int q = p0; pure && q <= p1 && q < p0 + 64; ++q) pure = (cflags[order[q]] & NS_FILLED) != 0;
+        if (p1 >= p0 + 64) pure = 0;
+      }
+      s_pure = pure;
+    }
+    __syncthreads();
+    if (s_pure) {
+      if (threadIdx.x == 0) {
+        bsum[blockIdx.x] = 0;
+        bp.bflag[blockIdx.x] = 0;
+      }
+      return;
+    }
+  }
+  int cnt = 0, culled = 0, other = 0;
   // the block total is all that is kept, so consecutive threads take
   // consecutive Gaussians (coalesced loads and stores)
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     const long long g = base + k * 256 + threadIdx.x;
     int live_key = -1, live_ix = 0, live_iy = 0;   // fill layers: live grid point of curve live_key
-    if (g < G) {
+    bool skip = false;
+    if (g < G && fast) {
+      const int cv = gcurve[g];
+      skip = cv >= 0 && cv < bp.n_curves && (cflags[cv] & NS_FILLED);
+    }
+    if (g < G && !skip) {
+      other = 1;
       const float4 r = rec[g];
       int x0, y0, nx;
       const int cv = gcurve[g];
@@ -269,7 +322,7 @@ __global__ void __launch_bounds__(256) k_bin_count(const float4* __restrict__ re
       }
       culled += (r.z > 0.f && r.w < bp.alpha_min) ? 1 : 0;
     }
-    if (bp.fill_layers) {
+    if (bp.fill_layers && !fast) {   // warp-uniform
       // extremes of the live grid points per curve: lanes of one curve reduce, one lane adds
       const unsigned int peers = __match_any_sync(0xffffffffu, live_key);
       if (live_key >= 0) {
@@ -288,8 +341,10 @@ __global__ void __launch_bounds__(256) k_bin_count(const float4* __restrict__ re
   block_excl_scan_int(cnt, s_warp, total);
   int ctot;
   block_excl_scan_int(culled, s_warp, ctot);
+  const int any_other = __syncthreads_or(other);
   if (threadIdx.x == 0) {
     bsum[blockIdx.x] = total;
+    if (bp.fill_layers) bp.bflag[blockIdx.x] = fast ? any_other : 1;
     if (ctot) atomicAdd(&st->culled, (unsigned long long)ctot);
   }
 }
@@ -298,15 +353,64 @@ __global__ void __launch_bounds__(256) k_bin_count(const float4* __restrict__ re
 // joins the count of the binning block that holds its first Gaussian, where
 // k_bin_emit writes the layer's pairs.
 __global__ void k_layer_count(ns_curves cv, const CurvePlan* __restrict__ plan, const float4* __restrict__ rec,
-                              const int* __restrict__ gcount, BinParams bp, int* bsum) {
+                              const int* __restrict__ gcount, BinParams bp, int* bsum, const DevState* st) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= cv.n_curves || !(cv.flags[c] & NS_FILLED)) return;
+  if (c >= cv.n_curves) return;
+  bp.lcount[c] = 0;
+  if (!(cv.flags[c] & NS_FILLED)) return;
   const CurvePlan p = plan[c];
   const long long G = min((long long)*gcount, (long long)bp.gcap);
   if (p.g_off < 0 || p.g_off >= G || p.count <= 0) return;
+  if (sampled_boxes(bp, st)) {   // the live box nurbs_sample found
+    const int4 b = bp.lbox[c];
+    bp.lmin[c] = make_int2(b.x, b.y);
+    bp.lmax[c] = make_int2(b.z, b.w);
+  }
   int x0, y0, nx;
   const int nt = layer_rect_live(rec, p, G, bp, c, x0, y0, nx);
+  bp.lcount[c] = nt;
   if (nt) atomicAdd(&bsum[p.g_off / kBinItems], nt);
+}
+
+// The pairs of the fill layers whose first Gaussian lies in a binning block of
+// fill Gaussians only (k_bin_emit leaves those blocks out), one thread per
+// curve: after the pairs of the layers that start earlier in the same block
+// (the curves before it in front-to-back order), in the pair order k_bin_emit
+// would give them.
+__global__ void k_layer_emit(ns_curves cv, const CurvePlan* __restrict__ plan, const float4* __restrict__ rec,
+                             const int* __restrict__ gcount, const int* __restrict__ curve_scene, BinParams bp,
+                             const int* __restrict__ boff, const int* __restrict__ order, uint32_t* keys,
+                             uint32_t* vals, long long pcap, const DevState* st) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cv.n_curves || !sampled_boxes(bp, st)) return;
+  const int nt = bp.lcount[c];
+  if (nt <= 0) return;
+  const CurvePlan p = plan[c];
+  const long long G = min((long long)*gcount, (long long)bp.gcap);
+  const int blk = p.g_off / kBinItems;
+  if (bp.bflag[blk]) return;   // a mixed block: k_bin_emit writes this layer's pairs
+  // position in front-to-back order: within its scene the last curve comes first
+  int s0 = 0, s1 = cv.n_curves;
+  if (cv.scene_curve_offset) {
+    s0 = cv.scene_curve_offset[p.scene];
+    s1 = cv.scene_curve_offset[p.scene + 1];
+  }
+  long long off = boff[blk];
+  const long long base = (long long)blk * kBinItems;
+  for (int q = s0 + (s1 - 1 - c) - 1; q >= 0; --q) {
+    const int c2 = order[q];
+    if (plan[c2].g_off < base) break;
+    off += bp.lcount[c2];
+  }
+  int x0, y0, nx;
+  layer_rect_live(rec, p, G, bp, c, x0, y0, nx);
+  const int sbase = curve_scene[c] * bp.tiles_per_scene;
+  const uint32_t val = uint32_t(p.g_off) | kLayerBit;
+  for (int j = 0; j < nt; ++j, ++off) {
+    if (off >= pcap) break;
+    keys[off] = uint32_t(sbase + (y0 + j / nx) * bp.tiles_x + x0 + j % nx);
+    vals[off] = val;
+  }
 }
 
 __global__ void k_scan_small(int* vals, const int* gcount, int gcap, int items_per_block, DevState* st,
@@ -367,6 +471,9 @@ __global__ void __launch_bounds__(256) k_bin_emit(const float4* __restrict__ rec
   // a block whose Gaussians emit no pair (the inside of a fill layer, culled
   // points) has the same offset as the next block
   if (base + kBinItems < G && boff[blockIdx.x + 1] == boff[blockIdx.x]) return;
+  // a block of fill Gaussians only, with nurbs_sample's live boxes: its layers'
+  // pairs come from k_layer_emit
+  if (bp.fill_layers && !bp.bflag[blockIdx.x]) return;
   // 1. rectangles, consecutive threads on consecutive Gaussians (coalesced)
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
@@ -2415,6 +2522,9 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
   bp.fill_layers = use_layers(rp, g) ? 1 : 0;
   bp.lmin = at<int2>(ws, L.o_lmin);
   bp.lmax = at<int2>(ws, L.o_lmax);
+  bp.lbox = at<const int4>(ws, L.o_lbox);
+  bp.bflag = at<int>(ws, L.o_bflag);
+  bp.lcount = at<int>(ws, L.o_lcount);
   const CurvePlan* plan = at<CurvePlan>(ws, L.o_plan);
   if (bp.fill_layers && L.nc > 0) {
     cudaMemsetAsync(bp.lmin, 0x7f, sizeof(int2) * (size_t)L.nc, s);   // 0x7f7f7f7f: above every index
@@ -2426,11 +2536,16 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
   if (bin_blocks > 0) {
     auto kc = aniso ? &k_bin_count<true> : &k_bin_count<false>;
     NS_LAUNCH(NS_KERNEL_BIN_COUNT, kc, bin_blocks, 256, 0, s, rec, shape, g->curve, curves->flags, g->count, bp, bsum, st,
-              at<float4>(ws, L.o_prep), at<float2>(ws, L.o_prep2), at<float2>(ws, L.o_reach), plan);
+              at<float4>(ws, L.o_prep), at<float2>(ws, L.o_prep2), at<float2>(ws, L.o_reach), plan,
+              at<const int>(ws, L.o_order), curves->scene_curve_offset);
   }
   if (bp.fill_layers && L.nc > 0 && bin_blocks > 0)
-    NS_LAUNCH(NS_KERNEL_OTHER, k_layer_count, (L.nc + 127) / 128, 128, 0, s, *curves, plan, rec, g->count, bp, bsum);
+    NS_LAUNCH(NS_KERNEL_OTHER, k_layer_count, (L.nc + 127) / 128, 128, 0, s, *curves, plan, rec, g->count, bp, bsum,
+              st);
   NS_LAUNCH(NS_KERNEL_SCAN, k_scan_small, 1, 1024, 0, s, bsum, g->count, int(L.gcap), kBinItems, st, cap->pairs);
+  if (bp.fill_layers && L.nc > 0 && bin_blocks > 0)
+    NS_LAUNCH(NS_KERNEL_OTHER, k_layer_emit, (L.nc + 127) / 128, 128, 0, s, *curves, plan, rec, g->count,
+              curve_scene, bp, bsum, at<const int>(ws, L.o_order), k0, v0, cap->pairs, st);
   if (bin_blocks > 0) {
     auto ke = aniso ? &k_bin_emit<true> : &k_bin_emit<false>;
     NS_LAUNCH(NS_KERNEL_BIN_EMIT, ke, bin_blocks, 256, 0, s, rec, shape, g->curve, g->count, curve_scene, bp, bsum,

@@ -505,9 +505,11 @@ __global__ void __launch_bounds__(256) k_boundary(ns_curves cv, const CurvePlan*
 // the fill-layer blend work with.
 __global__ void __launch_bounds__(256) k_boundary_box(ns_curves cv, ns_sample_params sp, CurvePlan* plan,
                                                       const float* __restrict__ knots, float4* bloc, float2* glo,
-                                                      long long bcap) {
+                                                      long long bcap, int4* lbox, DevState* st) {
   const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
+  if (c == 0 && lane == 0) st->cull_thr = sp.fill_cull;   // the threshold k_fill_sdf counts for
+  if (c < cv.n_curves && lane == 0) lbox[c] = make_int4(0x7fffffff, 0x7fffffff, -1, -1);
   if (c >= cv.n_curves) return;
   const CurvePlan pl = plan[c];
   if (pl.kind != kFill) return;
@@ -852,9 +854,10 @@ template <int TE>
 __global__ void __launch_bounds__(TE * TE, 2048 / (TE * TE)) k_fill_sdf(ns_curves cv, ns_sample_params sp,
                                                      const CurvePlan* __restrict__ plan, const int* __restrict__ order,
                                                      const float4* __restrict__ bloc, const float2* __restrict__ glo,
-                                                     const float4* __restrict__ cbox, const DevState* __restrict__ st,
+                                                     const float4* __restrict__ cbox, DevState* st,
                                                      float4* rec, int* gcurve, int* gaux, long long gcap,
-                                                     long long bcap, const int* __restrict__ tmap, long long tcap) {
+                                                     long long bcap, const int* __restrict__ tmap, long long tcap,
+                                                     int4* lbox) {
   // The lists and keys alternate between two buffers from task to task: the
   // points of one task clear the other buffer, so a task takes three block
   // barriers (after the lists, after the band, after the points).
@@ -869,12 +872,14 @@ __global__ void __launch_bounds__(TE * TE, 2048 / (TE * TE)) k_fill_sdf(ns_curve
   __shared__ float s_xy1[2][TE][kRowX];  // and their end heights
   __shared__ int s_xcnt[2][TE];
   __shared__ int s_nnear[2];
+  __shared__ int s_box[2][5];   // the tile's live box {min x, min y, max x, max y} and culled count
   const int n_fill = st->n_chunks;
   const int nc = cv.n_curves;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   s_key[0][tid] = ~0ull;
   if (tid < TE) s_xcnt[0][tid] = 0;
   if (tid == 0) s_nnear[0] = 0;
+  if (tid < 5) s_box[0][tid] = tid < 2 ? 0x7fffffff : (tid < 4 ? -1 : 0);
   __syncthreads();
   int buf = 0;
   for (int task = blockIdx.x; task < n_fill; task += gridDim.x) {
@@ -983,6 +988,7 @@ __global__ void __launch_bounds__(TE * TE, 2048 / (TE * TE)) k_fill_sdf(ns_curve
       }
     }
     __syncthreads();
+    bool live = false, culled = false;
     if (valid) {
       // winding number from the row's crossing list (or the whole polyline)
       int wn = 0;
@@ -1026,16 +1032,48 @@ __global__ void __launch_bounds__(TE * TE, 2048 / (TE * TE)) k_fill_sdf(ns_curve
         sig = 1.f / (1.f + __expf(-z));
       }
       const float2 lo = glo[c];
+      const float oj = o * sig;
       rec[g] = make_float4(__fadd_rn(pl.x0, __fadd_rn(qx, lo.x)), __fadd_rn(pl.y0, __fadd_rn(qy, lo.y)),
-                           sp.eta * h / sp.rho, o * sig);
+                           sp.eta * h / sp.rho, oj);
       gcurve[g] = c;
       gaux[g] = deep ? kAuxDeep : (far ? kAuxFar : (inside ? arg : ~arg));
+      live = oj > 0.f && oj >= sp.fill_cull;   // sigma > 0 here
+      culled = oj < sp.fill_cull;
+    }
+    {
+      // the tile's box of live grid points and culled count (the rule the binning
+      // applies for alpha_min = fill_cull): warps reduce, then shared atomics;
+      // one thread adds the tile's to the curve's after the barrier
+      const int bx0 = __reduce_min_sync(0xffffffffu, live ? ix : 0x7fffffff);
+      const int by0 = __reduce_min_sync(0xffffffffu, live ? iy : 0x7fffffff);
+      const int bx1 = __reduce_max_sync(0xffffffffu, live ? ix : -1);
+      const int by1 = __reduce_max_sync(0xffffffffu, live ? iy : -1);
+      const int nculled = __popc(__ballot_sync(0xffffffffu, culled));
+      if (lane == 0) {
+        if (bx1 >= 0) {
+          atomicMin(&s_box[buf][0], bx0);
+          atomicMin(&s_box[buf][1], by0);
+          atomicMax(&s_box[buf][2], bx1);
+          atomicMax(&s_box[buf][3], by1);
+        }
+        if (nculled) atomicAdd(&s_box[buf][4], nculled);
+      }
     }
     // clear the other buffer for the next task
     s_key[buf ^ 1][tid] = ~0ull;
     if (tid < TE) s_xcnt[buf ^ 1][tid] = 0;
     if (tid == 0) s_nnear[buf ^ 1] = 0;
+    if (tid < 5) s_box[buf ^ 1][tid] = tid < 2 ? 0x7fffffff : (tid < 4 ? -1 : 0);
     __syncthreads();
+    if (tid == 0) {
+      if (s_box[buf][2] >= 0) {
+        atomicMin(&lbox[c].x, s_box[buf][0]);
+        atomicMin(&lbox[c].y, s_box[buf][1]);
+        atomicMax(&lbox[c].z, s_box[buf][2]);
+        atomicMax(&lbox[c].w, s_box[buf][3]);
+      }
+      if (s_box[buf][4]) atomicAdd(&st->culled_s, (unsigned long long)s_box[buf][4]);
+    }
     buf ^= 1;
   }
 }
@@ -1096,8 +1134,9 @@ extern "C" ns_status nurbs_sample(const ns_curves* curves, const ns_sample_param
               256, 0, s, *curves, plan, knots, at<const float>(ws, L.o_knots_lo), krcp, st, bpts,
               at<int>(ws, L.o_bcurve),
               bloc, cap->boundary);
+  int4* lbox = at<int4>(ws, L.o_lbox);
   NS_LAUNCH(NS_KERNEL_OTHER, k_boundary_box, (nc + 7) / 8, 256, 0, s, *curves, *sp, plan, knots, bloc,
-            at<float2>(ws, L.o_glo), cap->boundary);
+            at<float2>(ws, L.o_glo), cap->boundary, lbox, st);
   float4* cbox = at<float4>(ws, L.o_cbox);
   if (cap->boundary > 0)
     NS_LAUNCH(NS_KERNEL_OTHER, k_cluster_boxes, int((cap->boundary + 255) / 256), 256, 0, s, plan,
@@ -1119,11 +1158,11 @@ extern "C" ns_status nurbs_sample(const ns_curves* curves, const ns_sample_param
   if (ftile == 8)
     NS_LAUNCH(NS_KERNEL_FILL_SDF, k_fill_sdf<8>, num_sms() * 64, 64, 0, s, *curves, *sp, plan, order, bloc,
               at<const float2>(ws, L.o_glo), cbox, st, reinterpret_cast<float4*>(out->rec), out->curve, out->aux,
-              cap->gaussians, cap->boundary, tmap, (long long)L.tcap);
+              cap->gaussians, cap->boundary, tmap, (long long)L.tcap, lbox);
   else
     NS_LAUNCH(NS_KERNEL_FILL_SDF, k_fill_sdf<16>, num_sms() * 16, 256, 0, s, *curves, *sp, plan, order, bloc,
               at<const float2>(ws, L.o_glo), cbox, st, reinterpret_cast<float4*>(out->rec), out->curve, out->aux,
-              cap->gaussians, cap->boundary, tmap, (long long)L.tcap);
+              cap->gaussians, cap->boundary, tmap, (long long)L.tcap, lbox);
   NS_LAUNCH(NS_KERNEL_EMIT, k_emit, grid, 256, 0, s, *curves, *sp, plan, order, knots, st,
             reinterpret_cast<float4*>(out->rec), out->curve, out->aux, cap->gaussians, tmap, (long long)L.tcap);
   if (out->shape)
