@@ -537,17 +537,21 @@ __global__ void __launch_bounds__(256) k_radix_hist(const uint32_t* __restrict__
   __shared__ uint32_t h[256];
   const int n = st->pair_count;
   const int nb = (n + kSortItems - 1) / kSortItems;
-  if ((int)blockIdx.x >= nb) return;
   const int nd = 1 << bits;
-  for (int d = threadIdx.x; d < nd; d += blockDim.x) h[d] = 0;
-  __syncthreads();
-  const long long base = (long long)blockIdx.x * kSortItems;
-  for (int k = threadIdx.x; k < kSortItems; k += blockDim.x) {
-    const long long i = base + k;
-    if (i < n) atomicAdd(&h[(keys[i] >> shift) & (nd - 1)], 1u);
+  // sort blocks of kSortItems pairs, grid-stride (the grid is sized by the
+  // capacity, the pairs are known on the device only)
+  for (int vb = blockIdx.x; vb < nb; vb += gridDim.x) {
+    for (int d = threadIdx.x; d < nd; d += blockDim.x) h[d] = 0;
+    __syncthreads();
+    const long long base = (long long)vb * kSortItems;
+    for (int k = threadIdx.x; k < kSortItems; k += blockDim.x) {
+      const long long i = base + k;
+      if (i < n) atomicAdd(&h[(keys[i] >> shift) & (nd - 1)], 1u);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < nd; d += blockDim.x) hist[(long long)d * nb + vb] = h[d];
+    __syncthreads();
   }
-  __syncthreads();
-  for (int d = threadIdx.x; d < nd; d += blockDim.x) hist[(long long)d * nb + blockIdx.x] = h[d];
 }
 
 // Exclusive scan of the digit-major histogram hist[digit][block], in two
@@ -627,80 +631,83 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const uint32_t* __restric
   __shared__ uint32_t s_val[kSortItems];
   const int n = st->pair_count;
   const int nb = (n + kSortItems - 1) / kSortItems;
-  if ((int)blockIdx.x >= nb) return;
   const int nd = 1 << bits;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int d = lane; d < nd; d += 32) wcnt[w][d] = 0;
-  __syncwarp();
-  const long long blk0 = (long long)blockIdx.x * kSortItems;
-  const int nblk = (int)min((long long)kSortItems, n - blk0);
-  const long long base = blk0 + (long long)w * kPerWarp;
-  uint32_t key[kRounds], val[kRounds];
-  uint32_t rank[kRounds];
-#pragma unroll
-  for (int r = 0; r < kRounds; ++r) {
-    const long long i = base + r * 32 + lane;
-    const bool ok = i < n;
-    key[r] = ok ? kin[i] : 0u;
-    val[r] = ok ? vin[i] : 0u;
-    const uint32_t d = ok ? (key[r] >> shift) & (nd - 1) : 0xffffffffu;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    const uint32_t below = peers & ((1u << lane) - 1u);
-    const uint32_t base_cnt = ok ? wcnt[w][d] : 0u;
-    rank[r] = base_cnt + __popc(below);
+  // sort blocks of kSortItems pairs, grid-stride (see k_radix_hist)
+  for (int vb = blockIdx.x; vb < nb; vb += gridDim.x) {
+    __syncthreads();   // the previous block's shared arrays are read
+    for (int d = lane; d < nd; d += 32) wcnt[w][d] = 0;
     __syncwarp();
-    if (ok && below == 0u) wcnt[w][d] = base_cnt + __popc(peers);
-    __syncwarp();
-  }
-  __syncthreads();
-  // per digit: offsets of the warps inside the block's digit run, the run's
-  // start in the block's sorted order, and its global position
-  for (int d = threadIdx.x; d < nd; d += blockDim.x) {
-    uint32_t acc = 0;
+    const long long blk0 = (long long)vb * kSortItems;
+    const int nblk = (int)min((long long)kSortItems, n - blk0);
+    const long long base = blk0 + (long long)w * kPerWarp;
+    uint32_t key[kRounds], val[kRounds];
+    uint32_t rank[kRounds];
 #pragma unroll
-    for (int ww = 0; ww < kWarps; ++ww) {
-      const uint32_t c = wcnt[ww][d];
-      wcnt[ww][d] = acc;
-      acc += c;
+    for (int r = 0; r < kRounds; ++r) {
+      const long long i = base + r * 32 + lane;
+      const bool ok = i < n;
+      key[r] = ok ? kin[i] : 0u;
+      val[r] = ok ? vin[i] : 0u;
+      const uint32_t d = ok ? (key[r] >> shift) & (nd - 1) : 0xffffffffu;
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      const uint32_t below = peers & ((1u << lane) - 1u);
+      const uint32_t base_cnt = ok ? wcnt[w][d] : 0u;
+      rank[r] = base_cnt + __popc(below);
+      __syncwarp();
+      if (ok && below == 0u) wcnt[w][d] = base_cnt + __popc(peers);
+      __syncwarp();
     }
-    dstart[d] = acc;   // the digit's count for now
-    gbase[d] = hist[(long long)d * nb + blockIdx.x];
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {   // exclusive scan of the digit counts (nd <= 256)
-    uint32_t run = 0;
-    for (int c0 = 0; c0 < nd; c0 += 32) {
-      const int d = c0 + lane;
-      uint32_t v = d < nd ? dstart[d] : 0u;
-      uint32_t x = v;
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
+    __syncthreads();
+    // per digit: offsets of the warps inside the block's digit run, the run's
+    // start in the block's sorted order, and its global position
+    for (int d = threadIdx.x; d < nd; d += blockDim.x) {
+      uint32_t acc = 0;
+#pragma unroll
+      for (int ww = 0; ww < kWarps; ++ww) {
+        const uint32_t c = wcnt[ww][d];
+        wcnt[ww][d] = acc;
+        acc += c;
       }
-      if (d < nd) dstart[d] = run + x - v;
-      run += __shfl_sync(0xffffffffu, x, 31);
+      dstart[d] = acc;   // the digit's count for now
+      gbase[d] = hist[(long long)d * nb + vb];
     }
-  }
-  __syncthreads();
-  // stable local placement in shared memory
+    __syncthreads();
+    if (threadIdx.x < 32) {   // exclusive scan of the digit counts (nd <= 256)
+      uint32_t run = 0;
+      for (int c0 = 0; c0 < nd; c0 += 32) {
+        const int d = c0 + lane;
+        uint32_t v = d < nd ? dstart[d] : 0u;
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+          if (lane >= o) x += y;
+        }
+        if (d < nd) dstart[d] = run + x - v;
+        run += __shfl_sync(0xffffffffu, x, 31);
+      }
+    }
+    __syncthreads();
+    // stable local placement in shared memory
 #pragma unroll
-  for (int r = 0; r < kRounds; ++r) {
-    const long long i = base + r * 32 + lane;
-    if (i < n) {
-      const uint32_t d = (key[r] >> shift) & (nd - 1);
-      const uint32_t pos = dstart[d] + wcnt[w][d] + rank[r];
-      s_key[pos] = key[r];
-      s_val[pos] = val[r];
+    for (int r = 0; r < kRounds; ++r) {
+      const long long i = base + r * 32 + lane;
+      if (i < n) {
+        const uint32_t d = (key[r] >> shift) & (nd - 1);
+        const uint32_t pos = dstart[d] + wcnt[w][d] + rank[r];
+        s_key[pos] = key[r];
+        s_val[pos] = val[r];
+      }
     }
-  }
-  __syncthreads();
-  // contiguous runs per digit: consecutive threads write consecutive positions
-  for (int j = threadIdx.x; j < nblk; j += blockDim.x) {
-    const uint32_t k = s_key[j];
-    const uint32_t d = (k >> shift) & (nd - 1);
-    const uint32_t pos = gbase[d] + (uint32_t(j) - dstart[d]);
-    kout[pos] = k;
-    vout[pos] = s_val[j];
+    __syncthreads();
+    // contiguous runs per digit: consecutive threads write consecutive positions
+    for (int j = threadIdx.x; j < nblk; j += blockDim.x) {
+      const uint32_t k = s_key[j];
+      const uint32_t d = (k >> shift) & (nd - 1);
+      const uint32_t pos = gbase[d] + (uint32_t(j) - dstart[d]);
+      kout[pos] = k;
+      vout[pos] = s_val[j];
+    }
   }
 }
 __global__ void k_ranges(const uint32_t* __restrict__ keys, const DevState* st, int2* ranges) {
@@ -2553,14 +2560,16 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
   }
   const RasterPlan rpn = radix_plan(L.n_tiles);
   const int sort_blocks = int(L.sort_blocks);
+  const int sort_grid = std::min(sort_blocks, num_sms() * 4);   // the kernels stride over the pairs' blocks
   uint32_t *kin = k0, *vin = v0, *kout = k1, *vout = v1;
   for (int pass = 0; pass < rpn.passes; ++pass) {
     const int shift = pass * rpn.bits_per_pass;
     if (sort_blocks > 0) {
-      NS_LAUNCH(NS_KERNEL_RADIX_HIST, k_radix_hist, sort_blocks, 256, 0, s, kin, st, shift, rpn.bits_per_pass, hist);
+      NS_LAUNCH(NS_KERNEL_RADIX_HIST, k_radix_hist, sort_grid, 256, 0, s, kin, st, shift, rpn.bits_per_pass, hist);
       NS_LAUNCH(NS_KERNEL_SCAN, k_radix_totals, 1 << rpn.bits_per_pass, 256, 0, s, hist, st, totals);
       NS_LAUNCH(NS_KERNEL_SCAN, k_radix_scan, 1 << rpn.bits_per_pass, 256, 0, s, hist, st, totals);
-      NS_LAUNCH(NS_KERNEL_RADIX_SCATTER, k_radix_scatter, sort_blocks, 256, 0, s, kin, vin, kout, vout, hist, st, shift, rpn.bits_per_pass);
+      NS_LAUNCH(NS_KERNEL_RADIX_SCATTER, k_radix_scatter, sort_grid, 256, 0, s, kin, vin, kout, vout, hist, st, shift,
+                rpn.bits_per_pass);
     }
     std::swap(kin, kout);
     std::swap(vin, vout);
