@@ -213,8 +213,16 @@ __device__ __forceinline__ int block_excl_scan_int(int v, int* s_warp, int& tota
   return r;
 }
 
-// 256 threads x 8 consecutive Gaussians.
+// The exponent coefficient -1 / (2 sigma^2) of Eq. 9.
 __device__ __forceinline__ float ncoef(float sigma) { return __fdiv_rn(-0.5f, __fmul_rn(sigma, sigma)); }
+// The same coefficient times log2(e), for exponentials taken as powers of 2.
+__device__ __forceinline__ float ncoef2(float sigma) { return __fmul_rn(ncoef(sigma), 1.44269504088896341f); }
+// 2^x by the special-function unit's approximation (relative error near 2^-22).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
 // Squared reach of a Gaussian: beyond it alpha < alpha_min for certain
 // (a margin of 1e-3 in the logarithm covers the rounding of exp and of d^2).
@@ -1486,7 +1494,8 @@ struct LayerArgs {
   const float4* rec;
   const int* gcount;
   const int2* runs;   // per curve: covered column run per tile column, then row run per tile row
-  const float4* lconst;   // per curve: {X0, Y0, xoff, yoff}, {sigma, ncoef, nx bits, ny bits}, {h, 1/h, R, 0}
+  const float4* lconst;   // per curve: {X0, Y0, xoff, yoff}, {sigma, ncoef log2(e), nx bits, ny bits},
+                          // {h, 1/h, R, 0}
                           // with the grid origin X0 + xoff (X0 an integer), from k_layer_runs
   int gcap, tile, tiles_x, runs_stride;
   float k_sigma, inv_tile, log_amin;
@@ -1497,7 +1506,8 @@ struct LayerArgs {
 struct LayerView {
   long long g_off, G;   // first Gaussian; Gaussians in the set (nothing at or past G is read)
   int nx, ny;
-  float x0, y0, inv_h, sig, nc, R;   // x0, y0: the grid origin rounded to float (windows only)
+  float x0, y0, inv_h, sig, nc2, R;   // x0, y0: the grid origin rounded to float (windows only);
+                                      // nc2 = -log2(e) / (2 sigma^2)
   float X0, Y0, xoff, yoff, h;       // the origin as integer + offset, for the exact local offsets
   int cx0, cx1, cy0, cy1;   // columns and rows binned to this tile (empty when cx0 > cx1)
 };
@@ -1561,7 +1571,7 @@ __global__ void __launch_bounds__(128) k_layer_runs(ns_curves cv, const CurvePla
     const float2 lo = glo[c];
     const float X0 = floorf(p.x0), Y0 = floorf(p.y0);
     lconst[3 * c] = make_float4(X0, Y0, __fadd_rn(__fsub_rn(p.x0, X0), lo.x), __fadd_rn(__fsub_rn(p.y0, Y0), lo.y));
-    lconst[3 * c + 1] = make_float4(sig, ncoef(sig), __int_as_float(p.nx), __int_as_float(p.ny));
+    lconst[3 * c + 1] = make_float4(sig, ncoef2(sig), __int_as_float(p.nx), __int_as_float(p.ny));
     lconst[3 * c + 2] = make_float4(p.h, 1.f / p.h, R, 0.f);
   }
   int tx0, ty0, ntx;
@@ -1625,7 +1635,7 @@ __device__ __forceinline__ LayerView layer_view(const float4& k0, const float4& 
   v.inv_h = k2.y;
   v.R = k2.z;
   v.sig = k1.x;
-  v.nc = k1.y;
+  v.nc2 = k1.y;
   v.nx = __float_as_int(k1.z);
   v.ny = __float_as_int(k1.w);
   v.cx0 = rx.x;
@@ -1663,15 +1673,24 @@ __device__ __forceinline__ bool layer_point_binned(const float4& r, float alpha_
 // Grid-local coordinate of grid column (row) i, as nurbs_sample placed it.
 __device__ __forceinline__ float layer_qx(const LayerView& v, int i) { return (float(i) + 0.5f) * v.h; }
 
-// alpha of a layer's grid point (staged {qx, qy, ncoef, o} in grid-local
-// coordinates) at the pixel whose centre minus the integer origin is (fxl,
-// fyl): the offset (fxl - qx) - xoff is exact to ~1e-7 px, then as gauss_alpha.
-__device__ __forceinline__ float layer_alpha(const LayerView& v, float fxl, float fyl, const float4& q, float amax,
-                                             float& dx, float& dy, float& d2, float& e) {
+// The offset of grid row iy from the pixel row whose centre minus the integer
+// origin is fyl: (fyl - qy) - yoff, exact to ~1e-7 px.  It is the same for
+// every point of the row, so the walks form it (and its square) once per row.
+__device__ __forceinline__ float layer_dy(const LayerView& v, float fyl, int iy) {
+  return __fsub_rn(__fsub_rn(fyl, layer_qx(v, iy)), v.yoff);
+}
+
+// alpha of a layer's grid point (staged {qx, qy, nc2, o} in grid-local
+// coordinates, nc2 = -log2(e) / (2 sigma^2)) at the pixel whose centre minus
+// the integer origin has x part fxl, on a row at squared offset dy2:
+// alpha = min(alpha_max, o 2^(nc2 d^2)), which is o exp(-d^2 / (2 sigma^2))
+// of Eq. 9.  The forward and the adjoint call this one function, so they
+// compute the same bits.
+__device__ __forceinline__ float layer_alpha(const LayerView& v, float fxl, float dy2, const float4& q, float amax,
+                                             float& dx, float& d2, float& e) {
   dx = __fsub_rn(__fsub_rn(fxl, q.x), v.xoff);
-  dy = __fsub_rn(__fsub_rn(fyl, q.y), v.yoff);
-  d2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
-  e = __expf(__fmul_rn(q.z, d2));
+  d2 = __fmaf_rn(dx, dx, dy2);
+  e = ex2_approx(__fmul_rn(q.z, d2));
   return fminf(__fmul_rn(q.w, e), amax);
 }
 
@@ -1710,7 +1729,7 @@ __device__ __forceinline__ bool layer_stage(const LayerArgs& la, const LayerView
     if (g < v.G) {
       const float4 r = la.rec[g];
       if (layer_point_binned(r, alpha_min)) {
-        q = make_float4(layer_qx(v, rx0 + ixr), layer_qx(v, ry0 + iyr), r.z == v.sig ? v.nc : ncoef(r.z), r.w);
+        q = make_float4(layer_qx(v, rx0 + ixr), layer_qx(v, ry0 + iyr), r.z == v.sig ? v.nc2 : ncoef2(r.z), r.w);
         live = true;
       }
     }
@@ -1802,6 +1821,23 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
     float dx, dy, d2, e;
     composite_alpha(k, gauss_alpha(fx, fy, q, bp.alpha_max, dx, dy, d2, e), cc, pos, sub);
   };
+  // the same step for a grid point of a layer: every point of the layer has
+  // the curve's colour, so the weights a T of Eq. 8 are summed (wsum) and the
+  // colour is added once per layer
+  auto composite_layer = [&](int k, float a, float& wsum, int pos, int sub) {
+    ++evals;
+    if (a < bp.alpha_min) return;
+    const float test = T[k] * (1.f - a);
+    if (test < bp.t_min) {
+      done[k] = true;
+      return;
+    }
+    wsum = fmaf(a, T[k], wsum);
+    T[k] = test;
+    last[k] = pos;
+    lsub[k] = sub;
+    ++contribs;
+  };
   for (int base = 0; base < n && !__all_sync(0xffffffffu, all_done()); base += 32) {
     const int j = base + lane;
     bool hit = false;
@@ -1862,8 +1898,10 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
           int ix0, ix1, iy0, iy1;
           layer_window(v, fx, fy, ix0, ix1, iy0, iy1);
           const int pos = base + b + 1;
+          float wsum = 0.f;
           for (int iy = iy0; iy <= iy1 && !done[k]; ++iy) {
             const int rowsub = iy * v.nx;
+            const float dy = layer_dy(v, fyl, iy), dy2 = __fmul_rn(dy, dy);
             if (staged) {
               // two points per step: both alphas are independent of the
               // compositing state, which then takes them in order
@@ -1871,17 +1909,17 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
               int ix = ix0;
               for (; ix + 1 <= ix1 && !done[k]; ix += 2) {
                 const float4 qa = prow[ix], qb = prow[ix + 1];
-                float dx, dy, d2, ea, eb;
-                const float aa = layer_alpha(v, fxl, fyl, qa, bp.alpha_max, dx, dy, d2, ea);
-                const float ab = layer_alpha(v, fxl, fyl, qb, bp.alpha_max, dx, dy, d2, eb);
-                if (qa.w >= 0.f) composite_alpha(k, aa, cc, pos, rowsub + ix + 1);
-                if (qb.w >= 0.f && !done[k]) composite_alpha(k, ab, cc, pos, rowsub + ix + 2);
+                float dx, d2, ea, eb;
+                const float aa = layer_alpha(v, fxl, dy2, qa, bp.alpha_max, dx, d2, ea);
+                const float ab = layer_alpha(v, fxl, dy2, qb, bp.alpha_max, dx, d2, eb);
+                if (qa.w >= 0.f) composite_layer(k, aa, wsum, pos, rowsub + ix + 1);
+                if (qb.w >= 0.f && !done[k]) composite_layer(k, ab, wsum, pos, rowsub + ix + 2);
               }
               if (ix <= ix1 && !done[k]) {
                 const float4 q = prow[ix];
-                float dx, dy, d2, e;
+                float dx, d2, e;
                 if (q.w >= 0.f)
-                  composite_alpha(k, layer_alpha(v, fxl, fyl, q, bp.alpha_max, dx, dy, d2, e), cc, pos,
+                  composite_layer(k, layer_alpha(v, fxl, dy2, q, bp.alpha_max, dx, d2, e), wsum, pos,
                                   rowsub + ix + 1);
               }
             } else {
@@ -1890,12 +1928,17 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
                 if (g >= v.G) break;
                 const float4 r = la.rec[g];
                 if (!layer_point_binned(r, bp.alpha_min)) continue;
-                const float4 q = make_float4(layer_qx(v, ix), layer_qx(v, iy), r.z == v.sig ? v.nc : ncoef(r.z), r.w);
-                float dx, dy, d2, e;
-                composite_alpha(k, layer_alpha(v, fxl, fyl, q, bp.alpha_max, dx, dy, d2, e), cc, pos,
+                const float4 q = make_float4(layer_qx(v, ix), 0.f, r.z == v.sig ? v.nc2 : ncoef2(r.z), r.w);
+                float dx, d2, e;
+                composite_layer(k, layer_alpha(v, fxl, dy2, q, bp.alpha_max, dx, d2, e), wsum, pos,
                                 rowsub + ix + 1);
               }
             }
+          }
+          acc[k][0] = fmaf(cc.x, wsum, acc[k][0]);
+          if (C == 3) {
+            acc[k][1] = fmaf(cc.y, wsum, acc[k][1]);
+            acc[k][2] = fmaf(cc.z, wsum, acc[k][2]);
           }
         }
         if (staged) __syncwarp();
@@ -1967,7 +2010,10 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
   const int2 rg = ranges[blockIdx.x];
   const long long Gset = min((long long)*la.gcount, (long long)la.gcap);   // Gaussians in the set
   const bool per_pair = full_grads || dcurve == nullptr;
-  float T[PPT], dI[PPT][3], Bk[PPT][3];
+  // S[k] = B . dI: the colour B composited behind the current pair (the
+  // background first), projected on the pixel's image gradient; the opacity
+  // adjoint needs only this projection (dL/dalpha = (c - B) . dI T)
+  float T[PPT], dI[PPT][3], S[PPT];
   int last[PPT], lsub[PPT];
   int wmax = 0;
 #pragma unroll
@@ -1976,9 +2022,6 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
     T[k] = 1.f;
     last[k] = 0;
     lsub[k] = 0;
-    Bk[k][0] = bp.bg0;
-    Bk[k][1] = bp.bg1;
-    Bk[k][2] = bp.bg2;
     dI[k][0] = dI[k][1] = dI[k][2] = 0.f;
     if (px < bp.W && py < bp.H) {
       const long long pix = ((long long)s * bp.H + py) * bp.W + px;
@@ -1988,6 +2031,8 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
 #pragma unroll
       for (int ch = 0; ch < C; ++ch) dI[k][ch] = dimage[pix * C + ch];
     }
+    S[k] = bp.bg0 * dI[k][0];
+    if (C == 3) S[k] = fmaf(bp.bg2, dI[k][2], fmaf(bp.bg1, dI[k][1], S[k]));
     wmax = max(wmax, last[k]);
   }
   for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
@@ -1995,27 +2040,42 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
   // the adjoint of one pair of pixel k (blend constants q, colour cc):
   // returns false below alpha_min; else the opacity gradient dO, the colour
   // gradient col and, for the centre and sigma, da a and the offsets
+  auto color_dot = [&](int k, const float4& cc) {
+    float v = cc.x * dI[k][0];
+    if (C == 3) v = fmaf(cc.z, dI[k][2], fmaf(cc.y, dI[k][1], v));
+    return v;
+  };
   auto adjoint_alpha = [&](int k, float a, float e, float ow, const float4& cc, float& dO, float col[3],
                            float& daa) {
     ++evals;
     if (a < bp.alpha_min) return false;
     T[k] = __fdividef(T[k], 1.f - a);   // transmittance in front of this Gaussian
     const float wgt = a * T[k];
-    float da = (cc.x - Bk[k][0]) * dI[k][0];
+    const float diff = color_dot(k, cc) - S[k];
     col[0] = wgt * dI[k][0];
     col[1] = col[2] = 0.f;
-    Bk[k][0] = a * cc.x + (1.f - a) * Bk[k][0];
     if (C == 3) {
-      da += (cc.y - Bk[k][1]) * dI[k][1] + (cc.z - Bk[k][2]) * dI[k][2];
       col[1] = wgt * dI[k][1];
       col[2] = wgt * dI[k][2];
-      Bk[k][1] = a * cc.y + (1.f - a) * Bk[k][1];
-      Bk[k][2] = a * cc.z + (1.f - a) * Bk[k][2];
     }
-    da *= T[k];
+    S[k] = fmaf(a, diff, S[k]);   // B <- a c + (1 - a) B
+    const float da = diff * T[k];
     const bool uncapped = __fmul_rn(ow, e) < bp.alpha_max;
     dO = uncapped ? e * da : 0.f;
     daa = uncapped ? da * a : 0.f;
+    return true;
+  };
+  // the same for a grid point of a layer whose colour projection cc . dI is
+  // ccd: the colour gradient of the layer is the sum of the weights a T
+  // (wsum) times dI, formed once per layer
+  auto adjoint_layer = [&](int k, float a, float e, float ow, float ccd, float& wsum, float& dO) {
+    ++evals;
+    if (a < bp.alpha_min) return false;
+    T[k] = __fdividef(T[k], 1.f - a);
+    wsum = fmaf(a, T[k], wsum);
+    const float diff = ccd - S[k];
+    S[k] = fmaf(a, diff, S[k]);
+    dO = __fmul_rn(ow, e) < bp.alpha_max ? e * (diff * T[k]) : 0.f;
     return true;
   };
   auto adjoint = [&](int k, float fy, const float4& q, const float4& cc, float& dO, float col[3], float& daa,
@@ -2098,59 +2158,54 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
           int ix0, ix1, iy0, iy1;
           layer_window(v, fx, fy, ix0, ix1, iy0, iy1);
           if (staged) {
+            const float ccd = color_dot(k, cc);
+            float wsum = 0.f;
             for (int iy = iy1; iy >= iy0; --iy) {
               const int rowsub = iy * v.nx;
               const int ridx = (iy - ry0) * rw - rx0;
               const float4* prow = &s_pt[w][ridx];
               float* rreg = &s_reg[w][ridx];
+              const float dy = layer_dy(v, fyl, iy), dy2 = __fmul_rn(dy, dy);
               // the last layer of the pixel starts at its last composited point
               int ix = min(ix1, sstart - rowsub);
               // two points per step: both alphas first, then the adjoint in order
               for (; ix - 1 >= ix0; ix -= 2) {
                 const float4 qa = prow[ix], qb = prow[ix - 1];
-                float dxa, dya, d2a, ea, dxb, dyb, d2b, eb;
-                const float aa = layer_alpha(v, fxl, fyl, qa, bp.alpha_max, dxa, dya, d2a, ea);
-                const float ab = layer_alpha(v, fxl, fyl, qb, bp.alpha_max, dxb, dyb, d2b, eb);
-                float dO, col[3], daa;
-                if (qa.w >= 0.f && adjoint_alpha(k, aa, ea, qa.w, cc, dO, col, daa)) {
-                  csum[0] += col[0];
-                  csum[1] += col[1];
-                  csum[2] += col[2];
-                  if (dO != 0.f) atomicAdd(&rreg[ix], dO);
-                }
-                if (qb.w >= 0.f && adjoint_alpha(k, ab, eb, qb.w, cc, dO, col, daa)) {
-                  csum[0] += col[0];
-                  csum[1] += col[1];
-                  csum[2] += col[2];
-                  if (dO != 0.f) atomicAdd(&rreg[ix - 1], dO);
-                }
+                float dxa, d2a, ea, dxb, d2b, eb;
+                const float aa = layer_alpha(v, fxl, dy2, qa, bp.alpha_max, dxa, d2a, ea);
+                const float ab = layer_alpha(v, fxl, dy2, qb, bp.alpha_max, dxb, d2b, eb);
+                float dO;
+                if (qa.w >= 0.f && adjoint_layer(k, aa, ea, qa.w, ccd, wsum, dO) && dO != 0.f)
+                  atomicAdd(&rreg[ix], dO);
+                if (qb.w >= 0.f && adjoint_layer(k, ab, eb, qb.w, ccd, wsum, dO) && dO != 0.f)
+                  atomicAdd(&rreg[ix - 1], dO);
               }
               if (ix == ix0) {
                 const float4 q = prow[ix];
-                float dO, col[3], daa, dx, dy, d2, e;
+                float dO, dx, d2, e;
                 if (q.w >= 0.f &&
-                    adjoint_alpha(k, layer_alpha(v, fxl, fyl, q, bp.alpha_max, dx, dy, d2, e), e, q.w, cc, dO, col,
-                                  daa)) {
-                  csum[0] += col[0];
-                  csum[1] += col[1];
-                  csum[2] += col[2];
-                  if (dO != 0.f) atomicAdd(&rreg[ix], dO);
-                }
+                    adjoint_layer(k, layer_alpha(v, fxl, dy2, q, bp.alpha_max, dx, d2, e), e, q.w, ccd, wsum, dO) &&
+                    dO != 0.f)
+                  atomicAdd(&rreg[ix], dO);
               }
             }
+            csum[0] = fmaf(wsum, dI[k][0], csum[0]);
+            csum[1] = fmaf(wsum, dI[k][1], csum[1]);
+            csum[2] = fmaf(wsum, dI[k][2], csum[2]);
             continue;
           }
           for (int iy = iy1; iy >= iy0; --iy) {
             const int rowsub = iy * v.nx;
+            const float dy = layer_dy(v, fyl, iy), dy2 = __fmul_rn(dy, dy);
             for (int ix = ix1; ix >= ix0; --ix) {
               if (rowsub + ix > sstart) continue;
               const long long g = v.g_off + rowsub + ix;
               if (g >= v.G) continue;
               const float4 r = la.rec[g];
               if (!layer_point_binned(r, bp.alpha_min)) continue;
-              const float4 q = make_float4(layer_qx(v, ix), layer_qx(v, iy), r.z == v.sig ? v.nc : ncoef(r.z), r.w);
-              float dO, col[3], daa, dx, dy, d2, e;
-              if (!adjoint_alpha(k, layer_alpha(v, fxl, fyl, q, bp.alpha_max, dx, dy, d2, e), e, q.w, cc, dO, col,
+              const float4 q = make_float4(layer_qx(v, ix), 0.f, r.z == v.sig ? v.nc2 : ncoef2(r.z), r.w);
+              float dO, col[3], daa, dx, d2, e;
+              if (!adjoint_alpha(k, layer_alpha(v, fxl, dy2, q, bp.alpha_max, dx, d2, e), e, q.w, cc, dO, col,
                                  daa))
                 continue;
               if (!per_pair) {
