@@ -2,6 +2,7 @@
 // the Adam step and the error channel.
 #include <cuda_runtime.h>
 
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -47,6 +48,14 @@ void after_launch(int kernel_id, cudaStream_t s) {
       g_arms[i] = g_arms[--g_n_arms];   // one shot: drop the entry
       break;
     }
+}
+
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = getenv("NS_PDL");
+    return !(e && e[0] == '0');
+  }();
+  return on;
 }
 
 int num_sms() {
@@ -170,6 +179,7 @@ bool make_layout(const ns_curves* c, const ns_capacity* cap, const ns_raster_par
 int sorted_buffer(const Layout& L);
 
 __global__ void k_reset_state(DevState* st) {
+  grid_dep_wait();
   st->status = 0;
   st->bad_curve = -1;
   st->n_chunks = 0;
@@ -186,6 +196,7 @@ void launch_reset_state(DevState* st, cudaStream_t s) { NS_LAUNCH(NS_KERNEL_OTHE
 
 __global__ void __launch_bounds__(256) k_mse(const float* __restrict__ a, const float* __restrict__ b, long long n,
                                              float* __restrict__ grad, float* loss) {
+  grid_dep_wait();
   __shared__ float red[8];
   const float scale = 2.f / float(n);
   float acc = 0.f;
@@ -210,6 +221,7 @@ struct Clamp4 {
 
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
                        long long n, float b1, float b2, float eps, float c1, float c2, Clamp4 cl, int group) {
+  grid_dep_wait();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const float gi = g[i];
     const float mi = b1 * m[i] + (1.f - b1) * gi;

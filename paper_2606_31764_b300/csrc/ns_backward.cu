@@ -92,6 +92,7 @@ __global__ void __launch_bounds__(256, 8) k_chain(ns_curves cv, ChainParams cp, 
                                                const float4* __restrict__ rec, const int* __restrict__ gaux,
                                                const float* __restrict__ dgauss, long long gcap, long long bcap,
                                                float* dkey, float* dknots, float2* dbpts, float* dcolor, int row4) {
+  grid_dep_wait();
   __shared__ float2 s_db[kWinB];
   __shared__ float s_red[8];
   const int n_tasks = st->n_chunks;
@@ -336,6 +337,7 @@ __global__ void __launch_bounds__(kContourThreads) k_chain_contour(
     ns_curves cv, ChainParams cp, const CurvePlan* __restrict__ plan, const int* __restrict__ order,
     const float* __restrict__ knots, const DevState* __restrict__ st, const float* __restrict__ dgauss,
     long long gcap, float* dkey, float* dknots, float* dcolor) {
+  grid_dep_wait();
   __shared__ float s_cp[4 * kWin];
   __shared__ float s_kn[kWin + 2 * kMaxP];
   __shared__ float s_red[8];
@@ -427,6 +429,7 @@ template <bool KNOTS>
 __global__ void k_chain_boundary(ns_curves cv, const CurvePlan* __restrict__ plan, const float* __restrict__ knots,
                                  const DevState* __restrict__ st, const float2* __restrict__ dbpts,
                                  const int* __restrict__ bcurve, int freeze_w, float* dkey, float* dknots) {
+  grid_dep_wait();
   const int nb = st->b_count;
   const int nc = cv.n_curves;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nb; j += gridDim.x * blockDim.x) {
@@ -448,6 +451,7 @@ __global__ void k_chain_boundary(ns_curves cv, const CurvePlan* __restrict__ pla
 // knot down, with a running carry.
 __global__ void k_knot_grads(ns_curves cv, const CurvePlan* __restrict__ plan, const float* __restrict__ dknots,
                              float* dtau) {
+  grid_dep_wait();
   const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (c >= cv.n_curves || plan[c].kind == kNone) return;

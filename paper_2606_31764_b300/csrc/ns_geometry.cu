@@ -322,6 +322,7 @@ template <int P, int R>
 __global__ void __launch_bounds__(kGeoThreads) k_deriv_loss(ns_curves cv, const CurvePlan* __restrict__ plan,
                                                             const float* __restrict__ knots, GeoParams gp,
                                                             float* loss, float* dkey, float* dknots) {
+  grid_dep_wait();
   const int runs = (gp.nodes + kDerivRun - 1) / kDerivRun;
   const long long total = (long long)cv.n_curves * runs;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -452,6 +453,7 @@ template <int P, int R>
 __global__ void __launch_bounds__(kGeoCurveThreads) k_deriv_curve(ns_curves cv, const CurvePlan* __restrict__ plan,
                                                                   const float* __restrict__ knots, GeoParams gp,
                                                                   float* loss, float* dkey, float* dknots) {
+  grid_dep_wait();
   constexpr int kPoly = 1 + 3 * (P + 1);   // {m, A[0..P][3]}
   constexpr int KD = R + 1;                // derivatives needed: up to R + 1 (the last for d/du)
   __shared__ float sU[kGeoStage];
@@ -758,6 +760,7 @@ __global__ void __launch_bounds__(kGeoThreads) k_bbox_contour(ns_curves cv, cons
                                                               const int* __restrict__ gcurve,
                                                               const int* __restrict__ gcount, GeoParams gp,
                                                               float* loss, float* dkey, float* dknots) {
+  grid_dep_wait();
   const int n = *gcount;
   const int nc = cv.n_curves;
   const int stride = gridDim.x * blockDim.x;
@@ -796,6 +799,7 @@ __global__ void __launch_bounds__(kGeoThreads) k_bbox_boundary(ns_curves cv, con
                                                                const int* __restrict__ bcurve,
                                                                const DevState* __restrict__ st, GeoParams gp,
                                                                float* loss, float* dkey, float* dknots) {
+  grid_dep_wait();
   const int nb = st->b_count;
   const int nc = cv.n_curves;
   const int stride = gridDim.x * blockDim.x;

@@ -105,11 +105,37 @@ void launch_reset_state(DevState* st, cudaStream_t s);
 // Launch bookkeeping: counts launches and fires the armed profiling events.
 void before_launch(int kernel_id, cudaStream_t s);
 void after_launch(int kernel_id, cudaStream_t s);
-#define NS_LAUNCH(id, kernel, grid, block, smem, stream, ...)   \
-  do {                                                         \
-    ::ns::before_launch(id, stream);                           \
-    kernel<<<grid, block, smem, stream>>>(__VA_ARGS__);        \
-    ::ns::after_launch(id, stream);                            \
+
+// Programmatic dependent launch.  The library's kernels are launched with
+// programmatic stream serialization: a kernel's launch may overlap the end of
+// the kernel before it in the stream (or graph), and every kernel begins with
+// grid_dep_wait(), which returns once that kernel has completed and its
+// writes are visible.  So the order of memory effects is that of a plain
+// stream; what overlaps is the launch and the start of the next kernel's
+// blocks with the last blocks of this one.  A kernel launched without the
+// attribute returns from the wait at once.  The environment variable NS_PDL=0
+// launches without it.
+bool pdl_enabled();
+template <typename... KArgs, typename... Args>
+inline void launch_kernel(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                          Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+}
+#define NS_LAUNCH(id, kernel, grid, block, smem, stream, ...)                 \
+  do {                                                                       \
+    ::ns::before_launch(id, stream);                                         \
+    ::ns::launch_kernel(kernel, grid, block, smem, stream, __VA_ARGS__);     \
+    ::ns::after_launch(id, stream);                                          \
   } while (0)
 
 template <typename T>
@@ -117,6 +143,16 @@ inline T* at(void* ws, size_t off) { return reinterpret_cast<T*>(static_cast<cha
 
 // ---------------------------------------------------------------------------
 // device helpers
+
+// The first statement of every kernel (see launch_kernel): wait for the
+// kernel before, then allow the next kernel to launch.  Its blocks take SM
+// slots only as this grid's blocks finish (the trigger fires once every block
+// of this grid has run it) and wait in their own grid_dep_wait() until this
+// grid has completed.
+__device__ __forceinline__ void grid_dep_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" :::);
+}
 
 __device__ __forceinline__ void raise_status(DevState* st, int code) {
   atomicCAS(&st->status, 0, code);

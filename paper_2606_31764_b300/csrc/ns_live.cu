@@ -71,6 +71,7 @@ __global__ void __launch_bounds__(kLiveThreads) k_udf_sums(UdfParams up, const C
                                                            const int* __restrict__ new_curve,
                                                            const float* __restrict__ image,
                                                            const float* __restrict__ target, float* sums) {
+  grid_dep_wait();
   const long long hw = (long long)up.H * up.W;
   const long long n = hw * up.S;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -112,6 +113,7 @@ __global__ void __launch_bounds__(kLiveThreads) k_udf_sums(UdfParams up, const C
 // dL/dI = 2 scale w (I - I*) for a weighted scene, 2 |scale| (I - I*) for a
 // plain one (stored negative to tell them apart).
 __global__ void k_udf_finish(UdfParams up, const int* __restrict__ new_curve, float* sums, float* loss) {
+  grid_dep_wait();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   float tot = 0.f;
   for (int s = 0; s < up.S; ++s) {
@@ -134,6 +136,7 @@ __global__ void __launch_bounds__(kLiveThreads) k_udf_grad(UdfParams up, const C
                                                            const float* __restrict__ image,
                                                            const float* __restrict__ target,
                                                            const float* __restrict__ sums, float* dimage) {
+  grid_dep_wait();
   const long long hw = (long long)up.H * up.W;
   const long long n = hw * up.S;
   for (long long pix = blockIdx.x * (long long)blockDim.x + threadIdx.x; pix < n;
@@ -153,6 +156,7 @@ __global__ void __launch_bounds__(kLiveThreads) k_udf_grad(UdfParams up, const C
 
 // One warp per curve: the self-crossing penalty of its key-point polygon.
 __global__ void __launch_bounds__(128) k_xing(ns_curves cv, float lambda, float* loss, float* dkey) {
+  grid_dep_wait();
   const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (c >= cv.n_curves) return;
@@ -215,6 +219,7 @@ struct SeedParams {
 // Row pass: rows[pix] = sum of e over the window's columns in the pixel's row.
 __global__ void __launch_bounds__(kLiveThreads) k_seed_rows(SeedParams p, const float* __restrict__ image,
                                                             const float* __restrict__ target, float* rows) {
+  grid_dep_wait();
   const long long n = (long long)p.S * p.H * p.W;
   for (long long pix = blockIdx.x * (long long)blockDim.x + threadIdx.x; pix < n;
        pix += (long long)gridDim.x * blockDim.x) {
@@ -236,6 +241,7 @@ __global__ void __launch_bounds__(kLiveThreads) k_seed_rows(SeedParams p, const 
 // Column pass and the packed argmax per scene.
 __global__ void __launch_bounds__(kLiveThreads) k_seed_windows(SeedParams p, const float* __restrict__ rows,
                                                                unsigned long long* best) {
+  grid_dep_wait();
   const long long hw = (long long)p.H * p.W;
   const long long n = hw * p.S;
   for (long long pix = blockIdx.x * (long long)blockDim.x + threadIdx.x; pix < n;
@@ -254,6 +260,7 @@ __global__ void __launch_bounds__(kLiveThreads) k_seed_windows(SeedParams p, con
 
 __global__ void k_seed_unpack(int S, int W, const unsigned long long* __restrict__ best, int* seed_xy,
                               float* seed_value) {
+  grid_dep_wait();
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= S) return;
   const unsigned long long k = best[s];

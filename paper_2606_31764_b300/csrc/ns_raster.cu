@@ -43,6 +43,7 @@ namespace ns {
 
 
 __global__ void k_curve_scene(ns_curves cv, int* curve_scene) {
+  grid_dep_wait();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= cv.n_curves) return;
   int s = 0;
@@ -242,6 +243,7 @@ __global__ void __launch_bounds__(256) k_bin_count(const float4* __restrict__ re
                                                    float2* prep2, float2* reach, const CurvePlan* __restrict__ plan,
                                                    const int* __restrict__ order,
                                                    const int* __restrict__ scene_off) {
+  grid_dep_wait();
   __shared__ int s_warp[32];
   __shared__ int s_pure;
   const int G = min(*gcount, bp.gcap);
@@ -362,6 +364,7 @@ __global__ void __launch_bounds__(256) k_bin_count(const float4* __restrict__ re
 // k_bin_emit writes the layer's pairs.
 __global__ void k_layer_count(ns_curves cv, const CurvePlan* __restrict__ plan, const float4* __restrict__ rec,
                               const int* __restrict__ gcount, BinParams bp, int* bsum, const DevState* st) {
+  grid_dep_wait();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= cv.n_curves) return;
   bp.lcount[c] = 0;
@@ -389,6 +392,7 @@ __global__ void k_layer_emit(ns_curves cv, const CurvePlan* __restrict__ plan, c
                              const int* __restrict__ gcount, const int* __restrict__ curve_scene, BinParams bp,
                              const int* __restrict__ boff, const int* __restrict__ order, uint32_t* keys,
                              uint32_t* vals, long long pcap, const DevState* st) {
+  grid_dep_wait();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= cv.n_curves || !sampled_boxes(bp, st)) return;
   const int nt = bp.lcount[c];
@@ -423,6 +427,7 @@ __global__ void k_layer_emit(ns_curves cv, const CurvePlan* __restrict__ plan, c
 
 __global__ void k_scan_small(int* vals, const int* gcount, int gcap, int items_per_block, DevState* st,
                              long long cap) {
+  grid_dep_wait();
   __shared__ long long s_warp[32];
   __shared__ long long s_carry;
   const int G = min(*gcount, gcap);
@@ -470,6 +475,7 @@ __global__ void __launch_bounds__(256) k_bin_emit(const float4* __restrict__ rec
                                                   BinParams bp, const int* __restrict__ boff, uint32_t* keys,
                                                   uint32_t* vals, long long pcap, const int* __restrict__ cflags,
                                                   const CurvePlan* __restrict__ plan) {
+  grid_dep_wait();
   __shared__ int s_warp[32];
   __shared__ int s_off[kBinItems];    // tile count, then exclusive offset in Gaussian order
   __shared__ int2 s_rect[kBinItems];  // {x0 | nx << 16, y0 | ny << 16}
@@ -542,6 +548,7 @@ __global__ void __launch_bounds__(256) k_bin_emit(const float4* __restrict__ rec
 
 __global__ void __launch_bounds__(256) k_radix_hist(const uint32_t* __restrict__ keys, const DevState* st, int shift,
                                                     int bits, uint32_t* hist) {
+  grid_dep_wait();
   __shared__ uint32_t h[256];
   const int n = st->pair_count;
   const int nb = (n + kSortItems - 1) / kSortItems;
@@ -577,6 +584,7 @@ __device__ __forceinline__ uint32_t block_sum_u32(uint32_t v, uint32_t* s_warp) 
 
 __global__ void __launch_bounds__(256) k_radix_totals(const uint32_t* __restrict__ hist, const DevState* st,
                                                       uint32_t* totals) {
+  grid_dep_wait();
   __shared__ uint32_t s_warp[8];
   const int nb = (st->pair_count + kSortItems - 1) / kSortItems;
   const uint32_t* row = hist + (long long)blockIdx.x * nb;
@@ -588,6 +596,7 @@ __global__ void __launch_bounds__(256) k_radix_totals(const uint32_t* __restrict
 
 __global__ void __launch_bounds__(256) k_radix_scan(uint32_t* hist, const DevState* st,
                                                     const uint32_t* __restrict__ totals) {
+  grid_dep_wait();
   __shared__ uint32_t s_warp[8];
   __shared__ uint32_t s_carry;
   const int nb = (st->pair_count + kSortItems - 1) / kSortItems;
@@ -631,6 +640,7 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const uint32_t* __restric
                                                        const uint32_t* __restrict__ vin, uint32_t* kout,
                                                        uint32_t* vout, const uint32_t* __restrict__ hist,
                                                        const DevState* st, int shift, int bits) {
+  grid_dep_wait();
   constexpr int kWarps = 8, kPerWarp = kSortItems / kWarps, kRounds = kPerWarp / 32;
   __shared__ uint32_t wcnt[kWarps][256];
   __shared__ uint32_t dstart[256];        // first position of each digit in the block's sorted order
@@ -719,6 +729,7 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const uint32_t* __restric
   }
 }
 __global__ void k_ranges(const uint32_t* __restrict__ keys, const DevState* st, int2* ranges) {
+  grid_dep_wait();
   const int n = st->pair_count;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const uint32_t t = keys[i];
@@ -824,6 +835,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
                 const float2* __restrict__ prep2, const float2* __restrict__ reach, const int* __restrict__ gcurve,
                 const float4* __restrict__ color, BlendParams bp, float* image, float* Tfinal, int* nlast,
                 DevState* st) {
+  grid_dep_wait();
   using Gm = BlendGeom<TILE, PPT>;
   __shared__ float4 s_q[Gm::kWarps][32];
   __shared__ float4 s_c[Gm::kWarps][32];
@@ -946,6 +958,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
                 const float4* __restrict__ color, BlendParams bp, const float* __restrict__ dimage,
                 const float* __restrict__ Tfinal, const int* __restrict__ nlast, float* dgauss, DevState* st,
                 int full_grads, float* /* per-curve colour gradients: unused, the rows carry them */) {
+  grid_dep_wait();
   using Gm = BlendGeom<TILE, PPT>;
   constexpr int kRow = GradRow<ANISO>::kFloats;
   __shared__ float4 s_q[Gm::kWarps][32];
@@ -1190,6 +1203,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
                        const float2* __restrict__ reach, const int* __restrict__ gcurve,
                        const float4* __restrict__ color, BlendParams bp, float* image, float* Tfinal, int* nlast,
                        DevState* st) {
+  grid_dep_wait();
   using Gm = BlendGeom<TILE, PPT>;
   __shared__ float4 s_q[Gm::kWarps][32];
   __shared__ float4 s_c[Gm::kWarps][32];
@@ -1309,6 +1323,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, BlendGeom<TILE
                        const float4* __restrict__ color, BlendParams bp, const float* __restrict__ dimage,
                        const float* __restrict__ Tfinal, const int* __restrict__ nlast, float* dgauss, DevState* st,
                        int full_grads, float* /* per-curve colour gradients: unused, the rows carry them */) {
+  grid_dep_wait();
   using Gm = BlendGeom<TILE, PPT>;
   constexpr int kRow = GradRow<ANISO>::kFloats;
   __shared__ float4 s_q[Gm::kWarps][32];
@@ -1555,6 +1570,7 @@ __global__ void __launch_bounds__(128) k_layer_runs(ns_curves cv, const CurvePla
                                                     const float4* __restrict__ rec, const int* __restrict__ gcount,
                                                     BinParams bp, int2* runs, int stride, float4* lconst,
                                                     const float2* __restrict__ glo) {
+  grid_dep_wait();
   const int c = blockIdx.x;
   if (!(cv.flags[c] & NS_FILLED)) return;
   const CurvePlan p = plan[c];
@@ -1758,6 +1774,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
                        const float4* __restrict__ prep, const float2* __restrict__ reach,
                        const int* __restrict__ gcurve, const float4* __restrict__ color, BlendParams bp,
                        LayerArgs la, float* image, float* Tfinal, int* nlast, DevState* st) {
+  grid_dep_wait();
   using Gm = BlendGeom<TILE, PPT>;
   constexpr int kPts = LayerGeom<TILE, PPT>::kPts;
   __shared__ float4 s_q[Gm::kWarps][32];     // blend constants, or a layer's first constants
@@ -1988,6 +2005,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
                        const int* __restrict__ gcurve, const float4* __restrict__ color, BlendParams bp,
                        LayerArgs la, const float* __restrict__ dimage, const float* __restrict__ Tfinal,
                        const int* __restrict__ nlast, float* dgauss, DevState* st, int full_grads, float* dcurve) {
+  grid_dep_wait();
   using Gm = BlendGeom<TILE, PPT>;
   constexpr int kRow = 8;
   constexpr int kPts = LayerGeom<TILE, PPT>::kPts;

@@ -231,6 +231,7 @@ __device__ float arc_length_part(const float4* key, const CurveRef& cr, const fl
 __global__ void __launch_bounds__(kPlanThreads, 7) k_plan(ns_curves cv, ns_sample_params sp, CurvePlan* plan,
                                                        float* knots, float* knots_lo, float2* krcp, int* order,
                                                        DevState* st) {
+  grid_dep_wait();
   __shared__ float red[32];
   __shared__ int s_ok;
   __shared__ float sU[kStageKnots];   // the intervals first, then the knot vector (stage_curve)
@@ -402,6 +403,7 @@ __device__ long long block_scan_items(int n, Get get, Put put) {
 }
 
 __global__ void k_scan_boundary(int nc, CurvePlan* plan, DevState* st, long long bcap) {
+  grid_dep_wait();
   const long long tot = block_scan_items(
       nc, [&](int c) { return plan[c].kind == kFill ? plan[c].M : 0; },
       [&](int c, long long off) { plan[c].b_off = int(off); });
@@ -459,6 +461,7 @@ __global__ void __launch_bounds__(256) k_boundary(ns_curves cv, const CurvePlan*
                                                   const float2* __restrict__ krcp,
                                                   const DevState* __restrict__ st, float2* bpts, int* bcurve,
                                                   float4* bloc, long long bcap) {
+  grid_dep_wait();
   const long long nb = min((long long)st->b_count, bcap);
   const int nc = cv.n_curves;
   for (long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x; o < nb;
@@ -506,6 +509,7 @@ __global__ void __launch_bounds__(256) k_boundary(ns_curves cv, const CurvePlan*
 __global__ void __launch_bounds__(256) k_boundary_box(ns_curves cv, ns_sample_params sp, CurvePlan* plan,
                                                       const float* __restrict__ knots, float4* bloc, float2* glo,
                                                       long long bcap, int4* lbox, DevState* st) {
+  grid_dep_wait();
   const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (c == 0 && lane == 0) st->cull_thr = sp.fill_cull;   // the threshold k_fill_sdf counts for
@@ -583,6 +587,7 @@ __global__ void __launch_bounds__(256) k_boundary_box(ns_curves cv, ns_sample_pa
 // can be searched over the one ordered list (see curve_of_task).
 __global__ void k_scan_gauss(int nc, CurvePlan* plan, const int* order, DevState* st, long long gcap,
                              int* g_count_out, int ftile) {
+  grid_dep_wait();
   const long long tot = block_scan_items(
       nc, [&](int f) { return plan[order[f]].count; },
       [&](int f, long long off) { plan[order[f]].g_off = int(off < 0x7fffffff ? off : 0x7fffffff); });
@@ -613,6 +618,7 @@ __global__ void k_scan_gauss(int nc, CurvePlan* plan, const int* order, DevState
 // tasks (fill tasks numbered first, contour tasks after them).
 __global__ void k_task_map(int nc, const CurvePlan* __restrict__ plan, const DevState* __restrict__ st, int* tmap,
                            long long tcap, int ftile) {
+  grid_dep_wait();
   const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (c >= nc) return;
@@ -675,6 +681,7 @@ __global__ void __launch_bounds__(256) k_emit_shape(ns_curves cv, ns_sample_para
                                                     const DevState* __restrict__ st,
                                                     const float4* __restrict__ rec, const int* __restrict__ gcurve,
                                                     float4* shape) {
+  grid_dep_wait();
   const int G = st->g_count;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
     const int c = gcurve[g];
@@ -707,6 +714,7 @@ __global__ void __launch_bounds__(256) k_cluster_boxes(const CurvePlan* __restri
                                                        const float4* __restrict__ bloc,
                                                        const DevState* __restrict__ st, float4* cbox,
                                                        long long bcap, int nc) {
+  grid_dep_wait();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nb = min((long long)st->b_count, bcap);
   if (i >= nb) return;
@@ -750,6 +758,7 @@ __global__ void __launch_bounds__(256, 5) k_emit(ns_curves cv, ns_sample_params 
                                               const int* __restrict__ order, const float* __restrict__ knots,
                                               const DevState* __restrict__ st, float4* rec, int* gcurve, int* gaux,
                                               long long gcap, const int* __restrict__ tmap, long long tcap) {
+  grid_dep_wait();
   const int n_fill = st->n_chunks;
   const int n_tasks = st->n_ctasks;
   const int nc = cv.n_curves;
@@ -858,6 +867,7 @@ __global__ void __launch_bounds__(TE * TE, 2048 / (TE * TE)) k_fill_sdf(ns_curve
                                                      float4* rec, int* gcurve, int* gaux, long long gcap,
                                                      long long bcap, const int* __restrict__ tmap, long long tcap,
                                                      int4* lbox) {
+  grid_dep_wait();
   // The lists and keys alternate between two buffers from task to task: the
   // points of one task clear the other buffer, so a task takes three block
   // barriers (after the lists, after the band, after the points).
