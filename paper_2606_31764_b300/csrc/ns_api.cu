@@ -155,7 +155,7 @@ bool make_layout(const ns_curves* c, const ns_capacity* cap, const ns_raster_par
   L->o_v0 = take(sizeof(uint32_t) * (size_t)L->pcap);
   L->o_k1 = take(sizeof(uint32_t) * (size_t)L->pcap);
   L->o_v1 = take(sizeof(uint32_t) * (size_t)L->pcap);
-  L->o_hist = take(sizeof(uint32_t) * 256 * (size_t)(L->sort_blocks + 1));
+  L->o_hist = take(sizeof(uint32_t) * 256 * (size_t)(L->sort_blocks + kMaxRadixPasses));   // + digit totals
   L->o_ranges = take(sizeof(int2) * (size_t)L->n_tiles);
   L->o_T = take(sizeof(float) * (size_t)L->n_pix);
   L->o_nlast = take(sizeof(int) * (size_t)L->n_pix);

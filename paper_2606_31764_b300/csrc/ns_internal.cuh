@@ -17,6 +17,8 @@ constexpr int kChunk = 256;          // Gaussians per sampling / chain task (one
 constexpr int kFillTileMax = 16;     // a fill task: a T x T tile of its curve's grid, T = 8 or 16
 constexpr int kBinItems = 2048;      // Gaussians per binning block (256 threads x 8)
 constexpr int kSortItems = 4096;     // pairs per radix-sort block (256 threads x 16)
+constexpr int kSortThreads = 256;
+constexpr int kMaxRadixPasses = 4;   // 32 tile bits at 8 bits per pass
 constexpr int kKnotPad = 2 * kMaxP + 1;  // knots per curve = intervals + 2p + 1
 
 enum CurveKind : int { kNone = 0, kOpen = 1, kClosedStroke = 2, kFill = 3 };

@@ -6,7 +6,10 @@
 //                   float32 rule), block sums; with fill layers, the live box
 //                   of every filled curve's grid
 //   k_layer_count   fill layers: each layer's tile count joins its block's sum
-//   k_scan_small    one block: block sums -> block offsets, pair total
+//   k_scan_small    one block: block sums -> block offsets, pair total; zeroes
+//                   the radix sort's digit totals
+//   k_layer_emit    fill layers whose first Gaussian lies in a block of fill
+//                   Gaussians only: their pairs, one block per curve
 //   k_bin_emit      recount, block-local scan, write (tile, Gaussian) pairs in
 //                   Gaussian order, which is front to back inside each scene
 //                   (a fill layer: one pair per tile of its live grid box)
@@ -15,6 +18,8 @@
 //                   constants
 //   k_radix_hist / k_radix_scan / k_radix_scatter
 //                   stable LSD radix sort of the pairs on the tile id bits
+//                   (per pass: digit counts per block of 4096 pairs and the
+//                   digit totals, their scan, the stable scatter)
 //                   only: pairs enter in (layer, sample) order, so a stable sort
 //                   by tile yields the full (tile, layer, sample) order
 //   k_ranges        [start, end) of every tile's run
@@ -384,16 +389,18 @@ __global__ void k_layer_count(ns_curves cv, const CurvePlan* __restrict__ plan, 
 }
 
 // The pairs of the fill layers whose first Gaussian lies in a binning block of
-// fill Gaussians only (k_bin_emit leaves those blocks out), one thread per
-// curve: after the pairs of the layers that start earlier in the same block
-// (the curves before it in front-to-back order), in the pair order k_bin_emit
-// would give them.
-__global__ void k_layer_emit(ns_curves cv, const CurvePlan* __restrict__ plan, const float4* __restrict__ rec,
-                             const int* __restrict__ gcount, const int* __restrict__ curve_scene, BinParams bp,
-                             const int* __restrict__ boff, const int* __restrict__ order, uint32_t* keys,
-                             uint32_t* vals, long long pcap, const DevState* st) {
+// fill Gaussians only (k_bin_emit leaves those blocks out), one block per
+// curve, a pair per thread: after the pairs of the layers that start earlier
+// in the same binning block (the curves before it in front-to-back order), in
+// the pair order k_bin_emit would give them.
+__global__ void __launch_bounds__(128) k_layer_emit(ns_curves cv, const CurvePlan* __restrict__ plan,
+                                                    const float4* __restrict__ rec, const int* __restrict__ gcount,
+                                                    const int* __restrict__ curve_scene, BinParams bp,
+                                                    const int* __restrict__ boff, const int* __restrict__ order,
+                                                    uint32_t* keys, uint32_t* vals, long long pcap,
+                                                    const DevState* st) {
   grid_dep_wait();
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.x;
   if (c >= cv.n_curves || !sampled_boxes(bp, st)) return;
   const int nt = bp.lcount[c];
   if (nt <= 0) return;
@@ -418,16 +425,17 @@ __global__ void k_layer_emit(ns_curves cv, const CurvePlan* __restrict__ plan, c
   layer_rect_live(rec, p, G, bp, c, x0, y0, nx);
   const int sbase = curve_scene[c] * bp.tiles_per_scene;
   const uint32_t val = uint32_t(p.g_off) | kLayerBit;
-  for (int j = 0; j < nt; ++j, ++off) {
-    if (off >= pcap) break;
-    keys[off] = uint32_t(sbase + (y0 + j / nx) * bp.tiles_x + x0 + j % nx);
-    vals[off] = val;
+  for (int j = threadIdx.x; j < nt && off + j < pcap; j += blockDim.x) {
+    const int jy = j / nx;
+    keys[off + j] = uint32_t(sbase + (y0 + jy) * bp.tiles_x + x0 + (j - jy * nx));
+    vals[off + j] = val;
   }
 }
 
 __global__ void k_scan_small(int* vals, const int* gcount, int gcap, int items_per_block, DevState* st,
-                             long long cap) {
+                             long long cap, uint32_t* zero, int nzero) {
   grid_dep_wait();
+  for (int i = threadIdx.x; i < nzero; i += blockDim.x) zero[i] = 0u;   // the radix sort's digit totals
   __shared__ long long s_warp[32];
   __shared__ long long s_carry;
   const int G = min(*gcount, gcap);
@@ -546,9 +554,13 @@ __global__ void __launch_bounds__(256) k_bin_emit(const float4* __restrict__ rec
 // ---------------------------------------------------------------------------
 // stable LSD radix sort of (tile, Gaussian) pairs on the tile bits
 
-__global__ void __launch_bounds__(256) k_radix_hist(const uint32_t* __restrict__ keys, const DevState* st, int shift,
-                                                    int bits, uint32_t* hist) {
+// Per sort block, the count of each digit (digit-major: hist[digit][block]);
+// the digit totals over all blocks are added to totals[digit] (zeroed by
+// k_scan_small).
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __restrict__ keys, const DevState* st,
+                                                             int shift, int bits, uint32_t* hist, uint32_t* totals) {
   grid_dep_wait();
+  constexpr int kPer = kSortItems / kSortThreads;
   __shared__ uint32_t h[256];
   const int n = st->pair_count;
   const int nb = (n + kSortItems - 1) / kSortItems;
@@ -556,22 +568,31 @@ __global__ void __launch_bounds__(256) k_radix_hist(const uint32_t* __restrict__
   // sort blocks of kSortItems pairs, grid-stride (the grid is sized by the
   // capacity, the pairs are known on the device only)
   for (int vb = blockIdx.x; vb < nb; vb += gridDim.x) {
-    for (int d = threadIdx.x; d < nd; d += blockDim.x) h[d] = 0;
-    __syncthreads();
-    const long long base = (long long)vb * kSortItems;
-    for (int k = threadIdx.x; k < kSortItems; k += blockDim.x) {
-      const long long i = base + k;
-      if (i < n) atomicAdd(&h[(keys[i] >> shift) & (nd - 1)], 1u);
+    for (int d = threadIdx.x; d < nd; d += kSortThreads) h[d] = 0;
+    const long long base = (long long)vb * kSortItems + threadIdx.x;
+    uint32_t kk[kPer];   // every load in flight before the first count
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+      const long long i = base + r * kSortThreads;
+      kk[r] = i < n ? keys[i] : 0u;
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < nd; d += blockDim.x) hist[(long long)d * nb + vb] = h[d];
+#pragma unroll
+    for (int r = 0; r < kPer; ++r)
+      if (base + r * kSortThreads < n) atomicAdd(&h[(kk[r] >> shift) & (nd - 1)], 1u);
+    __syncthreads();
+    for (int d = threadIdx.x; d < nd; d += kSortThreads) {
+      const uint32_t c = h[d];
+      hist[(long long)d * nb + vb] = c;
+      if (c) atomicAdd(&totals[d], c);
+    }
     __syncthreads();
   }
 }
 
-// Exclusive scan of the digit-major histogram hist[digit][block], in two
-// parallel steps: one block per digit sums its row, then one block per digit
-// scans its row starting from the total of all smaller digits.
+// Exclusive scan of the digit-major histogram hist[digit][block]: one block
+// per digit scans its row, starting from the total of all smaller digits
+// (totals, from k_radix_hist).
 __device__ __forceinline__ uint32_t block_sum_u32(uint32_t v, uint32_t* s_warp) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = v;
@@ -580,18 +601,6 @@ __device__ __forceinline__ uint32_t block_sum_u32(uint32_t v, uint32_t* s_warp) 
   for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_warp[w];
   __syncthreads();
   return t;
-}
-
-__global__ void __launch_bounds__(256) k_radix_totals(const uint32_t* __restrict__ hist, const DevState* st,
-                                                      uint32_t* totals) {
-  grid_dep_wait();
-  __shared__ uint32_t s_warp[8];
-  const int nb = (st->pair_count + kSortItems - 1) / kSortItems;
-  const uint32_t* row = hist + (long long)blockIdx.x * nb;
-  uint32_t v = 0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) v += row[b];
-  const uint32_t t = block_sum_u32(v, s_warp);
-  if (threadIdx.x == 0) totals[blockIdx.x] = t;
 }
 
 __global__ void __launch_bounds__(256) k_radix_scan(uint32_t* hist, const DevState* st,
@@ -636,12 +645,12 @@ __global__ void __launch_bounds__(256) k_radix_scan(uint32_t* hist, const DevSta
 
 // Each warp ranks its 512 consecutive pairs in 16 rounds of 32 with
 // __match_any_sync; per-warp digit counters keep the order stable.
-__global__ void __launch_bounds__(256) k_radix_scatter(const uint32_t* __restrict__ kin,
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* __restrict__ kin,
                                                        const uint32_t* __restrict__ vin, uint32_t* kout,
                                                        uint32_t* vout, const uint32_t* __restrict__ hist,
                                                        const DevState* st, int shift, int bits) {
   grid_dep_wait();
-  constexpr int kWarps = 8, kPerWarp = kSortItems / kWarps, kRounds = kPerWarp / 32;
+  constexpr int kWarps = kSortThreads / 32, kPerWarp = kSortItems / kWarps, kRounds = kPerWarp / 32;
   __shared__ uint32_t wcnt[kWarps][256];
   __shared__ uint32_t dstart[256];        // first position of each digit in the block's sorted order
   __shared__ uint32_t gbase[256];         // global position of each digit's first item of this block
@@ -661,12 +670,19 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const uint32_t* __restric
     const long long base = blk0 + (long long)w * kPerWarp;
     uint32_t key[kRounds], val[kRounds];
     uint32_t rank[kRounds];
+    // every load in flight first: the rounds below are separated by
+    // __syncwarp, which would hold each round's loads back until the last
 #pragma unroll
     for (int r = 0; r < kRounds; ++r) {
       const long long i = base + r * 32 + lane;
       const bool ok = i < n;
       key[r] = ok ? kin[i] : 0u;
       val[r] = ok ? vin[i] : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+      const long long i = base + r * 32 + lane;
+      const bool ok = i < n;
       const uint32_t d = ok ? (key[r] >> shift) & (nd - 1) : 0xffffffffu;
       const uint32_t peers = __match_any_sync(0xffffffffu, d);
       const uint32_t below = peers & ((1u << lane) - 1u);
@@ -2577,7 +2593,7 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
   uint32_t* k1 = at<uint32_t>(ws, L.o_k1);
   uint32_t* v1 = at<uint32_t>(ws, L.o_v1);
   uint32_t* hist = at<uint32_t>(ws, L.o_hist);
-  uint32_t* totals = hist + 256 * (size_t)L.sort_blocks;   // the layout's spare 256 entries
+  uint32_t* totals = hist + 256 * (size_t)L.sort_blocks;   // 256 per radix pass, after the histogram
   int2* ranges = at<int2>(ws, L.o_ranges);
   float* Tf = at<float>(ws, L.o_T);
   int* nl = at<int>(ws, L.o_nlast);
@@ -2622,9 +2638,10 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
   if (bp.fill_layers && L.nc > 0 && bin_blocks > 0)
     NS_LAUNCH(NS_KERNEL_OTHER, k_layer_count, (L.nc + 127) / 128, 128, 0, s, *curves, plan, rec, g->count, bp, bsum,
               st);
-  NS_LAUNCH(NS_KERNEL_SCAN, k_scan_small, 1, 1024, 0, s, bsum, g->count, int(L.gcap), kBinItems, st, cap->pairs);
+  NS_LAUNCH(NS_KERNEL_SCAN, k_scan_small, 1, 1024, 0, s, bsum, g->count, int(L.gcap), kBinItems, st, cap->pairs,
+            totals, 256 * kMaxRadixPasses);
   if (bp.fill_layers && L.nc > 0 && bin_blocks > 0)
-    NS_LAUNCH(NS_KERNEL_OTHER, k_layer_emit, (L.nc + 127) / 128, 128, 0, s, *curves, plan, rec, g->count,
+    NS_LAUNCH(NS_KERNEL_OTHER, k_layer_emit, L.nc, 128, 0, s, *curves, plan, rec, g->count,
               curve_scene, bp, bsum, at<const int>(ws, L.o_order), k0, v0, cap->pairs, st);
   if (bin_blocks > 0) {
     auto ke = aniso ? &k_bin_emit<true> : &k_bin_emit<false>;
@@ -2638,11 +2655,12 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
   for (int pass = 0; pass < rpn.passes; ++pass) {
     const int shift = pass * rpn.bits_per_pass;
     if (sort_blocks > 0) {
-      NS_LAUNCH(NS_KERNEL_RADIX_HIST, k_radix_hist, sort_grid, 256, 0, s, kin, st, shift, rpn.bits_per_pass, hist);
-      NS_LAUNCH(NS_KERNEL_SCAN, k_radix_totals, 1 << rpn.bits_per_pass, 256, 0, s, hist, st, totals);
-      NS_LAUNCH(NS_KERNEL_SCAN, k_radix_scan, 1 << rpn.bits_per_pass, 256, 0, s, hist, st, totals);
-      NS_LAUNCH(NS_KERNEL_RADIX_SCATTER, k_radix_scatter, sort_grid, 256, 0, s, kin, vin, kout, vout, hist, st, shift,
-                rpn.bits_per_pass);
+      uint32_t* tot = totals + 256 * pass;
+      NS_LAUNCH(NS_KERNEL_RADIX_HIST, k_radix_hist, sort_grid, kSortThreads, 0, s, kin, st, shift,
+                rpn.bits_per_pass, hist, tot);
+      NS_LAUNCH(NS_KERNEL_SCAN, k_radix_scan, 1 << rpn.bits_per_pass, 256, 0, s, hist, st, tot);
+      NS_LAUNCH(NS_KERNEL_RADIX_SCATTER, k_radix_scatter, sort_grid, kSortThreads, 0, s, kin, vin, kout, vout, hist,
+                st, shift, rpn.bits_per_pass);
     }
     std::swap(kin, kout);
     std::swap(vin, vout);

@@ -402,6 +402,58 @@ __device__ long long block_scan_items(int n, Get get, Put put) {
   return s_carry;
 }
 
+// K exclusive scans over the same items in one sweep of a single block:
+// get(i, v) gives item i's K values, put(i, off) receives their K offsets,
+// tot the K totals.
+template <int K, class Get, class Put>
+__device__ void block_scan_multi(int n, Get get, Put put, long long tot[K]) {
+  __shared__ long long s_carry[K];
+  __shared__ long long s_warp[K][32];
+  if (threadIdx.x < K) s_carry[threadIdx.x] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int base = 0; base < n; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    long long v[K], x[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = 0;
+    if (i < n) get(i, v);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      x[k] = v[k];
+      for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, x[k], o);
+        if (lane >= o) x[k] += y;
+      }
+      if (lane == 31) s_warp[k][w] = x[k];
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        long long t = lane < nw ? s_warp[k][lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+          const long long y = __shfl_up_sync(0xffffffffu, t, o);
+          if (lane >= o) t += y;
+        }
+        if (lane < nw) s_warp[k][lane] = t;
+      }
+    }
+    __syncthreads();
+    long long off[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) off[k] = s_carry[k] + (w > 0 ? s_warp[k][w - 1] : 0) + x[k] - v[k];
+    if (i < n) put(i, off);
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1)
+#pragma unroll
+      for (int k = 0; k < K; ++k) s_carry[k] = off[k] + v[k];
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) tot[k] = s_carry[k];
+}
+
 __global__ void k_scan_boundary(int nc, CurvePlan* plan, DevState* st, long long bcap) {
   grid_dep_wait();
   const long long tot = block_scan_items(
@@ -588,21 +640,26 @@ __global__ void __launch_bounds__(256) k_boundary_box(ns_curves cv, ns_sample_pa
 __global__ void k_scan_gauss(int nc, CurvePlan* plan, const int* order, DevState* st, long long gcap,
                              int* g_count_out, int ftile) {
   grid_dep_wait();
-  const long long tot = block_scan_items(
-      nc, [&](int f) { return plan[order[f]].count; },
-      [&](int f, long long off) { plan[order[f]].g_off = int(off < 0x7fffffff ? off : 0x7fffffff); });
-  const long long ftasks = block_scan_items(
-      nc, [&](int f) { const CurvePlan& q = plan[order[f]]; return q.kind == kFill ? fill_task_count(q.nx, q.ny, ftile) : 0; },
-      [&](int f, long long off) {
+  // three scans in front-to-back order: Gaussians, fill tasks, contour tasks;
+  // a curve's own tasks start at chunk_off, pad[0] holds the other kind's
+  // offset (the search of curve_of_task)
+  long long t3[3];
+  block_scan_multi<3>(
+      nc,
+      [&](int f, long long v[3]) {
+        const CurvePlan& q = plan[order[f]];
+        v[0] = q.count;
+        v[1] = q.kind == kFill ? fill_task_count(q.nx, q.ny, ftile) : 0;
+        v[2] = q.kind != kFill ? (q.count + kChunk - 1) / kChunk : 0;
+      },
+      [&](int f, const long long off[3]) {
         CurvePlan& q = plan[order[f]];
-        if (q.kind == kFill) q.chunk_off = int(off); else q.pad[0] = int(off);
-      });
-  const long long ctasks = block_scan_items(
-      nc, [&](int f) { const CurvePlan& q = plan[order[f]]; return q.kind != kFill ? (q.count + kChunk - 1) / kChunk : 0; },
-      [&](int f, long long off) {
-        CurvePlan& q = plan[order[f]];
-        if (q.kind != kFill) q.chunk_off = int(off); else q.pad[0] = int(off);
-      });
+        q.g_off = int(off[0] < 0x7fffffff ? off[0] : 0x7fffffff);
+        q.chunk_off = int(q.kind == kFill ? off[1] : off[2]);
+        q.pad[0] = int(q.kind == kFill ? off[2] : off[1]);
+      },
+      t3);
+  const long long tot = t3[0], ftasks = t3[1], ctasks = t3[2];
   if (threadIdx.x == 0) {
     st->g_total = (unsigned long long)tot;
     const int gc = int(tot < gcap ? tot : gcap);
