@@ -18,6 +18,7 @@ constexpr int kFillTileMax = 16;     // a fill task: a T x T tile of its curve's
 constexpr int kBinItems = 2048;      // Gaussians per binning block (256 threads x 8)
 constexpr int kSortItems = 4096;     // pairs per radix-sort block (256 threads x 16)
 constexpr int kSortThreads = 256;
+constexpr int kFormStride = 20;      // floats per span Taylor form row (19 used at degree 5)
 constexpr int kMaxRadixPasses = 4;   // 32 tile bits at 8 bits per pass
 constexpr int kKnotPad = 2 * kMaxP + 1;  // knots per curve = intervals + 2p + 1
 
@@ -96,6 +97,7 @@ struct Layout {
   size_t o_lcount = 0;       // per curve: tile pairs of its fill layer (splat_forward)
   size_t o_krcp = 0;         // per knot slot k and width j = 1..kMaxP: 1 / (U[k + j] - U[k]) as {hi, lo} (filled curves)
   int64_t tcap = 0;          // entries of that table
+  size_t o_forms = 0;        // per knot slot: the Taylor form {m, A[0..p][3]} of the span it starts (20 floats)
 };
 
 // Host helpers (ns_api.cu).

@@ -1,8 +1,12 @@
 // nurbs_sample: curves -> Gaussians (paper §3.1-§3.3).
 //
 // Kernels, in launch order:
-//   k_plan          one block per curve: validation, knot vector (FP64 running
-//                   sum, stored as FP32 high and low parts), arc length by N_L-node midpoint
+//   k_plan_forms    one block per curve: validation, scene order, knot vector
+//                   (exact running sum stored as FP32 high and low parts);
+//                   then one thread per span: the span's Taylor form of the
+//                   rational curve (Eq. 1), and reciprocals of knot
+//                   differences for filled curves
+//   k_plan_length   one block per curve: arc length by N_L-node midpoint
 //                   quadrature of |C'| (Eq. 2-3, block reduction), counts
 //   k_scan_boundary one block: boundary-point offsets of filled curves
 //   k_boundary      one thread per boundary point b_i of the filled curves,
@@ -30,7 +34,7 @@ namespace ns {
 // unevaluated sum hi + lo of two floats (about 48 significant bits), built
 // from the error-free transformations TwoSum (Knuth) and TwoProduct (Dekker;
 // here with the fused multiply-add, as Ogita, Rump and Oishi write it).  The
-// knot vector (the same sums as k_plan), the parameters, the Cox-de Boor
+// knot vector (the same sums as k_plan_forms), the parameters, the Cox-de Boor
 // triangle and the rational quotient of Eq. 1 all carry that precision.
 // FP32 evaluation at pixel coordinates near 1000 has errors of about 1e-4 px,
 // which the grid origin and, through the sigmoid of Eq. 7, the fill opacities
@@ -114,31 +118,6 @@ __device__ __forceinline__ float block_reduce_minmax(float v, float* red, bool i
   return red[0];
 }
 
-// Copies a curve's knots and key points into shared memory when they fit;
-// returns the pointers (and key offset) the evaluator should use.
-constexpr int kStageKnots = 1024, kStageKeys = 1024;
-
-struct Staged {
-  const float4* key;
-  const float* U;
-  CurveRef cr;
-};
-
-__device__ __forceinline__ Staged stage_curve(const ns_curves& cv, CurveRef cr, const float* U, float* sU,
-                                              float4* sK) {
-  const int nkn = cr.ntau + 2 * cr.p + 1;
-  if (nkn > kStageKnots || cr.nk > kStageKeys) {
-    __syncthreads();
-    return Staged{reinterpret_cast<const float4*>(cv.key), U, cr};
-  }
-  const float4* key = reinterpret_cast<const float4*>(cv.key) + cr.key0;
-  for (int i = threadIdx.x; i < nkn; i += blockDim.x) sU[i] = U[i];
-  for (int i = threadIdx.x; i < cr.nk; i += blockDim.x) sK[i] = key[i];
-  __syncthreads();
-  cr.key0 = 0;
-  return Staged{sK, sU, cr};
-}
-
 // |C'_xy(u)| (Eq. 2) from the span's Taylor form: C = S/W, C' = (S' - C W')/W.
 template <int P>
 __device__ __forceinline__ float span_speed(const SpanPoly<P>& sp, float u) {
@@ -159,97 +138,95 @@ __device__ __forceinline__ float span_speed(const SpanPoly<P>& sp, float u) {
   return sqrtf(dx * dx + dy * dy);
 }
 
-// Each thread sums a contiguous run of the N_L midpoint nodes (Eq. 3).  With at
-// most kSmemSpans spans the block first builds every span's Taylor form once
-// (one thread per span) in shared memory; otherwise each thread builds the form
-// whenever its run enters a new span.
-constexpr int kSmemSpans = 128;
+// The Taylor form {m, A[0..P][3]} of every non-empty span of every curve, one
+// row of kFormStride floats per knot slot (the row of the knot that starts
+// the span), written by k_plan_forms and read by the arc-length nodes.
+static_assert(kFormStride >= 1 + 3 * (kMaxP + 1), "a span form row holds m and A[0..p][3]");
 
 template <int P>
-__device__ float arc_length_part(const float4* key, const CurveRef& cr, const float* U, float a, float b, int NL,
-                                 float* s_poly) {
+__device__ __forceinline__ void load_form(const float* __restrict__ d, SpanPoly<P>& sp) {
+  sp.m = d[0];
+#pragma unroll
+  for (int k = 0; k <= P; ++k) {
+    sp.A[k][0] = d[1 + 3 * k];
+    sp.A[k][1] = d[2 + 3 * k];
+    sp.A[k][2] = d[3 + 3 * k];
+  }
+}
+
+// Each thread sums a contiguous run of the N_L midpoint nodes (Eq. 3),
+// loading a span's form whenever its run enters that span.
+template <int P>
+__device__ float arc_length_part(const float* __restrict__ forms, const CurveRef& cr, const float* __restrict__ U,
+                                 float a, float b, int NL) {
   const float du = (b - a) / float(NL);
   const int per = (NL + blockDim.x - 1) / blockDim.x;
   const int j0 = threadIdx.x * per, j1 = min(NL, j0 + per);
-  const int nspan = cr.n - P + 1;
-  constexpr int kPoly = 1 + 3 * (P + 1);   // {m, A[0..P][3]}
+  const float* F = forms + (long long)cr.knot0 * kFormStride;   // knot0 = 0 when forms is the curve's own
   float acc = 0.f;
   SpanPoly<P> sp;
-  if (nspan <= kSmemSpans) {
-    for (int sidx = threadIdx.x; sidx < nspan; sidx += blockDim.x) {
-      const int i = P + sidx;
-      if (!(U[i] < U[i + 1])) continue;   // empty span: never the span of a node
-      span_poly<P>(key, cr, U, i, sp);
-      float* d = s_poly + sidx * kPoly;
-      d[0] = sp.m;
-#pragma unroll
-      for (int k = 0; k <= P; ++k) {
-        d[1 + 3 * k] = sp.A[k][0];
-        d[2 + 3 * k] = sp.A[k][1];
-        d[3 + 3 * k] = sp.A[k][2];
-      }
-    }
-    __syncthreads();
-    int span = -1;
-    float hi = 0.f;
-    for (int j = j0; j < j1; ++j) {
-      const float u = a + (float(j) + 0.5f) * du;
-      if (span < 0 || !(u < hi)) {
-        span = find_span(U, P, cr.n, u);
-        hi = span < cr.n ? U[span + 1] : 3.0e38f;
-        const float* d = s_poly + (span - P) * kPoly;
-        sp.m = d[0];
-#pragma unroll
-        for (int k = 0; k <= P; ++k) {
-          sp.A[k][0] = d[1 + 3 * k];
-          sp.A[k][1] = d[2 + 3 * k];
-          sp.A[k][2] = d[3 + 3 * k];
-        }
-      }
-      acc += span_speed<P>(sp, u);
-    }
-    return acc * du;
-  }
   int span = -1;
   float hi = 0.f;
   for (int j = j0; j < j1; ++j) {
     const float u = a + (float(j) + 0.5f) * du;
     if (span < 0 || !(u < hi)) {
-      const int i = find_span(U, P, cr.n, u);
-      if (i != span) {
-        span = i;
-        span_poly<P>(key, cr, U, i, sp);
-        hi = i < cr.n ? U[i + 1] : 3.0e38f;
-      }
+      span = find_span(U, P, cr.n, u);
+      hi = span < cr.n ? U[span + 1] : 3.0e38f;
+      load_form<P>(F + (long long)span * kFormStride, sp);
     }
     acc += span_speed<P>(sp, u);
   }
   return acc * du;
 }
 
-// One block per curve.
-__global__ void __launch_bounds__(kPlanThreads, 7) k_plan(ns_curves cv, ns_sample_params sp, CurvePlan* plan,
-                                                       float* knots, float* knots_lo, float2* krcp, int* order,
-                                                       DevState* st) {
+// k_plan_forms: one block per curve.  Thread 0 validates the curve, places it
+// in its scene's front-to-back order and builds the knot vector (§3.1: open
+// -> p zero intervals on both sides; closed -> the last p core intervals
+// before, the first p after; cumulative sum from 0) as an exact running sum
+// kept as FP32 high and low parts.  Then, one thread per span, the Taylor
+// form of the rational curve on each non-empty span (span_poly), and for
+// filled curves the reciprocals of the knot differences of widths 1..p
+// (k_boundary).
+constexpr int kFormThreads = 64;
+constexpr int kTauStage = 1024;   // intervals staged (longer curves read them from global memory)
+
+template <int P>
+__device__ void span_forms(const float4* key, const CurveRef& cr, const float* U, float* F) {
+  const int nspan = cr.n - P + 1;
+  for (int sidx = threadIdx.x; sidx < nspan; sidx += blockDim.x) {
+    const int i = P + sidx;
+    if (!(U[i] < U[i + 1])) continue;   // empty span: never the span of a node
+    SpanPoly<P> sp;
+    span_poly<P>(key, cr, U, i, sp);
+    float* d = F + (long long)i * kFormStride;
+    d[0] = sp.m;
+#pragma unroll
+    for (int k = 0; k <= P; ++k) {
+      d[1 + 3 * k] = sp.A[k][0];
+      d[2 + 3 * k] = sp.A[k][1];
+      d[3 + 3 * k] = sp.A[k][2];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kFormThreads) k_plan_forms(ns_curves cv, CurvePlan* plan, float* knots,
+                                                             float* knots_lo, float2* krcp, int* order,
+                                                             DevState* st, float* forms) {
   grid_dep_wait();
-  __shared__ float red[32];
+  __shared__ float s_tau[kTauStage];
   __shared__ int s_ok;
-  __shared__ float sU[kStageKnots];   // the intervals first, then the knot vector (stage_curve)
-  __shared__ float4 sK[kStageKeys];
-  float* s_tau = sU;
   const int c = blockIdx.x;
   const CurveRef cr = curve_ref(cv, c);
   float* U = knots + cr.knot0;
-  // the intervals go to shared memory first (all threads), so that the serial
-  // cumulative sum below reads them without a global-memory round trip each
+  float* Ulo = knots_lo + cr.knot0;
   const int t0 = cv.tau_offset[c];
-  const bool tau_staged = cr.ntau >= 0 && cr.ntau <= kStageKnots && t0 >= 0 && cv.tau_offset[c + 1] <= cv.n_taus;
+  const bool tau_staged = cr.ntau >= 0 && cr.ntau <= kTauStage && t0 >= 0 && cv.tau_offset[c + 1] <= cv.n_taus;
   if (tau_staged)
     for (int q = threadIdx.x; q < cr.ntau; q += blockDim.x) s_tau[q] = cv.tau[t0 + q];
   __syncthreads();
   if (threadIdx.x == 0) {
-    int ok = cr.p >= 1 && cr.p <= kMaxP && cr.key0 >= 0 && cr.nk >= 0 && cv.tau_offset[c] >= 0 &&
-             cr.ntau >= 0 && cv.key_offset[c + 1] <= cv.n_keys && cv.tau_offset[c + 1] <= cv.n_taus;
+    int ok = cr.p >= 1 && cr.p <= kMaxP && cr.key0 >= 0 && cr.nk >= 0 && t0 >= 0 && cr.ntau >= 0 &&
+             cv.key_offset[c + 1] <= cv.n_keys && cv.tau_offset[c + 1] <= cv.n_taus;
     if (ok) ok = cr.closed ? (cr.nk >= cr.p && cr.nk >= 2 && cr.ntau == cr.nk)
                            : (cr.nk >= cr.p + 1 && cr.ntau == cr.nk - cr.p);
     if (ok && cr.filled && !cr.closed) ok = 0;
@@ -268,28 +245,26 @@ __global__ void __launch_bounds__(kPlanThreads, 7) k_plan(ns_curves cv, ns_sampl
     if (s0 <= c && c < s1 && s1 <= cv.n_curves) order[s0 + (s1 - 1 - c)] = c;
     else ok = 0;   // inconsistent scene offsets
     plan[c].scene = s;
-    // knot vector (§3.1): open -> p zero intervals on both sides; closed ->
-    // last p core intervals before, first p after; cumulative sum from 0.
     if (ok) {
-      const float* tau = tau_staged ? s_tau : cv.tau + cv.tau_offset[c];
+      const float* tau = tau_staged ? s_tau : cv.tau + t0;
       const int p = cr.p, nt = cr.ntau;
       const int n_int = nt + 2 * p;
       // exact running sum as hi + lo: TwoSum keeps each addition's rounding
       // error, which the low part collects (the sums of float intervals need
       // far fewer than 48 bits)
-      float acc_h = 0.f, acc_l = 0.f;
-      float* Ulo = knots_lo + cr.knot0;
+      float acc_h = 0.f, acc_l = 0.f, u_p = 0.f, u_end = 0.f;
       U[0] = 0.f;
       Ulo[0] = 0.f;
+      // the interval of step q: open curves pad with zeros, closed curves
+      // wrap (from interval nt - p on, modulo nt)
+      int k = cr.closed ? ((nt - p) % nt + nt) % nt : 0;
       for (int q = 0; q < n_int; ++q) {
         float v;
         if (!cr.closed) {
           v = (q < p || q >= p + nt) ? 0.f : tau[q - p];
         } else {
-          int k = q < p ? nt - p + q : (q < p + nt ? q - p : q - p - nt);
-          k %= nt;
-          if (k < 0) k += nt;
           v = tau[k];
+          if (++k == nt) k = 0;
         }
         if (!(v >= 0.f)) ok = 0;   // negative or NaN interval
         const df t = df_two_sum(acc_h, v);
@@ -298,69 +273,98 @@ __global__ void __launch_bounds__(kPlanThreads, 7) k_plan(ns_curves cv, ns_sampl
         const df u = df_fast_two_sum(acc_h, acc_l);
         U[q + 1] = u.h;
         Ulo[q + 1] = u.l;
+        if (q + 1 == p) u_p = u.h;
+        if (q + 1 == cr.n + 1) u_end = u.h;
       }
-      if (ok && !(U[cr.n + 1] > U[p])) ok = 0;   // empty domain
+      if (ok && !(u_end > u_p)) ok = 0;   // empty domain
     }
     if (!ok) {
       atomicCAS(&st->bad_curve, -1, c);
       raise_status(st, NS_ERR_INVALID_CURVE);
-    }
-    s_ok = ok;
-  }
-  __syncthreads();
-  if (s_ok && cr.filled) {
-    // reciprocals of the knot differences of width 1..p (double-float), for
-    // the boundary points' Cox-de Boor triangle (k_boundary)
-    const int nkn = cr.ntau + 2 * cr.p + 1;
-    const float* Uh = U;
-    const float* Ul = knots_lo + cr.knot0;
-    float2* rc = krcp + (long long)kMaxP * cr.knot0;
-    for (int q = threadIdx.x; q < cr.p * nkn; q += blockDim.x) {
-      const int j = q / nkn + 1, k = q - (j - 1) * nkn;
-      const df d = k + j < nkn ? df_sub(df{Uh[k + j], Ul[k + j]}, df{Uh[k], Ul[k]}) : df{0.f, 0.f};
-      const df r = d.h > 0.f ? df_rcp(d) : df{0.f, 0.f};
-      rc[(j - 1) * nkn + k] = make_float2(r.h, r.l);
-    }
-  }
-  CurvePlan pl;
-  if (!s_ok) {
-    if (threadIdx.x == 0) {
       plan[c].kind = kNone;
       plan[c].count = 0;
       plan[c].M = 0;
       plan[c].L = 0.f;
+    } else {
+      plan[c].kind = cr.filled ? kFill : (cr.closed ? kClosedStroke : kOpen);
     }
-    return;
+    s_ok = ok;
+  }
+  __syncthreads();   // thread 0's knots are visible to the block
+  if (!s_ok) return;
+  const float4* key = reinterpret_cast<const float4*>(cv.key);
+  NS_DISPATCH_P(cr.p, span_forms<P>(key, cr, U, forms + (long long)cr.knot0 * kFormStride));
+  if (cr.filled) {
+    // reciprocals of the knot differences of width 1..p (double-float), for
+    // the boundary points' Cox-de Boor triangle
+    const int nkn = cr.ntau + 2 * cr.p + 1;
+    float2* rc = krcp + (long long)kMaxP * cr.knot0;
+    for (int q = threadIdx.x; q < cr.p * nkn; q += blockDim.x) {
+      const int j = q / nkn + 1, kk = q - (j - 1) * nkn;
+      const df d = kk + j < nkn ? df_sub(df{U[kk + j], Ulo[kk + j]}, df{U[kk], Ulo[kk]}) : df{0.f, 0.f};
+      const df r = d.h > 0.f ? df_rcp(d) : df{0.f, 0.f};
+      rc[(j - 1) * nkn + kk] = make_float2(r.h, r.l);
+    }
+  }
+}
+
+// k_plan_length: one block per valid curve: the arc length by the N_L-node
+// midpoint rule of Eq. 3 on the span forms (block reduction), then the
+// counts (§3.2, §3.3).  The curve's knots and forms are staged in shared
+// memory when they fit.
+constexpr int kLenStage = 128;   // knots (and span rows) staged per curve
+
+__global__ void __launch_bounds__(kPlanThreads, 8) k_plan_length(ns_curves cv, ns_sample_params sp, CurvePlan* plan,
+                                                                 const float* __restrict__ knots,
+                                                                 const float* __restrict__ forms) {
+  grid_dep_wait();
+  __shared__ float red[32];
+  __shared__ float sU[kLenStage];
+  __shared__ float sF[kLenStage * kFormStride];
+  const int c = blockIdx.x;
+  const int kind = plan[c].kind;
+  if (kind == kNone) return;
+  CurveRef cr = curve_ref(cv, c);
+  const float* U = knots + cr.knot0;
+  const float* F = forms + (long long)cr.knot0 * kFormStride;
+  const int nkn = cr.ntau + 2 * cr.p + 1;
+  if (nkn <= kLenStage) {   // spans p..n < nkn
+    for (int q = threadIdx.x; q < nkn; q += blockDim.x) sU[q] = U[q];
+    // the rows of spans p..n (the others are never read)
+    const int f0 = cr.p * kFormStride, f1 = (cr.n + 1) * kFormStride;
+    for (int q = f0 + threadIdx.x; q < f1; q += blockDim.x) sF[q] = F[q];
+    __syncthreads();
+    U = sU;
+    F = sF;
   }
   const float a = U[cr.p], b = U[cr.n + 1];
   const int NL = sp.nl_mult * max(cv.width, cv.height);
-  const Staged sg = stage_curve(cv, cr, U, sU, sK);
   float part = 0.f;
-  __shared__ float s_poly[kSmemSpans * (1 + 3 * (kMaxP + 1))];
-  NS_DISPATCH_P(cr.p, part = arc_length_part<P>(sg.key, sg.cr, sg.U, a, b, NL, s_poly));
+  cr.knot0 = 0;   // F is the curve's own table
+  NS_DISPATCH_P(cr.p, part = arc_length_part<P>(F, cr, U, a, b, NL));
   const float L = block_sum(part, red);
   if (threadIdx.x == 0) {
+    CurvePlan pl;
     pl.L = L;
     pl.a = a;
     pl.b = b;
     pl.x0 = pl.y0 = 0.f;
     pl.nx = pl.ny = 0;
     pl.h = 0.f;
-    if (cr.filled) {
-      pl.kind = kFill;
+    pl.kind = kind;
+    if (kind == kFill) {
       pl.M = max(3, int(ceilf(sp.delta_b * L)));
       pl.count = 0;   // set by k_boundary_box
-    } else if (cr.closed) {
-      pl.kind = kClosedStroke;
+    } else if (kind == kClosedStroke) {
       pl.M = max(1, int(ceilf(sp.delta_c * L)));
       pl.count = pl.M;
     } else {
-      pl.kind = kOpen;
       pl.M = max(2, int(ceilf(sp.delta_c * L)));
       pl.count = pl.M + 2 * sp.kappa;
     }
     pl.scene = plan[c].scene;
     pl.g_off = pl.b_off = pl.chunk_off = 0;
+    pl.pad[0] = 0;
     plan[c] = pl;
   }
 }
@@ -1192,8 +1196,19 @@ extern "C" ns_status nurbs_sample(const ns_curves* curves, const ns_sample_param
     return cudaGetLastError() == cudaSuccess ? NS_OK : NS_ERR_CUDA;
   }
   float2* krcp = at<float2>(ws, L.o_krcp);
-  NS_LAUNCH(NS_KERNEL_PLAN, k_plan, nc, kPlanThreads, 0, s, *curves, *sp, plan, knots, at<float>(ws, L.o_knots_lo),
-            krcp, order, st);
+  {
+    // the plan: knot vectors and span forms, then arc lengths and counts
+    // (one profiled range)
+    float* forms = at<float>(ws, L.o_forms);
+    ::ns::before_launch(NS_KERNEL_PLAN, s);
+    launch_kernel(k_plan_forms, dim3(nc), dim3(kFormThreads), 0, s, *curves, plan, knots,
+                  at<float>(ws, L.o_knots_lo), krcp, order, st, forms);
+    ::ns::after_launch(-1, s);
+    ::ns::before_launch(-1, s);
+    launch_kernel(k_plan_length, dim3(nc), dim3(kPlanThreads), 0, s, *curves, *sp, plan,
+                  static_cast<const float*>(knots), static_cast<const float*>(forms));
+    ::ns::after_launch(NS_KERNEL_PLAN, s);
+  }
   NS_LAUNCH(NS_KERNEL_SCAN, k_scan_boundary, 1, 1024, 0, s, nc, plan, st, cap->boundary);
   float4* bloc = at<float4>(ws, L.o_bloc);
   if (cap->boundary > 0)
