@@ -28,7 +28,8 @@ namespace ns {
 
 ns_status launch_blend_bwd(const Layout& L, const ns_curves* curves, const ns_gaussians* g,
                            const ns_raster_params* rp, const float* dimage, float* dgauss, void* ws,
-                           cudaStream_t s, int full_grads, float* dcurve);
+                           cudaStream_t s, int full_grads, float* dcurve, float* dop);
+bool layers_active(const ns_raster_params* rp, const ns_gaussians* g);
 bool raster_params_ok(const ns_raster_params* rp);
 
 constexpr int kWin = 1024;   // control points (and knots) per task window in shared memory
@@ -84,112 +85,157 @@ __device__ __forceinline__ int span_at(const CurveRef& cr, const float* U, float
   return find_span(U, P, cr.n, u);
 }
 
+// Clears the gradient rows of the Gaussians of every curve that is not
+// filled, one warp per curve (row floats per Gaussian).
+__global__ void __launch_bounds__(256) k_zero_rows(int nc, const CurvePlan* __restrict__ plan,
+                                                   const int* __restrict__ gcount, long long gcap, float* dg,
+                                                   int row) {
+  grid_dep_wait();
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= nc) return;
+  const CurvePlan& p = plan[c];
+  if (p.kind == kFill || p.kind == kNone || p.count <= 0 || p.g_off < 0) return;
+  const long long G = min((long long)*gcount, gcap);
+  const long long g0 = p.g_off, g1 = min(g0 + p.count, G);
+  if (g1 <= g0) return;
+  float* r = dg + g0 * row;
+  const long long n = (g1 - g0) * row;
+  for (long long i = lane; i < n; i += 32) r[i] = 0.f;
+}
+
 // Fill tasks: each thread one fill Gaussian (latency-bound loads and a few
 // arithmetic steps; the contour tasks have a kernel of their own).
+// The fields of a curve's plan a fill task reads.
+struct FillTaskPlan {
+  int g_off, nx, ny, chunk_off, b_off, M;
+  float h;
+};
+__device__ __forceinline__ FillTaskPlan fill_task_plan(const CurvePlan* __restrict__ plan, int c) {
+  const CurvePlan& p = plan[c];
+  return FillTaskPlan{p.g_off, p.nx, p.ny, p.chunk_off, p.b_off, p.M, p.h};
+}
+
 __global__ void __launch_bounds__(256, 8) k_chain(ns_curves cv, ChainParams cp, const CurvePlan* __restrict__ plan,
                                                const int* __restrict__ order, const float* __restrict__ knots,
                                                const float4* __restrict__ bloc, const DevState* __restrict__ st,
                                                const float4* __restrict__ rec, const int* __restrict__ gaux,
                                                const float* __restrict__ dgauss, long long gcap, long long bcap,
-                                               float* dkey, float* dknots, float2* dbpts, float* dcolor, int row4) {
+                                               float* dkey, float* dknots, float2* dbpts, float* dcolor, int row4,
+                                               const float* __restrict__ dop) {
   grid_dep_wait();
   __shared__ float2 s_db[kWinB];
   __shared__ float s_red[8];
   const int n_tasks = st->n_chunks;
   const int nc = cv.n_curves;
-  for (int task = blockIdx.x; task < n_tasks; task += gridDim.x) {
-    const int c = task_curve(cp.tmap, cp.tcap, n_tasks, plan, order, nc, task, true);
-    const CurvePlan pl = plan[c];
-    const CurveRef cr = curve_ref(cv, c);
+  // the boundary-point sums start at zero, and every flush leaves them so
+  for (int k = threadIdx.x; k < kWinB; k += blockDim.x) s_db[k] = make_float2(0.f, 0.f);
+  if (threadIdx.x < 8) s_red[threadIdx.x] = 0.f;
+  // the curve and plan of the block's next task are loaded while the
+  // current task runs
+  int task = blockIdx.x;
+  int c = task < n_tasks ? task_curve(cp.tmap, cp.tcap, n_tasks, plan, order, nc, task, true) : 0;
+  FillTaskPlan pl = fill_task_plan(plan, c);
+  for (; task < n_tasks; task += gridDim.x) {
+    const int next = task + gridDim.x;
+    const int c_next = next < n_tasks ? task_curve(cp.tmap, cp.tcap, n_tasks, plan, order, nc, next, true) : c;
+    const FillTaskPlan pl_next = fill_task_plan(plan, c_next);
     // a fill task is a tile of the curve's grid (ftile x ftile points)
     int ix, iy;
     const bool in_grid = fill_task_point(task - pl.chunk_off, pl.nx, pl.ny, threadIdx.x, cp.ftile, ix, iy);
     const long long g = (long long)pl.g_off + (long long)iy * pl.nx + ix;
     const bool valid = in_grid && g < gcap;
-    __syncthreads();
-    if (threadIdx.x < 8) s_red[threadIdx.x] = 0.f;
     // a culled point (opacity 0, marked far) is never composited: its row is
-    // zero and nothing of it is read
+    // zero and nothing of it is read.  With dop (fill layers) the opacity
+    // gradient is there and the colour went to the curve directly.
     const int aux = valid ? gaux[g] : 0;
     float4 g1 = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (valid && aux != kAuxFar) g1 = reinterpret_cast<const float4*>(dgauss)[row4 * g + 1];
-    {
-    // fill task (skipped when its polyline overflowed the boundary capacity)
-    if ((long long)pl.b_off + pl.M > bcap) continue;
-    const int B = pl.M;
-    const bool use_smem = B <= kWinB;
-    if (use_smem)
-      for (int k = threadIdx.x; k < B; k += blockDim.x) s_db[k] = make_float2(0.f, 0.f);
-    __syncthreads();
-    float dO = 0.f;
-    const float gop = g1.x;   // row layout {dmu_x, dmu_y, dsigma, 0, do, dr, dg, db}
-    if (valid && gop != 0.f && aux == kAuxDeep) {
-      dO = gop;   // sigmoid exactly 1: the opacity gradient passes through, none reaches the boundary
-    } else if (valid && gop != 0.f && aux != kAuxFar) {   // no opacity gradient: only the colour
-      const float o = cv.color[4 * c + 3];
-      const bool inside = aux >= 0;
-      const int i0 = inside ? aux : ~aux;
-      const int i1 = i0 + 1 == B ? 0 : i0 + 1;
-      // in grid-local coordinates with the polyline's low parts, as nurbs_sample
-      // formed the distance (the direction below stays exact near the polyline)
-      const float qx = (float(ix) + 0.5f) * pl.h, qy = (float(iy) + 0.5f) * pl.h;
-      const float4 b0 = bloc[pl.b_off + i0], b1 = bloc[pl.b_off + i1];
-      const float ex = __fadd_rn(__fsub_rn(b1.x, b0.x), __fsub_rn(b1.z, b0.z));
-      const float ey = __fadd_rn(__fsub_rn(b1.y, b0.y), __fsub_rn(b1.w, b0.w));
-      const float rx = __fsub_rn(__fsub_rn(qx, b0.x), b0.z), ry = __fsub_rn(__fsub_rn(qy, b0.y), b0.w);
-      const float ee = ex * ex + ey * ey;
-      const float t = ee > 0.f ? fminf(fmaxf((rx * ex + ry * ey) / ee, 0.f), 1.f) : 0.f;
-      const float dx = rx - t * ex, dy = ry - t * ey;
-      const float d = sqrtf(dx * dx + dy * dy);
-      const float sdf = inside ? d : -d;
-      // sigmoid and its slope from E = exp(-|z|): s (1 - s) = E / (1 + E)^2 has no
-      // cancellation inside the shape, where s rounds towards 1 and 1 - s in
-      // float32 would keep only a few significant bits
-      const float z = cp.gamma / cp.h * sdf;
-      const float E = __expf(-fabsf(z));
-      const float inv = 1.f / (1.f + E);
-      const float sig = z >= 0.f ? inv : E * inv;
-      dO = sig * gop;
-      const float dsdf = gop * o * (E * inv * inv) * (cp.gamma / cp.h);
-      const float dd = inside ? dsdf : -dsdf;
-      if (d > 0.f && dd != 0.f) {
-        // d = |q - b0 - t e|, t at its optimum: dd/db0 = -(1-t) n, dd/db1 = -t n
-        const float nx = dx / d, ny = dy / d;
-        const float a0 = -dd * (1.f - t), a1 = -dd * t;
-        if (use_smem) {
-          atomicAdd(&s_db[i0].x, a0 * nx);
-          atomicAdd(&s_db[i0].y, a0 * ny);
-          atomicAdd(&s_db[i1].x, a1 * nx);
-          atomicAdd(&s_db[i1].y, a1 * ny);
-        } else {
-          atomicAdd(&dbpts[pl.b_off + i0].x, a0 * nx);
-          atomicAdd(&dbpts[pl.b_off + i0].y, a0 * ny);
-          atomicAdd(&dbpts[pl.b_off + i1].x, a1 * nx);
-          atomicAdd(&dbpts[pl.b_off + i1].y, a1 * ny);
+    if (valid && aux != kAuxFar) {
+      if (dop) g1.x = dop[g];
+      else g1 = reinterpret_cast<const float4*>(dgauss)[row4 * g + 1];
+    }
+    __syncthreads();   // the previous task's sums are flushed
+    // (skipped when the polyline overflowed the boundary capacity)
+    if ((long long)pl.b_off + pl.M <= bcap) {
+      const int B = pl.M;
+      const bool use_smem = B <= kWinB;
+      float dO = 0.f;
+      bool band = false;
+      const float gop = g1.x;   // row layout {dmu_x, dmu_y, dsigma, 0, do, dr, dg, db}
+      if (valid && gop != 0.f && aux == kAuxDeep) {
+        dO = gop;   // sigmoid exactly 1: the opacity gradient passes through, none reaches the boundary
+      } else if (valid && gop != 0.f && aux != kAuxFar) {   // no opacity gradient: only the colour
+        const float o = cv.color[4 * c + 3];
+        const bool inside = aux >= 0;
+        const int i0 = inside ? aux : ~aux;
+        const int i1 = i0 + 1 == B ? 0 : i0 + 1;
+        // in grid-local coordinates with the polyline's low parts, as nurbs_sample
+        // formed the distance (the direction below stays exact near the polyline)
+        const float qx = (float(ix) + 0.5f) * pl.h, qy = (float(iy) + 0.5f) * pl.h;
+        const float4 b0 = bloc[pl.b_off + i0], b1 = bloc[pl.b_off + i1];
+        const float ex = __fadd_rn(__fsub_rn(b1.x, b0.x), __fsub_rn(b1.z, b0.z));
+        const float ey = __fadd_rn(__fsub_rn(b1.y, b0.y), __fsub_rn(b1.w, b0.w));
+        const float rx = __fsub_rn(__fsub_rn(qx, b0.x), b0.z), ry = __fsub_rn(__fsub_rn(qy, b0.y), b0.w);
+        const float ee = ex * ex + ey * ey;
+        const float t = ee > 0.f ? fminf(fmaxf((rx * ex + ry * ey) / ee, 0.f), 1.f) : 0.f;
+        const float dx = rx - t * ex, dy = ry - t * ey;
+        const float d = sqrtf(dx * dx + dy * dy);
+        const float sdf = inside ? d : -d;
+        // sigmoid and its slope from E = exp(-|z|): s (1 - s) = E / (1 + E)^2 has no
+        // cancellation inside the shape, where s rounds towards 1 and 1 - s in
+        // float32 would keep only a few significant bits
+        const float z = cp.gamma / cp.h * sdf;
+        const float E = __expf(-fabsf(z));
+        const float inv = 1.f / (1.f + E);
+        const float sig = z >= 0.f ? inv : E * inv;
+        dO = sig * gop;
+        const float dsdf = gop * o * (E * inv * inv) * (cp.gamma / cp.h);
+        const float dd = inside ? dsdf : -dsdf;
+        if (d > 0.f && dd != 0.f) {
+          // d = |q - b0 - t e|, t at its optimum: dd/db0 = -(1-t) n, dd/db1 = -t n
+          const float nx = dx / d, ny = dy / d;
+          const float a0 = -dd * (1.f - t), a1 = -dd * t;
+          if (use_smem) {
+            band = true;
+            atomicAdd(&s_db[i0].x, a0 * nx);
+            atomicAdd(&s_db[i0].y, a0 * ny);
+            atomicAdd(&s_db[i1].x, a1 * nx);
+            atomicAdd(&s_db[i1].y, a1 * ny);
+          } else {
+            atomicAdd(&dbpts[pl.b_off + i0].x, a0 * nx);
+            atomicAdd(&dbpts[pl.b_off + i0].y, a0 * ny);
+            atomicAdd(&dbpts[pl.b_off + i1].x, a1 * nx);
+            atomicAdd(&dbpts[pl.b_off + i1].y, a1 * ny);
+          }
         }
       }
-    }
-    {
-      const float v[8] = {0.f, 0.f, g1.y, g1.z, g1.w, dO, 0.f, 0.f};
-      const float tot = warp_sum8(v);
-      const int lane = threadIdx.x & 31;
-      if ((lane & 3) == 0 && (lane >> 2) >= 2 && (lane >> 2) < 6 && tot != 0.f) atomicAdd(&s_red[lane >> 2], tot);
-    }
-    __syncthreads();
-    if (use_smem) {
-      for (int k = threadIdx.x; k < B; k += blockDim.x) {
-        const float2 v = s_db[k];
-        if (v.x != 0.f) atomicAdd(&dbpts[pl.b_off + k].x, v.x);
-        if (v.y != 0.f) atomicAdd(&dbpts[pl.b_off + k].y, v.y);
+      {
+        const float v[8] = {0.f, 0.f, g1.y, g1.z, g1.w, dO, 0.f, 0.f};
+        const float tot = warp_sum8(v);
+        const int lane = threadIdx.x & 31;
+        if ((lane & 3) == 0 && (lane >> 2) >= 2 && (lane >> 2) < 6 && tot != 0.f) atomicAdd(&s_red[lane >> 2], tot);
+      }
+      // only a task with band points has boundary sums to flush
+      if (__syncthreads_or(band)) {
+        for (int k = threadIdx.x; k < B; k += blockDim.x) {
+          const float2 v = s_db[k];
+          if (v.x != 0.f || v.y != 0.f) {
+            s_db[k] = make_float2(0.f, 0.f);
+            if (v.x != 0.f) atomicAdd(&dbpts[pl.b_off + k].x, v.x);
+            if (v.y != 0.f) atomicAdd(&dbpts[pl.b_off + k].y, v.y);
+          }
+        }
+      }
+      if (threadIdx.x == 0) {
+        atomicAdd(dcolor + 4 * c + 0, s_red[2]);
+        atomicAdd(dcolor + 4 * c + 1, s_red[3]);
+        atomicAdd(dcolor + 4 * c + 2, s_red[4]);
+        atomicAdd(dcolor + 4 * c + 3, s_red[5]);
+        s_red[2] = s_red[3] = s_red[4] = s_red[5] = 0.f;
       }
     }
-    if (threadIdx.x == 0) {
-      atomicAdd(dcolor + 4 * c + 0, s_red[2]);
-      atomicAdd(dcolor + 4 * c + 1, s_red[3]);
-      atomicAdd(dcolor + 4 * c + 2, s_red[4]);
-      atomicAdd(dcolor + 4 * c + 3, s_red[5]);
-    }
-    }
+    c = c_next;
+    pl = pl_next;
   }
 }
 
@@ -519,17 +565,31 @@ extern "C" ns_status splat_backward(const ns_curves* curves, const ns_gaussians*
   const bool aniso = g->shape != nullptr;
   const int row = aniso ? 12 : 8;   // floats per per-Gaussian gradient row
   float* dg = dgauss ? dgauss : at<float>(ws, L.o_dgauss);
-  cudaMemsetAsync(dg, 0, sizeof(float) * row * (size_t)L.gcap, s);
+  // the centre and sigma gradients of fill Gaussians are needed only when the
+  // caller asked for the per-Gaussian gradients themselves; otherwise their
+  // colour gradients may go straight to the per-curve output
+  const bool full = dgauss != nullptr || out == nullptr;
+  // Fill layers with workspace rows: the adjoint writes the layer points'
+  // opacity gradients (all the chain reads of a fill Gaussian) to one float
+  // per Gaussian, in the workspace rows' spare tail (the rows take 8 of the 12
+  // floats per Gaussian reserved), and only the contour Gaussians' rows are
+  // cleared and used.
+  const bool compact = !full && layers_active(rp, g);
+  float* dop = compact ? dg + 8 * (size_t)L.gcap : nullptr;
+  if (compact) {
+    cudaMemsetAsync(dop, 0, sizeof(float) * (size_t)L.gcap, s);
+    if (L.nc > 0)
+      NS_LAUNCH(NS_KERNEL_OTHER, k_zero_rows, (L.nc + 7) / 8, 256, 0, s, curves->n_curves,
+                at<const CurvePlan>(ws, L.o_plan), g->count, L.gcap, dg, row);
+  } else {
+    cudaMemsetAsync(dg, 0, sizeof(float) * row * (size_t)L.gcap, s);
+  }
   if (out && zero_outputs) {
     cudaMemsetAsync(out->dkey, 0, sizeof(float) * 4 * (size_t)L.nk, s);
     if (out->dtau) cudaMemsetAsync(out->dtau, 0, sizeof(float) * (size_t)L.nt, s);
     cudaMemsetAsync(out->dcolor, 0, sizeof(float) * 4 * (size_t)L.nc, s);
   }
-  // the centre and sigma gradients of fill Gaussians are needed only when the
-  // caller asked for the per-Gaussian gradients themselves; otherwise their
-  // colour gradients may go straight to the per-curve output
-  const bool full = dgauss != nullptr || out == nullptr;
-  launch_blend_bwd(L, curves, g, rp, dL_dimage, dg, ws, s, full, full ? nullptr : out->dcolor);
+  launch_blend_bwd(L, curves, g, rp, dL_dimage, dg, ws, s, full, full ? nullptr : out->dcolor, dop);
   if (out) {
     DevState* st = at<DevState>(ws, L.o_state);
     const CurvePlan* plan = at<CurvePlan>(ws, L.o_plan);
@@ -555,7 +615,7 @@ extern "C" ns_status splat_backward(const ns_curves* curves, const ns_gaussians*
       NS_LAUNCH(NS_KERNEL_CHAIN, k_chain, num_sms() * 8 * (256 / (cp.ftile * cp.ftile)), cp.ftile * cp.ftile, 0, s, *curves, cp, plan, order, knots,
                 at<const float4>(ws, L.o_bloc), st,
                 reinterpret_cast<const float4*>(g->rec), g->aux, dg, cap->gaussians,
-                cap->boundary, out->dkey, dknots, dbpts, out->dcolor, row / 4);
+                cap->boundary, out->dkey, dknots, dbpts, out->dcolor, row / 4, static_cast<const float*>(dop));
       {
         // one launch per degree present among the curves (the host knows the
         // degrees only on the device, so all five are launched; a launch with

@@ -1531,7 +1531,14 @@ struct LayerArgs {
   int gcap, tile, tiles_x, runs_stride;
   float k_sigma, inv_tile, log_amin;
   int* nsub;   // per pixel: 1 + sample index of the last composited fill Gaussian (0: none)
+  float* dop;  // the adjoint's opacity gradients of layer points, one float per Gaussian (NULL: entry 4
+               // of the Gaussian's gradient row)
 };
+
+// Where the adjoint adds the opacity gradient of grid point g of a fill layer.
+__device__ __forceinline__ float* layer_dop(const LayerArgs& la, float* dgauss, long long g, int row) {
+  return la.dop ? la.dop + g : dgauss + g * row + 4;
+}
 
 // One layer as a warp sees it on one tile (the same in every lane).
 struct LayerView {
@@ -2246,7 +2253,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
                 csum[0] += col[0];
                 csum[1] += col[1];
                 csum[2] += col[2];
-                if (dO != 0.f) atomicAdd(dgauss + g * kRow + 4, dO);
+                if (dO != 0.f) atomicAdd(layer_dop(la, dgauss, g, kRow), dO);
               } else {
                 if (full_grads && daa != 0.f) {
                   const float isg = 1.f / la.rec[g].z;
@@ -2275,7 +2282,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
             if (val != 0.f) {
               const int iyr = int((float(i) + 0.5f) * inv_rw);
               const int ixr = i - iyr * rw;
-              atomicAdd(dgauss + (v.g_off + (long long)(ry0 + iyr) * v.nx + rx0 + ixr) * kRow + 4, val);
+              atomicAdd(layer_dop(la, dgauss, v.g_off + (long long)(ry0 + iyr) * v.nx + rx0 + ixr, kRow), val);
             }
           }
           __syncwarp();
@@ -2535,6 +2542,7 @@ static LayerArgs layer_args(const Layout& L, const ns_raster_params* rp, const n
   la.lconst = at<float4>(ws, L.o_lconst);
   la.tiles_x = L.tiles_x;
   la.runs_stride = L.tiles_x + L.tiles_y;
+  la.dop = nullptr;
   return la;
 }
 
@@ -2688,18 +2696,21 @@ namespace ns {
 // the caller's per-curve colour gradients `dcurve` ({r, g, b, o} per curve,
 // already zeroed or accumulating) may receive the colour gradients of fill
 // Gaussians directly instead of their per-Gaussian rows.
+bool layers_active(const ns_raster_params* rp, const ns_gaussians* g) { return use_layers(rp, g); }
+
 ns_status launch_blend_bwd(const Layout& L, const ns_curves* curves, const ns_gaussians* g,
                            const ns_raster_params* rp, const float* dimage, float* dgauss, void* ws,
-                           cudaStream_t s, int full_grads, float* dcurve) {
+                           cudaStream_t s, int full_grads, float* dcurve, float* dop) {
   const RasterPlan rpn = radix_plan(L.n_tiles);
   const uint32_t* vsorted = (rpn.passes & 1) ? at<uint32_t>(ws, L.o_v1) : at<uint32_t>(ws, L.o_v0);
   DevState* st = at<DevState>(ws, L.o_state);
   cudaMemsetAsync(&st->blend_bwd_evals, 0, sizeof(unsigned long long), s);
   cudaMemsetAsync(&st->blend_bwd_visits, 0, sizeof(unsigned long long), s);
-  const BlendArgs ba{at<int2>(ws, L.o_ranges), vsorted, at<float4>(ws, L.o_prep), at<float2>(ws, L.o_prep2),
-                     at<float2>(ws, L.o_reach), g->curve, reinterpret_cast<const float4*>(curves->color),
-                     blend_params(L, rp), at<float>(ws, L.o_T), at<int>(ws, L.o_nlast), st,
-                     use_layers(rp, g), layer_args(L, rp, g, ws)};
+  BlendArgs ba{at<int2>(ws, L.o_ranges), vsorted, at<float4>(ws, L.o_prep), at<float2>(ws, L.o_prep2),
+               at<float2>(ws, L.o_reach), g->curve, reinterpret_cast<const float4*>(curves->color),
+               blend_params(L, rp), at<float>(ws, L.o_T), at<int>(ws, L.o_nlast), st,
+               use_layers(rp, g), layer_args(L, rp, g, ws)};
+  ba.la.dop = dop;
   dispatch_bwd(L.C, g->shape != nullptr, rp->tile, resolve_ppt(rp->tile, rp->ppt_bwd), L.n_tiles, s, ba, dimage,
                dgauss, full_grads, full_grads ? nullptr : dcurve);
   return NS_OK;
