@@ -11,9 +11,9 @@
 //                     span is unchanged, then go to the task's shared-memory
 //                     window, which is flushed once per task.
 //   k_chain           persistent over the fill tasks: dL/do_j -> curve opacity
-//                     (times the sigmoid), and dL/dsdf -> the two end points of
-//                     the nearest segment (Eq. 7, S1), accumulated per boundary
-//                     point in shared memory.
+//                     (times the sigmoid, summed per warp), and dL/dsdf -> the
+//                     two end points of the nearest segment (Eq. 7, S1), added
+//                     to the boundary points' gradients.
 //   k_chain_boundary  per boundary point: dL/db_i -> control points, weights
 //                     and knots through C(u_i), as for contours.
 //   k_knot_grads      per curve: dL/dU -> dL/dtau by suffix sums over the
@@ -33,7 +33,6 @@ bool layers_active(const ns_raster_params* rp, const ns_gaussians* g);
 bool raster_params_ok(const ns_raster_params* rp);
 
 constexpr int kWin = 1024;   // control points (and knots) per task window in shared memory
-constexpr int kWinB = 2 * kWin;  // boundary points per fill task window
 
 // Reverse of one curve point: gC = dL/dC (x, y, s) at parameter u (span i,
 // domain fraction t).  Hands the control-point and knot gradients to the
@@ -124,15 +123,12 @@ __global__ void __launch_bounds__(256, 8) k_chain(ns_curves cv, ChainParams cp, 
                                                float* dkey, float* dknots, float2* dbpts, float* dcolor, int row4,
                                                const float* __restrict__ dop) {
   grid_dep_wait();
-  __shared__ float2 s_db[kWinB];
-  __shared__ float s_red[8];
   const int n_tasks = st->n_chunks;
   const int nc = cv.n_curves;
-  // the boundary-point sums start at zero, and every flush leaves them so
-  for (int k = threadIdx.x; k < kWinB; k += blockDim.x) s_db[k] = make_float2(0.f, 0.f);
-  if (threadIdx.x < 8) s_red[threadIdx.x] = 0.f;
+  const int lane = threadIdx.x & 31;
   // the curve and plan of the block's next task are loaded while the
-  // current task runs
+  // current task runs; no block barrier: each thread handles its point, the
+  // sums go out per warp
   int task = blockIdx.x;
   int c = task < n_tasks ? task_curve(cp.tmap, cp.tcap, n_tasks, plan, order, nc, task, true) : 0;
   FillTaskPlan pl = fill_task_plan(plan, c);
@@ -140,27 +136,24 @@ __global__ void __launch_bounds__(256, 8) k_chain(ns_curves cv, ChainParams cp, 
     const int next = task + gridDim.x;
     const int c_next = next < n_tasks ? task_curve(cp.tmap, cp.tcap, n_tasks, plan, order, nc, next, true) : c;
     const FillTaskPlan pl_next = fill_task_plan(plan, c_next);
-    // a fill task is a tile of the curve's grid (ftile x ftile points)
-    int ix, iy;
-    const bool in_grid = fill_task_point(task - pl.chunk_off, pl.nx, pl.ny, threadIdx.x, cp.ftile, ix, iy);
-    const long long g = (long long)pl.g_off + (long long)iy * pl.nx + ix;
-    const bool valid = in_grid && g < gcap;
-    // a culled point (opacity 0, marked far) is never composited: its row is
-    // zero and nothing of it is read.  With dop (fill layers) the opacity
-    // gradient is there and the colour went to the curve directly.
-    const int aux = valid ? gaux[g] : 0;
-    float4 g1 = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (valid && aux != kAuxFar) {
-      if (dop) g1.x = dop[g];
-      else g1 = reinterpret_cast<const float4*>(dgauss)[row4 * g + 1];
-    }
-    __syncthreads();   // the previous task's sums are flushed
-    // (skipped when the polyline overflowed the boundary capacity)
+    // a fill task is a tile of the curve's grid (ftile x ftile points);
+    // skipped when the polyline overflowed the boundary capacity
     if ((long long)pl.b_off + pl.M <= bcap) {
+      int ix, iy;
+      const bool in_grid = fill_task_point(task - pl.chunk_off, pl.nx, pl.ny, threadIdx.x, cp.ftile, ix, iy);
+      const long long g = (long long)pl.g_off + (long long)iy * pl.nx + ix;
+      const bool valid = in_grid && g < gcap;
+      // a culled point (opacity 0, marked far) is never composited: its row
+      // is zero and nothing of it is read.  With dop (fill layers) the
+      // opacity gradient is there and the colour went to the curve directly.
+      const int aux = valid ? gaux[g] : 0;
+      float4 g1 = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (valid && aux != kAuxFar) {
+        if (dop) g1.x = dop[g];
+        else g1 = reinterpret_cast<const float4*>(dgauss)[row4 * g + 1];
+      }
       const int B = pl.M;
-      const bool use_smem = B <= kWinB;
       float dO = 0.f;
-      bool band = false;
       const float gop = g1.x;   // row layout {dmu_x, dmu_y, dsigma, 0, do, dr, dg, db}
       if (valid && gop != 0.f && aux == kAuxDeep) {
         dO = gop;   // sigmoid exactly 1: the opacity gradient passes through, none reaches the boundary
@@ -195,43 +188,21 @@ __global__ void __launch_bounds__(256, 8) k_chain(ns_curves cv, ChainParams cp, 
           // d = |q - b0 - t e|, t at its optimum: dd/db0 = -(1-t) n, dd/db1 = -t n
           const float nx = dx / d, ny = dy / d;
           const float a0 = -dd * (1.f - t), a1 = -dd * t;
-          if (use_smem) {
-            band = true;
-            atomicAdd(&s_db[i0].x, a0 * nx);
-            atomicAdd(&s_db[i0].y, a0 * ny);
-            atomicAdd(&s_db[i1].x, a1 * nx);
-            atomicAdd(&s_db[i1].y, a1 * ny);
-          } else {
-            atomicAdd(&dbpts[pl.b_off + i0].x, a0 * nx);
-            atomicAdd(&dbpts[pl.b_off + i0].y, a0 * ny);
-            atomicAdd(&dbpts[pl.b_off + i1].x, a1 * nx);
-            atomicAdd(&dbpts[pl.b_off + i1].y, a1 * ny);
-          }
+          atomicAdd(&dbpts[pl.b_off + i0].x, a0 * nx);
+          atomicAdd(&dbpts[pl.b_off + i0].y, a0 * ny);
+          atomicAdd(&dbpts[pl.b_off + i1].x, a1 * nx);
+          atomicAdd(&dbpts[pl.b_off + i1].y, a1 * ny);
         }
       }
-      {
-        const float v[8] = {0.f, 0.f, g1.y, g1.z, g1.w, dO, 0.f, 0.f};
-        const float tot = warp_sum8(v);
-        const int lane = threadIdx.x & 31;
-        if ((lane & 3) == 0 && (lane >> 2) >= 2 && (lane >> 2) < 6 && tot != 0.f) atomicAdd(&s_red[lane >> 2], tot);
-      }
-      // only a task with band points has boundary sums to flush
-      if (__syncthreads_or(band)) {
-        for (int k = threadIdx.x; k < B; k += blockDim.x) {
-          const float2 v = s_db[k];
-          if (v.x != 0.f || v.y != 0.f) {
-            s_db[k] = make_float2(0.f, 0.f);
-            if (v.x != 0.f) atomicAdd(&dbpts[pl.b_off + k].x, v.x);
-            if (v.y != 0.f) atomicAdd(&dbpts[pl.b_off + k].y, v.y);
-          }
-        }
-      }
-      if (threadIdx.x == 0) {
-        atomicAdd(dcolor + 4 * c + 0, s_red[2]);
-        atomicAdd(dcolor + 4 * c + 1, s_red[3]);
-        atomicAdd(dcolor + 4 * c + 2, s_red[4]);
-        atomicAdd(dcolor + 4 * c + 3, s_red[5]);
-        s_red[2] = s_red[3] = s_red[4] = s_red[5] = 0.f;
+      if (dop) {
+        // the curve's opacity gradient: one sum per warp
+        float v = dO;
+        for (int o2 = 16; o2 > 0; o2 >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o2);
+        if (lane == 0 && v != 0.f) atomicAdd(dcolor + 4 * c + 3, v);
+      } else {
+        const float v[4] = {g1.y, g1.z, g1.w, dO};
+        const float tot = warp_sum4(v);   // value k in the lanes with (lane >> 3) == k
+        if ((lane & 7) == 0 && tot != 0.f) atomicAdd(dcolor + 4 * c + (lane >> 3), tot);
       }
     }
     c = c_next;
