@@ -143,6 +143,7 @@ bool make_layout(const ns_curves* c, const ns_capacity* cap, const ns_raster_par
   L->o_knots_lo = take(sizeof(float) * nkn);
   L->o_krcp = take(sizeof(float2) * kMaxP * nkn);
   L->o_forms = take(sizeof(float) * kFormStride * nkn);   // span Taylor forms, one row per knot slot
+  L->o_boffs = take(sizeof(int) * (size_t)L->nc);          // first boundary point of each curve, packed
   L->o_lbox = take(sizeof(int4) * (size_t)L->nc);
   // contour tasks cover a curve's samples in chunks of kChunk, fill tasks its
   // grid in T x T tiles, T = 8 or 16 (at most (nx ny + (T - 1)(nx + ny) +

@@ -97,6 +97,7 @@ struct Layout {
   size_t o_lcount = 0;       // per curve: tile pairs of its fill layer (splat_forward)
   size_t o_krcp = 0;         // per knot slot k and width j = 1..kMaxP: 1 / (U[k + j] - U[k]) as {hi, lo} (filled curves)
   int64_t tcap = 0;          // entries of that table
+  size_t o_boffs = 0;        // per curve: its first boundary point (plan b_off, packed for searches)
   size_t o_forms = 0;        // per knot slot: the Taylor form {m, A[0..p][3]} of the span it starts (20 floats)
 };
 

@@ -1584,6 +1584,27 @@ __device__ __forceinline__ void covered_run(int n, float guess, F ok, int& lo, i
   while (hi + 1 < n && ok(hi + 1)) ++hi;
 }
 
+// The same run from arithmetic guesses of both ends (g_lo, g_hi: the real
+// bounds of the indices whose grid coordinate the bin rule puts on the tile),
+// confirmed by four independent reads: the ends hold and their outer
+// neighbours do not.  The walk above when the check fails.
+template <typename F>
+__device__ __forceinline__ void covered_run_guess(int n, float g_lo, float g_hi, F ok, int& lo, int& hi) {
+  if (n > 0) {
+    const int a = max(int(ceilf(fminf(fmaxf(g_lo, -1.f), float(n)))), 0);
+    const int b = min(int(ceilf(fminf(fmaxf(g_hi, -1.f), float(n + 1)))) - 1, n - 1);
+    if (a <= b) {
+      const bool in_a = ok(a), in_b = ok(b), in_am = ok(max(a - 1, 0)), in_bp = ok(min(b + 1, n - 1));
+      if (in_a && in_b && (a == 0 || !in_am) && (b == n - 1 || !in_bp)) {
+        lo = a;
+        hi = b;
+        return;
+      }
+    }
+  }
+  covered_run(n, g_lo, ok, lo, hi);
+}
+
 // One block per curve: for each tile column (row) of a fill layer's tile
 // rectangle, the run of grid columns (rows) the bin rule puts on it.
 // Thread 0 also writes the layer's constants: origin, 1/h, the reach bound R
@@ -1626,18 +1647,18 @@ __global__ void __launch_bounds__(128) k_layer_runs(ns_curves cv, const CurvePla
     int lo, hi;
     if (k < ntx) {
       const int tx = tx0 + k;
-      covered_run(p.nx, (tx * T - ks - p.x0) * inv_h - 0.5f,
-                  [&](int ix) { return bin_covers(rec[min((long long)p.g_off + ix, lastg)].x, ks, bp.inv_tile, tx); },
-                  lo, hi);
+      covered_run_guess(p.nx, (tx * T - ks - p.x0) * inv_h - 0.5f, ((tx + 1) * T + ks - p.x0) * inv_h - 0.5f,
+                        [&](int ix) { return bin_covers(rec[min((long long)p.g_off + ix, lastg)].x, ks, bp.inv_tile, tx); },
+                        lo, hi);
       out[tx] = make_int2(max(lo, live0.x), min(hi, live1.x));
     } else {
       const int ty = ty0 + (k - ntx);
-      covered_run(p.ny, (ty * T - ks - p.y0) * inv_h - 0.5f,
-                  [&](int iy) {
-                    return bin_covers(rec[min((long long)p.g_off + (long long)iy * p.nx, lastg)].y, ks,
-                                      bp.inv_tile, ty);
-                  },
-                  lo, hi);
+      covered_run_guess(p.ny, (ty * T - ks - p.y0) * inv_h - 0.5f, ((ty + 1) * T + ks - p.y0) * inv_h - 0.5f,
+                        [&](int iy) {
+                          return bin_covers(rec[min((long long)p.g_off + (long long)iy * p.nx, lastg)].y, ks,
+                                            bp.inv_tile, ty);
+                        },
+                        lo, hi);
       out[bp.tiles_x + ty] = make_int2(max(lo, live0.y), min(hi, live1.y));
     }
   }

@@ -458,11 +458,15 @@ __device__ void block_scan_multi(int n, Get get, Put put, long long tot[K]) {
   for (int k = 0; k < K; ++k) tot[k] = s_carry[k];
 }
 
-__global__ void k_scan_boundary(int nc, CurvePlan* plan, DevState* st, long long bcap) {
+__global__ void k_scan_boundary(int nc, CurvePlan* plan, DevState* st, long long bcap, int* boffs) {
   grid_dep_wait();
+  // the offsets also go to a packed array, which k_boundary searches
   const long long tot = block_scan_items(
       nc, [&](int c) { return plan[c].kind == kFill ? plan[c].M : 0; },
-      [&](int c, long long off) { plan[c].b_off = int(off); });
+      [&](int c, long long off) {
+        plan[c].b_off = int(off);
+        boffs[c] = int(off);
+      });
   if (threadIdx.x == 0) {
     st->b_total = (unsigned long long)tot;
     st->b_count = int(tot < bcap ? tot : bcap);
@@ -516,18 +520,19 @@ __global__ void __launch_bounds__(256) k_boundary(ns_curves cv, const CurvePlan*
                                                   const float* __restrict__ knots, const float* __restrict__ knots_lo,
                                                   const float2* __restrict__ krcp,
                                                   const DevState* __restrict__ st, float2* bpts, int* bcurve,
-                                                  float4* bloc, long long bcap) {
+                                                  float4* bloc, long long bcap, const int* __restrict__ boffs) {
   grid_dep_wait();
   const long long nb = min((long long)st->b_count, bcap);
   const int nc = cv.n_curves;
   for (long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x; o < nb;
        o += (long long)gridDim.x * blockDim.x) {
     // the curve: the largest c with b_off <= o (curves without points share
-    // the offset of the next one, and the largest index is the filled curve)
+    // the offset of the next one, and the largest index is the filled curve);
+    // searched in the packed offsets, whose last levels share cache lines
     int lo = 0, hi = nc - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
-      if (plan[mid].b_off <= o) lo = mid; else hi = mid - 1;
+      if (boffs[mid] <= o) lo = mid; else hi = mid - 1;
     }
     const int c = lo;
     const CurvePlan pl = plan[c];
@@ -1209,13 +1214,14 @@ extern "C" ns_status nurbs_sample(const ns_curves* curves, const ns_sample_param
                   static_cast<const float*>(knots), static_cast<const float*>(forms));
     ::ns::after_launch(NS_KERNEL_PLAN, s);
   }
-  NS_LAUNCH(NS_KERNEL_SCAN, k_scan_boundary, 1, 1024, 0, s, nc, plan, st, cap->boundary);
+  int* boffs = at<int>(ws, L.o_boffs);
+  NS_LAUNCH(NS_KERNEL_SCAN, k_scan_boundary, 1, 1024, 0, s, nc, plan, st, cap->boundary, boffs);
   float4* bloc = at<float4>(ws, L.o_bloc);
   if (cap->boundary > 0)
     NS_LAUNCH(NS_KERNEL_BOUNDARY, k_boundary, int(std::min<long long>((cap->boundary + 255) / 256, num_sms() * 16LL)),
               256, 0, s, *curves, plan, knots, at<const float>(ws, L.o_knots_lo), krcp, st, bpts,
               at<int>(ws, L.o_bcurve),
-              bloc, cap->boundary);
+              bloc, cap->boundary, static_cast<const int*>(boffs));
   int4* lbox = at<int4>(ws, L.o_lbox);
   NS_LAUNCH(NS_KERNEL_OTHER, k_boundary_box, (nc + 7) / 8, 256, 0, s, *curves, *sp, plan, knots, bloc,
             at<float2>(ws, L.o_glo), cap->boundary, lbox, st);
