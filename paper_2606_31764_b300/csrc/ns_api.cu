@@ -2,6 +2,7 @@
 // the Adam step and the error channel.
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <string>
@@ -202,7 +203,26 @@ __global__ void __launch_bounds__(256) k_mse(const float* __restrict__ a, const 
   __shared__ float red[8];
   const float scale = 2.f / float(n);
   float acc = 0.f;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long head = 0;   // values handled four at a time
+  if (((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(grad)) & 15) == 0) {
+    const long long n4 = n >> 2;
+    const float4* a4 = reinterpret_cast<const float4*>(a);
+    const float4* b4 = reinterpret_cast<const float4*>(b);
+    float4* g4 = reinterpret_cast<float4*>(grad);
+    for (long long i = t0; i < n4; i += stride) {
+      const float4 x = a4[i], y = b4[i];
+      const float d0 = x.x - y.x, d1 = x.y - y.y, d2 = x.z - y.z, d3 = x.w - y.w;
+      acc = fmaf(d0, d0, acc);
+      acc = fmaf(d1, d1, acc);
+      acc = fmaf(d2, d2, acc);
+      acc = fmaf(d3, d3, acc);
+      if (grad) g4[i] = make_float4(scale * d0, scale * d1, scale * d2, scale * d3);
+    }
+    head = n4 << 2;
+  }
+  for (long long i = head + t0; i < n; i += stride) {
     const float d = a[i] - b[i];
     acc = fmaf(d, d, acc);
     if (grad) grad[i] = scale * d;
@@ -331,7 +351,7 @@ ns_status ns_mse_loss(const float* image, const float* target, int64_t n, float*
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaMemsetAsync(loss, 0, sizeof(float), s);
-  const long long blocks = (n + 255) / 256;
+  const long long blocks = (n / 4 + 255) / 256 + 1;
   const int grid = int(blocks < num_sms() * 8 ? blocks : num_sms() * 8);
   NS_LAUNCH(NS_KERNEL_MSE, k_mse, grid, 256, 0, s, image, target, n, dL, loss);
   const cudaError_t e = cudaGetLastError();

@@ -599,15 +599,19 @@ extern "C" ns_status splat_backward(const ns_curves* curves, const ns_gaussians*
         auto k4 = NS_CC(4);
         auto k5 = NS_CC(5);
 #undef NS_CC
-        const int grid = num_sms() * 16;
         // the five launches form one profiled range (armed events bracket
-        // the first and the last)
+        // the first and the last); each persistent grid holds the blocks
+        // its registers let every SM keep resident
         auto run = [&](void (*k)(ns_curves, ChainParams, const CurvePlan*, const int*, const float*,
                                   const DevState*, const float*, long long, float*, float*, float*),
                        int first_id, int last_id) {
+          int per_sm = 0;
+          if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kContourThreads, 0) != cudaSuccess ||
+              per_sm < 1)
+            per_sm = 4;
           ::ns::before_launch(first_id, s);
-          k<<<grid, kContourThreads, 0, s>>>(*curves, cp, plan, order, knots, st, dg, cap->gaussians, out->dkey,
-                                              dknots, out->dcolor);
+          launch_kernel(k, dim3(num_sms() * per_sm), dim3(kContourThreads), 0, s, *curves, cp, plan, order, knots,
+                        st, static_cast<const float*>(dg), cap->gaussians, out->dkey, dknots, out->dcolor);
           ::ns::after_launch(last_id, s);
         };
         run(k1, NS_KERNEL_CHAIN_CONTOUR, -1);
