@@ -442,8 +442,9 @@ __device__ void chain_boundary_point(const ns_curves& cv, const CurveRef& cr, co
   }
 }
 
+// One thread per boundary point; 3 blocks of 256 per SM (at most 85 registers).
 template <bool KNOTS>
-__global__ void k_chain_boundary(ns_curves cv, const CurvePlan* __restrict__ plan, const float* __restrict__ knots,
+__global__ void __launch_bounds__(256, 3) k_chain_boundary(ns_curves cv, const CurvePlan* __restrict__ plan, const float* __restrict__ knots,
                                  const DevState* __restrict__ st, const float2* __restrict__ dbpts,
                                  const int* __restrict__ bcurve, int freeze_w, float* dkey, float* dknots) {
   grid_dep_wait();
@@ -622,7 +623,7 @@ extern "C" ns_status splat_backward(const ns_curves* curves, const ns_gaussians*
       }
       if (L.bcap > 0) {
         auto kb = knots_on ? &k_chain_boundary<true> : &k_chain_boundary<false>;
-        NS_LAUNCH(NS_KERNEL_CHAIN_BOUNDARY, kb, num_sms() * 4, 256, 0, s, *curves, plan, knots, st, dbpts,
+        NS_LAUNCH(NS_KERNEL_CHAIN_BOUNDARY, kb, num_sms() * 3, 256, 0, s, *curves, plan, knots, st, dbpts,
                   at<const int>(ws, L.o_bcurve), cp.freeze_w, out->dkey, dknots);
       }
       if (knots_on)
