@@ -38,24 +38,25 @@ PEAKS_FALLBACK = dict(hbm_gbs=6400.0, sm_max_mhz=2032.0)
 # with fill layers, with the units that launch processed and the hash of the
 # kernel source it ran.  The bench scales the bytes to its own launch by the
 # units processed, and reports null if the source, the tile or the binning has
-# changed since the capture.  The fill SDF is left out: at 512 paths the
-# records it writes stay in L2, at 2048 they do not, so its traffic does not
-# grow in proportion.
+# changed since the capture.  The plan's entry is the sum of its two kernels
+# (knots and span forms, arc lengths).  The fill SDF is left out: at 512 paths
+# the records it writes stay in L2, at 2048 they do not, so its traffic does
+# not grow in proportion.
 TRAFFIC = dict(
-    blend_bwd=dict(bytes=86780416, units=2027197, unit="gaussians", tile=8, layers=1,
-                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="219d18604a2c9810"),
-    blend_fwd=dict(bytes=28441344, units=2027197, unit="gaussians", tile=8, layers=1,
-                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="219d18604a2c9810"),
-    chain=dict(bytes=43591424, units=2027197, unit="gaussians", tile=None, layers=None,
-               src="paper_2606_31764_b300/csrc/ns_backward.cu", sha="3d0a96c1d14d779a"),
-    bin_count=dict(bytes=40628992, units=2027197, unit="gaussians", tile=8, layers=1,
-                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="219d18604a2c9810"),
-    bin_emit=dict(bytes=3822336, units=2027197, unit="gaussians", tile=8, layers=1,
-                  src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="219d18604a2c9810"),
-    plan=dict(bytes=477440, units=512, unit="curves", tile=None, layers=None,
-              src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="f92e9b313b6601c2"),
-    boundary=dict(bytes=1273344, units=512, unit="curves", tile=None, layers=None,
-                  src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="f92e9b313b6601c2"),
+    blend_bwd=dict(bytes=57531648, units=2027197, unit="gaussians", tile=8, layers=1,
+                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="ba08ad6f9dcd19fa"),
+    blend_fwd=dict(bytes=27530752, units=2027197, unit="gaussians", tile=8, layers=1,
+                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="ba08ad6f9dcd19fa"),
+    chain=dict(bytes=15444224, units=2027197, unit="gaussians", tile=None, layers=None,
+               src="paper_2606_31764_b300/csrc/ns_backward.cu", sha="762a00cd74cc7909"),
+    bin_count=dict(bytes=338176, units=2027197, unit="gaussians", tile=8, layers=1,
+                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="ba08ad6f9dcd19fa"),
+    bin_emit=dict(bytes=63744, units=2027197, unit="gaussians", tile=8, layers=1,
+                  src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="ba08ad6f9dcd19fa"),
+    plan=dict(bytes=2105344, units=512, unit="curves", tile=None, layers=None,
+              src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="215421c85426d63a"),
+    boundary=dict(bytes=1277440, units=512, unit="curves", tile=None, layers=None,
+                  src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="215421c85426d63a"),
 )
 
 
