@@ -3,9 +3,11 @@ curve are binned as one tile pair per tile of the whole grid, and the blend
 kernels find the grid points that reach each pixel by index arithmetic.
 
 Every pixel composites the same Gaussians in the same order as with one pair
-per Gaussian.  The two paths differ in one rounding: per-Gaussian pairs read
+per Gaussian.  The two paths differ in rounding only: per-Gaussian pairs read
 the records' absolute FP32 centres, while fill layers form the offset of a
-pixel from a grid point in grid-local coordinates, exact to about 1e-7 px.
+pixel from a grid point in grid-local coordinates, exact to about 1e-7 px,
+take the exponential as a power of 2 with a prescaled coefficient and add a
+layer's colour once from its summed weights.
 So the fill-layer image is checked against the FP64 oracle at the 1e-5 gate
 (outside pixels where a production threshold decision lies within 1e-4 of its
 tie), and against the per-Gaussian image within the rounding of the records'
