@@ -1882,11 +1882,11 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
     float dx, dy, d2, e;
     composite_alpha(k, gauss_alpha(fx, fy, q, bp.alpha_max, dx, dy, d2, e), cc, pos, sub);
   };
-  // the same step for a grid point of a layer: every point of the layer has
-  // the curve's colour, so the weights a T of Eq. 8 are summed (wsum) and the
-  // colour is added once per layer
-  auto composite_layer = [&](int k, float a, float& wsum, int pos, int sub) {
-    ++evals;
+  // the same step for grid point (column ix) of a layer: every point of the
+  // layer has the curve's colour, so the weights a T of Eq. 8 are summed
+  // (wsum) and the colour is added once per layer; the walk counts its
+  // evaluations per row and records the row's last composited column (lix)
+  auto composite_layer = [&](int k, float a, float& wsum, int ix, int& lix) {
     if (a < bp.alpha_min) return;
     const float test = T[k] * (1.f - a);
     if (test < bp.t_min) {
@@ -1895,8 +1895,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
     }
     wsum = fmaf(a, T[k], wsum);
     T[k] = test;
-    last[k] = pos;
-    lsub[k] = sub;
+    lix = ix;
     ++contribs;
   };
   for (int base = 0; base < n && !__all_sync(0xffffffffu, all_done()); base += 32) {
@@ -1963,6 +1962,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
           for (int iy = iy0; iy <= iy1 && !done[k]; ++iy) {
             const int rowsub = iy * v.nx;
             const float dy = layer_dy(v, fyl, iy), dy2 = __fmul_rn(dy, dy);
+            int lix = -1;   // the row's last composited column
             if (staged) {
               // two points per step: both alphas are independent of the
               // compositing state, which then takes them in order
@@ -1973,15 +1973,15 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
                 float dx, d2, ea, eb;
                 const float aa = layer_alpha(v, fxl, dy2, qa, bp.alpha_max, dx, d2, ea);
                 const float ab = layer_alpha(v, fxl, dy2, qb, bp.alpha_max, dx, d2, eb);
-                if (qa.w >= 0.f) composite_layer(k, aa, wsum, pos, rowsub + ix + 1);
-                if (qb.w >= 0.f && !done[k]) composite_layer(k, ab, wsum, pos, rowsub + ix + 2);
+                if (qa.w >= 0.f) composite_layer(k, aa, wsum, ix, lix);
+                if (qb.w >= 0.f && !done[k]) composite_layer(k, ab, wsum, ix + 1, lix);
               }
+              evals += ix - ix0;   // points whose alpha the loop formed
               if (ix <= ix1 && !done[k]) {
                 const float4 q = prow[ix];
                 float dx, d2, e;
-                if (q.w >= 0.f)
-                  composite_layer(k, layer_alpha(v, fxl, dy2, q, bp.alpha_max, dx, d2, e), wsum, pos,
-                                  rowsub + ix + 1);
+                ++evals;
+                if (q.w >= 0.f) composite_layer(k, layer_alpha(v, fxl, dy2, q, bp.alpha_max, dx, d2, e), wsum, ix, lix);
               }
             } else {
               for (int ix = ix0; ix <= ix1 && !done[k]; ++ix) {
@@ -1991,9 +1991,13 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
                 if (!layer_point_binned(r, bp.alpha_min)) continue;
                 const float4 q = make_float4(layer_qx(v, ix), 0.f, r.z == v.sig ? v.nc2 : ncoef2(r.z), r.w);
                 float dx, d2, e;
-                composite_layer(k, layer_alpha(v, fxl, dy2, q, bp.alpha_max, dx, d2, e), wsum, pos,
-                                rowsub + ix + 1);
+                ++evals;
+                composite_layer(k, layer_alpha(v, fxl, dy2, q, bp.alpha_max, dx, d2, e), wsum, ix, lix);
               }
+            }
+            if (lix >= 0) {
+              last[k] = pos;
+              lsub[k] = rowsub + lix + 1;
             }
           }
           acc[k][0] = fmaf(cc.x, wsum, acc[k][0]);
@@ -2129,9 +2133,9 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
   };
   // the same for a grid point of a layer whose colour projection cc . dI is
   // ccd: the colour gradient of the layer is the sum of the weights a T
-  // (wsum) times dI, formed once per layer
+  // (wsum) times dI, formed once per layer (the walk counts its evaluations
+  // per row)
   auto adjoint_layer = [&](int k, float a, float e, float ow, float ccd, float& wsum, float& dO) {
-    ++evals;
     if (a < bp.alpha_min) return false;
     T[k] = __fdividef(T[k], 1.f - a);
     wsum = fmaf(a, T[k], wsum);
@@ -2230,6 +2234,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
               const float dy = layer_dy(v, fyl, iy), dy2 = __fmul_rn(dy, dy);
               // the last layer of the pixel starts at its last composited point
               int ix = min(ix1, sstart - rowsub);
+              const int ix_start = ix;
               // two points per step: both alphas first, then the adjoint in order
               for (; ix - 1 >= ix0; ix -= 2) {
                 const float4 qa = prow[ix], qb = prow[ix - 1];
@@ -2242,9 +2247,11 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
                 if (qb.w >= 0.f && adjoint_layer(k, ab, eb, qb.w, ccd, wsum, dO) && dO != 0.f)
                   atomicAdd(&rreg[ix - 1], dO);
               }
+              evals += ix_start - ix;   // points whose alpha the loop formed
               if (ix == ix0) {
                 const float4 q = prow[ix];
                 float dO, dx, d2, e;
+                ++evals;
                 if (q.w >= 0.f &&
                     adjoint_layer(k, layer_alpha(v, fxl, dy2, q, bp.alpha_max, dx, d2, e), e, q.w, ccd, wsum, dO) &&
                     dO != 0.f)
