@@ -115,6 +115,7 @@ __device__ __forceinline__ FillTaskPlan fill_task_plan(const CurvePlan* __restri
   return FillTaskPlan{p.g_off, p.nx, p.ny, p.chunk_off, p.b_off, p.M, p.h};
 }
 
+template <int FT>   // the fill tile edge (8 or 16): FT x FT threads, one grid point each
 __global__ void __launch_bounds__(256, 8) k_chain(ns_curves cv, ChainParams cp, const CurvePlan* __restrict__ plan,
                                                const int* __restrict__ order, const float* __restrict__ knots,
                                                const float4* __restrict__ bloc, const DevState* __restrict__ st,
@@ -140,7 +141,7 @@ __global__ void __launch_bounds__(256, 8) k_chain(ns_curves cv, ChainParams cp, 
     // skipped when the polyline overflowed the boundary capacity
     if ((long long)pl.b_off + pl.M <= bcap) {
       int ix, iy;
-      const bool in_grid = fill_task_point(task - pl.chunk_off, pl.nx, pl.ny, threadIdx.x, cp.ftile, ix, iy);
+      const bool in_grid = fill_task_point(task - pl.chunk_off, pl.nx, pl.ny, threadIdx.x, FT, ix, iy);
       const long long g = (long long)pl.g_off + (long long)iy * pl.nx + ix;
       const bool valid = in_grid && g < gcap;
       // a culled point (opacity 0, marked far) is never composited: its row
@@ -170,23 +171,27 @@ __global__ void __launch_bounds__(256, 8) k_chain(ns_curves cv, ChainParams cp, 
         const float ey = __fadd_rn(__fsub_rn(b1.y, b0.y), __fsub_rn(b1.w, b0.w));
         const float rx = __fsub_rn(__fsub_rn(qx, b0.x), b0.z), ry = __fsub_rn(__fsub_rn(qy, b0.y), b0.w);
         const float ee = ex * ex + ey * ey;
-        const float t = ee > 0.f ? fminf(fmaxf((rx * ex + ry * ey) / ee, 0.f), 1.f) : 0.f;
+        const float t = ee > 0.f ? fminf(fmaxf(__fdividef(rx * ex + ry * ey, ee), 0.f), 1.f) : 0.f;
         const float dx = rx - t * ex, dy = ry - t * ey;
-        const float d = sqrtf(dx * dx + dy * dy);
+        // the distance and the unit normal from one reciprocal square root (the
+        // gradients need them to a few ulps, the records hold the exact opacity)
+        const float d2 = dx * dx + dy * dy;
+        const float rd = d2 > 0.f ? rsqrtf(d2) : 0.f;
+        const float d = d2 * rd;
         const float sdf = inside ? d : -d;
         // sigmoid and its slope from E = exp(-|z|): s (1 - s) = E / (1 + E)^2 has no
         // cancellation inside the shape, where s rounds towards 1 and 1 - s in
         // float32 would keep only a few significant bits
         const float z = cp.gamma / cp.h * sdf;
         const float E = __expf(-fabsf(z));
-        const float inv = 1.f / (1.f + E);
+        const float inv = __fdividef(1.f, 1.f + E);
         const float sig = z >= 0.f ? inv : E * inv;
         dO = sig * gop;
         const float dsdf = gop * o * (E * inv * inv) * (cp.gamma / cp.h);
         const float dd = inside ? dsdf : -dsdf;
         if (d > 0.f && dd != 0.f) {
           // d = |q - b0 - t e|, t at its optimum: dd/db0 = -(1-t) n, dd/db1 = -t n
-          const float nx = dx / d, ny = dy / d;
+          const float nx = dx * rd, ny = dy * rd;
           const float a0 = -dd * (1.f - t), a1 = -dd * t;
           atomicAdd(&dbpts[pl.b_off + i0].x, a0 * nx);
           atomicAdd(&dbpts[pl.b_off + i0].y, a0 * ny);
@@ -584,7 +589,8 @@ extern "C" ns_status splat_backward(const ns_curves* curves, const ns_gaussians*
       cp.tmap = at<const int>(ws, L.o_tasks);
       cp.tcap = L.tcap;
       // one block per fill task: ftile x ftile threads
-      NS_LAUNCH(NS_KERNEL_CHAIN, k_chain, num_sms() * 8 * (256 / (cp.ftile * cp.ftile)), cp.ftile * cp.ftile, 0, s, *curves, cp, plan, order, knots,
+      auto kf = cp.ftile == 8 ? &k_chain<8> : &k_chain<16>;
+      NS_LAUNCH(NS_KERNEL_CHAIN, kf, num_sms() * 8 * (256 / (cp.ftile * cp.ftile)), cp.ftile * cp.ftile, 0, s, *curves, cp, plan, order, knots,
                 at<const float4>(ws, L.o_bloc), st,
                 reinterpret_cast<const float4*>(g->rec), g->aux, dg, cap->gaussians,
                 cap->boundary, out->dkey, dknots, dbpts, out->dcolor, row / 4, static_cast<const float*>(dop));
