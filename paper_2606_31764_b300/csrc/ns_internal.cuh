@@ -551,6 +551,79 @@ __device__ __forceinline__ float warp_sum4(const float v[4]) {
   return d;
 }
 
+// K exclusive scans over the same items in one sweep of a single block:
+// get(i, v) gives item i's K values, put(i, off) receives their K offsets,
+// tot the K totals.  Each thread takes a run of up to kScanRun consecutive
+// items per pass (all its reads in flight together), the block scans the
+// runs' sums, and each thread hands out its items' offsets.
+constexpr int kScanRun = 4;
+
+template <int K, class Get, class Put>
+__device__ void block_scan_multi(int n, Get get, Put put, long long tot[K]) {
+  __shared__ long long s_carry[K];
+  __shared__ long long s_warp[K][32];
+  if (threadIdx.x < K) s_carry[threadIdx.x] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nb = blockDim.x;
+  for (int base = 0; base < n; base += nb * kScanRun) {
+    const int run = min(kScanRun, (n - base + nb - 1) / nb);   // items per thread in this pass
+    const int i0 = base + threadIdx.x * run;
+    long long v[kScanRun][K], x[K];
+#pragma unroll
+    for (int j = 0; j < kScanRun; ++j) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) v[j][k] = 0;
+      if (j < run && i0 + j < n) get(i0 + j, v[j]);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      x[k] = 0;
+#pragma unroll
+      for (int j = 0; j < kScanRun; ++j) x[k] += v[j][k];
+    }
+    long long sum[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      sum[k] = x[k];
+      for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, x[k], o);
+        if (lane >= o) x[k] += y;
+      }
+      if (lane == 31) s_warp[k][w] = x[k];
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        long long t = lane < nw ? s_warp[k][lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+          const long long y = __shfl_up_sync(0xffffffffu, t, o);
+          if (lane >= o) t += y;
+        }
+        if (lane < nw) s_warp[k][lane] = t;
+      }
+    }
+    __syncthreads();
+    long long off[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) off[k] = s_carry[k] + (w > 0 ? s_warp[k][w - 1] : 0) + x[k] - sum[k];
+#pragma unroll
+    for (int j = 0; j < kScanRun; ++j) {
+      if (j < run && i0 + j < n) put(i0 + j, off);
+#pragma unroll
+      for (int k = 0; k < K; ++k) off[k] += v[j][k];
+    }
+    __syncthreads();
+    if (threadIdx.x == nb - 1)
+#pragma unroll
+      for (int k = 0; k < K; ++k) s_carry[k] = off[k];
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) tot[k] = s_carry[k];
+}
+
 // Runtime degree -> template dispatch.
 #define NS_DISPATCH_P(p, ...)                     \
   switch (p) {                                    \

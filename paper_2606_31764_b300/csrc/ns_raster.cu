@@ -436,40 +436,14 @@ __global__ void k_scan_small(int* vals, const int* gcount, int gcap, int items_p
                              long long cap, uint32_t* zero, int nzero) {
   grid_dep_wait();
   for (int i = threadIdx.x; i < nzero; i += blockDim.x) zero[i] = 0u;   // the radix sort's digit totals
-  __shared__ long long s_warp[32];
-  __shared__ long long s_carry;
   const int G = min(*gcount, gcap);
   const int n = (G + items_per_block - 1) / items_per_block;
-  if (threadIdx.x == 0) s_carry = 0;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int base = 0; base < n; base += blockDim.x) {
-    const int i = base + threadIdx.x;
-    const long long v = i < n ? vals[i] : 0;
-    long long x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-      const long long y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) s_warp[w] = x;
-    __syncthreads();
-    if (w == 0) {
-      long long t = lane < nw ? s_warp[lane] : 0;
-      for (int o = 1; o < 32; o <<= 1) {
-        const long long y = __shfl_up_sync(0xffffffffu, t, o);
-        if (lane >= o) t += y;
-      }
-      if (lane < nw) s_warp[lane] = t;
-    }
-    __syncthreads();
-    const long long excl = s_carry + (w > 0 ? s_warp[w - 1] : 0) + x - v;
-    if (i < n) vals[i] = int(excl < 0x7fffffffLL ? excl : 0x7fffffffLL);
-    __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) s_carry = excl + v;
-    __syncthreads();
-  }
+  long long t1[1];
+  block_scan_multi<1>(
+      n, [&](int i, long long v[1]) { v[0] = vals[i]; },
+      [&](int i, const long long off[1]) { vals[i] = int(off[0] < 0x7fffffffLL ? off[0] : 0x7fffffffLL); }, t1);
   if (threadIdx.x == 0) {
-    const long long tot = s_carry;
+    const long long tot = t1[0];
     st->pair_total = (unsigned long long)tot;
     st->pair_count = int(tot < cap ? tot : cap);
     if (tot > cap) raise_status(st, NS_ERR_CAPACITY);

@@ -369,104 +369,18 @@ __global__ void __launch_bounds__(kPlanThreads, 8) k_plan_length(ns_curves cv, n
   }
 }
 
-// Exclusive scan of one int per item with a single block; `get(i)` gives the
-// item's value, `put(i, offset)` receives its offset; returns the total.
-template <class Get, class Put>
-__device__ long long block_scan_items(int n, Get get, Put put) {
-  __shared__ long long s_carry;
-  __shared__ long long s_warp[32];
-  if (threadIdx.x == 0) s_carry = 0;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int base = 0; base < n; base += blockDim.x) {
-    const int i = base + threadIdx.x;
-    long long v = i < n ? (long long)get(i) : 0;
-    long long x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-      const long long y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) s_warp[w] = x;
-    __syncthreads();
-    if (w == 0) {
-      long long t = lane < nw ? s_warp[lane] : 0;
-      for (int o = 1; o < 32; o <<= 1) {
-        const long long y = __shfl_up_sync(0xffffffffu, t, o);
-        if (lane >= o) t += y;
-      }
-      if (lane < nw) s_warp[lane] = t;
-    }
-    __syncthreads();
-    const long long excl = s_carry + (w > 0 ? s_warp[w - 1] : 0) + x - v;
-    if (i < n) put(i, excl);
-    __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) s_carry = excl + v;
-    __syncthreads();
-  }
-  return s_carry;
-}
-
-// K exclusive scans over the same items in one sweep of a single block:
-// get(i, v) gives item i's K values, put(i, off) receives their K offsets,
-// tot the K totals.
-template <int K, class Get, class Put>
-__device__ void block_scan_multi(int n, Get get, Put put, long long tot[K]) {
-  __shared__ long long s_carry[K];
-  __shared__ long long s_warp[K][32];
-  if (threadIdx.x < K) s_carry[threadIdx.x] = 0;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int base = 0; base < n; base += blockDim.x) {
-    const int i = base + threadIdx.x;
-    long long v[K], x[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) v[k] = 0;
-    if (i < n) get(i, v);
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      x[k] = v[k];
-      for (int o = 1; o < 32; o <<= 1) {
-        const long long y = __shfl_up_sync(0xffffffffu, x[k], o);
-        if (lane >= o) x[k] += y;
-      }
-      if (lane == 31) s_warp[k][w] = x[k];
-    }
-    __syncthreads();
-    if (w == 0) {
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        long long t = lane < nw ? s_warp[k][lane] : 0;
-        for (int o = 1; o < 32; o <<= 1) {
-          const long long y = __shfl_up_sync(0xffffffffu, t, o);
-          if (lane >= o) t += y;
-        }
-        if (lane < nw) s_warp[k][lane] = t;
-      }
-    }
-    __syncthreads();
-    long long off[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) off[k] = s_carry[k] + (w > 0 ? s_warp[k][w - 1] : 0) + x[k] - v[k];
-    if (i < n) put(i, off);
-    __syncthreads();
-    if (threadIdx.x == blockDim.x - 1)
-#pragma unroll
-      for (int k = 0; k < K; ++k) s_carry[k] = off[k] + v[k];
-    __syncthreads();
-  }
-#pragma unroll
-  for (int k = 0; k < K; ++k) tot[k] = s_carry[k];
-}
-
 __global__ void k_scan_boundary(int nc, CurvePlan* plan, DevState* st, long long bcap, int* boffs) {
   grid_dep_wait();
   // the offsets also go to a packed array, which k_boundary searches
-  const long long tot = block_scan_items(
-      nc, [&](int c) { return plan[c].kind == kFill ? plan[c].M : 0; },
-      [&](int c, long long off) {
-        plan[c].b_off = int(off);
-        boffs[c] = int(off);
-      });
+  long long t1[1];
+  block_scan_multi<1>(
+      nc, [&](int c, long long v[1]) { v[0] = plan[c].kind == kFill ? plan[c].M : 0; },
+      [&](int c, const long long off[1]) {
+        plan[c].b_off = int(off[0]);
+        boffs[c] = int(off[0]);
+      },
+      t1);
+  const long long tot = t1[0];
   if (threadIdx.x == 0) {
     st->b_total = (unsigned long long)tot;
     st->b_count = int(tot < bcap ? tot : bcap);
