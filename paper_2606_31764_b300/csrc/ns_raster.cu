@@ -1698,12 +1698,6 @@ __device__ __forceinline__ void layer_window(const LayerView& v, float fx, float
   }
 }
 
-// A grid point the per-Gaussian binning would have listed (tile_rect's
-// per-Gaussian conditions; the tile itself is covered by construction).
-__device__ __forceinline__ bool layer_point_binned(const float4& r, float alpha_min) {
-  return r.z > 0.f && r.w > 0.f && r.w >= alpha_min;
-}
-
 // Grid-local coordinate of grid column (row) i, as nurbs_sample placed it.
 __device__ __forceinline__ float layer_qx(const LayerView& v, int i) { return (float(i) + 0.5f) * v.h; }
 
@@ -1712,20 +1706,6 @@ __device__ __forceinline__ float layer_qx(const LayerView& v, int i) { return (f
 // every point of the row, so the walks form it (and its square) once per row.
 __device__ __forceinline__ float layer_dy(const LayerView& v, float fyl, int iy) {
   return __fsub_rn(__fsub_rn(fyl, layer_qx(v, iy)), v.yoff);
-}
-
-// alpha of a layer's grid point (staged {qx, qy, nc2, o} in grid-local
-// coordinates, nc2 = -log2(e) / (2 sigma^2)) at the pixel whose centre minus
-// the integer origin has x part fxl, on a row at squared offset dy2:
-// alpha = min(alpha_max, o 2^(nc2 d^2)), which is o exp(-d^2 / (2 sigma^2))
-// of Eq. 9.  The forward and the adjoint call this one function, so they
-// compute the same bits.
-__device__ __forceinline__ float layer_alpha(const LayerView& v, float fxl, float dy2, const float4& q, float amax,
-                                             float& dx, float& d2, float& e) {
-  dx = __fsub_rn(__fsub_rn(fxl, q.x), v.xoff);
-  d2 = __fmaf_rn(dx, dx, dy2);
-  e = ex2_approx(__fmul_rn(q.z, d2));
-  return fminf(__fmul_rn(q.w, e), amax);
 }
 
 // The warp's region of a layer: the grid points the pixel centres of its
@@ -1746,28 +1726,102 @@ __device__ __forceinline__ bool layer_region(const LayerView& v, const float4& w
   return rx1 >= rx0 && ry1 >= ry0;
 }
 
-// Stages the region's points as the blend constants {mu_x, mu_y, ncoef, o}
-// the per-Gaussian binning would prepare; points it would not bin get
-// o = -1.  Returns whether any point is live (the same in every lane).
-__device__ __forceinline__ bool layer_stage(const LayerArgs& la, const LayerView& v, int rx0, int ry0, int rw,
-                                            int rh, float alpha_min, float4* pts) {
+// What a warp keeps per fill-layer entry of a list batch, prepared by the
+// lane that loads the entry (the 32 entries of a batch in parallel): the
+// region of grid points the warp's pixel rectangle wr can see (rx0 > rx1:
+// none), and the layer's constants for the pixels' windows and the walk.
+// Fill Gaussians of one curve share sigma (eta h / rho, Eq. 6), so a layer
+// has one exponent coefficient.
+__device__ __forceinline__ void layer_prepare(const LayerArgs& la, int c, int tx, int ty, const float4& wr,
+                                              int4& reg, float4& win, float4& loc, float4& org) {
+  float4 k0, k1, k2;
+  int4 run;
+  layer_entry(la, c, tx, ty, k0, k1, k2, run);
+  const LayerView v = layer_view(k0, k1, k2, run, 0, 0);
+  int rx0, rx1, ry0, ry1;
+  if (!(v.sig > 0.f) || !layer_region(v, wr, rx0, rx1, ry0, ry1)) {
+    rx0 = ry0 = 1;
+    rx1 = ry1 = 0;
+  }
+  reg = make_int4(rx0, rx1, ry0, ry1);
+  win = make_float4(v.x0, v.y0, v.inv_h, v.R);
+  loc = make_float4(v.xoff, v.yoff, v.h, v.nc2);
+  org = make_float4(v.X0, v.Y0, __int_as_float(v.nx), v.sig);
+}
+
+// The layer as the warp sees it, from the prepared entry: the region's bounds
+// stand in for the tile's runs (every pixel window lies inside the region,
+// and both clamp to the runs and the reach the same way).
+__device__ __forceinline__ LayerView layer_unpack(const int4& reg, const float4& win, const float4& loc,
+                                                  const float4& org, long long g_off, long long G) {
+  LayerView v;
+  v.g_off = g_off;
+  v.G = G;
+  v.x0 = win.x;
+  v.y0 = win.y;
+  v.inv_h = win.z;
+  v.R = win.w;
+  v.xoff = loc.x;
+  v.yoff = loc.y;
+  v.h = loc.z;
+  v.nc2 = loc.w;
+  v.X0 = org.x;
+  v.Y0 = org.y;
+  v.nx = __float_as_int(org.z);
+  v.sig = org.w;
+  v.ny = 0;
+  v.cx0 = reg.x;
+  v.cx1 = reg.y;
+  v.cy0 = reg.z;
+  v.cy1 = reg.w;
+  return v;
+}
+
+// alpha of a staged grid point {qx, o} (o < 0: not listed) at the pixel whose
+// centre minus the integer origin has x part fxl, on a row at squared offset
+// dy2 (as layer_alpha, with the layer's coefficient).
+__device__ __forceinline__ float layer_alpha_o(const LayerView& v, float fxl, float dy2, const float2& q, float amax,
+                                               float& dx, float& d2, float& e) {
+  dx = __fsub_rn(__fsub_rn(fxl, q.x), v.xoff);
+  d2 = __fmaf_rn(dx, dx, dy2);
+  e = ex2_approx(__fmul_rn(v.nc2, d2));
+  return fminf(__fmul_rn(q.y, e), amax);
+}
+
+// A grid point of opacity o the per-Gaussian binning would list (sigma > 0
+// is checked once per layer).
+__device__ __forceinline__ bool layer_o_binned(float o, float alpha_min) { return o > 0.f && o >= alpha_min; }
+
+// Stages the region's points as {qx, o} (o = -1 for points the per-Gaussian
+// binning would not list): each lane reads the opacities of its kIt points
+// first, all reads in flight together, then writes them.  Returns whether
+// any point is live (the same in every lane).
+template <int kIt>
+__device__ __forceinline__ bool layer_stage_o(const LayerArgs& la, const LayerView& v, int rx0, int ry0, int rw,
+                                              int rh, float alpha_min, float2* pts) {
   const int lane = threadIdx.x & 31;
   const int npt = rw * rh;
   const float inv_rw = 1.f / float(rw);
+  const float* op = reinterpret_cast<const float*>(la.rec) + 3;   // the records' opacities
+  float o[kIt];
+  int ixr[kIt];
+#pragma unroll
+  for (int it = 0; it < kIt; ++it) {
+    const int i = lane + 32 * it;
+    const int iyr = int((float(i) + 0.5f) * inv_rw);   // exact for the region sizes staged here
+    ixr[it] = i - iyr * rw;
+    const long long g = v.g_off + (long long)(ry0 + iyr) * v.nx + (rx0 + ixr[it]);
+    o[it] = (i < npt && g < v.G) ? op[4 * g] : -1.f;
+  }
   bool live = false;
-  for (int i = lane; i < npt; i += 32) {
-    int iyr = int((float(i) + 0.5f) * inv_rw);   // exact for the region sizes staged here
-    int ixr = i - iyr * rw;
-    const long long g = v.g_off + (long long)(ry0 + iyr) * v.nx + (rx0 + ixr);
-    float4 q = make_float4(0.f, 0.f, 0.f, -1.f);
-    if (g < v.G) {
-      const float4 r = la.rec[g];
-      if (layer_point_binned(r, alpha_min)) {
-        q = make_float4(layer_qx(v, rx0 + ixr), layer_qx(v, ry0 + iyr), r.z == v.sig ? v.nc2 : ncoef2(r.z), r.w);
-        live = true;
-      }
+#pragma unroll
+  for (int it = 0; it < kIt; ++it) {
+    const int i = lane + 32 * it;
+    if (i < npt) {
+      const bool ok = layer_o_binned(o[it], alpha_min);
+      live = live || ok;
+      pts[i] = make_float2(layer_qx(v, rx0 + ixr[it]), ok ? o[it] : -1.f);
     }
-    pts[i] = q;
   }
   return __any_sync(0xffffffffu, live);
 }
@@ -1795,13 +1849,13 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
   grid_dep_wait();
   using Gm = BlendGeom<TILE, PPT>;
   constexpr int kPts = LayerGeom<TILE, PPT>::kPts;
-  __shared__ float4 s_q[Gm::kWarps][32];     // blend constants, or a layer's first constants
+  __shared__ float4 s_q[Gm::kWarps][32];     // blend constants, or a layer's {xoff, yoff, h, nc2}
   __shared__ float4 s_c[Gm::kWarps][32];
   __shared__ uint32_t s_id[Gm::kWarps][32];
-  __shared__ float4 s_k1[Gm::kWarps][32];    // a layer's second constants
-  __shared__ float4 s_k2[Gm::kWarps][32];    // a layer's third constants
-  __shared__ int4 s_run[Gm::kWarps][32];     // a layer's grid runs on this tile
-  __shared__ float4 s_pt[Gm::kWarps][kPts];
+  __shared__ float4 s_win[Gm::kWarps][32];   // a layer's {x0, y0, 1/h, R}
+  __shared__ float4 s_org[Gm::kWarps][32];   // a layer's {X0, Y0, nx bits, sigma}
+  __shared__ int4 s_rg[Gm::kWarps][32];      // a layer's region for this warp
+  __shared__ float2 s_pt[Gm::kWarps][kPts];
   int s, px, py0;
   float4 wr;
   tile_pixels<TILE, PPT>(bp, s, px, py0, wr);
@@ -1879,17 +1933,19 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
       const uint32_t g = gid[rg.x + j];
       const uint32_t gi = g & ~kLayerBit;
       if (g & kLayerBit) {
-        hit = true;
         const int c = gcurve[gi];
-        float4 k0, k1, k2;
-        int4 run;
-        layer_entry(la, c, tx, ty, k0, k1, k2, run);
-        s_id[w][lane] = g;
-        s_c[w][lane] = color[c];
-        s_q[w][lane] = k0;
-        s_k1[w][lane] = k1;
-        s_k2[w][lane] = k2;
-        s_run[w][lane] = run;
+        int4 reg;
+        float4 win, loc, org;
+        layer_prepare(la, c, tx, ty, wr, reg, win, loc, org);
+        hit = reg.x <= reg.y;
+        if (hit) {
+          s_id[w][lane] = g;
+          s_c[w][lane] = color[c];
+          s_q[w][lane] = loc;
+          s_win[w][lane] = win;
+          s_org[w][lane] = org;
+          s_rg[w][lane] = reg;
+        }
       } else {
         const float4 q = prep[gi];
         hit = rect_d2(q.x, q.y, wr.x, wr.y, wr.z, wr.w) <= reach[gi].x;
@@ -1910,14 +1966,14 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
       if (id & kLayerBit) {
         if (!__any_sync(0xffffffffu, !all_done())) break;
         const uint32_t g0 = id & ~kLayerBit;
-        const LayerView v = layer_view(s_q[w][b], s_k1[w][b], s_k2[w][b], s_run[w][b], g0, Gset);
+        const int4 reg = s_rg[w][b];
+        const LayerView v = layer_unpack(reg, s_win[w][b], s_q[w][b], s_org[w][b], g0, Gset);
         const float fxl = __fsub_rn(fx, v.X0);
-        int rx0, rx1, ry0, ry1;
-        if (!layer_region(v, wr, rx0, rx1, ry0, ry1)) continue;
-        const int rw = rx1 - rx0 + 1, rh = ry1 - ry0 + 1;
+        const int rx0 = reg.x, ry0 = reg.z;
+        const int rw = reg.y - reg.x + 1, rh = reg.w - reg.z + 1;
         const bool staged = (long long)rw * rh <= kPts;
         if (staged) {
-          const bool live = layer_stage(la, v, rx0, ry0, rw, rh, bp.alpha_min, s_pt[w]);
+          const bool live = layer_stage_o<kPts / 32>(la, v, rx0, ry0, rw, rh, bp.alpha_min, s_pt[w]);
           __syncwarp();
           if (!live) {
             __syncwarp();
@@ -1940,33 +1996,33 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
             if (staged) {
               // two points per step: both alphas are independent of the
               // compositing state, which then takes them in order
-              const float4* prow = &s_pt[w][(iy - ry0) * rw - rx0];
+              const float2* prow = &s_pt[w][(iy - ry0) * rw - rx0];
               int ix = ix0;
               for (; ix + 1 <= ix1 && !done[k]; ix += 2) {
-                const float4 qa = prow[ix], qb = prow[ix + 1];
+                const float2 qa = prow[ix], qb = prow[ix + 1];
                 float dx, d2, ea, eb;
-                const float aa = layer_alpha(v, fxl, dy2, qa, bp.alpha_max, dx, d2, ea);
-                const float ab = layer_alpha(v, fxl, dy2, qb, bp.alpha_max, dx, d2, eb);
-                if (qa.w >= 0.f) composite_layer(k, aa, wsum, ix, lix);
-                if (qb.w >= 0.f && !done[k]) composite_layer(k, ab, wsum, ix + 1, lix);
+                const float aa = layer_alpha_o(v, fxl, dy2, qa, bp.alpha_max, dx, d2, ea);
+                const float ab = layer_alpha_o(v, fxl, dy2, qb, bp.alpha_max, dx, d2, eb);
+                if (qa.y >= 0.f) composite_layer(k, aa, wsum, ix, lix);
+                if (qb.y >= 0.f && !done[k]) composite_layer(k, ab, wsum, ix + 1, lix);
               }
               evals += ix - ix0;   // points whose alpha the loop formed
               if (ix <= ix1 && !done[k]) {
-                const float4 q = prow[ix];
+                const float2 q = prow[ix];
                 float dx, d2, e;
                 ++evals;
-                if (q.w >= 0.f) composite_layer(k, layer_alpha(v, fxl, dy2, q, bp.alpha_max, dx, d2, e), wsum, ix, lix);
+                if (q.y >= 0.f) composite_layer(k, layer_alpha_o(v, fxl, dy2, q, bp.alpha_max, dx, d2, e), wsum, ix, lix);
               }
             } else {
               for (int ix = ix0; ix <= ix1 && !done[k]; ++ix) {
                 const long long g = v.g_off + rowsub + ix;
                 if (g >= v.G) break;
-                const float4 r = la.rec[g];
-                if (!layer_point_binned(r, bp.alpha_min)) continue;
-                const float4 q = make_float4(layer_qx(v, ix), 0.f, r.z == v.sig ? v.nc2 : ncoef2(r.z), r.w);
+                const float o = la.rec[g].w;
+                if (!layer_o_binned(o, bp.alpha_min)) continue;
                 float dx, d2, e;
                 ++evals;
-                composite_layer(k, layer_alpha(v, fxl, dy2, q, bp.alpha_max, dx, d2, e), wsum, ix, lix);
+                composite_layer(k, layer_alpha_o(v, fxl, dy2, make_float2(layer_qx(v, ix), o), bp.alpha_max, dx, d2, e),
+                                wsum, ix, lix);
               }
             }
             if (lix >= 0) {
@@ -2031,14 +2087,14 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
   using Gm = BlendGeom<TILE, PPT>;
   constexpr int kRow = 8;
   constexpr int kPts = LayerGeom<TILE, PPT>::kPts;
-  __shared__ float4 s_q[Gm::kWarps][32];     // blend constants, or a layer's first constants
+  __shared__ float4 s_q[Gm::kWarps][32];     // blend constants, or a layer's {xoff, yoff, h, nc2}
   __shared__ float4 s_c[Gm::kWarps][32];
   __shared__ float s_isig[Gm::kWarps][32];   // +-1/sigma, or a layer's curve (int bits)
   __shared__ uint32_t s_id[Gm::kWarps][32];
-  __shared__ float4 s_k1[Gm::kWarps][32];    // a layer's second constants
-  __shared__ float4 s_k2[Gm::kWarps][32];    // a layer's third constants
-  __shared__ int4 s_run[Gm::kWarps][32];     // a layer's grid runs on this tile
-  __shared__ float4 s_pt[Gm::kWarps][kPts];
+  __shared__ float4 s_win[Gm::kWarps][32];   // a layer's {x0, y0, 1/h, R}
+  __shared__ float4 s_org[Gm::kWarps][32];   // a layer's {X0, Y0, nx bits, sigma}
+  __shared__ int4 s_rg[Gm::kWarps][32];      // a layer's region for this warp
+  __shared__ float2 s_pt[Gm::kWarps][kPts];
   __shared__ float s_reg[Gm::kWarps][kPts];
   int s, px, py0;
   float4 wr;
@@ -2131,18 +2187,20 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
       const uint32_t g = gid[rg.x + j];
       const uint32_t gi = g & ~kLayerBit;
       if (g & kLayerBit) {
-        hit = true;
         const int c = gcurve[gi];
-        float4 k0, k1, k2;
-        int4 run;
-        layer_entry(la, c, tx, ty, k0, k1, k2, run);
-        s_id[w][lane] = g;
-        s_c[w][lane] = color[c];
-        s_q[w][lane] = k0;
-        s_k1[w][lane] = k1;
-        s_k2[w][lane] = k2;
-        s_run[w][lane] = run;
-        s_isig[w][lane] = __int_as_float(c);
+        int4 reg;
+        float4 win, loc, org;
+        layer_prepare(la, c, tx, ty, wr, reg, win, loc, org);
+        hit = reg.x <= reg.y;
+        if (hit) {
+          s_id[w][lane] = g;
+          s_c[w][lane] = color[c];
+          s_q[w][lane] = loc;
+          s_win[w][lane] = win;
+          s_org[w][lane] = org;
+          s_rg[w][lane] = reg;
+          s_isig[w][lane] = __int_as_float(c);
+        }
       } else {
         const float4 q = prep[gi];
         const float2 rs = reach[gi];
@@ -2173,15 +2231,15 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
         if (!__any_sync(0xffffffffu, any)) continue;   // no pixel of the warp walks this far back
         const uint32_t g0 = id & ~kLayerBit;
         const int c = __float_as_int(s_isig[w][b]);
-        const LayerView v = layer_view(s_q[w][b], s_k1[w][b], s_k2[w][b], s_run[w][b], g0, Gset);
+        const int4 reg = s_rg[w][b];
+        const LayerView v = layer_unpack(reg, s_win[w][b], s_q[w][b], s_org[w][b], g0, Gset);
         const float fxl = __fsub_rn(fx, v.X0);
-        int rx0, rx1, ry0, ry1;
-        if (!layer_region(v, wr, rx0, rx1, ry0, ry1)) continue;
-        const int rw = rx1 - rx0 + 1, rh = ry1 - ry0 + 1;
+        const int rx0 = reg.x, ry0 = reg.z;
+        const int rw = reg.y - reg.x + 1, rh = reg.w - reg.z + 1;
         const bool staged = !per_pair && (long long)rw * rh <= kPts;
         if (staged) {
           for (int i = lane; i < rw * rh; i += 32) s_reg[w][i] = 0.f;
-          const bool live = layer_stage(la, v, rx0, ry0, rw, rh, bp.alpha_min, s_pt[w]);
+          const bool live = layer_stage_o<kPts / 32>(la, v, rx0, ry0, rw, rh, bp.alpha_min, s_pt[w]);
           __syncwarp();
           if (!live) {
             __syncwarp();
@@ -2203,7 +2261,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
             for (int iy = iy1; iy >= iy0; --iy) {
               const int rowsub = iy * v.nx;
               const int ridx = (iy - ry0) * rw - rx0;
-              const float4* prow = &s_pt[w][ridx];
+              const float2* prow = &s_pt[w][ridx];
               float* rreg = &s_reg[w][ridx];
               const float dy = layer_dy(v, fyl, iy), dy2 = __fmul_rn(dy, dy);
               // the last layer of the pixel starts at its last composited point
@@ -2211,23 +2269,23 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
               const int ix_start = ix;
               // two points per step: both alphas first, then the adjoint in order
               for (; ix - 1 >= ix0; ix -= 2) {
-                const float4 qa = prow[ix], qb = prow[ix - 1];
+                const float2 qa = prow[ix], qb = prow[ix - 1];
                 float dxa, d2a, ea, dxb, d2b, eb;
-                const float aa = layer_alpha(v, fxl, dy2, qa, bp.alpha_max, dxa, d2a, ea);
-                const float ab = layer_alpha(v, fxl, dy2, qb, bp.alpha_max, dxb, d2b, eb);
+                const float aa = layer_alpha_o(v, fxl, dy2, qa, bp.alpha_max, dxa, d2a, ea);
+                const float ab = layer_alpha_o(v, fxl, dy2, qb, bp.alpha_max, dxb, d2b, eb);
                 float dO;
-                if (qa.w >= 0.f && adjoint_layer(k, aa, ea, qa.w, ccd, wsum, dO) && dO != 0.f)
+                if (qa.y >= 0.f && adjoint_layer(k, aa, ea, qa.y, ccd, wsum, dO) && dO != 0.f)
                   atomicAdd(&rreg[ix], dO);
-                if (qb.w >= 0.f && adjoint_layer(k, ab, eb, qb.w, ccd, wsum, dO) && dO != 0.f)
+                if (qb.y >= 0.f && adjoint_layer(k, ab, eb, qb.y, ccd, wsum, dO) && dO != 0.f)
                   atomicAdd(&rreg[ix - 1], dO);
               }
               evals += ix_start - ix;   // points whose alpha the loop formed
               if (ix == ix0) {
-                const float4 q = prow[ix];
+                const float2 q = prow[ix];
                 float dO, dx, d2, e;
                 ++evals;
-                if (q.w >= 0.f &&
-                    adjoint_layer(k, layer_alpha(v, fxl, dy2, q, bp.alpha_max, dx, d2, e), e, q.w, ccd, wsum, dO) &&
+                if (q.y >= 0.f &&
+                    adjoint_layer(k, layer_alpha_o(v, fxl, dy2, q, bp.alpha_max, dx, d2, e), e, q.y, ccd, wsum, dO) &&
                     dO != 0.f)
                   atomicAdd(&rreg[ix], dO);
               }
@@ -2244,12 +2302,12 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
               if (rowsub + ix > sstart) continue;
               const long long g = v.g_off + rowsub + ix;
               if (g >= v.G) continue;
-              const float4 r = la.rec[g];
-              if (!layer_point_binned(r, bp.alpha_min)) continue;
-              const float4 q = make_float4(layer_qx(v, ix), 0.f, r.z == v.sig ? v.nc2 : ncoef2(r.z), r.w);
+              const float o = la.rec[g].w;
+              if (!layer_o_binned(o, bp.alpha_min)) continue;
               float dO, col[3], daa, dx, d2, e;
-              if (!adjoint_alpha(k, layer_alpha(v, fxl, dy2, q, bp.alpha_max, dx, d2, e), e, q.w, cc, dO, col,
-                                 daa))
+              if (!adjoint_alpha(k, layer_alpha_o(v, fxl, dy2, make_float2(layer_qx(v, ix), o), bp.alpha_max, dx, d2,
+                                                  e),
+                                 e, o, cc, dO, col, daa))
                 continue;
               if (!per_pair) {
                 csum[0] += col[0];
