@@ -1792,38 +1792,75 @@ __device__ __forceinline__ float layer_alpha_o(const LayerView& v, float fxl, fl
 // is checked once per layer).
 __device__ __forceinline__ bool layer_o_binned(float o, float alpha_min) { return o > 0.f && o >= alpha_min; }
 
-// Stages the region's points as {qx, o} (o = -1 for points the per-Gaussian
-// binning would not list): each lane reads the opacities of its kIt points
-// first, all reads in flight together, then writes them.  Returns whether
-// any point is live (the same in every lane).
+// Asynchronous 4-byte copy from global to shared memory (cp.async; bytes past
+// src_bytes are zero-filled), its group commit and the wait for all groups.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, int src_bytes) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Requests a layer region (reg, of at most 32 kIt points) as {qx, o}: the
+// grid coordinates are written at once, the opacities arrive by cp.async
+// (0 past the Gaussian set).  The caller commits the group and waits for it
+// before reading.
 template <int kIt>
-__device__ __forceinline__ bool layer_stage_o(const LayerArgs& la, const LayerView& v, int rx0, int ry0, int rw,
-                                              int rh, float alpha_min, float2* pts) {
+__device__ __forceinline__ void layer_prefetch(const LayerArgs& la, long long g_off, long long G, int nx, float h,
+                                               const int4& reg, float2* pts) {
   const int lane = threadIdx.x & 31;
-  const int npt = rw * rh;
+  const int rw = reg.y - reg.x + 1, npt = rw * (reg.w - reg.z + 1);
   const float inv_rw = 1.f / float(rw);
   const float* op = reinterpret_cast<const float*>(la.rec) + 3;   // the records' opacities
-  float o[kIt];
-  int ixr[kIt];
-#pragma unroll
-  for (int it = 0; it < kIt; ++it) {
-    const int i = lane + 32 * it;
-    const int iyr = int((float(i) + 0.5f) * inv_rw);   // exact for the region sizes staged here
-    ixr[it] = i - iyr * rw;
-    const long long g = v.g_off + (long long)(ry0 + iyr) * v.nx + (rx0 + ixr[it]);
-    o[it] = (i < npt && g < v.G) ? op[4 * g] : -1.f;
-  }
-  bool live = false;
 #pragma unroll
   for (int it = 0; it < kIt; ++it) {
     const int i = lane + 32 * it;
     if (i < npt) {
-      const bool ok = layer_o_binned(o[it], alpha_min);
-      live = live || ok;
-      pts[i] = make_float2(layer_qx(v, rx0 + ixr[it]), ok ? o[it] : -1.f);
+      const int iyr = int((float(i) + 0.5f) * inv_rw);   // exact for the region sizes staged here
+      const int ix = reg.x + (i - iyr * rw);
+      const long long g = g_off + (long long)(reg.z + iyr) * nx + ix;
+      pts[i].x = (float(ix) + 0.5f) * h;
+      const bool in = g < G;
+      cp_async4(&pts[i].y, op + 4 * (in ? g : 0), in ? 4 : 0);
     }
   }
+}
+
+// Requests entry b of a warp's batch (a staged fill layer) into pts.
+template <int kIt>
+__device__ __forceinline__ void layer_request(const LayerArgs& la, long long G, const uint32_t* ids, const int4* regs,
+                                              const float4* locs, const float4* orgs, int b, float2* pts) {
+  layer_prefetch<kIt>(la, ids[b] & ~kLayerBit, G, __float_as_int(orgs[b].z), locs[b].z, regs[b], pts);
+  cp_async_commit();
+}
+
+// Whether any point of a staged region is one the per-Gaussian binning would
+// list (the same in every lane).
+template <int kIt>
+__device__ __forceinline__ bool layer_live(const float2* pts, int npt, float alpha_min) {
+  const int lane = threadIdx.x & 31;
+  bool live = false;
+#pragma unroll
+  for (int it = 0; it < kIt; ++it) {
+    const int i = lane + 32 * it;
+    if (i < npt) live = live || layer_o_binned(pts[i].y, alpha_min);
+  }
   return __any_sync(0xffffffffu, live);
+}
+
+// The next entry of a batch (bits of mask, lowest first, or highest first for
+// the adjoint) that is a fill layer with a region of at most kPts points, or -1.
+template <int kPts, bool kHighFirst>
+__device__ __forceinline__ int next_staged_layer(unsigned int mask, const uint32_t* ids, const int4* regs) {
+  while (mask) {
+    const int b = kHighFirst ? 31 - __clz(mask) : __ffs(mask) - 1;
+    mask &= ~(1u << b);
+    if (ids[b] & kLayerBit) {
+      const int4 r = regs[b];
+      if ((long long)(r.y - r.x + 1) * (r.w - r.z + 1) <= kPts) return b;
+    }
+  }
+  return -1;
 }
 
 template <int TILE, int PPT>
@@ -1855,7 +1892,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
   __shared__ float4 s_win[Gm::kWarps][32];   // a layer's {x0, y0, 1/h, R}
   __shared__ float4 s_org[Gm::kWarps][32];   // a layer's {X0, Y0, nx bits, sigma}
   __shared__ int4 s_rg[Gm::kWarps][32];      // a layer's region for this warp
-  __shared__ float2 s_pt[Gm::kWarps][kPts];
+  __shared__ float2 s_pt[Gm::kWarps][2][kPts];   // staged regions: the current entry's and the next one's
   int s, px, py0;
   float4 wr;
   tile_pixels<TILE, PPT>(bp, s, px, py0, wr);
@@ -1885,6 +1922,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
     return d;
   };
   unsigned int evals = 0, contribs = 0;
+  int cur = 0;   // the buffer holding the current staged entry's region
   // composite one Gaussian (blend constants q) into pixel k; false once the pixel is done
   // the compositing step of Eq. 8 once alpha is known
   auto composite_alpha = [&](int k, float a, const float4& cc, int pos, int sub) {
@@ -1958,6 +1996,12 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
     }
     unsigned int mask = __ballot_sync(0xffffffffu, hit);
     __syncwarp();
+    // the first staged layer entry's region is requested now; each staged
+    // entry requests the next one's before its own walk
+    {
+      const int nb = next_staged_layer<kPts, false>(mask, s_id[w], s_rg[w]);
+      if (nb >= 0) layer_request<kPts / 32>(la, Gset, s_id[w], s_rg[w], s_q[w], s_org[w], nb, s_pt[w][cur]);
+    }
     while (mask) {
       const int b = __ffs(mask) - 1;
       mask &= mask - 1;
@@ -1973,10 +2017,12 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
         const int rw = reg.y - reg.x + 1, rh = reg.w - reg.z + 1;
         const bool staged = (long long)rw * rh <= kPts;
         if (staged) {
-          const bool live = layer_stage_o<kPts / 32>(la, v, rx0, ry0, rw, rh, bp.alpha_min, s_pt[w]);
+          cp_async_wait_all();
           __syncwarp();
-          if (!live) {
-            __syncwarp();
+          const int nb = next_staged_layer<kPts, false>(mask, s_id[w], s_rg[w]);
+          if (nb >= 0) layer_request<kPts / 32>(la, Gset, s_id[w], s_rg[w], s_q[w], s_org[w], nb, s_pt[w][cur ^ 1]);
+          if (!layer_live<kPts / 32>(s_pt[w][cur], rw * rh, bp.alpha_min)) {
+            cur ^= 1;
             continue;
           }
         }
@@ -1996,22 +2042,22 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
             if (staged) {
               // two points per step: both alphas are independent of the
               // compositing state, which then takes them in order
-              const float2* prow = &s_pt[w][(iy - ry0) * rw - rx0];
+              const float2* prow = &s_pt[w][cur][(iy - ry0) * rw - rx0];
               int ix = ix0;
               for (; ix + 1 <= ix1 && !done[k]; ix += 2) {
                 const float2 qa = prow[ix], qb = prow[ix + 1];
                 float dx, d2, ea, eb;
                 const float aa = layer_alpha_o(v, fxl, dy2, qa, bp.alpha_max, dx, d2, ea);
                 const float ab = layer_alpha_o(v, fxl, dy2, qb, bp.alpha_max, dx, d2, eb);
-                if (qa.y >= 0.f) composite_layer(k, aa, wsum, ix, lix);
-                if (qb.y >= 0.f && !done[k]) composite_layer(k, ab, wsum, ix + 1, lix);
+                if (qa.y > 0.f) composite_layer(k, aa, wsum, ix, lix);
+                if (qb.y > 0.f && !done[k]) composite_layer(k, ab, wsum, ix + 1, lix);
               }
               evals += ix - ix0;   // points whose alpha the loop formed
               if (ix <= ix1 && !done[k]) {
                 const float2 q = prow[ix];
                 float dx, d2, e;
                 ++evals;
-                if (q.y >= 0.f) composite_layer(k, layer_alpha_o(v, fxl, dy2, q, bp.alpha_max, dx, d2, e), wsum, ix, lix);
+                if (q.y > 0.f) composite_layer(k, layer_alpha_o(v, fxl, dy2, q, bp.alpha_max, dx, d2, e), wsum, ix, lix);
               }
             } else {
               for (int ix = ix0; ix <= ix1 && !done[k]; ++ix) {
@@ -2036,7 +2082,10 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
             acc[k][2] = fmaf(cc.z, wsum, acc[k][2]);
           }
         }
-        if (staged) __syncwarp();
+        if (staged) {
+          __syncwarp();
+          cur ^= 1;
+        }
       } else {
         const float4 q = s_q[w][b];
 #pragma unroll
@@ -2046,6 +2095,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
         }
       }
     }
+    cp_async_wait_all();   // a request left behind by a warp whose pixels are done
     __syncwarp();
   }
   count_evals(&st->blend_evals, evals);
@@ -2094,7 +2144,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
   __shared__ float4 s_win[Gm::kWarps][32];   // a layer's {x0, y0, 1/h, R}
   __shared__ float4 s_org[Gm::kWarps][32];   // a layer's {X0, Y0, nx bits, sigma}
   __shared__ int4 s_rg[Gm::kWarps][32];      // a layer's region for this warp
-  __shared__ float2 s_pt[Gm::kWarps][kPts];
+  __shared__ float2 s_pt[Gm::kWarps][2][kPts];   // staged regions: the current entry's and the next one's
   __shared__ float s_reg[Gm::kWarps][kPts];
   int s, px, py0;
   float4 wr;
@@ -2180,6 +2230,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
     const float a = gauss_alpha(fx, fy, q, bp.alpha_max, dx, dy, d2, e);
     return adjoint_alpha(k, a, e, q.w, cc, dO, col, daa);
   };
+  int cur = 0;   // the buffer holding the current staged entry's region
   for (int base = ((wmax - 1) >> 5) << 5; base >= 0 && wmax > 0; base -= 32) {
     const int j = base + lane;
     bool hit = false;
@@ -2215,6 +2266,13 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
     }
     unsigned int mask = __ballot_sync(0xffffffffu, hit);
     __syncwarp();
+    // the first staged layer entry's region is requested now; each staged
+    // entry requests the next one's before its own walk (every hit entry is
+    // walked: wmax bounds the batch)
+    if (!per_pair) {
+      const int nb = next_staged_layer<kPts, true>(mask, s_id[w], s_rg[w]);
+      if (nb >= 0) layer_request<kPts / 32>(la, Gset, s_id[w], s_rg[w], s_q[w], s_org[w], nb, s_pt[w][cur]);
+    }
     while (mask) {
       const int b = 31 - __clz(mask);
       mask &= ~(1u << b);
@@ -2228,7 +2286,18 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
           want[k] = jpos < last[k];
           any = any || want[k];
         }
-        if (!__any_sync(0xffffffffu, any)) continue;   // no pixel of the warp walks this far back
+        if (!__any_sync(0xffffffffu, any)) {   // no pixel of the warp walks this far back
+          const int4 r = s_rg[w][b];
+          if (!per_pair && (long long)(r.y - r.x + 1) * (r.w - r.z + 1) <= kPts) {
+            // its region was requested: pass the request on to the next entry
+            cp_async_wait_all();
+            __syncwarp();
+            const int nb = next_staged_layer<kPts, true>(mask, s_id[w], s_rg[w]);
+            if (nb >= 0) layer_request<kPts / 32>(la, Gset, s_id[w], s_rg[w], s_q[w], s_org[w], nb, s_pt[w][cur ^ 1]);
+            cur ^= 1;
+          }
+          continue;
+        }
         const uint32_t g0 = id & ~kLayerBit;
         const int c = __float_as_int(s_isig[w][b]);
         const int4 reg = s_rg[w][b];
@@ -2239,10 +2308,12 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
         const bool staged = !per_pair && (long long)rw * rh <= kPts;
         if (staged) {
           for (int i = lane; i < rw * rh; i += 32) s_reg[w][i] = 0.f;
-          const bool live = layer_stage_o<kPts / 32>(la, v, rx0, ry0, rw, rh, bp.alpha_min, s_pt[w]);
+          cp_async_wait_all();
           __syncwarp();
-          if (!live) {
-            __syncwarp();
+          const int nb = next_staged_layer<kPts, true>(mask, s_id[w], s_rg[w]);
+          if (nb >= 0) layer_request<kPts / 32>(la, Gset, s_id[w], s_rg[w], s_q[w], s_org[w], nb, s_pt[w][cur ^ 1]);
+          if (!layer_live<kPts / 32>(s_pt[w][cur], rw * rh, bp.alpha_min)) {
+            cur ^= 1;
             continue;
           }
         }
@@ -2261,7 +2332,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
             for (int iy = iy1; iy >= iy0; --iy) {
               const int rowsub = iy * v.nx;
               const int ridx = (iy - ry0) * rw - rx0;
-              const float2* prow = &s_pt[w][ridx];
+              const float2* prow = &s_pt[w][cur][ridx];
               float* rreg = &s_reg[w][ridx];
               const float dy = layer_dy(v, fyl, iy), dy2 = __fmul_rn(dy, dy);
               // the last layer of the pixel starts at its last composited point
@@ -2274,9 +2345,9 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
                 const float aa = layer_alpha_o(v, fxl, dy2, qa, bp.alpha_max, dxa, d2a, ea);
                 const float ab = layer_alpha_o(v, fxl, dy2, qb, bp.alpha_max, dxb, d2b, eb);
                 float dO;
-                if (qa.y >= 0.f && adjoint_layer(k, aa, ea, qa.y, ccd, wsum, dO) && dO != 0.f)
+                if (qa.y > 0.f && adjoint_layer(k, aa, ea, qa.y, ccd, wsum, dO) && dO != 0.f)
                   atomicAdd(&rreg[ix], dO);
-                if (qb.y >= 0.f && adjoint_layer(k, ab, eb, qb.y, ccd, wsum, dO) && dO != 0.f)
+                if (qb.y > 0.f && adjoint_layer(k, ab, eb, qb.y, ccd, wsum, dO) && dO != 0.f)
                   atomicAdd(&rreg[ix - 1], dO);
               }
               evals += ix_start - ix;   // points whose alpha the loop formed
@@ -2284,7 +2355,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
                 const float2 q = prow[ix];
                 float dO, dx, d2, e;
                 ++evals;
-                if (q.y >= 0.f &&
+                if (q.y > 0.f &&
                     adjoint_layer(k, layer_alpha_o(v, fxl, dy2, q, bp.alpha_max, dx, d2, e), e, q.y, ccd, wsum, dO) &&
                     dO != 0.f)
                   atomicAdd(&rreg[ix], dO);
@@ -2346,6 +2417,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
             }
           }
           __syncwarp();
+          cur ^= 1;
         }
       } else {
         const float4 q = s_q[w][b];
@@ -2389,6 +2461,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
         }
       }
     }
+    cp_async_wait_all();
     __syncwarp();
   }
   count_evals(&st->blend_bwd_evals, evals);
