@@ -43,20 +43,20 @@ PEAKS_FALLBACK = dict(hbm_gbs=6400.0, sm_max_mhz=2032.0)
 # the records it writes stay in L2, at 2048 they do not, so its traffic does
 # not grow in proportion.
 TRAFFIC = dict(
-    blend_bwd=dict(bytes=57531648, units=2027197, unit="gaussians", tile=8, layers=1,
-                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="ba08ad6f9dcd19fa"),
-    blend_fwd=dict(bytes=27530752, units=2027197, unit="gaussians", tile=8, layers=1,
-                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="ba08ad6f9dcd19fa"),
+    blend_bwd=dict(bytes=57579264, units=2027197, unit="gaussians", tile=8, layers=1,
+                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="a956187ad189ee89"),
+    blend_fwd=dict(bytes=27760640, units=2027197, unit="gaussians", tile=8, layers=1,
+                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="a956187ad189ee89"),
     chain=dict(bytes=15444224, units=2027197, unit="gaussians", tile=None, layers=None,
-               src="paper_2606_31764_b300/csrc/ns_backward.cu", sha="762a00cd74cc7909"),
+               src="paper_2606_31764_b300/csrc/ns_backward.cu", sha="b78eb000dfbb283b"),
     bin_count=dict(bytes=338176, units=2027197, unit="gaussians", tile=8, layers=1,
-                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="ba08ad6f9dcd19fa"),
-    bin_emit=dict(bytes=63744, units=2027197, unit="gaussians", tile=8, layers=1,
-                  src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="ba08ad6f9dcd19fa"),
-    plan=dict(bytes=2105344, units=512, unit="curves", tile=None, layers=None,
-              src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="215421c85426d63a"),
-    boundary=dict(bytes=1277440, units=512, unit="curves", tile=None, layers=None,
-                  src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="215421c85426d63a"),
+                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="a956187ad189ee89"),
+    bin_emit=dict(bytes=63488, units=2027197, unit="gaussians", tile=8, layers=1,
+                  src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="a956187ad189ee89"),
+    plan=dict(bytes=2104576, units=512, unit="curves", tile=None, layers=None,
+              src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="546259017b024a84"),
+    boundary=dict(bytes=1276672, units=512, unit="curves", tile=None, layers=None,
+                  src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="546259017b024a84"),
 )
 
 
