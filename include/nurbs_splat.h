@@ -28,6 +28,11 @@
  *     with the size that would have been needed.
  *   - Coordinates are pixels; pixel (x, y) is sampled at (x + 1/2, y + 1/2);
  *     y grows downwards.  Images are float32 [n_scenes, height, width, channels].
+ *   - The library's kernels are launched with programmatic stream
+ *     serialization (programmatic dependent launch): each begins by waiting
+ *     for the kernel before it in the stream, so results and the order of
+ *     memory effects are those of a plain stream.  Setting the environment
+ *     variable NS_PDL=0 before the first call launches them without it.
  */
 #ifndef NURBS_SPLAT_H
 #define NURBS_SPLAT_H
@@ -276,7 +281,9 @@ ns_status splat_forward(const ns_curves* curves, const ns_gaussians* g,
  *     gradients of the exponent A dx^2 + B2 dx dy + C dy^2's coefficients.
  *     When dgauss is NULL and `out` is given, the workspace holds them and the
  *     centre and sigma gradients of fill Gaussians, which the chain does not
- *     use (their grid is fixed), are not computed.
+ *     use (their grid is fixed), are not computed; with fill layers the fill
+ *     Gaussians' opacity gradients are then kept as one float per Gaussian
+ *     and only the contour Gaussians' rows are cleared and written.
  *   zero_outputs: 1 zeroes *out before accumulating, 0 adds to it.
  */
 ns_status splat_backward(const ns_curves* curves, const ns_gaussians* g,
