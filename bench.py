@@ -573,7 +573,8 @@ def run_gpu(args, dist, rank, world):
     out["geometry"] = run_geometry(torch, step, args)
     out["schedule"] = run_schedule(torch, step, tuning)
     if not args.no_per_scene:
-        out["per_scene"] = run_per_scene(torch, step, args, value)
+        out["per_scene"] = run_per_scene(torch, step, args, value,
+                                         raster={k: int(tuning[k]) for k in ("tile", "fill_layers", "ppt_fwd", "ppt_bwd")})
         out["long_spline"] = run_long_spline(torch, args)
         out["layerwise"] = run_layerwise(torch)
     return out, step
@@ -884,7 +885,7 @@ def run_e2e(torch, step, g1, args):
                        "overlapping the neighbouring steps")
 
 
-def run_per_scene(torch, step, args, batched_value):
+def run_per_scene(torch, step, args, batched_value, raster=None):
     """The unbatched comparison: the batched 64-scene workload (256x256 RGB,
     1-40 closed paths per scene, half filled at h = 1) launched scene by scene
     with host reads of the counts between stages and no graph, against the
@@ -893,6 +894,7 @@ def run_per_scene(torch, step, args, batched_value):
     sc = scenes.config4()
     K = max(2, min(args.steps, 5))
     # batched
+    sc = sc.with_raster(**(raster or {}))   # the headline's tuned raster, for both paths
     bstep = Step(sc, capacity=(4_000_000, 8_000_000, 200_000))
     gb = capture(torch, bstep)
     for _ in range(2):
@@ -928,7 +930,7 @@ def run_per_scene(torch, step, args, batched_value):
     return dict(workload="batched-64x256: 64 scenes 256x256 RGB, 1-40 closed paths each",
                 batched_gaussians_per_s=round(Gb / tb, 1), per_scene_gaussians_per_s=round(Gs / tp, 1),
                 speedup=round((Gb / tb) / (Gs / tp), 2), gaussians_per_step=Gb, ms_batched=round(tb * 1e3, 3),
-                ms_per_scene_path=round(tp * 1e3, 3))
+                ms_per_scene_path=round(tp * 1e3, 3), raster=raster)
 
 
 # ----------------------------------------------------------------------------
