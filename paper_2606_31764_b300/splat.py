@@ -177,9 +177,11 @@ class Splatter:
         bits = {"weights": B.NS_FROZEN_WEIGHTS, "knots": B.NS_FROZEN_KNOTS}
         return sum(bits[f] for f in set(frozen))
 
-    def backward(self, key, tau, color, dimage, grads=None, chain=True, frozen=()):
+    def backward(self, key, tau, color, dimage, grads=None, chain=True, frozen=(), rows=False):
         """splat_backward; frozen may name "weights" and/or "knots": their
-        gradients are not formed (dtau is left untouched for frozen knots)."""
+        gradients are not formed (dtau is left untouched for frozen knots).
+        rows=True also writes every per-Gaussian gradient row to self.dgauss
+        alongside the chain."""
         cs = self.dev.struct(key, tau, color)
         if grads is None:
             grads = (torch.empty_like(key), torch.empty_like(tau), torch.empty_like(color))
@@ -189,7 +191,7 @@ class Splatter:
         # to self.dgauss when no chain is asked for; with the chain the workspace
         # holds them and the library skips what the chain does not use
         B.call("splat_backward", C.byref(cs), C.byref(self.g), C.byref(self.sp), C.byref(self.rp),
-               C.byref(self.cap), _ptr(dimage.contiguous()), None if chain else _ptr(self.dgauss),
+               C.byref(self.cap), _ptr(dimage.contiguous()), _ptr(self.dgauss) if (rows or not chain) else None,
                C.byref(out) if out is not None else None, C.c_int32(1), _ptr(self.ws),
                C.c_size_t(self.ws_bytes), _stream())
         return grads

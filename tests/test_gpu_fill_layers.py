@@ -117,3 +117,25 @@ def test_layers_need_far_fewer_pairs():
     a = run_step(sc.with_raster(tile=8, fill_layers=0))
     b = run_step(sc.with_raster(tile=8, fill_layers=1))
     assert b["report"].pairs * 20 < a["report"].pairs
+
+
+def test_compact_opacity_gradients_match_rows():
+    """With fill layers and the per-Gaussian rows left to the workspace, the
+    step keeps the fill Gaussians' opacity gradients in one float per Gaussian
+    and clears only the contour Gaussians' rows.  The curve gradients equal
+    those of the same backward writing every per-Gaussian row (within the
+    rounding of atomic sums), and a second call gives them again (nothing of
+    the first is left in the workspace)."""
+    sc = scenes.small_closed(352, n_curves=4, size=64, filled="alternate", h=1.0).with_raster(
+        **dict(scenes.RASTER_DEFAULTS, tile=8, fill_layers=1))
+    sp, img, rep, (k, t, c), G = run_scene(sc)
+    dimg = torch.as_tensor(np.random.default_rng(353).standard_normal(tuple(img.shape)).astype(np.float32),
+                           device="cuda")
+    a = [x.cpu().numpy() for x in sp.backward(k, t, c, dimg)]
+    b = [x.cpu().numpy() for x in sp.backward(k, t, c, dimg, rows=True)]
+    a2 = [x.cpu().numpy() for x in sp.backward(k, t, c, dimg)]
+    torch.cuda.synchronize()
+    for nm, x, y, z in zip(("dkey", "dtau", "dcolor"), a, b, a2):
+        assert np.isfinite(x).all(), nm
+        assert _rel(x, y) <= 1e-5, nm
+        assert _rel(z, x) <= 1e-5, nm
