@@ -842,7 +842,7 @@ def run_e2e(torch, step, g1, args):
     h2d = hin.numel() * 4
     d2h = A_out.numel() * 4
     G = step.gaussians()
-    K = max(2, args.steps // 2)
+    K = max(10, args.steps)
     s0 = torch.cuda.current_stream()
     cs = torch.cuda.Stream()
     up = [torch.cuda.Event() for _ in range(2)]       # inputs of buffer b uploaded
