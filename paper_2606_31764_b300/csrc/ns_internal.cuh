@@ -314,25 +314,6 @@ __device__ __forceinline__ void eval_curve(const float4* __restrict__ key, const
   e.C[2] = e.S[2] * iw;
 }
 
-// |C'_xy(u)| by the quotient rule (Eq. 2), after eval_curve.
-template <int P>
-__device__ __forceinline__ float speed_xy(const Eval<P>& e) {
-  float dN[P + 1];
-  basis_deriv<P>(e.t, dN);
-  float dS0 = 0.f, dS1 = 0.f, dW = 0.f;
-#pragma unroll
-  for (int l = 0; l <= P; ++l) {
-    const float nw = dN[l] * e.cp[l].w;
-    dS0 = fmaf(nw, e.cp[l].x, dS0);
-    dS1 = fmaf(nw, e.cp[l].y, dS1);
-    dW += nw;
-  }
-  const float iw = 1.f / e.W;
-  const float dx = (dS0 - e.C[0] * dW) * iw;   // (W S' - S W')/W^2 = (S' - C W')/W
-  const float dy = (dS1 - e.C[1] * dW) * iw;
-  return sqrtf(dx * dx + dy * dy);
-}
-
 // Reverse of C = S/W at one evaluated point: given gC = dL/dC (x, y, s), adds
 // dL/d{x, y, s, w} of the span's control points to dcp[l], dL/dU of its 2P
 // knots to dkn (as basis_bwd) and returns dL/du in *du.  Without KNOTS (knot

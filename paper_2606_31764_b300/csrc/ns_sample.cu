@@ -97,27 +97,6 @@ __device__ __forceinline__ float block_sum(float v, float* red) {
   return red[0];
 }
 
-__device__ __forceinline__ float block_reduce_minmax(float v, float* red, bool is_max) {
-  for (int o = 16; o > 0; o >>= 1) {
-    const float x = __shfl_xor_sync(0xffffffffu, v, o);
-    v = is_max ? fmaxf(v, x) : fminf(v, x);
-  }
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) red[w] = v;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    float s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : (is_max ? -FLT_MAX : FLT_MAX);
-    for (int o = 16; o > 0; o >>= 1) {
-      const float x = __shfl_xor_sync(0xffffffffu, s, o);
-      s = is_max ? fmaxf(s, x) : fminf(s, x);
-    }
-    if (threadIdx.x == 0) red[0] = s;
-  }
-  __syncthreads();
-  return red[0];
-}
-
 // |C'_xy(u)| (Eq. 2) from the span's Taylor form: C = S/W, C' = (S' - C W')/W.
 template <int P>
 __device__ __forceinline__ float span_speed(const SpanPoly<P>& sp, float u) {
