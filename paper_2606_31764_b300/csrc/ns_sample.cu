@@ -112,9 +112,12 @@ __device__ __forceinline__ float span_speed(const SpanPoly<P>& sp, float u) {
     S1 = fmaf(S1, t, sp.A[k][1]);
     W = fmaf(W, t, sp.A[k][2]);
   }
-  const float iw = 1.f / W;
+  // the reciprocal and the square root of the special-function unit (about
+  // 1e-7 relative each; the sum over the nodes carries more rounding than that)
+  const float iw = __fdividef(1.f, W);
   const float dx = (D0 - S0 * iw * DW) * iw, dy = (D1 - S1 * iw * DW) * iw;
-  return sqrtf(dx * dx + dy * dy);
+  const float v2 = dx * dx + dy * dy;
+  return v2 > 0.f ? v2 * rsqrtf(v2) : 0.f;
 }
 
 // The Taylor form {m, A[0..P][3]} of every non-empty span of every curve, one
