@@ -55,7 +55,7 @@ struct DevState {
   // fill_cull): the culled count, and (in the workspace) each curve's box of
   // live grid points; the binning uses them when its alpha_min is the same
   float cull_thr;                      // the threshold they were counted for (-1: none)
-  int pad2;
+  int sdf_next;                        // the next fill task k_fill_sdf hands out (k_boundary_box resets it)
   unsigned long long culled_s;         // fill Gaussians with opacity below cull_thr (sigma > 0)
 };
 

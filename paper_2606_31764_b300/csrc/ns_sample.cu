@@ -469,7 +469,10 @@ __global__ void __launch_bounds__(256) k_boundary_box(ns_curves cv, ns_sample_pa
   grid_dep_wait();
   const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (c == 0 && lane == 0) st->cull_thr = sp.fill_cull;   // the threshold k_fill_sdf counts for
+  if (c == 0 && lane == 0) {
+    st->cull_thr = sp.fill_cull;   // the threshold k_fill_sdf counts for
+    st->sdf_next = 0;
+  }
   if (c < cv.n_curves && lane == 0) lbox[c] = make_int4(0x7fffffff, 0x7fffffff, -1, -1);
   if (c >= cv.n_curves) return;
   const CurvePlan pl = plan[c];
@@ -821,6 +824,8 @@ __device__ void polyline_scan(const float4* __restrict__ bl, const float4* __res
   }
 }
 
+constexpr int kSdfClaim = 2;   // fill tasks a block claims at a time
+
 template <int TE>
 __global__ void __launch_bounds__(TE * TE, 2048 / (TE * TE)) k_fill_sdf(ns_curves cv, ns_sample_params sp,
                                                      const CurvePlan* __restrict__ plan, const int* __restrict__ order,
@@ -854,12 +859,28 @@ __global__ void __launch_bounds__(TE * TE, 2048 / (TE * TE)) k_fill_sdf(ns_curve
   if (tid < 5) s_box[0][tid] = tid < 2 ? 0x7fffffff : (tid < 4 ? -1 : 0);
   __syncthreads();
   int buf = 0;
-  for (int task = blockIdx.x; task < n_fill; task += gridDim.x) {
+  // blocks claim runs of kSdfClaim consecutive tasks from a counter: the tiles
+  // of a run mostly belong to one curve, whose polyline and cluster boxes then
+  // stay in the SM's L1, and the claims balance the blocks' work
+  __shared__ int s_claim;
+  int task = 0, task_end = 0;
+  for (;;) {
+    if (task == task_end) {
+      if (tid == 0) s_claim = atomicAdd(&st->sdf_next, kSdfClaim);
+      __syncthreads();
+      task = s_claim;
+      task_end = min(n_fill, task + kSdfClaim);
+      __syncthreads();   // s_claim is read by every thread before it is claimed again
+      if (task >= n_fill) break;
+    }
     const int c = task_curve(tmap, tcap, n_fill, plan, order, nc, task, true);
     const CurvePlan pl = plan[c];
     // a curve whose polyline did not fit the boundary capacity emits nothing
     // (block-uniform: the buffers stay as they are)
-    if (pl.kind != kFill || (long long)pl.b_off + pl.M > bcap) continue;
+    if (pl.kind != kFill || (long long)pl.b_off + pl.M > bcap) {
+      ++task;
+      continue;
+    }
     const int k = task - pl.chunk_off;
     int ix, iy;
     const bool in_grid = fill_task_point(k, pl.nx, pl.ny, tid, TE, ix, iy);
@@ -1047,6 +1068,7 @@ __global__ void __launch_bounds__(TE * TE, 2048 / (TE * TE)) k_fill_sdf(ns_curve
       if (s_box[buf][4]) atomicAdd(&st->culled_s, (unsigned long long)s_box[buf][4]);
     }
     buf ^= 1;
+    ++task;
   }
 }
 
@@ -1140,11 +1162,11 @@ extern "C" ns_status nurbs_sample(const ns_curves* curves, const ns_sample_param
     carveout = true;
   }
   if (ftile == 8)
-    NS_LAUNCH(NS_KERNEL_FILL_SDF, k_fill_sdf<8>, num_sms() * 64, 64, 0, s, *curves, *sp, plan, order, bloc,
+    NS_LAUNCH(NS_KERNEL_FILL_SDF, k_fill_sdf<8>, num_sms() * 32, 64, 0, s, *curves, *sp, plan, order, bloc,
               at<const float2>(ws, L.o_glo), cbox, st, reinterpret_cast<float4*>(out->rec), out->curve, out->aux,
               cap->gaussians, cap->boundary, tmap, (long long)L.tcap, lbox);
   else
-    NS_LAUNCH(NS_KERNEL_FILL_SDF, k_fill_sdf<16>, num_sms() * 16, 256, 0, s, *curves, *sp, plan, order, bloc,
+    NS_LAUNCH(NS_KERNEL_FILL_SDF, k_fill_sdf<16>, num_sms() * 8, 256, 0, s, *curves, *sp, plan, order, bloc,
               at<const float2>(ws, L.o_glo), cbox, st, reinterpret_cast<float4*>(out->rec), out->curve, out->aux,
               cap->gaussians, cap->boundary, tmap, (long long)L.tcap, lbox);
   NS_LAUNCH(NS_KERNEL_EMIT, k_emit, grid, 256, 0, s, *curves, *sp, plan, order, knots, st,
