@@ -53,10 +53,10 @@ TRAFFIC = dict(
                    src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="a956187ad189ee89"),
     bin_emit=dict(bytes=63488, units=2027197, unit="gaussians", tile=8, layers=1,
                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="a956187ad189ee89"),
-    plan=dict(bytes=2104576, units=512, unit="curves", tile=None, layers=None,
-              src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="546259017b024a84"),
-    boundary=dict(bytes=1276672, units=512, unit="curves", tile=None, layers=None,
-                  src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="546259017b024a84"),
+    plan=dict(bytes=2102016, units=512, unit="curves", tile=None, layers=None,
+              src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="87451ed3e021526b"),
+    boundary=dict(bytes=1278976, units=512, unit="curves", tile=None, layers=None,
+                  src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="87451ed3e021526b"),
 )
 
 
