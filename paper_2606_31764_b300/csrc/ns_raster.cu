@@ -1964,6 +1964,19 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
     lix = ix;
     ++contribs;
   };
+  // the same without branches for a staged point of opacity o (o <= 0: not
+  // listed), after which pixel k may be done
+  auto composite_point = [&](int k, float a, float o, float& wsum, int ix, int& lix) {
+    const bool ok = o > 0.f && a >= bp.alpha_min && !done[k];
+    const float test = T[k] * (1.f - a);
+    const bool stop = ok && test < bp.t_min;
+    const bool comp = ok && !stop;
+    done[k] = done[k] || stop;
+    wsum = comp ? fmaf(a, T[k], wsum) : wsum;
+    T[k] = comp ? test : T[k];
+    lix = comp ? ix : lix;
+    contribs += comp ? 1u : 0u;
+  };
   for (int base = 0; base < n && !__all_sync(0xffffffffu, all_done()); base += 32) {
     const int j = base + lane;
     bool hit = false;
@@ -2049,15 +2062,15 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
                 float dx, d2, ea, eb;
                 const float aa = layer_alpha_o(v, fxl, dy2, qa, bp.alpha_max, dx, d2, ea);
                 const float ab = layer_alpha_o(v, fxl, dy2, qb, bp.alpha_max, dx, d2, eb);
-                if (qa.y > 0.f) composite_layer(k, aa, wsum, ix, lix);
-                if (qb.y > 0.f && !done[k]) composite_layer(k, ab, wsum, ix + 1, lix);
+                composite_point(k, aa, qa.y, wsum, ix, lix);
+                composite_point(k, ab, qb.y, wsum, ix + 1, lix);
               }
               evals += ix - ix0;   // points whose alpha the loop formed
               if (ix <= ix1 && !done[k]) {
                 const float2 q = prow[ix];
                 float dx, d2, e;
                 ++evals;
-                if (q.y > 0.f) composite_layer(k, layer_alpha_o(v, fxl, dy2, q, bp.alpha_max, dx, d2, e), wsum, ix, lix);
+                composite_point(k, layer_alpha_o(v, fxl, dy2, q, bp.alpha_max, dx, d2, e), q.y, wsum, ix, lix);
               }
             } else {
               for (int ix = ix0; ix <= ix1 && !done[k]; ++ix) {
@@ -2145,7 +2158,9 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
   __shared__ float4 s_org[Gm::kWarps][32];   // a layer's {X0, Y0, nx bits, sigma}
   __shared__ int4 s_rg[Gm::kWarps][32];      // a layer's region for this warp
   __shared__ float2 s_pt[Gm::kWarps][2][kPts];   // staged regions: the current entry's and the next one's
-  __shared__ float s_reg[Gm::kWarps][kPts];
+  // the opacity gradients of the current entry's region; zero between
+  // entries (each flush clears what it reads)
+  __shared__ __align__(16) float s_reg[Gm::kWarps][kPts];
   int s, px, py0;
   float4 wr;
   tile_pixels<TILE, PPT>(bp, s, px, py0, wr);
@@ -2182,6 +2197,8 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
     wmax = max(wmax, last[k]);
   }
   for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+  for (int i = lane; i < kPts; i += 32) s_reg[w][i] = 0.f;
+  __syncwarp();
   unsigned int evals = 0;
   // the adjoint of one pair of pixel k (blend constants q, colour cc):
   // returns false below alpha_min; else the opacity gradient dO, the colour
@@ -2223,6 +2240,19 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
     S[k] = fmaf(a, diff, S[k]);
     dO = __fmul_rn(ow, e) < bp.alpha_max ? e * (diff * T[k]) : 0.f;
     return true;
+  };
+  // the same without branches for a staged point (o = ow): a point below
+  // alpha_min (or not listed, o <= 0) leaves T, wsum and S as they are and
+  // returns a zero gradient
+  auto adjoint_point = [&](int k, float a, float e, float ow, float ccd, float& wsum) {
+    const bool ok = ow > 0.f && a >= bp.alpha_min;
+    const float Tn = __fdividef(T[k], 1.f - a);
+    T[k] = ok ? Tn : T[k];
+    const float ae = ok ? a : 0.f;
+    wsum = fmaf(ae, T[k], wsum);
+    const float diff = ccd - S[k];
+    S[k] = fmaf(ae, diff, S[k]);
+    return ok && __fmul_rn(ow, e) < bp.alpha_max ? e * (diff * T[k]) : 0.f;
   };
   auto adjoint = [&](int k, float fy, const float4& q, const float4& cc, float& dO, float col[3], float& daa,
                      float& dx, float& dy, float& d2) {
@@ -2306,8 +2336,14 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
         const int rx0 = reg.x, ry0 = reg.z;
         const int rw = reg.y - reg.x + 1, rh = reg.w - reg.z + 1;
         const bool staged = !per_pair && (long long)rw * rh <= kPts;
+        // the region's opacity gradients in s_reg: row r at r rs + a_r, a_r
+        // the row's first Gaussian index mod 4, so that an aligned float4 of
+        // s_reg holds 4 consecutive Gaussians (quads) when that fits, else
+        // packed rows (rs = rw, a_r = 0)
+        const int rs_q = (rw + 6) & ~3;
+        const bool quads = staged && la.dop != nullptr && rh * rs_q <= kPts;
+        const int rs = quads ? rs_q : rw;
         if (staged) {
-          for (int i = lane; i < rw * rh; i += 32) s_reg[w][i] = 0.f;
           cp_async_wait_all();
           __syncwarp();
           const int nb = next_staged_layer<kPts, true>(mask, s_id[w], s_rg[w]);
@@ -2331,9 +2367,8 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
             float wsum = 0.f;
             for (int iy = iy1; iy >= iy0; --iy) {
               const int rowsub = iy * v.nx;
-              const int ridx = (iy - ry0) * rw - rx0;
-              const float2* prow = &s_pt[w][cur][ridx];
-              float* rreg = &s_reg[w][ridx];
+              const float2* prow = &s_pt[w][cur][(iy - ry0) * rw - rx0];
+              float* rreg = &s_reg[w][(iy - ry0) * rs + (quads ? int((g0 + uint32_t(rowsub + rx0)) & 3u) : 0) - rx0];
               const float dy = layer_dy(v, fyl, iy), dy2 = __fmul_rn(dy, dy);
               // the last layer of the pixel starts at its last composited point
               int ix = min(ix1, sstart - rowsub);
@@ -2344,21 +2379,18 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
                 float dxa, d2a, ea, dxb, d2b, eb;
                 const float aa = layer_alpha_o(v, fxl, dy2, qa, bp.alpha_max, dxa, d2a, ea);
                 const float ab = layer_alpha_o(v, fxl, dy2, qb, bp.alpha_max, dxb, d2b, eb);
-                float dO;
-                if (qa.y > 0.f && adjoint_layer(k, aa, ea, qa.y, ccd, wsum, dO) && dO != 0.f)
-                  atomicAdd(&rreg[ix], dO);
-                if (qb.y > 0.f && adjoint_layer(k, ab, eb, qb.y, ccd, wsum, dO) && dO != 0.f)
-                  atomicAdd(&rreg[ix - 1], dO);
+                const float dOa = adjoint_point(k, aa, ea, qa.y, ccd, wsum);
+                if (dOa != 0.f) atomicAdd(&rreg[ix], dOa);
+                const float dOb = adjoint_point(k, ab, eb, qb.y, ccd, wsum);
+                if (dOb != 0.f) atomicAdd(&rreg[ix - 1], dOb);
               }
               evals += ix_start - ix;   // points whose alpha the loop formed
               if (ix == ix0) {
                 const float2 q = prow[ix];
-                float dO, dx, d2, e;
+                float dx, d2, e;
                 ++evals;
-                if (q.y > 0.f &&
-                    adjoint_layer(k, layer_alpha_o(v, fxl, dy2, q, bp.alpha_max, dx, d2, e), e, q.y, ccd, wsum, dO) &&
-                    dO != 0.f)
-                  atomicAdd(&rreg[ix], dO);
+                const float dO = adjoint_point(k, layer_alpha_o(v, fxl, dy2, q, bp.alpha_max, dx, d2, e), e, q.y, ccd, wsum);
+                if (dO != 0.f) atomicAdd(&rreg[ix], dO);
               }
             }
             csum[0] = fmaf(wsum, dI[k][0], csum[0]);
@@ -2407,13 +2439,39 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
         }
         if (staged) {
           __syncwarp();
-          const float inv_rw = 1.f / float(rw);
-          for (int i = lane; i < rw * rh; i += 32) {
-            const float val = s_reg[w][i];
-            if (val != 0.f) {
-              const int iyr = int((float(i) + 0.5f) * inv_rw);
-              const int ixr = i - iyr * rw;
-              atomicAdd(layer_dop(la, dgauss, v.g_off + (long long)(ry0 + iyr) * v.nx + rx0 + ixr, kRow), val);
+          if (quads) {
+            // one vector reduction per quad of consecutive Gaussians (adding
+            // zeros for the padding: other tiles' points, or none)
+            const int qr = rs >> 2;
+            const float inv_qr = 1.f / float(qr);
+            for (int i = lane; i < rh * qr; i += 32) {
+              const int r = int((float(i) + 0.5f) * inv_qr);   // exact for the region sizes staged here
+              const int jq = i - r * qr;
+              float4* sp = reinterpret_cast<float4*>(&s_reg[w][r * rs + 4 * jq]);
+              const float4 val = *sp;
+              if (val.x != 0.f || val.y != 0.f || val.z != 0.f || val.w != 0.f) {
+                *sp = make_float4(0.f, 0.f, 0.f, 0.f);
+                const long long gq = ((v.g_off + (long long)(ry0 + r) * v.nx + rx0) & ~3LL) + 4 * jq;
+                if (gq + 4 <= la.gcap) {
+                  red_add_v4(la.dop + gq, val.x, val.y, val.z, val.w);
+                } else {
+                  const float vq[4] = {val.x, val.y, val.z, val.w};
+#pragma unroll
+                  for (int e = 0; e < 4; ++e)
+                    if (vq[e] != 0.f && gq + e < la.gcap) atomicAdd(la.dop + gq + e, vq[e]);
+                }
+              }
+            }
+          } else {
+            const float inv_rw = 1.f / float(rw);
+            for (int i = lane; i < rw * rh; i += 32) {
+              const float val = s_reg[w][i];
+              if (val != 0.f) {
+                s_reg[w][i] = 0.f;
+                const int iyr = int((float(i) + 0.5f) * inv_rw);
+                const int ixr = i - iyr * rw;
+                atomicAdd(layer_dop(la, dgauss, v.g_off + (long long)(ry0 + iyr) * v.nx + rx0 + ixr, kRow), val);
+              }
             }
           }
           __syncwarp();
