@@ -146,13 +146,13 @@ __global__ void __launch_bounds__(256, 8) k_chain(ns_curves cv, ChainParams cp, 
       const bool valid = in_grid && g < gcap;
       // a culled point (opacity 0, marked far) is never composited: its row
       // is zero and nothing of it is read.  With dop (fill layers) the
-      // opacity gradient is there and the colour went to the curve directly.
+      // opacity gradient is there (zero for a culled point: it is loaded
+      // beside the aux code instead of after it) and the colour went to the
+      // curve directly.
       const int aux = valid ? gaux[g] : 0;
       float4 g1 = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (valid && aux != kAuxFar) {
-        if (dop) g1.x = dop[g];
-        else g1 = reinterpret_cast<const float4*>(dgauss)[row4 * g + 1];
-      }
+      if (valid && dop) g1.x = dop[g];
+      else if (valid && aux != kAuxFar) g1 = reinterpret_cast<const float4*>(dgauss)[row4 * g + 1];
       const int B = pl.M;
       float dO = 0.f;
       const float gop = g1.x;   // row layout {dmu_x, dmu_y, dsigma, 0, do, dr, dg, db}

@@ -139,3 +139,52 @@ def test_compact_opacity_gradients_match_rows():
         assert np.isfinite(x).all(), nm
         assert _rel(x, y) <= 1e-5, nm
         assert _rel(z, x) <= 1e-5, nm
+
+
+def _corner_scene(r):
+    """A filled circle past the bottom right corner, behind a filled star in
+    the middle.  The Gaussians are laid out front to back, so the circle's grid
+    comes last in the batch; the canvas clips it, so its last grid points lie
+    inside the shape and are live."""
+    rng = np.random.default_rng(354)
+    H, W = 40, 48
+    b = scenes._Builder(1, H, W, 3)
+    b.add(0, 2, scenes.circle_keys(W - 3.0, H - 2.0, r), scenes.circle_tau(), (0.9, 0.3, 0.1, 0.85), True, True)
+    b.add(0, 3, scenes.star_keys(rng, 18.0, 17.0, 9.0, 9, 1.0, 2.0), rng.uniform(0.5, 1.5, 9),
+          (0.2, 0.5, 0.8, 0.9), True, True)
+    tgt = scenes.blob_target(rng, 1, H, W, 3, 6)
+    return b.build("corner-circle", tgt, dict(scenes.SAMPLE_DEFAULTS, h=1.0),
+                   dict(scenes.RASTER_DEFAULTS, tile=8, fill_layers=1))
+
+
+def test_opacity_gradients_at_the_capacity_end():
+    """The adjoint adds a staged region's opacity gradients four consecutive
+    Gaussians at a time (one vector reduction); a quad that would run past the
+    Gaussian capacity is added point by point instead.  With the capacity
+    exactly the Gaussian count, not a multiple of 4, and the batch's last
+    Gaussians live, the curve gradients equal those of the backward writing
+    every per-Gaussian row (no quads) at the same capacity, and those of a run
+    with room to spare."""
+    for r in (12.0, 12.5, 13.0, 13.5, 14.0, 14.5, 15.0):
+        sc = _corner_scene(r)
+        sp, img, rep, (k, t, c), G = run_scene(sc)
+        if G % 4:
+            break
+    else:
+        pytest.fail("no corner scene with a Gaussian count that is not a multiple of 4")
+    dimg = torch.as_tensor(np.random.default_rng(355).standard_normal(tuple(img.shape)).astype(np.float32),
+                           device="cuda")
+    room = [x.cpu().numpy() for x in sp.backward(k, t, c, dimg)]
+    sp2, img2, rep2, _, G2 = run_scene(sc, capacity=(G, 1 << 16, 1 << 12))
+    assert G2 == G and sp2.cap.gaussians == G
+    assert np.array_equal(img2.cpu().numpy(), img.cpu().numpy())
+    # the circle's last grid point is a live Gaussian: opacity above the cull threshold
+    rec = sp2.rec[G - 1].cpu().numpy()
+    assert rec[3] >= sc.raster["alpha_min"]
+    exact = [x.cpu().numpy() for x in sp2.backward(k, t, c, dimg)]
+    rows = [x.cpu().numpy() for x in sp2.backward(k, t, c, dimg, rows=True)]
+    torch.cuda.synchronize()
+    for nm, x, y, z in zip(("dkey", "dtau", "dcolor"), exact, rows, room):
+        assert np.isfinite(x).all(), nm
+        assert _rel(x, y) <= 1e-5, nm
+        assert _rel(x, z) <= 1e-5, nm
