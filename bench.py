@@ -825,17 +825,14 @@ def run_e2e(torch, step, g1, args):
     key points, knot intervals and colours from pinned host memory (one copy:
     the step's inputs are views of one device buffer), runs the step and reads
     the loss and all gradients back (one copy of the results buffer).  The
-    inputs and results are double-buffered (a second graph of the same step
-    on a second pair of buffers), and the copies run on their own stream, so
-    that step i+1's upload and step i's download overlap the neighbouring
-    steps' compute; the steps themselves run one after another on one stream
-    and one workspace."""
+    inputs and results are double-buffered, and the copies run on a stream of
+    their own, so that step i+1's upload and step i's download overlap the
+    neighbouring steps' compute; the steps themselves run one after another on
+    one stream and one workspace.  The K steps and their copies are captured
+    as one CUDA graph (the copies on a forked branch joined at the end), as a
+    training loop would launch them."""
     A_in, A_out = step.inbuf, step.outbuf
     B_in, B_out = A_in.clone(), A_out.clone()
-    step.rebind(B_in, B_out)
-    g2 = capture(torch, step)
-    step.rebind(A_in, A_out)
-    graphs = (g1, g2)
     ins, outs = (A_in, B_in), (A_out, B_out)
     hin = A_in.cpu().pin_memory()
     hout = [torch.empty(A_out.shape, dtype=A_out.dtype, pin_memory=True) for _ in range(2)]
@@ -843,46 +840,67 @@ def run_e2e(torch, step, g1, args):
     d2h = A_out.numel() * 4
     G = step.gaussians()
     K = max(10, args.steps)
-    s0 = torch.cuda.current_stream()
     cs = torch.cuda.Stream()
-    up = [torch.cuda.Event() for _ in range(2)]       # inputs of buffer b uploaded
-    done = [torch.cuda.Event() for _ in range(2)]     # the step on buffer b finished
-    down = [torch.cuda.Event() for _ in range(2)]     # results of buffer b downloaded
-    for e in up + done + down:
-        e.record(s0)
-    g2.replay()          # warm the second graph
+
+    def pipeline():
+        s0 = torch.cuda.current_stream()
+        up = [torch.cuda.Event() for _ in range(2)]       # inputs of buffer b uploaded
+        done = [torch.cuda.Event() for _ in range(2)]     # the step on buffer b finished
+        down = [torch.cuda.Event() for _ in range(2)]     # results of buffer b downloaded
+        fork = torch.cuda.Event()
+        fork.record(s0)
+        cs.wait_event(fork)
+        with torch.cuda.stream(cs):              # step 0's inputs
+            ins[0].copy_(hin, non_blocking=True)
+            up[0].record(cs)
+        for i in range(K):
+            b = i & 1
+            if i + 1 < K:                        # the next step's inputs, once the step before it has read buffer 1-b
+                with torch.cuda.stream(cs):
+                    if i >= 1:
+                        cs.wait_event(done[1 - b])
+                    ins[1 - b].copy_(hin, non_blocking=True)
+                    up[1 - b].record(cs)
+            s0.wait_event(up[b])
+            if i >= 2:
+                s0.wait_event(down[b])           # results of buffer b from two steps back are out
+            step.rebind(ins[b], outs[b])
+            step()
+            done[b].record(s0)
+            with torch.cuda.stream(cs):
+                cs.wait_event(done[b])
+                hout[b].copy_(outs[b], non_blocking=True)
+                down[b].record(cs)
+        s0.wait_stream(cs)
+
+    try:
+        gE = capture(torch, pipeline)
+    finally:
+        step.rebind(A_in, A_out)
+    gE.replay()          # warm
     torch.cuda.synchronize()
+    s0 = torch.cuda.current_stream()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(s0)
-    cs.wait_event(e0)
-    with torch.cuda.stream(cs):              # step 0's inputs
-        ins[0].copy_(hin, non_blocking=True)
-        up[0].record(cs)
-    for i in range(K):
-        b = i & 1
-        if i + 1 < K:                        # the next step's inputs, once the step before it has read buffer 1-b
-            with torch.cuda.stream(cs):
-                cs.wait_event(done[1 - b])
-                ins[1 - b].copy_(hin, non_blocking=True)
-                up[1 - b].record(cs)
-        s0.wait_event(up[b])
-        s0.wait_event(down[b])               # results of buffer b from two steps back are out
-        graphs[b].replay()
-        done[b].record(s0)
-        with torch.cuda.stream(cs):
-            cs.wait_event(done[b])
-            hout[b].copy_(outs[b], non_blocking=True)
-            down[b].record(cs)
-    s0.wait_stream(cs)
+    gE.replay()
     e1.record(s0)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    del g2
+    del gE
+    # the results the last step downloaded equal those of the step run directly
+    # on the device inputs (the same parameters every step; the gradients'
+    # atomic sums may round differently)
+    step()
+    torch.cuda.synchronize()
+    ref = step.outbuf.cpu().double()
+    err = float((hout[(K - 1) & 1].double() - ref).norm() / max(float(ref.norm()), 1e-30))
+    if not err <= 1e-4:
+        raise RuntimeError(f"e2e results differ from the device step's: relative error {err:.3g}")
     return dict(value=round(G * K / (ms / 1e3), 1), unit="Gaussians/s", h2d_bytes_per_step=h2d,
-                d2h_bytes_per_step=d2h, steps=K, ms_per_step=round(ms / K, 4),
+                d2h_bytes_per_step=d2h, steps=K, ms_per_step=round(ms / K, 4), results_rel_err=float(f"{err:.3g}"),
                 copies="one H2D and one D2H per step from and to pinned host memory, on a copy stream "
-                       "overlapping the neighbouring steps")
+                       "overlapping the neighbouring steps; the K steps and their copies in one CUDA graph")
 
 
 def run_per_scene(torch, step, args, batched_value, raster=None):
