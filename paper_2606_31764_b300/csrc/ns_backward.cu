@@ -447,9 +447,11 @@ __device__ void chain_boundary_point(const ns_curves& cv, const CurveRef& cr, co
   }
 }
 
-// One thread per boundary point; 3 blocks of 256 per SM (at most 85 registers).
+// One thread per boundary point; 5 blocks of 256 per SM (48 registers: the
+// loads of a point form a long dependent chain, and more resident warps hide
+// it better than spill-free registers would).
 template <bool KNOTS>
-__global__ void __launch_bounds__(256, 3) k_chain_boundary(ns_curves cv, const CurvePlan* __restrict__ plan, const float* __restrict__ knots,
+__global__ void __launch_bounds__(256, 5) k_chain_boundary(ns_curves cv, const CurvePlan* __restrict__ plan, const float* __restrict__ knots,
                                  const DevState* __restrict__ st, const float2* __restrict__ dbpts,
                                  const int* __restrict__ bcurve, int freeze_w, float* dkey, float* dknots) {
   grid_dep_wait();
@@ -457,8 +459,8 @@ __global__ void __launch_bounds__(256, 3) k_chain_boundary(ns_curves cv, const C
   const int nc = cv.n_curves;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nb; j += gridDim.x * blockDim.x) {
     const float2 db = dbpts[j];
+    const int lo = bcurve[j];   // the curve that owns boundary point j (loaded beside its gradient)
     if (db.x == 0.f && db.y == 0.f) continue;
-    const int lo = bcurve[j];   // the curve that owns boundary point j
     if (lo < 0 || lo >= nc) continue;
     const CurvePlan pl = plan[lo];
     if (pl.kind != kFill) continue;
@@ -629,7 +631,7 @@ extern "C" ns_status splat_backward(const ns_curves* curves, const ns_gaussians*
       }
       if (L.bcap > 0) {
         auto kb = knots_on ? &k_chain_boundary<true> : &k_chain_boundary<false>;
-        NS_LAUNCH(NS_KERNEL_CHAIN_BOUNDARY, kb, num_sms() * 3, 256, 0, s, *curves, plan, knots, st, dbpts,
+        NS_LAUNCH(NS_KERNEL_CHAIN_BOUNDARY, kb, num_sms() * 5, 256, 0, s, *curves, plan, knots, st, dbpts,
                   at<const int>(ws, L.o_bcurve), cp.freeze_w, out->dkey, dknots);
       }
       if (knots_on)
