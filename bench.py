@@ -43,16 +43,16 @@ PEAKS_FALLBACK = dict(hbm_gbs=6400.0, sm_max_mhz=2032.0)
 # the records it writes stay in L2, at 2048 they do not, so its traffic does
 # not grow in proportion.
 TRAFFIC = dict(
-    blend_bwd=dict(bytes=57579264, units=2027197, unit="gaussians", tile=8, layers=1,
-                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="a956187ad189ee89"),
-    blend_fwd=dict(bytes=27760640, units=2027197, unit="gaussians", tile=8, layers=1,
-                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="a956187ad189ee89"),
-    chain=dict(bytes=15444224, units=2027197, unit="gaussians", tile=None, layers=None,
-               src="paper_2606_31764_b300/csrc/ns_backward.cu", sha="b78eb000dfbb283b"),
-    bin_count=dict(bytes=338176, units=2027197, unit="gaussians", tile=8, layers=1,
-                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="a956187ad189ee89"),
+    blend_bwd=dict(bytes=57676288, units=2027197, unit="gaussians", tile=8, layers=1,
+                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="8c7d900d4f6df113"),
+    blend_fwd=dict(bytes=27877376, units=2027197, unit="gaussians", tile=8, layers=1,
+                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="8c7d900d4f6df113"),
+    chain=dict(bytes=17377024, units=2027197, unit="gaussians", tile=None, layers=None,
+               src="paper_2606_31764_b300/csrc/ns_backward.cu", sha="01a669132abad508"),
+    bin_count=dict(bytes=340224, units=2027197, unit="gaussians", tile=8, layers=1,
+                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="8c7d900d4f6df113"),
     bin_emit=dict(bytes=63488, units=2027197, unit="gaussians", tile=8, layers=1,
-                  src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="a956187ad189ee89"),
+                  src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="8c7d900d4f6df113"),
     plan=dict(bytes=2102016, units=512, unit="curves", tile=None, layers=None,
               src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="87451ed3e021526b"),
     boundary=dict(bytes=1278976, units=512, unit="curves", tile=None, layers=None,
