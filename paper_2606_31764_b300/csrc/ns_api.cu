@@ -146,6 +146,7 @@ bool make_layout(const ns_curves* c, const ns_capacity* cap, const ns_raster_par
   L->o_forms = take(sizeof(float) * kFormStride * nkn);   // span Taylor forms, one row per knot slot
   L->o_boffs = take(sizeof(int) * (size_t)L->nc);          // first boundary point of each curve, packed
   L->o_lbox = take(sizeof(int4) * (size_t)L->nc);
+  L->o_bmix = take(sizeof(int) * (size_t)(L->bin_blocks + 1));
   // contour tasks cover a curve's samples in chunks of kChunk, fill tasks its
   // grid in T x T tiles, T = 8 or 16 (at most (nx ny + (T - 1)(nx + ny) +
   // (T - 1)^2) / T^2 of them): within the Gaussian capacity this table holds

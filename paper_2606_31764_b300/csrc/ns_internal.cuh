@@ -93,6 +93,7 @@ struct Layout {
   size_t o_glo = 0;          // per curve: the low parts {x0_lo, y0_lo} of the fill grid origin (plan x0, y0 = high parts)
   size_t o_knots_lo = 0;     // low parts of the knot vectors (knots = their high parts, the exact sums rounded)
   size_t o_lbox = 0;         // per curve: {min column, min row, max column, max row} of live fill grid points (nurbs_sample)
+  size_t o_bmix = 0;         // per binning block: 1 if a Gaussian of a stroke (not a filled curve) lies in it (nurbs_sample)
   size_t o_bflag = 0;        // per binning block: 1 if it holds a Gaussian that is not a fill layer's (splat_forward)
   size_t o_lcount = 0;       // per curve: tile pairs of its fill layer (splat_forward)
   size_t o_krcp = 0;         // per knot slot k and width j = 1..kMaxP: 1 / (U[k + j] - U[k]) as {hi, lo} (filled curves)

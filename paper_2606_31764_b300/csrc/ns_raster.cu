@@ -74,6 +74,7 @@ struct BinParams {
   // per binning block whether it holds a Gaussian outside the fill layers, per curve its
   // layer's pair count
   const int4* lbox;
+  const int* bmix;   // per binning block: 1 if a stroke's Gaussian lies in it (nurbs_sample)
   int* bflag;
   int* lcount;
 };
@@ -245,122 +246,102 @@ __global__ void __launch_bounds__(256) k_bin_count(const float4* __restrict__ re
                                                    const int* __restrict__ gcurve,
                                                    const int* __restrict__ cflags, const int* __restrict__ gcount,
                                                    BinParams bp, int* bsum, DevState* st, float4* prep,
-                                                   float2* prep2, float2* reach, const CurvePlan* __restrict__ plan,
-                                                   const int* __restrict__ order,
-                                                   const int* __restrict__ scene_off) {
+                                                   float2* prep2, float2* reach, const CurvePlan* __restrict__ plan) {
   grid_dep_wait();
   __shared__ int s_warp[32];
-  __shared__ int s_pure;
   const int G = min(*gcount, bp.gcap);
-  const long long base = (long long)blockIdx.x * kBinItems;
-  if (base >= G) return;
   // with nurbs_sample's live boxes and culled count a fill Gaussian needs
   // nothing here (its layer is counted per curve): only its curve is read
   const bool fast = sampled_boxes(bp, st);
-  if (fast && blockIdx.x == 0 && threadIdx.x == 0 && st->culled_s) atomicAdd(&st->culled, st->culled_s);
-  if (fast) {
-    // a block whose first and last Gaussians belong to filled curves, and all
-    // curves between them in front-to-back order too, holds fill Gaussians only
-    if (threadIdx.x == 0) {
-      int pure = 0;
-      const int c0 = gcurve[base], c1 = gcurve[min((long long)G, base + kBinItems) - 1];
-      if (c0 >= 0 && c0 < bp.n_curves && c1 >= 0 && c1 < bp.n_curves) {
-        auto pos = [&](int c) {
-          const int sc = plan[c].scene;
-          const int s0 = scene_off ? scene_off[sc] : 0, s1 = scene_off ? scene_off[sc + 1] : bp.n_curves;
-          return s0 + (s1 - 1 - c);
-        };
-        const int p0 = pos(c0), p1 = pos(c1);
-        pure = p0 <= p1;
-        for (int q = p0; pure && q <= p1 && q < p0 + 64; ++q) pure = (cflags[order[q]] & NS_FILLED) != 0;
-        if (p1 >= p0 + 64) pure = 0;
-      }
-      s_pure = pure;
-    }
-    __syncthreads();
-    if (s_pure) {
+  if (fast && blockIdx.x == 0 && threadIdx.x == 0 && G > 0 && st->culled_s) atomicAdd(&st->culled, st->culled_s);
+  // persistent over the binning blocks (most of them skip at once with fill layers)
+  for (int blk = blockIdx.x; (long long)blk * kBinItems < G; blk += gridDim.x) {
+    const long long base = (long long)blk * kBinItems;
+    // a block that holds no stroke Gaussian (nurbs_sample marked the others)
+    // holds fill Gaussians only: nothing to count here
+    if (fast && !bp.bmix[blk]) {
       if (threadIdx.x == 0) {
-        bsum[blockIdx.x] = 0;
-        bp.bflag[blockIdx.x] = 0;
+        bsum[blk] = 0;
+        bp.bflag[blk] = 0;
       }
-      return;
+      continue;
     }
-  }
-  int cnt = 0, culled = 0, other = 0;
-  // the block total is all that is kept, so consecutive threads take
-  // consecutive Gaussians (coalesced loads and stores)
+    int cnt = 0, culled = 0, other = 0;
+    // the block total is all that is kept, so consecutive threads take
+    // consecutive Gaussians (coalesced loads and stores)
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const long long g = base + k * 256 + threadIdx.x;
-    int live_key = -1, live_ix = 0, live_iy = 0;   // fill layers: live grid point of curve live_key
-    bool skip = false;
-    if (g < G && fast) {
-      const int cv = gcurve[g];
-      skip = cv >= 0 && cv < bp.n_curves && (cflags[cv] & NS_FILLED);
-    }
-    if (g < G && !skip) {
-      other = 1;
-      const float4 r = rec[g];
-      int x0, y0, nx;
-      const int cv = gcurve[g];
-      bool layer;
-      const int nt = gaussian_tiles<ANISO>(rec, shape, cflags, plan, g, cv, G, bp, false, layer, x0, y0, nx);
-      cnt += nt;
-      if (bp.fill_layers && cv >= 0 && cv < bp.n_curves && (cflags[cv] & NS_FILLED) && r.z > 0.f && r.w > 0.f &&
-          r.w >= bp.alpha_min) {
-        const CurvePlan& p = plan[cv];
-        const float ih = 1.f / p.h;
-        live_key = cv;
-        live_ix = __float2int_rn((r.x - p.x0) * ih - 0.5f);
-        live_iy = __float2int_rn((r.y - p.y0) * ih - 0.5f);
+    for (int k = 0; k < 8; ++k) {
+      const long long g = base + k * 256 + threadIdx.x;
+      int live_key = -1, live_ix = 0, live_iy = 0;   // fill layers: live grid point of curve live_key
+      bool skip = false;
+      if (g < G && fast) {
+        const int cv = gcurve[g];
+        skip = cv >= 0 && cv < bp.n_curves && (cflags[cv] & NS_FILLED);
       }
-      if (nt && !layer) {   // only Gaussians binned on their own are read through these
-        // 1/sigma, negative for the Gaussians of filled curves (their centre and
-        // sigma get no gradient through the chain, so the adjoint may skip
-        // them).  The curve's flag decides: a fill point's aux can equal the
-        // contour marker -1 (~0: outside, nearest segment 0).
-        const float isg = 1.f / r.z;
-        const float sgn_isg = (cflags[cv] & NS_FILLED) ? -isg : isg;
-        if constexpr (ANISO) {
-          const float4 sh = shape[g];
-          const float it = 1.f / (sh.x * sh.x), in = 1.f / (r.z * r.z);
-          const float A = -0.5f * (sh.y * sh.y * it + sh.z * sh.z * in);
-          const float B2 = -sh.y * sh.z * (it - in);
-          const float Cc = -0.5f * (sh.z * sh.z * it + sh.y * sh.y * in);
-          prep[g] = make_float4(r.x, r.y, A, r.w);
-          prep2[g] = make_float2(B2, Cc);
-          reach[g] = make_float2(reach2(fmaxf(sh.x, r.z), r.w, bp.log_amin), sgn_isg);
-        } else {
-          prep[g] = make_float4(r.x, r.y, ncoef(r.z), r.w);
-          reach[g] = make_float2(reach2(r.z, r.w, bp.log_amin), sgn_isg);
+      if (g < G && !skip) {
+        other = 1;
+        const float4 r = rec[g];
+        int x0, y0, nx;
+        const int cv = gcurve[g];
+        bool layer;
+        const int nt = gaussian_tiles<ANISO>(rec, shape, cflags, plan, g, cv, G, bp, false, layer, x0, y0, nx);
+        cnt += nt;
+        if (bp.fill_layers && cv >= 0 && cv < bp.n_curves && (cflags[cv] & NS_FILLED) && r.z > 0.f && r.w > 0.f &&
+            r.w >= bp.alpha_min) {
+          const CurvePlan& p = plan[cv];
+          const float ih = 1.f / p.h;
+          live_key = cv;
+          live_ix = __float2int_rn((r.x - p.x0) * ih - 0.5f);
+          live_iy = __float2int_rn((r.y - p.y0) * ih - 0.5f);
+        }
+        if (nt && !layer) {   // only Gaussians binned on their own are read through these
+          // 1/sigma, negative for the Gaussians of filled curves (their centre and
+          // sigma get no gradient through the chain, so the adjoint may skip
+          // them).  The curve's flag decides: a fill point's aux can equal the
+          // contour marker -1 (~0: outside, nearest segment 0).
+          const float isg = 1.f / r.z;
+          const float sgn_isg = (cflags[cv] & NS_FILLED) ? -isg : isg;
+          if constexpr (ANISO) {
+            const float4 sh = shape[g];
+            const float it = 1.f / (sh.x * sh.x), in = 1.f / (r.z * r.z);
+            const float A = -0.5f * (sh.y * sh.y * it + sh.z * sh.z * in);
+            const float B2 = -sh.y * sh.z * (it - in);
+            const float Cc = -0.5f * (sh.z * sh.z * it + sh.y * sh.y * in);
+            prep[g] = make_float4(r.x, r.y, A, r.w);
+            prep2[g] = make_float2(B2, Cc);
+            reach[g] = make_float2(reach2(fmaxf(sh.x, r.z), r.w, bp.log_amin), sgn_isg);
+          } else {
+            prep[g] = make_float4(r.x, r.y, ncoef(r.z), r.w);
+            reach[g] = make_float2(reach2(r.z, r.w, bp.log_amin), sgn_isg);
+          }
+        }
+        culled += (r.z > 0.f && r.w < bp.alpha_min) ? 1 : 0;
+      }
+      if (bp.fill_layers && !fast) {   // warp-uniform
+        // extremes of the live grid points per curve: lanes of one curve reduce, one lane adds
+        const unsigned int peers = __match_any_sync(0xffffffffu, live_key);
+        if (live_key >= 0) {
+          const int mnx = __reduce_min_sync(peers, live_ix), mxx = __reduce_max_sync(peers, live_ix);
+          const int mny = __reduce_min_sync(peers, live_iy), mxy = __reduce_max_sync(peers, live_iy);
+          if ((threadIdx.x & 31) == __ffs(peers) - 1) {
+            atomicMin(&bp.lmin[live_key].x, mnx);
+            atomicMax(&bp.lmax[live_key].x, mxx);
+            atomicMin(&bp.lmin[live_key].y, mny);
+            atomicMax(&bp.lmax[live_key].y, mxy);
+          }
         }
       }
-      culled += (r.z > 0.f && r.w < bp.alpha_min) ? 1 : 0;
     }
-    if (bp.fill_layers && !fast) {   // warp-uniform
-      // extremes of the live grid points per curve: lanes of one curve reduce, one lane adds
-      const unsigned int peers = __match_any_sync(0xffffffffu, live_key);
-      if (live_key >= 0) {
-        const int mnx = __reduce_min_sync(peers, live_ix), mxx = __reduce_max_sync(peers, live_ix);
-        const int mny = __reduce_min_sync(peers, live_iy), mxy = __reduce_max_sync(peers, live_iy);
-        if ((threadIdx.x & 31) == __ffs(peers) - 1) {
-          atomicMin(&bp.lmin[live_key].x, mnx);
-          atomicMax(&bp.lmax[live_key].x, mxx);
-          atomicMin(&bp.lmin[live_key].y, mny);
-          atomicMax(&bp.lmax[live_key].y, mxy);
-        }
-      }
+    int total;
+    block_excl_scan_int(cnt, s_warp, total);
+    int ctot;
+    block_excl_scan_int(culled, s_warp, ctot);
+    const int any_other = __syncthreads_or(other);
+    if (threadIdx.x == 0) {
+      bsum[blk] = total;
+      if (bp.fill_layers) bp.bflag[blk] = fast ? any_other : 1;
+      if (ctot) atomicAdd(&st->culled, (unsigned long long)ctot);
     }
-  }
-  int total;
-  block_excl_scan_int(cnt, s_warp, total);
-  int ctot;
-  block_excl_scan_int(culled, s_warp, ctot);
-  const int any_other = __syncthreads_or(other);
-  if (threadIdx.x == 0) {
-    bsum[blockIdx.x] = total;
-    if (bp.fill_layers) bp.bflag[blockIdx.x] = fast ? any_other : 1;
-    if (ctot) atomicAdd(&st->culled, (unsigned long long)ctot);
   }
 }
 
@@ -462,65 +443,68 @@ __global__ void __launch_bounds__(256) k_bin_emit(const float4* __restrict__ rec
   __shared__ int s_off[kBinItems];    // tile count, then exclusive offset in Gaussian order
   __shared__ int2 s_rect[kBinItems];  // {x0 | nx << 16, y0 | ny << 16}
   const int G = min(*gcount, bp.gcap);
-  const long long base = (long long)blockIdx.x * kBinItems;
-  if (base >= G) return;
-  // a block whose Gaussians emit no pair (the inside of a fill layer, culled
-  // points) has the same offset as the next block
-  if (base + kBinItems < G && boff[blockIdx.x + 1] == boff[blockIdx.x]) return;
-  // a block of fill Gaussians only, with nurbs_sample's live boxes: its layers'
-  // pairs come from k_layer_emit
-  if (bp.fill_layers && !bp.bflag[blockIdx.x]) return;
-  // 1. rectangles, consecutive threads on consecutive Gaussians (coalesced)
+  // persistent over the binning blocks (most of them skip at once with fill layers)
+  for (int blk = blockIdx.x; (long long)blk * kBinItems < G; blk += gridDim.x) {
+    const long long base = (long long)blk * kBinItems;
+    // a block whose Gaussians emit no pair (the inside of a fill layer, culled
+    // points) has the same offset as the next block
+    if (base + kBinItems < G && boff[blk + 1] == boff[blk]) continue;
+    // a block of fill Gaussians only, with nurbs_sample's live boxes: its layers'
+    // pairs come from k_layer_emit
+    if (bp.fill_layers && !bp.bflag[blk]) continue;
+    __syncthreads();   // the previous block's pairs have read s_off and s_rect
+    // 1. rectangles, consecutive threads on consecutive Gaussians (coalesced)
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const int gl = k * 256 + threadIdx.x;
-    const long long g = base + gl;
-    int c = 0, x0 = 0, y0 = 0, nx = 1;
-    if (g < G) {
-      bool layer;
-      c = gaussian_tiles<ANISO>(rec, shape, cflags, plan, g, gcurve[g], G, bp, true, layer, x0, y0, nx);
+    for (int k = 0; k < 8; ++k) {
+      const int gl = k * 256 + threadIdx.x;
+      const long long g = base + gl;
+      int c = 0, x0 = 0, y0 = 0, nx = 1;
+      if (g < G) {
+        bool layer;
+        c = gaussian_tiles<ANISO>(rec, shape, cflags, plan, g, gcurve[g], G, bp, true, layer, x0, y0, nx);
+      }
+      s_off[gl] = c;
+      s_rect[gl] = make_int2(x0 | (nx << 16), y0 | ((c ? c / nx : 0) << 16));
     }
-    s_off[gl] = c;
-    s_rect[gl] = make_int2(x0 | (nx << 16), y0 | ((c ? c / nx : 0) << 16));
-  }
-  __syncthreads();
-  // 2. exclusive offsets in Gaussian order (each thread 8 consecutive)
-  int cnt[8], tot = 0;
+    __syncthreads();
+    // 2. exclusive offsets in Gaussian order (each thread 8 consecutive)
+    int cnt[8], tot = 0;
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    cnt[k] = s_off[threadIdx.x * 8 + k];
-    tot += cnt[k];
-  }
-  int btot;
-  int run = block_excl_scan_int(tot, s_warp, btot);
+    for (int k = 0; k < 8; ++k) {
+      cnt[k] = s_off[threadIdx.x * 8 + k];
+      tot += cnt[k];
+    }
+    int btot;
+    int run = block_excl_scan_int(tot, s_warp, btot);
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    s_off[threadIdx.x * 8 + k] = run;
-    run += cnt[k];
-  }
-  __syncthreads();
-  // 3. pairs, consecutive threads on consecutive Gaussians again
-  const long long boff0 = boff[blockIdx.x];
+    for (int k = 0; k < 8; ++k) {
+      s_off[threadIdx.x * 8 + k] = run;
+      run += cnt[k];
+    }
+    __syncthreads();
+    // 3. pairs, consecutive threads on consecutive Gaussians again
+    const long long boff0 = boff[blk];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const int gl = k * 256 + threadIdx.x;
-    const long long g = base + gl;
-    if (g >= G) continue;
-    const int2 rr = s_rect[gl];
-    const int nx = rr.x >> 16, ny = rr.y >> 16;
-    const int c = nx * ny;
-    if (!c) continue;
-    const int x0 = rr.x & 0xffff, y0 = rr.y & 0xffff;
-    const int cv = gcurve[g];
-    const int sbase = curve_scene[cv] * bp.tiles_per_scene;
-    const uint32_t val = uint32_t(g) | ((bp.fill_layers && (cflags[cv] & NS_FILLED)) ? kLayerBit : 0u);
-    long long off = boff0 + s_off[gl];
-    for (int j = 0; j < c; ++j, ++off) {
-      if (off >= pcap) break;
-      const int tx = x0 + j % nx;
-      const int ty = y0 + j / nx;
-      keys[off] = uint32_t(sbase + ty * bp.tiles_x + tx);
-      vals[off] = val;
+    for (int k = 0; k < 8; ++k) {
+      const int gl = k * 256 + threadIdx.x;
+      const long long g = base + gl;
+      if (g >= G) continue;
+      const int2 rr = s_rect[gl];
+      const int nx = rr.x >> 16, ny = rr.y >> 16;
+      const int c = nx * ny;
+      if (!c) continue;
+      const int x0 = rr.x & 0xffff, y0 = rr.y & 0xffff;
+      const int cv = gcurve[g];
+      const int sbase = curve_scene[cv] * bp.tiles_per_scene;
+      const uint32_t val = uint32_t(g) | ((bp.fill_layers && (cflags[cv] & NS_FILLED)) ? kLayerBit : 0u);
+      long long off = boff0 + s_off[gl];
+      for (int j = 0; j < c; ++j, ++off) {
+        if (off >= pcap) break;
+        const int tx = x0 + j % nx;
+        const int ty = y0 + j / nx;
+        keys[off] = uint32_t(sbase + ty * bp.tiles_x + tx);
+        vals[off] = val;
+      }
     }
   }
 }
@@ -2818,6 +2802,7 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
   bp.lmin = at<int2>(ws, L.o_lmin);
   bp.lmax = at<int2>(ws, L.o_lmax);
   bp.lbox = at<const int4>(ws, L.o_lbox);
+  bp.bmix = at<const int>(ws, L.o_bmix);
   bp.bflag = at<int>(ws, L.o_bflag);
   bp.lcount = at<int>(ws, L.o_lcount);
   const CurvePlan* plan = at<CurvePlan>(ws, L.o_plan);
@@ -2830,9 +2815,8 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
   const float4* shape = reinterpret_cast<const float4*>(g->shape);
   if (bin_blocks > 0) {
     auto kc = aniso ? &k_bin_count<true> : &k_bin_count<false>;
-    NS_LAUNCH(NS_KERNEL_BIN_COUNT, kc, bin_blocks, 256, 0, s, rec, shape, g->curve, curves->flags, g->count, bp, bsum, st,
-              at<float4>(ws, L.o_prep), at<float2>(ws, L.o_prep2), at<float2>(ws, L.o_reach), plan,
-              at<const int>(ws, L.o_order), curves->scene_curve_offset);
+    NS_LAUNCH(NS_KERNEL_BIN_COUNT, kc, int(std::min<long long>(bin_blocks, num_sms() * 8LL)), 256, 0, s, rec, shape, g->curve, curves->flags, g->count, bp, bsum, st,
+              at<float4>(ws, L.o_prep), at<float2>(ws, L.o_prep2), at<float2>(ws, L.o_reach), plan);
   }
   if (bp.fill_layers && L.nc > 0 && bin_blocks > 0)
     NS_LAUNCH(NS_KERNEL_OTHER, k_layer_count, (L.nc + 127) / 128, 128, 0, s, *curves, plan, rec, g->count, bp, bsum,
@@ -2844,7 +2828,7 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
               curve_scene, bp, bsum, at<const int>(ws, L.o_order), k0, v0, cap->pairs, st);
   if (bin_blocks > 0) {
     auto ke = aniso ? &k_bin_emit<true> : &k_bin_emit<false>;
-    NS_LAUNCH(NS_KERNEL_BIN_EMIT, ke, bin_blocks, 256, 0, s, rec, shape, g->curve, g->count, curve_scene, bp, bsum,
+    NS_LAUNCH(NS_KERNEL_BIN_EMIT, ke, int(std::min<long long>(bin_blocks, num_sms() * 8LL)), 256, 0, s, rec, shape, g->curve, g->count, curve_scene, bp, bsum,
               k0, v0, cap->pairs, curves->flags, plan);
   }
   const RasterPlan rpn = radix_plan(L.n_tiles);

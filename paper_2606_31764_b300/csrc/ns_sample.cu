@@ -546,8 +546,12 @@ __global__ void __launch_bounds__(256) k_boundary_box(ns_curves cv, ns_sample_pa
 // the task count of the other kind before it, so that each kind's offsets
 // can be searched over the one ordered list (see curve_of_task).
 __global__ void k_scan_gauss(int nc, CurvePlan* plan, const int* order, DevState* st, long long gcap,
-                             int* g_count_out, int ftile) {
+                             int* g_count_out, int ftile, int* bmix, long long n_bins) {
   grid_dep_wait();
+  // the binning blocks (kBinItems Gaussians each) that hold a stroke's
+  // Gaussians are marked once the offsets are known; the others hold fill
+  // Gaussians only (the binning skips them with fill layers)
+  for (long long i = threadIdx.x; i < n_bins; i += blockDim.x) bmix[i] = 0;
   // three scans in front-to-back order: Gaussians, fill tasks, contour tasks;
   // a curve's own tasks start at chunk_off, pad[0] holds the other kind's
   // offset (the search of curve_of_task)
@@ -565,6 +569,10 @@ __global__ void k_scan_gauss(int nc, CurvePlan* plan, const int* order, DevState
         q.g_off = int(off[0] < 0x7fffffff ? off[0] : 0x7fffffff);
         q.chunk_off = int(q.kind == kFill ? off[1] : off[2]);
         q.pad[0] = int(q.kind == kFill ? off[2] : off[1]);
+        if (q.kind != kFill && q.count > 0 && off[0] < gcap) {
+          const long long e = min(off[0] + q.count, gcap) - 1;
+          for (long long b = off[0] / kBinItems; b <= e / kBinItems && b < n_bins; ++b) bmix[b] = 1;
+        }
       },
       t3);
   const long long tot = t3[0], ftasks = t3[1], ctasks = t3[2];
@@ -1148,7 +1156,8 @@ extern "C" ns_status nurbs_sample(const ns_curves* curves, const ns_sample_param
     NS_LAUNCH(NS_KERNEL_OTHER, k_cluster_boxes, int((cap->boundary + 255) / 256), 256, 0, s, plan,
               at<const int>(ws, L.o_bcurve), bloc, st, cbox, cap->boundary, nc);
   const int ftile = fill_tile_of(sp->fill_tile);
-  NS_LAUNCH(NS_KERNEL_SCAN, k_scan_gauss, 1, 1024, 0, s, nc, plan, order, st, cap->gaussians, out->count, ftile);
+  NS_LAUNCH(NS_KERNEL_SCAN, k_scan_gauss, 1, 1024, 0, s, nc, plan, order, st, cap->gaussians, out->count, ftile,
+            at<int>(ws, L.o_bmix), (long long)L.bin_blocks);
   int* tmap = at<int>(ws, L.o_tasks);
   NS_LAUNCH(NS_KERNEL_SCAN, k_task_map, (nc + 7) / 8, 256, 0, s, nc, plan, st, tmap, (long long)L.tcap, ftile);
   const int grid = num_sms() * 8;
