@@ -182,8 +182,14 @@ bool make_layout(const ns_curves* c, const ns_capacity* cap, const ns_raster_par
 
 int sorted_buffer(const Layout& L);
 
-__global__ void k_reset_state(DevState* st) {
+// Resets the status word and counters; with nurbs_sample also zeroes the
+// curve order (in range even if the scene offsets are bad) and the Gaussian
+// count (in this launch instead of a memset each).
+__global__ void k_reset_state(DevState* st, int* order, int n_order, int* count_out) {
   grid_dep_wait();
+  for (int i = threadIdx.x; i < n_order; i += blockDim.x) order[i] = 0;
+  if (threadIdx.x != 0) return;
+  if (count_out) *count_out = 0;
   st->status = 0;
   st->bad_curve = -1;
   st->n_chunks = 0;
@@ -196,7 +202,9 @@ __global__ void k_reset_state(DevState* st) {
   st->culled_s = 0;
 }
 
-void launch_reset_state(DevState* st, cudaStream_t s) { NS_LAUNCH(NS_KERNEL_OTHER, k_reset_state, 1, 1, 0, s, st); }
+void launch_reset_state(DevState* st, cudaStream_t s, int* order, int n_order, int* count_out) {
+  NS_LAUNCH(NS_KERNEL_OTHER, k_reset_state, 1, n_order > 0 ? 256 : 1, 0, s, st, order, n_order, count_out);
+}
 
 __global__ void __launch_bounds__(256) k_mse(const float* __restrict__ a, const float* __restrict__ b, long long n,
                                              float* __restrict__ grad, float* loss) {
@@ -341,7 +349,8 @@ ns_status ns_clear_status(void* ws, void* stream) {
     set_error("ns_clear_status: null workspace");
     return NS_ERR_INVALID_ARG;
   }
-  NS_LAUNCH(NS_KERNEL_OTHER, k_reset_state, 1, 1, 0, static_cast<cudaStream_t>(stream), static_cast<DevState*>(ws));
+  NS_LAUNCH(NS_KERNEL_OTHER, k_reset_state, 1, 1, 0, static_cast<cudaStream_t>(stream), static_cast<DevState*>(ws),
+            static_cast<int*>(nullptr), 0, static_cast<int*>(nullptr));
   return cudaGetLastError() == cudaSuccess ? NS_OK : NS_ERR_CUDA;
 }
 

@@ -84,23 +84,61 @@ __device__ __forceinline__ int span_at(const CurveRef& cr, const float* U, float
   return find_span(U, P, cr.n, u);
 }
 
-// Clears the gradient rows of the Gaussians of every curve that is not
-// filled, one warp per curve (row floats per Gaussian).
-__global__ void __launch_bounds__(256) k_zero_rows(int nc, const CurvePlan* __restrict__ plan,
+// What the backward clears before it accumulates, in one launch instead of a
+// memset per array: arrays of floats (the first one, when first_per_g > 0,
+// only for the Gaussians in the set: first_per_g floats each), the adjoint's
+// counters, and with fill layers the gradient rows of the Gaussians of every
+// curve that is not filled (one warp per curve, row floats per Gaussian; the
+// fill Gaussians' rows are neither written nor read).
+constexpr int kClearArrays = 6;
+struct ClearArrays {
+  float* p[kClearArrays];
+  long long n[kClearArrays];
+  int count;
+  void add(float* ptr, long long floats) {
+    if (ptr && floats > 0 && count < kClearArrays) {
+      p[count] = ptr;
+      n[count] = floats;
+      ++count;
+    }
+  }
+};
+
+__global__ void __launch_bounds__(256) k_bwd_clear(ClearArrays ca, int first_per_g, DevState* st, int nc,
+                                                   const CurvePlan* __restrict__ plan,
                                                    const int* __restrict__ gcount, long long gcap, float* dg,
-                                                   int row) {
+                                                   int row, int stroke_rows) {
   grid_dep_wait();
-  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (c >= nc) return;
-  const CurvePlan& p = plan[c];
-  if (p.kind == kFill || p.kind == kNone || p.count <= 0 || p.g_off < 0) return;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  if (tid == 0) {
+    st->blend_bwd_evals = 0;
+    st->blend_bwd_visits = 0;
+  }
   const long long G = min((long long)*gcount, gcap);
-  const long long g0 = p.g_off, g1 = min(g0 + p.count, G);
-  if (g1 <= g0) return;
-  float* r = dg + g0 * row;
-  const long long n = (g1 - g0) * row;
-  for (long long i = lane; i < n; i += 32) r[i] = 0.f;
+  for (int j = 0; j < ca.count; ++j) {
+    float* a = ca.p[j];
+    const long long n = (j == 0 && first_per_g > 0) ? min(ca.n[j], G * first_per_g) : ca.n[j];
+    long long head = 0;
+    if ((reinterpret_cast<uintptr_t>(a) & 15) == 0) {
+      float4* a4 = reinterpret_cast<float4*>(a);
+      const long long n4 = n >> 2;
+      for (long long i = tid; i < n4; i += nth) a4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      head = n4 << 2;
+    }
+    for (long long i = head + tid; i < n; i += nth) a[i] = 0.f;
+  }
+  if (!stroke_rows) return;
+  const int lane = threadIdx.x & 31;
+  for (long long c = tid >> 5; c < nc; c += nth >> 5) {
+    const CurvePlan& p = plan[c];
+    if (p.kind == kFill || p.kind == kNone || p.count <= 0 || p.g_off < 0) continue;
+    const long long g0 = p.g_off, g1 = min(g0 + p.count, G);
+    if (g1 <= g0) continue;
+    float* r = dg + g0 * row;
+    const long long n = (g1 - g0) * row;
+    for (long long i = lane; i < n; i += 32) r[i] = 0.f;
+  }
 }
 
 // Fill tasks: each thread one fill Gaussian (latency-bound loads and a few
@@ -555,18 +593,30 @@ extern "C" ns_status splat_backward(const ns_curves* curves, const ns_gaussians*
   // cleared and used.
   const bool compact = !full && layers_active(rp, g);
   float* dop = compact ? dg + 8 * (size_t)L.gcap : nullptr;
-  if (compact) {
-    cudaMemsetAsync(dop, 0, sizeof(float) * (size_t)L.gcap, s);
-    if (L.nc > 0)
-      NS_LAUNCH(NS_KERNEL_OTHER, k_zero_rows, (L.nc + 7) / 8, 256, 0, s, curves->n_curves,
-                at<const CurvePlan>(ws, L.o_plan), g->count, L.gcap, dg, row);
-  } else {
-    cudaMemsetAsync(dg, 0, sizeof(float) * row * (size_t)L.gcap, s);
-  }
-  if (out && zero_outputs) {
-    cudaMemsetAsync(out->dkey, 0, sizeof(float) * 4 * (size_t)L.nk, s);
-    if (out->dtau) cudaMemsetAsync(out->dtau, 0, sizeof(float) * (size_t)L.nt, s);
-    cudaMemsetAsync(out->dcolor, 0, sizeof(float) * 4 * (size_t)L.nc, s);
+  float* dknots = at<float>(ws, L.o_dknots);
+  float2* dbpts = at<float2>(ws, L.o_dbpts);
+  const size_t n_knots = (size_t)L.nt + (size_t)kKnotPad * L.nc;
+  {
+    // everything this call accumulates into, cleared by one kernel
+    ClearArrays ca;
+    ca.count = 0;
+    if (compact) ca.add(dop, L.gcap);                  // the Gaussians in the set only
+    else ca.add(dg, (long long)row * L.gcap);
+    if (out && zero_outputs) {
+      ca.add(out->dkey, 4LL * L.nk);
+      ca.add(out->dtau, L.nt);
+      ca.add(out->dcolor, 4LL * L.nc);
+    }
+    if (out) {
+      if (knots_on) ca.add(dknots, (long long)n_knots);
+      ca.add(reinterpret_cast<float*>(dbpts), 2LL * L.bcap);
+    }
+    long long total = 0;
+    for (int j = 0; j < ca.count; ++j) total += ca.n[j];
+    const long long want = std::max<long long>((total / 4 + 255) / 256, compact ? (L.nc + 7) / 8 : 1);
+    const int grid = int(std::max<long long>(1, std::min<long long>(want, num_sms() * 8LL)));
+    NS_LAUNCH(NS_KERNEL_OTHER, k_bwd_clear, grid, 256, 0, s, ca, compact ? 1 : 0, at<DevState>(ws, L.o_state),
+              curves->n_curves, at<const CurvePlan>(ws, L.o_plan), g->count, L.gcap, dg, row, compact ? 1 : 0);
   }
   launch_blend_bwd(L, curves, g, rp, dL_dimage, dg, ws, s, full, full ? nullptr : out->dcolor, dop);
   if (out) {
@@ -574,12 +624,7 @@ extern "C" ns_status splat_backward(const ns_curves* curves, const ns_gaussians*
     const CurvePlan* plan = at<CurvePlan>(ws, L.o_plan);
     const int* order = at<int>(ws, L.o_order);
     const float* knots = at<float>(ws, L.o_knots);
-    float* dknots = at<float>(ws, L.o_dknots);
     const float2* bpts = at<float2>(ws, L.o_bpts);
-    float2* dbpts = at<float2>(ws, L.o_dbpts);
-    const size_t n_knots = (size_t)L.nt + (size_t)kKnotPad * L.nc;
-    if (knots_on) cudaMemsetAsync(dknots, 0, sizeof(float) * n_knots, s);
-    cudaMemsetAsync(dbpts, 0, sizeof(float2) * (size_t)L.bcap, s);
     if (L.nc > 0) {
       ChainParams cp;
       cp.rho = sp->rho;

@@ -106,7 +106,7 @@ struct Layout {
 void set_error(const std::string& msg);
 bool make_layout(const ns_curves* c, const ns_capacity* cap, const ns_raster_params* rp, Layout* L);
 int num_sms();
-void launch_reset_state(DevState* st, cudaStream_t s);
+void launch_reset_state(DevState* st, cudaStream_t s, int* order, int n_order, int* count_out);
 
 // Launch bookkeeping: counts launches and fires the armed profiling events.
 void before_launch(int kernel_id, cudaStream_t s);

@@ -47,10 +47,27 @@
 namespace ns {
 
 
-__global__ void k_curve_scene(ns_curves cv, int* curve_scene) {
+// The scene of every curve, and what the forward clears before it
+// accumulates (in this launch instead of a memset each): the forward's
+// counters, the tile ranges, and with fill layers (lmin != NULL) the live
+// extremes of every curve's layer (lmin above every index, lmax -1).
+__global__ void k_curve_scene(ns_curves cv, int* curve_scene, DevState* st, int2* ranges, int n_tiles, int2* lmin,
+                              int2* lmax) {
   grid_dep_wait();
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0) {
+    st->culled = 0;
+    st->blend_evals = 0;
+    st->blend_contribs = 0;
+    st->blend_visits = 0;
+  }
+  for (int i = t; i < n_tiles; i += gridDim.x * blockDim.x) ranges[i] = make_int2(0, 0);
+  const int c = t;
   if (c >= cv.n_curves) return;
+  if (lmin) {
+    lmin[c] = make_int2(0x7f7f7f7f, 0x7f7f7f7f);
+    lmax[c] = make_int2(-1, -1);
+  }
   int s = 0;
   if (cv.scene_curve_offset) {
     int lo = 0, hi = cv.n_scenes - 1;
@@ -2782,12 +2799,6 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
   int* nl = at<int>(ws, L.o_nlast);
   const float4* rec = reinterpret_cast<const float4*>(g->rec);
 
-  cudaMemsetAsync(&st->culled, 0, sizeof(unsigned long long), s);
-  cudaMemsetAsync(&st->blend_evals, 0, sizeof(unsigned long long), s);
-  cudaMemsetAsync(&st->blend_contribs, 0, sizeof(unsigned long long), s);
-  cudaMemsetAsync(&st->blend_visits, 0, sizeof(unsigned long long), s);
-  if (curves->n_curves > 0)
-    NS_LAUNCH(NS_KERNEL_OTHER, k_curve_scene, (curves->n_curves + 255) / 256, 256, 0, s, *curves, curve_scene);
   BinParams bp;
   bp.k_sigma = rp->k_sigma;
   bp.inv_tile = 1.f / float(rp->tile);
@@ -2806,9 +2817,11 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
   bp.bflag = at<int>(ws, L.o_bflag);
   bp.lcount = at<int>(ws, L.o_lcount);
   const CurvePlan* plan = at<CurvePlan>(ws, L.o_plan);
-  if (bp.fill_layers && L.nc > 0) {
-    cudaMemsetAsync(bp.lmin, 0x7f, sizeof(int2) * (size_t)L.nc, s);   // 0x7f7f7f7f: above every index
-    cudaMemsetAsync(bp.lmax, 0xff, sizeof(int2) * (size_t)L.nc, s);   // -1
+  {
+    // curve scenes, counters, tile ranges and layer extremes in one launch
+    const int want = std::max((curves->n_curves + 255) / 256, std::min((L.n_tiles + 2047) / 2048, num_sms()));
+    NS_LAUNCH(NS_KERNEL_OTHER, k_curve_scene, std::max(1, want), 256, 0, s, *curves, curve_scene, st, ranges,
+              L.n_tiles, bp.fill_layers ? bp.lmin : nullptr, bp.lmax);
   }
   const int bin_blocks = int(L.bin_blocks);
   const bool aniso = g->shape != nullptr;
@@ -2852,7 +2865,6 @@ extern "C" ns_status splat_forward(const ns_curves* curves, const ns_gaussians* 
     NS_LAUNCH(NS_KERNEL_OTHER, k_layer_runs, L.nc, 128, 0, s, *curves, plan, rec, g->count, bp,
               at<int2>(ws, L.o_lruns), L.tiles_x + L.tiles_y, at<float4>(ws, L.o_lconst),
               at<const float2>(ws, L.o_glo));
-  cudaMemsetAsync(ranges, 0, sizeof(int2) * (size_t)L.n_tiles, s);
   NS_LAUNCH(NS_KERNEL_RANGES, k_ranges, num_sms() * 16, 256, 0, s, kin, st, ranges);
   const BlendArgs ba{ranges, vin, at<float4>(ws, L.o_prep), at<float2>(ws, L.o_prep2), at<float2>(ws, L.o_reach),
                      g->curve, reinterpret_cast<const float4*>(curves->color), blend_params(L, rp), Tf, nl, st,
@@ -2878,9 +2890,7 @@ ns_status launch_blend_bwd(const Layout& L, const ns_curves* curves, const ns_ga
                            cudaStream_t s, int full_grads, float* dcurve, float* dop) {
   const RasterPlan rpn = radix_plan(L.n_tiles);
   const uint32_t* vsorted = (rpn.passes & 1) ? at<uint32_t>(ws, L.o_v1) : at<uint32_t>(ws, L.o_v0);
-  DevState* st = at<DevState>(ws, L.o_state);
-  cudaMemsetAsync(&st->blend_bwd_evals, 0, sizeof(unsigned long long), s);
-  cudaMemsetAsync(&st->blend_bwd_visits, 0, sizeof(unsigned long long), s);
+  DevState* st = at<DevState>(ws, L.o_state);   // its counters were cleared by the caller
   BlendArgs ba{at<int2>(ws, L.o_ranges), vsorted, at<float4>(ws, L.o_prep), at<float2>(ws, L.o_prep2),
                at<float2>(ws, L.o_reach), g->curve, reinterpret_cast<const float4*>(curves->color),
                blend_params(L, rp), at<float>(ws, L.o_T), at<int>(ws, L.o_nlast), st,

@@ -1118,14 +1118,8 @@ extern "C" ns_status nurbs_sample(const ns_curves* curves, const ns_sample_param
   int* order = at<int>(ws, L.o_order);
   float2* bpts = at<float2>(ws, L.o_bpts);
   const int nc = curves->n_curves;
-  launch_reset_state(st, s);
-  if (nc > 0) cudaMemsetAsync(order, 0, sizeof(int) * (size_t)nc, s);   // in range even if offsets are bad
-  if (nc == 0) {
-    cudaMemsetAsync(out->count, 0, sizeof(int), s);
-    cudaMemsetAsync(&st->n_chunks, 0, 2 * sizeof(int), s);
-    cudaMemsetAsync(&st->g_count, 0, sizeof(int), s);
-    return cudaGetLastError() == cudaSuccess ? NS_OK : NS_ERR_CUDA;
-  }
+  launch_reset_state(st, s, order, nc, out->count);   // also zeroes the order and the Gaussian count
+  if (nc == 0) return cudaGetLastError() == cudaSuccess ? NS_OK : NS_ERR_CUDA;
   float2* krcp = at<float2>(ws, L.o_krcp);
   {
     // the plan: knot vectors and span forms, then arc lengths and counts
