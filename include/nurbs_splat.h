@@ -78,6 +78,13 @@ typedef struct {
   const float* key;                    /* device [n_keys*4]: {x, y, s, w} per key point */
   const float* tau;                    /* device [n_taus]: knot intervals, >= 0 */
   const float* color;                  /* device [n_curves*4]: {r, g, b, opacity} */
+  /* Host-side hint, optional: 0 = not given.  Otherwise bit 0 is set and bit p
+   * (1..NS_MAX_DEGREE) is set for every degree p among the curves that are not
+   * filled (strokes).  splat_backward then launches the contour-chain kernels
+   * of those degrees only (one per degree; none for a batch of fills).  A
+   * stroke whose degree's bit is clear while bit 0 is set is reported by
+   * nurbs_sample as an invalid curve (NS_ERR_INVALID_CURVE, bad_curve). */
+  int32_t stroke_degrees;
 } ns_curves;
 
 /* Sampling settings (§3.2, §3.3; defaults of Table S1 from ns_default_sample_params). */

@@ -24,7 +24,7 @@ class NsCurves(C.Structure):
     _fields_ = [("n_scenes", C.c_int32), ("n_curves", C.c_int32), ("n_keys", C.c_int32), ("n_taus", C.c_int32),
                 ("height", C.c_int32), ("width", C.c_int32), ("channels", C.c_int32),
                 ("scene_curve_offset", _p), ("degree", _p), ("flags", _p), ("key_offset", _p),
-                ("tau_offset", _p), ("key", _p), ("tau", _p), ("color", _p)]
+                ("tau_offset", _p), ("key", _p), ("tau", _p), ("color", _p), ("stroke_degrees", C.c_int32)]
 
 
 class NsSampleParams(C.Structure):

@@ -642,9 +642,9 @@ extern "C" ns_status splat_backward(const ns_curves* curves, const ns_gaussians*
                 reinterpret_cast<const float4*>(g->rec), g->aux, dg, cap->gaussians,
                 cap->boundary, out->dkey, dknots, dbpts, out->dcolor, row / 4, static_cast<const float*>(dop));
       {
-        // one launch per degree present among the curves (the host knows the
-        // degrees only on the device, so all five are launched; a launch with
-        // no task of its degree exits after scanning the task list)
+        // one launch per degree of the strokes: the degrees the caller's hint
+        // names (stroke_degrees), else all five (a launch with no task of its
+        // degree exits after scanning the task list)
 #define NS_CC(P) (aniso ? (knots_on ? &k_chain_contour<P, true, true> : &k_chain_contour<P, false, true>) \
                          : (knots_on ? &k_chain_contour<P, true, false> : &k_chain_contour<P, false, false>))
         auto k1 = NS_CC(1);
@@ -668,11 +668,14 @@ extern "C" ns_status splat_backward(const ns_curves* curves, const ns_gaussians*
                         st, static_cast<const float*>(dg), cap->gaussians, out->dkey, dknots, out->dcolor);
           ::ns::after_launch(last_id, s);
         };
-        run(k1, NS_KERNEL_CHAIN_CONTOUR, -1);
-        run(k2, -1, -1);
-        run(k3, -1, -1);
-        run(k4, -1, -1);
-        run(k5, -1, NS_KERNEL_CHAIN_CONTOUR);
+        decltype(k1) ks[5] = {k1, k2, k3, k4, k5};
+        const int hint = curves->stroke_degrees;
+        int todo[5], nk = 0;
+        for (int p = 1; p <= 5; ++p)
+          if (!(hint & 1) || (hint & (1 << p))) todo[nk++] = p;
+        for (int j = 0; j < nk; ++j)
+          run(ks[todo[j] - 1], j == 0 ? NS_KERNEL_CHAIN_CONTOUR : -1, j == nk - 1 ? NS_KERNEL_CHAIN_CONTOUR : -1);
+        if (nk == 0) ::ns::empty_range(NS_KERNEL_CHAIN_CONTOUR, s);   // an armed range stays well formed
       }
       if (L.bcap > 0) {
         auto kb = knots_on ? &k_chain_boundary<true> : &k_chain_boundary<false>;

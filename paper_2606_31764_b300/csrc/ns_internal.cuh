@@ -111,6 +111,7 @@ void launch_reset_state(DevState* st, cudaStream_t s, int* order, int n_order, i
 // Launch bookkeeping: counts launches and fires the armed profiling events.
 void before_launch(int kernel_id, cudaStream_t s);
 void after_launch(int kernel_id, cudaStream_t s);
+void empty_range(int kernel_id, cudaStream_t s);
 
 // Programmatic dependent launch.  The library's kernels are launched with
 // programmatic stream serialization: a kernel's launch may overlap the end of

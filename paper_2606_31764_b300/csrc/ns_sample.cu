@@ -212,6 +212,8 @@ __global__ void __launch_bounds__(kFormThreads) k_plan_forms(ns_curves cv, Curve
     if (ok) ok = cr.closed ? (cr.nk >= cr.p && cr.nk >= 2 && cr.ntau == cr.nk)
                            : (cr.nk >= cr.p + 1 && cr.ntau == cr.nk - cr.p);
     if (ok && cr.filled && !cr.closed) ok = 0;
+    // a stroke of a degree the caller's launch hint leaves out
+    if (ok && (cv.stroke_degrees & 1) && !cr.filled && !(cv.stroke_degrees & (1 << cr.p))) ok = 0;
     // scene and front-to-back position: reverse order inside the scene
     int s = 0, s0 = 0, s1 = cv.n_curves;
     if (cv.scene_curve_offset) {

@@ -80,6 +80,13 @@ class DeviceCurves:
         self.n_curves = int(scene.degree.shape[0])
         self.n_keys = int(scene.key.shape[0])
         self.n_taus = int(scene.tau.shape[0])
+        # the degrees of the strokes (curves that are not filled), as the
+        # library's launch hint: bit 0 = given, bit p = degree p present
+        mask = 1
+        for p, f in zip(scene.degree.tolist(), scene.flags.tolist()):
+            if not (int(f) & B.NS_FILLED) and 1 <= int(p) <= 5:
+                mask |= 1 << int(p)
+        self.stroke_degrees = mask
 
     def struct_sizes(self) -> B.NsCurves:
         """The table with placeholder parameter pointers: enough for
@@ -91,6 +98,7 @@ class DeviceCurves:
         c.degree, c.flags = _ptr(self.degree), _ptr(self.flags)
         c.key_offset, c.tau_offset = _ptr(self.key_offset), _ptr(self.tau_offset)
         c.key = c.tau = c.color = C.c_void_p(256)
+        c.stroke_degrees = self.stroke_degrees
         return c
 
     def struct(self, key, tau, color) -> B.NsCurves:
@@ -104,6 +112,7 @@ class DeviceCurves:
         c.degree, c.flags = _ptr(self.degree), _ptr(self.flags)
         c.key_offset, c.tau_offset = _ptr(self.key_offset), _ptr(self.tau_offset)
         c.key, c.tau, c.color = _ptr(key), _ptr(tau), _ptr(color)
+        c.stroke_degrees = self.stroke_degrees
         return c
 
 
