@@ -81,7 +81,8 @@ typedef struct {
   /* Host-side hint, optional: 0 = not given.  Otherwise bit 0 is set and bit p
    * (1..NS_MAX_DEGREE) is set for every degree p among the curves that are not
    * filled (strokes).  splat_backward then launches the contour-chain kernels
-   * of those degrees only (one per degree; none for a batch of fills).  A
+   * of those degrees only (one per degree; none for a batch of fills), and
+   * nurbs_sample no stroke sampling kernel for a batch of fills.  A
    * stroke whose degree's bit is clear while bit 0 is set is reported by
    * nurbs_sample as an invalid curve (NS_ERR_INVALID_CURVE, bad_curve). */
   int32_t stroke_degrees;

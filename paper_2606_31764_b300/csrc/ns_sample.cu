@@ -13,7 +13,9 @@
 //                   evaluated in double-float arithmetic
 //   k_boundary_box  one warp per filled curve: the polyline's padded and
 //                   clipped box, the fill grid origin (high and low parts) and
-//                   size, the points made relative to the origin
+//                   size, the points made relative to the origin, and the
+//                   bounding box of each cluster of 8 segments (the lower
+//                   bounds the fill SDF's segment lists test)
 //   k_scan_gauss    one block: Gaussian and task offsets in front-to-back order
 //   k_fill_sdf      persistent over the fill tasks (16 x 16 tiles of a curve's
 //                   grid): the SDF of Eq. S1-S3 from the band of segments
@@ -467,7 +469,7 @@ __global__ void __launch_bounds__(256) k_boundary(ns_curves cv, const CurvePlan*
 // the fill-layer blend work with.
 __global__ void __launch_bounds__(256) k_boundary_box(ns_curves cv, ns_sample_params sp, CurvePlan* plan,
                                                       const float* __restrict__ knots, float4* bloc, float2* glo,
-                                                      long long bcap, int4* lbox, DevState* st) {
+                                                      long long bcap, int4* lbox, DevState* st, float4* cbox) {
   grid_dep_wait();
   const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -528,6 +530,25 @@ __global__ void __launch_bounds__(256) k_boundary_box(ns_curves cv, ns_sample_pa
     const float4 v = bloc[pl.b_off + j];
     const df lx = df_sub(df{v.x, v.z}, ox), ly = df_sub(df{v.y, v.w}, oy);
     bloc[pl.b_off + j] = make_float4(lx.h, ly.h, lx.l, ly.l);
+  }
+  if (whole) {
+    // the box of each cluster of kCluster segments (grid-local high parts),
+    // at the index of the cluster's first point; the warp's own points above
+    // are visible to its lanes after the warp barrier
+    __syncwarp();
+    const int B = pl.M;
+    for (int k = lane * kCluster; k < B; k += 32 * kCluster) {
+      float cx0 = FLT_MAX, cx1 = -FLT_MAX, cy0 = FLT_MAX, cy1 = -FLT_MAX;
+      for (int j = k; j < min(B, k + kCluster); ++j) {
+        const float4 b0 = bloc[pl.b_off + j];
+        const float4 b1 = bloc[pl.b_off + (j + 1 == B ? 0 : j + 1)];
+        cx0 = fminf(cx0, fminf(b0.x, b1.x));
+        cx1 = fmaxf(cx1, fmaxf(b0.x, b1.x));
+        cy0 = fminf(cy0, fminf(b0.y, b1.y));
+        cy1 = fmaxf(cy1, fmaxf(b0.y, b1.y));
+      }
+      cbox[pl.b_off + k] = make_float4(cx0, cx1, cy0, cy1);
+    }
   }
   if (lane == 0) {
     const double h = double(sp.h);
@@ -677,41 +698,6 @@ __global__ void __launch_bounds__(256) k_emit_shape(ns_curves cv, ns_sample_para
 }
 
 
-
-// Bounding box {x0, x1, y0, y1} of each cluster of kCluster consecutive
-// segments of a fill polyline (the last cluster may be shorter; segment j
-// runs from point j to point j + 1, the last one back to point 0), in the
-// curve's grid-local coordinates (high parts), stored at the index of the
-// cluster's first point.  The sampling tasks of a curve all stage these
-// boxes, so they are computed once per curve here.
-__global__ void __launch_bounds__(256) k_cluster_boxes(const CurvePlan* __restrict__ plan,
-                                                       const int* __restrict__ bcurve,
-                                                       const float4* __restrict__ bloc,
-                                                       const DevState* __restrict__ st, float4* cbox,
-                                                       long long bcap, int nc) {
-  grid_dep_wait();
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long nb = min((long long)st->b_count, bcap);
-  if (i >= nb) return;
-  // points of a polyline that overflowed the capacity are never written:
-  // their curve entry is not trusted
-  const int c = bcurve[i];
-  if (c < 0 || c >= nc) return;
-  const CurvePlan p = plan[c];
-  const long long k = i - p.b_off;
-  if (k < 0 || k >= p.M || k % kCluster != 0 || (long long)p.b_off + p.M > bcap) return;
-  const int B = p.M;
-  float x0 = FLT_MAX, x1 = -FLT_MAX, y0 = FLT_MAX, y1 = -FLT_MAX;
-  for (int j = int(k); j < min(B, int(k) + kCluster); ++j) {
-    const float4 b0 = bloc[p.b_off + j];
-    const float4 b1 = bloc[p.b_off + (j + 1 == B ? 0 : j + 1)];
-    x0 = fminf(x0, fminf(b0.x, b1.x));
-    x1 = fmaxf(x1, fmaxf(b0.x, b1.x));
-    y0 = fminf(y0, fminf(b0.y, b1.y));
-    y1 = fmaxf(y1, fmaxf(b0.y, b1.y));
-  }
-  cbox[i] = make_float4(x0, x1, y0, y1);
-}
 
 // Distance from grid-local point q to the segment p0 -> p1 given as high and
 // low parts {x_hi, y_hi, x_lo, y_lo} (Eq. S1): q - p0 and p1 - p0 are formed
@@ -1145,12 +1131,9 @@ extern "C" ns_status nurbs_sample(const ns_curves* curves, const ns_sample_param
               at<int>(ws, L.o_bcurve),
               bloc, cap->boundary, static_cast<const int*>(boffs));
   int4* lbox = at<int4>(ws, L.o_lbox);
-  NS_LAUNCH(NS_KERNEL_OTHER, k_boundary_box, (nc + 7) / 8, 256, 0, s, *curves, *sp, plan, knots, bloc,
-            at<float2>(ws, L.o_glo), cap->boundary, lbox, st);
   float4* cbox = at<float4>(ws, L.o_cbox);
-  if (cap->boundary > 0)
-    NS_LAUNCH(NS_KERNEL_OTHER, k_cluster_boxes, int((cap->boundary + 255) / 256), 256, 0, s, plan,
-              at<const int>(ws, L.o_bcurve), bloc, st, cbox, cap->boundary, nc);
+  NS_LAUNCH(NS_KERNEL_OTHER, k_boundary_box, (nc + 7) / 8, 256, 0, s, *curves, *sp, plan, knots, bloc,
+            at<float2>(ws, L.o_glo), cap->boundary, lbox, st, cbox);
   const int ftile = fill_tile_of(sp->fill_tile);
   NS_LAUNCH(NS_KERNEL_SCAN, k_scan_gauss, 1, 1024, 0, s, nc, plan, order, st, cap->gaussians, out->count, ftile,
             at<int>(ws, L.o_bmix), (long long)L.bin_blocks);
@@ -1174,8 +1157,12 @@ extern "C" ns_status nurbs_sample(const ns_curves* curves, const ns_sample_param
     NS_LAUNCH(NS_KERNEL_FILL_SDF, k_fill_sdf<16>, num_sms() * 8, 256, 0, s, *curves, *sp, plan, order, bloc,
               at<const float2>(ws, L.o_glo), cbox, st, reinterpret_cast<float4*>(out->rec), out->curve, out->aux,
               cap->gaussians, cap->boundary, tmap, (long long)L.tcap, lbox);
-  NS_LAUNCH(NS_KERNEL_EMIT, k_emit, grid, 256, 0, s, *curves, *sp, plan, order, knots, st,
-            reinterpret_cast<float4*>(out->rec), out->curve, out->aux, cap->gaussians, tmap, (long long)L.tcap);
+  // the strokes' samples (none when the caller's hint says the batch holds fills only)
+  if (curves->stroke_degrees != 1)
+    NS_LAUNCH(NS_KERNEL_EMIT, k_emit, grid, 256, 0, s, *curves, *sp, plan, order, knots, st,
+              reinterpret_cast<float4*>(out->rec), out->curve, out->aux, cap->gaussians, tmap, (long long)L.tcap);
+  else
+    ::ns::empty_range(NS_KERNEL_EMIT, s);
   if (out->shape)
     NS_LAUNCH(NS_KERNEL_OTHER, k_emit_shape, grid, 256, 0, s, *curves, *sp, plan, knots, st,
               reinterpret_cast<const float4*>(out->rec), out->curve, reinterpret_cast<float4*>(out->shape));
