@@ -1811,7 +1811,7 @@ __device__ __forceinline__ void layer_prefetch(const LayerArgs& la, long long g_
                                                const int4& reg, float2* pts) {
   const int lane = threadIdx.x & 31;
   const int rw = reg.y - reg.x + 1, npt = rw * (reg.w - reg.z + 1);
-  const float inv_rw = 1.f / float(rw);
+  const float inv_rw = __fdividef(1.f, float(rw));   // the quotients below stay 0.5/rw off integers
   const float* op = reinterpret_cast<const float*>(la.rec) + 3;   // the records' opacities
 #pragma unroll
   for (int it = 0; it < kIt; ++it) {
@@ -2444,7 +2444,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
             // one vector reduction per quad of consecutive Gaussians (adding
             // zeros for the padding: other tiles' points, or none)
             const int qr = rs >> 2;
-            const float inv_qr = 1.f / float(qr);
+            const float inv_qr = __fdividef(1.f, float(qr));   // the quotients below stay 0.5/qr off integers
             for (int i = lane; i < rh * qr; i += 32) {
               const int r = int((float(i) + 0.5f) * inv_qr);   // exact for the region sizes staged here
               const int jq = i - r * qr;
@@ -2464,7 +2464,7 @@ __global__ void __launch_bounds__(BlendGeom<TILE, PPT>::kThreads, LayerGeom<TILE
               }
             }
           } else {
-            const float inv_rw = 1.f / float(rw);
+            const float inv_rw = __fdividef(1.f, float(rw));   // the quotients below stay 0.5/rw off integers
             for (int i = lane; i < rw * rh; i += 32) {
               const float val = s_reg[w][i];
               if (val != 0.f) {

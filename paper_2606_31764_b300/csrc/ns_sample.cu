@@ -883,7 +883,7 @@ __global__ void __launch_bounds__(TE * TE, 2048 / (TE * TE)) k_fill_sdf(ns_curve
     const long long g = (long long)pl.g_off + (long long)iy * pl.nx + ix;
     const bool valid = in_grid && g < gcap;
     const int tix0 = ix - (tid % TE), tiy0 = iy - (tid / TE);   // the tile's first column and row
-    const float h = sp.h;
+    const float h = sp.h, inv_h = 1.f / h;
     const float qx = (float(ix) + 0.5f) * h, qy = (float(iy) + 0.5f) * h;
     // the tile's point box
     const float tx0 = (float(tix0) + 0.5f) * h, tx1 = (float(min(pl.nx, tix0 + TE)) - 0.5f) * h;
@@ -933,8 +933,9 @@ __global__ void __launch_bounds__(TE * TE, 2048 / (TE * TE)) k_fill_sdf(ns_curve
       }
       if (ncl_cross && xhi >= tx0 - 0.01f) {
         // rows r of the tile with ylo <= qy_r < yhi (the straddle rule of the crossing test)
-        const int r0 = max(0, int(ceilf(ylo / h - 0.5f)) - tiy0 - 1);
-        const int r1 = min(TE - 1, int(ceilf(yhi / h - 0.5f)) - tiy0);
+        // (row bounds from the reciprocal of h with a margin: each row is tested exactly)
+        const int r0 = max(0, int(ceilf(ylo * inv_h - 0.5f - 1e-3f)) - tiy0 - 1);
+        const int r1 = min(TE - 1, int(ceilf(yhi * inv_h - 0.5f + 1e-3f)) - tiy0);
         for (int r = r0; r <= r1; ++r) {
           const float qyr = (float(tiy0 + r) + 0.5f) * h;
           if (ylo <= qyr && qyr < yhi) {
@@ -961,11 +962,16 @@ __global__ void __launch_bounds__(TE * TE, 2048 / (TE * TE)) k_fill_sdf(ns_curve
         const float y1 = s_ny1[buf][i];
         const float xlo = fminf(sg.x, sg.x + sg.z) - band, xhi = fmaxf(sg.x, sg.x + sg.z) + band;
         const float ylo = fminf(sg.y, y1) - band, yhi = fmaxf(sg.y, y1) + band;
-        const int ia = max(tix0, int(ceilf(xlo / h - 0.5f))), ib = min(tix0 + TE - 1, int(floorf(xhi / h - 0.5f)));
-        const int ja = max(tiy0, int(ceilf(ylo / h - 0.5f))), jb = min(tiy0 + TE - 1, int(floorf(yhi / h - 0.5f)));
+        // the band box in grid indices, from the reciprocal of h with a margin
+        // of 1e-3 (points it adds are outside the band: the distance test
+        // below rejects them)
+        const int ia = max(tix0, int(ceilf(xlo * inv_h - 0.5f - 1e-3f)));
+        const int ib = min(tix0 + TE - 1, int(floorf(xhi * inv_h - 0.5f + 1e-3f)));
+        const int ja = max(tiy0, int(ceilf(ylo * inv_h - 0.5f - 1e-3f)));
+        const int jb = min(tiy0 + TE - 1, int(floorf(yhi * inv_h - 0.5f + 1e-3f)));
         if (ia > ib || ja > jb) continue;
         const int w = ib - ia + 1, npts = w * (jb - ja + 1);
-        const float inv_w = 1.f / float(w);
+        const float inv_w = __fdividef(1.f, float(w));   // the quotients below stay 0.5/w off integers
         for (int p = lane; p < npts; p += 32) {
           const int py = int((float(p) + 0.5f) * inv_w);   // exact for the box sizes of a tile
           const int jx = ia + (p - py * w), jy = ja + py;
