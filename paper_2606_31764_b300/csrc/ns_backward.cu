@@ -169,6 +169,7 @@ __global__ void __launch_bounds__(256, 8) k_chain(ns_curves cv, ChainParams cp, 
   // current task runs; no block barrier: each thread handles its point, the
   // sums go out per warp
   int task = blockIdx.x;
+  const float gh = cp.gamma / cp.h;   // gamma / h of Eq. 7
   int c = task < n_tasks ? task_curve(cp.tmap, cp.tcap, n_tasks, plan, order, nc, task, true) : 0;
   FillTaskPlan pl = fill_task_plan(plan, c);
   for (; task < n_tasks; task += gridDim.x) {
@@ -220,12 +221,12 @@ __global__ void __launch_bounds__(256, 8) k_chain(ns_curves cv, ChainParams cp, 
         // sigmoid and its slope from E = exp(-|z|): s (1 - s) = E / (1 + E)^2 has no
         // cancellation inside the shape, where s rounds towards 1 and 1 - s in
         // float32 would keep only a few significant bits
-        const float z = cp.gamma / cp.h * sdf;
+        const float z = gh * sdf;
         const float E = __expf(-fabsf(z));
         const float inv = __fdividef(1.f, 1.f + E);
         const float sig = z >= 0.f ? inv : E * inv;
         dO = sig * gop;
-        const float dsdf = gop * o * (E * inv * inv) * (cp.gamma / cp.h);
+        const float dsdf = gop * o * (E * inv * inv) * gh;
         const float dd = inside ? dsdf : -dsdf;
         if (d > 0.f && dd != 0.f) {
           // d = |q - b0 - t e|, t at its optimum: dd/db0 = -(1-t) n, dd/db1 = -t n

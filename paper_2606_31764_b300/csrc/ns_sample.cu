@@ -703,14 +703,19 @@ __global__ void __launch_bounds__(256) k_emit_shape(ns_curves cv, ns_sample_para
 // low parts {x_hi, y_hi, x_lo, y_lo} (Eq. S1): q - p0 and p1 - p0 are formed
 // from the high parts first (exact for nearby points) and corrected by the
 // low parts, so a point near the polyline gets its distance to about 1e-7 px.
+// The projection parameter t takes the approximate quotient: at an interior
+// optimum the distance is stationary in t, so its error enters only to second
+// order; the distance takes the special-function unit's reciprocal square
+// root (about 1e-7 relative).
 __device__ __forceinline__ float seg_distance_hl(float qx, float qy, const float4& p0, const float4& p1) {
   const float rx = __fsub_rn(__fsub_rn(qx, p0.x), p0.z), ry = __fsub_rn(__fsub_rn(qy, p0.y), p0.w);
   const float ex = __fadd_rn(__fsub_rn(p1.x, p0.x), __fsub_rn(p1.z, p0.z));
   const float ey = __fadd_rn(__fsub_rn(p1.y, p0.y), __fsub_rn(p1.w, p0.w));
   const float ee = ex * ex + ey * ey;
-  const float t = ee > 0.f ? fminf(fmaxf((rx * ex + ry * ey) / ee, 0.f), 1.f) : 0.f;
+  const float t = ee > 0.f ? fminf(fmaxf(__fdividef(rx * ex + ry * ey, ee), 0.f), 1.f) : 0.f;
   const float dx = rx - t * ex, dy = ry - t * ey;
-  return sqrtf(dx * dx + dy * dy);
+  const float d2 = dx * dx + dy * dy;
+  return d2 > 0.f ? d2 * rsqrtf(d2) : 0.f;
 }
 
 // Persistent over the contour tasks: each block iteration handles 256 samples
@@ -1023,8 +1028,8 @@ __global__ void __launch_bounds__(TE * TE, 2048 / (TE * TE)) k_fill_sdf(ns_curve
       } else if (!deep) {
         const float d = seg_distance_hl(qx, qy, bl[arg], bl[arg + 1 == B ? 0 : arg + 1]);
         const float sdf = inside ? d : -d;
-        const float z = sp.gamma / h * sdf;
-        sig = 1.f / (1.f + __expf(-z));
+        const float z = sp.gamma * inv_h * sdf;
+        sig = __fdividef(1.f, 1.f + __expf(-z));   // 0 once exp(-z) overflows
       }
       const float2 lo = glo[c];
       const float oj = o * sig;
