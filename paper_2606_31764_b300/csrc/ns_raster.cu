@@ -1873,9 +1873,11 @@ struct LayerGeom {
   // 16 blocks of 2 warps per SM beat 12 blocks at 80 registers (a few bytes
   // of spills outside the walk)
   static constexpr int kMinBlocksBwd = 1024 / BlendGeom<TILE, PPT>::kThreads;
-  // the forward at 56 registers: 18 blocks of 2 warps per SM (at most 32 blocks)
+  // the forward at 56 registers: 18 blocks of 2 warps per SM; blocks of one
+  // warp (two pixels per thread) at 80 registers, 24 blocks per SM (at 64
+  // registers, 32 blocks, their pixel state spills)
   static constexpr int kMinBlocksFwd =
-      1152 / BlendGeom<TILE, PPT>::kThreads < 32 ? 1152 / BlendGeom<TILE, PPT>::kThreads : 32;
+      1152 / BlendGeom<TILE, PPT>::kThreads < 32 ? 1152 / BlendGeom<TILE, PPT>::kThreads : 24;
 };
 
 template <int TILE, int PPT, int C>
