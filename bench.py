@@ -43,20 +43,20 @@ PEAKS_FALLBACK = dict(hbm_gbs=6400.0, sm_max_mhz=2032.0)
 # the records it writes stay in L2, at 2048 they do not, so its traffic does
 # not grow in proportion.
 TRAFFIC = dict(
-    blend_bwd=dict(bytes=57676288, units=2027197, unit="gaussians", tile=8, layers=1,
-                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="8c7d900d4f6df113"),
-    blend_fwd=dict(bytes=27877376, units=2027197, unit="gaussians", tile=8, layers=1,
-                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="8c7d900d4f6df113"),
-    chain=dict(bytes=17377024, units=2027197, unit="gaussians", tile=None, layers=None,
-               src="paper_2606_31764_b300/csrc/ns_backward.cu", sha="01a669132abad508"),
-    bin_count=dict(bytes=340224, units=2027197, unit="gaussians", tile=8, layers=1,
-                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="8c7d900d4f6df113"),
-    bin_emit=dict(bytes=63488, units=2027197, unit="gaussians", tile=8, layers=1,
-                  src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="8c7d900d4f6df113"),
-    plan=dict(bytes=2102016, units=512, unit="curves", tile=None, layers=None,
-              src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="87451ed3e021526b"),
-    boundary=dict(bytes=1278976, units=512, unit="curves", tile=None, layers=None,
-                  src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="87451ed3e021526b"),
+    blend_bwd=dict(bytes=57382144, units=2027197, unit="gaussians", tile=8, layers=1,
+                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="848396ae473232c2"),
+    blend_fwd=dict(bytes=27754496, units=2027197, unit="gaussians", tile=8, layers=1,
+                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="848396ae473232c2"),
+    chain=dict(bytes=17374976, units=2027197, unit="gaussians", tile=None, layers=None,
+               src="paper_2606_31764_b300/csrc/ns_backward.cu", sha="cbd74131f2f815b2"),
+    bin_count=dict(bytes=51200, units=2027197, unit="gaussians", tile=8, layers=1,
+                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="848396ae473232c2"),
+    bin_emit=dict(bytes=52736, units=2027197, unit="gaussians", tile=8, layers=1,
+                  src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="848396ae473232c2"),
+    plan=dict(bytes=2104064, units=512, unit="curves", tile=None, layers=None,
+              src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="300f60bb328d7eff"),
+    boundary=dict(bytes=1276160, units=512, unit="curves", tile=None, layers=None,
+                  src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="300f60bb328d7eff"),
 )
 
 
