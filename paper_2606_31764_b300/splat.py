@@ -65,6 +65,17 @@ class Report:
     blend_bwd_visits: int = 0
 
 
+def stroke_degree_mask(degree, flags) -> int:
+    """The library's launch hint ns_curves.stroke_degrees from host copies of
+    the curves' degrees and flags: bit 0 set (the hint is given) and bit p for
+    every degree p among the curves that are not filled."""
+    mask = 1
+    for p, f in zip(list(degree), list(flags)):
+        if not (int(f) & B.NS_FILLED) and 1 <= int(p) <= 5:
+            mask |= 1 << int(p)
+    return mask
+
+
 class DeviceCurves:
     """The static curve tables of a scene batch on the device (int32 CSR)."""
 
@@ -80,13 +91,7 @@ class DeviceCurves:
         self.n_curves = int(scene.degree.shape[0])
         self.n_keys = int(scene.key.shape[0])
         self.n_taus = int(scene.tau.shape[0])
-        # the degrees of the strokes (curves that are not filled), as the
-        # library's launch hint: bit 0 = given, bit p = degree p present
-        mask = 1
-        for p, f in zip(scene.degree.tolist(), scene.flags.tolist()):
-            if not (int(f) & B.NS_FILLED) and 1 <= int(p) <= 5:
-                mask |= 1 << int(p)
-        self.stroke_degrees = mask
+        self.stroke_degrees = stroke_degree_mask(scene.degree, scene.flags)
 
     def struct_sizes(self) -> B.NsCurves:
         """The table with placeholder parameter pointers: enough for

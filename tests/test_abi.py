@@ -97,3 +97,23 @@ def test_geometry_loss_argument_errors_need_no_gpu():
                                   None, ws, C.c_size_t(1 << 20), None)
         assert st == binding.NS_ERR_INVALID_ARG
         assert word in lib.ns_last_error()
+
+
+def test_stroke_degree_hint_mask():
+    """The launch hint the Python tables give the library: bit 0 (given) and
+    one bit per degree among the curves that are not filled; a batch of fills
+    gives 1 (no stroke kernel to launch)."""
+    from paper_2606_31764_b300.splat import stroke_degree_mask
+    F, C = binding.NS_FILLED, binding.NS_CLOSED
+    assert stroke_degree_mask([2, 3, 5], [F | C, F | C, F | C]) == 1
+    assert stroke_degree_mask([2, 3, 5], [C, 0, F | C]) == 1 | (1 << 2) | (1 << 3)
+    assert stroke_degree_mask([1, 1, 4], [0, 0, C]) == 1 | (1 << 1) | (1 << 4)
+    assert stroke_degree_mask([], []) == 1
+
+
+def test_curve_table_carries_the_hint_last():
+    """ns_curves ends with the int32 launch hint after the colour pointer, so a
+    table built field by field (or zeroed) without it means 'not given'."""
+    names = [f[0] for f in binding.NsCurves._fields_]
+    assert names[-2:] == ["color", "stroke_degrees"]
+    assert binding.NsCurves().stroke_degrees == 0
