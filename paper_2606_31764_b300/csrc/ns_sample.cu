@@ -836,9 +836,12 @@ __global__ void __launch_bounds__(TE * TE, 2048 / (TE * TE)) k_fill_sdf(ns_curve
                                                      long long bcap, const int* __restrict__ tmap, long long tcap,
                                                      int4* lbox) {
   grid_dep_wait();
-  // The lists and keys alternate between two buffers from task to task: the
-  // points of one task clear the other buffer, so a task takes three block
-  // barriers (after the lists, after the band, after the points).
+  // The lists and keys alternate between two buffers from task to task, so a
+  // task takes two block barriers (after the lists, after the band): after
+  // the first barrier of a task every thread is past the previous task's
+  // points, and the previous task's buffer is cleared (its box added to its
+  // curve's) for the task after this one, which writes it only after this
+  // task's second barrier.
   // band segments listed per tile (a tile's band list beyond it falls back to
   // the search over the whole polyline): sized so that 2048 threads per SM fit
   constexpr int kNearCap = TE == 8 ? 64 : 256;
@@ -854,12 +857,29 @@ __global__ void __launch_bounds__(TE * TE, 2048 / (TE * TE)) k_fill_sdf(ns_curve
   const int n_fill = st->n_chunks;
   const int nc = cv.n_curves;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  s_key[0][tid] = ~0ull;
-  if (tid < TE) s_xcnt[0][tid] = 0;
-  if (tid == 0) s_nnear[0] = 0;
-  if (tid < 5) s_box[0][tid] = tid < 2 ? 0x7fffffff : (tid < 4 ? -1 : 0);
+  for (int b = 0; b < 2; ++b) {
+    s_key[b][tid] = ~0ull;
+    if (tid < TE) s_xcnt[b][tid] = 0;
+    if (tid == 0) s_nnear[b] = 0;
+    if (tid < 5) s_box[b][tid] = tid < 2 ? 0x7fffffff : (tid < 4 ? -1 : 0);
+  }
   __syncthreads();
   int buf = 0;
+  int prev_c = -1;   // the curve of the previous task, whose buffer (buf ^ 1) is not yet cleared
+  // one thread adds a task's box of live grid points and culled count to its
+  // curve's and resets the box
+  auto flush_box = [&](int cc, int* box) {
+    if (box[2] >= 0) {
+      atomicMin(&lbox[cc].x, box[0]);
+      atomicMin(&lbox[cc].y, box[1]);
+      atomicMax(&lbox[cc].z, box[2]);
+      atomicMax(&lbox[cc].w, box[3]);
+    }
+    if (box[4]) atomicAdd(&st->culled_s, (unsigned long long)box[4]);
+    box[0] = box[1] = 0x7fffffff;
+    box[2] = box[3] = -1;
+    box[4] = 0;
+  };
   // blocks claim runs of kSdfClaim consecutive tasks from a counter: the tiles
   // of a run mostly belong to one curve, whose polyline and cluster boxes then
   // stay in the SM's L1, and the claims balance the blocks' work
@@ -954,6 +974,15 @@ __global__ void __launch_bounds__(TE * TE, 2048 / (TE * TE)) k_fill_sdf(ns_curve
       }
     }
     __syncthreads();
+    if (prev_c >= 0) {   // the previous task's buffer: flushed and cleared
+      s_key[buf ^ 1][tid] = ~0ull;
+      if (tid < TE) s_xcnt[buf ^ 1][tid] = 0;
+      if (tid == 0) {
+        s_nnear[buf ^ 1] = 0;
+        flush_box(prev_c, s_box[buf ^ 1]);
+      }
+      prev_c = -1;
+    }
     const int nnear = s_nnear[buf];
     const bool near_ovf = nnear > kNearCap;
     unsigned long long* key = s_key[buf];
@@ -1059,24 +1088,13 @@ __global__ void __launch_bounds__(TE * TE, 2048 / (TE * TE)) k_fill_sdf(ns_curve
         if (nculled) atomicAdd(&s_box[buf][4], nculled);
       }
     }
-    // clear the other buffer for the next task
-    s_key[buf ^ 1][tid] = ~0ull;
-    if (tid < TE) s_xcnt[buf ^ 1][tid] = 0;
-    if (tid == 0) s_nnear[buf ^ 1] = 0;
-    if (tid < 5) s_box[buf ^ 1][tid] = tid < 2 ? 0x7fffffff : (tid < 4 ? -1 : 0);
-    __syncthreads();
-    if (tid == 0) {
-      if (s_box[buf][2] >= 0) {
-        atomicMin(&lbox[c].x, s_box[buf][0]);
-        atomicMin(&lbox[c].y, s_box[buf][1]);
-        atomicMax(&lbox[c].z, s_box[buf][2]);
-        atomicMax(&lbox[c].w, s_box[buf][3]);
-      }
-      if (s_box[buf][4]) atomicAdd(&st->culled_s, (unsigned long long)s_box[buf][4]);
-    }
+    prev_c = c;
     buf ^= 1;
     ++task;
   }
+  // the last task's box (every thread is past its points: the claim that
+  // ended the loop took two barriers)
+  if (prev_c >= 0 && tid == 0) flush_box(prev_c, s_box[buf ^ 1]);
 }
 
 }  // namespace ns
