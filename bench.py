@@ -53,10 +53,10 @@ TRAFFIC = dict(
                    src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="848396ae473232c2"),
     bin_emit=dict(bytes=52736, units=2027197, unit="gaussians", tile=8, layers=1,
                   src="paper_2606_31764_b300/csrc/ns_raster.cu", sha="848396ae473232c2"),
-    plan=dict(bytes=2104064, units=512, unit="curves", tile=None, layers=None,
-              src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="300f60bb328d7eff"),
-    boundary=dict(bytes=1276160, units=512, unit="curves", tile=None, layers=None,
-                  src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="300f60bb328d7eff"),
+    plan=dict(bytes=2103040, units=512, unit="curves", tile=None, layers=None,
+              src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="317e7b77fbcba6be"),
+    boundary=dict(bytes=1277696, units=512, unit="curves", tile=None, layers=None,
+                  src="paper_2606_31764_b300/csrc/ns_sample.cu", sha="317e7b77fbcba6be"),
 )
 
 
